@@ -1,0 +1,136 @@
+"""Pins of the oracle's HOLD integrator (Sec. 2.2, Algorithms 1-3): reduction to textbook
+KDK leapfrog, the Poisson-call count the paper prints, the schedule of kicks and drifts, a
+Kepler orbit, and momentum conservation to roundoff (Sec. 3.2.1)."""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1712_10116_gb300 import ics
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def test_rung_brackets_the_timestep():
+    dt_max = 1.0 / 64
+    for dt_i in [1.0, dt_max, dt_max * 0.99, dt_max / 2, dt_max / 2 * 0.999, 1e-4, 1e-9]:
+        k = oracle.rung(dt_i, dt_max, 30)
+        assert dt_max / 2 ** k <= dt_i or k == 30
+        if k > 0:
+            assert dt_i < dt_max / 2 ** (k - 1)
+    assert oracle.rung(1e-12, dt_max, 10) == 10
+    # dt_i = sqrt(eta eps / (|a_old| + |a_cur|)): fixed by the two magnitudes' sum
+    assert oracle.timestep(0.02, 0.01, 1.0, 3.0) == oracle.timestep(0.02, 0.01, 2.0, 2.0)
+    assert oracle.timestep(0.02, 0.01, 0.0, 4.0) == pytest.approx(0.5 * math.sqrt(0.02 * 0.01), rel=1e-15)
+    assert oracle.timestep(0.02, 0.01, 0.0, 0.0) == math.inf
+
+
+def test_single_rung_is_textbook_kdk():
+    # k_max = 0 keeps every particle on rung 0: Algorithms 1-3 reduce to kick-drift-kick
+    pos, vel, m = ics.plummer(300, 1001)
+    prm = oracle.params(p=4, theta=0.5, eps=0.01, kernel=oracle.PLUMMER, n_crit=16)
+    dt = 1.0 / 64
+    h = oracle.HHS(pos, vel, m, prm, eta=0.025, dt_max=dt, k_max=0)
+    x, v = pos.copy(), vel.copy()
+    for _ in range(4):
+        a, _ = oracle.fmm(x, m, prm)
+        v = v + a * (dt / 2)
+        x = x + v * dt
+        a, _ = oracle.fmm(x, m, prm)
+        v = v + a * (dt / 2)
+        stats, _ = h.step()
+        assert stats.poisson_calls == 2 and stats.max_rung == 0
+    assert np.array_equal(h.pos, x) and np.array_equal(h.vel, v)
+
+
+def _two_rung_system(k, eta=0.02, eps=1e-3):
+    """A circular binary that sits on rung k and 18 distant light particles on rung 0."""
+    mb, s = 0.1, 0.05
+    dt_bin = math.sqrt(eta * eps * s * s / mb)
+    dt_max = dt_bin * 2.0 ** (k - 0.5)
+    v = math.sqrt(mb / (2 * s))
+    ang = np.linspace(0, 2 * np.pi, 18, endpoint=False)
+    far = np.stack([10 * np.cos(ang), 10 * np.sin(ang), 0.3 * np.sin(3 * ang)])
+    pos = np.concatenate([np.array([[-s / 2, s / 2], [0, 0], [0, 0]]), far], axis=1)
+    vel = np.zeros_like(pos)
+    vel[1, 0], vel[1, 1] = -v, v
+    m = np.concatenate([[mb, mb], np.full(18, 0.8 / 18)])
+    return pos, vel, m, dt_max
+
+
+def _golden_calls():
+    rows = {}
+    for line in open(os.path.join(GOLDEN, "poisson_calls.txt")):
+        if line.startswith("#") or not line.strip():
+            continue
+        k, hhs, shared = map(int, line.split())
+        rows[k] = (hhs, shared)
+    return rows
+
+
+@pytest.mark.parametrize("k", [1, 2, 3, 4, 5])
+def test_poisson_calls_per_step_match_paper(k):
+    pos, vel, m, dt_max = _two_rung_system(k)
+    prm = oracle.params(p=4, theta=0.5, eps=1e-3, n_crit=8)
+    h = oracle.HHS(pos, vel, m, prm, eta=0.02, dt_max=dt_max, k_max=12)
+    want = _golden_calls()[k][0]
+    for _ in range(3):
+        stats, _ = h.step()
+        assert stats.max_rung == k
+        assert set(np.unique(h.rung)) == {0, k}
+        assert stats.poisson_calls == want
+
+
+def test_schedule_follows_algorithms_1_and_2():
+    pos, vel, m, dt_max = _two_rung_system(2)
+    prm = oracle.params(p=4, theta=0.5, eps=1e-3, n_crit=8)
+    h = oracle.HHS(pos, vel, m, prm, eta=0.02, dt_max=dt_max, k_max=12)
+    _, trace = h.step(trace_cap=256)
+    S2F, FS2S, DRIFT = 0, 1, 2
+    rung2_kdk = [(FS2S, 2, 2, 2), (DRIFT, 2, 2, 0), (FS2S, 2, 2, 2)]
+    empty_kdk = [(DRIFT, 1, 0, 0)]                      # rung 1 holds no slow particle
+    half = rung2_kdk + empty_kdk + rung2_kdk            # EVOLVE_HOLD(1, fast, ...) on the binary
+    kdk0 = [(S2F, 0, 2, 18), (FS2S, 0, 18, 20), (DRIFT, 0, 18, 0), (FS2S, 0, 18, 20), (S2F, 0, 2, 18)]
+    want = half + kdk0 + half
+    assert [tuple(r) for r in trace] == want
+
+
+def test_kepler_circular_orbit():
+    pos, vel, m, a = ics.two_body(1.0, 0.0)
+    prm = oracle.params(p=4, theta=0.5, eps=1e-4, n_crit=8)
+    dt_max = 1.0 / 64
+    h = oracle.HHS(pos, vel, m, prm, eta=0.02, dt_max=dt_max, k_max=10)
+    E0 = h.diagnostics()[6]
+    period = 2 * math.pi * a ** 1.5
+    nsteps = int(round(period / dt_max))
+    for _ in range(nsteps):
+        h.step()
+    # back near the start after one period; energy and the circular radius conserved
+    phase = 2 * math.pi * (nsteps * dt_max) / period
+    want = 0.5 * np.array([-math.cos(phase), -math.sin(phase), 0.0])
+    assert np.linalg.norm(h.pos[:, 0] - want) < 1e-4
+    sep = np.linalg.norm(h.pos[:, 1] - h.pos[:, 0])
+    assert sep == pytest.approx(1.0, abs=1e-5)
+    E1 = h.diagnostics()[6]
+    assert abs(E1 / E0 - 1) < 1e-6
+    assert set(np.unique(h.rung)) == {3}
+
+
+def test_momentum_conserved_over_multirung_run():
+    # Sec. 3.2.1: FMM + HHS conserves the total momentum to roundoff
+    pos, vel, m = ics.clustered(1200, 1007)
+    m = ics.random_masses(1200, 3)
+    vel = vel - (vel * m).sum(1, keepdims=True) / m.sum()
+    prm = oracle.params(p=4, theta=0.5, eps=0.002, n_crit=16)
+    h = oracle.HHS(pos, vel, m, prm, eta=0.02, dt_max=1.0 / 16, k_max=8)
+    P0 = (h.vel * m).sum(1)
+    scale = (np.abs(h.vel) * m).sum()
+    rungs = set()
+    for _ in range(3):
+        stats, _ = h.step()
+        rungs |= set(np.unique(h.rung).tolist())
+        P = (h.vel * m).sum(1)
+        assert np.abs(P - P0).max() < 1e-14 * max(scale, 1.0)
+    assert len(rungs) >= 3  # the run really used several rungs
