@@ -1,0 +1,339 @@
+"""Benchmark: particle-forces/s of the momentum-conserving FMM + HHS step on one GB300.
+
+Workload (default): cold collapse of a uniform-density sphere, N = 2^20, R = 1, at rest,
+Wendland C2 softening eps = 0.005, p = 6, theta = 0.5, kappa = 1, n_crit = 64, float32 P2P/M2L,
+HHS with eta = 0.025, k_max = 10 and dt_max = 1/16 (the t = 0 sphere then spans rungs 0-3).
+One step = one rung-0 step of EVOLVE_HOLD (every stage of the hot path: keys, sort, octree,
+P2M/M2M, walk, M2L, P2P, L2L/L2P, timestep split, kicks, drifts), starting each time from the
+same initial state.  A particle-force is one sink's acceleration from one FMM evaluation.
+
+Prints one JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle on a bounded
+sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "particle-forces/s (FMM+HHS, 1 GB300) at median force err <=1e-4; |sum m v| drift"
+WORKLOAD = "cold-collapse uniform sphere N=2^20, eps=0.005 Wendland C2, p=6, theta=0.5, fp32 P2P/M2L, " \
+           "HHS k_max=10 dt_max=1/16 eta=0.025 (one rung-0 step from t=0)"
+SM_COUNT = 152
+FP32_LANES_PER_SM = 128
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=1 << 20)
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample", type=int, default=512)
+    return ap.parse_args()
+
+
+def workload(n, seed=1002):
+    from paper_1712_10116_gb300 import ics
+    return ics.uniform_sphere(n, seed)
+
+
+PARAMS = dict(p=6, theta=0.5, eps=0.005, kernel=0, n_crit=64, kappa=1.0, eta=0.025, dt_max=1.0 / 16, k_max=10)
+
+
+# ---------------------------------------------------------------- clocks sampler
+class Clocks:
+    def __init__(self):
+        self.samples = []
+        self._stop = threading.Event()
+        self._th = None
+
+    def start(self):
+        def run():
+            q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+            while not self._stop.is_set():
+                try:
+                    out = subprocess.run(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                          "-i", os.environ.get("LOCAL_RANK", "0")],
+                                         capture_output=True, text=True, timeout=5).stdout.strip()
+                    if out:
+                        self.samples.append([x.strip() for x in out.split(",")])
+                except Exception:
+                    pass
+                self._stop.wait(0.2)
+        self._th = threading.Thread(target=run, daemon=True)
+        self._th.start()
+
+    def stop(self):
+        self._stop.set()
+        if self._th:
+            self._th.join(timeout=10)
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        mx = [float(s[2]) for s in self.samples if s[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for s in self.samples:
+            for k, nm in enumerate(names):
+                if len(s) > 5 + k and s[5 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(self.samples)}
+
+
+# ---------------------------------------------------------------- reference arm: the CPU oracle
+def cpu_oracle_rate(n, n_sample, seed=7):
+    import oracle
+    pos, _, mass = workload(n)
+    prm = oracle.params(p=PARAMS["p"], theta=PARAMS["theta"], eps=PARAMS["eps"], kernel=PARAMS["kernel"],
+                        n_crit=PARAMS["n_crit"], kappa=PARAMS["kappa"])
+    sample = np.random.default_rng(seed).choice(n, n_sample, replace=False)
+    t0 = time.perf_counter()
+    oracle.fmm_sample(pos, mass, prm, sample)
+    dt = time.perf_counter() - t0
+    return n_sample / dt, dt, oracle.num_threads()
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    n_sample = max(16, args.cpu_sample // 4)
+    times = []
+    for i in range(args.warmup + args.steps):
+        rate, dt, cores = cpu_oracle_rate(args.n, n_sample, seed=100 + i)
+        if i >= args.warmup:
+            times.append(dt)
+    value = n_sample * len(times) / sum(times)
+    sample_desc = f"oracle FMM (FP64, C, OpenMP) for {n_sample} random sinks of the N={args.n} sphere per step, " \
+                  f"tree + moments of all N included"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "particle-forces/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n": args.n, "l2": "cpu"},
+            "cpu_baseline": {"value": value, "unit": "particle-forces/s", "cores": cores, "kind": "oracle",
+                             "sample": sample_desc},
+            "e2e": {"value": value, "unit": "particle-forces/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- our arm
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_1712_10116_gb300 import binding as tg
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+
+    n = args.n
+    # replicas only: each rank integrates its own independent system (seed per rank)
+    pos0, vel0, mass0 = workload(n, seed=1002 + rank)
+    prec = tg.TG_PREC_FP32 if args.precision == "fp32" else tg.TG_PREC_FP64
+    prm = tg.Params(precision=prec, **PARAMS)
+    solver = tg.Solver(prm, stream)
+    P0 = torch.tensor(pos0, device=dev)
+    V0 = torch.tensor(vel0, device=dev)
+    M = torch.tensor(mass0, device=dev)
+    P = P0.clone()
+    V = V0.clone()
+    solver.hhs_init(P, V, M)
+    _, aold0, acur0 = tg.tg_hhs_state(solver.ctx, n, dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # 256 MB > 129 MB L2
+
+    def reset():
+        P.copy_(P0)
+        V.copy_(V0)
+        tg.tg_hhs_set_accel(solver.ctx, aold0, acur0)
+
+    d_start = solver.diagnostics()
+    for _ in range(args.warmup):
+        reset()
+        solver.hhs_step()
+    torch.cuda.synchronize()
+    tg.tg_set_profiling(solver.ctx, 1)
+    tg.tg_reset_stats(solver.ctx)
+    clocks = Clocks()
+    clocks.start()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    wall0 = time.perf_counter()
+    for k in range(args.steps):
+        reset()
+        flush.zero_()
+        ev[k][0].record(stream)
+        solver.hhs_step()
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    stats = solver.stats()
+    prof = tg.tg_get_profile(solver.ctx)
+    tg.tg_set_profiling(solver.ctx, 0)
+    d_end = solver.diagnostics()
+    # one extra (untimed) step with every launch timed, for the per-stage breakdown
+    tg.tg_reset_stats(solver.ctx)
+    tg.tg_set_profiling(solver.ctx, 2)
+    reset()
+    solver.hhs_step()
+    breakdown = {k: v["ms"] for k, v in tg.tg_get_profile(solver.ctx).items() if k != "_all"}
+    tg.tg_set_profiling(solver.ctx, 0)
+    t_dev = sum(step_ms) / 1e3
+    sinks = stats["sink_forces"]
+    if world > 1:
+        tt = torch.tensor([t_dev, float(sinks)], dtype=torch.float64, device=dev)
+        mx = tt.clone()
+        dist.all_reduce(mx[:1], op=dist.ReduceOp.MAX)
+        dist.all_reduce(tt[1:], op=dist.ReduceOp.SUM)
+        t_max, sinks_all = float(mx[0]), float(tt[1])
+    else:
+        t_max, sinks_all = t_dev, float(sinks)
+    value = sinks_all / t_max
+
+    # accuracy gate: one float32 evaluation of the initial state vs float64 direct summation
+    acc, _ = solver.fmm_forces(P0, M, want_pot=False)
+    sample = torch.tensor(np.random.default_rng(3).choice(n, 4096, replace=False), device=dev)
+    ad, _ = solver.direct_forces(P0, M, None, sample)
+    a = acc[:, sample]
+    err = (torch.linalg.norm(a - ad, dim=0) / torch.linalg.norm(ad, dim=0)).cpu().numpy()
+
+    # end to end through the C ABI with host buffers: pinned H2D of the state, the step, D2H
+    hP = P0.cpu().pin_memory()
+    hV = V0.cpu().pin_memory()
+    oP = torch.empty_like(hP).pin_memory()
+    oV = torch.empty_like(hV).pin_memory()
+    e2e_steps = max(1, min(args.steps, 3))
+    tg.tg_reset_stats(solver.ctx)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        P.copy_(hP, non_blocking=True)
+        V.copy_(hV, non_blocking=True)
+        tg.tg_hhs_set_accel(solver.ctx, aold0, acur0)
+        solver.hhs_step()
+        oP.copy_(P, non_blocking=True)
+        oV.copy_(V, non_blocking=True)
+        torch.cuda.synchronize()
+    e2e_t = time.perf_counter() - t0
+    e2e_sinks = solver.stats()["sink_forces"]
+    h2d = 2 * 3 * n * 8
+    d2h = 2 * 3 * n * 8
+
+    if rank != 0:
+        solver.close()
+        if world > 1:
+            dist.barrier()
+            dist.destroy_process_group()
+        return
+
+    # roofline of the dominant kernel (by live CUDA-event time)
+    clk = clocks.summary()
+    peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    sm_max = 2070.0
+    if os.path.exists(peaks_path):
+        try:
+            sm_max = float(json.load(open(peaks_path)).get("sm_max_mhz", 2070.0))
+        except Exception:
+            pass
+    fp32_peak_tflops = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    kernels = {k: v for k, v in prof.items() if v["launches"] > 0 and k != "_all"}
+    dom = max(kernels.items(), key=lambda kv: kv[1]["ms"])[0] if kernels else None
+    roof = None
+    if dom == "p2p":
+        flops = 30.0 * stats["p2p_pairs"]
+        achieved = flops / (kernels["p2p"]["ms"] / 1e3) / 1e12
+        roof = {"kernel": "p2p_mutual", "bound": "alu", "achieved": achieved, "peak": fp32_peak_tflops,
+                "unit": "TFLOP/s", "frac": achieved / fp32_peak_tflops, "traffic": None,
+                "per_launch": {"flops": flops / kernels["p2p"]["launches"],
+                               "ms": kernels["p2p"]["ms"] / kernels["p2p"]["launches"]}}
+    elif dom == "m2l":
+        flops = m2l_flops(PARAMS["p"], stats["m2l_pairs"], stats)
+        achieved = flops / (kernels["m2l"]["ms"] / 1e3) / 1e12
+        roof = {"kernel": "m2l_mutual", "bound": "alu", "achieved": achieved, "peak": fp32_peak_tflops,
+                "unit": "TFLOP/s", "frac": achieved / fp32_peak_tflops, "traffic": None,
+                "per_launch": {"flops": flops / kernels["m2l"]["launches"],
+                               "ms": kernels["m2l"]["ms"] / kernels["m2l"]["launches"]}}
+    cpu = None
+    if not args.no_cpu_baseline and world == 1 or (not args.no_cpu_baseline and rank == 0 and args.gpus == 1):
+        rate, dt, cores = cpu_oracle_rate(n, args.cpu_sample)
+        cpu = {"value": rate, "unit": "particle-forces/s", "cores": cores, "kind": "oracle",
+               "sample": f"oracle FMM (FP64) of {args.cpu_sample} random sinks of the same N={n} sphere, "
+                         f"tree + moments of all N included, {dt:.1f} s"}
+    mom_scale = float((M * V0.abs().sum(0)).sum()) or 1.0
+    line = {
+        "metric": METRIC, "value": value, "unit": "particle-forces/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32" if prec == tg.TG_PREC_FP32 else "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": n, "l2": "flushed (256 MB write) between timed steps",
+                   "parallelism": f"replicas x{world}", "kappa": PARAMS["kappa"], "n_crit": PARAMS["n_crit"]},
+        "accuracy": {"median_force_err_vs_fp64_direct": float(np.median(err)),
+                     "p99_force_err": float(np.percentile(err, 99)), "sample_sinks": int(sample.numel()),
+                     "momentum_drift_one_step": float(np.abs(d_end[:3] - d_start[:3]).max()),
+                     "momentum_scale": mom_scale},
+        "work": {"sink_forces_per_step": sinks / args.steps, "evaluations_per_step": stats["evaluations"] / args.steps,
+                 "p2p_pairs_per_step": stats["p2p_pairs"] / args.steps,
+                 "m2l_pairs_per_step": stats["m2l_pairs"] / args.steps, "max_rung": stats["max_rung"]},
+        "kernels_ms_per_step": {k: v["ms"] / args.steps for k, v in kernels.items() if v["ms"] > 0},
+        "stage_ms_one_step_all_timed": breakdown,
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_sinks / e2e_t, "unit": "particle-forces/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": int(prof.get("_all", {}).get("launches", 0)),
+        "clocks": clk,
+        "wall_s_timed": wall,
+    }
+    print(json.dumps(line), flush=True)
+    solver.close()
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def m2l_flops(p, pairs, stats):
+    # triangular terms: D-recurrence ~ 3 C(p+4,4) flops once per pair; contraction C(p+6,6) FMAs per
+    # direction and sink class (2 flops each); classes: 1 without masks, 2 with (counted as 1.5 avg)
+    from math import comb
+    d = 3 * comb(p + 4, 4)
+    contr = 2 * 2 * comb(p + 6, 6)
+    return pairs * (d + contr)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,181 @@
+/*
+ * taichi_gb.h -- C ABI of the GB300 (sm_103a) momentum-conserving FMM + HHS library.
+ *
+ * The method is Zhu (2017), "A momentum conserving N-body scheme with individual
+ * timesteps": a fast multipole gravity solver whose cell-cell (M2L) and particle-particle
+ * (P2P) interactions are evaluated mutually (F_AB = -F_BA, Sec. 2.1, Eq. 2), driven by the
+ * hierarchical Hamiltonian splitting (HOLD) integrator with individual timesteps
+ * (Sec. 2.2, Algorithms 1-3).  Every step runs in CUDA kernels of this library.
+ *
+ * Conventions for every entry point
+ *   - Particle arrays are CALLER-OWNED DEVICE memory (e.g. torch CUDA tensors), in the caller's
+ *     particle order.  Positions, velocities and accelerations are SoA float64 arrays of
+ *     3*n doubles: x[0..n), y[0..n), z[0..n).  Masses are n float64 values.
+ *   - G = 1; potentials are negative (-m/r far from a mass).
+ *   - The context owns all scratch memory (tree, lists, expansions) and grows it on demand.
+ *   - All work is issued on the CUDA stream given to tg_create.  Calls return when the work is
+ *     enqueued, except where a call is documented as synchronising.
+ *   - Errors are returned as tg_status codes; no exception crosses the ABI.  On an argument
+ *     error nothing is launched and outputs are untouched.  tg_last_error() gives a message.
+ *   - A context is not thread-safe; use one context per host thread.
+ */
+#ifndef TAICHI_GB_H
+#define TAICHI_GB_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    TG_OK = 0,
+    TG_ERR_ARG = -1,        /* invalid argument (null pointer, n < 0, p out of range, ...)  */
+    TG_ERR_OOM = -2,        /* device allocation failed                                     */
+    TG_ERR_CUDA = -3,       /* a CUDA runtime call or kernel launch failed                  */
+    TG_ERR_TIMEOUT = -4,    /* a bounded device-side wait gave up                           */
+    TG_ERR_NONFINITE = -5,  /* non-finite positions or masses                               */
+    TG_ERR_CAPACITY = -6,   /* an internal list exceeded its limit even after regrowth      */
+    TG_ERR_STATE = -7       /* call out of order (e.g. tg_hhs_step before tg_hhs_init)       */
+} tg_status;
+
+typedef enum {
+    TG_KERNEL_WENDLAND_C2 = 0,  /* Eq. (8), Sec. 2.3; cell pairs closer than eps use P2P      */
+    TG_KERNEL_PLUMMER = 1       /* phi = -1/sqrt(r^2 + eps^2); expansions of that kernel       */
+} tg_kernel;
+
+typedef enum {
+    TG_PREC_FP64 = 0,  /* plain path: every stage in float64                               */
+    TG_PREC_FP32 = 1   /* P2P, M2L, L2L, L2P in float32 relative to float32 cell centres;   */
+                       /* moments, drift, reductions and outputs in float64                */
+} tg_precision;
+
+typedef struct {
+    int p;            /* expansion order: Taylor terms of total degree <= p, 1 <= p <= 8      */
+    int n_crit;       /* a cell holding more than n_crit particles is split (Sec. 2.3), 1..128 */
+    int kernel;       /* tg_kernel                                                          */
+    int precision;    /* tg_precision                                                       */
+    int max_level;    /* deepest octree level, 1..21 (21 = Morton-key resolution)           */
+    int k_max;        /* deepest HHS rung (timestep dt_max / 2^k_max), 0..30                 */
+    double theta;     /* opening angle of Eq. (1), > 0                                       */
+    double kappa;     /* R in Eq. (1) = kappa * cell side; the paper's reading is kappa = 1  */
+    double eps;       /* softening length, > 0                                               */
+    double eta;       /* timestep parameter: dt_i = sqrt(eta * eps / |a|), Sec. 2.2          */
+    double dt_max;    /* step of rung 0                                                      */
+} tg_params;
+
+typedef struct tg_ctx tg_ctx;
+
+/* Counters of the work done since tg_create or the last tg_reset_stats (host copies). */
+typedef struct {
+    int64_t evaluations;     /* FMM evaluations (one per tg_fmm_forces / kick pair)            */
+    int64_t sink_forces;     /* particle forces delivered (particle-forces, the throughput unit) */
+    int64_t p2p_pairs;       /* unordered particle pairs evaluated by P2P (F-F pairs excluded)   */
+    int64_t m2l_pairs;       /* unordered cell pairs evaluated by M2L                           */
+    int64_t p2p_cell_pairs;  /* unordered leaf pairs (self pairs included)                      */
+    int64_t cells;           /* octree cells built, summed over evaluations                    */
+    int64_t kdk_frames;      /* KDK frames of the HHS schedule                                  */
+    int64_t max_rung;        /* deepest rung that held a slow particle                          */
+} tg_stats;
+
+/* Create a context bound to `cuda_stream` (a cudaStream_t, NULL = legacy default stream) on the
+ * current device.  Validates params (TG_ERR_ARG).  Allocates only small control blocks. */
+tg_status tg_create(const tg_params *params, void *cuda_stream, tg_ctx **out);
+tg_status tg_destroy(tg_ctx *ctx);
+const char *tg_last_error(const tg_ctx *ctx);
+tg_status tg_get_stats(const tg_ctx *ctx, tg_stats *out);
+tg_status tg_reset_stats(tg_ctx *ctx);
+
+/* Root cube, Morton keys, radix sort and octree of n particles (Sec. 2.3), kept in the context
+ * for tg_get_tree / tg_get_lists.  pos: device, 3*n float64.  Synchronising. */
+tg_status tg_build_tree(tg_ctx *ctx, int64_t n, const double *pos);
+
+/* One FMM evaluation: the Poisson-solver call of Algorithm 3 (get_force_potential), with the
+ * mutual M2L/P2P of Sec. 2.1 and the Algorithm 4 walk.
+ *   pos     device, 3*n float64 (SoA)
+ *   mass    device, n float64
+ *   is_fast device, n uint8 or NULL.  NULL: every particle feels every mass.  Otherwise the
+ *           particles with is_fast[i] != 0 form the fast set F: slow sinks feel all masses
+ *           (kickFS2S) and fast sinks feel slow masses only (kickS2F) -- one kick pair of
+ *           Algorithm 2 evaluated on a single tree and walk.
+ *   acc     device, 3*n float64 output (SoA), overwritten
+ *   pot     device, n float64 output or NULL
+ * Not synchronising (host reads of list sizes aside). */
+tg_status tg_fmm_forces(tg_ctx *ctx, int64_t n, const double *pos, const double *mass,
+                        const uint8_t *is_fast, double *acc, double *pot);
+
+/* Direct O(N^2) float64 summation for n_sink sinks (sink_idx device int64[n_sink], NULL = the
+ * first n_sink particles) from all n sources, with the same kernel and mask semantics as
+ * tg_fmm_forces.  acc: device 3*n_sink float64 (SoA); pot: device n_sink float64 or NULL.
+ * Used to measure FMM force errors on a sample of sinks. */
+tg_status tg_direct_forces(tg_ctx *ctx, int64_t n, const double *pos, const double *mass,
+                           const uint8_t *is_fast, int64_t n_sink, const int64_t *sink_idx,
+                           double *acc, double *pot);
+
+/* HOLD integrator (Sec. 2.2).  tg_hhs_init binds caller-owned device arrays pos (3*n), vel (3*n)
+ * and mass (n) to the context; they are updated in place by every tg_hhs_step and must stay
+ * allocated until tg_destroy or the next tg_hhs_init.  It performs the initial all-from-all
+ * evaluation that sets |a_current|; |a_old| starts at 0. */
+tg_status tg_hhs_init(tg_ctx *ctx, int64_t n, double *pos, double *vel, const double *mass);
+/* One rung-0 step of EVOLVE_HOLD (Algorithm 1) of length params.dt_max: recursive
+ * slow/fast split, KDK (Algorithm 2) with the kickS2F/kickFS2S pairs of Algorithm 3, drifts.
+ * Synchronising (the recursion reads the set sizes of each split). */
+tg_status tg_hhs_step(tg_ctx *ctx);
+/* Per-particle HHS state (device outputs, each nullable): rung (int32 n), |a_old| and
+ * |a_current| (float64 n).  Synchronising. */
+tg_status tg_hhs_state(tg_ctx *ctx, int32_t *rung, double *a_old, double *a_cur);
+/* Set the per-particle |a_old| and |a_current| (device float64 n each). */
+tg_status tg_hhs_set_accel(tg_ctx *ctx, const double *a_old, const double *a_cur);
+
+/* Conservation diagnostics of the bound HHS system (Sec. 3.2): out[0..2] = total momentum
+ * sum m v, out[3..5] = angular momentum sum m x cross v, out[6] = total energy
+ * sum m v^2/2 + sum m phi/2 (phi from a fresh all-from-all evaluation), out[7] = time.
+ * float64 device reductions.  Synchronising; out is host memory. */
+tg_status tg_diagnostics(tg_ctx *ctx, double out[8]);
+
+/* ---- test hooks (synchronising; outputs are HOST memory sized by the *_count calls) ---- */
+
+/* Geometry of the last tree: lo[3], L (root cube side), n, number of cells. */
+tg_status tg_tree_info(tg_ctx *ctx, double lo[3], double *L, int64_t *n, int64_t *n_cells);
+/* Sorted keys (uint64 n), permutation (int64 n: sorted position -> particle index) and cells
+ * (level int32, integer coords int64 3*nc SoA, first/count int64 nc, nchild int32 nc). */
+tg_status tg_get_tree(tg_ctx *ctx, uint64_t *keys, int64_t *perm, int32_t *level, int64_t *coords,
+                      int64_t *first, int64_t *count, int32_t *nchild);
+/* Unordered interaction lists of the last walk (cell ids as in tg_get_tree): counts first,
+ * then pairs (int64 a[], b[]). */
+tg_status tg_list_counts(tg_ctx *ctx, int64_t *n_m2l, int64_t *n_p2p);
+tg_status tg_get_lists(tg_ctx *ctx, int64_t *m2l_a, int64_t *m2l_b, int64_t *p2p_a, int64_t *p2p_b);
+
+/* ---- live kernel timing (CUDA events on the context's stream) ---- */
+typedef enum {
+    TG_K_TREE = 0,   /* root cube, Morton keys, radix sort, gather, octree build            */
+    TG_K_UP = 1,     /* leaf offsets, P2M, M2M                                             */
+    TG_K_WALK = 2,   /* dual tree walk (Algorithm 4)                                        */
+    TG_K_M2L = 3,    /* mutual cell-cell interaction                                        */
+    TG_K_P2P = 4,    /* mutual particle-particle interaction                                */
+    TG_K_DOWN = 5,   /* L2L, L2P, scatter to caller order                                   */
+    TG_K_HHS = 6,    /* timestep, split, kick, drift                                        */
+    TG_K_OTHER = 7,  /* scans, reductions, direct summation                                 */
+    TG_K_COUNT = 8
+} tg_kernel_class;
+
+typedef struct {
+    double ms[TG_K_COUNT];        /* summed event time per class (classes being timed only)  */
+    int64_t launches[TG_K_COUNT]; /* kernel launches per class (always counted)              */
+} tg_profile;
+
+/* level 0: off; 1: time the M2L and P2P launches; 2: time every launch.  Launch counts are
+ * always kept.  Timing adds an event record before and after each timed launch. */
+tg_status tg_set_profiling(tg_ctx *ctx, int level);
+/* Totals since the last tg_reset_stats.  Synchronising. */
+tg_status tg_get_profile(tg_ctx *ctx, tg_profile *out);
+
+/* Timestep kernel alone (Sec. 2.2): dt[i] = sqrt(eta*eps/(a_old[i] + a_cur[i])) and
+ * rung[i] = smallest k with dt_max/2^k <= dt[i], capped at k_max.  Device arrays. */
+tg_status tg_timesteps(tg_ctx *ctx, int64_t n, const double *a_old, const double *a_cur,
+                       double *dt, int32_t *rung);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,362 @@
+// capi.cu -- the extern "C" entry points declared in include/taichi_gb.h.
+#include <cmath>
+#include <cstring>
+#include <new>
+
+#include "tg_common.cuh"
+
+using namespace tg;
+
+namespace {
+
+tg_status validate(const tg_params *p, std::string &why)
+{
+    if (!p) {
+        why = "params is NULL";
+        return TG_ERR_ARG;
+    }
+    if (p->p < 1 || p->p > kPMaxGpu) why = "p must be in [1, 8]";
+    else if (p->n_crit < 1 || p->n_crit > kMaxNcrit) why = "n_crit must be in [1, 128]";
+    else if (p->kernel != TG_KERNEL_WENDLAND_C2 && p->kernel != TG_KERNEL_PLUMMER) why = "unknown kernel";
+    else if (p->precision != TG_PREC_FP64 && p->precision != TG_PREC_FP32) why = "unknown precision";
+    else if (p->max_level < 1 || p->max_level > kMaxLevel) why = "max_level must be in [1, 21]";
+    else if (p->k_max < 0 || p->k_max > 30) why = "k_max must be in [0, 30]";
+    else if (!(p->theta > 0.0) || !std::isfinite(p->theta)) why = "theta must be > 0";
+    else if (!(p->kappa > 0.0) || !std::isfinite(p->kappa)) why = "kappa must be > 0";
+    else if (!(p->eps > 0.0) || !std::isfinite(p->eps)) why = "eps must be > 0";
+    else if (!(p->eta > 0.0) || !std::isfinite(p->eta)) why = "eta must be > 0";
+    else if (!(p->dt_max > 0.0) || !std::isfinite(p->dt_max)) why = "dt_max must be > 0";
+    return why.empty() ? TG_OK : TG_ERR_ARG;
+}
+
+tg_status begin(tg_ctx *c)
+{
+    if (!c) return TG_ERR_ARG;
+    c->err = Err{};
+    return TG_OK;
+}
+
+int check_device_ptr(const void *p)
+{
+    if (!p) return 0;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+}  // namespace
+
+extern "C" {
+
+tg_status tg_create(const tg_params *params, void *cuda_stream, tg_ctx **out)
+{
+    if (!out) return TG_ERR_ARG;
+    *out = nullptr;
+    std::string why;
+    tg_status st = validate(params, why);
+    if (st) return st;
+    tg_ctx *c = new (std::nothrow) tg_ctx();
+    if (!c) return TG_ERR_OOM;
+    c->prm = *params;
+    c->stream = static_cast<cudaStream_t>(cuda_stream);
+    if (cudaGetDevice(&c->device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess) {
+        cudaGetLastError();
+        delete c;
+        return TG_ERR_CUDA;
+    }
+    if (cudaMalloc(&c->d_counters, 16 * sizeof(unsigned long long)) != cudaSuccess) {
+        cudaGetLastError();
+        delete c;
+        return TG_ERR_OOM;
+    }
+    if (cudaMallocHost(&c->h_pinned, 64 * sizeof(int64_t)) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(c->d_counters);
+        delete c;
+        return TG_ERR_OOM;
+    }
+    cudaMemset(c->d_counters, 0, 16 * sizeof(unsigned long long));
+    std::memset(c->h_pinned, 0, 64 * sizeof(int64_t));
+    *out = c;
+    return TG_OK;
+}
+
+tg_status tg_destroy(tg_ctx *c)
+{
+    if (!c) return TG_ERR_ARG;
+    cudaStreamSynchronize(c->stream);
+    for (auto &b : c->buf)
+        if (b.p) cudaFree(b.p);
+    for (cudaEvent_t e : c->prof_events) cudaEventDestroy(e);
+    if (c->d_counters) cudaFree(c->d_counters);
+    if (c->h_pinned) cudaFreeHost(c->h_pinned);
+    delete c;
+    return TG_OK;
+}
+
+const char *tg_last_error(const tg_ctx *c)
+{
+    if (!c) return "null context";
+    return c->err.msg.c_str();
+}
+
+tg_status tg_get_stats(const tg_ctx *c, tg_stats *out)
+{
+    if (!c || !out) return TG_ERR_ARG;
+    tg_ctx *m = const_cast<tg_ctx *>(c);
+    unsigned long long pairs = 0;
+    cudaStreamSynchronize(m->stream);
+    if (cudaMemcpy(&pairs, m->d_counters, sizeof pairs, cudaMemcpyDeviceToHost) != cudaSuccess) {
+        cudaGetLastError();
+        return TG_ERR_CUDA;
+    }
+    *out = c->stats;
+    out->p2p_pairs = (int64_t)pairs;
+    return TG_OK;
+}
+
+tg_status tg_set_profiling(tg_ctx *c, int level)
+{
+    if (!c || level < 0 || level > 2) return TG_ERR_ARG;
+    prof_collect(c);
+    c->prof_level = level;
+    return TG_OK;
+}
+
+tg_status tg_get_profile(tg_ctx *c, tg_profile *out)
+{
+    if (!c || !out) return TG_ERR_ARG;
+    tg_status st = prof_collect(c);
+    if (st) return st;
+    for (int k = 0; k < TG_K_COUNT; ++k) {
+        out->ms[k] = c->prof_ms[k];
+        out->launches[k] = c->prof_launches[k];
+    }
+    return TG_OK;
+}
+
+tg_status tg_reset_stats(tg_ctx *c)
+{
+    if (!c) return TG_ERR_ARG;
+    prof_collect(c);
+    for (int k = 0; k < TG_K_COUNT; ++k) {
+        c->prof_ms[k] = 0.0;
+        c->prof_launches[k] = 0;
+    }
+    c->stats = tg_stats{};
+    cudaMemsetAsync(c->d_counters, 0, sizeof(unsigned long long), c->stream);
+    return TG_OK;
+}
+
+tg_status tg_build_tree(tg_ctx *c, int64_t n, const double *pos)
+{
+    tg_status st = begin(c);
+    if (st) return st;
+    if (n <= 0 || n > INT32_MAX / 4 || !check_device_ptr(pos))
+        return set_err(c, TG_ERR_ARG, "tg_build_tree: need n > 0 and a device pointer");
+    Geom *g;
+    if ((st = ensure_t(c, B_GEOM, 1, &g)) || (st = root_cube(c, (int)n, pos, n, nullptr, g))) return st;
+    // masses are not needed for the tree; gather reads a dummy unit array
+    double *ones;
+    if ((st = ensure_t(c, B_DIAG_POT, n, &ones))) return st;
+    cudaMemsetAsync(ones, 0, sizeof(double) * n, c->stream);
+    if ((st = keys_sort_gather(c, (int)n, pos, n, nullptr, ones, nullptr, g))) return st;
+    int ncell = 0;
+    if ((st = build_octree(c, (int)n, &ncell))) return st;
+    c->last_n = n;
+    c->last_ncell = ncell;
+    c->last_nm2l = c->last_np2p = 0;
+    return cuda_check(c, cudaStreamSynchronize(c->stream), "tg_build_tree");
+}
+
+tg_status tg_fmm_forces(tg_ctx *c, int64_t n, const double *pos, const double *mass, const uint8_t *is_fast,
+                        double *acc, double *pot)
+{
+    tg_status st = begin(c);
+    if (st) return st;
+    if (n < 0 || n > INT32_MAX / 4) return set_err(c, TG_ERR_ARG, "tg_fmm_forces: n out of range");
+    if (n == 0) return TG_OK;
+    if (!check_device_ptr(pos) || !check_device_ptr(mass) || !check_device_ptr(acc) ||
+        (is_fast && !check_device_ptr(is_fast)) || (pot && !check_device_ptr(pot)))
+        return set_err(c, TG_ERR_ARG, "tg_fmm_forces: arrays must be device memory");
+    return fmm_eval(c, (int)n, pos, n, nullptr, mass, is_fast, acc, n, pot, true);
+}
+
+tg_status tg_direct_forces(tg_ctx *c, int64_t n, const double *pos, const double *mass, const uint8_t *is_fast,
+                           int64_t n_sink, const int64_t *sink_idx, double *acc, double *pot)
+{
+    tg_status st = begin(c);
+    if (st) return st;
+    if (n < 0 || n_sink < 0 || (sink_idx == nullptr && n_sink > n))
+        return set_err(c, TG_ERR_ARG, "tg_direct_forces: bad sizes");
+    if (n_sink == 0) return TG_OK;
+    if (!check_device_ptr(pos) || !check_device_ptr(mass) || !check_device_ptr(acc) ||
+        (sink_idx && !check_device_ptr(sink_idx)) || (is_fast && !check_device_ptr(is_fast)))
+        return set_err(c, TG_ERR_ARG, "tg_direct_forces: arrays must be device memory");
+    return direct_eval(c, n, pos, mass, is_fast, n_sink, sink_idx, acc, pot);
+}
+
+tg_status tg_hhs_init(tg_ctx *c, int64_t n, double *pos, double *vel, const double *mass)
+{
+    tg_status st = begin(c);
+    if (st) return st;
+    if (n <= 0 || n > INT32_MAX / 4 || !check_device_ptr(pos) || !check_device_ptr(vel) || !check_device_ptr(mass))
+        return set_err(c, TG_ERR_ARG, "tg_hhs_init: need n > 0 and device arrays");
+    c->hhs_n = n;
+    c->hhs_pos = pos;
+    c->hhs_vel = vel;
+    c->hhs_mass = mass;
+    st = hhs_init(c);
+    if (st) c->hhs_n = 0;
+    return st;
+}
+
+tg_status tg_hhs_step(tg_ctx *c)
+{
+    tg_status st = begin(c);
+    if (st) return st;
+    if (c->hhs_n <= 0) return set_err(c, TG_ERR_STATE, "tg_hhs_step before tg_hhs_init");
+    return hhs_step(c);
+}
+
+tg_status tg_hhs_state(tg_ctx *c, int32_t *rung, double *a_old, double *a_cur)
+{
+    tg_status st = begin(c);
+    if (st) return st;
+    if (c->hhs_n <= 0) return set_err(c, TG_ERR_STATE, "tg_hhs_state before tg_hhs_init");
+    const size_t n = (size_t)c->hhs_n;
+    if (rung) cudaMemcpyAsync(rung, c->buf[B_HHS_RUNG].p, n * sizeof(int32_t), cudaMemcpyDeviceToDevice, c->stream);
+    if (a_old) cudaMemcpyAsync(a_old, c->buf[B_HHS_AOLD].p, n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream);
+    if (a_cur) cudaMemcpyAsync(a_cur, c->buf[B_HHS_ACUR].p, n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream);
+    return cuda_check(c, cudaStreamSynchronize(c->stream), "tg_hhs_state");
+}
+
+tg_status tg_hhs_set_accel(tg_ctx *c, const double *a_old, const double *a_cur)
+{
+    tg_status st = begin(c);
+    if (st) return st;
+    if (c->hhs_n <= 0) return set_err(c, TG_ERR_STATE, "tg_hhs_set_accel before tg_hhs_init");
+    if (!check_device_ptr(a_old) || !check_device_ptr(a_cur)) return set_err(c, TG_ERR_ARG, "device arrays expected");
+    const size_t n = (size_t)c->hhs_n;
+    cudaMemcpyAsync(c->buf[B_HHS_AOLD].p, a_old, n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream);
+    cudaMemcpyAsync(c->buf[B_HHS_ACUR].p, a_cur, n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream);
+    return cuda_check(c, cudaGetLastError(), "tg_hhs_set_accel");
+}
+
+tg_status tg_diagnostics(tg_ctx *c, double out[8])
+{
+    tg_status st = begin(c);
+    if (st) return st;
+    if (!out) return set_err(c, TG_ERR_ARG, "out is NULL");
+    if (c->hhs_n <= 0) return set_err(c, TG_ERR_STATE, "tg_diagnostics before tg_hhs_init");
+    return hhs_diagnostics(c, out);
+}
+
+tg_status tg_tree_info(tg_ctx *c, double lo[3], double *L, int64_t *n, int64_t *n_cells)
+{
+    tg_status st = begin(c);
+    if (st) return st;
+    if (c->last_n <= 0) return set_err(c, TG_ERR_STATE, "no tree built yet");
+    Geom g;
+    cudaError_t e = cudaMemcpyAsync(&g, c->buf[B_GEOM].p, sizeof g, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_check(c, e, "tg_tree_info");
+    if (lo) {
+        lo[0] = g.lo[0];
+        lo[1] = g.lo[1];
+        lo[2] = g.lo[2];
+    }
+    if (L) *L = g.L;
+    if (n) *n = c->last_n;
+    if (n_cells) *n_cells = c->last_ncell;
+    return TG_OK;
+}
+
+tg_status tg_get_tree(tg_ctx *c, uint64_t *keys, int64_t *perm, int32_t *level, int64_t *coords, int64_t *first,
+                      int64_t *count, int32_t *nchild)
+{
+    tg_status st = begin(c);
+    if (st) return st;
+    if (c->last_n <= 0) return set_err(c, TG_ERR_STATE, "no tree built yet");
+    const size_t n = (size_t)c->last_n, nc = (size_t)c->last_ncell;
+    std::vector<uint32_t> p32(n), cx(nc), cy(nc), cz(nc);
+    std::vector<uint8_t> lv(nc), nch(nc);
+    std::vector<int32_t> f(nc), cnt(nc);
+    cudaError_t e = cudaSuccess;
+    auto cp = [&](void *dst, int slot, size_t bytes) {
+        if (e == cudaSuccess) e = cudaMemcpyAsync(dst, c->buf[slot].p, bytes, cudaMemcpyDeviceToHost, c->stream);
+    };
+    if (keys) cp(keys, B_KEYS0, n * sizeof(uint64_t));
+    cp(p32.data(), B_VALS0, n * sizeof(uint32_t));
+    cp(lv.data(), B_C_LEVEL, nc);
+    cp(cx.data(), B_C_X, nc * 4);
+    cp(cy.data(), B_C_Y, nc * 4);
+    cp(cz.data(), B_C_Z, nc * 4);
+    cp(f.data(), B_C_FIRST, nc * 4);
+    cp(cnt.data(), B_C_COUNT, nc * 4);
+    cp(nch.data(), B_C_NCHILD, nc);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_check(c, e, "tg_get_tree");
+    for (size_t s = 0; s < n; ++s)
+        if (perm) perm[s] = p32[s];
+    for (size_t i = 0; i < nc; ++i) {
+        if (level) level[i] = lv[i];
+        if (coords) {
+            coords[i] = cx[i];
+            coords[nc + i] = cy[i];
+            coords[2 * nc + i] = cz[i];
+        }
+        if (first) first[i] = f[i];
+        if (count) count[i] = cnt[i];
+        if (nchild) nchild[i] = nch[i];
+    }
+    return TG_OK;
+}
+
+tg_status tg_list_counts(tg_ctx *c, int64_t *n_m2l, int64_t *n_p2p)
+{
+    tg_status st = begin(c);
+    if (st) return st;
+    if (n_m2l) *n_m2l = c->last_nm2l;
+    if (n_p2p) *n_p2p = c->last_np2p;
+    return TG_OK;
+}
+
+tg_status tg_get_lists(tg_ctx *c, int64_t *m2l_a, int64_t *m2l_b, int64_t *p2p_a, int64_t *p2p_b)
+{
+    tg_status st = begin(c);
+    if (st) return st;
+    std::vector<uint2> m(c->last_nm2l), p(c->last_np2p);
+    cudaError_t e = cudaSuccess;
+    if (!m.empty()) e = cudaMemcpyAsync(m.data(), c->buf[B_M2L].p, m.size() * sizeof(uint2), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess && !p.empty())
+        e = cudaMemcpyAsync(p.data(), c->buf[B_P2P].p, p.size() * sizeof(uint2), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_check(c, e, "tg_get_lists");
+    for (size_t i = 0; i < m.size(); ++i) {
+        if (m2l_a) m2l_a[i] = m[i].x;
+        if (m2l_b) m2l_b[i] = m[i].y;
+    }
+    for (size_t i = 0; i < p.size(); ++i) {
+        if (p2p_a) p2p_a[i] = p[i].x;
+        if (p2p_b) p2p_b[i] = p[i].y;
+    }
+    return TG_OK;
+}
+
+tg_status tg_timesteps(tg_ctx *c, int64_t n, const double *a_old, const double *a_cur, double *dt, int32_t *rung)
+{
+    tg_status st = begin(c);
+    if (st) return st;
+    if (n < 0) return set_err(c, TG_ERR_ARG, "n < 0");
+    if (n == 0) return TG_OK;
+    if (!check_device_ptr(a_old) || !check_device_ptr(a_cur) || !check_device_ptr(dt) || !check_device_ptr(rung))
+        return set_err(c, TG_ERR_ARG, "device arrays expected");
+    return timesteps(c, n, a_old, a_cur, dt, rung);
+}
+
+}  // extern "C"

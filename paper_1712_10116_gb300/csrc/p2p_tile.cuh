@@ -1,0 +1,164 @@
+// p2p_tile.cuh -- mutual particle-particle interaction of leaf pairs (P2P, Sec. 2.1, Eq. 2).
+// Each unordered leaf pair (A, B) is visited once; for every particle pair the kernel value is
+// computed once and applied with opposite signs to both particles (a_i += m_j g d, a_j -= m_i g d).
+// Positions are relative to leaf centres (exact float offsets between centres).  F-F pairs are
+// skipped when classes are given (kickS2F feels slow masses only).
+#pragma once
+#include "tg_common.cuh"
+
+namespace tg {
+
+constexpr int kP2PThreads = 64;
+
+template <class T>
+__device__ __forceinline__ T tg_rsqrt(T x);
+template <>
+__device__ __forceinline__ float tg_rsqrt<float>(float x) { return rsqrtf(x); }
+template <>
+__device__ __forceinline__ double tg_rsqrt<double>(double x) { return rsqrt(x); }
+
+// pair kernel: g = phi'(r)/r and phi(r) of a unit mass, Wendland C2 (Eq. 8) or Plummer.
+// For u = r/eps in [1/2, 1) the Wendland terms are evaluated in the equivalent forms
+//   g = M(u)/r^3,  M(u) = 1 - (1-u)^5 (21u^3 + 15u^2 + 5u + 1)   (enclosed mass fraction),
+//   phi = -(1 - (1-u)^6 (3u^2 + 3u + 1))/r,
+// which avoid the cancellation of the expanded polynomial near u = 1 in float32; below u = 1/2
+// the expanded (Horner) forms are well conditioned.
+template <class T, int KERNEL>
+__device__ __forceinline__ void pair_kernel(T r2, T eps, T eps2, T inv_eps, T inv_eps3, T &g, T &phi)
+{
+    if (KERNEL == TG_KERNEL_PLUMMER) {
+        const T si = tg_rsqrt<T>(r2 + eps2);
+        phi = -si;
+        g = si * si * si;
+    } else if (r2 >= eps2) {
+        const T ri = tg_rsqrt<T>(r2);
+        phi = -ri;
+        g = ri * ri * ri;
+    } else if (r2 >= T(0.25) * eps2) {
+        const T ri = tg_rsqrt<T>(r2);
+        const T u = r2 * ri * inv_eps, w = T(1) - u, w2 = w * w, w5 = w2 * w2 * w;
+        const T mfrac = T(1) - w5 * (((T(21) * u + T(15)) * u + T(5)) * u + T(1));
+        g = mfrac * ri * ri * ri;
+        phi = -(T(1) - w5 * w * ((T(3) * u + T(3)) * u + T(1))) * ri;
+    } else {
+        const T u = sqrt(r2) * inv_eps, u2 = u * u;
+        // phi = (1/eps)(3u^7 - 15u^6 + 28u^5 - 21u^4 + 7u^2 - 3); g = (1/eps^3)(21u^5 - 90u^4 + 140u^3 - 84u^2 + 14)
+        phi = ((((((T(3) * u - T(15)) * u + T(28)) * u - T(21)) * u2 + T(7)) * u2) - T(3)) * inv_eps;
+        g = ((((T(21) * u - T(90)) * u + T(140)) * u - T(84)) * u2 + T(14)) * inv_eps3;
+    }
+}
+
+template <class T, class T4, bool MASKED, int KERNEL>
+__global__ void __launch_bounds__(kP2PThreads) p2p_mutual(TreeView t, const Geom *gp, const uint2 *pairs,
+                                                          int64_t npairs, const T4 *pf, const uint8_t *fs, T eps,
+                                                          double *acc4, int n, unsigned long long *pair_counter)
+{
+    __shared__ T4 sb[kMaxNcrit];
+    __shared__ uint8_t sfb[kMaxNcrit];
+    __shared__ T colacc[kMaxNcrit][4];
+    const Geom g = *gp;
+    const int lane = threadIdx.x & 31;
+    const T eps2 = eps * eps, inv_eps = T(1) / eps, inv_eps3 = inv_eps * inv_eps * inv_eps;
+    unsigned long long my_pairs = 0;
+    for (int64_t w = blockIdx.x; w < npairs; w += gridDim.x) {
+        const uint2 pr = pairs[w];
+        const int a = (int)pr.x, b = (int)pr.y;
+        const int fa = t.first[a], na = t.count[a], fb = t.first[b], nb = t.count[b];
+        const double sb_side = ldexp(g.L, -(int)t.level[b]), sa_side = ldexp(g.L, -(int)t.level[a]);
+        const T ox = (T)(((double)t.cx[b] + 0.5) * sb_side - ((double)t.cx[a] + 0.5) * sa_side);
+        const T oy = (T)(((double)t.cy[b] + 0.5) * sb_side - ((double)t.cy[a] + 0.5) * sa_side);
+        const T oz = (T)(((double)t.cz[b] + 0.5) * sb_side - ((double)t.cz[a] + 0.5) * sa_side);
+        const bool self = a == b;
+        // B is staged in chunks of kMaxNcrit (leaves at the deepest level may exceed n_crit)
+        for (int j0 = 0; j0 < nb; j0 += kMaxNcrit) {
+            const int nbc = min(kMaxNcrit, nb - j0);
+            __syncthreads();
+            for (int j = threadIdx.x; j < nbc; j += blockDim.x) {
+                T4 v = pf[fb + j0 + j];
+                v.x += ox;
+                v.y += oy;
+                v.z += oz;
+                sb[j] = v;
+                sfb[j] = MASKED ? fs[fb + j0 + j] : 0;
+                colacc[j][0] = colacc[j][1] = colacc[j][2] = colacc[j][3] = T(0);
+            }
+            __syncthreads();
+            for (int i0 = 0; i0 < na; i0 += blockDim.x) {
+                const int i = i0 + threadIdx.x;
+                const bool row = i < na;
+                T4 pi;
+                if (row) pi = pf[fa + i];
+                else pi.x = pi.y = pi.z = pi.w = T(0);
+                const uint8_t fi = (MASKED && row) ? fs[fa + i] : 0;
+                T rax = 0, ray = 0, raz = 0, rph = 0;
+                for (int j = 0; j < nbc; ++j) {
+                    const T4 pj = sb[j];
+                    const bool use = row && (!self || j0 + j > i) && !(MASKED && fi && sfb[j]);
+                    const T dx = pj.x - pi.x, dy = pj.y - pi.y, dz = pj.z - pi.z;
+                    const T r2 = dx * dx + dy * dy + dz * dz;
+                    T gk, ph;
+                    pair_kernel<T, KERNEL>(use ? r2 : T(1), eps, eps2, inv_eps, inv_eps3, gk, ph);
+                    if (!use) {
+                        gk = T(0);
+                        ph = T(0);
+                    }
+                    my_pairs += use ? 1 : 0;
+                    rax += pj.w * gk * dx;
+                    ray += pj.w * gk * dy;
+                    raz += pj.w * gk * dz;
+                    rph += pj.w * ph;
+                    T cx = -pi.w * gk * dx, cy = -pi.w * gk * dy, cz = -pi.w * gk * dz, cp = pi.w * ph;
+                    cx = warp_sum(cx);
+                    cy = warp_sum(cy);
+                    cz = warp_sum(cz);
+                    cp = warp_sum(cp);
+                    if (lane == 0) {
+                        atomicAdd(&colacc[j][0], cx);
+                        atomicAdd(&colacc[j][1], cy);
+                        atomicAdd(&colacc[j][2], cz);
+                        atomicAdd(&colacc[j][3], cp);
+                    }
+                }
+                if (row) {
+                    atomicAdd(&acc4[fa + i], (double)rax);
+                    atomicAdd(&acc4[(size_t)n + fa + i], (double)ray);
+                    atomicAdd(&acc4[2 * (size_t)n + fa + i], (double)raz);
+                    atomicAdd(&acc4[3 * (size_t)n + fa + i], (double)rph);
+                }
+            }
+            __syncthreads();
+            for (int j = threadIdx.x; j < nbc; j += blockDim.x) {
+                atomicAdd(&acc4[fb + j0 + j], (double)colacc[j][0]);
+                atomicAdd(&acc4[(size_t)n + fb + j0 + j], (double)colacc[j][1]);
+                atomicAdd(&acc4[2 * (size_t)n + fb + j0 + j], (double)colacc[j][2]);
+                atomicAdd(&acc4[3 * (size_t)n + fb + j0 + j], (double)colacc[j][3]);
+            }
+        }
+    }
+    my_pairs = warp_sum(my_pairs);
+    if (lane == 0 && my_pairs) atomicAdd(pair_counter, my_pairs);
+}
+
+template <class T, class T4>
+static tg_status launch_p2p(tg_ctx *c, const TreeView &t, const Geom *d_geom, const uint2 *pairs, int64_t npairs,
+                            const T4 *pf, const uint8_t *fs, bool masked, double *acc4)
+{
+    const int grid = (int)std::min<int64_t>(npairs, (int64_t)c->num_sms * 16);
+    const T eps = (T)c->prm.eps;
+    unsigned long long *ctr = c->d_counters;
+    const int kern = c->prm.kernel;
+    ProfScope ps_(c, TG_K_P2P);
+#define TG_P2P_LAUNCH(M, K) \
+    p2p_mutual<T, T4, M, K><<<grid, kP2PThreads, 0, c->stream>>>(t, d_geom, pairs, npairs, pf, fs, eps, acc4, t.n, ctr)
+    if (masked) {
+        if (kern == TG_KERNEL_PLUMMER) TG_P2P_LAUNCH(true, TG_KERNEL_PLUMMER);
+        else TG_P2P_LAUNCH(true, TG_KERNEL_WENDLAND_C2);
+    } else {
+        if (kern == TG_KERNEL_PLUMMER) TG_P2P_LAUNCH(false, TG_KERNEL_PLUMMER);
+        else TG_P2P_LAUNCH(false, TG_KERNEL_WENDLAND_C2);
+    }
+#undef TG_P2P_LAUNCH
+    return cuda_check(c, cudaGetLastError(), "p2p launch");
+}
+
+}  // namespace tg

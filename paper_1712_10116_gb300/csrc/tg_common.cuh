@@ -1,0 +1,193 @@
+// tg_common.cuh -- shared declarations of the CUDA library (device helpers, context, launches).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "../../include/taichi_gb.h"
+
+namespace tg {
+
+constexpr int kMaxLevel = 21;         // Morton keys carry 21 bits per axis
+constexpr int kMaxNcrit = 128;        // leaf capacity supported by the P2P tiles
+constexpr int kPMaxGpu = 8;           // expansion orders supported on the GPU
+
+inline int ncoef(int p) { return (p + 1) * (p + 2) * (p + 3) / 6; }
+
+// four doubles, 32-byte aligned (per-particle offset + mass in the float64 path)
+struct __align__(32) dbl4 {
+    double x, y, z, w;
+};
+
+// ---------------------------------------------------------------- grow-only device buffers
+struct Buf {
+    void *p = nullptr;
+    size_t bytes = 0;
+};
+
+// Error state shared by the host-side pipeline.  Each host function returns tg_status; the
+// first failure is recorded with a message.
+struct Err {
+    tg_status code = TG_OK;
+    std::string msg;
+};
+
+// Geometry of the root cube of one evaluation, computed on the device.
+struct Geom {
+    double lo[3];     // lower corner, multiple of h = L / 2^21
+    double L;         // side, a power of two
+    double inv_h;     // 2^21 / L
+    int log2L;        // L = 2^log2L
+    int pad;
+};
+
+// Octree of one evaluation (structure of arrays, cells in BFS order).
+struct TreeView {
+    int32_t n;           // particles
+    int32_t ncell;
+    const uint8_t *level;
+    const uint32_t *cx, *cy, *cz;   // integer coordinates at the cell's own level
+    const int32_t *first, *count, *child_first, *parent;
+    const uint8_t *nchild;
+};
+
+}  // namespace tg
+
+// ---------------------------------------------------------------- context
+struct tg_ctx {
+    tg_params prm;
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    int num_sms = 0;
+    tg::Err err;
+    tg_stats stats{};
+
+    // scratch buffers, grown on demand
+    tg::Buf buf[64];
+
+    // counters on the device (p2p pair count) and pinned host mirrors
+    unsigned long long *d_counters = nullptr;   // [0] p2p particle pairs
+    int64_t *h_pinned = nullptr;                // small pinned staging area (64 int64)
+
+    // last tree/walk (host copies of sizes)
+    int64_t last_n = 0, last_ncell = 0, last_nm2l = 0, last_np2p = 0;
+    std::vector<int32_t> level_begin;           // cell index range of each level (BFS)
+
+    // live kernel timing
+    int prof_level = 0;
+    std::vector<cudaEvent_t> prof_events;        // pool, reused after each tg_get_profile
+    std::vector<int> prof_class;                 // class of each recorded (start, end) pair
+    size_t prof_used = 0;
+    int64_t prof_launches[TG_K_COUNT] = {0};
+    double prof_ms[TG_K_COUNT] = {0};
+
+    // HHS binding
+    int64_t hhs_n = 0;
+    double *hhs_pos = nullptr, *hhs_vel = nullptr;
+    const double *hhs_mass = nullptr;
+    double hhs_time = 0.0;
+};
+
+namespace tg {
+
+// buffer slots of tg_ctx::buf
+enum Slot {
+    B_GEOM = 0, B_PARTIAL, B_KEYS0, B_KEYS1, B_VALS0, B_VALS1, B_HIST, B_SCAN_TMP,
+    B_XS, B_YS, B_ZS, B_MS, B_FS, B_PF, B_LEAF_OF,
+    B_C_LEVEL, B_C_X, B_C_Y, B_C_Z, B_C_FIRST, B_C_COUNT, B_C_CHILD, B_C_PARENT, B_C_NCHILD,
+    B_C_TMP0, B_C_TMP1,
+    B_MOM, B_MOMF, B_LOC, B_ACC,
+    B_FRONT0, B_FRONT1, B_M2L, B_P2P, B_WALK_CNT,
+    B_SUB_ACC, B_HHS_AOLD, B_HHS_ACUR, B_HHS_DT, B_HHS_RUNG, B_HHS_IDX, B_HHS_FLAG,
+    B_HHS_SCAN, B_HHS_TMP, B_RED, B_DIAG_POT, B_DIAG_ACC,
+    B_LAST_SLOT
+};
+
+tg_status set_err(tg_ctx *c, tg_status code, const char *fmt, ...);
+tg_status cuda_check(tg_ctx *c, cudaError_t e, const char *what);
+// Make buffer `slot` at least `bytes` long (contents are not preserved when it grows).
+tg_status ensure(tg_ctx *c, int slot, size_t bytes, void **out);
+template <class T>
+inline tg_status ensure_t(tg_ctx *c, int slot, size_t count, T **out)
+{
+    void *p = nullptr;
+    tg_status s = ensure(c, slot, count * sizeof(T) + 16, &p);
+    *out = static_cast<T *>(p);
+    return s;
+}
+
+// ---- tree.cu
+// Root cube of the n particles pos[q] (q < n, gathered through sub when non-null) -> geom.
+tg_status root_cube(tg_ctx *c, int n, const double *pos, int64_t stride, const int64_t *sub, Geom *d_geom);
+// Keys, stable radix sort and gather into sorted order.  Returns device pointers in the ctx
+// slots: B_KEYS0 (sorted keys), B_VALS0 (perm: sorted -> input index q), B_XS.. B_FS.
+tg_status keys_sort_gather(tg_ctx *c, int n, const double *pos, int64_t stride, const int64_t *sub,
+                           const double *mass, const uint8_t *fast, const Geom *d_geom);
+// Octree from the sorted keys; fills the cell slots and c->level_begin.  Returns ncell.
+tg_status build_octree(tg_ctx *c, int n, int *ncell_out);
+TreeView tree_view(tg_ctx *c, int n, int ncell);
+
+// Device-wide exclusive scan of uint32 (in place allowed); optional total to a device word.
+tg_status exclusive_scan_u32(tg_ctx *c, const uint32_t *in, uint32_t *out, int n, uint32_t *d_total);
+
+// ---- fmm.cu
+// Full FMM evaluation on a (sub)set of particles.  Outputs are in input order q:
+// acc (3 SoA arrays of length n with stride `out_stride`), pot (nullable).
+tg_status fmm_eval(tg_ctx *c, int n, const double *pos, int64_t stride, const int64_t *sub,
+                   const double *mass, const uint8_t *fast, double *acc, int64_t out_stride, double *pot,
+                   bool keep_tree);
+tg_status direct_eval(tg_ctx *c, int64_t n, const double *pos, const double *mass, const uint8_t *fast,
+                      int64_t n_sink, const int64_t *sink_idx, double *acc, double *pot);
+
+// ---- hhs.cu
+tg_status hhs_init(tg_ctx *c);
+tg_status hhs_step(tg_ctx *c);
+tg_status hhs_diagnostics(tg_ctx *c, double out[8]);
+tg_status timesteps(tg_ctx *c, int64_t n, const double *a_old, const double *a_cur, double *dt, int32_t *rung);
+
+// Wrap each kernel launch: counts launches per class and, when profiling is on for the class,
+// records CUDA events around it on the context stream.
+struct ProfScope {
+    tg_ctx *c;
+    int cls;
+    bool timed;
+    ProfScope(tg_ctx *ctx, int k);
+    ~ProfScope();
+};
+tg_status prof_collect(tg_ctx *c);
+
+// ---------------------------------------------------------------- device helpers
+__device__ __forceinline__ uint64_t spread3_21(uint64_t v)
+{
+    // spread the low 21 bits of v so that bit b lands on bit 3b
+    v &= 0x1fffffull;
+    v = (v | (v << 32)) & 0x1f00000000ffffull;
+    v = (v | (v << 16)) & 0x1f0000ff0000ffull;
+    v = (v | (v << 8)) & 0x100f00f00f00f00full;
+    v = (v | (v << 4)) & 0x10c30c30c30c30c3ull;
+    v = (v | (v << 2)) & 0x1249249249249249ull;
+    return v;
+}
+
+__host__ __device__ __forceinline__ int ncoef_dev(int p) { return (p + 1) * (p + 2) * (p + 3) / 6; }
+
+template <class T>
+__device__ __forceinline__ T warp_sum(T v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+inline int grid_for(int64_t n, int block, int max_blocks = 152 * 32)
+{
+    int64_t g = (n + block - 1) / block;
+    if (g < 1) g = 1;
+    if (g > max_blocks) g = max_blocks;
+    return (int)g;
+}
+
+}  // namespace tg

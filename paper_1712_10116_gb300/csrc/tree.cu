@@ -1,0 +1,671 @@
+// tree.cu -- root cube, Morton keys, stable LSD radix sort, gather and level-synchronous
+// octree build (Sec. 2.3 of Zhu 2017: octree with leaf size n_crit, built for every call).
+//
+// Keys: 21 bits per axis, x the most significant bit of each 3-bit group, so a cell at level l
+// is the run of sorted keys sharing the top 3l bits.  The sort orders (key, input index), so ties
+// keep input order.  Cells are emitted level by level in Morton order of their key prefix.
+#include <cstdarg>
+#include <cstring>
+
+#include "tg_common.cuh"
+
+namespace tg {
+
+// ------------------------------------------------------------------ errors and buffers
+tg_status set_err(tg_ctx *c, tg_status code, const char *fmt, ...)
+{
+    if (c->err.code == TG_OK) {
+        char msg[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(msg, sizeof msg, fmt, ap);
+        va_end(ap);
+        c->err.code = code;
+        c->err.msg = msg;
+    }
+    return code;
+}
+
+tg_status cuda_check(tg_ctx *c, cudaError_t e, const char *what)
+{
+    if (e == cudaSuccess) return TG_OK;
+    return set_err(c, e == cudaErrorMemoryAllocation ? TG_ERR_OOM : TG_ERR_CUDA, "%s: %s", what,
+                   cudaGetErrorString(e));
+}
+
+tg_status ensure(tg_ctx *c, int slot, size_t bytes, void **out)
+{
+    Buf &b = c->buf[slot];
+    if (b.bytes < bytes) {
+        size_t nb = bytes + bytes / 4 + 256;
+        if (b.p) {
+            cudaError_t e = cudaStreamSynchronize(c->stream);
+            if (e != cudaSuccess) return cuda_check(c, e, "sync before regrow");
+            cudaFree(b.p);
+            b.p = nullptr;
+            b.bytes = 0;
+        }
+        cudaError_t e = cudaMalloc(&b.p, nb);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return set_err(c, TG_ERR_OOM, "cudaMalloc(%zu) for scratch slot %d failed", nb, slot);
+        }
+        b.bytes = nb;
+    }
+    *out = b.p;
+    return TG_OK;
+}
+
+// grow keeping the first `keep` bytes
+static tg_status ensure_keep(tg_ctx *c, int slot, size_t bytes, size_t keep, void **out)
+{
+    Buf &b = c->buf[slot];
+    if (b.bytes >= bytes) {
+        *out = b.p;
+        return TG_OK;
+    }
+    size_t nb = bytes + bytes / 2 + 256;
+    void *np = nullptr;
+    cudaError_t e = cudaMalloc(&np, nb);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return set_err(c, TG_ERR_OOM, "cudaMalloc(%zu) for scratch slot %d failed", nb, slot);
+    }
+    if (b.p) {
+        if (keep) cudaMemcpyAsync(np, b.p, keep, cudaMemcpyDeviceToDevice, c->stream);
+        e = cudaStreamSynchronize(c->stream);
+        if (e != cudaSuccess) return cuda_check(c, e, "sync before regrow");
+        cudaFree(b.p);
+    }
+    b.p = np;
+    b.bytes = nb;
+    *out = np;
+    return TG_OK;
+}
+
+template <class T>
+static tg_status ensure_keep_t(tg_ctx *c, int slot, size_t count, size_t keep_count, T **out)
+{
+    void *p = nullptr;
+    tg_status s = ensure_keep(c, slot, count * sizeof(T) + 16, keep_count * sizeof(T), &p);
+    *out = static_cast<T *>(p);
+    return s;
+}
+
+// ------------------------------------------------------------------ live kernel timing
+ProfScope::ProfScope(tg_ctx *ctx, int k) : c(ctx), cls(k), timed(false)
+{
+    c->prof_launches[k] += 1;
+    if (c->prof_level >= 2 || (c->prof_level == 1 && (k == TG_K_M2L || k == TG_K_P2P))) {
+        if (c->prof_used >= 2048) prof_collect(c);
+        while (c->prof_events.size() < 2 * (c->prof_used + 1)) {
+            cudaEvent_t e;
+            if (cudaEventCreate(&e) != cudaSuccess) {
+                cudaGetLastError();
+                return;
+            }
+            c->prof_events.push_back(e);
+        }
+        if (c->prof_class.size() < c->prof_used + 1) c->prof_class.resize(c->prof_used + 1);
+        c->prof_class[c->prof_used] = k;
+        cudaEventRecord(c->prof_events[2 * c->prof_used], c->stream);
+        timed = true;
+    }
+}
+
+ProfScope::~ProfScope()
+{
+    if (!timed) return;
+    cudaEventRecord(c->prof_events[2 * c->prof_used + 1], c->stream);
+    c->prof_used += 1;
+}
+
+tg_status prof_collect(tg_ctx *c)
+{
+    if (c->prof_used == 0) return TG_OK;
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_check(c, e, "profile collect");
+    for (size_t i = 0; i < c->prof_used; ++i) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, c->prof_events[2 * i], c->prof_events[2 * i + 1]) == cudaSuccess)
+            c->prof_ms[c->prof_class[i]] += ms;
+        else
+            cudaGetLastError();
+    }
+    c->prof_used = 0;
+    return TG_OK;
+}
+
+// ------------------------------------------------------------------ exclusive scan (uint32)
+constexpr int kScanThreads = 512;
+constexpr int kScanItems = 4;
+constexpr int kScanTile = kScanThreads * kScanItems;
+
+__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t *total)
+{
+    __shared__ uint32_t warp_tot[32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_tot[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        const int nw = blockDim.x >> 5;
+        uint32_t t = lane < nw ? warp_tot[lane] : 0u;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(0xffffffffu, t, o);
+            if (lane >= o) t += y;
+        }
+        warp_tot[lane] = t;   // inclusive
+    }
+    __syncthreads();
+    uint32_t base = warp > 0 ? warp_tot[warp - 1] : 0u;
+    *total = warp_tot[(blockDim.x >> 5) - 1];
+    __syncthreads();
+    return base + x - v;
+}
+
+__global__ void scan_tiles(const uint32_t *in, uint32_t *out, uint32_t *tile_sums, int n)
+{
+    const int64_t base = (int64_t)blockIdx.x * kScanTile + threadIdx.x * kScanItems;
+    uint32_t v[kScanItems];
+    uint32_t s = 0;
+#pragma unroll
+    for (int i = 0; i < kScanItems; ++i) {
+        v[i] = (base + i < n) ? in[base + i] : 0u;
+        s += v[i];
+    }
+    uint32_t tot;
+    uint32_t pre = block_exclusive_scan(s, &tot);
+#pragma unroll
+    for (int i = 0; i < kScanItems; ++i) {
+        if (base + i < n) out[base + i] = pre;
+        pre += v[i];
+    }
+    if (threadIdx.x == 0) tile_sums[blockIdx.x] = tot;
+}
+
+__global__ void scan_add(uint32_t *out, const uint32_t *tile_pre, int n)
+{
+    const int64_t base = (int64_t)blockIdx.x * kScanTile + threadIdx.x * kScanItems;
+    const uint32_t add = tile_pre[blockIdx.x];
+#pragma unroll
+    for (int i = 0; i < kScanItems; ++i)
+        if (base + i < n) out[base + i] += add;
+}
+
+// Exclusive scan of n uint32 values (out may alias in).  The total is written to d_total
+// (device word) when it is not null.  Recursive over tile sums.
+tg_status exclusive_scan_u32(tg_ctx *c, const uint32_t *in, uint32_t *out, int n, uint32_t *d_total)
+{
+    if (n <= 0) {
+        if (d_total) cudaMemsetAsync(d_total, 0, sizeof(uint32_t), c->stream);
+        return cuda_check(c, cudaGetLastError(), "exclusive scan");
+    }
+    size_t need = 4;
+    for (int m = n; ; ) {
+        int nt = (m + kScanTile - 1) / kScanTile;
+        need += 2 * (size_t)nt + 2;
+        if (nt == 1) break;
+        m = nt;
+    }
+    uint32_t *tmp = nullptr;
+    tg_status st = ensure_t(c, B_SCAN_TMP, need, &tmp);
+    if (st) return st;
+    struct Level { uint32_t *out; int n, ntiles; uint32_t *sums, *pre; };
+    Level lv[8];
+    int depth = 0;
+    const uint32_t *cin = in;
+    uint32_t *cout = out;
+    int cn = n;
+    uint32_t *cursor = tmp;
+    while (true) {
+        int nt = (cn + kScanTile - 1) / kScanTile;
+        lv[depth] = {cout, cn, nt, cursor, cursor + nt};
+        {
+            ProfScope ps_(c, TG_K_OTHER);
+            scan_tiles<<<nt, kScanThreads, 0, c->stream>>>(cin, cout, cursor, cn);
+        }
+        ++depth;
+        if (nt == 1) break;
+        cin = cursor;
+        cout = cursor + nt;
+        cn = nt;
+        cursor += 2 * nt + 2;
+    }
+    for (int d = depth - 2; d >= 0; --d)
+        {
+            ProfScope ps_(c, TG_K_OTHER);
+            scan_add<<<lv[d].ntiles, kScanThreads, 0, c->stream>>>(lv[d].out, lv[d].pre, lv[d].n);
+        }
+    if (d_total)
+        cudaMemcpyAsync(d_total, lv[depth - 1].sums, sizeof(uint32_t), cudaMemcpyDeviceToDevice, c->stream);
+    return cuda_check(c, cudaGetLastError(), "exclusive scan");
+}
+
+// ------------------------------------------------------------------ root cube
+constexpr int kRedThreads = 256;
+
+__device__ __forceinline__ double pos_at(const double *pos, int64_t stride, const int64_t *sub, int64_t q, int axis)
+{
+    int64_t i = sub ? sub[q] : q;
+    return pos[axis * stride + i];
+}
+
+__global__ void bbox_partial(const double *pos, int64_t stride, const int64_t *sub, int n, double *partial)
+{
+    double mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            double v = pos_at(pos, stride, sub, q, a);
+            mn[a] = fmin(mn[a], v);
+            mx[a] = fmax(mx[a], v);
+        }
+    }
+    __shared__ double s[6][kRedThreads / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        double lo = mn[a], hi = mx[a];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            lo = fmin(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+            hi = fmax(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+        }
+        if (lane == 0) {
+            s[a][warp] = lo;
+            s[3 + a][warp] = hi;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < 6) {
+        double r = s[threadIdx.x][0];
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w)
+            r = threadIdx.x < 3 ? fmin(r, s[threadIdx.x][w]) : fmax(r, s[threadIdx.x][w]);
+        partial[blockIdx.x * 6 + threadIdx.x] = r;
+    }
+}
+
+// Root cube from the bounding box: L = smallest power of two >= extent * (1 + 2^-20) (1 if the
+// extent is 0), lo = floor(min / h) * h with h = L / 2^21.
+__global__ void bbox_final(const double *partial, int nparts, int n, Geom *g)
+{
+    if (threadIdx.x != 0) return;
+    double mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int b = 0; b < nparts; ++b)
+        for (int a = 0; a < 3; ++a) {
+            mn[a] = fmin(mn[a], partial[b * 6 + a]);
+            mx[a] = fmax(mx[a], partial[b * 6 + 3 + a]);
+        }
+    if (n <= 0) {
+        for (int a = 0; a < 3; ++a) g->lo[a] = 0.0;
+        g->L = 1.0;
+        g->log2L = 0;
+        g->inv_h = ldexp(1.0, kMaxLevel);
+        return;
+    }
+    double ext = 0.0;
+    for (int a = 0; a < 3; ++a) {
+        double e = __dsub_rn(mx[a], mn[a]);
+        if (e > ext) ext = e;
+    }
+    double L = 1.0;
+    int log2L = 0;
+    if (ext > 0.0) {
+        double t = __dmul_rn(ext, 1.0 + ldexp(1.0, -20));
+        int e;
+        double f = frexp(t, &e);
+        if (f == 0.5) {
+            L = t;
+            log2L = e - 1;
+        } else {
+            L = ldexp(1.0, e);
+            log2L = e;
+        }
+    }
+    double h = ldexp(L, -kMaxLevel);
+    for (int a = 0; a < 3; ++a) g->lo[a] = __dmul_rn(floor(__ddiv_rn(mn[a], h)), h);
+    g->L = L;
+    g->log2L = log2L;
+    g->inv_h = ldexp(1.0, kMaxLevel - log2L);
+}
+
+tg_status root_cube(tg_ctx *c, int n, const double *pos, int64_t stride, const int64_t *sub, Geom *d_geom)
+{
+    double *partial = nullptr;
+    int nb = grid_for(n, kRedThreads, 2 * 152);
+    tg_status st = ensure_t(c, B_PARTIAL, (size_t)nb * 6, &partial);
+    if (st) return st;
+    {
+        ProfScope ps_(c, TG_K_TREE);
+        bbox_partial<<<nb, kRedThreads, 0, c->stream>>>(pos, stride, sub, n, partial);
+    }
+    {
+        ProfScope ps_(c, TG_K_TREE);
+        bbox_final<<<1, 32, 0, c->stream>>>(partial, nb, n, d_geom);
+    }
+    return cuda_check(c, cudaGetLastError(), "root cube");
+}
+
+// ------------------------------------------------------------------ keys
+__device__ __forceinline__ uint64_t cell_coord(double x, double lo, double inv_h)
+{
+    double t = floor(__dmul_rn(__dsub_rn(x, lo), inv_h));
+    if (t < 0.0) t = 0.0;
+    const double top = (double)((1 << kMaxLevel) - 1);
+    if (t > top) t = top;
+    return (uint64_t)t;
+}
+
+__global__ void morton_keys(const double *pos, int64_t stride, const int64_t *sub, int n, const Geom *g,
+                            uint64_t *keys, uint32_t *vals)
+{
+    const double lo0 = g->lo[0], lo1 = g->lo[1], lo2 = g->lo[2], inv_h = g->inv_h;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x) {
+        uint64_t cx = cell_coord(pos_at(pos, stride, sub, q, 0), lo0, inv_h);
+        uint64_t cy = cell_coord(pos_at(pos, stride, sub, q, 1), lo1, inv_h);
+        uint64_t cz = cell_coord(pos_at(pos, stride, sub, q, 2), lo2, inv_h);
+        keys[q] = (spread3_21(cx) << 2) | (spread3_21(cy) << 1) | spread3_21(cz);
+        vals[q] = (uint32_t)q;
+    }
+}
+
+// ------------------------------------------------------------------ radix sort
+// Tiles of 2048 items: 8 warps x 8 rounds x 32 lanes, item index = warp*256 + round*32 + lane,
+// so a warp's rounds run in input order and ranks are stable.
+constexpr int kSortThreads = 256;
+constexpr int kSortItems = 8;
+constexpr int kSortTile = kSortThreads * kSortItems;
+
+__global__ void radix_hist(const uint64_t *keys, int n, int shift, uint32_t *hist, int nblocks)
+{
+    __shared__ uint32_t h[256];
+    h[threadIdx.x] = 0;
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t base = (int64_t)blockIdx.x * kSortTile + warp * 256 + lane;
+#pragma unroll
+    for (int r = 0; r < kSortItems; ++r) {
+        int64_t idx = base + r * 32;
+        if (idx < n) atomicAdd(&h[(keys[idx] >> shift) & 255u], 1u);
+    }
+    __syncthreads();
+    hist[threadIdx.x * nblocks + blockIdx.x] = h[threadIdx.x];
+}
+
+__global__ void radix_scatter(const uint64_t *keys_in, const uint32_t *vals_in, uint64_t *keys_out,
+                              uint32_t *vals_out, const uint32_t *offsets, int n, int shift, int nblocks)
+{
+    __shared__ uint32_t wcount[8][256];
+    for (int i = threadIdx.x; i < 8 * 256; i += kSortThreads) (&wcount[0][0])[i] = 0;
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t lt_mask = (1u << lane) - 1u;
+    const int64_t base = (int64_t)blockIdx.x * kSortTile + warp * 256 + lane;
+    uint64_t k[kSortItems];
+    uint32_t v[kSortItems], rank[kSortItems], dig[kSortItems];
+#pragma unroll
+    for (int r = 0; r < kSortItems; ++r) {
+        int64_t idx = base + r * 32;
+        bool valid = idx < n;
+        k[r] = valid ? keys_in[idx] : ~0ull;
+        v[r] = valid ? vals_in[idx] : 0u;
+        uint32_t d = valid ? (uint32_t)((k[r] >> shift) & 255u) : 255u;
+        dig[r] = d;
+        uint32_t peers = __match_any_sync(0xffffffffu, d);
+        uint32_t lower = peers & lt_mask;
+        uint32_t pre = wcount[warp][d];
+        rank[r] = pre + __popc(lower);
+        __syncwarp();
+        if (lower == 0) wcount[warp][d] = pre + __popc(peers);
+        __syncwarp();
+    }
+    __syncthreads();
+    {
+        uint32_t run = 0;
+        const int d = threadIdx.x;
+#pragma unroll
+        for (int w = 0; w < 8; ++w) {
+            uint32_t t = wcount[w][d];
+            wcount[w][d] = run;
+            run += t;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < kSortItems; ++r) {
+        int64_t idx = base + r * 32;
+        if (idx < n) {
+            uint32_t pos = offsets[dig[r] * nblocks + blockIdx.x] + wcount[warp][dig[r]] + rank[r];
+            keys_out[pos] = k[r];
+            vals_out[pos] = v[r];
+        }
+    }
+}
+
+// ------------------------------------------------------------------ gather
+__global__ void gather_sorted(const uint32_t *perm, const double *pos, int64_t stride, const int64_t *sub,
+                              const double *mass, const uint8_t *fast, int n, double *xs, double *ys, double *zs,
+                              double *ms, uint8_t *fs)
+{
+    for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < n; s += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t q = perm[s];
+        int64_t i = sub ? sub[q] : (int64_t)q;
+        xs[s] = pos[i];
+        ys[s] = pos[stride + i];
+        zs[s] = pos[2 * stride + i];
+        ms[s] = mass[i];
+        fs[s] = fast ? (fast[q] != 0) : 0;
+    }
+}
+
+tg_status keys_sort_gather(tg_ctx *c, int n, const double *pos, int64_t stride, const int64_t *sub,
+                           const double *mass, const uint8_t *fast, const Geom *d_geom)
+{
+    uint64_t *k0, *k1;
+    uint32_t *v0, *v1, *hist;
+    const int nblocks = (n + kSortTile - 1) / kSortTile;
+    tg_status st;
+    if ((st = ensure_t(c, B_KEYS0, n, &k0)) || (st = ensure_t(c, B_KEYS1, n, &k1)) ||
+        (st = ensure_t(c, B_VALS0, n, &v0)) || (st = ensure_t(c, B_VALS1, n, &v1)) ||
+        (st = ensure_t(c, B_HIST, (size_t)256 * nblocks + 1, &hist)))
+        return st;
+    {
+        ProfScope ps_(c, TG_K_TREE);
+        morton_keys<<<grid_for(n, 256), 256, 0, c->stream>>>(pos, stride, sub, n, d_geom, k0, v0);
+    }
+    uint64_t *kin = k0, *kout = k1;
+    uint32_t *vin = v0, *vout = v1;
+    for (int shift = 0; shift < 64; shift += 8) {
+        {
+            ProfScope ps_(c, TG_K_TREE);
+            radix_hist<<<nblocks, kSortThreads, 0, c->stream>>>(kin, n, shift, hist, nblocks);
+        }
+        if ((st = exclusive_scan_u32(c, hist, hist, 256 * nblocks, nullptr))) return st;
+        {
+            ProfScope ps_(c, TG_K_TREE);
+            radix_scatter<<<nblocks, kSortThreads, 0, c->stream>>>(kin, vin, kout, vout, hist, n, shift, nblocks);
+        }
+        std::swap(kin, kout);
+        std::swap(vin, vout);
+    }
+    // 8 passes: the sorted data is back in k0/v0
+    double *xs, *ys, *zs, *ms;
+    uint8_t *fs;
+    if ((st = ensure_t(c, B_XS, n, &xs)) || (st = ensure_t(c, B_YS, n, &ys)) || (st = ensure_t(c, B_ZS, n, &zs)) ||
+        (st = ensure_t(c, B_MS, n, &ms)) || (st = ensure_t(c, B_FS, n, &fs)))
+        return st;
+    {
+        ProfScope ps_(c, TG_K_TREE);
+        gather_sorted<<<grid_for(n, 256), 256, 0, c->stream>>>(v0, pos, stride, sub, mass, fast, n, xs, ys, zs, ms, fs);
+    }
+    return cuda_check(c, cudaGetLastError(), "keys/sort/gather");
+}
+
+// ------------------------------------------------------------------ octree
+__device__ __forceinline__ int key_digit(uint64_t key, int lvl) { return (int)((key >> (3 * (kMaxLevel - lvl))) & 7u); }
+
+// first index in [s, e) whose digit at level lvl is >= d (digits are sorted within a cell)
+__device__ __forceinline__ int digit_lower_bound(const uint64_t *keys, int s, int e, int lvl, int d)
+{
+    while (s < e) {
+        int m = (s + e) >> 1;
+        if (key_digit(keys[m], lvl) < d) s = m + 1;
+        else e = m;
+    }
+    return s;
+}
+
+__global__ void oct_count(const uint64_t *keys, int lb, int le, const uint8_t *level, const int32_t *first,
+                          const int32_t *count, int n_crit, int max_level, uint32_t *cnt)
+{
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    int cidx = lb + t;
+    if (cidx >= le) return;
+    if (count[cidx] <= n_crit || level[cidx] >= max_level) {
+        cnt[t] = 0;
+        return;
+    }
+    const int l = level[cidx] + 1, s = first[cidx], e = s + count[cidx];
+    int nch = 0, prev = s;
+    for (int d = 1; d <= 8; ++d) {
+        int b = d < 8 ? digit_lower_bound(keys, prev, e, l, d) : e;
+        if (b > prev) ++nch;
+        prev = b;
+    }
+    cnt[t] = nch;
+}
+
+__global__ void oct_emit(const uint64_t *keys, int lb, int le, uint8_t *level, uint32_t *cx, uint32_t *cy,
+                         uint32_t *cz, int32_t *first, int32_t *count, int32_t *child_first, int32_t *parent,
+                         uint8_t *nchild, const uint32_t *off, const uint32_t *cnt)
+{
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    int cidx = lb + t;
+    if (cidx >= le) return;
+    const int nch = cnt[t];
+    nchild[cidx] = (uint8_t)nch;
+    if (nch == 0) {
+        child_first[cidx] = -1;
+        return;
+    }
+    const int base = le + (int)off[t];
+    child_first[cidx] = base;
+    const int l = level[cidx] + 1, s0 = first[cidx], e = s0 + count[cidx];
+    int k = 0, prev = s0;
+    for (int d = 1; d <= 8; ++d) {
+        int b = d < 8 ? digit_lower_bound(keys, prev, e, l, d) : e;
+        if (b > prev) {
+            const int digit = d - 1, ch = base + k;
+            level[ch] = (uint8_t)l;
+            cx[ch] = 2u * cx[cidx] + ((digit >> 2) & 1);
+            cy[ch] = 2u * cy[cidx] + ((digit >> 1) & 1);
+            cz[ch] = 2u * cz[cidx] + (digit & 1);
+            first[ch] = prev;
+            count[ch] = b - prev;
+            parent[ch] = cidx;
+            nchild[ch] = 0;
+            child_first[ch] = -1;
+            ++k;
+        }
+        prev = b;
+    }
+}
+
+__global__ void oct_root(int n, uint8_t *level, uint32_t *cx, uint32_t *cy, uint32_t *cz, int32_t *first,
+                         int32_t *count, int32_t *child_first, int32_t *parent, uint8_t *nchild)
+{
+    level[0] = 0;
+    cx[0] = cy[0] = cz[0] = 0;
+    first[0] = 0;
+    count[0] = n;
+    child_first[0] = -1;
+    parent[0] = -1;
+    nchild[0] = 0;
+}
+
+tg_status build_octree(tg_ctx *c, int n, int *ncell_out)
+{
+    tg_status st;
+    const uint64_t *keys = static_cast<const uint64_t *>(c->buf[B_KEYS0].p);
+    int cap = 1024 + n / 4;
+    uint8_t *level, *nchild;
+    uint32_t *cx, *cy, *cz, *cnt, *off;
+    int32_t *first, *count, *child_first, *parent;
+    auto grow = [&](int need, int keep) -> tg_status {
+        tg_status s;
+        if ((s = ensure_keep_t(c, B_C_LEVEL, need, keep, &level)) || (s = ensure_keep_t(c, B_C_X, need, keep, &cx)) ||
+            (s = ensure_keep_t(c, B_C_Y, need, keep, &cy)) || (s = ensure_keep_t(c, B_C_Z, need, keep, &cz)) ||
+            (s = ensure_keep_t(c, B_C_FIRST, need, keep, &first)) ||
+            (s = ensure_keep_t(c, B_C_COUNT, need, keep, &count)) ||
+            (s = ensure_keep_t(c, B_C_CHILD, need, keep, &child_first)) ||
+            (s = ensure_keep_t(c, B_C_PARENT, need, keep, &parent)) ||
+            (s = ensure_keep_t(c, B_C_NCHILD, need, keep, &nchild)))
+            return s;
+        return TG_OK;
+    };
+    if ((st = grow(cap, 0))) return st;
+    {
+        ProfScope ps_(c, TG_K_TREE);
+        oct_root<<<1, 1, 0, c->stream>>>(n, level, cx, cy, cz, first, count, child_first, parent, nchild);
+    }
+    c->level_begin.assign(1, 0);
+    int lb = 0, le = 1;
+    uint32_t *h_total = reinterpret_cast<uint32_t *>(c->h_pinned);
+    uint32_t *d_total = reinterpret_cast<uint32_t *>(c->d_counters + 8);
+    for (int lvl = 0; lvl < c->prm.max_level && le > lb; ++lvl) {
+        const int m = le - lb;
+        if ((st = ensure_t(c, B_C_TMP0, m, &cnt)) || (st = ensure_t(c, B_C_TMP1, m, &off))) return st;
+        {
+            ProfScope ps_(c, TG_K_TREE);
+            oct_count<<<(m + 255) / 256, 256, 0, c->stream>>>(keys, lb, le, level, first, count, c->prm.n_crit,
+                                                             c->prm.max_level, cnt);
+        }
+        if ((st = exclusive_scan_u32(c, cnt, off, m, d_total))) return st;
+        cudaMemcpyAsync(h_total, d_total, sizeof(uint32_t), cudaMemcpyDeviceToHost, c->stream);
+        cudaError_t e = cudaStreamSynchronize(c->stream);
+        if (e != cudaSuccess) return cuda_check(c, e, "octree level");
+        const int total = (int)*h_total;
+        if (le + total > cap) {
+            int ncap = le + total + (le + total) / 2 + 1024;
+            if ((st = grow(ncap, le))) return st;
+            cap = ncap;
+        }
+        {
+            ProfScope ps_(c, TG_K_TREE);
+            oct_emit<<<(m + 255) / 256, 256, 0, c->stream>>>(keys, lb, le, level, cx, cy, cz, first, count, child_first,
+                                                            parent, nchild, off, cnt);
+        }
+        c->level_begin.push_back(le);
+        lb = le;
+        le = le + total;
+    }
+    if (c->level_begin.back() != le) c->level_begin.push_back(le);
+    *ncell_out = le;
+    return cuda_check(c, cudaGetLastError(), "octree");
+}
+
+TreeView tree_view(tg_ctx *c, int n, int ncell)
+{
+    TreeView t;
+    t.n = n;
+    t.ncell = ncell;
+    t.level = static_cast<const uint8_t *>(c->buf[B_C_LEVEL].p);
+    t.cx = static_cast<const uint32_t *>(c->buf[B_C_X].p);
+    t.cy = static_cast<const uint32_t *>(c->buf[B_C_Y].p);
+    t.cz = static_cast<const uint32_t *>(c->buf[B_C_Z].p);
+    t.first = static_cast<const int32_t *>(c->buf[B_C_FIRST].p);
+    t.count = static_cast<const int32_t *>(c->buf[B_C_COUNT].p);
+    t.child_first = static_cast<const int32_t *>(c->buf[B_C_CHILD].p);
+    t.parent = static_cast<const int32_t *>(c->buf[B_C_PARENT].p);
+    t.nchild = static_cast<const uint8_t *>(c->buf[B_C_NCHILD].p);
+    return t;
+}
+
+}  // namespace tg
