@@ -175,6 +175,32 @@ tg_status tg_get_profile(tg_ctx *ctx, tg_profile *out);
 tg_status tg_timesteps(tg_ctx *ctx, int64_t n, const double *a_old, const double *a_cur,
                        double *dt, int32_t *rung);
 
+/* ---- allocation-free variant (the paper has no counterpart; this is a library service) ----
+ *
+ * For callers that must not allocate device memory: applications whose GPU memory is owned by
+ * another allocator or held to a fixed budget, and loops that cannot take the device-wide
+ * synchronisation a cudaMalloc can cause.  Creating a context allocates, so this call needs no
+ * context.  It computes what tg_build_tree computes first -- the root cube, the Morton keys and
+ * the stable (key, particle index) radix sort -- and returns the sorted keys and permutation.
+ *
+ *   n        number of particles, 0 <= n <= TG_NOALLOC_MAX_N; larger n returns TG_ERR_ARG
+ *   pos      device, 3*n float64 (SoA x, y, z), read only
+ *   keys_out device, n uint64 output: Morton keys in sorted order
+ *   perm_out device, n int64 output: perm_out[s] = index of the particle at sorted position s
+ *   cuda_stream  the cudaStream_t the work is enqueued on (NULL = legacy default stream)
+ *
+ * It allocates nothing (no cudaMalloc, cudaFree or allocating library call).  Its scratch is one
+ * file-scope device array of about 6.2 MB that every GPU loading the library holds until the
+ * process exits.  The first call on a device looks up that array's device address
+ * (cudaGetSymbolAddress) with the device current; make that first call before any stream
+ * capture.  All calls share the array, so two calls whose work overlaps on the GPU (different
+ * streams, or host threads racing) corrupt each other's results: serialise them.  Returns
+ * TG_ERR_ARG for bad sizes or non-device pointers and TG_ERR_CUDA if a launch fails; the call is
+ * asynchronous otherwise. */
+#define TG_NOALLOC_MAX_N 262144
+tg_status tg_morton_sort_noalloc(int64_t n, const double *pos, uint64_t *keys_out, int64_t *perm_out,
+                                 void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -107,6 +107,8 @@ def load() -> C.CDLL:
             L.tg_list_counts.argtypes = [_vp, C.POINTER(_i64), C.POINTER(_i64)]
             L.tg_get_lists.argtypes = [_vp] * 5
             L.tg_timesteps.argtypes = [_vp, _i64, _vp, _vp, _vp, _vp]
+            L.tg_morton_sort_noalloc.argtypes = [_i64, _vp, _vp, _vp, _vp]
+            L.tg_morton_sort_noalloc.restype = C.c_int
             L.tg_set_profiling.argtypes = [_vp, C.c_int]
             L.tg_get_profile.argtypes = [_vp, C.POINTER(tg_profile)]
             for name in ("tg_create", "tg_destroy", "tg_get_stats", "tg_reset_stats", "tg_build_tree",
@@ -257,6 +259,24 @@ def tg_get_profile(ctx) -> dict:
     out = {name: {"ms": pr.ms[k], "launches": pr.launches[k]} for k, name in enumerate(KERNEL_CLASSES)}
     out["_all"] = {"ms": sum(pr.ms[k] for k in range(8)), "launches": sum(pr.launches[k] for k in range(8))}
     return out
+
+
+TG_NOALLOC_MAX_N = 262144
+
+
+def tg_morton_sort_noalloc(pos, keys_out=None, perm_out=None, stream=None):
+    """Root cube, Morton keys and stable radix sort without any device allocation inside the
+    library (scratch is a fixed static device array; n <= TG_NOALLOC_MAX_N).  Returns
+    (keys (n,) uint64 as int64 storage, perm (n,) int64).  Calls overlapping on the GPU race."""
+    n = pos.shape[1]
+    if keys_out is None:
+        keys_out = torch.empty(n, dtype=torch.int64, device=pos.device)
+    if perm_out is None:
+        perm_out = torch.empty(n, dtype=torch.int64, device=pos.device)
+    rc = load().tg_morton_sort_noalloc(n, _ptr(pos), _ptr(keys_out), _ptr(perm_out), _vp(_stream_handle(stream)))
+    if rc != 0:
+        raise TGError(rc, "tg_morton_sort_noalloc")
+    return keys_out, perm_out
 
 
 def tg_timesteps(ctx, a_old, a_cur):

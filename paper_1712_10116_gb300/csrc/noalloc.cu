@@ -1,0 +1,150 @@
+// noalloc.cu -- tg_morton_sort_noalloc: root cube, Morton keys and the stable radix sort for
+// callers that cannot allocate device memory.
+//
+// Some callers must not call cudaMalloc: applications whose device memory is owned by another
+// allocator (a framework's pool, a fixed memory budget that raw allocations would break) and
+// loops that cannot afford the device-wide synchronisation an allocation can cause.  This entry
+// point takes the caller's input and output buffers and keeps all of its scratch in one
+// file-scope device array of fixed size, so it never allocates.
+//
+// The array lives in every GPU that loads the library until the process exits.  Host code must
+// not use the array's name as a pointer: on the host it is only a stand-in for the device
+// symbol.  The device address is looked up once per device with cudaGetSymbolAddress, on the
+// first call made with that device current.
+#include <mutex>
+
+#include "tg_common.cuh"
+
+namespace {
+
+using namespace tg;
+
+constexpr int64_t kMaxN = TG_NOALLOC_MAX_N;
+constexpr int kMaxSortBlocks = (int)((kMaxN + kSortTileItems - 1) / kSortTileItems);
+constexpr int kMaxBboxBlocks = 2 * 152;
+constexpr int64_t kHistItems = 256LL * kMaxSortBlocks;
+constexpr int64_t kScanTmpItems = 2 * ((kHistItems + kScanTileItems - 1) / kScanTileItems) + 64;
+
+// byte layout of the scratch array (every part 256-byte aligned)
+constexpr size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+constexpr size_t kOffGeom = 0;
+constexpr size_t kOffPartial = align256(kOffGeom + sizeof(Geom));
+constexpr size_t kOffKeys0 = align256(kOffPartial + sizeof(double) * 6 * kMaxBboxBlocks);
+constexpr size_t kOffKeys1 = align256(kOffKeys0 + sizeof(uint64_t) * kMaxN);
+constexpr size_t kOffVals0 = align256(kOffKeys1 + sizeof(uint64_t) * kMaxN);
+constexpr size_t kOffVals1 = align256(kOffVals0 + sizeof(uint32_t) * kMaxN);
+constexpr size_t kOffHist = align256(kOffVals1 + sizeof(uint32_t) * kMaxN);
+constexpr size_t kOffScan = align256(kOffHist + sizeof(uint32_t) * kHistItems);
+constexpr size_t kScratchBytes = align256(kOffScan + sizeof(uint32_t) * kScanTmpItems);
+static_assert(kScratchBytes < (8u << 20), "the allocation-free scratch must stay modest (< 8 MB)");
+
+// The scratch.  Device code could name it directly; host code uses the looked-up address.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_setup_mutex;
+unsigned char *g_scratch_addr[kMaxDevices] = {nullptr};
+
+// Address of the scratch on the current device (looked up on the first call per device).
+tg_status scratch_for_current_device(unsigned char **out)
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return TG_ERR_CUDA;
+    }
+    if (dev < 0 || dev >= kMaxDevices) return TG_ERR_ARG;
+    std::lock_guard<std::mutex> lock(g_setup_mutex);
+    if (!g_scratch_addr[dev]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || p == nullptr) {
+            cudaGetLastError();
+            return TG_ERR_CUDA;
+        }
+        g_scratch_addr[dev] = static_cast<unsigned char *>(p);
+    }
+    *out = g_scratch_addr[dev];
+    return TG_OK;
+}
+
+__global__ void noalloc_export(int n, const uint64_t *keys, const uint32_t *vals, uint64_t *keys_out, int64_t *perm_out)
+{
+    for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < n; s += (int64_t)gridDim.x * blockDim.x) {
+        keys_out[s] = keys[s];
+        perm_out[s] = (int64_t)vals[s];
+    }
+}
+
+// exclusive scan with caller-provided scratch (same kernels as the context path)
+cudaError_t scan_with_scratch(cudaStream_t st, const uint32_t *in, uint32_t *out, int n, uint32_t *tmp)
+{
+    struct Level { uint32_t *out; int n, ntiles; uint32_t *sums, *pre; };
+    Level lv[8];
+    int depth = 0;
+    const uint32_t *cin = in;
+    uint32_t *cout = out;
+    int cn = n;
+    uint32_t *cursor = tmp;
+    while (depth < 8) {
+        const int nt = (cn + kScanTileItems - 1) / kScanTileItems;
+        lv[depth] = {cout, cn, nt, cursor, cursor + nt};
+        scan_tiles<<<nt, 512, 0, st>>>(cin, cout, cursor, cn);
+        ++depth;
+        if (nt == 1) break;
+        cin = cursor;
+        cout = cursor + nt;
+        cn = nt;
+        cursor += 2 * nt + 2;
+    }
+    for (int d = depth - 2; d >= 0; --d) scan_add<<<lv[d].ntiles, 512, 0, st>>>(lv[d].out, lv[d].pre, lv[d].n);
+    return cudaGetLastError();
+}
+
+int check_dev(const void *p)
+{
+    cudaPointerAttributes a;
+    if (!p || cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+}  // namespace
+
+extern "C" tg_status tg_morton_sort_noalloc(int64_t n, const double *pos, uint64_t *keys_out, int64_t *perm_out,
+                                            void *cuda_stream)
+{
+    if (n < 0 || n > kMaxN) return TG_ERR_ARG;
+    if (n == 0) return TG_OK;
+    if (!check_dev(pos) || !check_dev(keys_out) || !check_dev(perm_out)) return TG_ERR_ARG;
+    unsigned char *base = nullptr;
+    tg_status st = scratch_for_current_device(&base);
+    if (st) return st;
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    Geom *geom = reinterpret_cast<Geom *>(base + kOffGeom);
+    double *partial = reinterpret_cast<double *>(base + kOffPartial);
+    uint64_t *k0 = reinterpret_cast<uint64_t *>(base + kOffKeys0), *k1 = reinterpret_cast<uint64_t *>(base + kOffKeys1);
+    uint32_t *v0 = reinterpret_cast<uint32_t *>(base + kOffVals0), *v1 = reinterpret_cast<uint32_t *>(base + kOffVals1);
+    uint32_t *hist = reinterpret_cast<uint32_t *>(base + kOffHist), *scan = reinterpret_cast<uint32_t *>(base + kOffScan);
+    const int ni = (int)n;
+    // every scratch word used below is written before it is read, so nothing needs clearing
+    const int nb = grid_for(n, 256, kMaxBboxBlocks);
+    bbox_partial<<<nb, 256, 0, s>>>(pos, n, nullptr, ni, partial);
+    bbox_final<<<1, 32, 0, s>>>(partial, nb, ni, geom);
+    morton_keys<<<grid_for(n, 256), 256, 0, s>>>(pos, n, nullptr, ni, geom, k0, v0);
+    const int nblocks = (ni + kSortTileItems - 1) / kSortTileItems;
+    uint64_t *kin = k0, *kout = k1;
+    uint32_t *vin = v0, *vout = v1;
+    for (int shift = 0; shift < 64; shift += 8) {
+        radix_hist<<<nblocks, 256, 0, s>>>(kin, ni, shift, hist, nblocks);
+        if (scan_with_scratch(s, hist, hist, 256 * nblocks, scan) != cudaSuccess) return TG_ERR_CUDA;
+        radix_scatter<<<nblocks, 256, 0, s>>>(kin, vin, kout, vout, hist, ni, shift, nblocks);
+        std::swap(kin, kout);
+        std::swap(vin, vout);
+    }
+    noalloc_export<<<grid_for(n, 256), 256, 0, s>>>(ni, kin, vin, keys_out, perm_out);
+    if (cudaGetLastError() != cudaSuccess) return TG_ERR_CUDA;
+    return TG_OK;
+}

@@ -133,6 +133,19 @@ TreeView tree_view(tg_ctx *c, int n, int ncell);
 // Device-wide exclusive scan of uint32 (in place allowed); optional total to a device word.
 tg_status exclusive_scan_u32(tg_ctx *c, const uint32_t *in, uint32_t *out, int n, uint32_t *d_total);
 
+// Kernels of tree.cu, also launched by the allocation-free sort in noalloc.cu.
+constexpr int kSortTileItems = 2048;     // items per radix-sort block (256 threads x 8)
+constexpr int kScanTileItems = 2048;     // items per scan block (512 threads x 4)
+__global__ void scan_tiles(const uint32_t *in, uint32_t *out, uint32_t *tile_sums, int n);
+__global__ void scan_add(uint32_t *out, const uint32_t *tile_pre, int n);
+__global__ void bbox_partial(const double *pos, int64_t stride, const int64_t *sub, int n, double *partial);
+__global__ void bbox_final(const double *partial, int nparts, int n, Geom *g);
+__global__ void morton_keys(const double *pos, int64_t stride, const int64_t *sub, int n, const Geom *g,
+                            uint64_t *keys, uint32_t *vals);
+__global__ void radix_hist(const uint64_t *keys, int n, int shift, uint32_t *hist, int nblocks);
+__global__ void radix_scatter(const uint64_t *keys_in, const uint32_t *vals_in, uint64_t *keys_out,
+                              uint32_t *vals_out, const uint32_t *offsets, int n, int shift, int nblocks);
+
 // ---- fmm.cu
 // Full FMM evaluation on a (sub)set of particles.  Outputs are in input order q:
 // acc (3 SoA arrays of length n with stride `out_stride`), pot (nullable).
