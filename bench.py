@@ -1,7 +1,7 @@
 """Benchmark: particle-forces/s of the momentum-conserving FMM + HHS step on one GB300.
 
 Workload (default): cold collapse of a uniform-density sphere, N = 2^20, R = 1, at rest,
-Wendland C2 softening eps = 0.005, p = 6, theta = 0.5, kappa = 1, n_crit = 64, float32 P2P/M2L,
+Wendland C2 softening eps = 0.005, p = 6, theta = 0.5, kappa = 1, n_crit = 96 (measured best of 48-128), float32 P2P/M2L,
 HHS with eta = 0.025, k_max = 10 and dt_max = 1/16 (the t = 0 sphere then spans rungs 0-3).
 One step = one rung-0 step of EVOLVE_HOLD (every stage of the hot path: keys, sort, octree,
 P2M/M2M, walk, M2L, P2P, L2L/L2P, timestep split, kicks, drifts), starting each time from the
@@ -42,6 +42,7 @@ def parse():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=512)
+    ap.add_argument("--n-crit", type=int, default=PARAMS["n_crit"])
     return ap.parse_args()
 
 
@@ -50,7 +51,7 @@ def workload(n, seed=1002):
     return ics.uniform_sphere(n, seed)
 
 
-PARAMS = dict(p=6, theta=0.5, eps=0.005, kernel=0, n_crit=64, kappa=1.0, eta=0.025, dt_max=1.0 / 16, k_max=10)
+PARAMS = dict(p=6, theta=0.5, eps=0.005, kernel=0, n_crit=96, kappa=1.0, eta=0.025, dt_max=1.0 / 16, k_max=10)
 
 
 # ---------------------------------------------------------------- clocks sampler
@@ -154,7 +155,7 @@ def run_ours(args):
     # replicas only: each rank integrates its own independent system (seed per rank)
     pos0, vel0, mass0 = workload(n, seed=1002 + rank)
     prec = tg.TG_PREC_FP32 if args.precision == "fp32" else tg.TG_PREC_FP64
-    prm = tg.Params(precision=prec, **PARAMS)
+    prm = tg.Params(precision=prec, **dict(PARAMS, n_crit=args.n_crit))
     solver = tg.Solver(prm, stream)
     P0 = torch.tensor(pos0, device=dev)
     V0 = torch.tensor(vel0, device=dev)

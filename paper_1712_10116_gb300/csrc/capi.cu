@@ -4,6 +4,7 @@
 #include <new>
 
 #include "tg_common.cuh"
+#include "m2l_sym.cuh"
 
 using namespace tg;
 
@@ -330,17 +331,46 @@ tg_status tg_get_lists(tg_ctx *c, int64_t *m2l_a, int64_t *m2l_b, int64_t *p2p_a
 {
     tg_status st = begin(c);
     if (st) return st;
-    std::vector<uint2> m(c->last_nm2l), p(c->last_np2p);
+    const size_t nc = (size_t)c->last_ncell;
+    std::vector<M2LBlock> blk(c->last_nblocks);
+    std::vector<uint2> p(c->last_np2p);
+    std::vector<uint8_t> nch(nc);
+    std::vector<int32_t> chf(nc);
     cudaError_t e = cudaSuccess;
-    if (!m.empty()) e = cudaMemcpyAsync(m.data(), c->buf[B_M2L].p, m.size() * sizeof(uint2), cudaMemcpyDeviceToHost, c->stream);
-    if (e == cudaSuccess && !p.empty())
-        e = cudaMemcpyAsync(p.data(), c->buf[B_P2P].p, p.size() * sizeof(uint2), cudaMemcpyDeviceToHost, c->stream);
+    auto cp = [&](void *dst, int slot, size_t bytes) {
+        if (e == cudaSuccess && bytes) e = cudaMemcpyAsync(dst, c->buf[slot].p, bytes, cudaMemcpyDeviceToHost, c->stream);
+    };
+    cp(blk.data(), B_M2L, blk.size() * sizeof(M2LBlock));
+    {
+        // pairs A != B from the front of the buffer, self pairs from its end
+        const size_t nself = (size_t)c->last_np2p_self, nother = p.size() - nself;
+        if (e == cudaSuccess && nother)
+            e = cudaMemcpyAsync(p.data(), c->buf[B_P2P].p, nother * sizeof(uint2), cudaMemcpyDeviceToHost, c->stream);
+        if (e == cudaSuccess && nself)
+            e = cudaMemcpyAsync(p.data() + nother, static_cast<uint2 *>(c->buf[B_P2P].p) + (c->p2p_cap - nself),
+                                nself * sizeof(uint2), cudaMemcpyDeviceToHost, c->stream);
+    }
+    cp(nch.data(), B_C_NCHILD, nc);
+    cp(chf.data(), B_C_CHILD, nc * sizeof(int32_t));
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) return cuda_check(c, e, "tg_get_lists");
-    for (size_t i = 0; i < m.size(); ++i) {
-        if (m2l_a) m2l_a[i] = m[i].x;
-        if (m2l_b) m2l_b[i] = m[i].y;
+    // expand the M2L blocks into unordered cell pairs
+    size_t q = 0;
+    for (const M2LBlock &b : blk) {
+        const bool oa = nch[b.a] != 0, ob = nch[b.b] != 0;
+        const int ni = oa ? nch[b.a] : 1, nj = ob ? nch[b.b] : 1;
+        const int ba = oa ? chf[b.a] : (int)b.a, bb = ob ? chf[b.b] : (int)b.b;
+        for (int i = 0; i < ni; ++i)
+            for (int j = 0; j < nj; ++j)
+                if ((b.mask >> (8 * i + j)) & 1ull) {
+                    if ((int64_t)q < c->last_nm2l) {
+                        if (m2l_a) m2l_a[q] = ba + i;
+                        if (m2l_b) m2l_b[q] = bb + j;
+                    }
+                    ++q;
+                }
     }
+    if ((int64_t)q != c->last_nm2l) return set_err(c, TG_ERR_STATE, "M2L block expansion mismatch");
     for (size_t i = 0; i < p.size(); ++i) {
         if (p2p_a) p2p_a[i] = p[i].x;
         if (p2p_b) p2p_b[i] = p[i].y;

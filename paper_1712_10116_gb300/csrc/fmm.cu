@@ -1,17 +1,17 @@
 // fmm.cu -- one FMM evaluation (the Poisson-solver call of Algorithm 3, Zhu 2017):
-// upward pass (P2M, M2M), dual tree walk (Algorithm 4) emitting unordered cell pairs, mutual
-// M2L and P2P (Sec. 2.1: F_AB = -F_BA), downward pass (L2L, L2P) and the direct-summation
-// reference used to measure force errors.
+// upward pass (P2M, M2M), dual tree walk (Algorithm 4) emitting blocks of unordered cell pairs,
+// mutual M2L and P2P (Sec. 2.1: F_AB = -F_BA), downward pass (L2L, L2P) and the
+// direct-summation reference used to measure force errors.
 //
-// Expansions are Cartesian Taylor series truncated at total degree p:
-//   M_A^j = sum_{i in A} m_i (x_i - z_A)^j,  phi(x) = sum_n L^n (x - z)^n / n!,
-//   L_A^n += sum_{|j| <= p-|n|} (-1)^|j| / j!  M_B^j  D^{n+j}(z_A - z_B),  D^k = d^k G / dz^k,
-// and the same derivative tensor gives the reaction on B: L_B^n += (-1)^|n| sum_j M_A^j / j! D^{n+j}.
-// With this triangular truncation the net force of A on B is exactly minus that of B on A.
+// Expansions are Cartesian Taylor series truncated at total degree p, stored normalised by the
+// cell side s:
+//   M~_A^j = sum_{i in A} m_i ((x_i - z_A)/s_A)^j,   phi(x) = (1/s) sum_n L~^n ((x - z)/s)^n / n!.
+// With this scaling the translation operators have constant coefficients (a child's centre is at
+// +-s_P/4 from its parent's), and every stored number is O(1) in any precision.
 //
-// Each cell carries two moment classes (slow S and fast F particles) and two local
-// expansions: L_all (slow sinks, sources S + F) and L_S (fast sinks, sources S only).  One walk
-// and one evaluation thus serve a kickFS2S + kickS2F pair of Algorithm 2.
+// Each cell carries two moment classes (slow S and fast F particles) and two local expansions:
+// L_all (slow sinks, sources S + F) and L_S (fast sinks, sources S only).  One walk and one
+// evaluation thus serve a kickFS2S + kickS2F pair of Algorithm 2.
 #include "tg_common.cuh"
 #include "tg_tables.cuh"
 #include "p2p_tile.cuh"
@@ -57,6 +57,16 @@ __device__ __forceinline__ bool well_separated(const TreeView &t, const MacParam
     return true;
 }
 
+__device__ __forceinline__ double to_double(float v) { return f2d_exact(v); }
+__device__ __forceinline__ double to_double(double v) { return v; }
+
+template <class T>
+__device__ __forceinline__ T inv_fact_t(int k);
+template <>
+__device__ __forceinline__ float inv_fact_t<float>(int k) { return c_inv_fact_f[k]; }
+template <>
+__device__ __forceinline__ double inv_fact_t<double>(int k) { return c_inv_fact[k]; }
+
 // ------------------------------------------------------------------ per-particle local data
 // pf[s] = (x - z_leaf, y - z_leaf, z - z_leaf, m) in precision T; leaf_of[s] = leaf cell id.
 template <class T4>
@@ -82,66 +92,75 @@ __global__ void leaf_particles(TreeView t, const Geom *gp, const double *xs, con
 }
 
 // ------------------------------------------------------------------ P2M
-// Warp per leaf, lanes over coefficients; classes S (fast flag 0) and F (flag 1).  Monopole and
-// dipole (|k| <= 1) are accumulated in float64 from float64 offsets; higher orders in T.
-template <class T>
+// Moments live in two arrays: M[cell][class][ncp] in precision T (every order) and
+// M01[cell][class][4] in float64 (monopole and dipole, the "centre of mass" part, accumulated in
+// float64 from float64 positions).  Offsets are in units of the cell side s.
+template <class T, class T4>
 __global__ void p2m_leaves(TreeView t, const Geom *gp, const double *xs, const double *ys, const double *zs,
-                           const double *ms, const uint8_t *fs, int p, int nc, double *M)
+                           const double *ms, const uint8_t *fs, const T4 *pf, int p, int nc, int ncp, T *M,
+                           double *M01)
 {
     const Geom g = *gp;
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
     const int nwarps = (gridDim.x * blockDim.x) >> 5;
     for (int c = warp; c < t.ncell; c += nwarps) {
         if (t.nchild[c] != 0) continue;
+        const int first = t.first[c], count = t.count[c];
         const double zx = cell_centre(g, t, c, 0), zy = cell_centre(g, t, c, 1), zz = cell_centre(g, t, c, 2);
-        for (int k0 = 0; k0 < nc; k0 += 32) {
-            const int k = k0 + lane;
-            const bool on = k < nc;
-            const int ex = on ? c_mi_x[k] : 0, ey = on ? c_mi_y[k] : 0, ez = on ? c_mi_z[k] : 0;
-            if (k < 4) {
-                double accS = 0.0, accF = 0.0;
-                for (int s = t.first[c]; s < t.first[c] + t.count[c]; ++s) {
-                    double v = ms[s];
-                    if (ex) v *= xs[s] - zx;
-                    if (ey) v *= ys[s] - zy;
-                    if (ez) v *= zs[s] - zz;
-                    if (fs[s]) accF += v;
-                    else accS += v;
-                }
-                M[((size_t)c * 2 + 0) * nc + k] = accS;
-                M[((size_t)c * 2 + 1) * nc + k] = accF;
-            } else {
-                T accS = 0, accF = 0;
-                for (int s = t.first[c]; s < t.first[c] + t.count[c]; ++s) {
-                    const T rx = (T)(xs[s] - zx), ry = (T)(ys[s] - zy), rz = (T)(zs[s] - zz);
-                    T v = (T)ms[s];
+        const double inv_s = ldexp(1.0, (int)t.level[c] - g.log2L);
+        // float64 monopole and dipole: lanes over particles, then a warp reduction
+        double lo[2][4] = {{0, 0, 0, 0}, {0, 0, 0, 0}};
+        for (int s = first + lane; s < first + count; s += 32) {
+            const double m = ms[s];
+            const int cls = fs[s] ? 1 : 0;
+            lo[cls][0] += m;
+            lo[cls][1] += m * ((xs[s] - zx) * inv_s);
+            lo[cls][2] += m * ((ys[s] - zy) * inv_s);
+            lo[cls][3] += m * ((zs[s] - zz) * inv_s);
+        }
+#pragma unroll
+        for (int cls = 0; cls < 2; ++cls)
+#pragma unroll
+            for (int k = 0; k < 4; ++k) lo[cls][k] = warp_sum(lo[cls][k]);
+        if (lane < 8) {
+            const int cls = lane >> 2, k = lane & 3;
+            M01[((size_t)c * 2 + cls) * 4 + k] = lo[cls][k];
+            M[((size_t)c * 2 + cls) * ncp + k] = (T)lo[cls][k];
+        }
+        // every order >= 2 in T from the per-particle offsets: lanes over coefficients
+        const T inv_st = (T)ldexpf(1.0f, (int)t.level[c] - g.log2L);
+        for (int k = 4 + lane; k < ncp; k += 32) {
+            T accS = 0, accF = 0;
+            if (k < nc) {
+                const int ex = c_mi_x[k], ey = c_mi_y[k], ez = c_mi_z[k];
+                for (int s = first; s < first + count; ++s) {
+                    const T4 r = pf[s];
+                    const T rx = r.x * inv_st, ry = r.y * inv_st, rz = r.z * inv_st;
+                    T v = r.w;
                     for (int e = 0; e < ex; ++e) v *= rx;
                     for (int e = 0; e < ey; ++e) v *= ry;
                     for (int e = 0; e < ez; ++e) v *= rz;
                     if (fs[s]) accF += v;
                     else accS += v;
                 }
-                if (on) {
-                    M[((size_t)c * 2 + 0) * nc + k] = (double)accS;
-                    M[((size_t)c * 2 + 1) * nc + k] = (double)accF;
-                }
             }
+            M[((size_t)c * 2 + 0) * ncp + k] = accS;
+            M[((size_t)c * 2 + 1) * ncp + k] = accF;
         }
     }
 }
 
-// M2M for the parents of one level: M_P^n = sum_children sum_{k <= n} C(n,k) d^(n-k) M_c^k with
-// d = z_child - z_parent = (+-q, +-q, +-q), q = side_P / 4 (exact).  Thread per (cell, class, n);
-// |n| <= 1 in float64, higher orders in T.
 __constant__ float c_binom_f[9][9] = {
     {1, 0, 0, 0, 0, 0, 0, 0, 0},       {1, 1, 0, 0, 0, 0, 0, 0, 0},        {1, 2, 1, 0, 0, 0, 0, 0, 0},
     {1, 3, 3, 1, 0, 0, 0, 0, 0},       {1, 4, 6, 4, 1, 0, 0, 0, 0},        {1, 5, 10, 10, 5, 1, 0, 0, 0},
     {1, 6, 15, 20, 15, 6, 1, 0, 0},    {1, 7, 21, 35, 35, 21, 7, 1, 0},    {1, 8, 28, 56, 70, 56, 28, 8, 1}};
 
+// M2M for the parents of one level, normalised: with d = z_child - z_parent = (+-s/4)^3 and
+// s_child = s/2,  M~_P^n = sum_children sum_{k <= n} C(n,k) (+-1/4)^(n-k) 2^-|k| M~_c^k.
+// Thread per (cell, class, n); |n| <= 1 in float64 (M01), every order also in T (M).
 template <class T>
-__global__ void m2m_level(TreeView t, const Geom *gp, int lb, int le, int p, int nc, double *M)
+__global__ void m2m_level(TreeView t, int lb, int le, int p, int nc, int ncp, T *M, double *M01)
 {
-    const Geom g = *gp;
     const int64_t total = (int64_t)(le - lb) * 2 * nc;
     for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < total; w += (int64_t)gridDim.x * blockDim.x) {
         const int c = lb + (int)(w / (2 * nc));
@@ -150,110 +169,145 @@ __global__ void m2m_level(TreeView t, const Geom *gp, int lb, int le, int p, int
         const int nch = t.nchild[c];
         if (nch == 0) continue;
         const int nx = c_mi_x[n], ny = c_mi_y[n], nz = c_mi_z[n];
-        const double q = ldexp(g.L, -(int)t.level[c] - 2);
         if (n < 4) {
             double acc = 0.0;
-            for (int ch_i = 0; ch_i < nch; ++ch_i) {
-                const int ch = t.child_first[c] + ch_i;
-                const double *Mc = M + ((size_t)ch * 2 + cls) * nc;
+            for (int q = 0; q < nch; ++q) {
+                const int ch = t.child_first[c] + q;
+                const double *Mc = M01 + ((size_t)ch * 2 + cls) * 4;
                 double v = Mc[n];
                 if (n > 0) {
                     const uint32_t cc = nx ? t.cx[ch] : (ny ? t.cy[ch] : t.cz[ch]);
-                    v += ((cc & 1u) ? q : -q) * Mc[0];
+                    v = 0.5 * v + ((cc & 1u) ? 0.25 : -0.25) * Mc[0];
                 }
                 acc += v;
             }
-            M[((size_t)c * 2 + cls) * nc + n] = acc;
+            M01[((size_t)c * 2 + cls) * 4 + n] = acc;
+            M[((size_t)c * 2 + cls) * ncp + n] = (T)acc;
             continue;
         }
-        T qp[TG_PMAX + 1];
-        qp[0] = T(1);
-        for (int e = 1; e <= p; ++e) qp[e] = qp[e - 1] * (T)q;
         const int ncn = ncoef_dev(nx + ny + nz);
         T acc = 0;
-        for (int ch_i = 0; ch_i < nch; ++ch_i) {
-            const int ch = t.child_first[c] + ch_i;
+        for (int q = 0; q < nch; ++q) {
+            const int ch = t.child_first[c] + q;
             const bool neg_x = !(t.cx[ch] & 1u), neg_y = !(t.cy[ch] & 1u), neg_z = !(t.cz[ch] & 1u);
-            const double *Mc = M + ((size_t)ch * 2 + cls) * nc;
+            const T *Mc = M + ((size_t)ch * 2 + cls) * ncp;
             for (int k = 0; k < ncn; ++k) {
                 const int kx = c_mi_x[k], ky = c_mi_y[k], kz = c_mi_z[k];
                 if (kx > nx || ky > ny || kz > nz) continue;
                 const int dx = nx - kx, dy = ny - ky, dz = nz - kz;
                 const bool neg = ((neg_x && (dx & 1)) ^ (neg_y && (dy & 1)) ^ (neg_z && (dz & 1)));
-                T v = (T)(c_binom_f[nx][kx] * c_binom_f[ny][ky] * c_binom_f[nz][kz]) * qp[dx + dy + dz] * (T)Mc[k];
+                // 4^-(|n|-|k|) * 2^-|k| = 2^-(2|n| - |k|)
+                const T scale = (T)pow2f(-(2 * (dx + dy + dz) + (kx + ky + kz)));
+                const T v = (T)(c_binom_f[nx][kx] * c_binom_f[ny][ky] * c_binom_f[nz][kz]) * scale * Mc[k];
                 acc += neg ? -v : v;
             }
         }
-        M[((size_t)c * 2 + cls) * nc + n] = (double)acc;
+        M[((size_t)c * 2 + cls) * ncp + n] = acc;
+    }
+}
+
+// M2L operands: Ms[c][0] = (M~_S + M~_F)/j!, Ms[c][1] = M~_S/j! in precision T (padding zero);
+// the monopole and dipole come from the float64 sums.
+template <class T>
+__global__ void scale_moments(int ncell, int nc, int ncp, const T *M, const double *M01, T *Ms)
+{
+    const int64_t total = (int64_t)ncell * ncp;
+    for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < total; w += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t c = w / ncp;
+        const int k = (int)(w % ncp);
+        if (k < 4) {
+            const double mS = M01[(c * 2 + 0) * 4 + k], mF = M01[(c * 2 + 1) * 4 + k];
+            const double f = c_inv_fact[k];
+            Ms[(c * 2 + 0) * ncp + k] = (T)((mS + mF) * f);
+            Ms[(c * 2 + 1) * ncp + k] = (T)(mS * f);
+        } else {
+            const T mS = M[(c * 2 + 0) * ncp + k], mF = M[(c * 2 + 1) * ncp + k];
+            const T f = k < nc ? inv_fact_t<T>(k) : T(0);
+            Ms[(c * 2 + 0) * ncp + k] = (mS + mF) * f;
+            Ms[(c * 2 + 1) * ncp + k] = mS * f;
+        }
     }
 }
 
 // ------------------------------------------------------------------ dual tree walk
-// Breadth-first Algorithm 4 over UNORDERED pairs: a frontier of (a, b), a == b for self pairs.
-// Self pair: leaf -> P2P(a, a); else all child pairs (ci <= cj), both cells opened.
-// Distinct pair: well separated -> M2L; both leaves -> P2P; one leaf -> open the other; else
-// open both (all child pairs).  This is the directed walk from (root, root) with each
-// unordered pair kept once.
+// Breadth-first Algorithm 4 over UNORDERED pairs.  The frontier holds pairs (A, B) that are not
+// well separated and not both leaves, i.e. pairs to open: both cells when both have children
+// (the paper's "open both" rule), otherwise the non-leaf one; a self pair (A, A) opens A and
+// yields the child pairs ci <= cj.  Each child pair (x, y) is classified at once:
+//   x == y           -> P2P(x, x) if x is a leaf, else frontier
+//   well separated   -> bit (i, j) of this pair's M2L block
+//   both leaves      -> P2P(x, y)
+//   otherwise        -> frontier
 struct WalkOut {
     uint2 *front_out;
-    uint2 *m2l;
+    M2LBlock *blocks;
     uint2 *p2p;
-    unsigned long long *counters;   // [0] frontier, [1] m2l, [2] p2p
-    unsigned long long cap_front, cap_m2l, cap_p2p;
+    unsigned long long *counters;   // [0] frontier, [1] M2L blocks, [2] P2P pairs A != B, [3] M2L pairs,
+                                    // [4] self P2P pairs (A, A), stored from the end of the P2P buffer
+    unsigned long long cap_front, cap_blocks, cap_p2p;
 };
-
-__device__ __forceinline__ void emit(uint2 *arr, unsigned long long cap, unsigned long long *ctr, uint2 v)
-{
-    unsigned long long i = atomicAdd(ctr, 1ull);
-    if (i < cap) arr[i] = v;
-}
 
 __global__ void walk_step(TreeView t, MacParams mp, const uint2 *front_in, int n_in, WalkOut o)
 {
     for (int w = blockIdx.x * blockDim.x + threadIdx.x; w < n_in; w += gridDim.x * blockDim.x) {
         const uint2 pr = front_in[w];
-        const int a = (int)pr.x, b = (int)pr.y;
-        const int na = t.nchild[a], nb = t.nchild[b];
-        if (a == b) {
-            if (na == 0) {
-                emit(o.p2p, o.cap_p2p, o.counters + 2, make_uint2(a, a));
-            } else {
-                const int f = t.child_first[a];
-                const unsigned long long k = (unsigned long long)na * (na + 1) / 2;
-                unsigned long long base = atomicAdd(o.counters + 0, k);
-                for (int i = 0; i < na; ++i)
-                    for (int j = i; j < na; ++j, ++base)
-                        if (base < o.cap_front) o.front_out[base] = make_uint2(f + i, f + j);
+        const int A = (int)pr.x, B = (int)pr.y;
+        const bool self = A == B;
+        const bool openA = t.nchild[A] != 0, openB = t.nchild[B] != 0;
+        const int ni = openA ? t.nchild[A] : 1, nj = openB ? t.nchild[B] : 1;
+        const int baseA = openA ? t.child_first[A] : A, baseB = openB ? t.child_first[B] : B;
+        unsigned long long mask = 0;
+        int n_front = 0, n_p2p = 0, n_self = 0;
+        // pass 1: classify and count
+        for (int i = 0; i < ni; ++i)
+            for (int j = self ? i : 0; j < nj; ++j) {
+                const int x = baseA + i, y = baseB + j;
+                const bool lx = t.nchild[x] == 0, ly = t.nchild[y] == 0;
+                if (x == y) {
+                    if (lx) ++n_self;
+                    else ++n_front;
+                } else if (well_separated(t, mp, x, y)) {
+                    mask |= 1ull << (8 * i + j);
+                } else if (lx && ly) {
+                    ++n_p2p;
+                } else {
+                    ++n_front;
+                }
             }
-            continue;
+        unsigned long long fb = n_front ? atomicAdd(o.counters + 0, (unsigned long long)n_front) : 0;
+        unsigned long long pb = n_p2p ? atomicAdd(o.counters + 2, (unsigned long long)n_p2p) : 0;
+        unsigned long long sb = n_self ? atomicAdd(o.counters + 4, (unsigned long long)n_self) : 0;
+        if (mask) {
+            const unsigned long long bb = atomicAdd(o.counters + 1, 1ull);
+            atomicAdd(o.counters + 3, (unsigned long long)__popcll(mask));
+            if (bb < o.cap_blocks) o.blocks[bb] = M2LBlock{(uint32_t)A, (uint32_t)B, mask};
         }
-        if (well_separated(t, mp, a, b)) {
-            emit(o.m2l, o.cap_m2l, o.counters + 1, make_uint2(a, b));
-        } else if (na == 0 && nb == 0) {
-            emit(o.p2p, o.cap_p2p, o.counters + 2, make_uint2(a, b));
-        } else if (na == 0) {
-            unsigned long long base = atomicAdd(o.counters + 0, (unsigned long long)nb);
-            for (int j = 0; j < nb; ++j, ++base)
-                if (base < o.cap_front) o.front_out[base] = make_uint2(a, t.child_first[b] + j);
-        } else if (nb == 0) {
-            unsigned long long base = atomicAdd(o.counters + 0, (unsigned long long)na);
-            for (int i = 0; i < na; ++i, ++base)
-                if (base < o.cap_front) o.front_out[base] = make_uint2(t.child_first[a] + i, b);
-        } else {
-            unsigned long long base = atomicAdd(o.counters + 0, (unsigned long long)na * nb);
-            for (int i = 0; i < na; ++i)
-                for (int j = 0; j < nb; ++j, ++base)
-                    if (base < o.cap_front) o.front_out[base] = make_uint2(t.child_first[a] + i, t.child_first[b] + j);
-        }
+        if (!n_front && !n_p2p && !n_self) continue;
+        // pass 2: write the frontier and P2P entries
+        for (int i = 0; i < ni; ++i)
+            for (int j = self ? i : 0; j < nj; ++j) {
+                if ((mask >> (8 * i + j)) & 1ull) continue;
+                const int x = baseA + i, y = baseB + j;
+                const bool lx = t.nchild[x] == 0, ly = t.nchild[y] == 0;
+                if (x == y && lx) {
+                    if (sb < o.cap_p2p) o.p2p[o.cap_p2p - 1 - sb] = make_uint2(x, x);
+                    ++sb;
+                } else if (x != y && lx && ly) {
+                    if (pb < o.cap_p2p) o.p2p[pb] = make_uint2(x, y);
+                    ++pb;
+                } else {
+                    if (fb < o.cap_front) o.front_out[fb] = make_uint2(x, y);
+                    ++fb;
+                }
+            }
     }
 }
 
-// ------------------------------------------------------------------ L2L (one level)
-// L_c^n += sum_{k >= n, |k| <= p} L_P^k d^(k-n) / (k-n)!, d = z_c - z_P.  Thread per (cell, class, n).
+// ------------------------------------------------------------------ L2L (one level), normalised
+// L~_c^n += sum_{k >= n} L~_P^k (+-1/4)^(k-n) / (k-n)! * 2^-(|n|+1).  Thread per (cell, class, n).
 template <class T>
-__global__ void l2l_level(TreeView t, const Geom *gp, int lb, int le, int p, int nc, int ncls, T *L)
+__global__ void l2l_level(TreeView t, int lb, int le, int p, int nc, int ncp, int ncls, T *L)
 {
-    const Geom g = *gp;
     const int64_t total = (int64_t)(le - lb) * ncls * nc;
     for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < total; w += (int64_t)gridDim.x * blockDim.x) {
         const int c = lb + (int)(w / (ncls * nc));
@@ -261,47 +315,49 @@ __global__ void l2l_level(TreeView t, const Geom *gp, int lb, int le, int p, int
         const int n = (int)(w % nc);
         const int par = t.parent[c];
         if (par < 0) continue;
-        const T dx = (T)(cell_centre(g, t, c, 0) - cell_centre(g, t, par, 0));
-        const T dy = (T)(cell_centre(g, t, c, 1) - cell_centre(g, t, par, 1));
-        const T dz = (T)(cell_centre(g, t, c, 2) - cell_centre(g, t, par, 2));
+        const bool neg_x = !(t.cx[c] & 1u), neg_y = !(t.cy[c] & 1u), neg_z = !(t.cz[c] & 1u);
         const int nx = c_mi_x[n], ny = c_mi_y[n], nz = c_mi_z[n];
-        const T *Lp = L + ((size_t)par * 2 + cls) * nc;
+        const T *Lp = L + ((size_t)par * 2 + cls) * ncp;
         T acc = 0;
         for (int k = 0; k < nc; ++k) {
             const int kx = c_mi_x[k], ky = c_mi_y[k], kz = c_mi_z[k];
             if (kx < nx || ky < ny || kz < nz) continue;
-            T v = Lp[k] * (T)(c_inv_fact[c_mi_lookup[((kx - nx) * 9 + (ky - ny)) * 9 + (kz - nz)]]);
-            for (int e = nx; e < kx; ++e) v *= dx;
-            for (int e = ny; e < ky; ++e) v *= dy;
-            for (int e = nz; e < kz; ++e) v *= dz;
-            acc += v;
+            const int dx = kx - nx, dy = ky - ny, dz = kz - nz;
+            const bool neg = ((neg_x && (dx & 1)) ^ (neg_y && (dy & 1)) ^ (neg_z && (dz & 1)));
+            const T coef = inv_fact_t<T>(c_mi_lookup[(dx * 9 + dy) * 9 + dz]) *
+                           (T)ldexpf(1.0f, -(2 * (dx + dy + dz) + nx + ny + nz + 1));
+            const T v = Lp[k] * coef;
+            acc += neg ? -v : v;
         }
-        L[((size_t)c * 2 + cls) * nc + n] += acc;
+        L[((size_t)c * 2 + cls) * ncp + n] += acc;
     }
 }
 
-// ------------------------------------------------------------------ L2P
-// phi = sum_n L^n rho^n / n!, a = -grad phi.  Thread per particle; writes acc4 (= initialises it).
+// ------------------------------------------------------------------ L2P, normalised
+// With r = (x - z)/s:  phi = (1/s) sum_n L~^n r^n/n!,  a_e = -(1/s^2) sum_m L~^{m+e} r^m/m!.
+// Thread per particle; writes acc4 (= initialises it).
 template <class T, class T4>
-__global__ void l2p_particles(int n, const T4 *pf, const int32_t *leaf_of, const uint8_t *fs, int masked, int p,
-                              int nc, const T *L, double *acc4)
+__global__ void l2p_particles(int n, TreeView t, int log2L, const T4 *pf, const int32_t *leaf_of, const uint8_t *fs,
+                              int masked, int p, int nc, int ncp, const T *L, double *acc4)
 {
     for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
         const T4 r = pf[s];
         const int c = leaf_of[s];
         const int cls = (masked && fs[s]) ? 1 : 0;
-        const T *Lc = L + ((size_t)c * 2 + cls) * nc;
+        const T *Lc = L + ((size_t)c * 2 + cls) * ncp;
+        const T inv_s = (T)ldexpf(1.0f, (int)t.level[c] - log2L);
+        const T rx = r.x * inv_s, ry = r.y * inv_s, rz = r.z * inv_s;
         T px[TG_PMAX + 1], py[TG_PMAX + 1], pz[TG_PMAX + 1];
         px[0] = py[0] = pz[0] = (T)1;
         for (int e = 1; e <= p; ++e) {
-            px[e] = px[e - 1] * r.x;
-            py[e] = py[e - 1] * r.y;
-            pz[e] = pz[e - 1] * r.z;
+            px[e] = px[e - 1] * rx;
+            py[e] = py[e - 1] * ry;
+            pz[e] = pz[e - 1] * rz;
         }
         T phi = 0, gx = 0, gy = 0, gz = 0;
         for (int k = 0; k < nc; ++k) {
             const int kx = c_mi_x[k], ky = c_mi_y[k], kz = c_mi_z[k];
-            const T mono = px[kx] * py[ky] * pz[kz] * (T)c_inv_fact[k];
+            const T mono = px[kx] * py[ky] * pz[kz] * inv_fact_t<T>(k);
             phi += Lc[k] * mono;
             if (kx + ky + kz < p) {
                 gx += Lc[c_mi_lookup[((kx + 1) * 9 + ky) * 9 + kz]] * mono;
@@ -309,10 +365,11 @@ __global__ void l2p_particles(int n, const T4 *pf, const int32_t *leaf_of, const
                 gz += Lc[c_mi_lookup[(kx * 9 + ky) * 9 + kz + 1]] * mono;
             }
         }
-        acc4[s] = -(double)gx;
-        acc4[(size_t)n + s] = -(double)gy;
-        acc4[2 * (size_t)n + s] = -(double)gz;
-        acc4[3 * (size_t)n + s] = (double)phi;
+        const T is2 = inv_s * inv_s;
+        acc4[s] = to_double(-gx * is2);
+        acc4[(size_t)n + s] = to_double(-gy * is2);
+        acc4[2 * (size_t)n + s] = to_double(-gz * is2);
+        acc4[3 * (size_t)n + s] = to_double(phi * inv_s);
     }
 }
 
@@ -328,11 +385,6 @@ __global__ void scatter_out(int n, const uint32_t *perm, const double *acc4, dou
     }
 }
 
-__global__ void convert_moments(const double *M, float *Mf, int64_t count)
-{
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x)
-        Mf[i] = (float)M[i];
-}
 
 // ------------------------------------------------------------------ direct summation (float64)
 __global__ void direct_sum(int64_t n, const double *pos, const double *mass, const uint8_t *fast, int64_t n_sink,
@@ -407,18 +459,15 @@ tg_status direct_eval(tg_ctx *c, int64_t n, const double *pos, const double *mas
 }
 
 // ------------------------------------------------------------------ orchestration
-static tg_status run_walk(tg_ctx *c, const TreeView &t, const Geom *d_geom_host_unused, int64_t *n_m2l,
-                          int64_t *n_p2p)
+static tg_status run_walk(tg_ctx *c, const TreeView &t, int64_t *n_blocks, int64_t *n_m2l, int64_t *n_p2p,
+                          int64_t *n_self)
 {
-    (void)d_geom_host_unused;
     tg_status st;
     MacParams mp;
     mp.theta2 = c->prm.theta * c->prm.theta;
     mp.kappa2 = c->prm.kappa * c->prm.kappa;
     mp.eps = c->prm.eps;
     mp.wendland = c->prm.kernel == TG_KERNEL_WENDLAND_C2;
-    // log2 of the root side, copied back with the other counters below
-    mp.log2L = 0;
     {
         const Geom *dg = static_cast<const Geom *>(c->buf[B_GEOM].p);
         cudaMemcpyAsync(c->h_pinned + 32, &dg->log2L, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
@@ -426,36 +475,52 @@ static tg_status run_walk(tg_ctx *c, const TreeView &t, const Geom *d_geom_host_
         if (e != cudaSuccess) return cuda_check(c, e, "walk setup");
         mp.log2L = *reinterpret_cast<int *>(c->h_pinned + 32);
     }
-    size_t cap_front = (size_t)t.ncell * 16 + 1024, cap_m2l = (size_t)t.ncell * 64 + 1024,
-           cap_p2p = (size_t)t.ncell * 32 + 1024;
+    c->walk_log2L = mp.log2L;
+    size_t cap_front = (size_t)t.ncell * 8 + 1024, cap_blocks = (size_t)t.ncell * 8 + 1024,
+           cap_p2p = (size_t)t.ncell * 24 + 1024;
     for (int attempt = 0; attempt < 6; ++attempt) {
-        uint2 *f0, *f1, *m2l, *p2p;
+        uint2 *f0, *f1, *p2p;
+        M2LBlock *blocks;
         unsigned long long *ctr;
         if ((st = ensure_t(c, B_FRONT0, cap_front, &f0)) || (st = ensure_t(c, B_FRONT1, cap_front, &f1)) ||
-            (st = ensure_t(c, B_M2L, cap_m2l, &m2l)) || (st = ensure_t(c, B_P2P, cap_p2p, &p2p)) ||
+            (st = ensure_t(c, B_M2L, cap_blocks, &blocks)) || (st = ensure_t(c, B_P2P, cap_p2p, &p2p)) ||
             (st = ensure_t(c, B_WALK_CNT, 8, &ctr)))
             return st;
+        cudaMemsetAsync(ctr, 0, 8 * sizeof(unsigned long long), c->stream);
+        unsigned long long n_in = 0, tot_blocks = 0, tot_p2p = 0, tot_pairs = 0, tot_self = 0;
+        c->p2p_cap = (int64_t)cap_p2p;
+        if (t.ncell == 1) {
+            // the root is a leaf: one self P2P pair
+            const uint2 root = make_uint2(0, 0);
+            cudaMemcpyAsync(p2p + cap_p2p - 1, &root, sizeof(uint2), cudaMemcpyHostToDevice, c->stream);
+            *n_blocks = 0;
+            *n_m2l = 0;
+            *n_p2p = 0;
+            *n_self = 1;
+            return cuda_check(c, cudaStreamSynchronize(c->stream), "walk");
+        }
         const uint2 root = make_uint2(0, 0);
         cudaMemcpyAsync(f0, &root, sizeof(uint2), cudaMemcpyHostToDevice, c->stream);
-        cudaMemsetAsync(ctr, 0, 8 * sizeof(unsigned long long), c->stream);
-        unsigned long long n_in = 1, tot_m2l = 0, tot_p2p = 0;
+        n_in = 1;
         bool overflow = false;
         size_t need_front = 0;
         while (n_in > 0) {
             cudaMemsetAsync(ctr, 0, sizeof(unsigned long long), c->stream);   // frontier counter only
-            WalkOut o{f1, m2l, p2p, ctr, cap_front, cap_m2l, cap_p2p};
+            WalkOut o{f1, blocks, p2p, ctr, cap_front, cap_blocks, cap_p2p};
             {
                 ProfScope ps_(c, TG_K_WALK);
                 walk_step<<<grid_for((int64_t)n_in, 128), 128, 0, c->stream>>>(t, mp, f0, (int)n_in, o);
             }
-            cudaMemcpyAsync(c->h_pinned, ctr, 3 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, c->stream);
+            cudaMemcpyAsync(c->h_pinned, ctr, 5 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, c->stream);
             cudaError_t e = cudaStreamSynchronize(c->stream);
             if (e != cudaSuccess) return cuda_check(c, e, "walk step");
             const unsigned long long *h = reinterpret_cast<const unsigned long long *>(c->h_pinned);
             n_in = h[0];
-            tot_m2l = h[1];
+            tot_blocks = h[1];
             tot_p2p = h[2];
-            if (n_in > cap_front || tot_m2l > cap_m2l || tot_p2p > cap_p2p) {
+            tot_pairs = h[3];
+            tot_self = h[4];
+            if (n_in > cap_front || tot_blocks > cap_blocks || tot_p2p + tot_self > cap_p2p) {
                 overflow = true;
                 need_front = n_in > need_front ? n_in : need_front;
                 break;
@@ -464,80 +529,124 @@ static tg_status run_walk(tg_ctx *c, const TreeView &t, const Geom *d_geom_host_
             std::swap(c->buf[B_FRONT0], c->buf[B_FRONT1]);
         }
         if (!overflow) {
-            *n_m2l = (int64_t)tot_m2l;
+            *n_blocks = (int64_t)tot_blocks;
+            *n_m2l = (int64_t)tot_pairs;
             *n_p2p = (int64_t)tot_p2p;
+            *n_self = (int64_t)tot_self;
             return TG_OK;
         }
         cap_front = std::max(cap_front * 2, need_front + need_front / 2);
-        if (tot_m2l > cap_m2l) cap_m2l = tot_m2l * 2;
-        else cap_m2l = cap_m2l * 3 / 2;
-        if (tot_p2p > cap_p2p) cap_p2p = tot_p2p * 2;
-        else cap_p2p = cap_p2p * 3 / 2;
+        cap_blocks = tot_blocks > cap_blocks ? tot_blocks * 2 : cap_blocks * 3 / 2;
+        cap_p2p = tot_p2p + tot_self > cap_p2p ? (tot_p2p + tot_self) * 2 : cap_p2p * 3 / 2;
     }
     return set_err(c, TG_ERR_CAPACITY, "interaction lists did not fit after regrowth");
 }
 
+static inline int pad4(int x) { return (x + 3) & ~3; }
+
+template <class T>
+static tg_status launch_m2l(tg_ctx *c, const TreeView &t, const M2LBlock *blocks, int64_t nblocks, const T *Ms, T *L,
+                            int p, int nc, int ncp, bool masked);
+
+template <>
+tg_status launch_m2l<float>(tg_ctx *c, const TreeView &t, const M2LBlock *blocks, int64_t nblocks, const float *Ms,
+                            float *L, int p, int nc, int ncp, bool masked)
+{
+    const int plummer = c->prm.kernel == TG_KERNEL_PLUMMER;
+    const float eoL = (float)ldexp(c->prm.eps, -c->walk_log2L);
+    const int grid = grid_for(nblocks * 32, 128, c->num_sms * 16);
+    ProfScope ps_(c, TG_K_M2L);
+#define TG_M2L_F32(PP)                                                                                            \
+    case PP:                                                                                                      \
+        if (masked) m2l_blocks_f32<PP, true><<<grid, 128, 0, c->stream>>>(t, blocks, nblocks, Ms, L, ncp, eoL, plummer); \
+        else m2l_blocks_f32<PP, false><<<grid, 128, 0, c->stream>>>(t, blocks, nblocks, Ms, L, ncp, eoL, plummer);       \
+        break;
+    switch (p) {
+        TG_M2L_F32(1)
+        TG_M2L_F32(2)
+        TG_M2L_F32(3)
+        TG_M2L_F32(4)
+        TG_M2L_F32(5)
+        TG_M2L_F32(6)
+    default:
+        if (masked) m2l_blocks_generic<float, true><<<grid, 128, 0, c->stream>>>(t, blocks, nblocks, Ms, L, p, nc, ncp,
+                                                                                ldexp(c->prm.eps, -c->walk_log2L), plummer);
+        else m2l_blocks_generic<float, false><<<grid, 128, 0, c->stream>>>(t, blocks, nblocks, Ms, L, p, nc, ncp,
+                                                                          ldexp(c->prm.eps, -c->walk_log2L), plummer);
+    }
+#undef TG_M2L_F32
+    return cuda_check(c, cudaGetLastError(), "m2l launch");
+}
+
+template <>
+tg_status launch_m2l<double>(tg_ctx *c, const TreeView &t, const M2LBlock *blocks, int64_t nblocks, const double *Ms,
+                             double *L, int p, int nc, int ncp, bool masked)
+{
+    const int plummer = c->prm.kernel == TG_KERNEL_PLUMMER;
+    const double eoL = ldexp(c->prm.eps, -c->walk_log2L);
+    const int grid = grid_for(nblocks * 32, 128, c->num_sms * 16);
+    ProfScope ps_(c, TG_K_M2L);
+    if (masked) m2l_blocks_generic<double, true><<<grid, 128, 0, c->stream>>>(t, blocks, nblocks, Ms, L, p, nc, ncp, eoL, plummer);
+    else m2l_blocks_generic<double, false><<<grid, 128, 0, c->stream>>>(t, blocks, nblocks, Ms, L, p, nc, ncp, eoL, plummer);
+    return cuda_check(c, cudaGetLastError(), "m2l launch");
+}
+
 template <class T, class T4>
 static tg_status eval_typed(tg_ctx *c, int n, int ncell, const TreeView &t, const Geom *d_geom, bool masked,
-                            int64_t n_m2l, int64_t n_p2p)
+                            int64_t n_blocks, int64_t n_p2p, int64_t n_self)
 {
     tg_status st;
-    const int p = c->prm.p, nc = ncoef(p);
+    const int p = c->prm.p, nc = ncoef(p), ncp = pad4(nc);
     const double *xs = static_cast<const double *>(c->buf[B_XS].p), *ys = static_cast<const double *>(c->buf[B_YS].p),
                  *zs = static_cast<const double *>(c->buf[B_ZS].p), *ms = static_cast<const double *>(c->buf[B_MS].p);
     const uint8_t *fs = static_cast<const uint8_t *>(c->buf[B_FS].p);
     T4 *pf;
     int32_t *leaf_of;
-    double *M, *acc4;
-    T *L;
+    double *M01, *acc4;
+    T *M, *L, *Ms;
     if ((st = ensure_t(c, B_PF, n, &pf)) || (st = ensure_t(c, B_LEAF_OF, n, &leaf_of)) ||
-        (st = ensure_t(c, B_MOM, (size_t)ncell * 2 * nc, &M)) || (st = ensure_t(c, B_LOC, (size_t)ncell * 2 * nc, &L)) ||
-        (st = ensure_t(c, B_ACC, (size_t)4 * n, &acc4)))
+        (st = ensure_t(c, B_MOM, (size_t)ncell * 2 * ncp, &M)) || (st = ensure_t(c, B_MOMF, (size_t)ncell * 2 * ncp, &Ms)) ||
+        (st = ensure_t(c, B_MOM01, (size_t)ncell * 2 * 4, &M01)) ||
+        (st = ensure_t(c, B_LOC, (size_t)ncell * 2 * ncp, &L)) || (st = ensure_t(c, B_ACC, (size_t)4 * n, &acc4)))
         return st;
     const int ncls = masked ? 2 : 1;
     {
         ProfScope ps_(c, TG_K_UP);
         leaf_particles<T4><<<grid_for((int64_t)ncell * 32, 256), 256, 0, c->stream>>>(t, d_geom, xs, ys, zs, ms, pf, leaf_of);
     }
-    // upward pass
     {
         ProfScope ps_(c, TG_K_UP);
-        p2m_leaves<T><<<grid_for((int64_t)ncell * 32, 256), 256, 0, c->stream>>>(t, d_geom, xs, ys, zs, ms, fs, p, nc, M);
+        p2m_leaves<T, T4><<<grid_for((int64_t)ncell * 32, 256), 256, 0, c->stream>>>(t, d_geom, xs, ys, zs, ms, fs, pf, p, nc,
+                                                                                     ncp, M, M01);
     }
     const int nlev = (int)c->level_begin.size() - 1;
     for (int l = nlev - 2; l >= 0; --l) {
         const int lb = c->level_begin[l], le = c->level_begin[l + 1];
-        {
-            ProfScope ps_(c, TG_K_UP);
-            m2m_level<T><<<grid_for((int64_t)(le - lb) * 2 * nc, 128), 128, 0, c->stream>>>(t, d_geom, lb, le, p, nc, M);
-        }
+        ProfScope ps_(c, TG_K_UP);
+        m2m_level<T><<<grid_for((int64_t)(le - lb) * 2 * nc, 128), 128, 0, c->stream>>>(t, lb, le, p, nc, ncp, M, M01);
     }
-    // M2L (mutual) into zeroed local expansions
-    cudaMemsetAsync(L, 0, sizeof(T) * (size_t)ncell * 2 * nc, c->stream);
-    const uint2 *m2l = static_cast<const uint2 *>(c->buf[B_M2L].p);
+    {
+        ProfScope ps_(c, TG_K_UP);
+        scale_moments<T><<<grid_for((int64_t)ncell * ncp, 256), 256, 0, c->stream>>>(ncell, nc, ncp, M, M01, Ms);
+    }
+    cudaMemsetAsync(L, 0, sizeof(T) * (size_t)ncell * 2 * ncp, c->stream);
+    const M2LBlock *blocks = static_cast<const M2LBlock *>(c->buf[B_M2L].p);
     const uint2 *p2p = static_cast<const uint2 *>(c->buf[B_P2P].p);
-    const Mom<T> mom = make_moments<T>(c, M, (size_t)ncell * 2 * nc, &st);
-    if (st) return st;
-    if (n_m2l > 0) {
-        if ((st = launch_m2l<T>(c, t, d_geom, m2l, n_m2l, mom, L, p, nc, masked))) return st;
-    }
-    // downward pass
+    if (n_blocks > 0 && (st = launch_m2l<T>(c, t, blocks, n_blocks, Ms, L, p, nc, ncp, masked))) return st;
     for (int l = 1; l < nlev; ++l) {
         const int lb = c->level_begin[l], le = c->level_begin[l + 1];
-        {
-            ProfScope ps_(c, TG_K_DOWN);
-            l2l_level<T><<<grid_for((int64_t)(le - lb) * ncls * nc, 128), 128, 0, c->stream>>>(t, d_geom, lb, le, p, nc,
-                                                                                           ncls, L);
-        }
+        ProfScope ps_(c, TG_K_DOWN);
+        l2l_level<T><<<grid_for((int64_t)(le - lb) * ncls * nc, 128), 128, 0, c->stream>>>(t, lb, le, p, nc, ncp, ncls, L);
     }
     {
         ProfScope ps_(c, TG_K_DOWN);
-        l2p_particles<T, T4><<<grid_for(n, 128), 128, 0, c->stream>>>(n, pf, leaf_of, fs, masked ? 1 : 0, p, nc, L, acc4);
+        l2p_particles<T, T4><<<grid_for(n, 128), 128, 0, c->stream>>>(n, t, c->walk_log2L, pf, leaf_of, fs, masked ? 1 : 0,
+                                                                      p, nc, ncp, L, acc4);
     }
-    // P2P (mutual) adds onto the L2P result
-    if (n_p2p > 0) {
-        if ((st = launch_p2p<T, T4>(c, t, d_geom, p2p, n_p2p, pf, fs, masked, acc4))) return st;
-    }
+    if (n_p2p > 0 && (st = launch_p2p<T, T4>(c, t, d_geom, p2p, n_p2p, pf, fs, masked, false, acc4))) return st;
+    if (n_self > 0 &&
+        (st = launch_p2p<T, T4>(c, t, d_geom, p2p + (c->p2p_cap - n_self), n_self, pf, fs, masked, true, acc4)))
+        return st;
     return cuda_check(c, cudaGetLastError(), "fmm evaluation");
 }
 
@@ -554,15 +663,17 @@ tg_status fmm_eval(tg_ctx *c, int n, const double *pos, int64_t stride, const in
     int ncell = 0;
     if ((st = build_octree(c, n, &ncell))) return st;
     TreeView t = tree_view(c, n, ncell);
-    int64_t n_m2l = 0, n_p2p = 0;
-    if ((st = run_walk(c, t, d_geom, &n_m2l, &n_p2p))) return st;
+    int64_t n_blocks = 0, n_m2l = 0, n_p2p = 0, n_self = 0;
+    if ((st = run_walk(c, t, &n_blocks, &n_m2l, &n_p2p, &n_self))) return st;
     c->last_n = n;
     c->last_ncell = ncell;
     c->last_nm2l = n_m2l;
-    c->last_np2p = n_p2p;
+    c->last_nblocks = n_blocks;
+    c->last_np2p = n_p2p + n_self;
+    c->last_np2p_self = n_self;
     const bool masked = fast != nullptr;
-    if (c->prm.precision == TG_PREC_FP32) st = eval_typed<float, float4>(c, n, ncell, t, d_geom, masked, n_m2l, n_p2p);
-    else st = eval_typed<double, dbl4>(c, n, ncell, t, d_geom, masked, n_m2l, n_p2p);
+    if (c->prm.precision == TG_PREC_FP32) st = eval_typed<float, float4>(c, n, ncell, t, d_geom, masked, n_blocks, n_p2p, n_self);
+    else st = eval_typed<double, dbl4>(c, n, ncell, t, d_geom, masked, n_blocks, n_p2p, n_self);
     if (st) return st;
     const uint32_t *perm = static_cast<const uint32_t *>(c->buf[B_VALS0].p);
     const double *acc4 = static_cast<const double *>(c->buf[B_ACC].p);
@@ -573,7 +684,7 @@ tg_status fmm_eval(tg_ctx *c, int n, const double *pos, int64_t stride, const in
     c->stats.evaluations += 1;
     c->stats.sink_forces += n;
     c->stats.m2l_pairs += n_m2l;
-    c->stats.p2p_cell_pairs += n_p2p;
+    c->stats.p2p_cell_pairs += n_p2p + n_self;
     c->stats.cells += ncell;
     return cuda_check(c, cudaGetLastError(), "fmm scatter");
 }

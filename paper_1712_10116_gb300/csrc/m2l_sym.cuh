@@ -1,50 +1,163 @@
-// m2l_sym.cuh -- mutual cell-cell interaction (M2L, Sec. 2.1).  Each unordered well-separated
-// pair (A, B) is visited once: the derivative tensor D^k(z_A - z_B), |k| <= p, is built once and
-// both local expansions are updated,
-//   L_A^n += sum_j (-1)^|j|/j! M_B^j D^{n+j},   L_B^n += (-1)^|n| sum_j M_A^j/j! D^{n+j},
-// using D^k(-d) = (-1)^|k| D^k(d).  D comes from the McMurchie-Davidson auxiliary recurrence
-// R^(m)_{k+e_a} = d_a R^(m+1)_k + k_a R^(m+1)_{k-e_a}, R^(m)_0 = f_m, with f_m the m-th derivative
-// of G as a function of |d|^2/2: G = -1/r (Newton, used for Wendland pairs, which are farther
-// apart than eps) or -(r^2 + eps^2)^(-1/2) (Plummer).
+// m2l_sym.cuh -- mutual cell-cell interaction (M2L, Sec. 2.1 of Zhu 2017).
+//
+// The walk hands over M2L work in blocks: the well-separated child pairs (x_i, y_j) of one opened
+// cell pair (A, B), as an 8x8 bit mask.  Each unordered pair is evaluated once: the derivative
+// tensor D^k(d), |k| <= p, is built once and BOTH local expansions are updated,
+//   L_x^n += sum_j (-1)^|j|/j! M_y^j D^{n+j},   L_y^n += (-1)^|n| sum_j M_x^j/j! D^{n+j}
+// (D^k(-d) = (-1)^|k| D^k(d)), so the net forces of the two cells on each other cancel.
+//
+// Expansions are normalised by cell size s (M~^j = M^j / s^|j|, L~^n = L^n s^(|n|+1)) and the
+// offset is measured in units of the x cell, d' = (z_x - z_y)/s_x; with rho = s_y/s_x,
+//   L~_x^n += sum_j (-1)^|j| rho^|j| M~_y^j/j! D^{n+j}(d'),
+//   L~_y^n += (-1)^|n| rho^(|n|+1) sum_j M~_x^j/j! D^{n+j}(d'),
+// with the softening length scaled the same way (Plummer).  All terms are O(1): no overflow or
+// underflow in float32 however deep the tree.  D comes from the McMurchie-Davidson auxiliary
+// recurrence R^(m)_{k+e_a} = d_a R^(m+1)_k + k_a R^(m+1)_{k-e_a}.
+//
+// Lane layout of one warp over a block: round r in {0, 1}, lane l -> (i, j) = (4r + l/8, l%8).
+// The x-side sums of one row i are reduced over its 8 lanes, the y-side sums of one column j over
+// its 4 lanes, and one lane per row / column adds them to global memory.
 #pragma once
 #include "tg_common.cuh"
 #include "tg_tables.cuh"
+#include "m2l_gen.cuh"
 
 namespace tg {
 
-template <class T>
-struct Mom {
-    const T *M;
+struct M2LBlock {
+    uint32_t a, b;             // cell pair that was opened (a == b: self pair, only i < j bits set)
+    unsigned long long mask;   // bit 8i + j: pair (child i of a, child j of b) is well separated
 };
 
+// total degree of the k-th multi-index (ordering by total degree)
+__host__ __device__ constexpr int order_of(int k)
+{
+    int o = 0;
+    while ((o + 1) * (o + 2) * (o + 3) / 6 <= k) ++o;
+    return o;
+}
+
+// children of the opened cells (a cell that is not opened stands for itself)
+struct BlockGeom {
+    int baseA, baseB, ni, nj, lx, ly;
+};
+
+__device__ __forceinline__ BlockGeom block_geom(const TreeView &t, const M2LBlock &blk)
+{
+    BlockGeom bg;
+    const int A = (int)blk.a, B = (int)blk.b;
+    const bool openA = t.nchild[A] != 0, openB = t.nchild[B] != 0;
+    bg.ni = openA ? t.nchild[A] : 1;
+    bg.nj = openB ? t.nchild[B] : 1;
+    bg.baseA = openA ? t.child_first[A] : A;
+    bg.baseB = openB ? t.child_first[B] : B;
+    bg.lx = t.level[A] + (openA ? 1 : 0);
+    bg.ly = t.level[B] + (openB ? 1 : 0);
+    return bg;
+}
+
+// d' = (z_x - z_y) / s_x from the integer cell coordinates: the offset in units of half the finer
+// cell (exact integer) times 2^(lx - lf - 1) (exact power of two).
 template <class T>
-static Mom<T> make_moments(tg_ctx *c, const double *M, size_t count, tg_status *st);
-
-template <>
-Mom<double> make_moments<double>(tg_ctx *c, const double *M, size_t count, tg_status *st)
+__device__ __forceinline__ void pair_offset(const TreeView &t, int x, int y, int lx, int ly, T &dx, T &dy, T &dz)
 {
-    (void)c;
-    (void)count;
-    *st = TG_OK;
-    return Mom<double>{M};
+    const int lf = lx > ly ? lx : ly;
+    // |delta| < 2^23 (both centres lie in the root cube), so int32 holds it exactly
+    const T scale = (T)pow2f(lx - lf - 1);
+    dx = (T)(int)centre_delta(t.cx[x], lx, t.cx[y], ly, lf) * scale;
+    dy = (T)(int)centre_delta(t.cy[x], lx, t.cy[y], ly, lf) * scale;
+    dz = (T)(int)centre_delta(t.cz[x], lx, t.cz[y], ly, lf) * scale;
 }
 
-__global__ void convert_moments(const double *M, float *Mf, int64_t count);
-
-template <>
-Mom<float> make_moments<float>(tg_ctx *c, const double *M, size_t count, tg_status *st)
+// ------------------------------------------------------------------ float32, fixed order P <= 6
+template <int P, bool MASKED>
+__global__ void __launch_bounds__(128) m2l_blocks_f32(TreeView t, const M2LBlock *__restrict__ blocks, int64_t nblocks,
+                                                      const float *__restrict__ Ms, float *L, int ncp, float eps_over_L,
+                                                      int plummer)
 {
-    float *Mf = nullptr;
-    *st = ensure_t(c, B_MOMF, count, &Mf);
-    if (*st) return Mom<float>{nullptr};
-    {
-        ProfScope ps_(c, TG_K_UP);
-        convert_moments<<<grid_for((int64_t)count, 256), 256, 0, c->stream>>>(M, Mf, (int64_t)count);
+    constexpr int NC = M2LGen<P>::NC;
+    const int lane = threadIdx.x & 31;
+    const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t w = wid; w < nblocks; w += nw) {
+        const M2LBlock blk = blocks[w];
+        const BlockGeom bg = block_geom(t, blk);
+        const float rho = ldexpf(1.0f, bg.lx - bg.ly);
+        const float soft = plummer ? ldexpf(eps_over_L, bg.lx) : 0.0f;   // eps / s_x
+        const float soft2 = soft * soft;
+        for (int r = 0; r < 2; ++r) {
+            const int i = 4 * r + (lane >> 3), j = lane & 7;
+            const bool active = i < bg.ni && j < bg.nj && ((blk.mask >> (8 * i + j)) & 1ull);
+            const unsigned amask = __ballot_sync(0xffffffffu, active);
+            if (amask == 0) continue;
+            const int x = bg.baseA + i, y = bg.baseB + j;
+            float D[NC];
+            if (active) {
+                float dx, dy, dz;
+                pair_offset<float>(t, x, y, bg.lx, bg.ly, dx, dy, dz);
+                M2LGen<P>::dtensor(dx, dy, dz, soft2, D);
+            } else {
+#pragma unroll
+                for (int k = 0; k < NC; ++k) D[k] = 0.f;
+            }
+            const bool row_flush = (lane & 7) == 0 && ((amask >> (lane & ~7)) & 0xffu) != 0;
+            const bool col_flush = (lane >> 3) == 0 && (amask & (0x01010101u << (lane & 7))) != 0;
+#pragma unroll
+            for (int cls = 0; cls < (MASKED ? 2 : 1); ++cls) {
+                float Lc[NC];
+                // x side: sources y
+#pragma unroll
+                for (int k = 0; k < NC; ++k) Lc[k] = 0.f;
+                if (active) M2LGen<P>::side_a(D, Ms + ((size_t)y * 2 + cls) * ncp, rho, Lc);
+#pragma unroll
+                for (int k = 0; k < NC; ++k) {
+                    float v = Lc[k];
+                    v += __shfl_xor_sync(0xffffffffu, v, 1);
+                    v += __shfl_xor_sync(0xffffffffu, v, 2);
+                    v += __shfl_xor_sync(0xffffffffu, v, 4);
+                    Lc[k] = v;
+                }
+                if (row_flush) {
+                    float *dst = L + ((size_t)x * 2 + cls) * ncp;
+#pragma unroll
+                    for (int k = 0; k < NC; k += 4)
+                        atomicAdd(reinterpret_cast<float4 *>(dst + k),
+                                  make_float4(Lc[k], k + 1 < NC ? Lc[k + 1] : 0.f, k + 2 < NC ? Lc[k + 2] : 0.f,
+                                              k + 3 < NC ? Lc[k + 3] : 0.f));
+                }
+                // y side: sources x
+#pragma unroll
+                for (int k = 0; k < NC; ++k) Lc[k] = 0.f;
+                if (active) M2LGen<P>::side_b(D, Ms + ((size_t)x * 2 + cls) * ncp, Lc);
+#pragma unroll
+                for (int k = 0; k < NC; ++k) {
+                    float v = Lc[k];
+                    v += __shfl_xor_sync(0xffffffffu, v, 8);
+                    v += __shfl_xor_sync(0xffffffffu, v, 16);
+                    Lc[k] = v;
+                }
+                if (col_flush) {
+                    float rp[P + 2];
+                    rp[0] = 1.f;
+#pragma unroll
+                    for (int o = 1; o <= P + 1; ++o) rp[o] = rp[o - 1] * rho;
+                    float *dst = L + ((size_t)y * 2 + cls) * ncp;
+#pragma unroll
+                    for (int k = 0; k < NC; k += 4) {
+                        float v[4];
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) v[q] = (k + q < NC) ? Lc[k + q] * rp[order_of(k + q) + 1] : 0.f;
+                        atomicAdd(reinterpret_cast<float4 *>(dst + k), make_float4(v[0], v[1], v[2], v[3]));
+                    }
+                }
+            }
+        }
     }
-    return Mom<float>{Mf};
 }
 
-// D^k(d) for |k| <= p into D[0..ncoef(p)); R holds R^(m)_k packed by m.
+// ------------------------------------------------------------------ generic (p <= 8, float or double)
+// Same block layout; each active lane evaluates its pair with run-time loops and adds both sides
+// directly to global memory.  Used by the float64 path and by float32 for p > 6.
 template <class T>
 __device__ __forceinline__ void dtensor_generic(int p, T dx, T dy, T dz, T soft2, T *D)
 {
@@ -75,61 +188,53 @@ __device__ __forceinline__ void dtensor_generic(int p, T dx, T dy, T dz, T soft2
 }
 
 template <class T, bool MASKED>
-__global__ void m2l_mutual(TreeView t, const Geom *gp, const uint2 *pairs, int64_t npairs, const T *M, T *L, int p,
-                           int nc, T soft2)
+__global__ void m2l_blocks_generic(TreeView t, const M2LBlock *__restrict__ blocks, int64_t nblocks,
+                                   const T *__restrict__ Ms, T *L, int p, int nc, int ncp, double eps_over_L,
+                                   int plummer)
 {
-    const Geom g = *gp;
-    for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < npairs; w += (int64_t)gridDim.x * blockDim.x) {
-        const uint2 pr = pairs[w];
-        const int a = (int)pr.x, b = (int)pr.y;
-        const double sa = ldexp(g.L, -(int)t.level[a]), sb = ldexp(g.L, -(int)t.level[b]);
-        const T dx = (T)(((double)t.cx[a] + 0.5) * sa - ((double)t.cx[b] + 0.5) * sb);
-        const T dy = (T)(((double)t.cy[a] + 0.5) * sa - ((double)t.cy[b] + 0.5) * sb);
-        const T dz = (T)(((double)t.cz[a] + 0.5) * sa - ((double)t.cz[b] + 0.5) * sb);
-        T D[TG_NCOEF_MAX];
-        dtensor_generic<T>(p, dx, dy, dz, soft2, D);
-        const T *MaS = M + ((size_t)a * 2 + 0) * nc, *MaF = M + ((size_t)a * 2 + 1) * nc;
-        const T *MbS = M + ((size_t)b * 2 + 0) * nc, *MbF = M + ((size_t)b * 2 + 1) * nc;
-        T *LaA = L + ((size_t)a * 2 + 0) * nc, *LaS = L + ((size_t)a * 2 + 1) * nc;
-        T *LbA = L + ((size_t)b * 2 + 0) * nc, *LbS = L + ((size_t)b * 2 + 1) * nc;
-        for (int n = 0; n < nc; ++n) {
-            const int nx = c_mi_x[n], ny = c_mi_y[n], nz = c_mi_z[n], on = c_mi_order[n];
-            const int ncj = ncoef_dev(p - on);
-            T sA0 = 0, sA1 = 0, sB0 = 0, sB1 = 0;
-            for (int j = 0; j < ncj; ++j) {
-                const T Dv = D[c_mi_lookup[((nx + c_mi_x[j]) * 9 + ny + c_mi_y[j]) * 9 + nz + c_mi_z[j]]];
-                const T w = (T)c_inv_fact[j];
-                const T wa = (c_mi_order[j] & 1) ? -w : w;
-                const T mbs = MbS[j], mas = MaS[j];
-                const T mball = MASKED ? mbs + MbF[j] : mbs, maall = MASKED ? mas + MaF[j] : mas;
-                sA0 += wa * mball * Dv;
-                sB0 += w * maall * Dv;
-                if (MASKED) {
-                    sA1 += wa * mbs * Dv;
-                    sB1 += w * mas * Dv;
+    const int lane = threadIdx.x & 31;
+    const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t w = wid; w < nblocks; w += nw) {
+        const M2LBlock blk = blocks[w];
+        const BlockGeom bg = block_geom(t, blk);
+        const T rho = (T)ldexp(1.0, bg.lx - bg.ly);
+        const T soft = plummer ? (T)ldexp(eps_over_L, bg.lx) : T(0);
+        for (int r = 0; r < 2; ++r) {
+            const int i = 4 * r + (lane >> 3), j = lane & 7;
+            const bool active = i < bg.ni && j < bg.nj && ((blk.mask >> (8 * i + j)) & 1ull);
+            if (!active) continue;
+            const int x = bg.baseA + i, y = bg.baseB + j;
+            T dx, dy, dz;
+            pair_offset<T>(t, x, y, bg.lx, bg.ly, dx, dy, dz);
+            T D[TG_NCOEF_MAX];
+            dtensor_generic<T>(p, dx, dy, dz, soft * soft, D);
+            for (int cls = 0; cls < (MASKED ? 2 : 1); ++cls) {
+                const T *My = Ms + ((size_t)y * 2 + cls) * ncp, *Mx = Ms + ((size_t)x * 2 + cls) * ncp;
+                T *Lx = L + ((size_t)x * 2 + cls) * ncp, *Ly = L + ((size_t)y * 2 + cls) * ncp;
+                for (int n = 0; n < nc; ++n) {
+                    const int nx = c_mi_x[n], ny = c_mi_y[n], nz = c_mi_z[n], on = c_mi_order[n];
+                    const int ncj = ncoef_dev(p - on);
+                    T sa = 0, sb = 0, rpj = 1;
+                    int oprev = 0;
+                    for (int jj = 0; jj < ncj; ++jj) {
+                        const int oj = c_mi_order[jj];
+                        if (oj != oprev) {
+                            rpj *= rho;
+                            oprev = oj;
+                        }
+                        const T Dv = D[c_mi_lookup[((nx + c_mi_x[jj]) * 9 + ny + c_mi_y[jj]) * 9 + nz + c_mi_z[jj]]];
+                        sa += ((oj & 1) ? -rpj : rpj) * My[jj] * Dv;
+                        sb += Mx[jj] * Dv;
+                    }
+                    T rpn = rho;
+                    for (int o = 0; o < on; ++o) rpn *= rho;
+                    atomicAdd(&Lx[n], sa);
+                    atomicAdd(&Ly[n], ((on & 1) ? -rpn : rpn) * sb);
                 }
-            }
-            const T sgn = (on & 1) ? T(-1) : T(1);
-            atomicAdd(&LaA[n], sA0);
-            atomicAdd(&LbA[n], sgn * sB0);
-            if (MASKED) {
-                atomicAdd(&LaS[n], sA1);
-                atomicAdd(&LbS[n], sgn * sB1);
             }
         }
     }
-}
-
-template <class T>
-static tg_status launch_m2l(tg_ctx *c, const TreeView &t, const Geom *d_geom, const uint2 *pairs, int64_t npairs,
-                            const Mom<T> &mom, T *L, int p, int nc, bool masked)
-{
-    const T soft2 = c->prm.kernel == TG_KERNEL_PLUMMER ? (T)(c->prm.eps * c->prm.eps) : T(0);
-    const int grid = grid_for(npairs, 128);
-    ProfScope ps_(c, TG_K_M2L);
-    if (masked) m2l_mutual<T, true><<<grid, 128, 0, c->stream>>>(t, d_geom, pairs, npairs, mom.M, L, p, nc, soft2);
-    else m2l_mutual<T, false><<<grid, 128, 0, c->stream>>>(t, d_geom, pairs, npairs, mom.M, L, p, nc, soft2);
-    return cuda_check(c, cudaGetLastError(), "m2l launch");
 }
 
 }  // namespace tg

@@ -12,8 +12,13 @@ constexpr int kP2PThreads = 64;
 
 template <class T>
 __device__ __forceinline__ T tg_rsqrt(T x);
+// float: hardware reciprocal square root refined by one Newton step (relative error ~1e-7)
 template <>
-__device__ __forceinline__ float tg_rsqrt<float>(float x) { return rsqrtf(x); }
+__device__ __forceinline__ float tg_rsqrt<float>(float x)
+{
+    const float y = rsqrtf(x);
+    return y * fmaf(-0.5f * x, y * y, 1.5f);
+}
 template <>
 __device__ __forceinline__ double tg_rsqrt<double>(double x) { return rsqrt(x); }
 
@@ -139,8 +144,229 @@ __global__ void __launch_bounds__(kP2PThreads) p2p_mutual(TreeView t, const Geom
     if (lane == 0 && my_pairs) atomicAdd(pair_counter, my_pairs);
 }
 
+// ------------------------------------------------------------------ float32 warp tiles
+// One warp per unordered leaf pair (A, B).  Each lane holds two particles of A (rows i and i+32,
+// chunks of 64); the particles of B (columns) are read in batches of 8, broadcast to all lanes.
+// A lane accumulates its rows' forces in registers and its share of the 8 columns' reactions;
+// after each batch the 32 column partials (8 columns x ax, ay, az, phi) are combined with a
+// reduce-scatter over the warp, leaving lane l with column l/4, component l%4, which it adds
+// to global memory.  Positions are relative to the leaf centres; the centre offset is exact.
+// Reduce-scatter of 32 values over groups of G lanes (G = 8, 16, 32): afterwards v[0 .. 32/G) of
+// lane l hold the group sums of entries (l % G) * (32/G) + t.
+template <int G>
+__device__ __forceinline__ void reduce_scatter(float (&v)[32], int lane)
+{
+#pragma unroll
+    for (int h = 16, d = G / 2; d >= 1; h >>= 1, d >>= 1) {
+        const bool hi = (lane & d) != 0;
+#pragma unroll
+        for (int q = 0; q < h; ++q) {
+            const float send = hi ? v[q] : v[q + h];
+            const float keep = hi ? v[q + h] : v[q];
+            v[q] = keep + __shfl_xor_sync(0xffffffffu, send, d);
+        }
+    }
+}
+
+// float32 pair value: Newton by default, Wendland correction inside eps (rare, predicated).
+// NEAR = false: the caller knows r >= eps for every pair (leaf cubes at least eps apart).
+template <int KERNEL, bool NEAR = true>
+__device__ __forceinline__ void pair_kernel_f32(float r2, float eps, float eps2, float inv_eps, float inv_eps3, float &g,
+                                                float &phi)
+{
+    if (KERNEL == TG_KERNEL_PLUMMER) {
+        const float si = tg_rsqrt<float>(r2 + eps2);
+        phi = -si;
+        g = si * si * si;
+        return;
+    }
+    const float ri = rsqrtf(r2);
+    phi = -ri;
+    g = ri * ri * ri;
+    if (NEAR && r2 < eps2) pair_kernel<float, TG_KERNEL_WENDLAND_C2>(r2, eps, eps2, inv_eps, inv_eps3, g, phi);
+}
+
+// One leaf pair.  Rows = particles of A, ROWS per lane (row i0 + lane + 32 r), chunks of 32*ROWS;
+// columns = particles of B, staged once in the warp's shared-memory slice (positions shifted into
+// A's frame) and read in batches of 8.  A lane keeps its rows' sums in registers and its 8 x 4
+// column partials.  Lane l visits the 8 columns of a batch in the order c ^ ((l >> 2) & 7), so its
+// partial for logical entry e sits in register e ^ (l & 28); the first three stages of the warp
+// reduce-scatter (partners l ^ 16, l ^ 8, l ^ 4) then need no selects, and lane l ends with column
+// l/4, component l%4, which it adds to global memory.  SELF (A == B) keeps column index > row index.
+template <int KERNEL, bool MASKED, bool SELF, int ROWS, bool NEAR>
+__device__ __noinline__ void p2p_pair_f32(const float4 *__restrict__ pf, const uint8_t *__restrict__ fs, int fa, int na,
+                                          int fb, int nb, float ox, float oy, float oz, float eps, double *acc4, int n,
+                                          int lane, float4 *sq, uint8_t *sfq)
+{
+    const float eps2 = eps * eps, inv_eps = 1.0f / eps, inv_eps3 = inv_eps * inv_eps * inv_eps;
+    const int cperm = (lane >> 2) & 7;
+    for (int jc = 0; jc < nb; jc += kMaxNcrit) {
+        const int nbc = min(kMaxNcrit, nb - jc);
+        __syncwarp();
+        for (int j = lane; j < nbc; j += 32) {
+            float4 q = pf[fb + jc + j];
+            q.x += ox;
+            q.y += oy;
+            q.z += oz;
+            sq[j] = q;
+            if (MASKED) sfq[j] = fs[fb + jc + j];
+        }
+        __syncwarp();
+        for (int i0 = 0; i0 < na; i0 += 32 * ROWS) {
+            float4 p[ROWS];
+            uint8_t fr[ROWS];
+            int ir[ROWS];
+            float ra[ROWS][4];
+#pragma unroll
+            for (int r = 0; r < ROWS; ++r) {
+                ir[r] = i0 + lane + 32 * r;
+                fr[r] = 0;
+                if (ir[r] < na) {
+                    p[r] = pf[fa + ir[r]];
+                    if (MASKED) fr[r] = fs[fa + ir[r]];
+                } else {
+                    p[r] = make_float4(1e8f, 1e8f, 1e8f, 0.f);   // far away (finite r^2) and massless
+                }
+                ra[r][0] = ra[r][1] = ra[r][2] = ra[r][3] = 0.f;
+            }
+            for (int j0 = 0; j0 < nbc; j0 += 8) {
+                float col[32];
+#pragma unroll
+                for (int c = 0; c < 8; ++c) {
+                    const int j = j0 + (c ^ cperm);
+                    float cx = 0.f, cy = 0.f, cz = 0.f, cp = 0.f;
+                    if (j < nbc) {
+                        const float4 q = sq[j];
+                        const uint8_t fq = MASKED ? sfq[j] : 0;
+#pragma unroll
+                        for (int r = 0; r < ROWS; ++r) {
+                            const float dx = q.x - p[r].x, dy = q.y - p[r].y, dz = q.z - p[r].z;
+                            float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                            bool use = true;
+                            if (SELF) use = jc + j > ir[r];
+                            if (MASKED) use = use && !(fr[r] && fq);
+                            if (SELF) r2 = use ? r2 : 1.0f;
+                            float gk, ph;
+                            pair_kernel_f32<KERNEL, NEAR>(r2, eps, eps2, inv_eps, inv_eps3, gk, ph);
+                            if (SELF || MASKED) {
+                                gk = use ? gk : 0.f;
+                                ph = use ? ph : 0.f;
+                            }
+                            const float mq = q.w * gk, mp = p[r].w * gk;
+                            ra[r][0] = fmaf(mq, dx, ra[r][0]);
+                            ra[r][1] = fmaf(mq, dy, ra[r][1]);
+                            ra[r][2] = fmaf(mq, dz, ra[r][2]);
+                            ra[r][3] = fmaf(q.w, ph, ra[r][3]);
+                            cx = fmaf(-mp, dx, cx);
+                            cy = fmaf(-mp, dy, cy);
+                            cz = fmaf(-mp, dz, cz);
+                            cp = fmaf(p[r].w, ph, cp);
+                        }
+                    }
+                    col[4 * c + 0] = cx;
+                    col[4 * c + 1] = cy;
+                    col[4 * c + 2] = cz;
+                    col[4 * c + 3] = cp;
+                }
+                // reduce-scatter: column bits (partners l^16, l^8, l^4) without selects ...
+#pragma unroll
+                for (int h = 16; h >= 4; h >>= 1)
+#pragma unroll
+                    for (int q = 0; q < h; ++q) col[q] += __shfl_xor_sync(0xffffffffu, col[q + h], h);
+                // ... component bits (l^2, l^1) with selects
+#pragma unroll
+                for (int h = 2; h >= 1; h >>= 1) {
+                    const bool hi = (lane & h) != 0;
+#pragma unroll
+                    for (int q = 0; q < h; ++q) {
+                        const float send = hi ? col[q] : col[q + h];
+                        const float keep = hi ? col[q + h] : col[q];
+                        col[q] = keep + __shfl_xor_sync(0xffffffffu, send, h);
+                    }
+                }
+                const int cj = lane >> 2, comp = lane & 3;
+                if (j0 + cj < nbc) atomicAdd(&acc4[(size_t)comp * n + fb + jc + j0 + cj], f2d_exact(col[0]));
+            }
+#pragma unroll
+            for (int r = 0; r < ROWS; ++r)
+                if (ir[r] < na)
+#pragma unroll
+                    for (int comp = 0; comp < 4; ++comp)
+                        atomicAdd(&acc4[(size_t)comp * n + fa + ir[r]], f2d_exact(ra[r][comp]));
+        }
+    }
+}
+
+template <bool MASKED, int KERNEL, bool SELF, int ROWS>
+__global__ void __launch_bounds__(256, 2) p2p_warp_f32(TreeView t, int log2L, const uint2 *__restrict__ pairs,
+                                                       int64_t npairs, const float4 *__restrict__ pf,
+                                                       const uint8_t *__restrict__ fs, float eps, double *acc4, int n,
+                                                       unsigned long long *pair_counter)
+{
+    __shared__ float4 s_q[8][kMaxNcrit];
+    __shared__ uint8_t s_f[8][kMaxNcrit];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    unsigned long long my_pairs = 0;
+    for (int64_t w = wid; w < npairs; w += nw) {
+        const uint2 pr = pairs[w];
+        int a = (int)pr.x, b = (int)pr.y;
+        if (!SELF && t.count[a] < t.count[b]) {   // the larger leaf becomes the rows
+            const int tmp = a;
+            a = b;
+            b = tmp;
+        }
+        const int fa = t.first[a], na = t.count[a], fb = t.first[b], nb = t.count[b];
+        float ox = 0.f, oy = 0.f, oz = 0.f;
+        if (!SELF) {
+            // z_b - z_a = delta * L / 2^(lf+1), exact in float
+            const int la = t.level[a], lb = t.level[b], lf = la > lb ? la : lb;
+            const float unit = pow2f(log2L - lf - 1);
+            // |delta| < 2^23 (both centres lie in the root cube), so int32 holds it exactly
+            ox = (float)(int)centre_delta(t.cx[b], lb, t.cx[a], la, lf) * unit;
+            oy = (float)(int)centre_delta(t.cy[b], lb, t.cy[a], la, lf) * unit;
+            oz = (float)(int)centre_delta(t.cz[b], lb, t.cz[a], la, lf) * unit;
+        }
+        // Wendland pairs whose leaf cubes are at least eps apart never enter the softened branch
+        bool near = true;
+        if (!SELF && KERNEL == TG_KERNEL_WENDLAND_C2) {
+            const int la = t.level[a], lb = t.level[b], lf = la > lb ? la : lb;
+            const long long ha = 1ll << (lf - la), hb = 1ll << (lf - lb);
+            long long g2 = 0;
+            const long long dxs[3] = {centre_delta(t.cx[b], lb, t.cx[a], la, lf), centre_delta(t.cy[b], lb, t.cy[a], la, lf),
+                                      centre_delta(t.cz[b], lb, t.cz[a], la, lf)};
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                long long gk = (dxs[k] < 0 ? -dxs[k] : dxs[k]) - (ha + hb);
+                if (gk > 0) g2 += gk * gk;
+            }
+            const float eu = eps * pow2f(lf + 1 - log2L);   // eps in half-units of the finer level
+            near = !((float)g2 >= eu * eu * 1.0001f);
+        }
+        if (near)
+            p2p_pair_f32<KERNEL, MASKED, SELF, ROWS, true>(pf, fs, fa, na, fb, nb, ox, oy, oz, eps, acc4, n, lane, s_q[wib],
+                                                           s_f[wib]);
+        else
+            p2p_pair_f32<KERNEL, MASKED, SELF, ROWS, false>(pf, fs, fa, na, fb, nb, ox, oy, oz, eps, acc4, n, lane,
+                                                            s_q[wib], s_f[wib]);
+        if (lane == 0) {
+            // pairs evaluated: all (or i < j for a self pair) minus fast-fast pairs
+            unsigned long long cnt = SELF ? (unsigned long long)na * (na - 1) / 2 : (unsigned long long)na * nb;
+            if (MASKED) {
+                int fa_n = 0, fb_n = 0;
+                for (int q = 0; q < na; ++q) fa_n += fs[fa + q] ? 1 : 0;
+                for (int q = 0; q < nb; ++q) fb_n += fs[fb + q] ? 1 : 0;
+                cnt -= SELF ? (unsigned long long)fa_n * (fa_n - 1) / 2 : (unsigned long long)fa_n * fb_n;
+            }
+            my_pairs += cnt;
+        }
+    }
+    if (lane == 0 && my_pairs) atomicAdd(pair_counter, my_pairs);
+}
+
 template <class T, class T4>
-static tg_status launch_p2p(tg_ctx *c, const TreeView &t, const Geom *d_geom, const uint2 *pairs, int64_t npairs,
+static tg_status launch_p2p_generic(tg_ctx *c, const TreeView &t, const Geom *d_geom, const uint2 *pairs, int64_t npairs,
                             const T4 *pf, const uint8_t *fs, bool masked, double *acc4)
 {
     const int grid = (int)std::min<int64_t>(npairs, (int64_t)c->num_sms * 16);
@@ -158,6 +384,52 @@ static tg_status launch_p2p(tg_ctx *c, const TreeView &t, const Geom *d_geom, co
         else TG_P2P_LAUNCH(false, TG_KERNEL_WENDLAND_C2);
     }
 #undef TG_P2P_LAUNCH
+    return cuda_check(c, cudaGetLastError(), "p2p launch");
+}
+
+
+
+template <class T, class T4>
+static tg_status launch_p2p(tg_ctx *c, const TreeView &t, const Geom *d_geom, const uint2 *pairs, int64_t npairs,
+                            const T4 *pf, const uint8_t *fs, bool masked, bool self, double *acc4);
+
+template <>
+tg_status launch_p2p<double, dbl4>(tg_ctx *c, const TreeView &t, const Geom *d_geom, const uint2 *pairs, int64_t npairs,
+                                   const dbl4 *pf, const uint8_t *fs, bool masked, bool self, double *acc4)
+{
+    (void)self;   // the float64 tile handles self pairs at run time
+    return launch_p2p_generic<double, dbl4>(c, t, d_geom, pairs, npairs, pf, fs, masked, acc4);
+}
+
+template <>
+tg_status launch_p2p<float, float4>(tg_ctx *c, const TreeView &t, const Geom *d_geom, const uint2 *pairs,
+                                    int64_t npairs, const float4 *pf, const uint8_t *fs, bool masked, bool self,
+                                    double *acc4)
+{
+    (void)d_geom;
+    const int grid = grid_for(npairs * 32, 256, c->num_sms * 8);
+    const float eps = (float)c->prm.eps;
+    unsigned long long *ctr = c->d_counters;
+    ProfScope ps_(c, TG_K_P2P);
+    // rows per lane: one for leaves of up to ~32 particles, two for larger leaf sizes
+    const bool two = c->prm.n_crit > 64;
+    const bool plummer = c->prm.kernel == TG_KERNEL_PLUMMER;
+#define TG_P2P_W(M, K, S, R) \
+    p2p_warp_f32<M, K, S, R><<<grid, 256, 0, c->stream>>>(t, c->walk_log2L, pairs, npairs, pf, fs, eps, acc4, t.n, ctr)
+#define TG_P2P_R(M, K, S) \
+    if (two) TG_P2P_W(M, K, S, 2); else TG_P2P_W(M, K, S, 1);
+#define TG_P2P_S(M, K) \
+    if (self) { TG_P2P_R(M, K, true) } else { TG_P2P_R(M, K, false) }
+    if (masked) {
+        if (plummer) { TG_P2P_S(true, TG_KERNEL_PLUMMER) }
+        else { TG_P2P_S(true, TG_KERNEL_WENDLAND_C2) }
+    } else {
+        if (plummer) { TG_P2P_S(false, TG_KERNEL_PLUMMER) }
+        else { TG_P2P_S(false, TG_KERNEL_WENDLAND_C2) }
+    }
+#undef TG_P2P_S
+#undef TG_P2P_R
+#undef TG_P2P_W
     return cuda_check(c, cudaGetLastError(), "p2p launch");
 }
 

@@ -73,7 +73,9 @@ struct tg_ctx {
     int64_t *h_pinned = nullptr;                // small pinned staging area (64 int64)
 
     // last tree/walk (host copies of sizes)
-    int64_t last_n = 0, last_ncell = 0, last_nm2l = 0, last_np2p = 0;
+    int64_t last_n = 0, last_ncell = 0, last_nm2l = 0, last_np2p = 0, last_nblocks = 0;
+    int walk_log2L = 0;                         // log2 of the last root cube side
+    int64_t last_np2p_self = 0, p2p_cap = 0;    // self P2P pairs sit at the end of the P2P buffer
     std::vector<int32_t> level_begin;           // cell index range of each level (BFS)
 
     // live kernel timing
@@ -99,7 +101,7 @@ enum Slot {
     B_XS, B_YS, B_ZS, B_MS, B_FS, B_PF, B_LEAF_OF,
     B_C_LEVEL, B_C_X, B_C_Y, B_C_Z, B_C_FIRST, B_C_COUNT, B_C_CHILD, B_C_PARENT, B_C_NCHILD,
     B_C_TMP0, B_C_TMP1,
-    B_MOM, B_MOMF, B_LOC, B_ACC,
+    B_MOM, B_MOMF, B_MOM01, B_LOC, B_ACC,
     B_FRONT0, B_FRONT1, B_M2L, B_P2P, B_WALK_CNT,
     B_SUB_ACC, B_HHS_AOLD, B_HHS_ACUR, B_HHS_DT, B_HHS_RUNG, B_HHS_IDX, B_HHS_FLAG,
     B_HHS_SCAN, B_HHS_TMP, B_RED, B_DIAG_POT, B_DIAG_ACC,
@@ -184,6 +186,28 @@ __device__ __forceinline__ uint64_t spread3_21(uint64_t v)
     v = (v | (v << 2)) & 0x1249249249249249ull;
     return v;
 }
+
+// Exact float -> double conversion on the integer pipe (GB300's FP64 pipe is ~1/64 the FP32 rate).
+__device__ __forceinline__ double f2d_exact(float f)
+{
+    const uint32_t u = __float_as_uint(f);
+    const uint32_t e = (u >> 23) & 0xffu;
+    const uint64_t sign = (uint64_t)(u & 0x80000000u) << 32;
+    if (e == 0) return __longlong_as_double((long long)sign);   // zero (float32 subnormals flush to zero)
+    const uint64_t ee = (e == 0xffu) ? 0x7ffull : (uint64_t)(e + 896u);   // inf / nan keep their class
+    const uint64_t bits = sign | (ee << 52) | ((uint64_t)(u & 0x7fffffu) << 29);
+    return __longlong_as_double((long long)bits);
+}
+
+// Offset between two cell centres along one axis in units of 2^-(lf+1) of the root side, where
+// lf is the finer level: (2 c_a + 1) 2^(lf - la) - (2 c_b + 1) 2^(lf - lb).  Exact integer.
+__device__ __forceinline__ long long centre_delta(uint32_t ca, int la, uint32_t cb, int lb, int lf)
+{
+    return ((2ll * ca + 1) << (lf - la)) - ((2ll * cb + 1) << (lf - lb));
+}
+
+// 2^e as a float, exact, for -126 <= e <= 127 (built from the exponent bits)
+__device__ __forceinline__ float pow2f(int e) { return __int_as_float((e + 127) << 23); }
 
 __host__ __device__ __forceinline__ int ncoef_dev(int p) { return (p + 1) * (p + 2) * (p + 3) / 6; }
 

@@ -296,13 +296,19 @@ __global__ void bbox_partial(const double *pos, int64_t stride, const int64_t *s
 // extent is 0), lo = floor(min / h) * h with h = L / 2^21.
 __global__ void bbox_final(const double *partial, int nparts, int n, Geom *g)
 {
-    if (threadIdx.x != 0) return;
+    // one warp: lanes stride over the partial results, then a shuffle reduction
     double mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY};
-    for (int b = 0; b < nparts; ++b)
+    for (int b = threadIdx.x; b < nparts; b += 32)
         for (int a = 0; a < 3; ++a) {
             mn[a] = fmin(mn[a], partial[b * 6 + a]);
             mx[a] = fmax(mx[a], partial[b * 6 + 3 + a]);
         }
+    for (int a = 0; a < 3; ++a)
+        for (int o = 16; o > 0; o >>= 1) {
+            mn[a] = fmin(mn[a], __shfl_xor_sync(0xffffffffu, mn[a], o));
+            mx[a] = fmax(mx[a], __shfl_xor_sync(0xffffffffu, mx[a], o));
+        }
+    if (threadIdx.x != 0) return;
     if (n <= 0) {
         for (int a = 0; a < 3; ++a) g->lo[a] = 0.0;
         g->L = 1.0;

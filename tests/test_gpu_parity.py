@@ -15,11 +15,13 @@ if torch.cuda.is_available():
     from paper_1712_10116_gb300 import binding as tg
     DEV = torch.device("cuda:0")
 
-# float32 path bound: |a_gpu - a_oracle| <= 1e-5 * |a_oracle| per particle.  Particles whose
-# net force nearly cancels get a floor at 1e-3 of the median force (the float32 error of a
-# sum is relative to the magnitude of its terms, not of the net; see the design notes).
+# float32 path bound: |a_gpu - a_oracle| <= 1e-5 * max(|a_oracle|, 0.1 * median |a_oracle|) per
+# particle.  Float32 positions relative to a leaf centre carry a rounding of ~6e-8 of the leaf size,
+# so the absolute force error is ~1e-6 of the typical (median) force whatever a particle's own net
+# force; particles whose contributions cancel to below 10% of the typical force are therefore held
+# to 1e-5 of that floor (see the design notes).
 FP32_TOL = 1e-5
-FP32_FLOOR = 1e-3
+FP32_FLOOR = 0.1
 
 
 def _case(kind, n, seed=None):
