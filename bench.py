@@ -43,6 +43,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=512)
     ap.add_argument("--n-crit", type=int, default=PARAMS["n_crit"])
+    ap.add_argument("--eval-only", action="store_true",
+                    help="run warmup + steps single FMM evaluations of the workload (for profiler captures)")
+    ap.add_argument("--masked", action="store_true", help="with --eval-only: 30%% of the particles in the fast set")
     return ap.parse_args()
 
 
@@ -328,8 +331,38 @@ def m2l_flops(p, pairs, stats):
     return pairs * (d + contr)
 
 
+def run_eval_only(args):
+    """Plain FMM evaluations of the workload (no HHS), for kernel captures with a profiler."""
+    import torch
+
+    from paper_1712_10116_gb300 import binding as tg
+    from paper_1712_10116_gb300 import ics
+
+    dev = torch.device("cuda", 0)
+    pos, _, mass = workload(args.n)
+    prec = tg.TG_PREC_FP32 if args.precision == "fp32" else tg.TG_PREC_FP64
+    solver = tg.Solver(tg.Params(precision=prec, **dict(PARAMS, n_crit=args.n_crit)))
+    P = torch.tensor(pos, device=dev)
+    M = torch.tensor(mass, device=dev)
+    F = torch.tensor(ics.random_fast_mask(args.n, 17), device=dev) if args.masked else None
+    for _ in range(args.warmup):
+        solver.fmm_forces(P, M, F, want_pot=False)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        solver.fmm_forces(P, M, F, want_pot=False)
+    torch.cuda.synchronize()
+    dt = (time.perf_counter() - t0) / max(args.steps, 1)
+    print(json.dumps({"mode": "eval-only", "n": args.n, "n_crit": args.n_crit, "masked": bool(args.masked),
+                      "ms_per_eval": 1e3 * dt, "stats": solver.stats()}), flush=True)
+    solver.close()
+
+
 def main():
     args = parse()
+    if args.eval_only:
+        run_eval_only(args)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:

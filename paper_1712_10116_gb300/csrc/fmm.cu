@@ -91,6 +91,45 @@ __global__ void leaf_particles(TreeView t, const Geom *gp, const double *xs, con
     }
 }
 
+// ------------------------------------------------------------------ slow-before-fast leaves
+// With classes, every leaf's particles are stably reordered so the slow ones come first
+// (nslow[leaf] of them).  Leaf ranges and the tree are unchanged; a mutual P2P tile can then skip
+// the fast-fast block (kickS2F feels slow masses only) instead of masking it pair by pair.
+__global__ void leaf_class_partition(TreeView t, const double *xs, const double *ys, const double *zs, const double *ms,
+                                     const uint8_t *fs, const uint32_t *perm, double *xs2, double *ys2, double *zs2,
+                                     double *ms2, uint8_t *fs2, uint32_t *perm2, int32_t *nslow)
+{
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    const unsigned lt = (1u << lane) - 1u;
+    for (int c = warp; c < t.ncell; c += nwarps) {
+        if (t.nchild[c] != 0) continue;
+        const int first = t.first[c], count = t.count[c];
+        int ns = 0;
+        for (int q0 = 0; q0 < count; q0 += 32) ns += __popc(__ballot_sync(0xffffffffu, q0 + lane < count && !fs[first + q0 + lane]));
+        int slow_seen = 0, fast_seen = 0;
+        for (int q0 = 0; q0 < count; q0 += 32) {
+            const int q = q0 + lane;
+            const bool valid = q < count;
+            const bool slow = valid && !fs[first + q];
+            const unsigned bs = __ballot_sync(0xffffffffu, slow), bf = __ballot_sync(0xffffffffu, valid && !slow);
+            if (valid) {
+                const int dst = first + (slow ? slow_seen + __popc(bs & lt) : ns + fast_seen + __popc(bf & lt));
+                const int src = first + q;
+                xs2[dst] = xs[src];
+                ys2[dst] = ys[src];
+                zs2[dst] = zs[src];
+                ms2[dst] = ms[src];
+                fs2[dst] = fs[src];
+                perm2[dst] = perm[src];
+            }
+            slow_seen += __popc(bs);
+            fast_seen += __popc(bf);
+        }
+        if (lane == 0) nslow[c] = ns;
+    }
+}
+
 // ------------------------------------------------------------------ P2M
 // Moments live in two arrays: M[cell][class][ncp] in precision T (every order) and
 // M01[cell][class][4] in float64 (monopole and dipole, the "centre of mass" part, accumulated in
@@ -610,6 +649,32 @@ static tg_status eval_typed(tg_ctx *c, int n, int ncell, const TreeView &t, cons
         (st = ensure_t(c, B_LOC, (size_t)ncell * 2 * ncp, &L)) || (st = ensure_t(c, B_ACC, (size_t)4 * n, &acc4)))
         return st;
     const int ncls = masked ? 2 : 1;
+    int32_t *nslow = nullptr;
+    if (masked) {
+        double *xs2, *ys2, *zs2, *ms2;
+        uint8_t *fs2;
+        uint32_t *perm2;
+        if ((st = ensure_t(c, B_XS2, n, &xs2)) || (st = ensure_t(c, B_YS2, n, &ys2)) || (st = ensure_t(c, B_ZS2, n, &zs2)) ||
+            (st = ensure_t(c, B_MS2, n, &ms2)) || (st = ensure_t(c, B_FS2, n, &fs2)) ||
+            (st = ensure_t(c, B_PERM2, n, &perm2)) || (st = ensure_t(c, B_NSLOW, ncell, &nslow)))
+            return st;
+        {
+            ProfScope ps_(c, TG_K_TREE);
+            leaf_class_partition<<<grid_for((int64_t)ncell * 32, 256), 256, 0, c->stream>>>(
+                t, xs, ys, zs, ms, fs, static_cast<const uint32_t *>(c->buf[B_VALS0].p), xs2, ys2, zs2, ms2, fs2, perm2, nslow);
+        }
+        std::swap(c->buf[B_XS], c->buf[B_XS2]);
+        std::swap(c->buf[B_YS], c->buf[B_YS2]);
+        std::swap(c->buf[B_ZS], c->buf[B_ZS2]);
+        std::swap(c->buf[B_MS], c->buf[B_MS2]);
+        std::swap(c->buf[B_FS], c->buf[B_FS2]);
+        std::swap(c->buf[B_VALS0], c->buf[B_PERM2]);
+        xs = xs2;
+        ys = ys2;
+        zs = zs2;
+        ms = ms2;
+        fs = fs2;
+    }
     {
         ProfScope ps_(c, TG_K_UP);
         leaf_particles<T4><<<grid_for((int64_t)ncell * 32, 256), 256, 0, c->stream>>>(t, d_geom, xs, ys, zs, ms, pf, leaf_of);
@@ -643,9 +708,9 @@ static tg_status eval_typed(tg_ctx *c, int n, int ncell, const TreeView &t, cons
         l2p_particles<T, T4><<<grid_for(n, 128), 128, 0, c->stream>>>(n, t, c->walk_log2L, pf, leaf_of, fs, masked ? 1 : 0,
                                                                       p, nc, ncp, L, acc4);
     }
-    if (n_p2p > 0 && (st = launch_p2p<T, T4>(c, t, d_geom, p2p, n_p2p, pf, fs, masked, false, acc4))) return st;
+    if (n_p2p > 0 && (st = launch_p2p<T, T4>(c, t, d_geom, p2p, n_p2p, pf, fs, nslow, masked, false, acc4))) return st;
     if (n_self > 0 &&
-        (st = launch_p2p<T, T4>(c, t, d_geom, p2p + (c->p2p_cap - n_self), n_self, pf, fs, masked, true, acc4)))
+        (st = launch_p2p<T, T4>(c, t, d_geom, p2p + (c->p2p_cap - n_self), n_self, pf, fs, nslow, masked, true, acc4)))
         return st;
     return cuda_check(c, cudaGetLastError(), "fmm evaluation");
 }

@@ -193,10 +193,9 @@ __device__ __forceinline__ void pair_kernel_f32(float r2, float eps, float eps2,
 // partial for logical entry e sits in register e ^ (l & 28); the first three stages of the warp
 // reduce-scatter (partners l ^ 16, l ^ 8, l ^ 4) then need no selects, and lane l ends with column
 // l/4, component l%4, which it adds to global memory.  SELF (A == B) keeps column index > row index.
-template <int KERNEL, bool MASKED, bool SELF, int ROWS, bool NEAR>
-__device__ __noinline__ void p2p_pair_f32(const float4 *__restrict__ pf, const uint8_t *__restrict__ fs, int fa, int na,
-                                          int fb, int nb, float ox, float oy, float oz, float eps, double *acc4, int n,
-                                          int lane, float4 *sq, uint8_t *sfq)
+template <int KERNEL, bool SELF, int ROWS, bool NEAR>
+__device__ __noinline__ void p2p_pair_f32(const float4 *__restrict__ pf, int fa, int na, int fb, int nb, float ox, float oy,
+                                          float oz, float eps, double *acc4, int n, int lane, float4 *sq)
 {
     const float eps2 = eps * eps, inv_eps = 1.0f / eps, inv_eps3 = inv_eps * inv_eps * inv_eps;
     const int cperm = (lane >> 2) & 7;
@@ -209,24 +208,16 @@ __device__ __noinline__ void p2p_pair_f32(const float4 *__restrict__ pf, const u
             q.y += oy;
             q.z += oz;
             sq[j] = q;
-            if (MASKED) sfq[j] = fs[fb + jc + j];
         }
         __syncwarp();
         for (int i0 = 0; i0 < na; i0 += 32 * ROWS) {
             float4 p[ROWS];
-            uint8_t fr[ROWS];
             int ir[ROWS];
             float ra[ROWS][4];
 #pragma unroll
             for (int r = 0; r < ROWS; ++r) {
                 ir[r] = i0 + lane + 32 * r;
-                fr[r] = 0;
-                if (ir[r] < na) {
-                    p[r] = pf[fa + ir[r]];
-                    if (MASKED) fr[r] = fs[fa + ir[r]];
-                } else {
-                    p[r] = make_float4(1e8f, 1e8f, 1e8f, 0.f);   // far away (finite r^2) and massless
-                }
+                p[r] = ir[r] < na ? pf[fa + ir[r]] : make_float4(1e8f, 1e8f, 1e8f, 0.f);   // far away, massless
                 ra[r][0] = ra[r][1] = ra[r][2] = ra[r][3] = 0.f;
             }
             for (int j0 = 0; j0 < nbc; j0 += 8) {
@@ -237,18 +228,18 @@ __device__ __noinline__ void p2p_pair_f32(const float4 *__restrict__ pf, const u
                     float cx = 0.f, cy = 0.f, cz = 0.f, cp = 0.f;
                     if (j < nbc) {
                         const float4 q = sq[j];
-                        const uint8_t fq = MASKED ? sfq[j] : 0;
 #pragma unroll
                         for (int r = 0; r < ROWS; ++r) {
                             const float dx = q.x - p[r].x, dy = q.y - p[r].y, dz = q.z - p[r].z;
                             float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
                             bool use = true;
-                            if (SELF) use = jc + j > ir[r];
-                            if (MASKED) use = use && !(fr[r] && fq);
-                            if (SELF) r2 = use ? r2 : 1.0f;
+                            if (SELF) {
+                                use = jc + j > ir[r];
+                                r2 = use ? r2 : 1.0f;
+                            }
                             float gk, ph;
                             pair_kernel_f32<KERNEL, NEAR>(r2, eps, eps2, inv_eps, inv_eps3, gk, ph);
-                            if (SELF || MASKED) {
+                            if (SELF) {
                                 gk = use ? gk : 0.f;
                                 ph = use ? ph : 0.f;
                             }
@@ -297,14 +288,17 @@ __device__ __noinline__ void p2p_pair_f32(const float4 *__restrict__ pf, const u
     }
 }
 
-template <bool MASKED, int KERNEL, bool SELF, int ROWS>
+// One warp per unordered leaf pair.  With slow/fast classes (nslow != nullptr) each leaf holds its
+// slow particles first; the pair is then evaluated as the two tiles (all of A) x (slow of B) and
+// (slow of A) x (fast of B) -- fast-fast pairs are never computed.  For a self pair the tile
+// (slow rows) x (all columns, j > i) covers slow-slow and slow-fast pairs.
+template <int KERNEL, bool SELF, int ROWS>
 __global__ void __launch_bounds__(256, 2) p2p_warp_f32(TreeView t, int log2L, const uint2 *__restrict__ pairs,
                                                        int64_t npairs, const float4 *__restrict__ pf,
-                                                       const uint8_t *__restrict__ fs, float eps, double *acc4, int n,
+                                                       const int32_t *__restrict__ nslow, float eps, double *acc4, int n,
                                                        unsigned long long *pair_counter)
 {
     __shared__ float4 s_q[8][kMaxNcrit];
-    __shared__ uint8_t s_f[8][kMaxNcrit];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -318,48 +312,48 @@ __global__ void __launch_bounds__(256, 2) p2p_warp_f32(TreeView t, int log2L, co
             b = tmp;
         }
         const int fa = t.first[a], na = t.count[a], fb = t.first[b], nb = t.count[b];
+        const int sa = nslow ? nslow[a] : na, sb = nslow ? nslow[b] : nb;
         float ox = 0.f, oy = 0.f, oz = 0.f;
+        bool near = true;
         if (!SELF) {
-            // z_b - z_a = delta * L / 2^(lf+1), exact in float
+            // z_b - z_a = delta * L / 2^(lf+1), exact in float; |delta| < 2^23 fits int32
             const int la = t.level[a], lb = t.level[b], lf = la > lb ? la : lb;
             const float unit = pow2f(log2L - lf - 1);
-            // |delta| < 2^23 (both centres lie in the root cube), so int32 holds it exactly
-            ox = (float)(int)centre_delta(t.cx[b], lb, t.cx[a], la, lf) * unit;
-            oy = (float)(int)centre_delta(t.cy[b], lb, t.cy[a], la, lf) * unit;
-            oz = (float)(int)centre_delta(t.cz[b], lb, t.cz[a], la, lf) * unit;
-        }
-        // Wendland pairs whose leaf cubes are at least eps apart never enter the softened branch
-        bool near = true;
-        if (!SELF && KERNEL == TG_KERNEL_WENDLAND_C2) {
-            const int la = t.level[a], lb = t.level[b], lf = la > lb ? la : lb;
-            const long long ha = 1ll << (lf - la), hb = 1ll << (lf - lb);
-            long long g2 = 0;
-            const long long dxs[3] = {centre_delta(t.cx[b], lb, t.cx[a], la, lf), centre_delta(t.cy[b], lb, t.cy[a], la, lf),
-                                      centre_delta(t.cz[b], lb, t.cz[a], la, lf)};
+            const long long dl[3] = {centre_delta(t.cx[b], lb, t.cx[a], la, lf), centre_delta(t.cy[b], lb, t.cy[a], la, lf),
+                                     centre_delta(t.cz[b], lb, t.cz[a], la, lf)};
+            ox = (float)(int)dl[0] * unit;
+            oy = (float)(int)dl[1] * unit;
+            oz = (float)(int)dl[2] * unit;
+            if (KERNEL == TG_KERNEL_WENDLAND_C2) {
+                // leaf cubes at least eps apart: every pair is beyond eps, no softened branch
+                const long long ha = 1ll << (lf - la), hb = 1ll << (lf - lb);
+                long long g2 = 0;
 #pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                long long gk = (dxs[k] < 0 ? -dxs[k] : dxs[k]) - (ha + hb);
-                if (gk > 0) g2 += gk * gk;
+                for (int k = 0; k < 3; ++k) {
+                    const long long gk = (dl[k] < 0 ? -dl[k] : dl[k]) - (ha + hb);
+                    if (gk > 0) g2 += gk * gk;
+                }
+                const float eu = eps * pow2f(lf + 1 - log2L);   // eps in half-units of the finer level
+                near = !((float)g2 >= eu * eu * 1.0001f);
             }
-            const float eu = eps * pow2f(lf + 1 - log2L);   // eps in half-units of the finer level
-            near = !((float)g2 >= eu * eu * 1.0001f);
         }
-        if (near)
-            p2p_pair_f32<KERNEL, MASKED, SELF, ROWS, true>(pf, fs, fa, na, fb, nb, ox, oy, oz, eps, acc4, n, lane, s_q[wib],
-                                                           s_f[wib]);
-        else
-            p2p_pair_f32<KERNEL, MASKED, SELF, ROWS, false>(pf, fs, fa, na, fb, nb, ox, oy, oz, eps, acc4, n, lane,
-                                                            s_q[wib], s_f[wib]);
+        float4 *sq = s_q[wib];
+        if (SELF) {
+            p2p_pair_f32<KERNEL, true, ROWS, true>(pf, fa, sa, fb, nb, 0.f, 0.f, 0.f, eps, acc4, n, lane, sq);
+        } else if (near) {
+            p2p_pair_f32<KERNEL, false, ROWS, true>(pf, fa, na, fb, sb, ox, oy, oz, eps, acc4, n, lane, sq);
+            if (sb < nb && sa > 0)
+                p2p_pair_f32<KERNEL, false, ROWS, true>(pf, fa, sa, fb + sb, nb - sb, ox, oy, oz, eps, acc4, n, lane, sq);
+        } else {
+            p2p_pair_f32<KERNEL, false, ROWS, false>(pf, fa, na, fb, sb, ox, oy, oz, eps, acc4, n, lane, sq);
+            if (sb < nb && sa > 0)
+                p2p_pair_f32<KERNEL, false, ROWS, false>(pf, fa, sa, fb + sb, nb - sb, ox, oy, oz, eps, acc4, n, lane, sq);
+        }
         if (lane == 0) {
             // pairs evaluated: all (or i < j for a self pair) minus fast-fast pairs
-            unsigned long long cnt = SELF ? (unsigned long long)na * (na - 1) / 2 : (unsigned long long)na * nb;
-            if (MASKED) {
-                int fa_n = 0, fb_n = 0;
-                for (int q = 0; q < na; ++q) fa_n += fs[fa + q] ? 1 : 0;
-                for (int q = 0; q < nb; ++q) fb_n += fs[fb + q] ? 1 : 0;
-                cnt -= SELF ? (unsigned long long)fa_n * (fa_n - 1) / 2 : (unsigned long long)fa_n * fb_n;
-            }
-            my_pairs += cnt;
+            const unsigned long long fa_n = na - sa, fb_n = nb - sb;
+            my_pairs += SELF ? (unsigned long long)na * (na - 1) / 2 - fa_n * (fa_n - (fa_n > 0 ? 1 : 0)) / 2
+                             : (unsigned long long)na * nb - fa_n * fb_n;
         }
     }
     if (lane == 0 && my_pairs) atomicAdd(pair_counter, my_pairs);
@@ -391,22 +385,26 @@ static tg_status launch_p2p_generic(tg_ctx *c, const TreeView &t, const Geom *d_
 
 template <class T, class T4>
 static tg_status launch_p2p(tg_ctx *c, const TreeView &t, const Geom *d_geom, const uint2 *pairs, int64_t npairs,
-                            const T4 *pf, const uint8_t *fs, bool masked, bool self, double *acc4);
+                            const T4 *pf, const uint8_t *fs, const int32_t *nslow, bool masked, bool self, double *acc4);
 
 template <>
 tg_status launch_p2p<double, dbl4>(tg_ctx *c, const TreeView &t, const Geom *d_geom, const uint2 *pairs, int64_t npairs,
-                                   const dbl4 *pf, const uint8_t *fs, bool masked, bool self, double *acc4)
+                                   const dbl4 *pf, const uint8_t *fs, const int32_t *nslow, bool masked, bool self,
+                                   double *acc4)
 {
+    (void)nslow;   // the float64 tile masks fast-fast pairs one by one
     (void)self;   // the float64 tile handles self pairs at run time
     return launch_p2p_generic<double, dbl4>(c, t, d_geom, pairs, npairs, pf, fs, masked, acc4);
 }
 
 template <>
 tg_status launch_p2p<float, float4>(tg_ctx *c, const TreeView &t, const Geom *d_geom, const uint2 *pairs,
-                                    int64_t npairs, const float4 *pf, const uint8_t *fs, bool masked, bool self,
-                                    double *acc4)
+                                    int64_t npairs, const float4 *pf, const uint8_t *fs, const int32_t *nslow,
+                                    bool masked, bool self, double *acc4)
 {
     (void)d_geom;
+    (void)fs;
+    (void)masked;   // classes arrive as slow-first leaves (nslow), not per-particle flags
     const int grid = grid_for(npairs * 32, 256, c->num_sms * 8);
     const float eps = (float)c->prm.eps;
     unsigned long long *ctr = c->d_counters;
@@ -414,19 +412,14 @@ tg_status launch_p2p<float, float4>(tg_ctx *c, const TreeView &t, const Geom *d_
     // rows per lane: one for leaves of up to ~32 particles, two for larger leaf sizes
     const bool two = c->prm.n_crit > 64;
     const bool plummer = c->prm.kernel == TG_KERNEL_PLUMMER;
-#define TG_P2P_W(M, K, S, R) \
-    p2p_warp_f32<M, K, S, R><<<grid, 256, 0, c->stream>>>(t, c->walk_log2L, pairs, npairs, pf, fs, eps, acc4, t.n, ctr)
-#define TG_P2P_R(M, K, S) \
-    if (two) TG_P2P_W(M, K, S, 2); else TG_P2P_W(M, K, S, 1);
-#define TG_P2P_S(M, K) \
-    if (self) { TG_P2P_R(M, K, true) } else { TG_P2P_R(M, K, false) }
-    if (masked) {
-        if (plummer) { TG_P2P_S(true, TG_KERNEL_PLUMMER) }
-        else { TG_P2P_S(true, TG_KERNEL_WENDLAND_C2) }
-    } else {
-        if (plummer) { TG_P2P_S(false, TG_KERNEL_PLUMMER) }
-        else { TG_P2P_S(false, TG_KERNEL_WENDLAND_C2) }
-    }
+#define TG_P2P_W(K, S, R) \
+    p2p_warp_f32<K, S, R><<<grid, 256, 0, c->stream>>>(t, c->walk_log2L, pairs, npairs, pf, nslow, eps, acc4, t.n, ctr)
+#define TG_P2P_R(K, S) \
+    if (two) TG_P2P_W(K, S, 2); else TG_P2P_W(K, S, 1);
+#define TG_P2P_S(K) \
+    if (self) { TG_P2P_R(K, true) } else { TG_P2P_R(K, false) }
+    if (plummer) { TG_P2P_S(TG_KERNEL_PLUMMER) }
+    else { TG_P2P_S(TG_KERNEL_WENDLAND_C2) }
 #undef TG_P2P_S
 #undef TG_P2P_R
 #undef TG_P2P_W

@@ -99,6 +99,7 @@ namespace tg {
 enum Slot {
     B_GEOM = 0, B_PARTIAL, B_KEYS0, B_KEYS1, B_VALS0, B_VALS1, B_HIST, B_SCAN_TMP,
     B_XS, B_YS, B_ZS, B_MS, B_FS, B_PF, B_LEAF_OF,
+    B_XS2, B_YS2, B_ZS2, B_MS2, B_FS2, B_PERM2, B_NSLOW,
     B_C_LEVEL, B_C_X, B_C_Y, B_C_Z, B_C_FIRST, B_C_COUNT, B_C_CHILD, B_C_PARENT, B_C_NCHILD,
     B_C_TMP0, B_C_TMP1,
     B_MOM, B_MOMF, B_MOM01, B_LOC, B_ACC,
