@@ -27,33 +27,66 @@ __device__ __forceinline__ double cell_centre(const Geom &g, const TreeView &t, 
 }
 
 // Eq. (1) with R = kappa * side, and the rule that cell pairs closer than eps (cube gap) never use
-// M2L for the Wendland kernel.  Exact: integer units of half the finer cell's side.
+// M2L for the Wendland kernel.  In integer units of half the finer cell's side the tests read
+//   (double)d2 * theta^2 > kappa^2 * (2 (h_a + h_b))^2   and   (double)g2 > (eps / u)^2,
+// where one of h_a, h_b is 1 and the other 2^dl (dl = level difference), u = L / 2^(lf+1).  Both
+// sides are monotone in the integers d2, g2, so the host turns each comparison into an integer
+// threshold per dl (MAC) and per finer level lf (gap), reproducing the float64 decisions exactly.
 struct MacParams {
-    double theta2, kappa2, eps;
-    int log2L, wendland;
+    long long mac_min_d2[kMaxLevel + 1];   // well separated iff d2 >= mac_min_d2[dl]
+    long long gap_min_g2[kMaxLevel + 1];   // gap rule passes iff g2 >= gap_min_g2[lf]
+    int wendland;
 };
+
+// smallest integer v >= 0 with pred(v) (pred monotone), searched over [0, 2^62)
+template <class Pred>
+static long long min_true(Pred pred)
+{
+    long long lo = 0, hi = 1ll << 62;   // pred(hi) assumed true
+    if (pred(0)) return 0;
+    while (hi - lo > 1) {
+        const long long mid = lo + (hi - lo) / 2;
+        if (pred(mid)) hi = mid;
+        else lo = mid;
+    }
+    return hi;
+}
+
+static MacParams make_mac_params(const tg_params &prm, int log2L)
+{
+    MacParams mp;
+    const double theta2 = prm.theta * prm.theta, kappa2 = prm.kappa * prm.kappa;
+    for (int dl = 0; dl <= kMaxLevel; ++dl) {
+        const double rsum = (double)(2 * (1ll + (1ll << dl)));
+        const double K = kappa2 * (rsum * rsum);
+        mp.mac_min_d2[dl] = min_true([&](long long d2) { return (double)d2 * theta2 > K; });
+    }
+    for (int lf = 0; lf <= kMaxLevel; ++lf) {
+        const double eu = ldexp(prm.eps, lf + 1 - log2L);
+        const double E = eu * eu;
+        mp.gap_min_g2[lf] = min_true([&](long long g2) { return (double)g2 > E; });
+    }
+    mp.wendland = prm.kernel == TG_KERNEL_WENDLAND_C2;
+    return mp;
+}
 
 __device__ __forceinline__ bool well_separated(const TreeView &t, const MacParams &mp, int a, int b)
 {
     const int la = t.level[a], lb = t.level[b];
     const int lf = la > lb ? la : lb;
-    const int64_t ha = (int64_t)1 << (lf - la), hb = (int64_t)1 << (lf - lb);
-    const uint32_t ca[3] = {t.cx[a], t.cy[a], t.cz[a]}, cb[3] = {t.cx[b], t.cy[b], t.cz[b]};
-    int64_t d2 = 0, g2 = 0;
+    const long long ha = 1ll << (lf - la), hb = 1ll << (lf - lb);
+    const long long dxs[3] = {centre_delta(t.cx[a], la, t.cx[b], lb, lf), centre_delta(t.cy[a], la, t.cy[b], lb, lf),
+                              centre_delta(t.cz[a], la, t.cz[b], lb, lf)};
+    long long d2 = 0, g2 = 0;
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-        int64_t dk = (2 * (int64_t)ca[k] + 1) * ha - (2 * (int64_t)cb[k] + 1) * hb;
-        if (dk < 0) dk = -dk;
+        const long long dk = dxs[k] < 0 ? -dxs[k] : dxs[k];
         d2 += dk * dk;
-        int64_t gk = dk - (ha + hb);
+        const long long gk = dk - (ha + hb);
         if (gk > 0) g2 += gk * gk;
     }
-    const double rsum = (double)(2 * (ha + hb));
-    if (!(__dmul_rn((double)d2, mp.theta2) > __dmul_rn(mp.kappa2, __dmul_rn(rsum, rsum)))) return false;
-    if (mp.wendland) {
-        const double eu = ldexp(mp.eps, lf + 1 - mp.log2L);
-        if (!((double)g2 > __dmul_rn(eu, eu))) return false;
-    }
+    if (d2 < mp.mac_min_d2[la > lb ? la - lb : lb - la]) return false;
+    if (mp.wendland && g2 < mp.gap_min_g2[lf]) return false;
     return true;
 }
 
@@ -286,41 +319,69 @@ struct WalkOut {
     unsigned long long cap_front, cap_blocks, cap_p2p;
 };
 
+// Warp-aggregated slot reservation on a shared counter: one atomic per warp, each lane gets its
+// own base.  Every lane of the warp must call it (lanes with nothing to add pass 0).
+__device__ __forceinline__ unsigned long long warp_reserve(unsigned long long *ctr, unsigned cnt)
+{
+    const int lane = threadIdx.x & 31;
+    unsigned incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    const unsigned total = __shfl_sync(0xffffffffu, incl, 31);
+    unsigned long long base = 0;
+    if (lane == 31 && total) base = atomicAdd(ctr, (unsigned long long)total);
+    base = __shfl_sync(0xffffffffu, base, 31);
+    return base + (incl - cnt);
+}
+
 __global__ void walk_step(TreeView t, MacParams mp, const uint2 *front_in, int n_in, WalkOut o)
 {
-    for (int w = blockIdx.x * blockDim.x + threadIdx.x; w < n_in; w += gridDim.x * blockDim.x) {
-        const uint2 pr = front_in[w];
-        const int A = (int)pr.x, B = (int)pr.y;
-        const bool self = A == B;
-        const bool openA = t.nchild[A] != 0, openB = t.nchild[B] != 0;
-        const int ni = openA ? t.nchild[A] : 1, nj = openB ? t.nchild[B] : 1;
-        const int baseA = openA ? t.child_first[A] : A, baseB = openB ? t.child_first[B] : B;
+    // whole warps iterate together so that the counters can be reserved per warp
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t w0 = (int64_t)blockIdx.x * blockDim.x; w0 < n_in; w0 += stride) {
+        const int64_t w = w0 + threadIdx.x;
+        const bool active = w < n_in;
+        int A = 0, B = 0, ni = 0, nj = 0, baseA = 0, baseB = 0;
+        bool self = false;
         unsigned long long mask = 0;
-        int n_front = 0, n_p2p = 0, n_self = 0;
-        // pass 1: classify and count
-        for (int i = 0; i < ni; ++i)
-            for (int j = self ? i : 0; j < nj; ++j) {
-                const int x = baseA + i, y = baseB + j;
-                const bool lx = t.nchild[x] == 0, ly = t.nchild[y] == 0;
-                if (x == y) {
-                    if (lx) ++n_self;
-                    else ++n_front;
-                } else if (well_separated(t, mp, x, y)) {
-                    mask |= 1ull << (8 * i + j);
-                } else if (lx && ly) {
-                    ++n_p2p;
-                } else {
-                    ++n_front;
+        unsigned n_front = 0, n_p2p = 0, n_self = 0;
+        if (active) {
+            const uint2 pr = front_in[w];
+            A = (int)pr.x;
+            B = (int)pr.y;
+            self = A == B;
+            const bool openA = t.nchild[A] != 0, openB = t.nchild[B] != 0;
+            ni = openA ? t.nchild[A] : 1;
+            nj = openB ? t.nchild[B] : 1;
+            baseA = openA ? t.child_first[A] : A;
+            baseB = openB ? t.child_first[B] : B;
+            // pass 1: classify and count
+            for (int i = 0; i < ni; ++i)
+                for (int j = self ? i : 0; j < nj; ++j) {
+                    const int x = baseA + i, y = baseB + j;
+                    const bool lx = t.nchild[x] == 0, ly = t.nchild[y] == 0;
+                    if (x == y) {
+                        if (lx) ++n_self;
+                        else ++n_front;
+                    } else if (well_separated(t, mp, x, y)) {
+                        mask |= 1ull << (8 * i + j);
+                    } else if (lx && ly) {
+                        ++n_p2p;
+                    } else {
+                        ++n_front;
+                    }
                 }
-            }
-        unsigned long long fb = n_front ? atomicAdd(o.counters + 0, (unsigned long long)n_front) : 0;
-        unsigned long long pb = n_p2p ? atomicAdd(o.counters + 2, (unsigned long long)n_p2p) : 0;
-        unsigned long long sb = n_self ? atomicAdd(o.counters + 4, (unsigned long long)n_self) : 0;
-        if (mask) {
-            const unsigned long long bb = atomicAdd(o.counters + 1, 1ull);
-            atomicAdd(o.counters + 3, (unsigned long long)__popcll(mask));
-            if (bb < o.cap_blocks) o.blocks[bb] = M2LBlock{(uint32_t)A, (uint32_t)B, mask};
         }
+        unsigned long long fb = warp_reserve(o.counters + 0, n_front);
+        unsigned long long pb = warp_reserve(o.counters + 2, n_p2p);
+        unsigned long long sb = warp_reserve(o.counters + 4, n_self);
+        const unsigned long long bb = warp_reserve(o.counters + 1, mask ? 1u : 0u);
+        warp_reserve(o.counters + 3, (unsigned)__popcll(mask));
+        if (!active) continue;
+        if (mask && bb < o.cap_blocks) o.blocks[bb] = M2LBlock{(uint32_t)A, (uint32_t)B, mask};
         if (!n_front && !n_p2p && !n_self) continue;
         // pass 2: write the frontier and P2P entries
         for (int i = 0; i < ni; ++i)
@@ -502,19 +563,16 @@ static tg_status run_walk(tg_ctx *c, const TreeView &t, int64_t *n_blocks, int64
                           int64_t *n_self)
 {
     tg_status st;
-    MacParams mp;
-    mp.theta2 = c->prm.theta * c->prm.theta;
-    mp.kappa2 = c->prm.kappa * c->prm.kappa;
-    mp.eps = c->prm.eps;
-    mp.wendland = c->prm.kernel == TG_KERNEL_WENDLAND_C2;
+    int log2L = 0;
     {
         const Geom *dg = static_cast<const Geom *>(c->buf[B_GEOM].p);
         cudaMemcpyAsync(c->h_pinned + 32, &dg->log2L, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
         cudaError_t e = cudaStreamSynchronize(c->stream);
         if (e != cudaSuccess) return cuda_check(c, e, "walk setup");
-        mp.log2L = *reinterpret_cast<int *>(c->h_pinned + 32);
+        log2L = *reinterpret_cast<int *>(c->h_pinned + 32);
     }
-    c->walk_log2L = mp.log2L;
+    const MacParams mp = make_mac_params(c->prm, log2L);
+    c->walk_log2L = log2L;
     size_t cap_front = (size_t)t.ncell * 8 + 1024, cap_blocks = (size_t)t.ncell * 8 + 1024,
            cap_p2p = (size_t)t.ncell * 24 + 1024;
     for (int attempt = 0; attempt < 6; ++attempt) {
