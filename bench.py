@@ -268,20 +268,25 @@ def run_ours(args):
             pass
     fp32_peak_tflops = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
     kernels = {k: v for k, v in prof.items() if v["launches"] > 0 and k != "_all"}
+    traffic = captured_traffic()
     dom = max(kernels.items(), key=lambda kv: kv[1]["ms"])[0] if kernels else None
     roof = None
     if dom == "p2p":
         flops = 30.0 * stats["p2p_pairs"]
         achieved = flops / (kernels["p2p"]["ms"] / 1e3) / 1e12
+        units = stats["p2p_pairs"] / kernels["p2p"]["launches"]
         roof = {"kernel": "p2p_mutual", "bound": "alu", "achieved": achieved, "peak": fp32_peak_tflops,
-                "unit": "TFLOP/s", "frac": achieved / fp32_peak_tflops, "traffic": None,
+                "unit": "TFLOP/s", "frac": achieved / fp32_peak_tflops,
+                "traffic": scaled_traffic(traffic, "p2p", units),
                 "per_launch": {"flops": flops / kernels["p2p"]["launches"],
                                "ms": kernels["p2p"]["ms"] / kernels["p2p"]["launches"]}}
     elif dom == "m2l":
         flops = m2l_flops(PARAMS["p"], stats["m2l_pairs"], stats)
         achieved = flops / (kernels["m2l"]["ms"] / 1e3) / 1e12
+        units = stats["m2l_pairs"] / kernels["m2l"]["launches"]
         roof = {"kernel": "m2l_mutual", "bound": "alu", "achieved": achieved, "peak": fp32_peak_tflops,
-                "unit": "TFLOP/s", "frac": achieved / fp32_peak_tflops, "traffic": None,
+                "unit": "TFLOP/s", "frac": achieved / fp32_peak_tflops,
+                "traffic": scaled_traffic(traffic, "m2l", units),
                 "per_launch": {"flops": flops / kernels["m2l"]["launches"],
                                "ms": kernels["m2l"]["ms"] / kernels["m2l"]["launches"]}}
     cpu = None
@@ -320,6 +325,36 @@ def run_ours(args):
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
+
+
+def captured_traffic():
+    """DRAM bytes per launch from the committed ncu captures, kept only while the kernel source
+    hash recorded with them still matches the source being run."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "roofline_traffic.json")
+    if not os.path.exists(path):
+        return {}
+    data = json.load(open(path))
+    out = {}
+    for key, rec in data.items():
+        if not isinstance(rec, dict) or "source" not in rec:
+            continue
+        h = hashlib.sha256()
+        for part in rec["source"].split("+"):
+            f = part if os.path.isabs(part) else os.path.join(ROOT, part) if "/" in part else \
+                os.path.join(ROOT, "paper_1712_10116_gb300", "csrc", part)
+            h.update(open(f, "rb").read())
+        if h.hexdigest()[:16] == rec["source_sha256_16"]:
+            out[key] = rec
+    return out
+
+
+def scaled_traffic(traffic, key, units_per_launch):
+    """Captured bytes per launch scaled to the bench's average launch by the units it processes."""
+    rec = traffic.get(key)
+    if not rec:
+        return None
+    return rec["bytes_per_launch"] * units_per_launch / rec["units_per_launch"]
 
 
 def m2l_flops(p, pairs, stats):
