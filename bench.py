@@ -388,8 +388,14 @@ def run_eval_only(args):
         solver.fmm_forces(P, M, F, want_pot=False)
     torch.cuda.synchronize()
     dt = (time.perf_counter() - t0) / max(args.steps, 1)
+    # one more evaluation with every launch timed, for the per-stage breakdown
+    tg.tg_reset_stats(solver.ctx)
+    tg.tg_set_profiling(solver.ctx, 2)
+    solver.fmm_forces(P, M, F, want_pot=False)
+    stages = {k: round(v["ms"], 3) for k, v in tg.tg_get_profile(solver.ctx).items()}
+    tg.tg_set_profiling(solver.ctx, 0)
     print(json.dumps({"mode": "eval-only", "n": args.n, "n_crit": args.n_crit, "masked": bool(args.masked),
-                      "ms_per_eval": 1e3 * dt, "stats": solver.stats()}), flush=True)
+                      "ms_per_eval": 1e3 * dt, "stage_ms": stages, "stats": solver.stats()}), flush=True)
     solver.close()
 
 
