@@ -15,6 +15,7 @@
 #include "tg_common.cuh"
 #include "tg_tables.cuh"
 #include "p2p_tile.cuh"
+#include "p2p_owner.cuh"
 #include "m2l_sym.cuh"
 
 namespace tg {
@@ -688,6 +689,24 @@ tg_status launch_m2l<double>(tg_ctx *c, const TreeView &t, const M2LBlock *block
     return cuda_check(c, cudaGetLastError(), "m2l launch");
 }
 
+// Distinct leaf pairs: float32 packs rows by owner leaf, float64 keeps one block per pair.
+template <class T, class T4>
+static tg_status launch_p2p_pairs(tg_ctx *c, const TreeView &t, const Geom *d_geom, const uint2 *pairs, int64_t npairs,
+                                  const T4 *pf, const uint8_t *fs, const int32_t *nslow, bool masked, double *acc4)
+{
+    return launch_p2p<T, T4>(c, t, d_geom, pairs, npairs, pf, fs, nslow, masked, false, acc4);
+}
+template <>
+tg_status launch_p2p_pairs<float, float4>(tg_ctx *c, const TreeView &t, const Geom *d_geom, const uint2 *pairs,
+                                          int64_t npairs, const float4 *pf, const uint8_t *fs, const int32_t *nslow,
+                                          bool masked, double *acc4)
+{
+    (void)d_geom;
+    (void)fs;
+    (void)masked;   // classes arrive as slow-first leaves (nslow)
+    return launch_p2p_owner(c, t, pairs, npairs, pf, nslow, acc4);
+}
+
 template <class T, class T4>
 static tg_status eval_typed(tg_ctx *c, int n, int ncell, const TreeView &t, const Geom *d_geom, bool masked,
                             int64_t n_blocks, int64_t n_p2p, int64_t n_self)
@@ -766,7 +785,7 @@ static tg_status eval_typed(tg_ctx *c, int n, int ncell, const TreeView &t, cons
         l2p_particles<T, T4><<<grid_for(n, 128), 128, 0, c->stream>>>(n, t, c->walk_log2L, pf, leaf_of, fs, masked ? 1 : 0,
                                                                       p, nc, ncp, L, acc4);
     }
-    if (n_p2p > 0 && (st = launch_p2p<T, T4>(c, t, d_geom, p2p, n_p2p, pf, fs, nslow, masked, false, acc4))) return st;
+    if (n_p2p > 0 && (st = launch_p2p_pairs<T, T4>(c, t, d_geom, p2p, n_p2p, pf, fs, nslow, masked, acc4))) return st;
     if (n_self > 0 &&
         (st = launch_p2p<T, T4>(c, t, d_geom, p2p + (c->p2p_cap - n_self), n_self, pf, fs, nslow, masked, true, acc4)))
         return st;

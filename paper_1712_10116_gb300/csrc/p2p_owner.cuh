@@ -1,0 +1,330 @@
+// p2p_owner.cuh -- mutual P2P of distinct leaf pairs with rows packed across partners (float32).
+//
+// Each unordered leaf pair {A, B} (A != B) gets one owner: the larger leaf (ties: the larger
+// index).  A warp takes an owner B.  B's particles are the columns.  They are staged once in
+// shared memory, together with B's reaction sums.  The particles of B's partners are packed
+// densely into the rows, in chunks of 32*ROWS.  Each row is shifted into B's frame by the exact
+// centre offset of its own leaf, so no row slot is wasted on the tail of a small leaf.  For every
+// row/column pair the kernel value is computed once and applied to both particles, with opposite
+// signs (Sec. 2.1, Eq. 2).  Rows keep their sums in registers and flush them once per chunk.
+// Columns combine their partials with a warp reduce-scatter into shared memory, and flush them
+// once per work unit (kOwnUnit partners of the owner; the units of all owners are handed out
+// dynamically to the warps).
+//
+// With slow/fast classes the leaves hold their slow particles first.  Slow rows meet every
+// column; fast rows meet only the owner's slow columns, so fast-fast pairs are never computed
+// (a kickS2F feels the slow masses only).  Within a batch the partners whose cube lies closer
+// than eps to the owner's come first, and chunks made only of the other partners' rows skip the
+// softened branch of the pair kernel.
+#pragma once
+#include "p2p_tile.cuh"
+
+namespace tg {
+
+constexpr int kOwnUnit = 16;   // partners per work unit of the owner kernel
+
+// Owner and partner of each distinct leaf pair, and per-owner partner counts (own_cnt starts at zero).
+__global__ void p2p_owner_count(const uint2 *__restrict__ pairs, int64_t npairs, const int32_t *__restrict__ count,
+                                uint32_t *own_cnt, uint2 *tagged)
+{
+    for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < npairs; w += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t x = pairs[w].x, y = pairs[w].y;
+        const int cx = count[x], cy = count[y];
+        const uint32_t owner = (cx > cy || (cx == cy && x > y)) ? x : y;
+        tagged[w] = make_uint2(owner, owner == x ? y : x);
+        atomicAdd(&own_cnt[owner], 1u);
+    }
+}
+
+// Partners grouped by owner: partners[own_off[B] .. own_off[B] + own_cnt[B]).  Every kOwnUnit-th
+// partner of an owner also opens a work unit (owner, position); ctr[0] counts the units.
+// own_fill and ctr start at zero.
+__global__ void p2p_owner_fill(const uint2 *__restrict__ tagged, int64_t npairs, const uint32_t *__restrict__ own_off,
+                               uint32_t *own_fill, int32_t *partners, uint2 *units, uint32_t *ctr)
+{
+    for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < npairs; w += (int64_t)gridDim.x * blockDim.x) {
+        const uint2 op = tagged[w];
+        const uint32_t f = atomicAdd(&own_fill[op.x], 1u);
+        partners[own_off[op.x] + f] = (int32_t)op.y;
+        if (f % kOwnUnit == 0) units[atomicAdd(&ctr[0], 1u)] = make_uint2(op.x, f);
+    }
+}
+
+// The partners of one work unit (at most 32), in slot order (near partners first).
+struct OwnerBatch {
+    float4 off[32];    // centre of the partner minus centre of the owner
+    int first[32];     // first particle of the partner
+    int nslow[32];     // slow particles of the partner (all of them without classes)
+    int inc[2][32];    // inclusive row counts over slots: [0] slow rows, [1] fast rows
+};
+
+struct OwnerShared {
+    float4 q[8][kMaxNcrit];       // owner's particles (columns), per warp
+    float acc[8][kMaxNcrit][4];   // owner's reaction sums (ax, ay, az, phi), per warp
+    OwnerBatch b[8];
+};
+
+// Rows i0 .. i0 + 32*ROWS of one phase (0: slow rows, 1: fast rows) against the first ncol columns.
+template <int KERNEL, int ROWS, bool NEAR>
+__device__ __noinline__ void owner_rows(const float4 *__restrict__ pf, const OwnerBatch *ob, int phase, int i0, int nrows,
+                                        const float4 *sq, float (*sacc)[4], int ncol, float eps, double *acc4, int n,
+                                        int lane)
+{
+    const float eps2 = eps * eps, inv_eps = 1.0f / eps, inv_eps3 = inv_eps * inv_eps * inv_eps;
+    const int *inc = ob->inc[phase];
+    float4 p[ROWS];
+    int gi[ROWS];
+    float ra[ROWS][4];
+#pragma unroll
+    for (int r = 0; r < ROWS; ++r) {
+        const int i = i0 + lane + 32 * r;
+        gi[r] = -1;
+        p[r] = make_float4(1e8f, 1e8f, 1e8f, 0.f);   // far away, massless
+        if (i < nrows) {
+            // slot s: the first with inc[s] > i (inc is non-decreasing and inc[31] = nrows > i)
+            int s = 0;
+#pragma unroll
+            for (int b = 16; b >= 1; b >>= 1)
+                if (inc[s + b - 1] <= i) s += b;
+            const int loc = i - (s ? inc[s - 1] : 0);
+            gi[r] = ob->first[s] + (phase ? ob->nslow[s] : 0) + loc;
+            const float4 o = ob->off[s];
+            float4 q = pf[gi[r]];
+            q.x += o.x;
+            q.y += o.y;
+            q.z += o.z;
+            p[r] = q;
+        }
+        ra[r][0] = ra[r][1] = ra[r][2] = ra[r][3] = 0.f;
+    }
+    // columns in batches of 8; lane l visits column c ^ ((l >> 2) & 7) of a batch (see p2p_pair_f32)
+    const int cperm = (lane >> 2) & 7;
+    for (int j0 = 0; j0 < ncol; j0 += 8) {
+        float col[32];
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            const int j = j0 + (c ^ cperm);
+            float cx = 0.f, cy = 0.f, cz = 0.f, cp = 0.f;
+            if (j < ncol) {
+                const float4 q = sq[j];
+#pragma unroll
+                for (int r = 0; r < ROWS; ++r) {
+                    const float dx = q.x - p[r].x, dy = q.y - p[r].y, dz = q.z - p[r].z;
+                    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                    float gk, ph;
+                    pair_kernel_f32<KERNEL, NEAR>(r2, eps, eps2, inv_eps, inv_eps3, gk, ph);
+                    const float mq = q.w * gk, mp = p[r].w * gk;
+                    ra[r][0] = fmaf(mq, dx, ra[r][0]);
+                    ra[r][1] = fmaf(mq, dy, ra[r][1]);
+                    ra[r][2] = fmaf(mq, dz, ra[r][2]);
+                    ra[r][3] = fmaf(q.w, ph, ra[r][3]);
+                    cx = fmaf(-mp, dx, cx);
+                    cy = fmaf(-mp, dy, cy);
+                    cz = fmaf(-mp, dz, cz);
+                    cp = fmaf(p[r].w, ph, cp);
+                }
+            }
+            col[4 * c + 0] = cx;
+            col[4 * c + 1] = cy;
+            col[4 * c + 2] = cz;
+            col[4 * c + 3] = cp;
+        }
+#pragma unroll
+        for (int h = 16; h >= 4; h >>= 1)
+#pragma unroll
+            for (int q = 0; q < h; ++q) col[q] += __shfl_xor_sync(0xffffffffu, col[q + h], h);
+#pragma unroll
+        for (int h = 2; h >= 1; h >>= 1) {
+            const bool hi = (lane & h) != 0;
+#pragma unroll
+            for (int q = 0; q < h; ++q) {
+                const float send = hi ? col[q] : col[q + h];
+                const float keep = hi ? col[q + h] : col[q];
+                col[q] = keep + __shfl_xor_sync(0xffffffffu, send, h);
+            }
+        }
+        // lane l holds column j0 + l/4, component l%4; each (column, component) has one lane
+        const int cj = lane >> 2, comp = lane & 3;
+        if (j0 + cj < ncol) sacc[j0 + cj][comp] += col[0];
+    }
+#pragma unroll
+    for (int r = 0; r < ROWS; ++r)
+        if (gi[r] >= 0)
+#pragma unroll
+            for (int comp = 0; comp < 4; ++comp) atomicAdd(&acc4[(size_t)comp * n + gi[r]], f2d_exact(ra[r][comp]));
+}
+
+__device__ __forceinline__ int warp_incl_scan(int v, int lane)
+{
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const int u = __shfl_up_sync(0xffffffffu, v, d);
+        if (lane >= d) v += u;
+    }
+    return v;
+}
+
+// One warp per work unit (kOwnUnit partners of one owner), units taken from a shared counter
+// (ctr[1], starts at zero) so that the load stays balanced whatever the spread of leaf work.
+template <int KERNEL, int ROWS>
+__global__ void __launch_bounds__(256, 2) p2p_owner_f32(TreeView t, int log2L, const uint2 *__restrict__ units,
+                                                        uint32_t *ctr, const uint32_t *__restrict__ own_off,
+                                                        const uint32_t *__restrict__ own_cnt,
+                                                        const int32_t *__restrict__ partners, const float4 *__restrict__ pf,
+                                                        const int32_t *__restrict__ nslow, float eps, double *acc4, int n,
+                                                        unsigned long long *pair_counter)
+{
+    static_assert(kOwnUnit <= 32, "one partner per lane");
+    __shared__ OwnerShared sh;
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const unsigned lt = (1u << lane) - 1u;
+    float4 *sq = sh.q[wib];
+    float(*sacc)[4] = sh.acc[wib];
+    OwnerBatch *ob = &sh.b[wib];
+    const uint32_t nunits = ctr[0];
+    unsigned long long my_pairs = 0;
+    for (;;) {
+        uint32_t k = 0;
+        if (lane == 0) k = atomicAdd(&ctr[1], 1u);
+        k = __shfl_sync(0xffffffffu, k, 0);
+        if (k >= nunits) break;
+        const uint2 u = units[k];
+        const int B = (int)u.x, pb = (int)u.y;
+        const int cnt = (int)own_cnt[B], base = (int)own_off[B];
+        const int fb = t.first[B], nb = t.count[B], sB = nslow ? nslow[B] : nb, lB = t.level[B];
+        {
+            const int np = min(kOwnUnit, cnt - pb);
+            int fa = 0, na = 0, sa = 0;
+            float4 off = make_float4(0.f, 0.f, 0.f, 0.f);
+            bool near = false;
+            if (lane < np) {
+                const int A = partners[base + pb + lane];
+                fa = t.first[A];
+                na = t.count[A];
+                sa = nslow ? nslow[A] : na;
+                // z_A - z_B = delta * L / 2^(lf+1), exact in float; |delta| < 2^23 fits int32
+                const int lA = t.level[A], lf = lA > lB ? lA : lB;
+                const long long dl[3] = {centre_delta(t.cx[A], lA, t.cx[B], lB, lf),
+                                         centre_delta(t.cy[A], lA, t.cy[B], lB, lf),
+                                         centre_delta(t.cz[A], lA, t.cz[B], lB, lf)};
+                const float unit = pow2f(log2L - lf - 1);
+                off = make_float4((float)(int)dl[0] * unit, (float)(int)dl[1] * unit, (float)(int)dl[2] * unit, 0.f);
+                if (KERNEL == TG_KERNEL_WENDLAND_C2) {
+                    // cube gap below eps: some pair may fall inside the softening length
+                    const long long ha = 1ll << (lf - lA), hb = 1ll << (lf - lB);
+                    long long g2 = 0;
+#pragma unroll
+                    for (int d = 0; d < 3; ++d) {
+                        const long long gd = (dl[d] < 0 ? -dl[d] : dl[d]) - (ha + hb);
+                        if (gd > 0) g2 += gd * gd;
+                    }
+                    const float eu = eps * pow2f(lf + 1 - log2L);   // eps in half-units of the finer level
+                    near = !((float)g2 >= eu * eu * 1.0001f);
+                }
+                // pairs evaluated: all minus fast-fast
+                my_pairs += (unsigned long long)na * nb - (unsigned long long)(na - sa) * (nb - sB);
+            }
+            const unsigned bn = __ballot_sync(0xffffffffu, lane < np && near);
+            const unsigned bf = __ballot_sync(0xffffffffu, lane < np && !near);
+            const int n_near = __popc(bn);
+            const int slot = near ? __popc(bn & lt) : n_near + __popc(bf & lt);
+            __syncwarp();
+            if (lane < np) {
+                ob->off[slot] = off;
+                ob->first[slot] = fa;
+                ob->nslow[slot] = sa;
+                ob->inc[1][slot] = na;   // partner size, replaced by the fast-row scan below
+            }
+            __syncwarp();
+            const int cS = lane < np ? ob->nslow[lane] : 0;
+            const int cF = lane < np ? ob->inc[1][lane] - cS : 0;
+            const int incS = warp_incl_scan(cS, lane), incF = warp_incl_scan(cF, lane);
+            __syncwarp();
+            ob->inc[0][lane] = incS;
+            ob->inc[1][lane] = incF;
+            const int Ts = __shfl_sync(0xffffffffu, incS, 31), Tf = __shfl_sync(0xffffffffu, incF, 31);
+            const int nearS = n_near ? __shfl_sync(0xffffffffu, incS, n_near - 1) : 0;
+            const int nearF = n_near ? __shfl_sync(0xffffffffu, incF, n_near - 1) : 0;
+            for (int jc = 0; jc < nb; jc += kMaxNcrit) {
+                const int nbc = min(kMaxNcrit, nb - jc);
+                const int nsc = max(0, min(sB - jc, nbc));   // slow columns of this chunk (slow-first leaf)
+                __syncwarp();
+                for (int j = lane; j < nbc; j += 32) {
+                    sq[j] = pf[fb + jc + j];
+                    sacc[j][0] = sacc[j][1] = sacc[j][2] = sacc[j][3] = 0.f;
+                }
+                __syncwarp();
+                for (int i0 = 0; i0 < Ts; i0 += 32 * ROWS) {
+                    if (i0 < nearS) owner_rows<KERNEL, ROWS, true>(pf, ob, 0, i0, Ts, sq, sacc, nbc, eps, acc4, n, lane);
+                    else owner_rows<KERNEL, ROWS, false>(pf, ob, 0, i0, Ts, sq, sacc, nbc, eps, acc4, n, lane);
+                }
+                if (nsc > 0)
+                    for (int i0 = 0; i0 < Tf; i0 += 32 * ROWS) {
+                        if (i0 < nearF) owner_rows<KERNEL, ROWS, true>(pf, ob, 1, i0, Tf, sq, sacc, nsc, eps, acc4, n, lane);
+                        else owner_rows<KERNEL, ROWS, false>(pf, ob, 1, i0, Tf, sq, sacc, nsc, eps, acc4, n, lane);
+                    }
+                __syncwarp();
+                for (int j = lane; j < nbc; j += 32)
+#pragma unroll
+                    for (int comp = 0; comp < 4; ++comp)
+                        atomicAdd(&acc4[(size_t)comp * n + fb + jc + j], f2d_exact(sacc[j][comp]));
+            }
+        }
+    }
+    my_pairs = warp_sum(my_pairs);
+    if (lane == 0 && my_pairs) atomicAdd(pair_counter, my_pairs);
+}
+
+}  // namespace tg
+
+namespace tg {
+
+// Distinct leaf pairs in float32: group them by owner, then one warp per owner.
+static tg_status launch_p2p_owner(tg_ctx *c, const TreeView &t, const uint2 *pairs, int64_t npairs, const float4 *pf,
+                                  const int32_t *nslow, double *acc4)
+{
+    tg_status st;
+    const int ncell = t.ncell;
+    uint32_t *own_cnt, *own_fill, *own_off;
+    uint2 *tagged, *units;
+    int32_t *partners;
+    const int64_t max_units = npairs / kOwnUnit + ncell + 1;
+    if ((st = ensure_t(c, B_OWN_CNT, (size_t)ncell + 2, &own_cnt)) || (st = ensure_t(c, B_OWN_FILL, ncell, &own_fill)) ||
+        (st = ensure_t(c, B_OWN_OFF, ncell, &own_off)) || (st = ensure_t(c, B_OWN_LIST, max_units, &units)) ||
+        (st = ensure_t(c, B_OWN_TAG, npairs, &tagged)) || (st = ensure_t(c, B_OWN_PART, npairs, &partners)))
+        return st;
+    uint32_t *ctr = own_cnt + ncell;   // [0] work units, [1] next unit to take
+    cudaMemsetAsync(own_cnt, 0, sizeof(uint32_t) * ((size_t)ncell + 2), c->stream);
+    cudaMemsetAsync(own_fill, 0, sizeof(uint32_t) * (size_t)ncell, c->stream);
+    {
+        ProfScope ps_(c, TG_K_OTHER);
+        p2p_owner_count<<<grid_for(npairs, 256), 256, 0, c->stream>>>(pairs, npairs, t.count, own_cnt, tagged);
+    }
+    if ((st = exclusive_scan_u32(c, own_cnt, own_off, ncell, nullptr))) return st;
+    {
+        ProfScope ps_(c, TG_K_OTHER);
+        p2p_owner_fill<<<grid_for(npairs, 256), 256, 0, c->stream>>>(tagged, npairs, own_off, own_fill, partners, units, ctr);
+    }
+    const float eps = (float)c->prm.eps;
+    unsigned long long *pc = c->d_counters;
+    const bool plummer = c->prm.kernel == TG_KERNEL_PLUMMER;
+    ProfScope ps_(c, TG_K_P2P);
+    // two rows per lane: rows are packed densely, so the chunk is full whatever the leaf size
+    static int occ_w = 0, occ_p = 0;
+    int &occ = plummer ? occ_p : occ_w;
+    if (occ == 0) {
+        cudaError_t e = plummer ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, p2p_owner_f32<TG_KERNEL_PLUMMER, 2>, 256, 0)
+                                : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, p2p_owner_f32<TG_KERNEL_WENDLAND_C2, 2>, 256, 0);
+        if (e != cudaSuccess || occ < 1) occ = 1;
+    }
+    const int grid = c->num_sms * occ;
+    if (plummer)
+        p2p_owner_f32<TG_KERNEL_PLUMMER, 2><<<grid, 256, 0, c->stream>>>(t, c->walk_log2L, units, ctr, own_off, own_cnt,
+                                                                          partners, pf, nslow, eps, acc4, t.n, pc);
+    else
+        p2p_owner_f32<TG_KERNEL_WENDLAND_C2, 2><<<grid, 256, 0, c->stream>>>(t, c->walk_log2L, units, ctr, own_off, own_cnt,
+                                                                              partners, pf, nslow, eps, acc4, t.n, pc);
+    return cuda_check(c, cudaGetLastError(), "p2p owner launch");
+}
+
+}  // namespace tg
