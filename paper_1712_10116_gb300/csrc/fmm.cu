@@ -169,12 +169,24 @@ __global__ void leaf_class_partition(TreeView t, const double *xs, const double 
 // M01[cell][class][4] in float64 (monopole and dipole, the "centre of mass" part, accumulated in
 // float64 from float64 positions).  Offsets are in units of the cell side s.
 template <class T, class T4>
-__global__ void p2m_leaves(TreeView t, const Geom *gp, const double *xs, const double *ys, const double *zs,
-                           const double *ms, const uint8_t *fs, const T4 *pf, int p, int nc, int ncp, T *M,
-                           double *M01)
+__global__ void __launch_bounds__(128) p2m_leaves(TreeView t, const Geom *gp, const double *xs, const double *ys,
+                                                  const double *zs, const double *ms, const uint8_t *fs, const T4 *pf,
+                                                  int p, int nc, int ncp, T *M, double *M01)
 {
+    // per warp: powers r_a^e (axis a, 0 <= e <= p) of 32 particles, rows padded to 33 against bank
+    // conflicts, and the particles' masses split by class
+    __shared__ T s_pw[4][3][TG_PMAX + 1][33];
+    __shared__ T s_w[4][2][32];
+    __shared__ uint8_t s_e[3][168];
+    for (int k = threadIdx.x; k < 168; k += blockDim.x) {
+        s_e[0][k] = k < nc ? c_mi_x[k] : 0;
+        s_e[1][k] = k < nc ? c_mi_y[k] : 0;
+        s_e[2][k] = k < nc ? c_mi_z[k] : 0;
+    }
+    __syncthreads();
     const Geom g = *gp;
-    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nwarps = (gridDim.x * blockDim.x) >> 5;
     for (int c = warp; c < t.ncell; c += nwarps) {
         if (t.nchild[c] != 0) continue;
@@ -185,40 +197,76 @@ __global__ void p2m_leaves(TreeView t, const Geom *gp, const double *xs, const d
         double lo[2][4] = {{0, 0, 0, 0}, {0, 0, 0, 0}};
         for (int s = first + lane; s < first + count; s += 32) {
             const double m = ms[s];
-            const int cls = fs[s] ? 1 : 0;
-            lo[cls][0] += m;
-            lo[cls][1] += m * ((xs[s] - zx) * inv_s);
-            lo[cls][2] += m * ((ys[s] - zy) * inv_s);
-            lo[cls][3] += m * ((zs[s] - zz) * inv_s);
+            const bool fast = fs[s] != 0;
+            const double r[4] = {1.0, (xs[s] - zx) * inv_s, (ys[s] - zy) * inv_s, (zs[s] - zz) * inv_s};
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const double v = k ? m * r[k] : m;
+                lo[0][k] += fast ? 0.0 : v;
+                lo[1][k] += fast ? v : 0.0;
+            }
         }
+        double mine = 0.0;   // lane l < 8 keeps class l / 4, component l % 4
 #pragma unroll
         for (int cls = 0; cls < 2; ++cls)
 #pragma unroll
-            for (int k = 0; k < 4; ++k) lo[cls][k] = warp_sum(lo[cls][k]);
+            for (int k = 0; k < 4; ++k) {
+                const double v = warp_sum(lo[cls][k]);
+                if (lane == cls * 4 + k) mine = v;
+            }
         if (lane < 8) {
             const int cls = lane >> 2, k = lane & 3;
-            M01[((size_t)c * 2 + cls) * 4 + k] = lo[cls][k];
-            M[((size_t)c * 2 + cls) * ncp + k] = (T)lo[cls][k];
+            M01[((size_t)c * 2 + cls) * 4 + k] = mine;
+            M[((size_t)c * 2 + cls) * ncp + k] = (T)mine;
         }
-        // every order >= 2 in T from the per-particle offsets: lanes over coefficients
+        // orders >= 2 in T from the per-particle offsets: lanes over coefficients k = 4 + lane + 32 q
         const T inv_st = (T)ldexpf(1.0f, (int)t.level[c] - g.log2L);
-        for (int k = 4 + lane; k < ncp; k += 32) {
-            T accS = 0, accF = 0;
-            if (k < nc) {
-                const int ex = c_mi_x[k], ey = c_mi_y[k], ez = c_mi_z[k];
-                for (int s = first; s < first + count; ++s) {
-                    const T4 r = pf[s];
-                    const T rx = r.x * inv_st, ry = r.y * inv_st, rz = r.z * inv_st;
-                    T v = r.w;
-                    for (int e = 0; e < ex; ++e) v *= rx;
-                    for (int e = 0; e < ey; ++e) v *= ry;
-                    for (int e = 0; e < ez; ++e) v *= rz;
-                    if (fs[s]) accF += v;
-                    else accS += v;
+        T accS[(168 - 4 + 31) / 32], accF[(168 - 4 + 31) / 32];
+#pragma unroll
+        for (int q = 0; q < (168 - 4 + 31) / 32; ++q) accS[q] = accF[q] = T(0);
+        for (int s0 = 0; s0 < count; s0 += 32) {
+            const int m = min(32, count - s0);
+            __syncwarp();
+            if (lane < m) {
+                const T4 r = pf[first + s0 + lane];
+                const T rv[3] = {r.x * inv_st, r.y * inv_st, r.z * inv_st};
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    T v = T(1);
+                    s_pw[wib][a][0][lane] = v;
+                    for (int e = 1; e <= p; ++e) {
+                        v *= rv[a];
+                        s_pw[wib][a][e][lane] = v;
+                    }
+                }
+                const bool fast = fs[first + s0 + lane] != 0;
+                s_w[wib][0][lane] = fast ? T(0) : r.w;
+                s_w[wib][1][lane] = fast ? r.w : T(0);
+            }
+            __syncwarp();
+#pragma unroll
+            for (int q = 0; q < (168 - 4 + 31) / 32; ++q) {
+                const int k = 4 + lane + 32 * q;
+                if (4 + 32 * q < nc && k < nc) {
+                    const int ex = s_e[0][k], ey = s_e[1][k], ez = s_e[2][k];
+                    T aS = 0, aF = 0;
+                    for (int i = 0; i < m; ++i) {
+                        const T v = s_pw[wib][0][ex][i] * s_pw[wib][1][ey][i] * s_pw[wib][2][ez][i];
+                        aS += s_w[wib][0][i] * v;
+                        aF += s_w[wib][1][i] * v;
+                    }
+                    accS[q] += aS;
+                    accF[q] += aF;
                 }
             }
-            M[((size_t)c * 2 + 0) * ncp + k] = accS;
-            M[((size_t)c * 2 + 1) * ncp + k] = accF;
+        }
+#pragma unroll
+        for (int q = 0; q < (168 - 4 + 31) / 32; ++q) {
+            const int k = 4 + lane + 32 * q;
+            if (k < ncp) {
+                M[((size_t)c * 2 + 0) * ncp + k] = k < nc ? accS[q] : T(0);
+                M[((size_t)c * 2 + 1) * ncp + k] = k < nc ? accF[q] : T(0);
+            }
         }
     }
 }
@@ -229,53 +277,87 @@ __constant__ float c_binom_f[9][9] = {
     {1, 6, 15, 20, 15, 6, 1, 0, 0},    {1, 7, 21, 35, 35, 21, 7, 1, 0},    {1, 8, 28, 56, 70, 56, 28, 8, 1}};
 
 // M2M for the parents of one level, normalised: with d = z_child - z_parent = (+-s/4)^3 and
-// s_child = s/2,  M~_P^n = sum_children sum_{k <= n} C(n,k) (+-1/4)^(n-k) 2^-|k| M~_c^k.
-// Thread per (cell, class, n); |n| <= 1 in float64 (M01), every order also in T (M).
+// s_child = s/2,  M~_P^n = sum_{k <= n} C(n,k) 2^-(2|n-k| + |k|) sum_children (+-1)^(n-k) M~_c^k.
+// Warp per parent cell, lanes over the coefficients n; |n| <= 1 in float64 (M01), every order also
+// in T (M).  Only the terms k <= n (componentwise) are visited; multi-index tables live in shared
+// memory because the lanes index them with different n.
+constexpr int kM2MWarps = 2;   // warps per block of the M2M/L2L level kernels
+
 template <class T>
-__global__ void m2m_level(TreeView t, int lb, int le, int p, int nc, int ncp, T *M, double *M01)
+__global__ void __launch_bounds__(32 * kM2MWarps) m2m_level(TreeView t, int lb, int le, int p, int nc, int ncp, T *M,
+                                                            double *M01)
 {
-    const int64_t total = (int64_t)(le - lb) * 2 * nc;
-    for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < total; w += (int64_t)gridDim.x * blockDim.x) {
-        const int c = lb + (int)(w / (2 * nc));
-        const int cls = (int)((w / nc) % 2);
-        const int n = (int)(w % nc);
+    extern __shared__ __align__(16) unsigned char m2m_smem[];
+    T *s_mc = reinterpret_cast<T *>(m2m_smem) + (size_t)(threadIdx.x >> 5) * 8 * 2 * ncp;   // children's M, this warp
+    __shared__ uint8_t s_lookup[9 * 9 * 9];
+    __shared__ uint8_t s_e[3][168];
+    __shared__ float s_binom[9][9];
+    for (int k = threadIdx.x; k < 729; k += blockDim.x) s_lookup[k] = c_mi_lookup[k];
+    for (int k = threadIdx.x; k < 168; k += blockDim.x) {
+        s_e[0][k] = k < nc ? c_mi_x[k] : 0;
+        s_e[1][k] = k < nc ? c_mi_y[k] : 0;
+        s_e[2][k] = k < nc ? c_mi_z[k] : 0;
+    }
+    for (int k = threadIdx.x; k < 81; k += blockDim.x) s_binom[k / 9][k % 9] = c_binom_f[k / 9][k % 9];
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (int c = lb + warp; c < le; c += nwarps) {
         const int nch = t.nchild[c];
         if (nch == 0) continue;
-        const int nx = c_mi_x[n], ny = c_mi_y[n], nz = c_mi_z[n];
-        if (n < 4) {
+        const int cf = t.child_first[c];
+        // bit q of negx: child q lies on the negative side of the parent centre along x
+        uint32_t negx = 0, negy = 0, negz = 0;
+        for (int q = 0; q < nch; ++q) {
+            negx |= (uint32_t)!(t.cx[cf + q] & 1u) << q;
+            negy |= (uint32_t)!(t.cy[cf + q] & 1u) << q;
+            negz |= (uint32_t)!(t.cz[cf + q] & 1u) << q;
+        }
+        // the children are consecutive cells: their moments form one contiguous block
+        __syncwarp();
+        for (int k = lane; k < nch * 2 * ncp; k += 32) s_mc[k] = M[(size_t)cf * 2 * ncp + k];
+        __syncwarp();
+        if (lane < 8) {
+            const int cls = lane >> 2, n = lane & 3;
+            const uint32_t negn = n == 1 ? negx : (n == 2 ? negy : negz);
             double acc = 0.0;
             for (int q = 0; q < nch; ++q) {
-                const int ch = t.child_first[c] + q;
-                const double *Mc = M01 + ((size_t)ch * 2 + cls) * 4;
+                const double *Mc = M01 + ((size_t)(cf + q) * 2 + cls) * 4;
                 double v = Mc[n];
-                if (n > 0) {
-                    const uint32_t cc = nx ? t.cx[ch] : (ny ? t.cy[ch] : t.cz[ch]);
-                    v = 0.5 * v + ((cc & 1u) ? 0.25 : -0.25) * Mc[0];
-                }
+                if (n > 0) v = 0.5 * v + (((negn >> q) & 1u) ? -0.25 : 0.25) * Mc[0];
                 acc += v;
             }
             M01[((size_t)c * 2 + cls) * 4 + n] = acc;
             M[((size_t)c * 2 + cls) * ncp + n] = (T)acc;
-            continue;
         }
-        const int ncn = ncoef_dev(nx + ny + nz);
-        T acc = 0;
-        for (int q = 0; q < nch; ++q) {
-            const int ch = t.child_first[c] + q;
-            const bool neg_x = !(t.cx[ch] & 1u), neg_y = !(t.cy[ch] & 1u), neg_z = !(t.cz[ch] & 1u);
-            const T *Mc = M + ((size_t)ch * 2 + cls) * ncp;
-            for (int k = 0; k < ncn; ++k) {
-                const int kx = c_mi_x[k], ky = c_mi_y[k], kz = c_mi_z[k];
-                if (kx > nx || ky > ny || kz > nz) continue;
-                const int dx = nx - kx, dy = ny - ky, dz = nz - kz;
-                const bool neg = ((neg_x && (dx & 1)) ^ (neg_y && (dy & 1)) ^ (neg_z && (dz & 1)));
-                // 4^-(|n|-|k|) * 2^-|k| = 2^-(2|n| - |k|)
-                const T scale = (T)pow2f(-(2 * (dx + dy + dz) + (kx + ky + kz)));
-                const T v = (T)(c_binom_f[nx][kx] * c_binom_f[ny][ky] * c_binom_f[nz][kz]) * scale * Mc[k];
-                acc += neg ? -v : v;
+        for (int n = 4 + lane; n < ncp; n += 32) {
+            T accS = 0, accF = 0;
+            if (n < nc) {
+                const int nx = s_e[0][n], ny = s_e[1][n], nz = s_e[2][n], on = nx + ny + nz;
+                for (int kx = 0; kx <= nx; ++kx)
+                    for (int ky = 0; ky <= ny; ++ky)
+                        for (int kz = 0; kz <= nz; ++kz) {
+                            const int k = s_lookup[(kx * 9 + ky) * 9 + kz], ok = kx + ky + kz;
+                            const T coef = (T)(s_binom[nx][kx] * s_binom[ny][ky] * s_binom[nz][kz] *
+                                               pow2f(-(2 * (on - ok) + ok)));
+                            // children whose offset makes (+-1)^(n-k) negative
+                            const uint32_t neg = (((nx - kx) & 1) ? negx : 0u) ^ (((ny - ky) & 1) ? negy : 0u) ^
+                                                 (((nz - kz) & 1) ? negz : 0u);
+                            T sS = 0, sF = 0;
+                            for (int q = 0; q < nch; ++q) {
+                                const T *Mc = s_mc + q * 2 * ncp;
+                                const T vS = Mc[k], vF = Mc[ncp + k];
+                                const bool ng = (neg >> q) & 1u;
+                                sS += ng ? -vS : vS;
+                                sF += ng ? -vF : vF;
+                            }
+                            accS += coef * sS;
+                            accF += coef * sF;
+                        }
             }
+            M[((size_t)c * 2 + 0) * ncp + n] = accS;
+            M[((size_t)c * 2 + 1) * ncp + n] = accF;
         }
-        M[((size_t)c * 2 + cls) * ncp + n] = acc;
     }
 }
 
@@ -315,8 +397,9 @@ struct WalkOut {
     uint2 *front_out;
     M2LBlock *blocks;
     uint2 *p2p;
-    unsigned long long *counters;   // [0] frontier, [1] M2L blocks, [2] P2P pairs A != B, [3] M2L pairs,
+    unsigned long long *counters;   // [1] M2L blocks, [2] P2P pairs A != B, [3] M2L pairs,
                                     // [4] self P2P pairs (A, A), stored from the end of the P2P buffer
+    unsigned long long *front_ctr;  // length of front_out
     unsigned long long cap_front, cap_blocks, cap_p2p;
 };
 
@@ -338,8 +421,12 @@ __device__ __forceinline__ unsigned long long warp_reserve(unsigned long long *c
     return base + (incl - cnt);
 }
 
-__global__ void walk_step(TreeView t, MacParams mp, const uint2 *front_in, int n_in, WalkOut o)
+// One step of the dual walk.  The input length is read on the device (it is the previous step's
+// output counter), so that all steps can be queued without waiting for the host.
+__global__ void walk_step(TreeView t, MacParams mp, const uint2 *front_in, const unsigned long long *n_in_ctr, WalkOut o)
 {
+    const unsigned long long n_in_raw = *n_in_ctr;
+    const int64_t n_in = (int64_t)(n_in_raw < o.cap_front ? n_in_raw : o.cap_front);
     // whole warps iterate together so that the counters can be reserved per warp
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t w0 = (int64_t)blockIdx.x * blockDim.x; w0 < n_in; w0 += stride) {
@@ -376,7 +463,7 @@ __global__ void walk_step(TreeView t, MacParams mp, const uint2 *front_in, int n
                     }
                 }
         }
-        unsigned long long fb = warp_reserve(o.counters + 0, n_front);
+        unsigned long long fb = warp_reserve(o.front_ctr, n_front);
         unsigned long long pb = warp_reserve(o.counters + 2, n_p2p);
         unsigned long long sb = warp_reserve(o.counters + 4, n_self);
         const unsigned long long bb = warp_reserve(o.counters + 1, mask ? 1u : 0u);
@@ -405,32 +492,51 @@ __global__ void walk_step(TreeView t, MacParams mp, const uint2 *front_in, int n
 }
 
 // ------------------------------------------------------------------ L2L (one level), normalised
-// L~_c^n += sum_{k >= n} L~_P^k (+-1/4)^(k-n) / (k-n)! * 2^-(|n|+1).  Thread per (cell, class, n).
+// L~_c^n += sum_{d} L~_P^(n+d) (+-1)^d 2^-(2|d| + |n| + 1) / d!  over |d| <= p - |n|.
+// Warp per cell of the level, lanes over the coefficients n, both classes.  d runs through the
+// multi-indices in their table order (the same d for every lane at each step); the index of n + d
+// comes from a lookup table in shared memory.
 template <class T>
-__global__ void l2l_level(TreeView t, int lb, int le, int p, int nc, int ncp, int ncls, T *L)
+__global__ void __launch_bounds__(32 * kM2MWarps) l2l_level(TreeView t, int lb, int le, int p, int nc, int ncp, int ncls,
+                                                            T *L)
 {
-    const int64_t total = (int64_t)(le - lb) * ncls * nc;
-    for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < total; w += (int64_t)gridDim.x * blockDim.x) {
-        const int c = lb + (int)(w / (ncls * nc));
-        const int cls = (int)((w / nc) % ncls);
-        const int n = (int)(w % nc);
+    extern __shared__ __align__(16) unsigned char l2l_smem[];
+    T *s_lp = reinterpret_cast<T *>(l2l_smem) + (size_t)(threadIdx.x >> 5) * 2 * ncp;   // parent's L, this warp
+    __shared__ uint8_t s_lookup[9 * 9 * 9];
+    __shared__ uint8_t s_e[3][168];
+    for (int k = threadIdx.x; k < 729; k += blockDim.x) s_lookup[k] = c_mi_lookup[k];
+    for (int k = threadIdx.x; k < 168; k += blockDim.x) {
+        s_e[0][k] = k < nc ? c_mi_x[k] : 0;
+        s_e[1][k] = k < nc ? c_mi_y[k] : 0;
+        s_e[2][k] = k < nc ? c_mi_z[k] : 0;
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (int c = lb + warp; c < le; c += nwarps) {
         const int par = t.parent[c];
         if (par < 0) continue;
         const bool neg_x = !(t.cx[c] & 1u), neg_y = !(t.cy[c] & 1u), neg_z = !(t.cz[c] & 1u);
-        const int nx = c_mi_x[n], ny = c_mi_y[n], nz = c_mi_z[n];
-        const T *Lp = L + ((size_t)par * 2 + cls) * ncp;
-        T acc = 0;
-        for (int k = 0; k < nc; ++k) {
-            const int kx = c_mi_x[k], ky = c_mi_y[k], kz = c_mi_z[k];
-            if (kx < nx || ky < ny || kz < nz) continue;
-            const int dx = kx - nx, dy = ky - ny, dz = kz - nz;
-            const bool neg = ((neg_x && (dx & 1)) ^ (neg_y && (dy & 1)) ^ (neg_z && (dz & 1)));
-            const T coef = inv_fact_t<T>(c_mi_lookup[(dx * 9 + dy) * 9 + dz]) *
-                           (T)ldexpf(1.0f, -(2 * (dx + dy + dz) + nx + ny + nz + 1));
-            const T v = Lp[k] * coef;
-            acc += neg ? -v : v;
+        __syncwarp();
+        for (int k = lane; k < ncls * ncp; k += 32) s_lp[k] = L[(size_t)par * 2 * ncp + k];
+        __syncwarp();
+        const T *Lp = s_lp;
+        for (int n = lane; n < nc; n += 32) {
+            const int nx = s_e[0][n], ny = s_e[1][n], nz = s_e[2][n], on = nx + ny + nz;
+            const int nd = ncoef_dev(p - on);   // multi-indices d with |d| <= p - |n|
+            T acc0 = 0, acc1 = 0;
+            for (int d = 0; d < nd; ++d) {
+                const int dx = c_mi_x[d], dy = c_mi_y[d], dz = c_mi_z[d];
+                const int k = s_lookup[((nx + dx) * 9 + ny + dy) * 9 + nz + dz];
+                const bool neg = (neg_x && (dx & 1)) ^ (neg_y && (dy & 1)) ^ (neg_z && (dz & 1));
+                const T coef = inv_fact_t<T>(d) * (T)pow2f(-(2 * (dx + dy + dz) + on + 1));
+                const T cs = neg ? -coef : coef;
+                acc0 += Lp[k] * cs;
+                if (ncls > 1) acc1 += Lp[ncp + k] * cs;
+            }
+            L[((size_t)c * 2 + 0) * ncp + n] += acc0;
+            if (ncls > 1) L[((size_t)c * 2 + 1) * ncp + n] += acc1;
         }
-        L[((size_t)c * 2 + cls) * ncp + n] += acc;
     }
 }
 
@@ -560,6 +666,14 @@ tg_status direct_eval(tg_ctx *c, int64_t n, const double *pos, const double *mas
 }
 
 // ------------------------------------------------------------------ orchestration
+__global__ void walk_init(uint2 *front, unsigned long long *front_ctr)
+{
+    front[0] = make_uint2(0, 0);
+    front_ctr[0] = 1;
+}
+
+constexpr int kWalkMaxSteps = 24;   // a step descends one level; the octree has at most 22 levels
+
 static tg_status run_walk(tg_ctx *c, const TreeView &t, int64_t *n_blocks, int64_t *n_m2l, int64_t *n_p2p,
                           int64_t *n_self)
 {
@@ -582,10 +696,11 @@ static tg_status run_walk(tg_ctx *c, const TreeView &t, int64_t *n_blocks, int64
         unsigned long long *ctr;
         if ((st = ensure_t(c, B_FRONT0, cap_front, &f0)) || (st = ensure_t(c, B_FRONT1, cap_front, &f1)) ||
             (st = ensure_t(c, B_M2L, cap_blocks, &blocks)) || (st = ensure_t(c, B_P2P, cap_p2p, &p2p)) ||
-            (st = ensure_t(c, B_WALK_CNT, 8, &ctr)))
+            (st = ensure_t(c, B_WALK_CNT, 8 + kWalkMaxSteps + 1, &ctr)))
             return st;
-        cudaMemsetAsync(ctr, 0, 8 * sizeof(unsigned long long), c->stream);
-        unsigned long long n_in = 0, tot_blocks = 0, tot_p2p = 0, tot_pairs = 0, tot_self = 0;
+        unsigned long long *front_ctr = ctr + 8;   // front_ctr[s]: input length of step s
+        cudaMemsetAsync(ctr, 0, (8 + kWalkMaxSteps + 1) * sizeof(unsigned long long), c->stream);
+        unsigned long long tot_blocks = 0, tot_p2p = 0, tot_pairs = 0, tot_self = 0;
         c->p2p_cap = (int64_t)cap_p2p;
         if (t.ncell == 1) {
             // the root is a leaf: one self P2P pair
@@ -597,35 +712,32 @@ static tg_status run_walk(tg_ctx *c, const TreeView &t, int64_t *n_blocks, int64
             *n_self = 1;
             return cuda_check(c, cudaStreamSynchronize(c->stream), "walk");
         }
-        const uint2 root = make_uint2(0, 0);
-        cudaMemcpyAsync(f0, &root, sizeof(uint2), cudaMemcpyHostToDevice, c->stream);
-        n_in = 1;
-        bool overflow = false;
-        size_t need_front = 0;
-        while (n_in > 0) {
-            cudaMemsetAsync(ctr, 0, sizeof(unsigned long long), c->stream);   // frontier counter only
-            WalkOut o{f1, blocks, p2p, ctr, cap_front, cap_blocks, cap_p2p};
-            {
-                ProfScope ps_(c, TG_K_WALK);
-                walk_step<<<grid_for((int64_t)n_in, 128), 128, 0, c->stream>>>(t, mp, f0, (int)n_in, o);
-            }
-            cudaMemcpyAsync(c->h_pinned, ctr, 5 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, c->stream);
-            cudaError_t e = cudaStreamSynchronize(c->stream);
-            if (e != cudaSuccess) return cuda_check(c, e, "walk step");
-            const unsigned long long *h = reinterpret_cast<const unsigned long long *>(c->h_pinned);
-            n_in = h[0];
-            tot_blocks = h[1];
-            tot_p2p = h[2];
-            tot_pairs = h[3];
-            tot_self = h[4];
-            if (n_in > cap_front || tot_blocks > cap_blocks || tot_p2p + tot_self > cap_p2p) {
-                overflow = true;
-                need_front = n_in > need_front ? n_in : need_front;
-                break;
-            }
-            std::swap(f0, f1);
-            std::swap(c->buf[B_FRONT0], c->buf[B_FRONT1]);
+        {
+            ProfScope ps_(c, TG_K_WALK);
+            walk_init<<<1, 1, 0, c->stream>>>(f0, front_ctr);
         }
+        // every frontier pair holds a cell with children, at the level of the step: the walk ends
+        // after at most (levels - 1) steps; all of them are queued, then the counters read once
+        const int nsteps = std::min<int>(kWalkMaxSteps, std::max<int>(1, (int)c->level_begin.size() - 1));
+        const int grid = c->num_sms * 4;
+        for (int s = 0; s < nsteps; ++s) {
+            WalkOut o{(s & 1) ? f0 : f1, blocks, p2p, ctr, front_ctr + s + 1, cap_front, cap_blocks, cap_p2p};
+            ProfScope ps_(c, TG_K_WALK);
+            walk_step<<<grid, 128, 0, c->stream>>>(t, mp, (s & 1) ? f1 : f0, front_ctr + s, o);
+        }
+        cudaMemcpyAsync(c->h_pinned, ctr, (8 + nsteps + 1) * sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                        c->stream);
+        cudaError_t e = cudaStreamSynchronize(c->stream);
+        if (e != cudaSuccess) return cuda_check(c, e, "walk");
+        const unsigned long long *h = reinterpret_cast<const unsigned long long *>(c->h_pinned);
+        tot_blocks = h[1];
+        tot_p2p = h[2];
+        tot_pairs = h[3];
+        tot_self = h[4];
+        size_t need_front = 0;
+        for (int s = 1; s <= nsteps; ++s) need_front = std::max<size_t>(need_front, h[8 + s]);
+        if (h[8 + nsteps] != 0) return set_err(c, TG_ERR_CAPACITY, "walk frontier not empty after %d steps", nsteps);
+        const bool overflow = need_front > cap_front || tot_blocks > cap_blocks || tot_p2p + tot_self > cap_p2p;
         if (!overflow) {
             *n_blocks = (int64_t)tot_blocks;
             *n_m2l = (int64_t)tot_pairs;
@@ -758,14 +870,15 @@ static tg_status eval_typed(tg_ctx *c, int n, int ncell, const TreeView &t, cons
     }
     {
         ProfScope ps_(c, TG_K_UP);
-        p2m_leaves<T, T4><<<grid_for((int64_t)ncell * 32, 256), 256, 0, c->stream>>>(t, d_geom, xs, ys, zs, ms, fs, pf, p, nc,
+        p2m_leaves<T, T4><<<grid_for((int64_t)ncell * 32, 128), 128, 0, c->stream>>>(t, d_geom, xs, ys, zs, ms, fs, pf, p, nc,
                                                                                      ncp, M, M01);
     }
     const int nlev = (int)c->level_begin.size() - 1;
     for (int l = nlev - 2; l >= 0; --l) {
         const int lb = c->level_begin[l], le = c->level_begin[l + 1];
         ProfScope ps_(c, TG_K_UP);
-        m2m_level<T><<<grid_for((int64_t)(le - lb) * 2 * nc, 128), 128, 0, c->stream>>>(t, lb, le, p, nc, ncp, M, M01);
+        m2m_level<T><<<grid_for((int64_t)(le - lb) * 32, 32 * kM2MWarps), 32 * kM2MWarps,
+                       kM2MWarps * 8 * 2 * ncp * sizeof(T), c->stream>>>(t, lb, le, p, nc, ncp, M, M01);
     }
     {
         ProfScope ps_(c, TG_K_UP);
@@ -778,7 +891,8 @@ static tg_status eval_typed(tg_ctx *c, int n, int ncell, const TreeView &t, cons
     for (int l = 1; l < nlev; ++l) {
         const int lb = c->level_begin[l], le = c->level_begin[l + 1];
         ProfScope ps_(c, TG_K_DOWN);
-        l2l_level<T><<<grid_for((int64_t)(le - lb) * ncls * nc, 128), 128, 0, c->stream>>>(t, lb, le, p, nc, ncp, ncls, L);
+        l2l_level<T><<<grid_for((int64_t)(le - lb) * 32, 32 * kM2MWarps), 32 * kM2MWarps,
+                       kM2MWarps * 2 * ncp * sizeof(T), c->stream>>>(t, lb, le, p, nc, ncp, ncls, L);
     }
     {
         ProfScope ps_(c, TG_K_DOWN);

@@ -14,8 +14,8 @@
 // With slow/fast classes the leaves hold their slow particles first.  Slow rows meet every
 // column; fast rows meet only the owner's slow columns, so fast-fast pairs are never computed
 // (a kickS2F feels the slow masses only).  Within a batch the partners whose cube lies closer
-// than eps to the owner's come first, and chunks made only of the other partners' rows skip the
-// softened branch of the pair kernel.
+// than eps to the owner's come first; chunks made only of the other partners' rows need no softening
+// test, the others take the pair value at max(r, eps) and correct the rare pairs with r < eps.
 #pragma once
 #include "p2p_tile.cuh"
 
@@ -58,13 +58,18 @@ struct OwnerBatch {
     int inc[2][32];    // inclusive row counts over slots: [0] slow rows, [1] fast rows
 };
 
+// Columns are staged as [slow | pad to 8 | fast | pad to 8]; the pads are massless particles far away
+// (on the other side of the origin from the padding rows), so every batch of 8 columns is full.
+constexpr int kOwnCols = kMaxNcrit + 16;
+
 struct OwnerShared {
-    float4 q[8][kMaxNcrit];       // owner's particles (columns), per warp
-    float acc[8][kMaxNcrit][4];   // owner's reaction sums (ax, ay, az, phi), per warp
+    float4 q[8][kOwnCols];       // owner's particles (columns), per warp
+    float acc[8][kOwnCols][4];   // owner's reaction sums (ax, ay, az, phi), per warp
     OwnerBatch b[8];
 };
 
-// Rows i0 .. i0 + 32*ROWS of one phase (0: slow rows, 1: fast rows) against the first ncol columns.
+// Rows i0 .. i0 + 32*ROWS of one phase (0: slow rows, 1: fast rows) against the first ncol staged
+// columns (a multiple of 8).
 template <int KERNEL, int ROWS, bool NEAR>
 __device__ __noinline__ void owner_rows(const float4 *__restrict__ pf, const OwnerBatch *ob, int phase, int i0, int nrows,
                                         const float4 *sq, float (*sacc)[4], int ncol, float eps, double *acc4, int n,
@@ -97,37 +102,75 @@ __device__ __noinline__ void owner_rows(const float4 *__restrict__ pf, const Own
         }
         ra[r][0] = ra[r][1] = ra[r][2] = ra[r][3] = 0.f;
     }
+    // Wendland C2 and a partner closer than eps: the pair value is first taken at max(r, eps), where
+    // it equals the Newtonian one, and pairs with r < eps are corrected after the batch (rare).
+    constexpr bool CLAMP = NEAR && KERNEL == TG_KERNEL_WENDLAND_C2;
     // columns in batches of 8; lane l visits column c ^ ((l >> 2) & 7) of a batch (see p2p_pair_f32)
     const int cperm = (lane >> 2) & 7;
     for (int j0 = 0; j0 < ncol; j0 += 8) {
         float col[32];
+        bool close = false;
 #pragma unroll
         for (int c = 0; c < 8; ++c) {
-            const int j = j0 + (c ^ cperm);
+            const float4 q = sq[j0 + (c ^ cperm)];
             float cx = 0.f, cy = 0.f, cz = 0.f, cp = 0.f;
-            if (j < ncol) {
-                const float4 q = sq[j];
 #pragma unroll
-                for (int r = 0; r < ROWS; ++r) {
-                    const float dx = q.x - p[r].x, dy = q.y - p[r].y, dz = q.z - p[r].z;
-                    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                    float gk, ph;
-                    pair_kernel_f32<KERNEL, NEAR>(r2, eps, eps2, inv_eps, inv_eps3, gk, ph);
-                    const float mq = q.w * gk, mp = p[r].w * gk;
-                    ra[r][0] = fmaf(mq, dx, ra[r][0]);
-                    ra[r][1] = fmaf(mq, dy, ra[r][1]);
-                    ra[r][2] = fmaf(mq, dz, ra[r][2]);
-                    ra[r][3] = fmaf(q.w, ph, ra[r][3]);
-                    cx = fmaf(-mp, dx, cx);
-                    cy = fmaf(-mp, dy, cy);
-                    cz = fmaf(-mp, dz, cz);
-                    cp = fmaf(p[r].w, ph, cp);
+            for (int r = 0; r < ROWS; ++r) {
+                const float dx = q.x - p[r].x, dy = q.y - p[r].y, dz = q.z - p[r].z;
+                const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                float gk, ph;
+                if (CLAMP) {
+                    close |= r2 < eps2;
+                    const float ri = rsqrtf(fmaxf(r2, eps2));
+                    ph = -ri;
+                    gk = ri * ri * ri;
+                } else {
+                    pair_kernel_f32<KERNEL, false>(r2, eps, eps2, inv_eps, inv_eps3, gk, ph);
                 }
+                const float mq = q.w * gk, mp = p[r].w * gk;
+                ra[r][0] = fmaf(mq, dx, ra[r][0]);
+                ra[r][1] = fmaf(mq, dy, ra[r][1]);
+                ra[r][2] = fmaf(mq, dz, ra[r][2]);
+                ra[r][3] = fmaf(q.w, ph, ra[r][3]);
+                cx = fmaf(-mp, dx, cx);
+                cy = fmaf(-mp, dy, cy);
+                cz = fmaf(-mp, dz, cz);
+                cp = fmaf(p[r].w, ph, cp);
             }
             col[4 * c + 0] = cx;
             col[4 * c + 1] = cy;
             col[4 * c + 2] = cz;
             col[4 * c + 3] = cp;
+        }
+        if (CLAMP && __any_sync(0xffffffffu, close)) {
+            // exact softened value minus the clamped one, for the pairs with r < eps; rows in registers,
+            // columns straight into the shared sums (before the batch's own column sums are added)
+#pragma unroll 1
+            for (int c = 0; c < 8; ++c) {
+                const int j = j0 + (c ^ cperm);
+                const float4 q = sq[j];
+#pragma unroll
+                for (int r = 0; r < ROWS; ++r) {
+                    const float dx = q.x - p[r].x, dy = q.y - p[r].y, dz = q.z - p[r].z;
+                    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                    if (r2 < eps2) {
+                        const float ri = rsqrtf(eps2);
+                        float g, ph;
+                        pair_kernel<float, TG_KERNEL_WENDLAND_C2>(r2, eps, eps2, inv_eps, inv_eps3, g, ph);
+                        const float dg = g - ri * ri * ri, dph = ph + ri;
+                        const float mq = q.w * dg, mp = p[r].w * dg;
+                        ra[r][0] = fmaf(mq, dx, ra[r][0]);
+                        ra[r][1] = fmaf(mq, dy, ra[r][1]);
+                        ra[r][2] = fmaf(mq, dz, ra[r][2]);
+                        ra[r][3] = fmaf(q.w, dph, ra[r][3]);
+                        atomicAdd(&sacc[j][0], -mp * dx);
+                        atomicAdd(&sacc[j][1], -mp * dy);
+                        atomicAdd(&sacc[j][2], -mp * dz);
+                        atomicAdd(&sacc[j][3], p[r].w * dph);
+                    }
+                }
+            }
+            __syncwarp();
         }
 #pragma unroll
         for (int h = 16; h >= 4; h >>= 1)
@@ -144,8 +187,7 @@ __device__ __noinline__ void owner_rows(const float4 *__restrict__ pf, const Own
             }
         }
         // lane l holds column j0 + l/4, component l%4; each (column, component) has one lane
-        const int cj = lane >> 2, comp = lane & 3;
-        if (j0 + cj < ncol) sacc[j0 + cj][comp] += col[0];
+        sacc[j0 + (lane >> 2)][lane & 3] += col[0];
     }
 #pragma unroll
     for (int r = 0; r < ROWS; ++r)
@@ -248,26 +290,31 @@ __global__ void __launch_bounds__(256, 2) p2p_owner_f32(TreeView t, int log2L, c
             for (int jc = 0; jc < nb; jc += kMaxNcrit) {
                 const int nbc = min(kMaxNcrit, nb - jc);
                 const int nsc = max(0, min(sB - jc, nbc));   // slow columns of this chunk (slow-first leaf)
+                const int ns8 = (nsc + 7) & ~7, nf = nbc - nsc, nt8 = ns8 + ((nf + 7) & ~7);
                 __syncwarp();
-                for (int j = lane; j < nbc; j += 32) {
-                    sq[j] = pf[fb + jc + j];
+                for (int j = lane; j < nt8; j += 32) {
+                    const int src = j < nsc ? j : (j >= ns8 && j < ns8 + nf ? nsc + j - ns8 : -1);
+                    sq[j] = src >= 0 ? pf[fb + jc + src] : make_float4(-1e8f, -1e8f, -1e8f, 0.f);
                     sacc[j][0] = sacc[j][1] = sacc[j][2] = sacc[j][3] = 0.f;
                 }
                 __syncwarp();
                 for (int i0 = 0; i0 < Ts; i0 += 32 * ROWS) {
-                    if (i0 < nearS) owner_rows<KERNEL, ROWS, true>(pf, ob, 0, i0, Ts, sq, sacc, nbc, eps, acc4, n, lane);
-                    else owner_rows<KERNEL, ROWS, false>(pf, ob, 0, i0, Ts, sq, sacc, nbc, eps, acc4, n, lane);
+                    if (i0 < nearS) owner_rows<KERNEL, ROWS, true>(pf, ob, 0, i0, Ts, sq, sacc, nt8, eps, acc4, n, lane);
+                    else owner_rows<KERNEL, ROWS, false>(pf, ob, 0, i0, Ts, sq, sacc, nt8, eps, acc4, n, lane);
                 }
                 if (nsc > 0)
                     for (int i0 = 0; i0 < Tf; i0 += 32 * ROWS) {
-                        if (i0 < nearF) owner_rows<KERNEL, ROWS, true>(pf, ob, 1, i0, Tf, sq, sacc, nsc, eps, acc4, n, lane);
-                        else owner_rows<KERNEL, ROWS, false>(pf, ob, 1, i0, Tf, sq, sacc, nsc, eps, acc4, n, lane);
+                        if (i0 < nearF) owner_rows<KERNEL, ROWS, true>(pf, ob, 1, i0, Tf, sq, sacc, ns8, eps, acc4, n, lane);
+                        else owner_rows<KERNEL, ROWS, false>(pf, ob, 1, i0, Tf, sq, sacc, ns8, eps, acc4, n, lane);
                     }
                 __syncwarp();
-                for (int j = lane; j < nbc; j += 32)
+                for (int j = lane; j < nt8; j += 32) {
+                    const int src = j < nsc ? j : (j >= ns8 && j < ns8 + nf ? nsc + j - ns8 : -1);
+                    if (src >= 0)
 #pragma unroll
-                    for (int comp = 0; comp < 4; ++comp)
-                        atomicAdd(&acc4[(size_t)comp * n + fb + jc + j], f2d_exact(sacc[j][comp]));
+                        for (int comp = 0; comp < 4; ++comp)
+                            atomicAdd(&acc4[(size_t)comp * n + fb + jc + src], f2d_exact(sacc[j][comp]));
+                }
             }
         }
     }

@@ -528,62 +528,71 @@ __device__ __forceinline__ int digit_lower_bound(const uint64_t *keys, int s, in
     return s;
 }
 
+// Child boundaries of a cell that splits: warp per cell, lane d (1..7) finds the first particle whose
+// digit at the child level is >= d; lane 0 holds the cell start and lanes 8..31 its end, so that child
+// d (lane d < 8) spans [b_d, b_{d+1}).  The seven binary searches run side by side.
+__device__ __forceinline__ int child_bound(const uint64_t *keys, int s, int e, int l, int lane)
+{
+    if (lane == 0) return s;
+    if (lane >= 8) return e;
+    return digit_lower_bound(keys, s, e, l, lane);
+}
+
 __global__ void oct_count(const uint64_t *keys, int lb, int le, const uint8_t *level, const int32_t *first,
                           const int32_t *count, int n_crit, int max_level, uint32_t *cnt)
 {
-    int t = blockIdx.x * blockDim.x + threadIdx.x;
-    int cidx = lb + t;
-    if (cidx >= le) return;
+    const int t = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+    const int cidx = lb + t;
+    if (cidx >= le) return;   // whole warp
     if (count[cidx] <= n_crit || level[cidx] >= max_level) {
-        cnt[t] = 0;
+        if (lane == 0) cnt[t] = 0;
         return;
     }
     const int l = level[cidx] + 1, s = first[cidx], e = s + count[cidx];
-    int nch = 0, prev = s;
-    for (int d = 1; d <= 8; ++d) {
-        int b = d < 8 ? digit_lower_bound(keys, prev, e, l, d) : e;
-        if (b > prev) ++nch;
-        prev = b;
-    }
-    cnt[t] = nch;
+    const int b = child_bound(keys, s, e, l, lane);
+    const int bn = __shfl_down_sync(0xffffffffu, b, 1);
+    const unsigned m = __ballot_sync(0xffffffffu, lane < 8 && bn > b);
+    if (lane == 0) cnt[t] = __popc(m);
 }
-
 __global__ void oct_emit(const uint64_t *keys, int lb, int le, uint8_t *level, uint32_t *cx, uint32_t *cy,
                          uint32_t *cz, int32_t *first, int32_t *count, int32_t *child_first, int32_t *parent,
                          uint8_t *nchild, const uint32_t *off, const uint32_t *cnt)
 {
-    int t = blockIdx.x * blockDim.x + threadIdx.x;
-    int cidx = lb + t;
-    if (cidx >= le) return;
+    const int t = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+    const int cidx = lb + t;
+    if (cidx >= le) return;   // whole warp
     const int nch = cnt[t];
-    nchild[cidx] = (uint8_t)nch;
     if (nch == 0) {
-        child_first[cidx] = -1;
+        if (lane == 0) {
+            nchild[cidx] = 0;
+            child_first[cidx] = -1;
+        }
         return;
     }
     const int base = le + (int)off[t];
-    child_first[cidx] = base;
-    const int l = level[cidx] + 1, s0 = first[cidx], e = s0 + count[cidx];
-    int k = 0, prev = s0;
-    for (int d = 1; d <= 8; ++d) {
-        int b = d < 8 ? digit_lower_bound(keys, prev, e, l, d) : e;
-        if (b > prev) {
-            const int digit = d - 1, ch = base + k;
-            level[ch] = (uint8_t)l;
-            cx[ch] = 2u * cx[cidx] + ((digit >> 2) & 1);
-            cy[ch] = 2u * cy[cidx] + ((digit >> 1) & 1);
-            cz[ch] = 2u * cz[cidx] + (digit & 1);
-            first[ch] = prev;
-            count[ch] = b - prev;
-            parent[ch] = cidx;
-            nchild[ch] = 0;
-            child_first[ch] = -1;
-            ++k;
-        }
-        prev = b;
+    const int l = level[cidx] + 1, s = first[cidx], e = s + count[cidx];
+    const uint32_t px = cx[cidx], py = cy[cidx], pz = cz[cidx];
+    const int b = child_bound(keys, s, e, l, lane);
+    const int bn = __shfl_down_sync(0xffffffffu, b, 1);
+    const bool nonempty = lane < 8 && bn > b;
+    const unsigned m = __ballot_sync(0xffffffffu, nonempty);
+    if (nonempty) {
+        const int digit = lane, ch = base + __popc(m & ((1u << lane) - 1u));
+        level[ch] = (uint8_t)l;
+        cx[ch] = 2u * px + ((digit >> 2) & 1);
+        cy[ch] = 2u * py + ((digit >> 1) & 1);
+        cz[ch] = 2u * pz + (digit & 1);
+        first[ch] = b;
+        count[ch] = bn - b;
+        parent[ch] = cidx;
+        nchild[ch] = 0;
+        child_first[ch] = -1;
+    }
+    if (lane == 0) {
+        nchild[cidx] = (uint8_t)nch;
+        child_first[cidx] = base;
     }
 }
-
 __global__ void oct_root(int n, uint8_t *level, uint32_t *cx, uint32_t *cy, uint32_t *cz, int32_t *first,
                          int32_t *count, int32_t *child_first, int32_t *parent, uint8_t *nchild)
 {
@@ -630,7 +639,7 @@ tg_status build_octree(tg_ctx *c, int n, int *ncell_out)
         if ((st = ensure_t(c, B_C_TMP0, m, &cnt)) || (st = ensure_t(c, B_C_TMP1, m, &off))) return st;
         {
             ProfScope ps_(c, TG_K_TREE);
-            oct_count<<<(m + 255) / 256, 256, 0, c->stream>>>(keys, lb, le, level, first, count, c->prm.n_crit,
+            oct_count<<<(int)(((int64_t)m * 32 + 255) / 256), 256, 0, c->stream>>>(keys, lb, le, level, first, count, c->prm.n_crit,
                                                              c->prm.max_level, cnt);
         }
         if ((st = exclusive_scan_u32(c, cnt, off, m, d_total))) return st;
@@ -645,7 +654,7 @@ tg_status build_octree(tg_ctx *c, int n, int *ncell_out)
         }
         {
             ProfScope ps_(c, TG_K_TREE);
-            oct_emit<<<(m + 255) / 256, 256, 0, c->stream>>>(keys, lb, le, level, cx, cy, cz, first, count, child_first,
+            oct_emit<<<(int)(((int64_t)m * 32 + 255) / 256), 256, 0, c->stream>>>(keys, lb, le, level, cx, cy, cz, first, count, child_first,
                                                             parent, nchild, off, cnt);
         }
         c->level_begin.push_back(le);

@@ -139,6 +139,23 @@ def test_fmm_fp32_matches_oracle(kind, kernel, p, theta, masked):
     assert np.abs(pot.cpu().numpy() - p_o).max() < FP32_TOL * np.abs(p_o).max()
 
 
+@pytest.mark.parametrize("kind", ["sphere", "clustered"])
+@pytest.mark.parametrize("masked", [False, True])
+def test_fmm_fp32_wide_softening(kind, masked):
+    # eps well above the mean spacing: many particle pairs of neighbouring leaves lie inside the
+    # Wendland kernel's support (Eq. 8), so the softened branch of P2P carries real weight
+    n = 9000
+    pos, _, mass = _case(kind, n)
+    fast = ics.random_fast_mask(n, 17) if masked else None
+    prm = tg.Params(p=5, theta=0.5, eps=0.1, kernel=0, precision=tg.TG_PREC_FP32, n_crit=64)
+    s = tg.Solver(prm)
+    acc, pot = s.fmm_forces(_t(pos), _t(mass), None if fast is None else _t(fast, torch.uint8))
+    a_o, p_o = oracle.fmm(pos, mass, _oprm(prm), fast)
+    r = _rel(acc.cpu().numpy(), a_o, FP32_FLOOR)
+    assert r.max() < FP32_TOL, (r.max(), np.median(r))
+    assert np.abs(pot.cpu().numpy() - p_o).max() < FP32_TOL * np.abs(p_o).max()
+
+
 @pytest.mark.parametrize("precision", [0, 1])
 def test_momentum_conserved_on_gpu(precision):
     n = 20000
