@@ -206,14 +206,24 @@ __global__ void __launch_bounds__(128) p2m_leaves(TreeView t, const Geom *gp, co
                 lo[1][k] += fast ? v : 0.0;
             }
         }
-        double mine = 0.0;   // lane l < 8 keeps class l / 4, component l % 4
+        // reduce-scatter of the 8 sums over the warp: after the stages over lane bits 4, 3, 2 lane l
+        // holds entry (l >> 2) & 7 summed over its group of four lanes, then bits 1, 0 finish the sum
+        double v8[8] = {lo[0][0], lo[0][1], lo[0][2], lo[0][3], lo[1][0], lo[1][1], lo[1][2], lo[1][3]};
 #pragma unroll
-        for (int cls = 0; cls < 2; ++cls)
+        for (int h = 4, d = 16; h >= 1; h >>= 1, d >>= 1) {
+            const bool hi = (lane & d) != 0;
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                const double v = warp_sum(lo[cls][k]);
-                if (lane == cls * 4 + k) mine = v;
+            for (int q = 0; q < h; ++q) {
+                const double send = hi ? v8[q] : v8[q + h];
+                const double keep = hi ? v8[q + h] : v8[q];
+                v8[q] = keep + __shfl_xor_sync(0xffffffffu, send, d);
             }
+        }
+        double mine = v8[0];
+        mine += __shfl_xor_sync(0xffffffffu, mine, 2);
+        mine += __shfl_xor_sync(0xffffffffu, mine, 1);
+        // entry e = cls * 4 + k sits in lanes 4e .. 4e + 3; move it to lane e
+        mine = __shfl_sync(0xffffffffu, mine, 4 * (lane & 7));
         if (lane < 8) {
             const int cls = lane >> 2, k = lane & 3;
             M01[((size_t)c * 2 + cls) * 4 + k] = mine;
@@ -277,18 +287,19 @@ __constant__ float c_binom_f[9][9] = {
     {1, 6, 15, 20, 15, 6, 1, 0, 0},    {1, 7, 21, 35, 35, 21, 7, 1, 0},    {1, 8, 28, 56, 70, 56, 28, 8, 1}};
 
 // M2M for the parents of one level, normalised: with d = z_child - z_parent = (+-s/4)^3 and
-// s_child = s/2,  M~_P^n = sum_{k <= n} C(n,k) 2^-(2|n-k| + |k|) sum_children (+-1)^(n-k) M~_c^k.
-// Warp per parent cell, lanes over the coefficients n; |n| <= 1 in float64 (M01), every order also
-// in T (M).  Only the terms k <= n (componentwise) are visited; multi-index tables live in shared
-// memory because the lanes index them with different n.
-constexpr int kM2MWarps = 2;   // warps per block of the M2M/L2L level kernels
+// s_child = s/2,  M~_P^n = sum_children sum_{k <= n} C(n,k) 2^-(2|n-k| + |k|) (+-1)^(n-k) M~_c^k.
+// Block per parent cell.  |n| <= 1 in float64 (M01, threads 0..7), every order also in T (M).
+// Orders >= 2: lane (n, q) with q = lane % 8 sums the terms k <= n (componentwise) of child q,
+// then the eight children are added with three shuffles.  The children's moments are staged in
+// shared memory; the multi-index tables too, since the lanes index them with different n.
+constexpr int kM2MThreads = 256;
 
 template <class T>
-__global__ void __launch_bounds__(32 * kM2MWarps) m2m_level(TreeView t, int lb, int le, int p, int nc, int ncp, T *M,
-                                                            double *M01)
+__global__ void __launch_bounds__(kM2MThreads) m2m_level(TreeView t, int lb, int le, int p, int nc, int ncp, T *M,
+                                                         double *M01)
 {
     extern __shared__ __align__(16) unsigned char m2m_smem[];
-    T *s_mc = reinterpret_cast<T *>(m2m_smem) + (size_t)(threadIdx.x >> 5) * 8 * 2 * ncp;   // children's M, this warp
+    T *s_mc = reinterpret_cast<T *>(m2m_smem);   // [8 children][2 classes][ncp]
     __shared__ uint8_t s_lookup[9 * 9 * 9];
     __shared__ uint8_t s_e[3][168];
     __shared__ float s_binom[9][9];
@@ -299,64 +310,71 @@ __global__ void __launch_bounds__(32 * kM2MWarps) m2m_level(TreeView t, int lb, 
         s_e[2][k] = k < nc ? c_mi_z[k] : 0;
     }
     for (int k = threadIdx.x; k < 81; k += blockDim.x) s_binom[k / 9][k % 9] = c_binom_f[k / 9][k % 9];
-    __syncthreads();
-    const int lane = threadIdx.x & 31;
-    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nwarps = (gridDim.x * blockDim.x) >> 5;
-    for (int c = lb + warp; c < le; c += nwarps) {
-        const int nch = t.nchild[c];
+    const int lane = threadIdx.x & 31, q = lane & 7;
+    const int sub = threadIdx.x >> 3;   // 0 .. blockDim/8 - 1: which n of the pass
+    const int per_pass = blockDim.x >> 3;
+    for (int c = lb + blockIdx.x; c < le; c += gridDim.x) {
+        const int nch = t.nchild[c];   // uniform over the block
         if (nch == 0) continue;
         const int cf = t.child_first[c];
-        // bit q of negx: child q lies on the negative side of the parent centre along x
-        uint32_t negx = 0, negy = 0, negz = 0;
-        for (int q = 0; q < nch; ++q) {
-            negx |= (uint32_t)!(t.cx[cf + q] & 1u) << q;
-            negy |= (uint32_t)!(t.cy[cf + q] & 1u) << q;
-            negz |= (uint32_t)!(t.cz[cf + q] & 1u) << q;
+        __syncthreads();   // tables ready / previous parent done with s_mc
+        {
+            const int tot = nch * 2 * ncp;
+            const T *src = M + (size_t)cf * 2 * ncp;
+            for (int k = threadIdx.x; k < tot; k += blockDim.x) s_mc[k] = src[k];
         }
-        // the children are consecutive cells: their moments form one contiguous block
-        __syncwarp();
-        for (int k = lane; k < nch * 2 * ncp; k += 32) s_mc[k] = M[(size_t)cf * 2 * ncp + k];
-        __syncwarp();
-        if (lane < 8) {
-            const int cls = lane >> 2, n = lane & 3;
-            const uint32_t negn = n == 1 ? negx : (n == 2 ? negy : negz);
+        __syncthreads();
+        if (threadIdx.x < 8) {
+            const int cls = threadIdx.x >> 2, n = threadIdx.x & 3;
             double acc = 0.0;
-            for (int q = 0; q < nch; ++q) {
-                const double *Mc = M01 + ((size_t)(cf + q) * 2 + cls) * 4;
+            for (int qq = 0; qq < nch; ++qq) {
+                const double *Mc = M01 + ((size_t)(cf + qq) * 2 + cls) * 4;
                 double v = Mc[n];
-                if (n > 0) v = 0.5 * v + (((negn >> q) & 1u) ? -0.25 : 0.25) * Mc[0];
+                if (n > 0) {
+                    const uint32_t cc = n == 1 ? t.cx[cf + qq] : (n == 2 ? t.cy[cf + qq] : t.cz[cf + qq]);
+                    v = 0.5 * v + ((cc & 1u) ? 0.25 : -0.25) * Mc[0];
+                }
                 acc += v;
             }
             M01[((size_t)c * 2 + cls) * 4 + n] = acc;
             M[((size_t)c * 2 + cls) * ncp + n] = (T)acc;
         }
-        for (int n = 4 + lane; n < ncp; n += 32) {
-            T accS = 0, accF = 0;
-            if (n < nc) {
+        // this lane's child: offsets toward the negative side flip the sign of odd powers
+        bool neg_x = false, neg_y = false, neg_z = false;
+        if (q < nch) {
+            neg_x = !(t.cx[cf + q] & 1u);
+            neg_y = !(t.cy[cf + q] & 1u);
+            neg_z = !(t.cz[cf + q] & 1u);
+        }
+        const T *MS = s_mc + q * 2 * ncp, *MF = MS + ncp;
+        for (int n0 = 4; n0 < ncp; n0 += per_pass) {
+            const int n = n0 + sub;
+            T sS = 0, sF = 0;
+            if (n < nc && q < nch) {
                 const int nx = s_e[0][n], ny = s_e[1][n], nz = s_e[2][n], on = nx + ny + nz;
                 for (int kx = 0; kx <= nx; ++kx)
                     for (int ky = 0; ky <= ny; ++ky)
                         for (int kz = 0; kz <= nz; ++kz) {
                             const int k = s_lookup[(kx * 9 + ky) * 9 + kz], ok = kx + ky + kz;
-                            const T coef = (T)(s_binom[nx][kx] * s_binom[ny][ky] * s_binom[nz][kz] *
-                                               pow2f(-(2 * (on - ok) + ok)));
-                            // children whose offset makes (+-1)^(n-k) negative
-                            const uint32_t neg = (((nx - kx) & 1) ? negx : 0u) ^ (((ny - ky) & 1) ? negy : 0u) ^
-                                                 (((nz - kz) & 1) ? negz : 0u);
-                            T sS = 0, sF = 0;
-                            for (int q = 0; q < nch; ++q) {
-                                const T *Mc = s_mc + q * 2 * ncp;
-                                const T vS = Mc[k], vF = Mc[ncp + k];
-                                const bool ng = (neg >> q) & 1u;
-                                sS += ng ? -vS : vS;
-                                sF += ng ? -vF : vF;
-                            }
-                            accS += coef * sS;
-                            accF += coef * sF;
+                            T coef = (T)(s_binom[nx][kx] * s_binom[ny][ky] * s_binom[nz][kz] *
+                                         pow2f(-(2 * (on - ok) + ok)));
+                            const bool neg = (neg_x && ((nx - kx) & 1)) ^ (neg_y && ((ny - ky) & 1)) ^
+                                             (neg_z && ((nz - kz) & 1));
+                            coef = neg ? -coef : coef;
+                            sS += coef * MS[k];
+                            sF += coef * MF[k];
                         }
             }
-            M[((size_t)c * 2 + 0) * ncp + n] = accS;
-            M[((size_t)c * 2 + 1) * ncp + n] = accF;
+            // sum over the eight children (lanes q = 0..7 of this n)
+#pragma unroll
+            for (int o = 1; o < 8; o <<= 1) {
+                sS += __shfl_xor_sync(0xffffffffu, sS, o);
+                sF += __shfl_xor_sync(0xffffffffu, sF, o);
+            }
+            if (q == 0 && n < ncp) {
+                M[((size_t)c * 2 + 0) * ncp + n] = n < nc ? sS : T(0);
+                M[((size_t)c * 2 + 1) * ncp + n] = n < nc ? sF : T(0);
+            }
         }
     }
 }
@@ -496,6 +514,8 @@ __global__ void walk_step(TreeView t, MacParams mp, const uint2 *front_in, const
 // Warp per cell of the level, lanes over the coefficients n, both classes.  d runs through the
 // multi-indices in their table order (the same d for every lane at each step); the index of n + d
 // comes from a lookup table in shared memory.
+constexpr int kM2MWarps = 2;   // warps per block of the L2L level kernel
+
 template <class T>
 __global__ void __launch_bounds__(32 * kM2MWarps) l2l_level(TreeView t, int lb, int le, int p, int nc, int ncp, int ncls,
                                                             T *L)
@@ -518,6 +538,7 @@ __global__ void __launch_bounds__(32 * kM2MWarps) l2l_level(TreeView t, int lb, 
         if (par < 0) continue;
         const bool neg_x = !(t.cx[c] & 1u), neg_y = !(t.cy[c] & 1u), neg_z = !(t.cz[c] & 1u);
         __syncwarp();
+#pragma unroll 4
         for (int k = lane; k < ncls * ncp; k += 32) s_lp[k] = L[(size_t)par * 2 * ncp + k];
         __syncwarp();
         const T *Lp = s_lp;
@@ -537,6 +558,81 @@ __global__ void __launch_bounds__(32 * kM2MWarps) l2l_level(TreeView t, int lb, 
             L[((size_t)c * 2 + 0) * ncp + n] += acc0;
             if (ncls > 1) L[((size_t)c * 2 + 1) * ncp + n] += acc1;
         }
+    }
+}
+
+// Multi-index k -> (kx, ky, kz) in the table order (total degree, then kx descending, then ky
+// descending), as constexpr functions: inside fully unrolled loops every index folds to a constant.
+struct MI3 {
+    int x, y, z;
+};
+__host__ __device__ constexpr MI3 mi3(int k)
+{
+    int o = 0;
+    while ((o + 1) * (o + 2) * (o + 3) / 6 <= k) ++o;
+    int r = k - o * (o + 1) * (o + 2) / 6;
+    for (int nx = o; nx >= 0; --nx) {
+        const int len = o - nx + 1;   // ny = o - nx .. 0
+        if (r < len) return MI3{nx, o - nx - r, r};
+        r -= len;
+    }
+    return MI3{0, 0, 0};
+}
+__host__ __device__ constexpr int mi3_index(int x, int y, int z)
+{
+    const int o = x + y + z;
+    int k = o * (o + 1) * (o + 2) / 6;
+    for (int nx = o; nx > x; --nx) k += o - nx + 1;
+    return k + (o - x - y);
+}
+__host__ __device__ constexpr int fact_i(int n)
+{
+    int f = 1;
+    for (int i = 2; i <= n; ++i) f *= i;
+    return f;
+}
+
+// L2P at a fixed order P: monomials, coefficients and indices are compile-time after unrolling.
+template <int P, class T, class T4>
+__global__ void l2p_fixed(int n, TreeView t, int log2L, const T4 *__restrict__ pf, const int32_t *__restrict__ leaf_of,
+                          const uint8_t *__restrict__ fs, int masked, int ncp, const T *__restrict__ L, double *acc4)
+{
+    constexpr int NC = (P + 1) * (P + 2) * (P + 3) / 6;
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
+        const T4 r = pf[s];
+        const int c = leaf_of[s];
+        const int cls = (masked && fs[s]) ? 1 : 0;
+        const T *__restrict__ Lc = L + ((size_t)c * 2 + cls) * ncp;
+        const T inv_s = (T)ldexpf(1.0f, (int)t.level[c] - log2L);
+        const T rx = r.x * inv_s, ry = r.y * inv_s, rz = r.z * inv_s;
+        T px[P + 1], py[P + 1], pz[P + 1];
+        px[0] = py[0] = pz[0] = (T)1;
+#pragma unroll
+        for (int e = 1; e <= P; ++e) {
+            px[e] = px[e - 1] * rx;
+            py[e] = py[e - 1] * ry;
+            pz[e] = pz[e - 1] * rz;
+        }
+        T Lk[NC];
+#pragma unroll
+        for (int k = 0; k < NC; ++k) Lk[k] = Lc[k];
+        T phi = 0, gx = 0, gy = 0, gz = 0;
+#pragma unroll
+        for (int k = 0; k < NC; ++k) {
+            const MI3 m = mi3(k);
+            const T mono = px[m.x] * py[m.y] * pz[m.z] * (T(1) / (T)(fact_i(m.x) * fact_i(m.y) * fact_i(m.z)));
+            phi += Lk[k] * mono;
+            if (m.x + m.y + m.z < P) {
+                gx += Lk[mi3_index(m.x + 1, m.y, m.z)] * mono;
+                gy += Lk[mi3_index(m.x, m.y + 1, m.z)] * mono;
+                gz += Lk[mi3_index(m.x, m.y, m.z + 1)] * mono;
+            }
+        }
+        const T is2 = inv_s * inv_s;
+        acc4[s] = to_double(-gx * is2);
+        acc4[(size_t)n + s] = to_double(-gy * is2);
+        acc4[2 * (size_t)n + s] = to_double(-gz * is2);
+        acc4[3 * (size_t)n + s] = to_double(phi * inv_s);
     }
 }
 
@@ -688,8 +784,11 @@ static tg_status run_walk(tg_ctx *c, const TreeView &t, int64_t *n_blocks, int64
     }
     const MacParams mp = make_mac_params(c->prm, log2L);
     c->walk_log2L = log2L;
-    size_t cap_front = (size_t)t.ncell * 8 + 1024, cap_blocks = (size_t)t.ncell * 8 + 1024,
-           cap_p2p = (size_t)t.ncell * 24 + 1024;
+    // capacities from the largest list sizes per cell seen so far (plus a margin), so that a walk is
+    // normally run once
+    size_t cap_front = (size_t)(t.ncell * c->walk_front_per_cell * 1.25) + 1024,
+           cap_blocks = (size_t)(t.ncell * c->walk_blocks_per_cell * 1.25) + 1024,
+           cap_p2p = (size_t)(t.ncell * c->walk_p2p_per_cell * 1.25) + 1024;
     for (int attempt = 0; attempt < 6; ++attempt) {
         uint2 *f0, *f1, *p2p;
         M2LBlock *blocks;
@@ -738,6 +837,10 @@ static tg_status run_walk(tg_ctx *c, const TreeView &t, int64_t *n_blocks, int64
         for (int s = 1; s <= nsteps; ++s) need_front = std::max<size_t>(need_front, h[8 + s]);
         if (h[8 + nsteps] != 0) return set_err(c, TG_ERR_CAPACITY, "walk frontier not empty after %d steps", nsteps);
         const bool overflow = need_front > cap_front || tot_blocks > cap_blocks || tot_p2p + tot_self > cap_p2p;
+        const double nc = (double)t.ncell;
+        c->walk_front_per_cell = std::max(c->walk_front_per_cell, need_front / nc);
+        c->walk_blocks_per_cell = std::max(c->walk_blocks_per_cell, tot_blocks / nc);
+        c->walk_p2p_per_cell = std::max(c->walk_p2p_per_cell, (tot_p2p + tot_self) / nc);
         if (!overflow) {
             *n_blocks = (int64_t)tot_blocks;
             *n_m2l = (int64_t)tot_pairs;
@@ -877,8 +980,8 @@ static tg_status eval_typed(tg_ctx *c, int n, int ncell, const TreeView &t, cons
     for (int l = nlev - 2; l >= 0; --l) {
         const int lb = c->level_begin[l], le = c->level_begin[l + 1];
         ProfScope ps_(c, TG_K_UP);
-        m2m_level<T><<<grid_for((int64_t)(le - lb) * 32, 32 * kM2MWarps), 32 * kM2MWarps,
-                       kM2MWarps * 8 * 2 * ncp * sizeof(T), c->stream>>>(t, lb, le, p, nc, ncp, M, M01);
+        m2m_level<T><<<std::min(le - lb, c->num_sms * 8), kM2MThreads, 8 * 2 * ncp * sizeof(T), c->stream>>>(
+            t, lb, le, p, nc, ncp, M, M01);
     }
     {
         ProfScope ps_(c, TG_K_UP);
@@ -896,8 +999,15 @@ static tg_status eval_typed(tg_ctx *c, int n, int ncell, const TreeView &t, cons
     }
     {
         ProfScope ps_(c, TG_K_DOWN);
-        l2p_particles<T, T4><<<grid_for(n, 128), 128, 0, c->stream>>>(n, t, c->walk_log2L, pf, leaf_of, fs, masked ? 1 : 0,
+        const int g = grid_for(n, 128), mk = masked ? 1 : 0;
+        switch (p) {
+        case 4: l2p_fixed<4, T, T4><<<g, 128, 0, c->stream>>>(n, t, c->walk_log2L, pf, leaf_of, fs, mk, ncp, L, acc4); break;
+        case 5: l2p_fixed<5, T, T4><<<g, 128, 0, c->stream>>>(n, t, c->walk_log2L, pf, leaf_of, fs, mk, ncp, L, acc4); break;
+        case 6: l2p_fixed<6, T, T4><<<g, 128, 0, c->stream>>>(n, t, c->walk_log2L, pf, leaf_of, fs, mk, ncp, L, acc4); break;
+        default:
+            l2p_particles<T, T4><<<grid_for(n, 128), 128, 0, c->stream>>>(n, t, c->walk_log2L, pf, leaf_of, fs, masked ? 1 : 0,
                                                                       p, nc, ncp, L, acc4);
+        }
     }
     if (n_p2p > 0 && (st = launch_p2p_pairs<T, T4>(c, t, d_geom, p2p, n_p2p, pf, fs, nslow, masked, acc4))) return st;
     if (n_self > 0 &&

@@ -76,6 +76,7 @@ struct tg_ctx {
     int64_t last_n = 0, last_ncell = 0, last_nm2l = 0, last_np2p = 0, last_nblocks = 0;
     int walk_log2L = 0;                         // log2 of the last root cube side
     int64_t last_np2p_self = 0, p2p_cap = 0;    // self P2P pairs sit at the end of the P2P buffer
+    double walk_front_per_cell = 8, walk_blocks_per_cell = 8, walk_p2p_per_cell = 24;   // list sizes seen so far
     std::vector<int32_t> level_begin;           // cell index range of each level (BFS)
 
     // live kernel timing
