@@ -904,22 +904,29 @@ tg_status launch_m2l<double>(tg_ctx *c, const TreeView &t, const M2LBlock *block
     return cuda_check(c, cudaGetLastError(), "m2l launch");
 }
 
-// Distinct leaf pairs: float32 packs rows by owner leaf, float64 keeps one block per pair.
+// All P2P pairs: float32 packs the rows of distinct pairs by owner leaf and runs the self pairs in
+// the same launch; float64 keeps one block per pair (two launches).
 template <class T, class T4>
-static tg_status launch_p2p_pairs(tg_ctx *c, const TreeView &t, const Geom *d_geom, const uint2 *pairs, int64_t npairs,
-                                  const T4 *pf, const uint8_t *fs, const int32_t *nslow, bool masked, double *acc4)
+static tg_status launch_p2p_all(tg_ctx *c, const TreeView &t, const Geom *d_geom, const uint2 *pairs, int64_t npairs,
+                                const uint2 *self_pairs, int64_t nself, const T4 *pf, const uint8_t *fs,
+                                const int32_t *nslow, bool masked, double *acc4)
 {
-    return launch_p2p<T, T4>(c, t, d_geom, pairs, npairs, pf, fs, nslow, masked, false, acc4);
+    tg_status st;
+    if (npairs > 0 && (st = launch_p2p<T, T4>(c, t, d_geom, pairs, npairs, pf, fs, nslow, masked, false, acc4)))
+        return st;
+    if (nself > 0 && (st = launch_p2p<T, T4>(c, t, d_geom, self_pairs, nself, pf, fs, nslow, masked, true, acc4)))
+        return st;
+    return TG_OK;
 }
 template <>
-tg_status launch_p2p_pairs<float, float4>(tg_ctx *c, const TreeView &t, const Geom *d_geom, const uint2 *pairs,
-                                          int64_t npairs, const float4 *pf, const uint8_t *fs, const int32_t *nslow,
-                                          bool masked, double *acc4)
+tg_status launch_p2p_all<float, float4>(tg_ctx *c, const TreeView &t, const Geom *d_geom, const uint2 *pairs,
+                                        int64_t npairs, const uint2 *self_pairs, int64_t nself, const float4 *pf,
+                                        const uint8_t *fs, const int32_t *nslow, bool masked, double *acc4)
 {
     (void)d_geom;
     (void)fs;
     (void)masked;   // classes arrive as slow-first leaves (nslow)
-    return launch_p2p_owner(c, t, pairs, npairs, pf, nslow, acc4);
+    return launch_p2p_owner(c, t, pairs, npairs, self_pairs, nself, pf, nslow, acc4);
 }
 
 template <class T, class T4>
@@ -1009,9 +1016,8 @@ static tg_status eval_typed(tg_ctx *c, int n, int ncell, const TreeView &t, cons
                                                                       p, nc, ncp, L, acc4);
         }
     }
-    if (n_p2p > 0 && (st = launch_p2p_pairs<T, T4>(c, t, d_geom, p2p, n_p2p, pf, fs, nslow, masked, acc4))) return st;
-    if (n_self > 0 &&
-        (st = launch_p2p<T, T4>(c, t, d_geom, p2p + (c->p2p_cap - n_self), n_self, pf, fs, nslow, masked, true, acc4)))
+    if ((st = launch_p2p_all<T, T4>(c, t, d_geom, p2p, n_p2p, p2p + (c->p2p_cap - n_self), n_self, pf, fs, nslow,
+                                    masked, acc4)))
         return st;
     return cuda_check(c, cudaGetLastError(), "fmm evaluation");
 }

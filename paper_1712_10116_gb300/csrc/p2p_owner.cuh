@@ -207,14 +207,17 @@ __device__ __forceinline__ int warp_incl_scan(int v, int lane)
 }
 
 // One warp per work unit (kOwnUnit partners of one owner), units taken from a shared counter
-// (ctr[1], starts at zero) so that the load stays balanced whatever the spread of leaf work.
+// (ctr[1], starts at zero) so that the load stays balanced whatever the spread of leaf work.  After
+// the units, the same counter hands out the self pairs (A, A): slow rows of A against every particle
+// of A with a larger index, i.e. each slow-slow and slow-fast pair once (p2p_pair_f32, SELF).
 template <int KERNEL, int ROWS>
 __global__ void __launch_bounds__(256, 2) p2p_owner_f32(TreeView t, int log2L, const uint2 *__restrict__ units,
                                                         uint32_t *ctr, const uint32_t *__restrict__ own_off,
                                                         const uint32_t *__restrict__ own_cnt,
-                                                        const int32_t *__restrict__ partners, const float4 *__restrict__ pf,
-                                                        const int32_t *__restrict__ nslow, float eps, double *acc4, int n,
-                                                        unsigned long long *pair_counter)
+                                                        const int32_t *__restrict__ partners,
+                                                        const uint2 *__restrict__ self_pairs, uint32_t nself,
+                                                        const float4 *__restrict__ pf, const int32_t *__restrict__ nslow,
+                                                        float eps, double *acc4, int n, unsigned long long *pair_counter)
 {
     static_assert(kOwnUnit <= 32, "one partner per lane");
     __shared__ OwnerShared sh;
@@ -229,7 +232,18 @@ __global__ void __launch_bounds__(256, 2) p2p_owner_f32(TreeView t, int log2L, c
         uint32_t k = 0;
         if (lane == 0) k = atomicAdd(&ctr[1], 1u);
         k = __shfl_sync(0xffffffffu, k, 0);
-        if (k >= nunits) break;
+        if (k >= nunits) {
+            if (k - nunits >= nself) break;
+            const int A = (int)self_pairs[k - nunits].x;
+            const int fa = t.first[A], na = t.count[A], sa = nslow ? nslow[A] : na;
+            __syncwarp();
+            p2p_pair_f32<KERNEL, true, ROWS, true>(pf, fa, sa, fa, na, 0.f, 0.f, 0.f, eps, acc4, n, lane, sq);
+            if (lane == 0) {
+                const unsigned long long nf = na - sa;
+                my_pairs += (unsigned long long)na * (na - 1) / 2 - nf * (nf - (nf > 0 ? 1 : 0)) / 2;
+            }
+            continue;
+        }
         const uint2 u = units[k];
         const int B = (int)u.x, pb = (int)u.y;
         const int cnt = (int)own_cnt[B], base = (int)own_off[B];
@@ -326,15 +340,18 @@ __global__ void __launch_bounds__(256, 2) p2p_owner_f32(TreeView t, int log2L, c
 
 namespace tg {
 
-// Distinct leaf pairs in float32: group them by owner, then one warp per owner.
-static tg_status launch_p2p_owner(tg_ctx *c, const TreeView &t, const uint2 *pairs, int64_t npairs, const float4 *pf,
-                                  const int32_t *nslow, double *acc4)
+// Every P2P pair in float32, one launch: the distinct leaf pairs grouped by owner, then the self pairs.
+static tg_status launch_p2p_owner(tg_ctx *c, const TreeView &t, const uint2 *pairs, int64_t npairs,
+                                  const uint2 *self_pairs, int64_t nself, const float4 *pf, const int32_t *nslow,
+                                  double *acc4)
 {
     tg_status st;
     const int ncell = t.ncell;
     uint32_t *own_cnt, *own_fill, *own_off;
     uint2 *tagged, *units;
     int32_t *partners;
+    if (npairs + nself == 0) return TG_OK;
+    if (nself > 0xffffffffll) return set_err(c, TG_ERR_CAPACITY, "too many self pairs for one P2P launch");
     const int64_t max_units = npairs / kOwnUnit + ncell + 1;
     if ((st = ensure_t(c, B_OWN_CNT, (size_t)ncell + 2, &own_cnt)) || (st = ensure_t(c, B_OWN_FILL, ncell, &own_fill)) ||
         (st = ensure_t(c, B_OWN_OFF, ncell, &own_off)) || (st = ensure_t(c, B_OWN_LIST, max_units, &units)) ||
@@ -343,14 +360,17 @@ static tg_status launch_p2p_owner(tg_ctx *c, const TreeView &t, const uint2 *pai
     uint32_t *ctr = own_cnt + ncell;   // [0] work units, [1] next unit to take
     cudaMemsetAsync(own_cnt, 0, sizeof(uint32_t) * ((size_t)ncell + 2), c->stream);
     cudaMemsetAsync(own_fill, 0, sizeof(uint32_t) * (size_t)ncell, c->stream);
-    {
-        ProfScope ps_(c, TG_K_OTHER);
-        p2p_owner_count<<<grid_for(npairs, 256), 256, 0, c->stream>>>(pairs, npairs, t.count, own_cnt, tagged);
-    }
-    if ((st = exclusive_scan_u32(c, own_cnt, own_off, ncell, nullptr))) return st;
-    {
-        ProfScope ps_(c, TG_K_OTHER);
-        p2p_owner_fill<<<grid_for(npairs, 256), 256, 0, c->stream>>>(tagged, npairs, own_off, own_fill, partners, units, ctr);
+    if (npairs > 0) {
+        {
+            ProfScope ps_(c, TG_K_OTHER);
+            p2p_owner_count<<<grid_for(npairs, 256), 256, 0, c->stream>>>(pairs, npairs, t.count, own_cnt, tagged);
+        }
+        if ((st = exclusive_scan_u32(c, own_cnt, own_off, ncell, nullptr))) return st;
+        {
+            ProfScope ps_(c, TG_K_OTHER);
+            p2p_owner_fill<<<grid_for(npairs, 256), 256, 0, c->stream>>>(tagged, npairs, own_off, own_fill, partners,
+                                                                         units, ctr);
+        }
     }
     const float eps = (float)c->prm.eps;
     unsigned long long *pc = c->d_counters;
@@ -367,10 +387,12 @@ static tg_status launch_p2p_owner(tg_ctx *c, const TreeView &t, const uint2 *pai
     const int grid = c->num_sms * occ;
     if (plummer)
         p2p_owner_f32<TG_KERNEL_PLUMMER, 2><<<grid, 256, 0, c->stream>>>(t, c->walk_log2L, units, ctr, own_off, own_cnt,
-                                                                          partners, pf, nslow, eps, acc4, t.n, pc);
+                                                                          partners, self_pairs, (uint32_t)nself, pf,
+                                                                          nslow, eps, acc4, t.n, pc);
     else
         p2p_owner_f32<TG_KERNEL_WENDLAND_C2, 2><<<grid, 256, 0, c->stream>>>(t, c->walk_log2L, units, ctr, own_off, own_cnt,
-                                                                              partners, pf, nslow, eps, acc4, t.n, pc);
+                                                                              partners, self_pairs, (uint32_t)nself,
+                                                                              pf, nslow, eps, acc4, t.n, pc);
     return cuda_check(c, cudaGetLastError(), "p2p owner launch");
 }
 

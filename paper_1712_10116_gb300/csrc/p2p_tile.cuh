@@ -145,28 +145,8 @@ __global__ void __launch_bounds__(kP2PThreads) p2p_mutual(TreeView t, const Geom
 }
 
 // ------------------------------------------------------------------ float32 warp tiles
-// One warp per unordered leaf pair (A, B).  Each lane holds two particles of A (rows i and i+32,
-// chunks of 64); the particles of B (columns) are read in batches of 8, broadcast to all lanes.
-// A lane accumulates its rows' forces in registers and its share of the 8 columns' reactions;
-// after each batch the 32 column partials (8 columns x ax, ay, az, phi) are combined with a
-// reduce-scatter over the warp, leaving lane l with column l/4, component l%4, which it adds
-// to global memory.  Positions are relative to the leaf centres; the centre offset is exact.
-// Reduce-scatter of 32 values over groups of G lanes (G = 8, 16, 32): afterwards v[0 .. 32/G) of
-// lane l hold the group sums of entries (l % G) * (32/G) + t.
-template <int G>
-__device__ __forceinline__ void reduce_scatter(float (&v)[32], int lane)
-{
-#pragma unroll
-    for (int h = 16, d = G / 2; d >= 1; h >>= 1, d >>= 1) {
-        const bool hi = (lane & d) != 0;
-#pragma unroll
-        for (int q = 0; q < h; ++q) {
-            const float send = hi ? v[q] : v[q + h];
-            const float keep = hi ? v[q + h] : v[q];
-            v[q] = keep + __shfl_xor_sync(0xffffffffu, send, d);
-        }
-    }
-}
+// Building blocks of the float32 P2P launch (p2p_owner.cuh): the pair value and the tile of one
+// leaf pair, used there for the self pairs (A, A).
 
 // float32 pair value: Newton by default, Wendland correction inside eps (rare, predicated).
 // NEAR = false: the caller knows r >= eps for every pair (leaf cubes at least eps apart).
@@ -288,77 +268,6 @@ __device__ __noinline__ void p2p_pair_f32(const float4 *__restrict__ pf, int fa,
     }
 }
 
-// One warp per unordered leaf pair.  With slow/fast classes (nslow != nullptr) each leaf holds its
-// slow particles first; the pair is then evaluated as the two tiles (all of A) x (slow of B) and
-// (slow of A) x (fast of B) -- fast-fast pairs are never computed.  For a self pair the tile
-// (slow rows) x (all columns, j > i) covers slow-slow and slow-fast pairs.
-template <int KERNEL, bool SELF, int ROWS>
-__global__ void __launch_bounds__(256, 2) p2p_warp_f32(TreeView t, int log2L, const uint2 *__restrict__ pairs,
-                                                       int64_t npairs, const float4 *__restrict__ pf,
-                                                       const int32_t *__restrict__ nslow, float eps, double *acc4, int n,
-                                                       unsigned long long *pair_counter)
-{
-    __shared__ float4 s_q[8][kMaxNcrit];
-    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    unsigned long long my_pairs = 0;
-    for (int64_t w = wid; w < npairs; w += nw) {
-        const uint2 pr = pairs[w];
-        int a = (int)pr.x, b = (int)pr.y;
-        if (!SELF && t.count[a] < t.count[b]) {   // the larger leaf becomes the rows
-            const int tmp = a;
-            a = b;
-            b = tmp;
-        }
-        const int fa = t.first[a], na = t.count[a], fb = t.first[b], nb = t.count[b];
-        const int sa = nslow ? nslow[a] : na, sb = nslow ? nslow[b] : nb;
-        float ox = 0.f, oy = 0.f, oz = 0.f;
-        bool near = true;
-        if (!SELF) {
-            // z_b - z_a = delta * L / 2^(lf+1), exact in float; |delta| < 2^23 fits int32
-            const int la = t.level[a], lb = t.level[b], lf = la > lb ? la : lb;
-            const float unit = pow2f(log2L - lf - 1);
-            const long long dl[3] = {centre_delta(t.cx[b], lb, t.cx[a], la, lf), centre_delta(t.cy[b], lb, t.cy[a], la, lf),
-                                     centre_delta(t.cz[b], lb, t.cz[a], la, lf)};
-            ox = (float)(int)dl[0] * unit;
-            oy = (float)(int)dl[1] * unit;
-            oz = (float)(int)dl[2] * unit;
-            if (KERNEL == TG_KERNEL_WENDLAND_C2) {
-                // leaf cubes at least eps apart: every pair is beyond eps, no softened branch
-                const long long ha = 1ll << (lf - la), hb = 1ll << (lf - lb);
-                long long g2 = 0;
-#pragma unroll
-                for (int k = 0; k < 3; ++k) {
-                    const long long gk = (dl[k] < 0 ? -dl[k] : dl[k]) - (ha + hb);
-                    if (gk > 0) g2 += gk * gk;
-                }
-                const float eu = eps * pow2f(lf + 1 - log2L);   // eps in half-units of the finer level
-                near = !((float)g2 >= eu * eu * 1.0001f);
-            }
-        }
-        float4 *sq = s_q[wib];
-        if (SELF) {
-            p2p_pair_f32<KERNEL, true, ROWS, true>(pf, fa, sa, fb, nb, 0.f, 0.f, 0.f, eps, acc4, n, lane, sq);
-        } else if (near) {
-            p2p_pair_f32<KERNEL, false, ROWS, true>(pf, fa, na, fb, sb, ox, oy, oz, eps, acc4, n, lane, sq);
-            if (sb < nb && sa > 0)
-                p2p_pair_f32<KERNEL, false, ROWS, true>(pf, fa, sa, fb + sb, nb - sb, ox, oy, oz, eps, acc4, n, lane, sq);
-        } else {
-            p2p_pair_f32<KERNEL, false, ROWS, false>(pf, fa, na, fb, sb, ox, oy, oz, eps, acc4, n, lane, sq);
-            if (sb < nb && sa > 0)
-                p2p_pair_f32<KERNEL, false, ROWS, false>(pf, fa, sa, fb + sb, nb - sb, ox, oy, oz, eps, acc4, n, lane, sq);
-        }
-        if (lane == 0) {
-            // pairs evaluated: all (or i < j for a self pair) minus fast-fast pairs
-            const unsigned long long fa_n = na - sa, fb_n = nb - sb;
-            my_pairs += SELF ? (unsigned long long)na * (na - 1) / 2 - fa_n * (fa_n - (fa_n > 0 ? 1 : 0)) / 2
-                             : (unsigned long long)na * nb - fa_n * fb_n;
-        }
-    }
-    if (lane == 0 && my_pairs) atomicAdd(pair_counter, my_pairs);
-}
-
 template <class T, class T4>
 static tg_status launch_p2p_generic(tg_ctx *c, const TreeView &t, const Geom *d_geom, const uint2 *pairs, int64_t npairs,
                             const T4 *pf, const uint8_t *fs, bool masked, double *acc4)
@@ -381,8 +290,7 @@ static tg_status launch_p2p_generic(tg_ctx *c, const TreeView &t, const Geom *d_
     return cuda_check(c, cudaGetLastError(), "p2p launch");
 }
 
-
-
+// float64 P2P (one block per leaf pair, self pairs included); float32 goes through p2p_owner.cuh.
 template <class T, class T4>
 static tg_status launch_p2p(tg_ctx *c, const TreeView &t, const Geom *d_geom, const uint2 *pairs, int64_t npairs,
                             const T4 *pf, const uint8_t *fs, const int32_t *nslow, bool masked, bool self, double *acc4);
@@ -395,35 +303,6 @@ tg_status launch_p2p<double, dbl4>(tg_ctx *c, const TreeView &t, const Geom *d_g
     (void)nslow;   // the float64 tile masks fast-fast pairs one by one
     (void)self;   // the float64 tile handles self pairs at run time
     return launch_p2p_generic<double, dbl4>(c, t, d_geom, pairs, npairs, pf, fs, masked, acc4);
-}
-
-template <>
-tg_status launch_p2p<float, float4>(tg_ctx *c, const TreeView &t, const Geom *d_geom, const uint2 *pairs,
-                                    int64_t npairs, const float4 *pf, const uint8_t *fs, const int32_t *nslow,
-                                    bool masked, bool self, double *acc4)
-{
-    (void)d_geom;
-    (void)fs;
-    (void)masked;   // classes arrive as slow-first leaves (nslow), not per-particle flags
-    const int grid = grid_for(npairs * 32, 256, c->num_sms * 8);
-    const float eps = (float)c->prm.eps;
-    unsigned long long *ctr = c->d_counters;
-    ProfScope ps_(c, TG_K_P2P);
-    // rows per lane: one for leaves of up to ~32 particles, two for larger leaf sizes
-    const bool two = c->prm.n_crit > 64;
-    const bool plummer = c->prm.kernel == TG_KERNEL_PLUMMER;
-#define TG_P2P_W(K, S, R) \
-    p2p_warp_f32<K, S, R><<<grid, 256, 0, c->stream>>>(t, c->walk_log2L, pairs, npairs, pf, nslow, eps, acc4, t.n, ctr)
-#define TG_P2P_R(K, S) \
-    if (two) TG_P2P_W(K, S, 2); else TG_P2P_W(K, S, 1);
-#define TG_P2P_S(K) \
-    if (self) { TG_P2P_R(K, true) } else { TG_P2P_R(K, false) }
-    if (plummer) { TG_P2P_S(TG_KERNEL_PLUMMER) }
-    else { TG_P2P_S(TG_KERNEL_WENDLAND_C2) }
-#undef TG_P2P_S
-#undef TG_P2P_R
-#undef TG_P2P_W
-    return cuda_check(c, cudaGetLastError(), "p2p launch");
 }
 
 }  // namespace tg
