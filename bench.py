@@ -359,11 +359,11 @@ def scaled_traffic(traffic, key, units_per_launch):
 
 def m2l_flops(p, pairs, stats):
     # triangular terms: D-recurrence ~ 3 C(p+4,4) flops once per pair; contraction C(p+6,6) FMAs per
-    # direction and sink class (2 flops each); classes: 1 without masks, 2 with (counted as 1.5 avg)
+    # direction and local-expansion class (2 flops each): one class per pair, two in a kick pair
     from math import comb
     d = 3 * comb(p + 4, 4)
     contr = 2 * 2 * comb(p + 6, 6)
-    return pairs * (d + contr)
+    return pairs * d + stats.get("m2l_class_pairs", pairs) * contr
 
 
 def run_eval_only(args):

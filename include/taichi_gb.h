@@ -76,6 +76,7 @@ typedef struct {
     int64_t cells;           /* octree cells built, summed over evaluations                    */
     int64_t kdk_frames;      /* KDK frames of the HHS schedule                                  */
     int64_t max_rung;        /* deepest rung that held a slow particle                          */
+    int64_t m2l_class_pairs; /* M2L cell pairs x local-expansion classes (1, or 2 for a kick pair) */
 } tg_stats;
 
 /* Create a context bound to `cuda_stream` (a cudaStream_t, NULL = legacy default stream) on the

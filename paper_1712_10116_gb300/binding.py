@@ -42,7 +42,7 @@ class tg_params(C.Structure):
 class tg_stats(C.Structure):
     _fields_ = [("evaluations", C.c_int64), ("sink_forces", C.c_int64), ("p2p_pairs", C.c_int64),
                 ("m2l_pairs", C.c_int64), ("p2p_cell_pairs", C.c_int64), ("cells", C.c_int64),
-                ("kdk_frames", C.c_int64), ("max_rung", C.c_int64)]
+                ("kdk_frames", C.c_int64), ("max_rung", C.c_int64), ("m2l_class_pairs", C.c_int64)]
 
 
 KERNEL_CLASSES = ["tree", "up", "walk", "m2l", "p2p", "down", "hhs", "other"]

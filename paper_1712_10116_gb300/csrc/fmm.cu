@@ -1056,6 +1056,7 @@ tg_status fmm_eval(tg_ctx *c, int n, const double *pos, int64_t stride, const in
     c->stats.evaluations += 1;
     c->stats.sink_forces += n;
     c->stats.m2l_pairs += n_m2l;
+    c->stats.m2l_class_pairs += n_m2l * (masked ? 2 : 1);
     c->stats.p2p_cell_pairs += n_p2p + n_self;
     c->stats.cells += ncell;
     return cuda_check(c, cudaGetLastError(), "fmm scatter");

@@ -14,9 +14,9 @@
 // underflow in float32 however deep the tree.  D comes from the McMurchie-Davidson auxiliary
 // recurrence R^(m)_{k+e_a} = d_a R^(m+1)_k + k_a R^(m+1)_{k-e_a}.
 //
-// Lane layout of one warp over a block: round r in {0, 1}, lane l -> (i, j) = (4r + l/8, l%8).
-// The x-side sums of one row i are reduced over its 8 lanes, the y-side sums of one column j over
-// its 4 lanes, and one lane per row / column adds them to global memory.
+// Lane layout of one warp over a block: lane l -> (row of the round l/8, column j = l%8); a round
+// covers four rows.  The x-side sums of one row are reduced over its 8 lanes, the y-side sums of one
+// column over its 4 lanes, each lane then adding its slice of the coefficients to global memory.
 #pragma once
 #include "tg_common.cuh"
 #include "tg_tables.cuh"
@@ -70,13 +70,40 @@ __device__ __forceinline__ void pair_offset(const TreeView &t, int x, int y, int
 }
 
 // ------------------------------------------------------------------ float32, fixed order P <= 6
+// Rounds take the block's non-empty rows four at a time (a block whose rows fit in four needs one
+// round).  The 8 lanes of a row and the 4 lanes of a column combine their partial expansions with a
+// reduce-scatter (coefficients padded to RL per row lane, CL per column lane), after which every
+// lane adds its own slice to global memory: no lane holds the whole sum.
+template <int P>
+struct M2LScatter {
+    static constexpr int NC = M2LGen<P>::NC;
+    static constexpr int RL = (NC + 31) / 32 * 4;   // coefficients per lane after the row reduction
+    static constexpr int CL = (NC + 15) / 16 * 4;   // ... after the column reduction
+    static constexpr int NP = 8 * RL > 4 * CL ? 8 * RL : 4 * CL;
+};
+
+// halve the live coefficients once: lanes with bit d keep the upper half, the others the lower half
+template <int NP, int H>
+__device__ __forceinline__ void m2l_halve(float (&v)[NP], int lane, int d)
+{
+    const bool hi = (lane & d) != 0;
+#pragma unroll
+    for (int q = 0; q < H; ++q) {
+        const float send = hi ? v[q] : v[q + H];
+        const float keep = hi ? v[q + H] : v[q];
+        v[q] = keep + __shfl_xor_sync(0xffffffffu, send, d);
+    }
+}
+
 template <int P, bool MASKED>
 __global__ void __launch_bounds__(128) m2l_blocks_f32(TreeView t, const M2LBlock *__restrict__ blocks, int64_t nblocks,
                                                       const float *__restrict__ Ms, float *L, int ncp, float eps_over_L,
                                                       int plummer)
 {
-    constexpr int NC = M2LGen<P>::NC;
+    using S = M2LScatter<P>;
+    constexpr int NC = S::NC, RL = S::RL, CL = S::CL, NP = S::NP;
     const int lane = threadIdx.x & 31;
+    const int j = lane & 7, rr = (lane >> 3) & 3;
     const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t w = wid; w < nblocks; w += nw) {
@@ -85,12 +112,23 @@ __global__ void __launch_bounds__(128) m2l_blocks_f32(TreeView t, const M2LBlock
         const float rho = ldexpf(1.0f, bg.lx - bg.ly);
         const float soft = plummer ? ldexpf(eps_over_L, bg.lx) : 0.0f;   // eps / s_x
         const float soft2 = soft * soft;
-        for (int r = 0; r < 2; ++r) {
-            const int i = 4 * r + (lane >> 3), j = lane & 7;
-            const bool active = i < bg.ni && j < bg.nj && ((blk.mask >> (8 * i + j)) & 1ull);
+        unsigned rowmask = 0;   // rows holding at least one well-separated pair
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+            if (((blk.mask >> (8 * i)) & 0xffull) != 0ull) rowmask |= 1u << i;
+        const int nrows = __popc(rowmask);
+        for (int r0 = 0; r0 < nrows; r0 += 4) {
+            // this lane's row: the (r0 + rr)-th non-empty row
+            int i = -1;
+            {
+                const int want = r0 + rr;
+#pragma unroll
+                for (int b = 0; b < 8; ++b)
+                    if (((rowmask >> b) & 1u) && __popc(rowmask & ((1u << b) - 1u)) == want) i = b;
+            }
+            const bool active = i >= 0 && j < bg.nj && ((blk.mask >> (8 * i + j)) & 1ull);
             const unsigned amask = __ballot_sync(0xffffffffu, active);
-            if (amask == 0) continue;
-            const int x = bg.baseA + i, y = bg.baseB + j;
+            const int x = bg.baseA + (i < 0 ? 0 : i), y = bg.baseB + j;
             float D[NC];
             if (active) {
                 float dx, dy, dz;
@@ -100,54 +138,55 @@ __global__ void __launch_bounds__(128) m2l_blocks_f32(TreeView t, const M2LBlock
 #pragma unroll
                 for (int k = 0; k < NC; ++k) D[k] = 0.f;
             }
-            const bool row_flush = (lane & 7) == 0 && ((amask >> (lane & ~7)) & 0xffu) != 0;
-            const bool col_flush = (lane >> 3) == 0 && (amask & (0x01010101u << (lane & 7))) != 0;
+            const bool row_used = ((amask >> (lane & ~7)) & 0xffu) != 0u;   // this lane's row, this round
+            const bool col_used = (amask & (0x01010101u << j)) != 0u;      // this lane's column, this round
 #pragma unroll
             for (int cls = 0; cls < (MASKED ? 2 : 1); ++cls) {
-                float Lc[NC];
-                // x side: sources y
+                float Lc[NP];
+                // x side: sources y; reduce-scatter over the row's lanes (bits 2, 1, 0):
+                // lane j keeps coefficients RL*j .. RL*j + RL - 1
 #pragma unroll
-                for (int k = 0; k < NC; ++k) Lc[k] = 0.f;
-                if (active) M2LGen<P>::side_a(D, Ms + ((size_t)y * 2 + cls) * ncp, rho, Lc);
-#pragma unroll
-                for (int k = 0; k < NC; ++k) {
-                    float v = Lc[k];
-                    v += __shfl_xor_sync(0xffffffffu, v, 1);
-                    v += __shfl_xor_sync(0xffffffffu, v, 2);
-                    v += __shfl_xor_sync(0xffffffffu, v, 4);
-                    Lc[k] = v;
-                }
-                if (row_flush) {
+                for (int k = 0; k < NP; ++k) Lc[k] = 0.f;
+                if (active) M2LGen<P>::side_a(D, Ms + ((size_t)y * 2 + cls) * ncp, rho, reinterpret_cast<float(&)[NC]>(Lc));
+                m2l_halve<NP, 4 * RL>(Lc, lane, 4);
+                m2l_halve<NP, 2 * RL>(Lc, lane, 2);
+                m2l_halve<NP, RL>(Lc, lane, 1);
+                if (row_used) {
                     float *dst = L + ((size_t)x * 2 + cls) * ncp;
 #pragma unroll
-                    for (int k = 0; k < NC; k += 4)
-                        atomicAdd(reinterpret_cast<float4 *>(dst + k),
-                                  make_float4(Lc[k], k + 1 < NC ? Lc[k + 1] : 0.f, k + 2 < NC ? Lc[k + 2] : 0.f,
-                                              k + 3 < NC ? Lc[k + 3] : 0.f));
+                    for (int g = 0; g < RL; g += 4) {
+                        const int k = RL * j + g;
+                        if (k < NC) atomicAdd(reinterpret_cast<float4 *>(dst + k), make_float4(Lc[g], Lc[g + 1], Lc[g + 2], Lc[g + 3]));
+                    }
                 }
-                // y side: sources x
+                // y side: sources x; reduce-scatter over the column's lanes (bits 4, 3):
+                // lane (rr, j) keeps coefficients CL*rr .. CL*rr + CL - 1 of column j
 #pragma unroll
-                for (int k = 0; k < NC; ++k) Lc[k] = 0.f;
-                if (active) M2LGen<P>::side_b(D, Ms + ((size_t)x * 2 + cls) * ncp, Lc);
-#pragma unroll
-                for (int k = 0; k < NC; ++k) {
-                    float v = Lc[k];
-                    v += __shfl_xor_sync(0xffffffffu, v, 8);
-                    v += __shfl_xor_sync(0xffffffffu, v, 16);
-                    Lc[k] = v;
-                }
-                if (col_flush) {
-                    float rp[P + 2];
-                    rp[0] = 1.f;
-#pragma unroll
-                    for (int o = 1; o <= P + 1; ++o) rp[o] = rp[o - 1] * rho;
+                for (int k = 0; k < NP; ++k) Lc[k] = 0.f;
+                if (active) M2LGen<P>::side_b(D, Ms + ((size_t)x * 2 + cls) * ncp, reinterpret_cast<float(&)[NC]>(Lc));
+                m2l_halve<NP, 2 * CL>(Lc, lane, 16);
+                m2l_halve<NP, CL>(Lc, lane, 8);
+                if (col_used) {
+                    // the sums are in the x normalisation: L~_y^n carries rho^(|n|+1)
                     float *dst = L + ((size_t)y * 2 + cls) * ncp;
+                    const int k0 = CL * rr;
+                    int o = order_of(k0);
+                    int next = (o + 1) * (o + 2) * (o + 3) / 6;   // first index of order o + 1
+                    float sc = ldexpf(1.0f, (bg.lx - bg.ly) * (o + 1));
 #pragma unroll
-                    for (int k = 0; k < NC; k += 4) {
+                    for (int g = 0; g < CL; g += 4) {
                         float v[4];
 #pragma unroll
-                        for (int q = 0; q < 4; ++q) v[q] = (k + q < NC) ? Lc[k + q] * rp[order_of(k + q) + 1] : 0.f;
-                        atomicAdd(reinterpret_cast<float4 *>(dst + k), make_float4(v[0], v[1], v[2], v[3]));
+                        for (int q = 0; q < 4; ++q) {
+                            const int k = k0 + g + q;
+                            if (k == next) {
+                                ++o;
+                                next = (o + 1) * (o + 2) * (o + 3) / 6;
+                                sc *= rho;
+                            }
+                            v[q] = Lc[g + q] * sc;
+                        }
+                        if (k0 + g < NC) atomicAdd(reinterpret_cast<float4 *>(dst + k0 + g), make_float4(v[0], v[1], v[2], v[3]));
                     }
                 }
             }
