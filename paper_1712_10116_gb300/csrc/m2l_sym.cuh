@@ -128,7 +128,10 @@ __global__ void __launch_bounds__(128) m2l_blocks_f32(TreeView t, const M2LBlock
             }
             const bool active = i >= 0 && j < bg.nj && ((blk.mask >> (8 * i + j)) & 1ull);
             const unsigned amask = __ballot_sync(0xffffffffu, active);
+            // x, y: this lane's row and column cells (every lane of a used row / column flushes a slice);
+            // inactive lanes run the contractions on a zero tensor and an existing cell's moments
             const int x = bg.baseA + (i < 0 ? 0 : i), y = bg.baseB + j;
+            const int xs = active ? x : bg.baseA, ys = active ? y : bg.baseB;
             float D[NC];
             if (active) {
                 float dx, dy, dz;
@@ -146,8 +149,8 @@ __global__ void __launch_bounds__(128) m2l_blocks_f32(TreeView t, const M2LBlock
                 // x side: sources y; reduce-scatter over the row's lanes (bits 2, 1, 0):
                 // lane j keeps coefficients RL*j .. RL*j + RL - 1
 #pragma unroll
-                for (int k = 0; k < NP; ++k) Lc[k] = 0.f;
-                if (active) M2LGen<P>::side_a(D, Ms + ((size_t)y * 2 + cls) * ncp, rho, reinterpret_cast<float(&)[NC]>(Lc));
+                for (int k = NC; k < NP; ++k) Lc[k] = 0.f;
+                M2LGen<P>::side_a(D, Ms + ((size_t)ys * 2 + cls) * ncp, rho, reinterpret_cast<float(&)[NC]>(Lc));
                 m2l_halve<NP, 4 * RL>(Lc, lane, 4);
                 m2l_halve<NP, 2 * RL>(Lc, lane, 2);
                 m2l_halve<NP, RL>(Lc, lane, 1);
@@ -162,8 +165,8 @@ __global__ void __launch_bounds__(128) m2l_blocks_f32(TreeView t, const M2LBlock
                 // y side: sources x; reduce-scatter over the column's lanes (bits 4, 3):
                 // lane (rr, j) keeps coefficients CL*rr .. CL*rr + CL - 1 of column j
 #pragma unroll
-                for (int k = 0; k < NP; ++k) Lc[k] = 0.f;
-                if (active) M2LGen<P>::side_b(D, Ms + ((size_t)x * 2 + cls) * ncp, reinterpret_cast<float(&)[NC]>(Lc));
+                for (int k = NC; k < NP; ++k) Lc[k] = 0.f;
+                M2LGen<P>::side_b(D, Ms + ((size_t)xs * 2 + cls) * ncp, reinterpret_cast<float(&)[NC]>(Lc));
                 m2l_halve<NP, 2 * CL>(Lc, lane, 16);
                 m2l_halve<NP, CL>(Lc, lane, 8);
                 if (col_used) {
