@@ -14,9 +14,6 @@
 // evaluation thus serve a kickFS2S + kickS2F pair of Algorithm 2.
 #include "tg_common.cuh"
 #include "tg_tables.cuh"
-#include "p2p_tile.cuh"
-#include "p2p_owner.cuh"
-#include "m2l_sym.cuh"
 
 namespace tg {
 
@@ -593,7 +590,8 @@ __host__ __device__ constexpr int fact_i(int n)
 }
 
 // L2P at a fixed order P: monomials, coefficients and indices are compile-time after unrolling.
-template <int P, class T, class T4>
+// POT = false: accelerations only (the potential slot is written as zero).
+template <int P, class T, class T4, bool POT>
 __global__ void l2p_fixed(int n, TreeView t, int log2L, const T4 *__restrict__ pf, const int32_t *__restrict__ leaf_of,
                           const uint8_t *__restrict__ fs, int masked, int ncp, const T *__restrict__ L, double *acc4)
 {
@@ -621,7 +619,7 @@ __global__ void l2p_fixed(int n, TreeView t, int log2L, const T4 *__restrict__ p
         for (int k = 0; k < NC; ++k) {
             const MI3 m = mi3(k);
             const T mono = px[m.x] * py[m.y] * pz[m.z] * (T(1) / (T)(fact_i(m.x) * fact_i(m.y) * fact_i(m.z)));
-            phi += Lk[k] * mono;
+            if (POT) phi += Lk[k] * mono;
             if (m.x + m.y + m.z < P) {
                 gx += Lk[mi3_index(m.x + 1, m.y, m.z)] * mono;
                 gy += Lk[mi3_index(m.x, m.y + 1, m.z)] * mono;
@@ -857,80 +855,38 @@ static tg_status run_walk(tg_ctx *c, const TreeView &t, int64_t *n_blocks, int64
 
 static inline int pad4(int x) { return (x + 3) & ~3; }
 
-template <class T>
-static tg_status launch_m2l(tg_ctx *c, const TreeView &t, const M2LBlock *blocks, int64_t nblocks, const T *Ms, T *L,
-                            int p, int nc, int ncp, bool masked);
-
-template <>
-tg_status launch_m2l<float>(tg_ctx *c, const TreeView &t, const M2LBlock *blocks, int64_t nblocks, const float *Ms,
-                            float *L, int p, int nc, int ncp, bool masked)
+// precision dispatch of the M2L and P2P launchers (m2l.cu, p2p.cu)
+static tg_status launch_m2l_t(tg_ctx *c, const TreeView &t, const M2LBlock *blocks, int64_t nblocks, const float *Ms,
+                              float *L, int p, int nc, int ncp, bool masked, bool pot)
 {
-    const int plummer = c->prm.kernel == TG_KERNEL_PLUMMER;
-    const float eoL = (float)ldexp(c->prm.eps, -c->walk_log2L);
-    const int grid = grid_for(nblocks * 32, 128, c->num_sms * 16);
-    ProfScope ps_(c, TG_K_M2L);
-#define TG_M2L_F32(PP)                                                                                            \
-    case PP:                                                                                                      \
-        if (masked) m2l_blocks_f32<PP, true><<<grid, 128, 0, c->stream>>>(t, blocks, nblocks, Ms, L, ncp, eoL, plummer); \
-        else m2l_blocks_f32<PP, false><<<grid, 128, 0, c->stream>>>(t, blocks, nblocks, Ms, L, ncp, eoL, plummer);       \
-        break;
-    switch (p) {
-        TG_M2L_F32(1)
-        TG_M2L_F32(2)
-        TG_M2L_F32(3)
-        TG_M2L_F32(4)
-        TG_M2L_F32(5)
-        TG_M2L_F32(6)
-    default:
-        if (masked) m2l_blocks_generic<float, true><<<grid, 128, 0, c->stream>>>(t, blocks, nblocks, Ms, L, p, nc, ncp,
-                                                                                ldexp(c->prm.eps, -c->walk_log2L), plummer);
-        else m2l_blocks_generic<float, false><<<grid, 128, 0, c->stream>>>(t, blocks, nblocks, Ms, L, p, nc, ncp,
-                                                                          ldexp(c->prm.eps, -c->walk_log2L), plummer);
-    }
-#undef TG_M2L_F32
-    return cuda_check(c, cudaGetLastError(), "m2l launch");
+    return launch_m2l_f32(c, t, blocks, nblocks, Ms, L, p, nc, ncp, masked, pot);
 }
-
-template <>
-tg_status launch_m2l<double>(tg_ctx *c, const TreeView &t, const M2LBlock *blocks, int64_t nblocks, const double *Ms,
-                             double *L, int p, int nc, int ncp, bool masked)
+static tg_status launch_m2l_t(tg_ctx *c, const TreeView &t, const M2LBlock *blocks, int64_t nblocks, const double *Ms,
+                              double *L, int p, int nc, int ncp, bool masked, bool pot)
 {
-    const int plummer = c->prm.kernel == TG_KERNEL_PLUMMER;
-    const double eoL = ldexp(c->prm.eps, -c->walk_log2L);
-    const int grid = grid_for(nblocks * 32, 128, c->num_sms * 16);
-    ProfScope ps_(c, TG_K_M2L);
-    if (masked) m2l_blocks_generic<double, true><<<grid, 128, 0, c->stream>>>(t, blocks, nblocks, Ms, L, p, nc, ncp, eoL, plummer);
-    else m2l_blocks_generic<double, false><<<grid, 128, 0, c->stream>>>(t, blocks, nblocks, Ms, L, p, nc, ncp, eoL, plummer);
-    return cuda_check(c, cudaGetLastError(), "m2l launch");
+    (void)pot;   // the float64 contraction always includes the potential term
+    return launch_m2l_f64(c, t, blocks, nblocks, Ms, L, p, nc, ncp, masked);
 }
-
-// All P2P pairs: float32 packs the rows of distinct pairs by owner leaf and runs the self pairs in
-// the same launch; float64 keeps one block per pair (two launches).
-template <class T, class T4>
-static tg_status launch_p2p_all(tg_ctx *c, const TreeView &t, const Geom *d_geom, const uint2 *pairs, int64_t npairs,
-                                const uint2 *self_pairs, int64_t nself, const T4 *pf, const uint8_t *fs,
-                                const int32_t *nslow, bool masked, double *acc4)
-{
-    tg_status st;
-    if (npairs > 0 && (st = launch_p2p<T, T4>(c, t, d_geom, pairs, npairs, pf, fs, nslow, masked, false, acc4)))
-        return st;
-    if (nself > 0 && (st = launch_p2p<T, T4>(c, t, d_geom, self_pairs, nself, pf, fs, nslow, masked, true, acc4)))
-        return st;
-    return TG_OK;
-}
-template <>
-tg_status launch_p2p_all<float, float4>(tg_ctx *c, const TreeView &t, const Geom *d_geom, const uint2 *pairs,
-                                        int64_t npairs, const uint2 *self_pairs, int64_t nself, const float4 *pf,
-                                        const uint8_t *fs, const int32_t *nslow, bool masked, double *acc4)
+static tg_status launch_p2p_t(tg_ctx *c, const TreeView &t, const Geom *d_geom, const uint2 *pairs, int64_t npairs,
+                              const uint2 *self_pairs, int64_t nself, const float4 *pf, const uint8_t *fs,
+                              const int32_t *nslow, bool masked, bool pot, double *acc4)
 {
     (void)d_geom;
     (void)fs;
     (void)masked;   // classes arrive as slow-first leaves (nslow)
-    return launch_p2p_owner(c, t, pairs, npairs, self_pairs, nself, pf, nslow, acc4);
+    return launch_p2p_f32(c, t, pairs, npairs, self_pairs, nself, pf, nslow, pot, acc4);
+}
+static tg_status launch_p2p_t(tg_ctx *c, const TreeView &t, const Geom *d_geom, const uint2 *pairs, int64_t npairs,
+                              const uint2 *self_pairs, int64_t nself, const dbl4 *pf, const uint8_t *fs,
+                              const int32_t *nslow, bool masked, bool pot, double *acc4)
+{
+    (void)nslow;   // the float64 tiles mask fast-fast pairs one by one
+    (void)pot;     // and always include the potential
+    return launch_p2p_f64(c, t, d_geom, pairs, npairs, self_pairs, nself, pf, fs, masked, acc4);
 }
 
 template <class T, class T4>
-static tg_status eval_typed(tg_ctx *c, int n, int ncell, const TreeView &t, const Geom *d_geom, bool masked,
+static tg_status eval_typed(tg_ctx *c, int n, int ncell, const TreeView &t, const Geom *d_geom, bool masked, bool want_pot,
                             int64_t n_blocks, int64_t n_p2p, int64_t n_self)
 {
     tg_status st;
@@ -997,7 +953,7 @@ static tg_status eval_typed(tg_ctx *c, int n, int ncell, const TreeView &t, cons
     cudaMemsetAsync(L, 0, sizeof(T) * (size_t)ncell * 2 * ncp, c->stream);
     const M2LBlock *blocks = static_cast<const M2LBlock *>(c->buf[B_M2L].p);
     const uint2 *p2p = static_cast<const uint2 *>(c->buf[B_P2P].p);
-    if (n_blocks > 0 && (st = launch_m2l<T>(c, t, blocks, n_blocks, Ms, L, p, nc, ncp, masked))) return st;
+    if (n_blocks > 0 && (st = launch_m2l_t(c, t, blocks, n_blocks, Ms, L, p, nc, ncp, masked, want_pot))) return st;
     for (int l = 1; l < nlev; ++l) {
         const int lb = c->level_begin[l], le = c->level_begin[l + 1];
         ProfScope ps_(c, TG_K_DOWN);
@@ -1007,17 +963,23 @@ static tg_status eval_typed(tg_ctx *c, int n, int ncell, const TreeView &t, cons
     {
         ProfScope ps_(c, TG_K_DOWN);
         const int g = grid_for(n, 128), mk = masked ? 1 : 0;
+#define TG_L2P(PP)                                                                                                 \
+    case PP:                                                                                                       \
+        if (want_pot) l2p_fixed<PP, T, T4, true><<<g, 128, 0, c->stream>>>(n, t, c->walk_log2L, pf, leaf_of, fs, mk, ncp, L, acc4); \
+        else l2p_fixed<PP, T, T4, false><<<g, 128, 0, c->stream>>>(n, t, c->walk_log2L, pf, leaf_of, fs, mk, ncp, L, acc4); \
+        break;
         switch (p) {
-        case 4: l2p_fixed<4, T, T4><<<g, 128, 0, c->stream>>>(n, t, c->walk_log2L, pf, leaf_of, fs, mk, ncp, L, acc4); break;
-        case 5: l2p_fixed<5, T, T4><<<g, 128, 0, c->stream>>>(n, t, c->walk_log2L, pf, leaf_of, fs, mk, ncp, L, acc4); break;
-        case 6: l2p_fixed<6, T, T4><<<g, 128, 0, c->stream>>>(n, t, c->walk_log2L, pf, leaf_of, fs, mk, ncp, L, acc4); break;
+            TG_L2P(4)
+            TG_L2P(5)
+            TG_L2P(6)
         default:
             l2p_particles<T, T4><<<grid_for(n, 128), 128, 0, c->stream>>>(n, t, c->walk_log2L, pf, leaf_of, fs, masked ? 1 : 0,
                                                                       p, nc, ncp, L, acc4);
         }
+#undef TG_L2P
     }
-    if ((st = launch_p2p_all<T, T4>(c, t, d_geom, p2p, n_p2p, p2p + (c->p2p_cap - n_self), n_self, pf, fs, nslow,
-                                    masked, acc4)))
+    if ((st = launch_p2p_t(c, t, d_geom, p2p, n_p2p, p2p + (c->p2p_cap - n_self), n_self, pf, fs, nslow, masked,
+                            want_pot, acc4)))
         return st;
     return cuda_check(c, cudaGetLastError(), "fmm evaluation");
 }
@@ -1044,8 +1006,8 @@ tg_status fmm_eval(tg_ctx *c, int n, const double *pos, int64_t stride, const in
     c->last_np2p = n_p2p + n_self;
     c->last_np2p_self = n_self;
     const bool masked = fast != nullptr;
-    if (c->prm.precision == TG_PREC_FP32) st = eval_typed<float, float4>(c, n, ncell, t, d_geom, masked, n_blocks, n_p2p, n_self);
-    else st = eval_typed<double, dbl4>(c, n, ncell, t, d_geom, masked, n_blocks, n_p2p, n_self);
+    if (c->prm.precision == TG_PREC_FP32) st = eval_typed<float, float4>(c, n, ncell, t, d_geom, masked, pot != nullptr, n_blocks, n_p2p, n_self);
+    else st = eval_typed<double, dbl4>(c, n, ncell, t, d_geom, masked, pot != nullptr, n_blocks, n_p2p, n_self);
     if (st) return st;
     const uint32_t *perm = static_cast<const uint32_t *>(c->buf[B_VALS0].p);
     const double *acc4 = static_cast<const double *>(c->buf[B_ACC].p);

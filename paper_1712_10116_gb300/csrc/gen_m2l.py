@@ -5,7 +5,9 @@ For each P in 1..6 it emits
                                          by the auxiliary recurrence R^(m)_{k+e_a} = d_a R^(m+1)_k + k_a R^(m+1)_{k-e_a}
   m2l_side_a_P(D, Ms, rho, L)           L^n = sum_j (-1)^|j| rho^|j| Ms^j D^{n+j}   (Ms = M/j!)
   m2l_side_b_P(D, Ms, L)                L^n = (-1)^|n| sum_j Ms^j D^{n+j}
-(both overwrite L: the j = 0 term, which reaches every n, initialises it).
+(both overwrite L: the j = 0 term, which reaches every n, initialises it), and the variants
+  m2l_side_a_forces_P, m2l_side_b_forces_P for accelerations only: L^0 (the potential term) is set to
+  zero and the |j| = p moments, which only reach L^0, are not read.
 Everything is unrolled with compile-time indices so that D and L live in registers.
 Multi-indices are ordered by total degree, then nx descending, then ny descending.
 Run: python gen_m2l.py > m2l_gen.cuh
@@ -63,48 +65,59 @@ def gen(P):
         out.append(f"    D[{k}] = r_0_{k};")
     out.append("}")
     out.append("")
-    # side A: L^n += sum_j (-1)^|j| rho^|j| Ms^j D^{n+j}
-    out.append(f"__device__ __forceinline__ void m2l_side_a_{P}(const float (&D)[{nc}], const float *__restrict__ Ms, float rho, float (&L)[{nc}])")
-    out.append("{")
-    out.append("    float rp = 1.0f;")
-    prev_order = 0
-    for j, (jx, jy, jz) in enumerate(mi):
-        oj = jx + jy + jz
-        if oj != prev_order:
-            out.append("    rp *= rho;")
-            prev_order = oj
-        neg = (oj % 2) == 1
-        out.append(f"    {{ const float m = {'-' if neg else ''}__ldg(Ms + {j}) * rp;")
-        for n, (nx, ny, nz) in enumerate(mi):
-            if nx + ny + nz + oj > P:
+    for pot in (True, False):
+        suf = "" if pot else "_forces"
+        first_n = 0 if pot else 1   # forces only: L^0 (the potential term) is left at zero
+        # side A: L^n = sum_j (-1)^|j| rho^|j| Ms^j D^{n+j}
+        out.append(f"__device__ __forceinline__ void m2l_side_a{suf}_{P}(const float (&D)[{nc}], const float *__restrict__ Ms, float rho, float (&L)[{nc}])")
+        out.append("{")
+        if not pot:
+            out.append("    L[0] = 0.0f;")
+        out.append("    float rp = 1.0f;")
+        prev_order = 0
+        for j, (jx, jy, jz) in enumerate(mi):
+            oj = jx + jy + jz
+            if not pot and oj == P:
+                continue   # only reaches n = 0
+            if oj != prev_order:
+                out.append("    rp *= rho;")
+                prev_order = oj
+            neg = (oj % 2) == 1
+            out.append(f"    {{ const float m = {'-' if neg else ''}__ldg(Ms + {j}) * rp;")
+            for n, (nx, ny, nz) in enumerate(mi):
+                if n < first_n or nx + ny + nz + oj > P:
+                    continue
+                t = idx[(nx + jx, ny + jy, nz + jz)]
+                if j == 0:
+                    out.append(f"      L[{n}] = D[{t}] * m;")
+                else:
+                    out.append(f"      L[{n}] = fmaf(D[{t}], m, L[{n}]);")
+            out.append("    }")
+        out.append("}")
+        out.append("")
+        # side B: L^n = (-1)^|n| sum_j Ms^j D^{n+j}
+        out.append(f"__device__ __forceinline__ void m2l_side_b{suf}_{P}(const float (&D)[{nc}], const float *__restrict__ Ms, float (&L)[{nc}])")
+        out.append("{")
+        if not pot:
+            out.append("    L[0] = 0.0f;")
+        for j, (jx, jy, jz) in enumerate(mi):
+            oj = jx + jy + jz
+            if not pot and oj == P:
                 continue
-            t = idx[(nx + jx, ny + jy, nz + jz)]
-            if j == 0:
-                out.append(f"      L[{n}] = D[{t}] * m;")
-            else:
-                out.append(f"      L[{n}] = fmaf(D[{t}], m, L[{n}]);")
-        out.append("    }")
-    out.append("}")
-    out.append("")
-    # side B: L^n += (-1)^|n| sum_j Ms^j D^{n+j}
-    out.append(f"__device__ __forceinline__ void m2l_side_b_{P}(const float (&D)[{nc}], const float *__restrict__ Ms, float (&L)[{nc}])")
-    out.append("{")
-    for j, (jx, jy, jz) in enumerate(mi):
-        oj = jx + jy + jz
-        out.append(f"    {{ const float m = __ldg(Ms + {j});")
-        for n, (nx, ny, nz) in enumerate(mi):
-            on = nx + ny + nz
-            if on + oj > P:
-                continue
-            t = idx[(nx + jx, ny + jy, nz + jz)]
-            sign = "-" if on % 2 else ""
-            if j == 0:
-                out.append(f"      L[{n}] = {sign}D[{t}] * m;")
-            else:
-                out.append(f"      L[{n}] = fmaf({sign}D[{t}], m, L[{n}]);")
-        out.append("    }")
-    out.append("}")
-    out.append("")
+            out.append(f"    {{ const float m = __ldg(Ms + {j});")
+            for n, (nx, ny, nz) in enumerate(mi):
+                on = nx + ny + nz
+                if n < first_n or on + oj > P:
+                    continue
+                t = idx[(nx + jx, ny + jy, nz + jz)]
+                sign = "-" if on % 2 else ""
+                if j == 0:
+                    out.append(f"      L[{n}] = {sign}D[{t}] * m;")
+                else:
+                    out.append(f"      L[{n}] = fmaf({sign}D[{t}], m, L[{n}]);")
+            out.append("    }")
+        out.append("}")
+        out.append("")
     return "\n".join(out)
 
 
@@ -122,6 +135,8 @@ def main():
         print(f"    static __device__ __forceinline__ void dtensor(float dx, float dy, float dz, float s, float (&D)[{nc}]) {{ m2l_dtensor_{P}(dx, dy, dz, s, D); }}")
         print(f"    static __device__ __forceinline__ void side_a(const float (&D)[{nc}], const float *Ms, float rho, float (&L)[{nc}]) {{ m2l_side_a_{P}(D, Ms, rho, L); }}")
         print(f"    static __device__ __forceinline__ void side_b(const float (&D)[{nc}], const float *Ms, float (&L)[{nc}]) {{ m2l_side_b_{P}(D, Ms, L); }}")
+        print(f"    static __device__ __forceinline__ void side_a_forces(const float (&D)[{nc}], const float *Ms, float rho, float (&L)[{nc}]) {{ m2l_side_a_forces_{P}(D, Ms, rho, L); }}")
+        print(f"    static __device__ __forceinline__ void side_b_forces(const float (&D)[{nc}], const float *Ms, float (&L)[{nc}]) {{ m2l_side_b_forces_{P}(D, Ms, L); }}")
         print("};")
 
 

@@ -24,11 +24,6 @@
 
 namespace tg {
 
-struct M2LBlock {
-    uint32_t a, b;             // cell pair that was opened (a == b: self pair, only i < j bits set)
-    unsigned long long mask;   // bit 8i + j: pair (child i of a, child j of b) is well separated
-};
-
 // total degree of the k-th multi-index (ordering by total degree)
 __host__ __device__ constexpr int order_of(int k)
 {
@@ -95,7 +90,8 @@ __device__ __forceinline__ void m2l_halve(float (&v)[NP], int lane, int d)
     }
 }
 
-template <int P, bool MASKED>
+// POT = false: accelerations only, L^0 is left at zero (see the generated *_forces contractions).
+template <int P, bool MASKED, bool POT>
 __global__ void __launch_bounds__(128) m2l_blocks_f32(TreeView t, const M2LBlock *__restrict__ blocks, int64_t nblocks,
                                                       const float *__restrict__ Ms, float *L, int ncp, float eps_over_L,
                                                       int plummer)
@@ -150,7 +146,8 @@ __global__ void __launch_bounds__(128) m2l_blocks_f32(TreeView t, const M2LBlock
                 // lane j keeps coefficients RL*j .. RL*j + RL - 1
 #pragma unroll
                 for (int k = NC; k < NP; ++k) Lc[k] = 0.f;
-                M2LGen<P>::side_a(D, Ms + ((size_t)ys * 2 + cls) * ncp, rho, reinterpret_cast<float(&)[NC]>(Lc));
+                if (POT) M2LGen<P>::side_a(D, Ms + ((size_t)ys * 2 + cls) * ncp, rho, reinterpret_cast<float(&)[NC]>(Lc));
+                else M2LGen<P>::side_a_forces(D, Ms + ((size_t)ys * 2 + cls) * ncp, rho, reinterpret_cast<float(&)[NC]>(Lc));
                 m2l_halve<NP, 4 * RL>(Lc, lane, 4);
                 m2l_halve<NP, 2 * RL>(Lc, lane, 2);
                 m2l_halve<NP, RL>(Lc, lane, 1);
@@ -166,7 +163,8 @@ __global__ void __launch_bounds__(128) m2l_blocks_f32(TreeView t, const M2LBlock
                 // lane (rr, j) keeps coefficients CL*rr .. CL*rr + CL - 1 of column j
 #pragma unroll
                 for (int k = NC; k < NP; ++k) Lc[k] = 0.f;
-                M2LGen<P>::side_b(D, Ms + ((size_t)xs * 2 + cls) * ncp, reinterpret_cast<float(&)[NC]>(Lc));
+                if (POT) M2LGen<P>::side_b(D, Ms + ((size_t)xs * 2 + cls) * ncp, reinterpret_cast<float(&)[NC]>(Lc));
+                else M2LGen<P>::side_b_forces(D, Ms + ((size_t)xs * 2 + cls) * ncp, reinterpret_cast<float(&)[NC]>(Lc));
                 m2l_halve<NP, 2 * CL>(Lc, lane, 16);
                 m2l_halve<NP, CL>(Lc, lane, 8);
                 if (col_used) {

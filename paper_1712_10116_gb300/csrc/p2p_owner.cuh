@@ -70,7 +70,7 @@ struct OwnerShared {
 
 // Rows i0 .. i0 + 32*ROWS of one phase (0: slow rows, 1: fast rows) against the first ncol staged
 // columns (a multiple of 8).
-template <int KERNEL, int ROWS, bool NEAR>
+template <int KERNEL, int ROWS, bool NEAR, bool POT>
 __device__ __noinline__ void owner_rows(const float4 *__restrict__ pf, const OwnerBatch *ob, int phase, int i0, int nrows,
                                         const float4 *sq, float (*sacc)[4], int ncol, float eps, double *acc4, int n,
                                         int lane)
@@ -131,11 +131,11 @@ __device__ __noinline__ void owner_rows(const float4 *__restrict__ pf, const Own
                 ra[r][0] = fmaf(mq, dx, ra[r][0]);
                 ra[r][1] = fmaf(mq, dy, ra[r][1]);
                 ra[r][2] = fmaf(mq, dz, ra[r][2]);
-                ra[r][3] = fmaf(q.w, ph, ra[r][3]);
+                if (POT) ra[r][3] = fmaf(q.w, ph, ra[r][3]);
                 cx = fmaf(-mp, dx, cx);
                 cy = fmaf(-mp, dy, cy);
                 cz = fmaf(-mp, dz, cz);
-                cp = fmaf(p[r].w, ph, cp);
+                if (POT) cp = fmaf(p[r].w, ph, cp);
             }
             col[4 * c + 0] = cx;
             col[4 * c + 1] = cy;
@@ -162,11 +162,13 @@ __device__ __noinline__ void owner_rows(const float4 *__restrict__ pf, const Own
                         ra[r][0] = fmaf(mq, dx, ra[r][0]);
                         ra[r][1] = fmaf(mq, dy, ra[r][1]);
                         ra[r][2] = fmaf(mq, dz, ra[r][2]);
-                        ra[r][3] = fmaf(q.w, dph, ra[r][3]);
                         atomicAdd(&sacc[j][0], -mp * dx);
                         atomicAdd(&sacc[j][1], -mp * dy);
                         atomicAdd(&sacc[j][2], -mp * dz);
-                        atomicAdd(&sacc[j][3], p[r].w * dph);
+                        if (POT) {
+                            ra[r][3] = fmaf(q.w, dph, ra[r][3]);
+                            atomicAdd(&sacc[j][3], p[r].w * dph);
+                        }
                     }
                 }
             }
@@ -193,7 +195,8 @@ __device__ __noinline__ void owner_rows(const float4 *__restrict__ pf, const Own
     for (int r = 0; r < ROWS; ++r)
         if (gi[r] >= 0)
 #pragma unroll
-            for (int comp = 0; comp < 4; ++comp) atomicAdd(&acc4[(size_t)comp * n + gi[r]], f2d_exact(ra[r][comp]));
+            for (int comp = 0; comp < (POT ? 4 : 3); ++comp)
+                atomicAdd(&acc4[(size_t)comp * n + gi[r]], f2d_exact(ra[r][comp]));
 }
 
 __device__ __forceinline__ int warp_incl_scan(int v, int lane)
@@ -210,7 +213,7 @@ __device__ __forceinline__ int warp_incl_scan(int v, int lane)
 // (ctr[1], starts at zero) so that the load stays balanced whatever the spread of leaf work.  After
 // the units, the same counter hands out the self pairs (A, A): slow rows of A against every particle
 // of A with a larger index, i.e. each slow-slow and slow-fast pair once (p2p_pair_f32, SELF).
-template <int KERNEL, int ROWS>
+template <int KERNEL, int ROWS, bool POT>
 __global__ void __launch_bounds__(256, 2) p2p_owner_f32(TreeView t, int log2L, const uint2 *__restrict__ units,
                                                         uint32_t *ctr, const uint32_t *__restrict__ own_off,
                                                         const uint32_t *__restrict__ own_cnt,
@@ -313,20 +316,20 @@ __global__ void __launch_bounds__(256, 2) p2p_owner_f32(TreeView t, int log2L, c
                 }
                 __syncwarp();
                 for (int i0 = 0; i0 < Ts; i0 += 32 * ROWS) {
-                    if (i0 < nearS) owner_rows<KERNEL, ROWS, true>(pf, ob, 0, i0, Ts, sq, sacc, nt8, eps, acc4, n, lane);
-                    else owner_rows<KERNEL, ROWS, false>(pf, ob, 0, i0, Ts, sq, sacc, nt8, eps, acc4, n, lane);
+                    if (i0 < nearS) owner_rows<KERNEL, ROWS, true, POT>(pf, ob, 0, i0, Ts, sq, sacc, nt8, eps, acc4, n, lane);
+                    else owner_rows<KERNEL, ROWS, false, POT>(pf, ob, 0, i0, Ts, sq, sacc, nt8, eps, acc4, n, lane);
                 }
                 if (nsc > 0)
                     for (int i0 = 0; i0 < Tf; i0 += 32 * ROWS) {
-                        if (i0 < nearF) owner_rows<KERNEL, ROWS, true>(pf, ob, 1, i0, Tf, sq, sacc, ns8, eps, acc4, n, lane);
-                        else owner_rows<KERNEL, ROWS, false>(pf, ob, 1, i0, Tf, sq, sacc, ns8, eps, acc4, n, lane);
+                        if (i0 < nearF) owner_rows<KERNEL, ROWS, true, POT>(pf, ob, 1, i0, Tf, sq, sacc, ns8, eps, acc4, n, lane);
+                        else owner_rows<KERNEL, ROWS, false, POT>(pf, ob, 1, i0, Tf, sq, sacc, ns8, eps, acc4, n, lane);
                     }
                 __syncwarp();
                 for (int j = lane; j < nt8; j += 32) {
                     const int src = j < nsc ? j : (j >= ns8 && j < ns8 + nf ? nsc + j - ns8 : -1);
                     if (src >= 0)
 #pragma unroll
-                        for (int comp = 0; comp < 4; ++comp)
+                        for (int comp = 0; comp < (POT ? 4 : 3); ++comp)
                             atomicAdd(&acc4[(size_t)comp * n + fb + jc + src], f2d_exact(sacc[j][comp]));
                 }
             }
@@ -341,9 +344,10 @@ __global__ void __launch_bounds__(256, 2) p2p_owner_f32(TreeView t, int log2L, c
 namespace tg {
 
 // Every P2P pair in float32, one launch: the distinct leaf pairs grouped by owner, then the self pairs.
+// pot = false: accelerations only (the potential slot of acc4 is left out).
 static tg_status launch_p2p_owner(tg_ctx *c, const TreeView &t, const uint2 *pairs, int64_t npairs,
                                   const uint2 *self_pairs, int64_t nself, const float4 *pf, const int32_t *nslow,
-                                  double *acc4)
+                                  bool pot, double *acc4)
 {
     tg_status st;
     const int ncell = t.ncell;
@@ -377,22 +381,25 @@ static tg_status launch_p2p_owner(tg_ctx *c, const TreeView &t, const uint2 *pai
     const bool plummer = c->prm.kernel == TG_KERNEL_PLUMMER;
     ProfScope ps_(c, TG_K_P2P);
     // two rows per lane: rows are packed densely, so the chunk is full whatever the leaf size
-    static int occ_w = 0, occ_p = 0;
-    int &occ = plummer ? occ_p : occ_w;
+    // occupancy is the same for every instantiation (same registers and shared memory)
+    static int occ = 0;
     if (occ == 0) {
-        cudaError_t e = plummer ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, p2p_owner_f32<TG_KERNEL_PLUMMER, 2>, 256, 0)
-                                : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, p2p_owner_f32<TG_KERNEL_WENDLAND_C2, 2>, 256, 0);
-        if (e != cudaSuccess || occ < 1) occ = 1;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, p2p_owner_f32<TG_KERNEL_WENDLAND_C2, 2, true>, 256, 0) !=
+                cudaSuccess || occ < 1)
+            occ = 1;
     }
     const int grid = c->num_sms * occ;
-    if (plummer)
-        p2p_owner_f32<TG_KERNEL_PLUMMER, 2><<<grid, 256, 0, c->stream>>>(t, c->walk_log2L, units, ctr, own_off, own_cnt,
-                                                                          partners, self_pairs, (uint32_t)nself, pf,
-                                                                          nslow, eps, acc4, t.n, pc);
-    else
-        p2p_owner_f32<TG_KERNEL_WENDLAND_C2, 2><<<grid, 256, 0, c->stream>>>(t, c->walk_log2L, units, ctr, own_off, own_cnt,
-                                                                              partners, self_pairs, (uint32_t)nself,
-                                                                              pf, nslow, eps, acc4, t.n, pc);
+#define TG_OWNER(K, PT)                                                                                           \
+    p2p_owner_f32<K, 2, PT><<<grid, 256, 0, c->stream>>>(t, c->walk_log2L, units, ctr, own_off, own_cnt, partners,  \
+                                                         self_pairs, (uint32_t)nself, pf, nslow, eps, acc4, t.n, pc)
+    if (plummer) {
+        if (pot) TG_OWNER(TG_KERNEL_PLUMMER, true);
+        else TG_OWNER(TG_KERNEL_PLUMMER, false);
+    } else {
+        if (pot) TG_OWNER(TG_KERNEL_WENDLAND_C2, true);
+        else TG_OWNER(TG_KERNEL_WENDLAND_C2, false);
+    }
+#undef TG_OWNER
     return cuda_check(c, cudaGetLastError(), "p2p owner launch");
 }
 

@@ -124,6 +124,12 @@ inline tg_status ensure_t(tg_ctx *c, int slot, size_t count, T **out)
     return s;
 }
 
+// M2L work unit handed over by the walk: the well-separated child pairs of one opened cell pair.
+struct M2LBlock {
+    uint32_t a, b;             // cell pair that was opened (a == b: self pair, only i < j bits set)
+    unsigned long long mask;   // bit 8i + j: pair (child i of a, child j of b) is well separated
+};
+
 // ---- tree.cu
 // Root cube of the n particles pos[q] (q < n, gathered through sub when non-null) -> geom.
 tg_status root_cube(tg_ctx *c, int n, const double *pos, int64_t stride, const int64_t *sub, Geom *d_geom);
@@ -137,6 +143,19 @@ TreeView tree_view(tg_ctx *c, int n, int ncell);
 
 // Device-wide exclusive scan of uint32 (in place allowed); optional total to a device word.
 tg_status exclusive_scan_u32(tg_ctx *c, const uint32_t *in, uint32_t *out, int n, uint32_t *d_total);
+
+// ---- m2l.cu: mutual M2L of the walk's blocks into L (normalised expansions).  pot = false: the
+// float32 kernels leave out the potential term L^0.
+tg_status launch_m2l_f32(tg_ctx *c, const TreeView &t, const M2LBlock *blocks, int64_t nblocks, const float *Ms,
+                         float *L, int p, int nc, int ncp, bool masked, bool pot);
+tg_status launch_m2l_f64(tg_ctx *c, const TreeView &t, const M2LBlock *blocks, int64_t nblocks, const double *Ms,
+                         double *L, int p, int nc, int ncp, bool masked);
+// ---- p2p.cu: mutual P2P of all leaf pairs (distinct pairs and self pairs) into acc4.
+tg_status launch_p2p_f32(tg_ctx *c, const TreeView &t, const uint2 *pairs, int64_t npairs, const uint2 *self_pairs,
+                         int64_t nself, const float4 *pf, const int32_t *nslow, bool pot, double *acc4);
+tg_status launch_p2p_f64(tg_ctx *c, const TreeView &t, const Geom *d_geom, const uint2 *pairs, int64_t npairs,
+                         const uint2 *self_pairs, int64_t nself, const dbl4 *pf, const uint8_t *fs, bool masked,
+                         double *acc4);
 
 // Kernels of tree.cu, also launched by the allocation-free sort in noalloc.cu.
 constexpr int kSortTileItems = 2048;     // items per radix-sort block (256 threads x 8)

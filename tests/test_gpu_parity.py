@@ -156,6 +156,28 @@ def test_fmm_fp32_wide_softening(kind, masked):
     assert np.abs(pot.cpu().numpy() - p_o).max() < FP32_TOL * np.abs(p_o).max()
 
 
+@pytest.mark.parametrize("kind,kernel,p", [("sphere", 0, 6), ("plummer", 1, 5), ("clustered", 0, 4)])
+@pytest.mark.parametrize("masked", [False, True])
+def test_fmm_fp32_forces_only(kind, kernel, p, masked):
+    # accelerations without the potential (what the HHS kicks ask for): the float32 kernels then skip
+    # the potential sums (P2P) and the L^0 term (M2L, L2P); the accelerations must not change
+    n = 9000
+    pos, _, mass = _case(kind, n)
+    fast = ics.random_fast_mask(n, 19) if masked else None
+    prm = tg.Params(p=p, theta=0.5, eps=0.005 if kernel == 0 else 0.01, kernel=kernel, precision=tg.TG_PREC_FP32,
+                    n_crit=64)
+    s = tg.Solver(prm)
+    fs = None if fast is None else _t(fast, torch.uint8)
+    acc_f, pot_f = s.fmm_forces(_t(pos), _t(mass), fs, want_pot=False)
+    acc_p, _ = s.fmm_forces(_t(pos), _t(mass), fs, want_pot=True)
+    assert pot_f is None
+    a_o, _ = oracle.fmm(pos, mass, _oprm(prm), fast)
+    r = _rel(acc_f.cpu().numpy(), a_o, FP32_FLOOR)
+    assert r.max() < FP32_TOL, (r.max(), np.median(r))
+    # same arithmetic for the accelerations in both forms, up to the order of float atomics
+    assert _rel(acc_f.cpu().numpy(), acc_p.cpu().numpy(), FP32_FLOOR).max() < 1e-6
+
+
 @pytest.mark.parametrize("precision", [0, 1])
 def test_momentum_conserved_on_gpu(precision):
     n = 20000
