@@ -191,7 +191,7 @@ tg_status tg_timesteps(tg_ctx *ctx, int64_t n, const double *a_old, const double
  *   cuda_stream  the cudaStream_t the work is enqueued on (NULL = legacy default stream)
  *
  * It allocates nothing (no cudaMalloc, cudaFree or allocating library call).  Its scratch is one
- * file-scope device array of about 6.2 MB that every GPU loading the library holds until the
+ * file-scope device array of about 6.3 MB that every GPU loading the library holds until the
  * process exits.  The first call on a device looks up that array's device address
  * (cudaGetSymbolAddress) with the device current; make that first call before any stream
  * capture.  All calls share the array, so two calls whose work overlaps on the GPU (different

@@ -22,7 +22,7 @@ using namespace tg;
 constexpr int64_t kMaxN = TG_NOALLOC_MAX_N;
 constexpr int kMaxSortBlocks = (int)((kMaxN + kSortTileItems - 1) / kSortTileItems);
 constexpr int kMaxBboxBlocks = 2 * 152;
-constexpr int64_t kHistItems = 256LL * kMaxSortBlocks;
+constexpr int64_t kHistItems = (int64_t)kSortBins * kMaxSortBlocks;
 constexpr int64_t kScanTmpItems = 2 * ((kHistItems + kScanTileItems - 1) / kScanTileItems) + 64;
 
 // byte layout of the scratch array (every part 256-byte aligned)
@@ -137,9 +137,10 @@ extern "C" tg_status tg_morton_sort_noalloc(int64_t n, const double *pos, uint64
     const int nblocks = (ni + kSortTileItems - 1) / kSortTileItems;
     uint64_t *kin = k0, *kout = k1;
     uint32_t *vin = v0, *vout = v1;
-    for (int shift = 0; shift < 64; shift += 8) {
+    for (int pass = 0; pass < kSortPasses; ++pass) {
+        const int shift = pass * kSortBits;
         radix_hist<<<nblocks, 256, 0, s>>>(kin, ni, shift, hist, nblocks);
-        if (scan_with_scratch(s, hist, hist, 256 * nblocks, scan) != cudaSuccess) return TG_ERR_CUDA;
+        if (scan_with_scratch(s, hist, hist, kSortBins * nblocks, scan) != cudaSuccess) return TG_ERR_CUDA;
         radix_scatter<<<nblocks, 256, 0, s>>>(kin, vin, kout, vout, hist, ni, shift, nblocks);
         std::swap(kin, kout);
         std::swap(vin, vout);

@@ -159,6 +159,9 @@ tg_status launch_p2p_f64(tg_ctx *c, const TreeView &t, const Geom *d_geom, const
 
 // Kernels of tree.cu, also launched by the allocation-free sort in noalloc.cu.
 constexpr int kSortTileItems = 2048;     // items per radix-sort block (256 threads x 8)
+constexpr int kSortBits = 9;             // radix digit width: 7 passes cover the 63 key bits
+constexpr int kSortBins = 1 << kSortBits;
+constexpr int kSortPasses = (63 + kSortBits - 1) / kSortBits;
 constexpr int kScanTileItems = 2048;     // items per scan block (512 threads x 4)
 __global__ void scan_tiles(const uint32_t *in, uint32_t *out, uint32_t *tile_sums, int n);
 __global__ void scan_add(uint32_t *out, const uint32_t *tile_pre, int n);

@@ -388,28 +388,38 @@ __global__ void morton_keys(const double *pos, int64_t stride, const int64_t *su
 constexpr int kSortThreads = 256;
 constexpr int kSortItems = 8;
 constexpr int kSortTile = kSortThreads * kSortItems;
+static_assert(kSortBins == 2 * kSortThreads, "the digit scan gives two digits to each thread");
+static_assert(kSortTile == kSortTileItems, "tile size shared with the allocation-free sort");
 
 __global__ void radix_hist(const uint64_t *keys, int n, int shift, uint32_t *hist, int nblocks)
 {
-    __shared__ uint32_t h[256];
-    h[threadIdx.x] = 0;
+    __shared__ uint32_t h[kSortBins];
+    for (int d = threadIdx.x; d < kSortBins; d += blockDim.x) h[d] = 0;
     __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t base = (int64_t)blockIdx.x * kSortTile + warp * 256 + lane;
 #pragma unroll
     for (int r = 0; r < kSortItems; ++r) {
         int64_t idx = base + r * 32;
-        if (idx < n) atomicAdd(&h[(keys[idx] >> shift) & 255u], 1u);
+        if (idx < n) atomicAdd(&h[(keys[idx] >> shift) & (kSortBins - 1u)], 1u);
     }
     __syncthreads();
-    hist[threadIdx.x * nblocks + blockIdx.x] = h[threadIdx.x];
+    for (int d = threadIdx.x; d < kSortBins; d += blockDim.x) hist[d * nblocks + blockIdx.x] = h[d];
 }
 
+// One pass of the stable LSD sort over a tile of kSortTile items.  Ranks: per warp in input order
+// (match_any over the lanes, item r after item r - 1), warps in order.  The tile is then laid out in
+// shared memory in digit order and written out by consecutive threads, so that each digit's run of
+// the tile goes to global memory as one contiguous stretch.
 __global__ void radix_scatter(const uint64_t *keys_in, const uint32_t *vals_in, uint64_t *keys_out,
                               uint32_t *vals_out, const uint32_t *offsets, int n, int shift, int nblocks)
 {
-    __shared__ uint32_t wcount[8][256];
-    for (int i = threadIdx.x; i < 8 * 256; i += kSortThreads) (&wcount[0][0])[i] = 0;
+    __shared__ uint32_t wcount[8][kSortBins];
+    __shared__ uint32_t dstart[kSortBins];
+    __shared__ uint32_t wsum[8];
+    __shared__ uint64_t sk[kSortTile];
+    __shared__ uint32_t sv[kSortTile];
+    for (int i = threadIdx.x; i < 8 * kSortBins; i += kSortThreads) (&wcount[0][0])[i] = 0;
     __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t lt_mask = (1u << lane) - 1u;
@@ -420,9 +430,9 @@ __global__ void radix_scatter(const uint64_t *keys_in, const uint32_t *vals_in, 
     for (int r = 0; r < kSortItems; ++r) {
         int64_t idx = base + r * 32;
         bool valid = idx < n;
-        k[r] = valid ? keys_in[idx] : ~0ull;
+        k[r] = valid ? keys_in[idx] : ~0ull;   // past the end: the largest digit, after every valid item
         v[r] = valid ? vals_in[idx] : 0u;
-        uint32_t d = valid ? (uint32_t)((k[r] >> shift) & 255u) : 255u;
+        uint32_t d = (uint32_t)((k[r] >> shift) & (kSortBins - 1u));
         dig[r] = d;
         uint32_t peers = __match_any_sync(0xffffffffu, d);
         uint32_t lower = peers & lt_mask;
@@ -433,29 +443,54 @@ __global__ void radix_scatter(const uint64_t *keys_in, const uint32_t *vals_in, 
         __syncwarp();
     }
     __syncthreads();
-    {
+    // per digit: exclusive prefix over the warps, and the tile total
+    for (int d = threadIdx.x; d < kSortBins; d += kSortThreads) {
         uint32_t run = 0;
-        const int d = threadIdx.x;
 #pragma unroll
         for (int w = 0; w < 8; ++w) {
-            uint32_t t = wcount[w][d];
+            const uint32_t t = wcount[w][d];
             wcount[w][d] = run;
             run += t;
         }
+        dstart[d] = run;
+    }
+    __syncthreads();
+    // exclusive scan of the tile totals over the digits: thread t owns digits 2t, 2t + 1
+    {
+        const uint32_t a = dstart[2 * threadIdx.x], b = dstart[2 * threadIdx.x + 1];
+        uint32_t incl = a + b;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        if (lane == 31) wsum[warp] = incl;
+        __syncthreads();
+        uint32_t before = 0;
+        for (int w = 0; w < warp; ++w) before += wsum[w];
+        const uint32_t excl = before + incl - (a + b);
+        dstart[2 * threadIdx.x] = excl;
+        dstart[2 * threadIdx.x + 1] = excl + a;
     }
     __syncthreads();
 #pragma unroll
     for (int r = 0; r < kSortItems; ++r) {
-        int64_t idx = base + r * 32;
-        if (idx < n) {
-            uint32_t pos = offsets[dig[r] * nblocks + blockIdx.x] + wcount[warp][dig[r]] + rank[r];
-            keys_out[pos] = k[r];
-            vals_out[pos] = v[r];
-        }
+        const uint32_t lp = dstart[dig[r]] + wcount[warp][dig[r]] + rank[r];
+        sk[lp] = k[r];
+        sv[lp] = v[r];
+    }
+    __syncthreads();
+    const int64_t tile0 = (int64_t)blockIdx.x * kSortTile;
+    const int cnt = (int)(n - tile0 < kSortTile ? n - tile0 : kSortTile);   // valid items: positions [0, cnt)
+    for (int i = threadIdx.x; i < cnt; i += kSortThreads) {
+        const uint64_t key = sk[i];
+        const uint32_t d = (uint32_t)((key >> shift) & (kSortBins - 1u));
+        const uint32_t pos = offsets[d * nblocks + blockIdx.x] + ((uint32_t)i - dstart[d]);
+        keys_out[pos] = key;
+        vals_out[pos] = sv[i];
     }
 }
 
-// ------------------------------------------------------------------ gather
 __global__ void gather_sorted(const uint32_t *perm, const double *pos, int64_t stride, const int64_t *sub,
                               const double *mass, const uint8_t *fast, int n, double *xs, double *ys, double *zs,
                               double *ms, uint8_t *fs)
@@ -480,7 +515,7 @@ tg_status keys_sort_gather(tg_ctx *c, int n, const double *pos, int64_t stride, 
     tg_status st;
     if ((st = ensure_t(c, B_KEYS0, n, &k0)) || (st = ensure_t(c, B_KEYS1, n, &k1)) ||
         (st = ensure_t(c, B_VALS0, n, &v0)) || (st = ensure_t(c, B_VALS1, n, &v1)) ||
-        (st = ensure_t(c, B_HIST, (size_t)256 * nblocks + 1, &hist)))
+        (st = ensure_t(c, B_HIST, (size_t)kSortBins * nblocks + 1, &hist)))
         return st;
     {
         ProfScope ps_(c, TG_K_TREE);
@@ -488,12 +523,13 @@ tg_status keys_sort_gather(tg_ctx *c, int n, const double *pos, int64_t stride, 
     }
     uint64_t *kin = k0, *kout = k1;
     uint32_t *vin = v0, *vout = v1;
-    for (int shift = 0; shift < 64; shift += 8) {
+    for (int pass = 0; pass < kSortPasses; ++pass) {
+        const int shift = pass * kSortBits;
         {
             ProfScope ps_(c, TG_K_TREE);
             radix_hist<<<nblocks, kSortThreads, 0, c->stream>>>(kin, n, shift, hist, nblocks);
         }
-        if ((st = exclusive_scan_u32(c, hist, hist, 256 * nblocks, nullptr))) return st;
+        if ((st = exclusive_scan_u32(c, hist, hist, kSortBins * nblocks, nullptr))) return st;
         {
             ProfScope ps_(c, TG_K_TREE);
             radix_scatter<<<nblocks, kSortThreads, 0, c->stream>>>(kin, vin, kout, vout, hist, n, shift, nblocks);
@@ -501,7 +537,12 @@ tg_status keys_sort_gather(tg_ctx *c, int n, const double *pos, int64_t stride, 
         std::swap(kin, kout);
         std::swap(vin, vout);
     }
-    // 8 passes: the sorted data is back in k0/v0
+    // the sorted keys and permutation live in the B_KEYS0 / B_VALS0 slots from here on
+    if (kin != k0) {
+        std::swap(c->buf[B_KEYS0], c->buf[B_KEYS1]);
+        std::swap(c->buf[B_VALS0], c->buf[B_VALS1]);
+        v0 = vin;
+    }
     double *xs, *ys, *zs, *ms;
     uint8_t *fs;
     if ((st = ensure_t(c, B_XS, n, &xs)) || (st = ensure_t(c, B_YS, n, &ys)) || (st = ensure_t(c, B_ZS, n, &zs)) ||
