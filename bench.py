@@ -41,7 +41,9 @@ def parse():
     ap.add_argument("--n", type=int, default=1 << 20)
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-sample", type=int, default=512)
+    ap.add_argument("--no-fp64-plain", action="store_true",
+                    help="skip the one-step timing of the plain float64 GPU path beside the float32 one")
+    ap.add_argument("--cpu-sample", type=int, default=3072)
     ap.add_argument("--n-crit", type=int, default=PARAMS["n_crit"])
     ap.add_argument("--eval-only", action="store_true",
                     help="run warmup + steps single FMM evaluations of the workload (for profiler captures)")
@@ -250,6 +252,30 @@ def run_ours(args):
     h2d = 2 * 3 * n * 8
     d2h = 2 * 3 * n * 8
 
+    # the plain float64 path on the same initial state (one rung-0 step, after its own hhs_init):
+    # same tree, walk and schedule, float64 P2P tiles and the generic float64 M2L, no potential skipping
+    fp64 = None
+    if rank == 0 and prec == tg.TG_PREC_FP32 and not args.no_fp64_plain:
+        s64 = tg.Solver(tg.Params(precision=tg.TG_PREC_FP64, **dict(PARAMS, n_crit=args.n_crit)), stream)
+        P64, V64 = P0.clone(), V0.clone()
+        s64.hhs_init(P64, V64, M)
+        tg.tg_hhs_set_accel(s64.ctx, aold0, acur0)
+        tg.tg_reset_stats(s64.ctx)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        flush.zero_()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        s64.hhs_step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms64 = e0.elapsed_time(e1)
+        sinks64 = s64.stats()["sink_forces"]
+        fp64 = {"ms_per_step": ms64, "value": sinks64 / (ms64 / 1e3), "unit": "particle-forces/s",
+                "steps": 1, "speedup_of_fp32_path": (sinks / t_max) / (sinks64 / (ms64 / 1e3)),
+                "note": "plain float64 path: same tree, walk and HHS schedule, float64 P2P (block per leaf pair) "
+                        "and generic float64 M2L; one rung-0 step from the same state"}
+        s64.close()
+
     if rank != 0:
         solver.close()
         if world > 1:
@@ -313,6 +339,7 @@ def run_ours(args):
         "kernels_ms_per_step": {k: v["ms"] / args.steps for k, v in kernels.items() if v["ms"] > 0},
         "stage_ms_one_step_all_timed": breakdown,
         "roofline": roof,
+        "fp64_plain_gpu": fp64,
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_sinks / e2e_t, "unit": "particle-forces/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},

@@ -36,7 +36,8 @@ typedef enum {
     TG_ERR_TIMEOUT = -4,    /* a bounded device-side wait gave up                           */
     TG_ERR_NONFINITE = -5,  /* non-finite positions or masses                               */
     TG_ERR_CAPACITY = -6,   /* an internal list exceeded its limit even after regrowth      */
-    TG_ERR_STATE = -7       /* call out of order (e.g. tg_hhs_step before tg_hhs_init)       */
+    TG_ERR_STATE = -7,      /* call out of order (e.g. tg_hhs_step before tg_hhs_init)       */
+    TG_ERR_IO = -8          /* checkpoint file cannot be written, read, or fails its check     */
 } tg_status;
 
 typedef enum {
@@ -133,6 +134,23 @@ tg_status tg_hhs_set_accel(tg_ctx *ctx, const double *a_old, const double *a_cur
  * sum m v^2/2 + sum m phi/2 (phi from a fresh all-from-all evaluation), out[7] = time.
  * float64 device reductions.  Synchronising; out is host memory. */
 tg_status tg_diagnostics(tg_ctx *ctx, double out[8]);
+
+/* Checkpoint and resume of the HHS run (the integrator state of Algorithms 1-3 between two
+ * rung-0 steps; the paper has no file format, this one is the library's own).
+ * tg_checkpoint writes, to the host file `path`, the bound system and its integrator state:
+ * n, the tg_params of the context, the time, pos (3n), vel (3n), mass (n), |a_old| (n),
+ * |a_current| (n) (float64) and the rungs (n, int32), followed by a 64-bit FNV-1a checksum of
+ * everything before it.  It goes through a temporary file renamed over `path`.  Synchronising;
+ * the device arrays are left unchanged.  TG_ERR_STATE before tg_hhs_init, TG_ERR_IO if the file
+ * cannot be written.
+ * tg_restore reads such a file into a context created with equal tg_params on which
+ * tg_hhs_init has bound a system of the same n: it overwrites pos and vel (the caller's arrays
+ * bound by tg_hhs_init), the integrator state and the time.  The masses in the file must equal
+ * the bound masses bit for bit.  TG_ERR_IO for a missing, short or corrupt file; TG_ERR_STATE
+ * before tg_hhs_init or when n, the parameters or the masses differ (nothing is changed then).
+ * Synchronising. */
+tg_status tg_checkpoint(tg_ctx *ctx, const char *path);
+tg_status tg_restore(tg_ctx *ctx, const char *path);
 
 /* ---- test hooks (synchronising; outputs are HOST memory sized by the *_count calls) ---- */
 

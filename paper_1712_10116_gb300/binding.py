@@ -24,7 +24,8 @@ TG_PREC_FP64 = 0
 TG_PREC_FP32 = 1
 
 STATUS = {0: "TG_OK", -1: "TG_ERR_ARG", -2: "TG_ERR_OOM", -3: "TG_ERR_CUDA", -4: "TG_ERR_TIMEOUT",
-          -5: "TG_ERR_NONFINITE", -6: "TG_ERR_CAPACITY", -7: "TG_ERR_STATE"}
+          -5: "TG_ERR_NONFINITE", -6: "TG_ERR_CAPACITY", -7: "TG_ERR_STATE",
+          -8: "TG_ERR_IO"}
 
 
 class TGError(RuntimeError):
@@ -101,6 +102,8 @@ def load() -> C.CDLL:
             L.tg_hhs_state.argtypes = [_vp, _vp, _vp, _vp]
             L.tg_hhs_set_accel.argtypes = [_vp, _vp, _vp]
             L.tg_diagnostics.argtypes = [_vp, C.POINTER(C.c_double)]
+            L.tg_checkpoint.argtypes = [_vp, C.c_char_p]
+            L.tg_restore.argtypes = [_vp, C.c_char_p]
             L.tg_tree_info.argtypes = [_vp, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(_i64),
                                        C.POINTER(_i64)]
             L.tg_get_tree.argtypes = [_vp] * 8
@@ -216,6 +219,14 @@ def tg_diagnostics(ctx) -> np.ndarray:
     return np.array(out[:])
 
 
+def tg_checkpoint(ctx, path) -> None:
+    _check(ctx, load().tg_checkpoint(ctx, os.fsencode(path)))
+
+
+def tg_restore(ctx, path) -> None:
+    _check(ctx, load().tg_restore(ctx, os.fsencode(path)))
+
+
 def tg_tree_info(ctx):
     lo = (C.c_double * 3)()
     L = C.c_double()
@@ -306,6 +317,12 @@ class Solver:
 
     def hhs_step(self):
         tg_hhs_step(self.ctx)
+
+    def checkpoint(self, path):
+        tg_checkpoint(self.ctx, path)
+
+    def restore(self, path):
+        tg_restore(self.ctx, path)
 
     def diagnostics(self):
         return tg_diagnostics(self.ctx)

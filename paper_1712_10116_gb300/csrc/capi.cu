@@ -1,7 +1,10 @@
 // capi.cu -- the extern "C" entry points declared in include/taichi_gb.h.
 #include <cmath>
+#include <cstdio>
 #include <cstring>
 #include <new>
+#include <string>
+#include <vector>
 
 #include "tg_common.cuh"
 #include "m2l_sym.cuh"
@@ -387,6 +390,147 @@ tg_status tg_timesteps(tg_ctx *c, int64_t n, const double *a_old, const double *
     if (!check_device_ptr(a_old) || !check_device_ptr(a_cur) || !check_device_ptr(dt) || !check_device_ptr(rung))
         return set_err(c, TG_ERR_ARG, "device arrays expected");
     return timesteps(c, n, a_old, a_cur, dt, rung);
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------ checkpoint / restore
+namespace {
+
+const char kCkptMagic[8] = {'T', 'G', 'C', 'K', 'P', 'T', '0', '1'};
+
+struct Fnv64 {
+    uint64_t h = 1469598103934665603ull;
+    void add(const void *p, size_t n)
+    {
+        const unsigned char *b = static_cast<const unsigned char *>(p);
+        for (size_t i = 0; i < n; ++i) {
+            h ^= b[i];
+            h *= 1099511628211ull;
+        }
+    }
+};
+
+bool same_params(const tg_params &a, const tg_params &b)
+{
+    return a.p == b.p && a.n_crit == b.n_crit && a.kernel == b.kernel && a.precision == b.precision &&
+           a.max_level == b.max_level && a.k_max == b.k_max && a.theta == b.theta && a.kappa == b.kappa &&
+           a.eps == b.eps && a.eta == b.eta && a.dt_max == b.dt_max;
+}
+
+}  // namespace
+
+extern "C" {
+
+tg_status tg_checkpoint(tg_ctx *c, const char *path)
+{
+    tg_status st = begin(c);
+    if (st) return st;
+    if (!path) return set_err(c, TG_ERR_ARG, "tg_checkpoint: path is NULL");
+    if (c->hhs_n <= 0) return set_err(c, TG_ERR_STATE, "tg_checkpoint before tg_hhs_init");
+    const size_t n = (size_t)c->hhs_n;
+    std::vector<double> pos(3 * n), vel(3 * n), mass(n), a_old(n), a_cur(n);
+    std::vector<int32_t> rung(n);
+    cudaMemcpyAsync(pos.data(), c->hhs_pos, 3 * n * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+    cudaMemcpyAsync(vel.data(), c->hhs_vel, 3 * n * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+    cudaMemcpyAsync(mass.data(), c->hhs_mass, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+    cudaMemcpyAsync(a_old.data(), c->buf[B_HHS_AOLD].p, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+    cudaMemcpyAsync(a_cur.data(), c->buf[B_HHS_ACUR].p, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+    cudaMemcpyAsync(rung.data(), c->buf[B_HHS_RUNG].p, n * sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream);
+    if ((st = cuda_check(c, cudaStreamSynchronize(c->stream), "tg_checkpoint"))) return st;
+    const std::string tmp = std::string(path) + ".tmp";
+    FILE *f = std::fopen(tmp.c_str(), "wb");
+    if (!f) return set_err(c, TG_ERR_IO, "tg_checkpoint: cannot open %s", tmp.c_str());
+    Fnv64 h;
+    bool ok = true;
+    auto put = [&](const void *p, size_t bytes) {
+        if (!ok) return;
+        h.add(p, bytes);
+        ok = std::fwrite(p, 1, bytes, f) == bytes;
+    };
+    const int64_t n64 = (int64_t)n;
+    put(kCkptMagic, sizeof(kCkptMagic));
+    put(&n64, sizeof(n64));
+    put(&c->prm, sizeof(c->prm));
+    put(&c->hhs_time, sizeof(double));
+    put(pos.data(), pos.size() * sizeof(double));
+    put(vel.data(), vel.size() * sizeof(double));
+    put(mass.data(), mass.size() * sizeof(double));
+    put(a_old.data(), a_old.size() * sizeof(double));
+    put(a_cur.data(), a_cur.size() * sizeof(double));
+    put(rung.data(), rung.size() * sizeof(int32_t));
+    const uint64_t sum = h.h;
+    ok = ok && std::fwrite(&sum, 1, sizeof(sum), f) == sizeof(sum);
+    ok = (std::fclose(f) == 0) && ok;
+    if (!ok || std::rename(tmp.c_str(), path) != 0) {
+        std::remove(tmp.c_str());
+        return set_err(c, TG_ERR_IO, "tg_checkpoint: cannot write %s", path);
+    }
+    return TG_OK;
+}
+
+tg_status tg_restore(tg_ctx *c, const char *path)
+{
+    tg_status st = begin(c);
+    if (st) return st;
+    if (!path) return set_err(c, TG_ERR_ARG, "tg_restore: path is NULL");
+    if (c->hhs_n <= 0) return set_err(c, TG_ERR_STATE, "tg_restore before tg_hhs_init");
+    FILE *f = std::fopen(path, "rb");
+    if (!f) return set_err(c, TG_ERR_IO, "tg_restore: cannot open %s", path);
+    std::vector<unsigned char> data;
+    {
+        unsigned char chunk[1 << 16];
+        size_t got;
+        while ((got = std::fread(chunk, 1, sizeof(chunk), f)) > 0) data.insert(data.end(), chunk, chunk + got);
+        std::fclose(f);
+    }
+    const size_t head = sizeof(kCkptMagic) + sizeof(int64_t) + sizeof(tg_params) + sizeof(double);
+    if (data.size() < head + sizeof(uint64_t) || std::memcmp(data.data(), kCkptMagic, sizeof(kCkptMagic)) != 0)
+        return set_err(c, TG_ERR_IO, "tg_restore: %s is not a checkpoint", path);
+    int64_t n64;
+    tg_params prm;
+    double time;
+    std::memcpy(&n64, data.data() + 8, sizeof(n64));
+    std::memcpy(&prm, data.data() + 16, sizeof(prm));
+    std::memcpy(&time, data.data() + 16 + sizeof(prm), sizeof(time));
+    if (n64 <= 0 || n64 > INT32_MAX / 4) return set_err(c, TG_ERR_IO, "tg_restore: corrupt size in %s", path);
+    const size_t n = (size_t)n64;
+    const size_t body = n * (3 + 3 + 1 + 1 + 1) * sizeof(double) + n * sizeof(int32_t);
+    if (data.size() != head + body + sizeof(uint64_t)) return set_err(c, TG_ERR_IO, "tg_restore: %s is truncated", path);
+    Fnv64 h;
+    h.add(data.data(), head + body);
+    uint64_t sum;
+    std::memcpy(&sum, data.data() + head + body, sizeof(sum));
+    if (sum != h.h) return set_err(c, TG_ERR_IO, "tg_restore: checksum mismatch in %s", path);
+    if (n64 != c->hhs_n) return set_err(c, TG_ERR_STATE, "tg_restore: file holds n = %lld, bound n = %lld",
+                                         (long long)n64, (long long)c->hhs_n);
+    if (!same_params(prm, c->prm)) return set_err(c, TG_ERR_STATE, "tg_restore: parameters differ from the context's");
+    const unsigned char *p = data.data() + head;
+    const double *pos = reinterpret_cast<const double *>(p);
+    const double *vel = pos + 3 * n;
+    const double *mass = vel + 3 * n;
+    const double *a_old = mass + n;
+    const double *a_cur = a_old + n;
+    std::vector<int32_t> rung(n);
+    std::memcpy(rung.data(), reinterpret_cast<const unsigned char *>(a_cur + n), n * sizeof(int32_t));
+    std::vector<double> bound_mass(n);
+    cudaMemcpyAsync(bound_mass.data(), c->hhs_mass, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+    if ((st = cuda_check(c, cudaStreamSynchronize(c->stream), "tg_restore"))) return st;
+    if (std::memcmp(bound_mass.data(), mass, n * sizeof(double)) != 0)
+        return set_err(c, TG_ERR_STATE, "tg_restore: the bound masses differ from the file's");
+    // the file body is not guaranteed to be 8-byte aligned in the vector: stage through aligned copies
+    std::vector<double> pv(8 * n);
+    std::memcpy(pv.data(), p, 3 * n * sizeof(double));
+    std::memcpy(pv.data() + 3 * n, p + 3 * n * sizeof(double), 3 * n * sizeof(double));
+    std::memcpy(pv.data() + 6 * n, p + 7 * n * sizeof(double), 2 * n * sizeof(double));
+    cudaMemcpyAsync(c->hhs_pos, pv.data(), 3 * n * sizeof(double), cudaMemcpyHostToDevice, c->stream);
+    cudaMemcpyAsync(c->hhs_vel, pv.data() + 3 * n, 3 * n * sizeof(double), cudaMemcpyHostToDevice, c->stream);
+    cudaMemcpyAsync(c->buf[B_HHS_AOLD].p, pv.data() + 6 * n, n * sizeof(double), cudaMemcpyHostToDevice, c->stream);
+    cudaMemcpyAsync(c->buf[B_HHS_ACUR].p, pv.data() + 7 * n, n * sizeof(double), cudaMemcpyHostToDevice, c->stream);
+    cudaMemcpyAsync(c->buf[B_HHS_RUNG].p, rung.data(), n * sizeof(int32_t), cudaMemcpyHostToDevice, c->stream);
+    if ((st = cuda_check(c, cudaStreamSynchronize(c->stream), "tg_restore"))) return st;
+    c->hhs_time = time;
+    return TG_OK;
 }
 
 }  // extern "C"
