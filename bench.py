@@ -59,6 +59,20 @@ def workload(n, seed=1002):
 PARAMS = dict(p=6, theta=0.5, eps=0.005, kernel=0, n_crit=96, kappa=1.0, eta=0.025, dt_max=1.0 / 16, k_max=10)
 
 
+def combine_ranks(t_dev, sinks, device, world):
+    """Whole-job figures of the replicas: the slowest rank's timed seconds and the particle-forces of
+    all ranks (every rank integrates its own system)."""
+    if world <= 1:
+        return t_dev, sinks
+    import torch
+    import torch.distributed as dist
+    mx = torch.tensor([t_dev], dtype=torch.float64, device=device)
+    sm = torch.tensor([sinks], dtype=torch.float64, device=device)
+    dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+    dist.all_reduce(sm, op=dist.ReduceOp.SUM)
+    return float(mx[0]), float(sm[0])
+
+
 # ---------------------------------------------------------------- clocks sampler
 class Clocks:
     def __init__(self):
@@ -213,14 +227,7 @@ def run_ours(args):
     tg.tg_set_profiling(solver.ctx, 0)
     t_dev = sum(step_ms) / 1e3
     sinks = stats["sink_forces"]
-    if world > 1:
-        tt = torch.tensor([t_dev, float(sinks)], dtype=torch.float64, device=dev)
-        mx = tt.clone()
-        dist.all_reduce(mx[:1], op=dist.ReduceOp.MAX)
-        dist.all_reduce(tt[1:], op=dist.ReduceOp.SUM)
-        t_max, sinks_all = float(mx[0]), float(tt[1])
-    else:
-        t_max, sinks_all = t_dev, float(sinks)
+    t_max, sinks_all = combine_ranks(t_dev, float(sinks), dev, world)
     value = sinks_all / t_max
 
     # accuracy gate: one float32 evaluation of the initial state vs float64 direct summation
