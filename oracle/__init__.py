@@ -46,7 +46,7 @@ class Params(C.Structure):
 
 
 class HHSParams(C.Structure):
-    _fields_ = [("eta", C.c_double), ("dt_max", C.c_double), ("k_max", C.c_int)]
+    _fields_ = [("eta", C.c_double), ("dt_max", C.c_double), ("k_max", C.c_int), ("eta_tot", C.c_double)]
 
 
 class HHSStats(C.Structure):
@@ -102,10 +102,12 @@ def lib():
                                          _d, _d, _d, _vp]
             L.orc_timestep.argtypes = [C.c_double, C.c_double, C.c_double, C.c_double]
             L.orc_timestep.restype = C.c_double
+            L.orc_timestep_tot.argtypes = [C.c_double] * 6
+            L.orc_timestep_tot.restype = C.c_double
             L.orc_rung.argtypes = [C.c_double, C.c_double, C.c_int]
-            L.orc_hhs_init.argtypes = [C.c_int64, _d, _d, _d, _d, C.POINTER(Params), _d, _d]
+            L.orc_hhs_init.argtypes = [C.c_int64, _d, _d, _d, _d, C.POINTER(Params), _d, _d, _d]
             L.orc_hhs_step.argtypes = [C.c_int64, _d, _d, _d, _d, _d, _d, _d, C.POINTER(Params),
-                                       C.POINTER(HHSParams), _d, _d, _i32, C.POINTER(HHSStats), _vp, C.c_int32]
+                                       C.POINTER(HHSParams), _d, _d, _d, _i32, C.POINTER(HHSStats), _vp, C.c_int32]
             L.orc_diagnostics.argtypes = [C.c_int64, _d, _d, _d, _d, _d, _d, _d, _vp, _d]
             _lib = L
     return _lib
@@ -323,6 +325,10 @@ def timestep(eta, eps, a_old, a_cur) -> float:
     return lib().orc_timestep(eta, eps, a_old, a_cur)
 
 
+def timestep_tot(eta, eps, a_old, a_cur, eta_tot, a_tot) -> float:
+    return lib().orc_timestep_tot(eta, eps, a_old, a_cur, eta_tot, a_tot)
+
+
 def rung(dt_i, dt_max, k_max) -> int:
     return lib().orc_rung(dt_i, dt_max, k_max)
 
@@ -330,20 +336,21 @@ def rung(dt_i, dt_max, k_max) -> int:
 class HHS:
     """State of one HOLD-integrated system (Algorithms 1-3) on the oracle."""
 
-    def __init__(self, pos, vel, mass, prm: Params, eta=0.025, dt_max=1.0 / 64, k_max=10):
+    def __init__(self, pos, vel, mass, prm: Params, eta=0.025, dt_max=1.0 / 64, k_max=10, eta_tot=0.0):
         self.pos = np.array(pos, dtype=np.float64, order="C")
         self.vel = np.array(vel, dtype=np.float64, order="C")
         self.mass = _f64(mass).copy()
         self.n = self.mass.shape[0]
         self.prm = prm
-        self.hp = HHSParams(eta=eta, dt_max=dt_max, k_max=k_max)
+        self.hp = HHSParams(eta=eta, dt_max=dt_max, k_max=k_max, eta_tot=eta_tot)
         self.a_old = np.zeros(self.n)
         self.a_cur = np.zeros(self.n)
+        self.a_tot = np.zeros(self.n)
         self.rung = np.zeros(self.n, np.int32)
         self.t = 0.0
         p = self.pos
         rc = lib().orc_hhs_init(self.n, _p(p[0]), _p(p[1]), _p(p[2]), _p(self.mass), C.byref(prm),
-                                _p(self.a_old), _p(self.a_cur))
+                                _p(self.a_old), _p(self.a_cur), _p(self.a_tot))
         if rc != 0:
             raise ValueError("orc_hhs_init failed")
 
@@ -353,7 +360,7 @@ class HHS:
         p, v = self.pos, self.vel
         rc = lib().orc_hhs_step(self.n, _p(p[0]), _p(p[1]), _p(p[2]), _p(v[0]), _p(v[1]), _p(v[2]),
                                 _p(self.mass), C.byref(self.prm), C.byref(self.hp), _p(self.a_old),
-                                _p(self.a_cur), _p(self.rung, _i32), C.byref(stats),
+                                _p(self.a_cur), _p(self.a_tot), _p(self.rung, _i32), C.byref(stats),
                                 trace.ctypes.data_as(_vp) if trace_cap > 0 else None, trace_cap)
         if rc != 0:
             raise ValueError("orc_hhs_step failed")

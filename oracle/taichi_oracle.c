@@ -825,6 +825,17 @@ double orc_timestep(double eta, double eps, double a_old, double a_cur)
     return sqrt(eta * eps / a);
 }
 
+/* Eq. (9): a minimum timestep from the total acceleration, imposed on the function above */
+double orc_timestep_tot(double eta, double eps, double a_old, double a_cur, double eta_tot, double a_tot)
+{
+    double dt = orc_timestep(eta, eps, a_old, a_cur);
+    if (eta_tot > 0.0 && a_tot > 0.0) {
+        double dt_tot = sqrt(eta_tot * eps / a_tot);
+        if (dt_tot < dt) dt = dt_tot;
+    }
+    return dt;
+}
+
 /* smallest k with dt_max / 2^k <= dt_i, capped at k_max */
 int orc_rung(double dt_i, double dt_max, int k_max)
 {
@@ -839,7 +850,7 @@ typedef struct {
     const double *m;
     const orc_params *prm;
     const orc_hhs_params *hp;
-    double *a_old, *a_cur, *dt;
+    double *a_old, *a_cur, *a_tot, *dt;
     int32_t *rung;
     orc_hhs_stats *stats;
     int64_t *trace;
@@ -886,6 +897,9 @@ static void kick(hhs_ctx *h, int rung, const int64_t *s1, int64_t n1, const int6
     h->stats->poisson_calls++;
     h->stats->sink_forces += n1;
     trace_push(h, kick_fs ? 0 : 1, rung, n1, kick_fs ? n2 : nj);
+    /* rung 0, second kickFS2S: the whole system with all masses, |a|_tot of every particle (Eq. 9) */
+    if (h->a_tot && !kick_fs && second && rung == 0)
+        for (q = 0; q < nj; ++q) h->a_tot[src[q]] = sqrt(ax[q] * ax[q] + ay[q] * ay[q] + az[q] * az[q]);
     for (q = 0; q < nj; ++q) {
         if (!in1[q]) continue;
         int64_t i = src[q];
@@ -923,7 +937,9 @@ static void evolve_hold(hhs_ctx *h, int rung, const int64_t *sys, int64_t ns, do
     if (calc)
         for (int64_t q = 0; q < ns; ++q) {
             int64_t i = sys[q];
-            h->dt[i] = orc_timestep(h->hp->eta, h->prm->eps, h->a_old[i], h->a_cur[i]);
+            h->dt[i] = h->a_tot ? orc_timestep_tot(h->hp->eta, h->prm->eps, h->a_old[i], h->a_cur[i],
+                                                   h->hp->eta_tot, h->a_tot[i])
+                                : orc_timestep(h->hp->eta, h->prm->eps, h->a_old[i], h->a_cur[i]);
         }
     /* split_slow_fast: slow = {dt_i >= dt}; at the deepest rung everything is slow */
     int64_t *S = (int64_t *)malloc(sizeof(int64_t) * (ns > 0 ? ns : 1));
@@ -943,7 +959,7 @@ static void evolve_hold(hhs_ctx *h, int rung, const int64_t *sys, int64_t ns, do
 }
 
 int orc_hhs_init(int64_t n, const double *x, const double *y, const double *z, const double *m,
-                 const orc_params *prm, double *a_old, double *a_cur)
+                 const orc_params *prm, double *a_old, double *a_cur, double *a_tot)
 {
     double *ax = (double *)malloc(sizeof(double) * (n > 0 ? n : 1));
     double *ay = (double *)malloc(sizeof(double) * (n > 0 ? n : 1));
@@ -952,6 +968,7 @@ int orc_hhs_init(int64_t n, const double *x, const double *y, const double *z, c
     for (int64_t i = 0; i < n; ++i) {
         a_old[i] = 0.0;
         a_cur[i] = sqrt(ax[i] * ax[i] + ay[i] * ay[i] + az[i] * az[i]);
+        if (a_tot) a_tot[i] = a_cur[i];
     }
     free(ax); free(ay); free(az);
     return rc;
@@ -959,7 +976,7 @@ int orc_hhs_init(int64_t n, const double *x, const double *y, const double *z, c
 
 int orc_hhs_step(int64_t n, double *x, double *y, double *z, double *vx, double *vy, double *vz,
                  const double *m, const orc_params *prm, const orc_hhs_params *hp,
-                 double *a_old, double *a_cur, int32_t *rung_out,
+                 double *a_old, double *a_cur, double *a_tot, int32_t *rung_out,
                  orc_hhs_stats *stats, int64_t *trace, int32_t trace_cap)
 {
     hhs_ctx h;
@@ -967,7 +984,7 @@ int orc_hhs_step(int64_t n, double *x, double *y, double *z, double *vx, double 
     orc_hhs_stats local;
     memset(&local, 0, sizeof(local));
     h.n = n; h.x = x; h.y = y; h.z = z; h.vx = vx; h.vy = vy; h.vz = vz; h.m = m;
-    h.prm = prm; h.hp = hp; h.a_old = a_old; h.a_cur = a_cur;
+    h.prm = prm; h.hp = hp; h.a_old = a_old; h.a_cur = a_cur; h.a_tot = a_tot;
     h.dt = (double *)malloc(sizeof(double) * (n > 0 ? n : 1));
     h.rung = rung_out ? rung_out : (int32_t *)malloc(sizeof(int32_t) * (n > 0 ? n : 1));
     h.stats = stats ? stats : &local;

@@ -36,6 +36,7 @@ typedef struct {
     double eta;       /* timestep parameter of dt_i = sqrt(eta*eps/|a|)           */
     double dt_max;    /* step of rung 0                                            */
     int k_max;        /* deepest rung                                              */
+    double eta_tot;   /* eta_1 of the Eq. (9) minimum-timestep constraint; 0 = off */
 } orc_hhs_params;
 
 #ifdef __cplusplus
@@ -94,6 +95,9 @@ int orc_fmm_sample(int64_t n, const double *x, const double *y, const double *z,
 
 /* Timestep function of Sec. 2.2 and the rung of a particle. */
 double orc_timestep(double eta, double eps, double a_old, double a_cur);
+/* The same with the minimum-timestep constraint of Eq. (9): min(dt_i, sqrt(eta_tot eps / |a|_tot)),
+ * |a|_tot the acceleration from all particles; eta_tot <= 0 or |a|_tot <= 0 leaves dt_i alone. */
+double orc_timestep_tot(double eta, double eps, double a_old, double a_cur, double eta_tot, double a_tot);
 int orc_rung(double dt_i, double dt_max, int k_max);
 
 /* HHS / HOLD integrator, Algorithms 1-3, with the two masked Poisson calls per kick pair. */
@@ -105,14 +109,17 @@ typedef struct {
     int32_t trace_len;       /* entries written to trace                                    */
 } orc_hhs_stats;
 
+/* a_tot (nullable): |a| of every particle from all masses, as kept for Eq. (9). */
 int orc_hhs_init(int64_t n, const double *x, const double *y, const double *z, const double *m,
-                 const orc_params *prm, double *a_old, double *a_cur);
+                 const orc_params *prm, double *a_old, double *a_cur, double *a_tot);
 /* One rung-0 step of EVOLVE_HOLD.  trace (nullable, capacity trace_cap entries of 4 int64):
  * (kind, rung, n_sinks, n_sources) per Poisson call, kind 0 = kickS2F, 1 = kickFS2S; drifts are
- * recorded as kind 2 with (2, rung, n_slow, 0). */
+ * recorded as kind 2 with (2, rung, n_slow, 0).  a_tot (nullable): the second kickFS2S of rung 0
+ * passes the whole system to the Poisson solver with all masses, and records |a| of every particle
+ * of it there; with hp->eta_tot > 0 the timesteps then follow orc_timestep_tot. */
 int orc_hhs_step(int64_t n, double *x, double *y, double *z, double *vx, double *vy, double *vz,
                  const double *m, const orc_params *prm, const orc_hhs_params *hp,
-                 double *a_old, double *a_cur, int32_t *rung_out,
+                 double *a_old, double *a_cur, double *a_tot, int32_t *rung_out,
                  orc_hhs_stats *stats, int64_t *trace, int32_t trace_cap);
 
 void orc_diagnostics(int64_t n, const double *x, const double *y, const double *z,

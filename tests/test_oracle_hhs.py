@@ -134,3 +134,50 @@ def test_momentum_conserved_over_multirung_run():
         P = (h.vel * m).sum(1)
         assert np.abs(P - P0).max() < 1e-14 * max(scale, 1.0)
     assert len(rungs) >= 3  # the run really used several rungs
+
+
+# ---------------------------------------------------------------- Eq. (9): minimum timestep from |a|_tot
+def test_eq9_timestep_exact_values():
+    # eta * eps = 1/4 and |a_old| + |a_cur| = 4: the default timestep is sqrt(1/16) = 1/4 exactly
+    assert oracle.timestep_tot(0.5, 0.5, 1.0, 3.0, 0.0, 16.0) == 0.25          # constraint off
+    assert oracle.timestep_tot(0.5, 0.5, 1.0, 3.0, 0.5, 16.0) == 0.125         # sqrt(1/64) binds
+    assert oracle.timestep_tot(0.5, 0.5, 1.0, 3.0, 0.5, 1.0) == 0.25           # sqrt(1/4) = 1/2 does not
+    assert oracle.timestep_tot(0.5, 0.5, 1.0, 3.0, 0.5, 0.0) == 0.25           # no total acceleration yet
+    assert oracle.timestep_tot(0.5, 0.5, 0.0, 0.0, 0.5, 4.0) == 0.25           # only the constraint is finite
+
+
+def _plummer_run(eta_tot, steps=2, k_max=6, n=400):
+    pos, vel, m = ics.plummer(n, 1001)
+    prm = oracle.params(p=4, theta=0.5, eps=0.01, kernel=oracle.PLUMMER, n_crit=16)
+    h = oracle.HHS(pos, vel, m, prm, eta=0.025, dt_max=1.0 / 16, k_max=k_max, eta_tot=eta_tot)
+    rungs = []
+    for _ in range(steps):
+        h.step()
+        rungs.append(h.rung.copy())
+    return h, rungs
+
+
+def test_eq9_constraint_that_never_binds_changes_nothing():
+    h0, r0 = _plummer_run(0.0)
+    h1, r1 = _plummer_run(1e9)
+    assert np.array_equal(h0.pos, h1.pos) and np.array_equal(h0.vel, h1.vel)
+    assert all(np.array_equal(a, b) for a, b in zip(r0, r1))
+
+
+def test_eq9_binding_constraint_deepens_rungs():
+    _, r0 = _plummer_run(0.0)
+    _, r1 = _plummer_run(0.0025)
+    assert all(np.all(b >= a) for a, b in zip(r0, r1))
+    assert any(np.any(b > a) for a, b in zip(r0, r1))
+
+
+def test_eq9_records_the_total_acceleration_at_rung_0():
+    # k_max = 0: the second kickFS2S of rung 0 sees the whole system at the end-of-step positions
+    pos, vel, m = ics.plummer(300, 1004)
+    prm = oracle.params(p=4, theta=0.5, eps=0.01, kernel=oracle.PLUMMER, n_crit=16)
+    h = oracle.HHS(pos, vel, m, prm, eta=0.025, dt_max=1.0 / 64, k_max=0, eta_tot=0.01)
+    a0, _ = oracle.fmm(pos, m, prm)
+    assert np.array_equal(h.a_tot, np.sqrt((a0 ** 2).sum(0)))                # from the initial evaluation
+    h.step()
+    a1, _ = oracle.fmm(h.pos, m, prm)
+    assert np.allclose(h.a_tot, np.sqrt((a1 ** 2).sum(0)), rtol=1e-14, atol=0)
