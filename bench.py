@@ -41,6 +41,8 @@ def parse():
     ap.add_argument("--n", type=int, default=1 << 20)
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--eta-tot", type=float, default=0.0,
+                    help="eta_1 of the Eq. (9) minimum timestep from the total acceleration (0 = off)")
     ap.add_argument("--no-fp64-plain", action="store_true",
                     help="skip the one-step timing of the plain float64 GPU path beside the float32 one")
     ap.add_argument("--cpu-sample", type=int, default=3072)
@@ -174,7 +176,7 @@ def run_ours(args):
     # replicas only: each rank integrates its own independent system (seed per rank)
     pos0, vel0, mass0 = workload(n, seed=1002 + rank)
     prec = tg.TG_PREC_FP32 if args.precision == "fp32" else tg.TG_PREC_FP64
-    prm = tg.Params(precision=prec, **dict(PARAMS, n_crit=args.n_crit))
+    prm = tg.Params(precision=prec, **dict(PARAMS, n_crit=args.n_crit, eta_tot=args.eta_tot))
     solver = tg.Solver(prm, stream)
     P0 = torch.tensor(pos0, device=dev)
     V0 = torch.tensor(vel0, device=dev)
@@ -182,13 +184,13 @@ def run_ours(args):
     P = P0.clone()
     V = V0.clone()
     solver.hhs_init(P, V, M)
-    _, aold0, acur0 = tg.tg_hhs_state(solver.ctx, n, dev)
+    _, aold0, acur0, atot0 = tg.tg_hhs_state(solver.ctx, n, dev, with_total=True)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # 256 MB > 129 MB L2
 
     def reset():
         P.copy_(P0)
         V.copy_(V0)
-        tg.tg_hhs_set_accel(solver.ctx, aold0, acur0)
+        tg.tg_hhs_set_accel(solver.ctx, aold0, acur0, atot0)
 
     d_start = solver.diagnostics()
     for _ in range(args.warmup):
@@ -249,7 +251,7 @@ def run_ours(args):
     for _ in range(e2e_steps):
         P.copy_(hP, non_blocking=True)
         V.copy_(hV, non_blocking=True)
-        tg.tg_hhs_set_accel(solver.ctx, aold0, acur0)
+        tg.tg_hhs_set_accel(solver.ctx, aold0, acur0, atot0)
         solver.hhs_step()
         oP.copy_(P, non_blocking=True)
         oV.copy_(V, non_blocking=True)
@@ -263,10 +265,11 @@ def run_ours(args):
     # same tree, walk and schedule, float64 P2P tiles and the generic float64 M2L, no potential skipping
     fp64 = None
     if rank == 0 and prec == tg.TG_PREC_FP32 and not args.no_fp64_plain:
-        s64 = tg.Solver(tg.Params(precision=tg.TG_PREC_FP64, **dict(PARAMS, n_crit=args.n_crit)), stream)
+        s64 = tg.Solver(tg.Params(precision=tg.TG_PREC_FP64, **dict(PARAMS, n_crit=args.n_crit, eta_tot=args.eta_tot)),
+                        stream)
         P64, V64 = P0.clone(), V0.clone()
         s64.hhs_init(P64, V64, M)
-        tg.tg_hhs_set_accel(s64.ctx, aold0, acur0)
+        tg.tg_hhs_set_accel(s64.ctx, aold0, acur0, atot0)
         tg.tg_reset_stats(s64.ctx)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         flush.zero_()
@@ -335,7 +338,8 @@ def run_ours(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32" if prec == tg.TG_PREC_FP32 else "f64",
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "n": n, "l2": "flushed (256 MB write) between timed steps",
-                   "parallelism": f"replicas x{world}", "kappa": PARAMS["kappa"], "n_crit": PARAMS["n_crit"]},
+                   "parallelism": f"replicas x{world}", "kappa": PARAMS["kappa"], "n_crit": args.n_crit,
+                   "eta_tot": args.eta_tot},
         "accuracy": {"median_force_err_vs_fp64_direct": float(np.median(err)),
                      "p99_force_err": float(np.percentile(err, 99)), "sample_sinks": int(sample.numel()),
                      "momentum_drift_one_step": float(np.abs(d_end[:3] - d_start[:3]).max()),

@@ -63,6 +63,9 @@ typedef struct {
     double eps;       /* softening length, > 0                                               */
     double eta;       /* timestep parameter: dt_i = sqrt(eta * eps / |a|), Sec. 2.2          */
     double dt_max;    /* step of rung 0                                                      */
+    double eta_tot;   /* eta_1 of the minimum-timestep constraint of Eq. (9), >= 0; 0 = off:  */
+                      /* dt_i = min(dt_i, sqrt(eta_tot * eps / |a|_tot,i)), |a|_tot from all  */
+                      /* masses, recorded at the second kickFS2S of rung 0 (the whole system) */
 } tg_params;
 
 typedef struct tg_ctx tg_ctx;
@@ -123,11 +126,11 @@ tg_status tg_hhs_init(tg_ctx *ctx, int64_t n, double *pos, double *vel, const do
  * slow/fast split, KDK (Algorithm 2) with the kickS2F/kickFS2S pairs of Algorithm 3, drifts.
  * Synchronising (the recursion reads the set sizes of each split). */
 tg_status tg_hhs_step(tg_ctx *ctx);
-/* Per-particle HHS state (device outputs, each nullable): rung (int32 n), |a_old| and
- * |a_current| (float64 n).  Synchronising. */
-tg_status tg_hhs_state(tg_ctx *ctx, int32_t *rung, double *a_old, double *a_cur);
-/* Set the per-particle |a_old| and |a_current| (device float64 n each). */
-tg_status tg_hhs_set_accel(tg_ctx *ctx, const double *a_old, const double *a_cur);
+/* Per-particle HHS state (device outputs, each nullable): rung (int32 n), |a_old|, |a_current|
+ * and |a|_tot of Eq. (9) (float64 n).  Synchronising. */
+tg_status tg_hhs_state(tg_ctx *ctx, int32_t *rung, double *a_old, double *a_cur, double *a_tot);
+/* Set the per-particle |a_old|, |a_current| and (nullable) |a|_tot (device float64 n each). */
+tg_status tg_hhs_set_accel(tg_ctx *ctx, const double *a_old, const double *a_cur, const double *a_tot);
 
 /* Conservation diagnostics of the bound HHS system (Sec. 3.2): out[0..2] = total momentum
  * sum m v, out[3..5] = angular momentum sum m x cross v, out[6] = total energy
@@ -139,7 +142,7 @@ tg_status tg_diagnostics(tg_ctx *ctx, double out[8]);
  * rung-0 steps; the paper has no file format, this one is the library's own).
  * tg_checkpoint writes, to the host file `path`, the bound system and its integrator state:
  * n, the tg_params of the context, the time, pos (3n), vel (3n), mass (n), |a_old| (n),
- * |a_current| (n) (float64) and the rungs (n, int32), followed by a 64-bit FNV-1a checksum of
+ * |a_current| (n), |a|_tot (n) (float64) and the rungs (n, int32), followed by a 64-bit FNV-1a checksum of
  * everything before it.  It goes through a temporary file renamed over `path`.  Synchronising;
  * the device arrays are left unchanged.  TG_ERR_STATE before tg_hhs_init, TG_ERR_IO if the file
  * cannot be written.
@@ -189,9 +192,10 @@ tg_status tg_set_profiling(tg_ctx *ctx, int level);
 /* Totals since the last tg_reset_stats.  Synchronising. */
 tg_status tg_get_profile(tg_ctx *ctx, tg_profile *out);
 
-/* Timestep kernel alone (Sec. 2.2): dt[i] = sqrt(eta*eps/(a_old[i] + a_cur[i])) and
- * rung[i] = smallest k with dt_max/2^k <= dt[i], capped at k_max.  Device arrays. */
-tg_status tg_timesteps(tg_ctx *ctx, int64_t n, const double *a_old, const double *a_cur,
+/* Timestep kernel alone (Sec. 2.2): dt[i] = sqrt(eta*eps/(a_old[i] + a_cur[i])), with a_tot
+ * given (nullable) and params.eta_tot > 0 capped by Eq. (9): min(dt[i], sqrt(eta_tot*eps/a_tot[i])),
+ * and rung[i] = smallest k with dt_max/2^k <= dt[i], capped at k_max.  Device arrays. */
+tg_status tg_timesteps(tg_ctx *ctx, int64_t n, const double *a_old, const double *a_cur, const double *a_tot,
                        double *dt, int32_t *rung);
 
 /* ---- allocation-free variant (the paper has no counterpart; this is a library service) ----

@@ -37,7 +37,7 @@ class TGError(RuntimeError):
 class tg_params(C.Structure):
     _fields_ = [("p", C.c_int), ("n_crit", C.c_int), ("kernel", C.c_int), ("precision", C.c_int),
                 ("max_level", C.c_int), ("k_max", C.c_int), ("theta", C.c_double), ("kappa", C.c_double),
-                ("eps", C.c_double), ("eta", C.c_double), ("dt_max", C.c_double)]
+                ("eps", C.c_double), ("eta", C.c_double), ("dt_max", C.c_double), ("eta_tot", C.c_double)]
 
 
 class tg_stats(C.Structure):
@@ -67,11 +67,12 @@ class Params:
     eta: float = 0.02
     dt_max: float = 1.0 / 64
     k_max: int = 10
+    eta_tot: float = 0.0   # Eq. (9) minimum-timestep constraint, 0 = off
 
     def to_c(self) -> tg_params:
         return tg_params(p=self.p, n_crit=self.n_crit, kernel=self.kernel, precision=self.precision,
                          max_level=self.max_level, k_max=self.k_max, theta=self.theta, kappa=self.kappa,
-                         eps=self.eps, eta=self.eta, dt_max=self.dt_max)
+                         eps=self.eps, eta=self.eta, dt_max=self.dt_max, eta_tot=self.eta_tot)
 
 
 _lib = None
@@ -99,8 +100,8 @@ def load() -> C.CDLL:
             L.tg_direct_forces.argtypes = [_vp, _i64, _vp, _vp, _vp, _i64, _vp, _vp, _vp]
             L.tg_hhs_init.argtypes = [_vp, _i64, _vp, _vp, _vp]
             L.tg_hhs_step.argtypes = [_vp]
-            L.tg_hhs_state.argtypes = [_vp, _vp, _vp, _vp]
-            L.tg_hhs_set_accel.argtypes = [_vp, _vp, _vp]
+            L.tg_hhs_state.argtypes = [_vp, _vp, _vp, _vp, _vp]
+            L.tg_hhs_set_accel.argtypes = [_vp, _vp, _vp, _vp]
             L.tg_diagnostics.argtypes = [_vp, C.POINTER(C.c_double)]
             L.tg_checkpoint.argtypes = [_vp, C.c_char_p]
             L.tg_restore.argtypes = [_vp, C.c_char_p]
@@ -109,7 +110,7 @@ def load() -> C.CDLL:
             L.tg_get_tree.argtypes = [_vp] * 8
             L.tg_list_counts.argtypes = [_vp, C.POINTER(_i64), C.POINTER(_i64)]
             L.tg_get_lists.argtypes = [_vp] * 5
-            L.tg_timesteps.argtypes = [_vp, _i64, _vp, _vp, _vp, _vp]
+            L.tg_timesteps.argtypes = [_vp, _i64, _vp, _vp, _vp, _vp, _vp]
             L.tg_morton_sort_noalloc.argtypes = [_i64, _vp, _vp, _vp, _vp]
             L.tg_morton_sort_noalloc.restype = C.c_int
             L.tg_set_profiling.argtypes = [_vp, C.c_int]
@@ -201,16 +202,17 @@ def tg_hhs_step(ctx):
     _check(ctx, load().tg_hhs_step(ctx))
 
 
-def tg_hhs_state(ctx, n: int, device="cuda"):
+def tg_hhs_state(ctx, n: int, device="cuda", with_total=False):
     rung = torch.empty(n, dtype=torch.int32, device=device)
     a_old = torch.empty(n, dtype=torch.float64, device=device)
     a_cur = torch.empty(n, dtype=torch.float64, device=device)
-    _check(ctx, load().tg_hhs_state(ctx, _ptr(rung), _ptr(a_old), _ptr(a_cur)))
-    return rung, a_old, a_cur
+    a_tot = torch.empty(n, dtype=torch.float64, device=device) if with_total else None
+    _check(ctx, load().tg_hhs_state(ctx, _ptr(rung), _ptr(a_old), _ptr(a_cur), _ptr(a_tot)))
+    return (rung, a_old, a_cur, a_tot) if with_total else (rung, a_old, a_cur)
 
 
-def tg_hhs_set_accel(ctx, a_old, a_cur):
-    _check(ctx, load().tg_hhs_set_accel(ctx, _ptr(a_old), _ptr(a_cur)))
+def tg_hhs_set_accel(ctx, a_old, a_cur, a_tot=None):
+    _check(ctx, load().tg_hhs_set_accel(ctx, _ptr(a_old), _ptr(a_cur), _ptr(a_tot)))
 
 
 def tg_diagnostics(ctx) -> np.ndarray:
@@ -290,11 +292,11 @@ def tg_morton_sort_noalloc(pos, keys_out=None, perm_out=None, stream=None):
     return keys_out, perm_out
 
 
-def tg_timesteps(ctx, a_old, a_cur):
+def tg_timesteps(ctx, a_old, a_cur, a_tot=None):
     n = a_old.shape[0]
     dt = torch.empty(n, dtype=torch.float64, device=a_old.device)
     rung = torch.empty(n, dtype=torch.int32, device=a_old.device)
-    _check(ctx, load().tg_timesteps(ctx, n, _ptr(a_old), _ptr(a_cur), _ptr(dt), _ptr(rung)))
+    _check(ctx, load().tg_timesteps(ctx, n, _ptr(a_old), _ptr(a_cur), _ptr(a_tot), _ptr(dt), _ptr(rung)))
     return dt, rung
 
 

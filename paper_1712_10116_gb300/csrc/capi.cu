@@ -30,6 +30,7 @@ tg_status validate(const tg_params *p, std::string &why)
     else if (!(p->eps > 0.0) || !std::isfinite(p->eps)) why = "eps must be > 0";
     else if (!(p->eta > 0.0) || !std::isfinite(p->eta)) why = "eta must be > 0";
     else if (!(p->dt_max > 0.0) || !std::isfinite(p->dt_max)) why = "dt_max must be > 0";
+    else if (!(p->eta_tot >= 0.0) || !std::isfinite(p->eta_tot)) why = "eta_tot must be >= 0";
     return why.empty() ? TG_OK : TG_ERR_ARG;
 }
 
@@ -227,7 +228,7 @@ tg_status tg_hhs_step(tg_ctx *c)
     return hhs_step(c);
 }
 
-tg_status tg_hhs_state(tg_ctx *c, int32_t *rung, double *a_old, double *a_cur)
+tg_status tg_hhs_state(tg_ctx *c, int32_t *rung, double *a_old, double *a_cur, double *a_tot)
 {
     tg_status st = begin(c);
     if (st) return st;
@@ -236,18 +237,21 @@ tg_status tg_hhs_state(tg_ctx *c, int32_t *rung, double *a_old, double *a_cur)
     if (rung) cudaMemcpyAsync(rung, c->buf[B_HHS_RUNG].p, n * sizeof(int32_t), cudaMemcpyDeviceToDevice, c->stream);
     if (a_old) cudaMemcpyAsync(a_old, c->buf[B_HHS_AOLD].p, n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream);
     if (a_cur) cudaMemcpyAsync(a_cur, c->buf[B_HHS_ACUR].p, n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream);
+    if (a_tot) cudaMemcpyAsync(a_tot, c->buf[B_HHS_ATOT].p, n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream);
     return cuda_check(c, cudaStreamSynchronize(c->stream), "tg_hhs_state");
 }
 
-tg_status tg_hhs_set_accel(tg_ctx *c, const double *a_old, const double *a_cur)
+tg_status tg_hhs_set_accel(tg_ctx *c, const double *a_old, const double *a_cur, const double *a_tot)
 {
     tg_status st = begin(c);
     if (st) return st;
     if (c->hhs_n <= 0) return set_err(c, TG_ERR_STATE, "tg_hhs_set_accel before tg_hhs_init");
-    if (!check_device_ptr(a_old) || !check_device_ptr(a_cur)) return set_err(c, TG_ERR_ARG, "device arrays expected");
+    if (!check_device_ptr(a_old) || !check_device_ptr(a_cur) || (a_tot && !check_device_ptr(a_tot)))
+        return set_err(c, TG_ERR_ARG, "device arrays expected");
     const size_t n = (size_t)c->hhs_n;
     cudaMemcpyAsync(c->buf[B_HHS_AOLD].p, a_old, n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream);
     cudaMemcpyAsync(c->buf[B_HHS_ACUR].p, a_cur, n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream);
+    if (a_tot) cudaMemcpyAsync(c->buf[B_HHS_ATOT].p, a_tot, n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream);
     return cuda_check(c, cudaGetLastError(), "tg_hhs_set_accel");
 }
 
@@ -381,15 +385,17 @@ tg_status tg_get_lists(tg_ctx *c, int64_t *m2l_a, int64_t *m2l_b, int64_t *p2p_a
     return TG_OK;
 }
 
-tg_status tg_timesteps(tg_ctx *c, int64_t n, const double *a_old, const double *a_cur, double *dt, int32_t *rung)
+tg_status tg_timesteps(tg_ctx *c, int64_t n, const double *a_old, const double *a_cur, const double *a_tot, double *dt,
+                       int32_t *rung)
 {
     tg_status st = begin(c);
     if (st) return st;
     if (n < 0) return set_err(c, TG_ERR_ARG, "n < 0");
     if (n == 0) return TG_OK;
-    if (!check_device_ptr(a_old) || !check_device_ptr(a_cur) || !check_device_ptr(dt) || !check_device_ptr(rung))
+    if (!check_device_ptr(a_old) || !check_device_ptr(a_cur) || !check_device_ptr(dt) || !check_device_ptr(rung) ||
+        (a_tot && !check_device_ptr(a_tot)))
         return set_err(c, TG_ERR_ARG, "device arrays expected");
-    return timesteps(c, n, a_old, a_cur, dt, rung);
+    return timesteps(c, n, a_old, a_cur, a_tot, dt, rung);
 }
 
 }  // extern "C"
@@ -397,7 +403,7 @@ tg_status tg_timesteps(tg_ctx *c, int64_t n, const double *a_old, const double *
 // ------------------------------------------------------------------ checkpoint / restore
 namespace {
 
-const char kCkptMagic[8] = {'T', 'G', 'C', 'K', 'P', 'T', '0', '1'};
+const char kCkptMagic[8] = {'T', 'G', 'C', 'K', 'P', 'T', '0', '2'};
 
 struct Fnv64 {
     uint64_t h = 1469598103934665603ull;
@@ -415,7 +421,7 @@ bool same_params(const tg_params &a, const tg_params &b)
 {
     return a.p == b.p && a.n_crit == b.n_crit && a.kernel == b.kernel && a.precision == b.precision &&
            a.max_level == b.max_level && a.k_max == b.k_max && a.theta == b.theta && a.kappa == b.kappa &&
-           a.eps == b.eps && a.eta == b.eta && a.dt_max == b.dt_max;
+           a.eps == b.eps && a.eta == b.eta && a.dt_max == b.dt_max && a.eta_tot == b.eta_tot;
 }
 
 }  // namespace
@@ -429,13 +435,14 @@ tg_status tg_checkpoint(tg_ctx *c, const char *path)
     if (!path) return set_err(c, TG_ERR_ARG, "tg_checkpoint: path is NULL");
     if (c->hhs_n <= 0) return set_err(c, TG_ERR_STATE, "tg_checkpoint before tg_hhs_init");
     const size_t n = (size_t)c->hhs_n;
-    std::vector<double> pos(3 * n), vel(3 * n), mass(n), a_old(n), a_cur(n);
+    std::vector<double> pos(3 * n), vel(3 * n), mass(n), a_old(n), a_cur(n), a_tot(n);
     std::vector<int32_t> rung(n);
     cudaMemcpyAsync(pos.data(), c->hhs_pos, 3 * n * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
     cudaMemcpyAsync(vel.data(), c->hhs_vel, 3 * n * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
     cudaMemcpyAsync(mass.data(), c->hhs_mass, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
     cudaMemcpyAsync(a_old.data(), c->buf[B_HHS_AOLD].p, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
     cudaMemcpyAsync(a_cur.data(), c->buf[B_HHS_ACUR].p, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+    cudaMemcpyAsync(a_tot.data(), c->buf[B_HHS_ATOT].p, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
     cudaMemcpyAsync(rung.data(), c->buf[B_HHS_RUNG].p, n * sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream);
     if ((st = cuda_check(c, cudaStreamSynchronize(c->stream), "tg_checkpoint"))) return st;
     const std::string tmp = std::string(path) + ".tmp";
@@ -458,6 +465,7 @@ tg_status tg_checkpoint(tg_ctx *c, const char *path)
     put(mass.data(), mass.size() * sizeof(double));
     put(a_old.data(), a_old.size() * sizeof(double));
     put(a_cur.data(), a_cur.size() * sizeof(double));
+    put(a_tot.data(), a_tot.size() * sizeof(double));
     put(rung.data(), rung.size() * sizeof(int32_t));
     const uint64_t sum = h.h;
     ok = ok && std::fwrite(&sum, 1, sizeof(sum), f) == sizeof(sum);
@@ -495,7 +503,7 @@ tg_status tg_restore(tg_ctx *c, const char *path)
     std::memcpy(&time, data.data() + 16 + sizeof(prm), sizeof(time));
     if (n64 <= 0 || n64 > INT32_MAX / 4) return set_err(c, TG_ERR_IO, "tg_restore: corrupt size in %s", path);
     const size_t n = (size_t)n64;
-    const size_t body = n * (3 + 3 + 1 + 1 + 1) * sizeof(double) + n * sizeof(int32_t);
+    const size_t body = n * (3 + 3 + 1 + 1 + 1 + 1) * sizeof(double) + n * sizeof(int32_t);
     if (data.size() != head + body + sizeof(uint64_t)) return set_err(c, TG_ERR_IO, "tg_restore: %s is truncated", path);
     Fnv64 h;
     h.add(data.data(), head + body);
@@ -511,22 +519,24 @@ tg_status tg_restore(tg_ctx *c, const char *path)
     const double *mass = vel + 3 * n;
     const double *a_old = mass + n;
     const double *a_cur = a_old + n;
+    const double *a_tot = a_cur + n;
     std::vector<int32_t> rung(n);
-    std::memcpy(rung.data(), reinterpret_cast<const unsigned char *>(a_cur + n), n * sizeof(int32_t));
+    std::memcpy(rung.data(), reinterpret_cast<const unsigned char *>(a_tot + n), n * sizeof(int32_t));
     std::vector<double> bound_mass(n);
     cudaMemcpyAsync(bound_mass.data(), c->hhs_mass, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
     if ((st = cuda_check(c, cudaStreamSynchronize(c->stream), "tg_restore"))) return st;
     if (std::memcmp(bound_mass.data(), mass, n * sizeof(double)) != 0)
         return set_err(c, TG_ERR_STATE, "tg_restore: the bound masses differ from the file's");
     // the file body is not guaranteed to be 8-byte aligned in the vector: stage through aligned copies
-    std::vector<double> pv(8 * n);
+    std::vector<double> pv(9 * n);
     std::memcpy(pv.data(), p, 3 * n * sizeof(double));
     std::memcpy(pv.data() + 3 * n, p + 3 * n * sizeof(double), 3 * n * sizeof(double));
-    std::memcpy(pv.data() + 6 * n, p + 7 * n * sizeof(double), 2 * n * sizeof(double));
+    std::memcpy(pv.data() + 6 * n, p + 7 * n * sizeof(double), 3 * n * sizeof(double));
     cudaMemcpyAsync(c->hhs_pos, pv.data(), 3 * n * sizeof(double), cudaMemcpyHostToDevice, c->stream);
     cudaMemcpyAsync(c->hhs_vel, pv.data() + 3 * n, 3 * n * sizeof(double), cudaMemcpyHostToDevice, c->stream);
     cudaMemcpyAsync(c->buf[B_HHS_AOLD].p, pv.data() + 6 * n, n * sizeof(double), cudaMemcpyHostToDevice, c->stream);
     cudaMemcpyAsync(c->buf[B_HHS_ACUR].p, pv.data() + 7 * n, n * sizeof(double), cudaMemcpyHostToDevice, c->stream);
+    cudaMemcpyAsync(c->buf[B_HHS_ATOT].p, pv.data() + 8 * n, n * sizeof(double), cudaMemcpyHostToDevice, c->stream);
     cudaMemcpyAsync(c->buf[B_HHS_RUNG].p, rung.data(), n * sizeof(int32_t), cudaMemcpyHostToDevice, c->stream);
     if ((st = cuda_check(c, cudaStreamSynchronize(c->stream), "tg_restore"))) return st;
     c->hhs_time = time;

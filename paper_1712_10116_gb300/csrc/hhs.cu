@@ -1,5 +1,6 @@
 // hhs.cu -- HOLD integrator with individual timesteps (Zhu 2017, Sec. 2.2, Algorithms 1-3):
-// timestep function dt_i = sqrt(eta eps / (|a_old| + |a_current|)), stable slow/fast split at
+// timestep function dt_i = sqrt(eta eps / (|a_old| + |a_current|)) (optionally capped by the
+// minimum timestep of Eq. 9 from the total acceleration), stable slow/fast split at
 // the pivot step of each rung, KDK with the kickS2F / kickFS2S pairs, drifts, and the
 // conservation diagnostics of Sec. 3.2.
 //
@@ -13,13 +14,38 @@ namespace tg {
 
 // ------------------------------------------------------------------ timestep and split
 // rung k pivot step dt_k = dt_max / 2^k; slow = {dt_i >= dt_k} (everything at k = k_max)
+// dt_i of Sec. 2.2, capped by Eq. (9) when a_tot is given and eta_tot_eps > 0 (same IEEE operations
+// as the float64 reference: eta*eps on the host, one division, one square root)
+__device__ __forceinline__ double timestep_of(double a_old, double a_cur, double eta_eps, const double *a_tot,
+                                              double eta_tot_eps, int64_t i)
+{
+    const double a = __dadd_rn(a_old, a_cur);
+    double d = (a > 0.0) ? sqrt(__ddiv_rn(eta_eps, a)) : INFINITY;
+    if (a_tot && eta_tot_eps > 0.0) {
+        const double at = a_tot[i];
+        if (at > 0.0) {
+            const double dt_tot = sqrt(__ddiv_rn(eta_tot_eps, at));
+            if (dt_tot < d) d = dt_tot;
+        }
+    }
+    return d;
+}
+
 __global__ void hhs_timestep(int64_t ns, const int64_t *sys, const double *a_old, const double *a_cur, double eta_eps,
-                             double *dt)
+                             const double *a_tot, double eta_tot_eps, double *dt)
 {
     for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < ns; q += (int64_t)gridDim.x * blockDim.x) {
         const int64_t i = sys ? sys[q] : q;
-        const double a = __dadd_rn(a_old[i], a_cur[i]);
-        dt[i] = (a > 0.0) ? sqrt(__ddiv_rn(eta_eps, a)) : INFINITY;
+        dt[i] = timestep_of(a_old[i], a_cur[i], eta_eps, a_tot, eta_tot_eps, i);
+    }
+}
+
+// |a|_tot of Eq. (9) for every member of the system from an all-masses evaluation
+__global__ void hhs_record_total(int64_t ns, const int64_t *sys, const double *acc, double *a_tot)
+{
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < ns; q += (int64_t)gridDim.x * blockDim.x) {
+        const double ax = acc[q], ay = acc[ns + q], az = acc[2 * ns + q];
+        a_tot[sys ? sys[q] : q] = sqrt(ax * ax + ay * ay + az * az);
     }
 }
 
@@ -82,12 +108,13 @@ __global__ void hhs_iota(int64_t n, int64_t *idx)
     for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x) idx[q] = q;
 }
 
-__global__ void hhs_init_accel(int64_t n, const double *acc, double *a_old, double *a_cur)
+__global__ void hhs_init_accel(int64_t n, const double *acc, double *a_old, double *a_cur, double *a_tot)
 {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const double ax = acc[i], ay = acc[n + i], az = acc[2 * n + i];
         a_old[i] = 0.0;
         a_cur[i] = sqrt(ax * ax + ay * ay + az * az);
+        a_tot[i] = a_cur[i];
     }
 }
 
@@ -104,7 +131,7 @@ struct Sched {
     tg_ctx *c;
     int64_t n;
     std::vector<Level> lv;
-    double *a_old, *a_cur, *dt, *acc;
+    double *a_old, *a_cur, *a_tot, *dt, *acc;
     int32_t *rung;
     int64_t *all;
 };
@@ -142,6 +169,14 @@ static tg_status kick_pair(Sched &s, int k, int64_t ns, int64_t nS, int64_t nF, 
         hhs_kick<<<grid_for(ns, 256), 256, 0, c->stream>>>(ns, L.sys, nF > 0 ? L.fast : nullptr, s.acc, 0.5 * dt, second,
                                                            s.n, c->hhs_vel, s.a_old, s.a_cur);
     }
+    if (k == 0 && second && c->prm.eta_tot > 0.0) {
+        // Eq. (9): the second kickFS2S of rung 0 passes the whole system with all masses to the
+        // Poisson solver; with a fast set the kick pair above masked F-F, so evaluate once more
+        if (nF > 0 && (st = fmm_eval(c, (int)ns, c->hhs_pos, s.n, L.sys, c->hhs_mass, nullptr, s.acc, ns, nullptr, false)))
+            return st;
+        ProfScope ps_(c, TG_K_HHS);
+        hhs_record_total<<<grid_for(ns, 256), 256, 0, c->stream>>>(ns, L.sys, s.acc, s.a_tot);
+    }
     return cuda_check(c, cudaGetLastError(), "kick");
 }
 
@@ -155,7 +190,7 @@ static tg_status evolve_hold(Sched &s, int k, int64_t ns, double dt, int calc)
         {
             ProfScope ps_(c, TG_K_HHS);
             hhs_timestep<<<grid_for(ns, 256), 256, 0, c->stream>>>(ns, L.sys, s.a_old, s.a_cur, c->prm.eta * c->prm.eps,
-                                                                   s.dt);
+                                                                   s.a_tot, c->prm.eta_tot * c->prm.eps, s.dt);
         }
     {
         ProfScope ps_(c, TG_K_HHS);
@@ -196,6 +231,7 @@ static tg_status make_sched(tg_ctx *c, Sched &s)
     s.c = c;
     s.n = c->hhs_n;
     if ((st = ensure_t(c, B_HHS_AOLD, s.n, &s.a_old)) || (st = ensure_t(c, B_HHS_ACUR, s.n, &s.a_cur)) ||
+        (st = ensure_t(c, B_HHS_ATOT, s.n, &s.a_tot)) ||
         (st = ensure_t(c, B_HHS_DT, s.n, &s.dt)) || (st = ensure_t(c, B_HHS_RUNG, s.n, &s.rung)) ||
         (st = ensure_t(c, B_SUB_ACC, 3 * s.n, &s.acc)))
         return st;
@@ -211,7 +247,7 @@ tg_status hhs_init(tg_ctx *c)
         return st;
     {
         ProfScope ps_(c, TG_K_HHS);
-        hhs_init_accel<<<grid_for(s.n, 256), 256, 0, c->stream>>>(s.n, s.acc, s.a_old, s.a_cur);
+        hhs_init_accel<<<grid_for(s.n, 256), 256, 0, c->stream>>>(s.n, s.acc, s.a_old, s.a_cur, s.a_tot);
     }
     cudaMemsetAsync(s.rung, 0, sizeof(int32_t) * s.n, c->stream);
     c->hhs_time = 0.0;
@@ -234,12 +270,11 @@ tg_status hhs_step(tg_ctx *c)
     return cuda_check(c, e, "hhs step");
 }
 
-__global__ void timestep_rungs(int64_t n, const double *a_old, const double *a_cur, double eta_eps, double dt_max,
-                               int k_max, double *dt, int32_t *rung)
+__global__ void timestep_rungs(int64_t n, const double *a_old, const double *a_cur, double eta_eps, const double *a_tot,
+                               double eta_tot_eps, double dt_max, int k_max, double *dt, int32_t *rung)
 {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const double a = __dadd_rn(a_old[i], a_cur[i]);
-        const double d = (a > 0.0) ? sqrt(__ddiv_rn(eta_eps, a)) : INFINITY;
+        const double d = timestep_of(a_old[i], a_cur[i], eta_eps, a_tot, eta_tot_eps, i);
         int k = 0;
         while (k < k_max && !(d >= ldexp(dt_max, -k))) ++k;
         dt[i] = d;
@@ -247,12 +282,14 @@ __global__ void timestep_rungs(int64_t n, const double *a_old, const double *a_c
     }
 }
 
-tg_status timesteps(tg_ctx *c, int64_t n, const double *a_old, const double *a_cur, double *dt, int32_t *rung)
+tg_status timesteps(tg_ctx *c, int64_t n, const double *a_old, const double *a_cur, const double *a_tot, double *dt,
+                    int32_t *rung)
 {
     {
         ProfScope ps_(c, TG_K_HHS);
-        timestep_rungs<<<grid_for(n, 256), 256, 0, c->stream>>>(n, a_old, a_cur, c->prm.eta * c->prm.eps, c->prm.dt_max,
-                                                              c->prm.k_max, dt, rung);
+        timestep_rungs<<<grid_for(n, 256), 256, 0, c->stream>>>(n, a_old, a_cur, c->prm.eta * c->prm.eps, a_tot,
+                                                              c->prm.eta_tot * c->prm.eps, c->prm.dt_max, c->prm.k_max,
+                                                              dt, rung);
     }
     return cuda_check(c, cudaGetLastError(), "timesteps");
 }

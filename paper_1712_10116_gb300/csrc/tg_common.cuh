@@ -105,7 +105,7 @@ enum Slot {
     B_C_TMP0, B_C_TMP1,
     B_MOM, B_MOMF, B_MOM01, B_LOC, B_ACC,
     B_FRONT0, B_FRONT1, B_M2L, B_P2P, B_WALK_CNT,
-    B_SUB_ACC, B_HHS_AOLD, B_HHS_ACUR, B_HHS_DT, B_HHS_RUNG, B_HHS_IDX, B_HHS_FLAG,
+    B_SUB_ACC, B_HHS_AOLD, B_HHS_ACUR, B_HHS_ATOT, B_HHS_DT, B_HHS_RUNG, B_HHS_IDX, B_HHS_FLAG,
     B_HHS_SCAN, B_HHS_TMP, B_RED, B_DIAG_POT, B_DIAG_ACC,
     B_OWN_CNT, B_OWN_FILL, B_OWN_OFF, B_OWN_LIST, B_OWN_TAG, B_OWN_PART,
     B_LAST_SLOT
@@ -186,7 +186,8 @@ tg_status direct_eval(tg_ctx *c, int64_t n, const double *pos, const double *mas
 tg_status hhs_init(tg_ctx *c);
 tg_status hhs_step(tg_ctx *c);
 tg_status hhs_diagnostics(tg_ctx *c, double out[8]);
-tg_status timesteps(tg_ctx *c, int64_t n, const double *a_old, const double *a_cur, double *dt, int32_t *rung);
+tg_status timesteps(tg_ctx *c, int64_t n, const double *a_old, const double *a_cur, const double *a_tot, double *dt,
+                    int32_t *rung);
 
 // Wrap each kernel launch: counts launches per class and, when profiling is on for the class,
 // records CUDA events around it on the context stream.

@@ -19,7 +19,7 @@ DEV = "cuda"
 
 def _params(**kw):
     base = dict(p=4, theta=0.5, eps=0.01, kernel=1, precision=tg.TG_PREC_FP64, n_crit=32, eta=0.025,
-                dt_max=1.0 / 64, k_max=8)
+                dt_max=1.0 / 64, k_max=8, eta_tot=0.01)
     base.update(kw)
     return tg.Params(**base)
 
@@ -31,8 +31,7 @@ def _system(n=3000, seed=1001):
 
 
 def _state(s, n):
-    rung, a_old, a_cur = tg.tg_hhs_state(s.ctx, n)
-    return rung.cpu().numpy(), a_old.cpu().numpy(), a_cur.cpu().numpy()
+    return tuple(a.cpu().numpy() for a in tg.tg_hhs_state(s.ctx, n, with_total=True))
 
 
 def test_resume_continues_the_run(tmp_path):
@@ -62,10 +61,11 @@ def test_resume_continues_the_run(tmp_path):
     # float64 throughout; only the order of the float64 atomic sums can differ between the runs
     assert torch.allclose(P2, P, rtol=1e-11, atol=1e-13)
     assert torch.allclose(V2, V, rtol=1e-11, atol=1e-13)
-    r1, o1, c1 = _state(s1, n)
-    r2, o2, c2 = _state(s2, n)
+    r1, o1, c1, t1 = _state(s1, n)
+    r2, o2, c2, t2 = _state(s2, n)
     assert np.array_equal(r1, r2)
     assert np.allclose(o1, o2, rtol=1e-11, atol=0) and np.allclose(c1, c2, rtol=1e-11, atol=0)
+    assert np.allclose(t1, t2, rtol=1e-11, atol=0)
 
 
 def _expect(code, fn, *args):

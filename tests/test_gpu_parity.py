@@ -223,6 +223,29 @@ def test_timesteps_bit_exact():
         assert rung[i] == oracle.rung(want, 1.0 / 128, 10)
 
 
+def test_timesteps_eq9_bit_exact():
+    # the Eq. (9) minimum timestep from |a|_tot, against the oracle's float64 function
+    g_ = np.random.default_rng(9)
+    n = 20000
+    a_old = np.where(g_.uniform(size=n) < 0.3, 0.0, 10 ** g_.uniform(-3, 3, n))
+    a_cur = 10 ** g_.uniform(-3, 3, n)
+    a_tot = np.where(g_.uniform(size=n) < 0.1, 0.0, 10 ** g_.uniform(-3, 4, n))
+    a_cur[:5] = 0.0
+    a_old[:3] = 0.0
+    prm = tg.Params(eps=0.005, eta=0.025, dt_max=1.0 / 128, k_max=10, eta_tot=0.004)
+    s = tg.Solver(prm)
+    dt, rung = tg.tg_timesteps(s.ctx, _t(a_old), _t(a_cur), _t(a_tot))
+    dt = dt.cpu().numpy()
+    rung = rung.cpu().numpy()
+    bound = 0
+    for i in range(n):
+        want = oracle.timestep_tot(0.025, 0.005, a_old[i], a_cur[i], 0.004, a_tot[i])
+        bound += want < oracle.timestep(0.025, 0.005, a_old[i], a_cur[i])
+        assert dt[i] == want or (np.isinf(dt[i]) and np.isinf(want))
+        assert rung[i] == oracle.rung(want, 1.0 / 128, 10)
+    assert 0 < bound < n   # the constraint binds for some particles, not all
+
+
 @pytest.mark.parametrize("n", [1, 2, 17])
 def test_small_and_degenerate_inputs(n):
     pos, _, mass = _case("plummer", max(n, 1))
@@ -314,6 +337,34 @@ def test_hhs_fp64_matches_oracle(kernel):
         assert np.abs(P.cpu().numpy() - h.pos).max() < 1e-11 * scale_x
         assert np.abs(V.cpu().numpy() - h.vel).max() < 1e-10 * np.abs(h.vel).max()
     assert len(np.unique(h.rung)) >= 2
+
+
+@pytest.mark.parametrize("kernel", [0, 1])
+def test_hhs_fp64_eq9_matches_oracle(kernel):
+    # HHS with the Eq. (9) minimum timestep: |a|_tot from the whole system at rung 0 (one extra
+    # all-masses evaluation on the GPU when a fast set exists) and the capped timesteps
+    n = 1500
+    pos, vel, mass = _case("plummer", n)
+    eps = 0.01
+    prm = tg.Params(p=4, theta=0.5, eps=eps, kernel=kernel, precision=tg.TG_PREC_FP64, n_crit=32, eta=0.025,
+                    dt_max=1.0 / 16, k_max=6, eta_tot=0.006)
+    s = tg.Solver(prm)
+    P, V, M = _t(pos), _t(vel), _t(mass)
+    s.hhs_init(P, V, M)
+    h = oracle.HHS(pos, vel, mass, _oprm(prm), eta=0.025, dt_max=1.0 / 16, k_max=6, eta_tot=0.006)
+    h0 = oracle.HHS(pos, vel, mass, _oprm(prm), eta=0.025, dt_max=1.0 / 16, k_max=6)
+    for step in range(3):
+        s.hhs_step()
+        h.step()
+        h0.step()
+        rung, a_old, a_cur, a_tot = tg.tg_hhs_state(s.ctx, n, with_total=True)
+        assert np.array_equal(rung.cpu().numpy(), h.rung), step
+        assert np.allclose(a_tot.cpu().numpy(), h.a_tot, rtol=1e-11, atol=0), step
+        scale_x = np.abs(h.pos).max()
+        assert np.abs(P.cpu().numpy() - h.pos).max() < 1e-11 * scale_x
+        assert np.abs(V.cpu().numpy() - h.vel).max() < 1e-10 * np.abs(h.vel).max()
+    # the constraint is active in this run: some particles sit deeper than without it
+    assert np.any(h.rung > h0.rung)
 
 
 @pytest.mark.parametrize("precision", [0, 1])
