@@ -103,6 +103,9 @@ def lib():
             L.orc_timestep.argtypes = [C.c_double, C.c_double, C.c_double, C.c_double]
             L.orc_timestep.restype = C.c_double
             L.orc_timestep_tot.argtypes = [C.c_double] * 6
+            L.orc_trad_init.argtypes = [C.c_int64, _d, _d, _d, _d, C.POINTER(Params), C.POINTER(HHSParams), _d, _i32]
+            L.orc_trad_step.argtypes = [C.c_int64, _d, _d, _d, _d, _d, _d, _d, C.POINTER(Params),
+                                        C.POINTER(HHSParams), _d, _i32, C.POINTER(HHSStats)]
             L.orc_timestep_tot.restype = C.c_double
             L.orc_rung.argtypes = [C.c_double, C.c_double, C.c_int]
             L.orc_hhs_init.argtypes = [C.c_int64, _d, _d, _d, _d, C.POINTER(Params), _d, _d, _d]
@@ -375,6 +378,35 @@ class HHS:
         lib().orc_diagnostics(self.n, _p(p[0]), _p(p[1]), _p(p[2]), _p(v[0]), _p(v[1]), _p(v[2]),
                               _p(self.mass), pot.ctypes.data_as(_vp), _p(out))
         return out
+
+
+class Traditional:
+    """The traditional individual-timestep integrator of Sec. 2.3 on the oracle (block steps,
+    kick-drift-kick per particle, forces on the active particles from all masses at unsynchronised
+    positions)."""
+
+    def __init__(self, pos, vel, mass, prm: Params, eta=0.025, dt_max=1.0 / 64, k_max=10):
+        self.pos = np.array(pos, dtype=np.float64, order="C")
+        self.vel = np.array(vel, dtype=np.float64, order="C")
+        self.mass = _f64(mass).copy()
+        self.n = self.mass.shape[0]
+        self.prm = prm
+        self.hp = HHSParams(eta=eta, dt_max=dt_max, k_max=k_max, eta_tot=0.0)
+        self.acc = np.zeros((3, self.n))
+        self.rung = np.zeros(self.n, np.int32)
+        p = self.pos
+        if lib().orc_trad_init(self.n, _p(p[0]), _p(p[1]), _p(p[2]), _p(self.mass), C.byref(prm), C.byref(self.hp),
+                               _p(self.acc), _p(self.rung, _i32)) != 0:
+            raise ValueError("orc_trad_init failed")
+
+    def step(self):
+        stats = HHSStats()
+        p, v = self.pos, self.vel
+        if lib().orc_trad_step(self.n, _p(p[0]), _p(p[1]), _p(p[2]), _p(v[0]), _p(v[1]), _p(v[2]), _p(self.mass),
+                               C.byref(self.prm), C.byref(self.hp), _p(self.acc), _p(self.rung, _i32),
+                               C.byref(stats)) != 0:
+            raise ValueError("orc_trad_step failed")
+        return stats
 
 
 def num_threads() -> int:

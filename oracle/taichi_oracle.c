@@ -998,6 +998,94 @@ int orc_hhs_step(int64_t n, double *x, double *y, double *z, double *vx, double 
     return h.status;
 }
 
+/* ------------------------------------------------------------------------------------ */
+/* Traditional individual timesteps (Sec. 2.3), the comparison integrator.              */
+/* ------------------------------------------------------------------------------------ */
+/* deepest rung allowed for a step that starts at substep m of a 2^k_max grid: the step must start on
+ * a multiple of itself, i.e. 2^(k_max - r) divides m */
+static int trad_aligned_rung(int64_t m, int k_max)
+{
+    if (m == 0) return 0;
+    int tz = 0;
+    while (tz < k_max && ((m >> tz) & 1) == 0) ++tz;
+    return k_max - tz;
+}
+
+static int trad_rung(const orc_hhs_params *hp, double eps, double amag, int64_t m)
+{
+    int r = orc_rung(orc_timestep(hp->eta, eps, 0.0, amag), hp->dt_max, hp->k_max);
+    int ra = trad_aligned_rung(m, hp->k_max);
+    return r > ra ? r : ra;
+}
+
+int orc_trad_init(int64_t n, const double *x, const double *y, const double *z, const double *m,
+                  const orc_params *prm, const orc_hhs_params *hp, double *acc, int32_t *rung)
+{
+    int rc = orc_fmm(n, x, y, z, m, NULL, prm, acc, acc + n, acc + 2 * n, NULL);
+    for (int64_t i = 0; i < n; ++i) {
+        double a = sqrt(acc[i] * acc[i] + acc[n + i] * acc[n + i] + acc[2 * n + i] * acc[2 * n + i]);
+        rung[i] = trad_rung(hp, prm->eps, a, 0);
+    }
+    return rc;
+}
+
+int orc_trad_step(int64_t n, double *x, double *y, double *z, double *vx, double *vy, double *vz,
+                  const double *m, const orc_params *prm, const orc_hhs_params *hp,
+                  double *acc, int32_t *rung, orc_hhs_stats *stats)
+{
+    orc_hhs_stats local;
+    if (!stats) stats = &local;
+    memset(stats, 0, sizeof(*stats));
+    const int K = hp->k_max;
+    const int64_t M = (int64_t)1 << K;            /* substeps of dt_max / 2^K in one call */
+    const double dt_min = ldexp(hp->dt_max, -K);
+    int64_t *end = (int64_t *)malloc(sizeof(int64_t) * (n > 0 ? n : 1));   /* substep where i's step ends */
+    double *ax = (double *)malloc(sizeof(double) * (n > 0 ? n : 1));
+    double *ay = (double *)malloc(sizeof(double) * (n > 0 ? n : 1));
+    double *az = (double *)malloc(sizeof(double) * (n > 0 ? n : 1));
+    int rc = 0;
+    /* opening half kicks at the start of the step, with the forces and rungs held from before */
+    for (int64_t i = 0; i < n; ++i) {
+        double h = 0.5 * ldexp(hp->dt_max, -rung[i]);
+        vx[i] += acc[i] * h; vy[i] += acc[n + i] * h; vz[i] += acc[2 * n + i] * h;
+        end[i] = (int64_t)1 << (K - rung[i]);
+        if (rung[i] > stats->max_rung) stats->max_rung = rung[i];
+    }
+    for (int64_t t = 1; t <= M; ++t) {
+        int64_t na = 0;
+        for (int64_t i = 0; i < n; ++i) na += end[i] == t;
+        if (na == 0) continue;
+        /* drift the particles whose step ends now over their whole step */
+        for (int64_t i = 0; i < n; ++i)
+            if (end[i] == t) {
+                double dt = ldexp(hp->dt_max, -rung[i]);
+                x[i] += vx[i] * dt; y[i] += vy[i] * dt; z[i] += vz[i] * dt;
+            }
+        /* forces on them from all masses at the stored positions */
+        if (orc_fmm(n, x, y, z, m, NULL, prm, ax, ay, az, NULL) != 0) rc = -1;
+        stats->poisson_calls++;
+        stats->sink_forces += na;
+        for (int64_t i = 0; i < n; ++i) {
+            if (end[i] != t) continue;
+            double h = 0.5 * ldexp(hp->dt_max, -rung[i]);
+            vx[i] += ax[i] * h; vy[i] += ay[i] * h; vz[i] += az[i] * h;     /* closing half kick */
+            acc[i] = ax[i]; acc[n + i] = ay[i]; acc[2 * n + i] = az[i];
+            double a = sqrt(ax[i] * ax[i] + ay[i] * ay[i] + az[i] * az[i]);
+            int r = trad_rung(hp, prm->eps, a, t == M ? 0 : t);
+            rung[i] = r;
+            if (t < M) {                                                     /* opening half kick */
+                double h2 = 0.5 * ldexp(hp->dt_max, -r);
+                vx[i] += ax[i] * h2; vy[i] += ay[i] * h2; vz[i] += az[i] * h2;
+                end[i] = t + ((int64_t)1 << (K - r));
+                if (r > stats->max_rung) stats->max_rung = r;
+            }
+        }
+    }
+    (void)dt_min;
+    free(end); free(ax); free(ay); free(az);
+    return rc;
+}
+
 /* P = sum m v, L = sum m x cross v, E = sum m v^2/2 + sum m phi / 2 */
 void orc_diagnostics(int64_t n, const double *x, const double *y, const double *z,
                      const double *vx, const double *vy, const double *vz,

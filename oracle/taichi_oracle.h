@@ -122,6 +122,22 @@ int orc_hhs_step(int64_t n, double *x, double *y, double *z, double *vx, double 
                  double *a_old, double *a_cur, double *a_tot, int32_t *rung_out,
                  orc_hhs_stats *stats, int64_t *trace, int32_t trace_cap);
 
+/* The traditional integrator with individual (block) timesteps that the paper sets beside HHS
+ * (Sec. 2.3): each particle steps dt_max / 2^rung with kick-drift-kick over its own step; at the end
+ * of a particle's step it drifts, gets its force from all masses at their stored positions (the
+ * inactive particles' positions are not synchronised to the current time), closes its step with a
+ * half kick, takes a new rung from dt_i = sqrt(eta eps / |a_i|) (deepened until its step starts on
+ * a multiple of the new step; at most k_max) and opens the next step with a half kick.  One call
+ * advances all particles by dt_max (every rung then ends together).
+ * acc (3n, x then y then z) and rung hold the state between calls: orc_trad_init evaluates the
+ * forces and picks the first rungs; the opening half kicks happen at the start of each step.
+ * stats (nullable): poisson_calls counts the force evaluations, sink_forces the active particles. */
+int orc_trad_init(int64_t n, const double *x, const double *y, const double *z, const double *m,
+                  const orc_params *prm, const orc_hhs_params *hp, double *acc, int32_t *rung);
+int orc_trad_step(int64_t n, double *x, double *y, double *z, double *vx, double *vy, double *vz,
+                  const double *m, const orc_params *prm, const orc_hhs_params *hp,
+                  double *acc, int32_t *rung, orc_hhs_stats *stats);
+
 void orc_diagnostics(int64_t n, const double *x, const double *y, const double *z,
                      const double *vx, const double *vy, const double *vz,
                      const double *m, const double *pot, double out[7]);

@@ -181,3 +181,68 @@ def test_eq9_records_the_total_acceleration_at_rung_0():
     h.step()
     a1, _ = oracle.fmm(h.pos, m, prm)
     assert np.allclose(h.a_tot, np.sqrt((a1 ** 2).sum(0)), rtol=1e-14, atol=0)
+
+
+# ---------------------------------------------------------------- traditional individual timesteps
+def test_traditional_single_rung_is_textbook_kdk():
+    pos, vel, m = ics.plummer(300, 1001)
+    prm = oracle.params(p=4, theta=0.5, eps=0.01, kernel=oracle.PLUMMER, n_crit=16)
+    dt = 1.0 / 64
+    t = oracle.Traditional(pos, vel, m, prm, eta=0.025, dt_max=dt, k_max=0)
+    x, v = pos.copy(), vel.copy()
+    a, _ = oracle.fmm(x, m, prm)
+    for _ in range(3):
+        v = v + a * (0.5 * dt)
+        x = x + v * dt
+        a, _ = oracle.fmm(x, m, prm)
+        v = v + a * (0.5 * dt)
+        st = t.step()
+        assert st.poisson_calls == 1 and st.sink_forces == 300
+    assert np.array_equal(t.pos, x) and np.array_equal(t.vel, v)
+
+
+def test_traditional_binary_sets_the_boundaries():
+    # a tight binary among far particles: it alone sits on rung k, so one step of dt_max has 2^k
+    # boundaries (force evaluations), the last one shared with everybody else
+    for k in (2, 4):
+        pos, vel, m, dt_max = _two_rung_binary(k)
+        prm = oracle.params(p=4, theta=0.5, eps=1e-3, kernel=oracle.PLUMMER, n_crit=8)
+        t = oracle.Traditional(pos, vel, m, prm, eta=0.02, dt_max=dt_max, k_max=12)
+        st = t.step()
+        assert st.max_rung == k
+        assert st.poisson_calls == 2 ** k
+        assert st.sink_forces == 2 * 2 ** k + (len(m) - 2)
+
+
+def _two_rung_binary(k, eta=0.02, eps=1e-3):
+    mb, sep = 0.1, 0.05
+    dt_bin = np.sqrt(eta * eps / (mb / sep ** 2))
+    dt_max = dt_bin * 2.0 ** (k - 0.5)
+    v = np.sqrt(mb / (2 * sep))
+    ang = np.linspace(0, 2 * np.pi, 18, endpoint=False)
+    far = np.stack([10 * np.cos(ang), 10 * np.sin(ang), 0.3 * np.sin(3 * ang)])
+    pos = np.concatenate([np.array([[-sep / 2, sep / 2], [0, 0], [0, 0]]), far], axis=1)
+    vel = np.zeros_like(pos)
+    vel[1, 0], vel[1, 1] = -v, v
+    m = np.concatenate([[mb, mb], np.full(18, 0.8 / 18)])
+    return pos, vel, m, dt_max
+
+
+def test_traditional_scheme_breaks_momentum_conservation():
+    # Sec. 3.2.1: forces on active particles from unsynchronised inactive ones, without reaction,
+    # leave a momentum error far above roundoff; HHS keeps it at roundoff on the same system
+    pos, vel, m = ics.plummer(800, 1005)
+    m = ics.random_masses(800, 41)
+    vel = vel - (vel * m).sum(1, keepdims=True) / m.sum()
+    prm = oracle.params(p=5, theta=0.45, eps=0.01, kernel=oracle.PLUMMER, n_crit=16)
+    t = oracle.Traditional(pos, vel, m, prm, eta=0.02, dt_max=1.0 / 8, k_max=8)
+    h = oracle.HHS(pos, vel, m, prm, eta=0.02, dt_max=1.0 / 8, k_max=8)
+    for _ in range(2):
+        t.step()
+        h.step()
+    scale = (m * np.abs(vel).sum(0)).sum()
+    p_trad = np.abs((t.vel * m).sum(1)).max() / scale
+    p_hhs = np.abs((h.vel * m).sum(1)).max() / scale
+    assert len(np.unique(t.rung)) >= 3
+    assert p_hhs < 1e-14
+    assert p_trad > 1e3 * max(p_hhs, 1e-16)
