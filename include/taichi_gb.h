@@ -126,8 +126,22 @@ tg_status tg_hhs_init(tg_ctx *ctx, int64_t n, double *pos, double *vel, const do
  * slow/fast split, KDK (Algorithm 2) with the kickS2F/kickFS2S pairs of Algorithm 3, drifts.
  * Synchronising (the recursion reads the set sizes of each split). */
 tg_status tg_hhs_step(tg_ctx *ctx);
+/* The traditional integrator with individual timesteps that the paper sets beside HHS (Sec. 2.3),
+ * on the same FMM.  tg_trad_init binds pos/vel/mass like tg_hhs_init (caller-owned device float64
+ * SoA), evaluates the forces and picks the first rungs from dt_i = sqrt(eta eps / |a_i|).
+ * tg_trad_step advances every particle by params.dt_max: block steps dt_max / 2^rung with
+ * kick-drift-kick per particle; at the end of a particle's step it drifts, gets its force from all
+ * masses at their stored positions (inactive particles are not synchronised), closes with a half
+ * kick, takes a new rung (deepened until the next step starts on a multiple of itself, at most
+ * k_max) and opens the next step.  No reaction reaches the sources, so momentum is not conserved:
+ * this is the paper's comparison scheme.  Each boundary is one evaluation of the whole system;
+ * tg_stats.sink_forces counts the active particles.  Synchronising (one read per boundary).
+ * TG_ERR_STATE for tg_trad_step without tg_trad_init (tg_hhs_step likewise needs tg_hhs_init). */
+tg_status tg_trad_init(tg_ctx *ctx, int64_t n, double *pos, double *vel, const double *mass);
+tg_status tg_trad_step(tg_ctx *ctx);
 /* Per-particle HHS state (device outputs, each nullable): rung (int32 n), |a_old|, |a_current|
- * and |a|_tot of Eq. (9) (float64 n).  Synchronising. */
+ * and |a|_tot of Eq. (9) (float64 n).  After tg_trad_init only the rungs are kept; the other
+ * arrays are written as zero.  Synchronising. */
 tg_status tg_hhs_state(tg_ctx *ctx, int32_t *rung, double *a_old, double *a_cur, double *a_tot);
 /* Set the per-particle |a_old|, |a_current| and (nullable) |a|_tot (device float64 n each). */
 tg_status tg_hhs_set_accel(tg_ctx *ctx, const double *a_old, const double *a_cur, const double *a_tot);

@@ -100,6 +100,8 @@ def load() -> C.CDLL:
             L.tg_direct_forces.argtypes = [_vp, _i64, _vp, _vp, _vp, _i64, _vp, _vp, _vp]
             L.tg_hhs_init.argtypes = [_vp, _i64, _vp, _vp, _vp]
             L.tg_hhs_step.argtypes = [_vp]
+            L.tg_trad_init.argtypes = [_vp, _i64, _vp, _vp, _vp]
+            L.tg_trad_step.argtypes = [_vp]
             L.tg_hhs_state.argtypes = [_vp, _vp, _vp, _vp, _vp]
             L.tg_hhs_set_accel.argtypes = [_vp, _vp, _vp, _vp]
             L.tg_diagnostics.argtypes = [_vp, C.POINTER(C.c_double)]
@@ -221,6 +223,14 @@ def tg_diagnostics(ctx) -> np.ndarray:
     return np.array(out[:])
 
 
+def tg_trad_init(ctx, pos, vel, mass) -> None:
+    _check(ctx, load().tg_trad_init(ctx, mass.shape[0], _ptr(pos), _ptr(vel), _ptr(mass)))
+
+
+def tg_trad_step(ctx) -> None:
+    _check(ctx, load().tg_trad_step(ctx))
+
+
 def tg_checkpoint(ctx, path) -> None:
     _check(ctx, load().tg_checkpoint(ctx, os.fsencode(path)))
 
@@ -319,6 +329,13 @@ class Solver:
 
     def hhs_step(self):
         tg_hhs_step(self.ctx)
+
+    def trad_init(self, pos, vel, mass):
+        self._hhs = (pos, vel, mass)
+        tg_trad_init(self.ctx, pos, vel, mass)
+
+    def trad_step(self):
+        tg_trad_step(self.ctx)
 
     def checkpoint(self, path):
         tg_checkpoint(self.ctx, path)

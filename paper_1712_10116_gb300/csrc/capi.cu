@@ -73,7 +73,7 @@ tg_status tg_create(const tg_params *params, void *cuda_stream, tg_ctx **out)
         delete c;
         return TG_ERR_CUDA;
     }
-    if (cudaMalloc(&c->d_counters, 16 * sizeof(unsigned long long)) != cudaSuccess) {
+    if (cudaMalloc(&c->d_counters, 32 * sizeof(unsigned long long)) != cudaSuccess) {
         cudaGetLastError();
         delete c;
         return TG_ERR_OOM;
@@ -84,7 +84,7 @@ tg_status tg_create(const tg_params *params, void *cuda_stream, tg_ctx **out)
         delete c;
         return TG_ERR_OOM;
     }
-    cudaMemset(c->d_counters, 0, 16 * sizeof(unsigned long long));
+    cudaMemset(c->d_counters, 0, 32 * sizeof(unsigned long long));
     std::memset(c->h_pinned, 0, 64 * sizeof(int64_t));
     *out = c;
     return TG_OK;
@@ -215,8 +215,12 @@ tg_status tg_hhs_init(tg_ctx *c, int64_t n, double *pos, double *vel, const doub
     c->hhs_pos = pos;
     c->hhs_vel = vel;
     c->hhs_mass = mass;
+    c->bound_integrator = 1;
     st = hhs_init(c);
-    if (st) c->hhs_n = 0;
+    if (st) {
+        c->hhs_n = 0;
+        c->bound_integrator = 0;
+    }
     return st;
 }
 
@@ -224,8 +228,35 @@ tg_status tg_hhs_step(tg_ctx *c)
 {
     tg_status st = begin(c);
     if (st) return st;
-    if (c->hhs_n <= 0) return set_err(c, TG_ERR_STATE, "tg_hhs_step before tg_hhs_init");
+    if (c->hhs_n <= 0 || c->bound_integrator != 1) return set_err(c, TG_ERR_STATE, "tg_hhs_step before tg_hhs_init");
     return hhs_step(c);
+}
+
+tg_status tg_trad_init(tg_ctx *c, int64_t n, double *pos, double *vel, const double *mass)
+{
+    tg_status st = begin(c);
+    if (st) return st;
+    if (n <= 0 || n > INT32_MAX / 4 || !check_device_ptr(pos) || !check_device_ptr(vel) || !check_device_ptr(mass))
+        return set_err(c, TG_ERR_ARG, "tg_trad_init: need n > 0 and device arrays");
+    c->hhs_n = n;
+    c->hhs_pos = pos;
+    c->hhs_vel = vel;
+    c->hhs_mass = mass;
+    c->bound_integrator = 2;
+    st = trad_init(c);
+    if (st) {
+        c->hhs_n = 0;
+        c->bound_integrator = 0;
+    }
+    return st;
+}
+
+tg_status tg_trad_step(tg_ctx *c)
+{
+    tg_status st = begin(c);
+    if (st) return st;
+    if (c->hhs_n <= 0 || c->bound_integrator != 2) return set_err(c, TG_ERR_STATE, "tg_trad_step before tg_trad_init");
+    return trad_step(c);
 }
 
 tg_status tg_hhs_state(tg_ctx *c, int32_t *rung, double *a_old, double *a_cur, double *a_tot)
@@ -234,10 +265,17 @@ tg_status tg_hhs_state(tg_ctx *c, int32_t *rung, double *a_old, double *a_cur, d
     if (st) return st;
     if (c->hhs_n <= 0) return set_err(c, TG_ERR_STATE, "tg_hhs_state before tg_hhs_init");
     const size_t n = (size_t)c->hhs_n;
-    if (rung) cudaMemcpyAsync(rung, c->buf[B_HHS_RUNG].p, n * sizeof(int32_t), cudaMemcpyDeviceToDevice, c->stream);
-    if (a_old) cudaMemcpyAsync(a_old, c->buf[B_HHS_AOLD].p, n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream);
-    if (a_cur) cudaMemcpyAsync(a_cur, c->buf[B_HHS_ACUR].p, n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream);
-    if (a_tot) cudaMemcpyAsync(a_tot, c->buf[B_HHS_ATOT].p, n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream);
+    // arrays the bound integrator does not keep (|a_old|, |a_cur|, |a|_tot of a traditional run) read as zero
+    auto out = [&](void *dst, int slot, size_t bytes) -> cudaError_t {
+        if (!dst) return cudaSuccess;
+        if (!c->buf[slot].p) return cudaMemsetAsync(dst, 0, bytes, c->stream);
+        return cudaMemcpyAsync(dst, c->buf[slot].p, bytes, cudaMemcpyDeviceToDevice, c->stream);
+    };
+    cudaError_t e = out(rung, B_HHS_RUNG, n * sizeof(int32_t));
+    if (e == cudaSuccess) e = out(a_old, B_HHS_AOLD, n * sizeof(double));
+    if (e == cudaSuccess) e = out(a_cur, B_HHS_ACUR, n * sizeof(double));
+    if (e == cudaSuccess) e = out(a_tot, B_HHS_ATOT, n * sizeof(double));
+    if (e != cudaSuccess) return cuda_check(c, e, "tg_hhs_state");
     return cuda_check(c, cudaStreamSynchronize(c->stream), "tg_hhs_state");
 }
 
@@ -433,7 +471,7 @@ tg_status tg_checkpoint(tg_ctx *c, const char *path)
     tg_status st = begin(c);
     if (st) return st;
     if (!path) return set_err(c, TG_ERR_ARG, "tg_checkpoint: path is NULL");
-    if (c->hhs_n <= 0) return set_err(c, TG_ERR_STATE, "tg_checkpoint before tg_hhs_init");
+    if (c->hhs_n <= 0 || c->bound_integrator != 1) return set_err(c, TG_ERR_STATE, "tg_checkpoint before tg_hhs_init");
     const size_t n = (size_t)c->hhs_n;
     std::vector<double> pos(3 * n), vel(3 * n), mass(n), a_old(n), a_cur(n), a_tot(n);
     std::vector<int32_t> rung(n);
@@ -482,7 +520,7 @@ tg_status tg_restore(tg_ctx *c, const char *path)
     tg_status st = begin(c);
     if (st) return st;
     if (!path) return set_err(c, TG_ERR_ARG, "tg_restore: path is NULL");
-    if (c->hhs_n <= 0) return set_err(c, TG_ERR_STATE, "tg_restore before tg_hhs_init");
+    if (c->hhs_n <= 0 || c->bound_integrator != 1) return set_err(c, TG_ERR_STATE, "tg_restore before tg_hhs_init");
     FILE *f = std::fopen(path, "rb");
     if (!f) return set_err(c, TG_ERR_IO, "tg_restore: cannot open %s", path);
     std::vector<unsigned char> data;

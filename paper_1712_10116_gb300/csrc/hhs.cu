@@ -294,6 +294,185 @@ tg_status timesteps(tg_ctx *c, int64_t n, const double *a_old, const double *a_c
     return cuda_check(c, cudaGetLastError(), "timesteps");
 }
 
+// ------------------------------------------------------------------ traditional individual timesteps
+// The comparison integrator of Sec. 2.3: block steps dt_max / 2^rung, kick-drift-kick per particle
+// over its own step.  At the end of a particle's step it drifts the whole step, gets its force from
+// all masses at their stored positions (inactive particles are not synchronised), closes the step
+// with a half kick, takes a new rung from dt_i = sqrt(eta eps / |a_i|) deepened until the next step
+// starts on a multiple of itself, and opens it with a half kick.  Time runs on a grid of 2^k_max
+// substeps per rung-0 step; end[i] is the substep where particle i's step ends.  The float64
+// operations follow the reference order with explicit rounding (no contraction).
+__device__ __forceinline__ double trad_amag(double ax, double ay, double az)
+{
+    return sqrt(__dadd_rn(__dadd_rn(__dmul_rn(ax, ax), __dmul_rn(ay, ay)), __dmul_rn(az, az)));
+}
+
+__device__ __forceinline__ int trad_rung_of(double amag, double eta_eps, double dt_max, int k_max, int64_t m)
+{
+    const double d = (amag > 0.0) ? sqrt(__ddiv_rn(eta_eps, amag)) : INFINITY;
+    int k = 0;
+    while (k < k_max && !(d >= ldexp(dt_max, -k))) ++k;
+    int ra = 0;   // a step starting at substep m must start on a multiple of itself
+    if (m != 0) {
+        int tz = 0;
+        while (tz < k_max && ((m >> tz) & 1) == 0) ++tz;
+        ra = k_max - tz;
+    }
+    return k > ra ? k : ra;
+}
+
+__global__ void trad_first_rungs(int64_t n, const double *acc, double eta_eps, double dt_max, int k_max, int32_t *rung)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        rung[i] = trad_rung_of(trad_amag(acc[i], acc[n + i], acc[2 * n + i]), eta_eps, dt_max, k_max, 0);
+}
+
+// opening half kicks at the start of a rung-0 step
+__global__ void trad_open(int64_t n, const double *acc, const int32_t *rung, double dt_max, int k_max, double *vel,
+                          int64_t *end, unsigned long long *max_rung)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double h = 0.5 * ldexp(dt_max, -rung[i]);
+#pragma unroll
+        for (int d = 0; d < 3; ++d) vel[d * n + i] = __dadd_rn(vel[d * n + i], __dmul_rn(acc[d * n + i], h));
+        end[i] = (int64_t)1 << (k_max - rung[i]);
+        atomicMax(max_rung, (unsigned long long)rung[i]);
+    }
+}
+
+// next boundary: the smallest end (out[0], atomicMin) and how many steps end there (out[1])
+__global__ void trad_next_min(int64_t n, const int64_t *end, unsigned long long *out)
+{
+    unsigned long long mn = ~0ull;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        mn = min(mn, (unsigned long long)end[i]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mn = min(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+    if ((threadIdx.x & 31) == 0) atomicMin(out, mn);
+}
+__global__ void trad_next_count(int64_t n, const int64_t *end, unsigned long long *out)
+{
+    const unsigned long long t = out[0];
+    unsigned long long c = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        c += (unsigned long long)end[i] == t;
+    c = warp_sum(c);
+    if ((threadIdx.x & 31) == 0 && c) atomicAdd(out + 1, c);
+}
+
+__global__ void trad_drift(int64_t n, const int64_t *end, const unsigned long long *tnow, const int32_t *rung,
+                           double dt_max, double *pos, const double *vel)
+{
+    const int64_t t = (int64_t)tnow[0];
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        if (end[i] != t) continue;
+        const double dt = ldexp(dt_max, -rung[i]);
+#pragma unroll
+        for (int d = 0; d < 3; ++d) pos[d * n + i] = __dadd_rn(pos[d * n + i], __dmul_rn(vel[d * n + i], dt));
+    }
+}
+
+__global__ void trad_close(int64_t n, int64_t *end, const unsigned long long *tnow, int64_t m_end,
+                           const double *acc_new, double *acc, int32_t *rung, double *vel, double eta_eps,
+                           double dt_max, int k_max, unsigned long long *max_rung)
+{
+    const int64_t t = (int64_t)tnow[0];
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        if (end[i] != t) continue;
+        const double a[3] = {acc_new[i], acc_new[n + i], acc_new[2 * n + i]};
+        const double h = 0.5 * ldexp(dt_max, -rung[i]);
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            vel[d * n + i] = __dadd_rn(vel[d * n + i], __dmul_rn(a[d], h));   // closing half kick
+            acc[d * n + i] = a[d];
+        }
+        const int r = trad_rung_of(trad_amag(a[0], a[1], a[2]), eta_eps, dt_max, k_max, t == m_end ? 0 : t);
+        rung[i] = r;
+        if (t < m_end) {
+            const double h2 = 0.5 * ldexp(dt_max, -r);
+#pragma unroll
+            for (int d = 0; d < 3; ++d) vel[d * n + i] = __dadd_rn(vel[d * n + i], __dmul_rn(a[d], h2));
+            end[i] = t + ((int64_t)1 << (k_max - r));
+            atomicMax(max_rung, (unsigned long long)r);
+        }
+    }
+}
+
+tg_status trad_init(tg_ctx *c)
+{
+    tg_status st;
+    const int64_t n = c->hhs_n;
+    double *acc;
+    int32_t *rung;
+    if ((st = ensure_t(c, B_TRAD_ACC, 3 * n, &acc)) || (st = ensure_t(c, B_HHS_RUNG, n, &rung))) return st;
+    if ((st = fmm_eval(c, (int)n, c->hhs_pos, n, nullptr, c->hhs_mass, nullptr, acc, n, nullptr, false))) return st;
+    {
+        ProfScope ps_(c, TG_K_HHS);
+        trad_first_rungs<<<grid_for(n, 256), 256, 0, c->stream>>>(n, acc, c->prm.eta * c->prm.eps, c->prm.dt_max,
+                                                                  c->prm.k_max, rung);
+    }
+    c->hhs_time = 0.0;
+    return cuda_check(c, cudaGetLastError(), "traditional init");
+}
+
+tg_status trad_step(tg_ctx *c)
+{
+    tg_status st;
+    const int64_t n = c->hhs_n;
+    const int K = c->prm.k_max;
+    const int64_t m_end = (int64_t)1 << K;
+    const double eta_eps = c->prm.eta * c->prm.eps, dt_max = c->prm.dt_max;
+    double *acc, *acc_new;
+    int32_t *rung;
+    int64_t *end;
+    unsigned long long *ctr = c->d_counters + 16;   // [0] next boundary, [1] steps ending there, [2] deepest rung
+    if ((st = ensure_t(c, B_TRAD_ACC, 3 * n, &acc)) || (st = ensure_t(c, B_HHS_RUNG, n, &rung)) ||
+        (st = ensure_t(c, B_TRAD_END, n, &end)) || (st = ensure_t(c, B_SUB_ACC, 3 * n, &acc_new)))
+        return st;
+    const int g = grid_for(n, 256);
+    cudaMemsetAsync(ctr + 2, 0, sizeof(unsigned long long), c->stream);
+    {
+        ProfScope ps_(c, TG_K_HHS);
+        trad_open<<<g, 256, 0, c->stream>>>(n, acc, rung, dt_max, K, c->hhs_vel, end, ctr + 2);
+    }
+    for (;;) {
+        const unsigned long long init[2] = {~0ull, 0ull};
+        cudaMemcpyAsync(ctr, init, sizeof(init), cudaMemcpyHostToDevice, c->stream);
+        {
+            ProfScope ps_(c, TG_K_HHS);
+            trad_next_min<<<g, 256, 0, c->stream>>>(n, end, ctr);
+            trad_next_count<<<g, 256, 0, c->stream>>>(n, end, ctr);
+        }
+        unsigned long long *h = reinterpret_cast<unsigned long long *>(c->h_pinned + 48);
+        cudaMemcpyAsync(h, ctr, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, c->stream);
+        cudaError_t e = cudaStreamSynchronize(c->stream);
+        if (e != cudaSuccess) return cuda_check(c, e, "traditional step");
+        const int64_t t = (int64_t)h[0], na = (int64_t)h[1];
+        if (t > m_end || na <= 0) return set_err(c, TG_ERR_STATE, "traditional step: no boundary found");
+        {
+            ProfScope ps_(c, TG_K_HHS);
+            trad_drift<<<g, 256, 0, c->stream>>>(n, end, ctr, rung, dt_max, c->hhs_pos, c->hhs_vel);
+        }
+        // forces on the active particles from all masses (the whole system is evaluated)
+        if ((st = fmm_eval(c, (int)n, c->hhs_pos, n, nullptr, c->hhs_mass, nullptr, acc_new, n, nullptr, false)))
+            return st;
+        c->stats.sink_forces -= n - na;   // count the active particles only
+        {
+            ProfScope ps_(c, TG_K_HHS);
+            trad_close<<<g, 256, 0, c->stream>>>(n, end, ctr, m_end, acc_new, acc, rung, c->hhs_vel, eta_eps, dt_max,
+                                                 K, ctr + 2);
+        }
+        if ((st = cuda_check(c, cudaGetLastError(), "traditional step"))) return st;
+        if (t == m_end) break;
+    }
+    unsigned long long *h = reinterpret_cast<unsigned long long *>(c->h_pinned + 48);
+    cudaMemcpyAsync(h, ctr + 2, sizeof(unsigned long long), cudaMemcpyDeviceToHost, c->stream);
+    if ((st = cuda_check(c, cudaStreamSynchronize(c->stream), "traditional step"))) return st;
+    if ((int64_t)h[0] > c->stats.max_rung) c->stats.max_rung = (int64_t)h[0];
+    c->hhs_time += dt_max;
+    return TG_OK;
+}
+
 // ------------------------------------------------------------------ diagnostics (float64)
 // out: P (3), L (3), kinetic, potential sum m phi / 2
 __global__ void diag_partial(int64_t n, const double *pos, const double *vel, const double *m, const double *pot,

@@ -69,7 +69,7 @@ struct tg_ctx {
     tg::Buf buf[64];
 
     // counters on the device (p2p pair count) and pinned host mirrors
-    unsigned long long *d_counters = nullptr;   // [0] p2p particle pairs
+    unsigned long long *d_counters = nullptr;   // 32 words: [0] p2p particle pairs
     int64_t *h_pinned = nullptr;                // small pinned staging area (64 int64)
 
     // last tree/walk (host copies of sizes)
@@ -92,6 +92,7 @@ struct tg_ctx {
     double *hhs_pos = nullptr, *hhs_vel = nullptr;
     const double *hhs_mass = nullptr;
     double hhs_time = 0.0;
+    int bound_integrator = 0;                   // 1: HHS (tg_hhs_init), 2: traditional (tg_trad_init)
 };
 
 namespace tg {
@@ -105,7 +106,7 @@ enum Slot {
     B_C_TMP0, B_C_TMP1,
     B_MOM, B_MOMF, B_MOM01, B_LOC, B_ACC,
     B_FRONT0, B_FRONT1, B_M2L, B_P2P, B_WALK_CNT,
-    B_SUB_ACC, B_HHS_AOLD, B_HHS_ACUR, B_HHS_ATOT, B_HHS_DT, B_HHS_RUNG, B_HHS_IDX, B_HHS_FLAG,
+    B_SUB_ACC, B_HHS_AOLD, B_HHS_ACUR, B_HHS_ATOT, B_TRAD_ACC, B_TRAD_END, B_HHS_DT, B_HHS_RUNG, B_HHS_IDX, B_HHS_FLAG,
     B_HHS_SCAN, B_HHS_TMP, B_RED, B_DIAG_POT, B_DIAG_ACC,
     B_OWN_CNT, B_OWN_FILL, B_OWN_OFF, B_OWN_LIST, B_OWN_TAG, B_OWN_PART,
     B_LAST_SLOT
@@ -185,6 +186,8 @@ tg_status direct_eval(tg_ctx *c, int64_t n, const double *pos, const double *mas
 // ---- hhs.cu
 tg_status hhs_init(tg_ctx *c);
 tg_status hhs_step(tg_ctx *c);
+tg_status trad_init(tg_ctx *c);
+tg_status trad_step(tg_ctx *c);
 tg_status hhs_diagnostics(tg_ctx *c, double out[8]);
 tg_status timesteps(tg_ctx *c, int64_t n, const double *a_old, const double *a_cur, const double *a_tot, double *dt,
                     int32_t *rung);
