@@ -41,6 +41,11 @@ def parse():
     ap.add_argument("--n", type=int, default=1 << 20)
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--momentum-contrast", action="store_true",
+                    help="run HHS and the traditional integrator to t = --contrast-t on the unit-cube collapse "
+                         "and print |sum m v| for both")
+    ap.add_argument("--contrast-n", type=int, default=10000)
+    ap.add_argument("--contrast-t", type=float, default=1.0)
     ap.add_argument("--eta-tot", type=float, default=0.0,
                     help="eta_1 of the Eq. (9) minimum timestep from the total acceleration (0 = off)")
     ap.add_argument("--no-fp64-plain", action="store_true",
@@ -444,10 +449,53 @@ def run_eval_only(args):
     solver.close()
 
 
+def run_momentum_contrast(args):
+    """|sum m v| after a cold collapse to t = 1 with HHS and with the traditional individual-timestep
+    integrator (Sec. 3.2.1, the paper's momentum test): unit cube, N = 10^4, eps = 0.01
+    (eps = 0.01 (N/10^4)^(-1/3)), Wendland C2, theta = 0.45, p = 5, float64 on the GPU."""
+    import torch
+    from paper_1712_10116_gb300 import binding as tg
+    from paper_1712_10116_gb300 import ics
+    n = args.contrast_n
+    eps = 0.01 * (n / 1e4) ** (-1.0 / 3.0)
+    pos, vel, mass = ics.uniform_cube(n, 1006)
+    dt_max = 1.0 / 64
+    steps = int(round(args.contrast_t / dt_max))
+    prm = tg.Params(p=5, theta=0.45, eps=eps, kernel=0, precision=tg.TG_PREC_FP64, n_crit=64, eta=0.02,
+                    dt_max=dt_max, k_max=10)
+    out = {"mode": "momentum-contrast", "workload": f"cold collapse of a unit cube at rest, N={n}, eps={eps:.4g} "
+           f"Wendland C2, theta=0.45, p=5, float64, eta=0.02, dt_max=1/64, k_max=10, t=0..{args.contrast_t}",
+           "data": "synthetic"}
+    for name in ("hhs", "traditional"):
+        s = tg.Solver(prm)
+        P = torch.tensor(pos, device="cuda")
+        V = torch.tensor(vel, device="cuda")
+        M = torch.tensor(mass, device="cuda")
+        (s.hhs_init if name == "hhs" else s.trad_init)(P, V, M)
+        tg.tg_reset_stats(s.ctx)
+        step = s.hhs_step if name == "hhs" else s.trad_step
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            step()
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        d = s.diagnostics()
+        st = s.stats()
+        pmag = float(np.linalg.norm(d[:3]))
+        out[name] = {"t": float(d[7]), "abs_P": pmag, "log10_abs_P": float(np.log10(max(pmag, 1e-300))),
+                     "evaluations": st["evaluations"], "sink_forces": st["sink_forces"], "max_rung": st["max_rung"],
+                     "wall_s": wall, "particle_forces_per_s": st["sink_forces"] / wall}
+        s.close()
+    print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse()
     if args.eval_only:
         run_eval_only(args)
+        return
+    if args.momentum_contrast:
+        run_momentum_contrast(args)
         return
     if args.impl == "reference":
         run_reference(args)
