@@ -508,14 +508,15 @@ __global__ void walk_step(TreeView t, MacParams mp, const uint2 *front_in, const
 
 // ------------------------------------------------------------------ L2L (one level), normalised
 // L~_c^n += sum_{d} L~_P^(n+d) (+-1)^d 2^-(2|d| + |n| + 1) / d!  over |d| <= p - |n|.
-// Warp per cell of the level, lanes over the coefficients n, both classes.  d runs through the
+// Warp per cell of the level, lanes over the coefficients n >= n_first (1 when only accelerations are
+// wanted: L^0 feeds no force), both classes.  d runs through the
 // multi-indices in their table order (the same d for every lane at each step); the index of n + d
 // comes from a lookup table in shared memory.
 constexpr int kM2MWarps = 2;   // warps per block of the L2L level kernel
 
 template <class T>
 __global__ void __launch_bounds__(32 * kM2MWarps) l2l_level(TreeView t, int lb, int le, int p, int nc, int ncp, int ncls,
-                                                            T *L)
+                                                            int n_first, T *L)
 {
     extern __shared__ __align__(16) unsigned char l2l_smem[];
     T *s_lp = reinterpret_cast<T *>(l2l_smem) + (size_t)(threadIdx.x >> 5) * 2 * ncp;   // parent's L, this warp
@@ -539,7 +540,7 @@ __global__ void __launch_bounds__(32 * kM2MWarps) l2l_level(TreeView t, int lb, 
         for (int k = lane; k < ncls * ncp; k += 32) s_lp[k] = L[(size_t)par * 2 * ncp + k];
         __syncwarp();
         const T *Lp = s_lp;
-        for (int n = lane; n < nc; n += 32) {
+        for (int n = n_first + lane; n < nc; n += 32) {
             const int nx = s_e[0][n], ny = s_e[1][n], nz = s_e[2][n], on = nx + ny + nz;
             const int nd = ncoef_dev(p - on);   // multi-indices d with |d| <= p - |n|
             T acc0 = 0, acc1 = 0;
@@ -958,7 +959,8 @@ static tg_status eval_typed(tg_ctx *c, int n, int ncell, const TreeView &t, cons
         const int lb = c->level_begin[l], le = c->level_begin[l + 1];
         ProfScope ps_(c, TG_K_DOWN);
         l2l_level<T><<<grid_for((int64_t)(le - lb) * 32, 32 * kM2MWarps), 32 * kM2MWarps,
-                       kM2MWarps * 2 * ncp * sizeof(T), c->stream>>>(t, lb, le, p, nc, ncp, ncls, L);
+                       kM2MWarps * 2 * ncp * sizeof(T), c->stream>>>(t, lb, le, p, nc, ncp, ncls,
+                                                                     want_pot ? 0 : 1, L);
     }
     {
         ProfScope ps_(c, TG_K_DOWN);

@@ -177,7 +177,9 @@ __device__ __noinline__ void owner_rows(const float4 *__restrict__ pf, const Own
 #pragma unroll
         for (int h = 16; h >= 4; h >>= 1)
 #pragma unroll
-            for (int q = 0; q < h; ++q) col[q] += __shfl_xor_sync(0xffffffffu, col[q + h], h);
+            for (int q = 0; q < h; ++q)
+                if (POT || (q & 3) != 3)   // without the potential, slots 4c + 3 stay zero
+                    col[q] += __shfl_xor_sync(0xffffffffu, col[q + h], h);
 #pragma unroll
         for (int h = 2; h >= 1; h >>= 1) {
             const bool hi = (lane & h) != 0;
