@@ -44,6 +44,8 @@ def parse():
     ap.add_argument("--momentum-contrast", action="store_true",
                     help="run HHS and the traditional integrator to t = --contrast-t on the unit-cube collapse "
                          "and print |sum m v| for both")
+    ap.add_argument("--sweep", action="store_true",
+                    help="theta / p sweep of the unit-cube collapse with HHS and the traditional integrator")
     ap.add_argument("--contrast-n", type=int, default=10000)
     ap.add_argument("--contrast-t", type=float, default=1.0)
     ap.add_argument("--eta-tot", type=float, default=0.0,
@@ -462,8 +464,8 @@ def run_momentum_contrast(args):
     dt_max = 1.0 / 64
     steps = int(round(args.contrast_t / dt_max))
     prm = tg.Params(p=5, theta=0.45, eps=eps, kernel=0, precision=tg.TG_PREC_FP64, n_crit=64, eta=0.02,
-                    dt_max=dt_max, k_max=10)
-    out = {"mode": "momentum-contrast", "workload": f"cold collapse of a unit cube at rest, N={n}, eps={eps:.4g} "
+                    dt_max=dt_max, k_max=10, eta_tot=args.eta_tot)
+    out = {"mode": "momentum-contrast", "eta_tot": args.eta_tot, "workload": f"cold collapse of a unit cube at rest, N={n}, eps={eps:.4g} "
            f"Wendland C2, theta=0.45, p=5, float64, eta=0.02, dt_max=1/64, k_max=10, t=0..{args.contrast_t}",
            "data": "synthetic"}
     for name in ("hhs", "traditional"):
@@ -472,6 +474,7 @@ def run_momentum_contrast(args):
         V = torch.tensor(vel, device="cuda")
         M = torch.tensor(mass, device="cuda")
         (s.hhs_init if name == "hhs" else s.trad_init)(P, V, M)
+        e0 = float(s.diagnostics()[6])
         tg.tg_reset_stats(s.ctx)
         step = s.hhs_step if name == "hhs" else s.trad_step
         t0 = time.perf_counter()
@@ -483,14 +486,63 @@ def run_momentum_contrast(args):
         st = s.stats()
         pmag = float(np.linalg.norm(d[:3]))
         out[name] = {"t": float(d[7]), "abs_P": pmag, "log10_abs_P": float(np.log10(max(pmag, 1e-300))),
+                     "rel_dE": float(abs((d[6] - e0) / e0)),
                      "evaluations": st["evaluations"], "sink_forces": st["sink_forces"], "max_rung": st["max_rung"],
                      "wall_s": wall, "particle_forces_per_s": st["sink_forces"] / wall}
         s.close()
     print(json.dumps(out), flush=True)
 
 
+def run_sweep(args):
+    """The theta / p sweeps of the cold-collapse tests (Sec. 3.2, Figs. 4-7 analogues) on the unit cube:
+    for each (theta, p), HHS and the traditional integrator from the same state to t = --contrast-t,
+    float64 on the GPU; |sum m v|, |sum m x cross v|, the relative energy error and the cost."""
+    import torch
+    from paper_1712_10116_gb300 import binding as tg
+    from paper_1712_10116_gb300 import ics
+    n = args.contrast_n
+    eps = 0.01 * (n / 1e4) ** (-1.0 / 3.0)
+    pos, vel, mass = ics.uniform_cube(n, 1006)
+    dt_max = 1.0 / 64
+    steps = int(round(args.contrast_t / dt_max))
+    grid = [(th, 5) for th in (0.7, 0.45, 0.3, 0.2, 0.1, 0.05)] + [(0.45, p) for p in (3, 4, 6, 7, 8)]
+    rows = []
+    for theta, p in grid:
+        row = {"theta": theta, "p": p}
+        for name in ("hhs", "traditional"):
+            prm = tg.Params(p=p, theta=theta, eps=eps, kernel=0, precision=tg.TG_PREC_FP64, n_crit=64, eta=0.02,
+                            dt_max=dt_max, k_max=10)
+            s = tg.Solver(prm)
+            P = torch.tensor(pos, device="cuda")
+            V = torch.tensor(vel, device="cuda")
+            M = torch.tensor(mass, device="cuda")
+            (s.hhs_init if name == "hhs" else s.trad_init)(P, V, M)
+            d0 = s.diagnostics()
+            tg.tg_reset_stats(s.ctx)
+            step = s.hhs_step if name == "hhs" else s.trad_step
+            t0 = time.perf_counter()
+            for _ in range(steps):
+                step()
+            torch.cuda.synchronize()
+            wall = time.perf_counter() - t0
+            d = s.diagnostics()
+            st = s.stats()
+            row[name] = {"abs_P": float(np.linalg.norm(d[:3])), "abs_L": float(np.linalg.norm(d[3:6])),
+                         "rel_dE": float(abs((d[6] - d0[6]) / d0[6])), "evaluations": st["evaluations"],
+                         "p2p_pairs": st["p2p_pairs"], "m2l_pairs": st["m2l_pairs"], "wall_s": wall}
+            s.close()
+        rows.append(row)
+        print(json.dumps({"mode": "sweep-point", **row}), flush=True)
+    print(json.dumps({"mode": "sweep", "workload": f"cold collapse of a unit cube at rest, N={n}, eps={eps:.4g} "
+                      f"Wendland C2, float64, eta=0.02, dt_max=1/64, k_max=10, t=0..{args.contrast_t}",
+                      "data": "synthetic", "points": rows}), flush=True)
+
+
 def main():
     args = parse()
+    if args.sweep:
+        run_sweep(args)
+        return
     if args.eval_only:
         run_eval_only(args)
         return
