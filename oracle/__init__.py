@@ -42,7 +42,7 @@ def build(force: bool = False) -> str:
 
 class Params(C.Structure):
     _fields_ = [("p", C.c_int), ("n_crit", C.c_int), ("kernel", C.c_int), ("max_level", C.c_int),
-                ("theta", C.c_double), ("kappa", C.c_double), ("eps", C.c_double)]
+                ("theta", C.c_double), ("kappa", C.c_double), ("eps", C.c_double), ("mac", C.c_int)]
 
 
 class HHSParams(C.Structure):
@@ -54,9 +54,12 @@ class HHSStats(C.Structure):
                 ("max_rung", C.c_int32), ("trace_len", C.c_int32)]
 
 
-def params(p=4, theta=0.5, eps=0.01, kernel=WENDLAND_C2, n_crit=64, kappa=1.0, max_level=21) -> Params:
+MAC_SIDE, MAC_SPHERE = 0, 1
+
+
+def params(p=4, theta=0.5, eps=0.01, kernel=WENDLAND_C2, n_crit=64, kappa=1.0, max_level=21, mac=MAC_SIDE) -> Params:
     return Params(p=p, n_crit=n_crit, kernel=kernel, max_level=max_level,
-                  theta=theta, kappa=kappa, eps=eps)
+                  theta=theta, kappa=kappa, eps=eps, mac=mac)
 
 
 _d = C.POINTER(C.c_double)
@@ -92,6 +95,7 @@ def lib():
             L.orc_tree_walk.argtypes = [_vp, _i64, _i64]
             L.orc_tree_lists.argtypes = [_vp, _i64, _i64, _i64, _i64]
             L.orc_well_separated.argtypes = [_vp, C.c_int64, C.c_int64]
+            L.orc_tree_radii.argtypes = [_vp, _d]
             L.orc_p2m.argtypes = [C.c_int, C.c_int64, _d, _d, _d, _d, _d, _d]
             L.orc_m2m.argtypes = [C.c_int, _d, _d, _d]
             L.orc_m2l.argtypes = [C.c_int, _d, _d, C.c_int, C.c_double, _d]
@@ -232,6 +236,11 @@ class Tree:
         p2p = np.zeros((2, npp.value), np.int64)
         lib().orc_tree_lists(self._h, _p(m2l[0], _i64), _p(m2l[1], _i64), _p(p2p[0], _i64), _p(p2p[1], _i64))
         return m2l, p2p
+
+    def radii(self):
+        r = np.zeros(self.ncell)
+        lib().orc_tree_radii(self._h, _p(r))
+        return r
 
     def well_separated(self, a, b) -> bool:
         return bool(lib().orc_well_separated(self._h, int(a), int(b)))

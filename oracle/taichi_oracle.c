@@ -18,7 +18,8 @@
  * Derivative tensors follow the McMurchie & Davidson (1978) auxiliary recurrence.
  *
  * Readings of points the paper leaves open (each also listed in the design notes):
- *   R in Eq. (1) = kappa * side (kappa = 1: the paper calls R the cell side length);
+ *   R in Eq. (1) = kappa * side (kappa = 1: the paper calls R the cell side length), or with mac = 1
+ *   the radius of a sphere about the cell centre that encloses the cell's particles;
  *   a cell is split iff it holds more than n_crit particles (leaves hold <= n_crit);
  *   expansion centres are geometric cell centres;
  *   "distance larger than eps" = the gap between the two cubes exceeds eps (Wendland only);
@@ -394,6 +395,7 @@ struct orc_tree {
     int64_t *c[3];          /* integer coordinates at the cell's own level */
     int64_t *first, *count, *child_first, *parent;
     int32_t *nchild;
+    double *radius;         /* enclosing radius per cell (mac = 1) */
     pair_list m2l, p2p;     /* directed lists from Algorithm 4 */
     int walked;
     /* optional pruning for one-sink evaluation: only cells with on_path set may be the
@@ -461,7 +463,37 @@ orc_tree *orc_tree_build(int64_t n, const double *x, const double *y, const doub
         t->child_first[head] = first_child;
         t->nchild[head] = nch;
     }
+    /* enclosing radii about the cell centres: leaves from their particles, parents bottom-up from
+     * their children (cells are in BFS order, so children come after their parent) */
+    t->radius = (double *)calloc((size_t)(t->ncell > 0 ? t->ncell : 1), sizeof(double));
+    for (int64_t c = t->ncell - 1; c >= 0; --c) {
+        double side = ldexp(t->L, -t->level[c]);
+        double zc[3];
+        for (int k = 0; k < 3; ++k) zc[k] = t->lo[k] + ((double)t->c[k][c] + 0.5) * side;
+        double r = 0.0;
+        if (t->nchild[c] == 0) {
+            for (int64_t s2 = t->first[c]; s2 < t->first[c] + t->count[c]; ++s2) {
+                int64_t i = t->perm[s2];
+                double dx = x[i] - zc[0], dy = y[i] - zc[1], dz = z[i] - zc[2];
+                double d = sqrt(dx * dx + dy * dy + dz * dz);
+                if (d > r) r = d;
+            }
+        } else {
+            /* |z_child - z_parent| = sqrt(3) side / 4 */
+            double dcp = sqrt(3.0) * ldexp(t->L, -(t->level[c] + 2));
+            for (int64_t q = t->child_first[c]; q < t->child_first[c] + t->nchild[c]; ++q) {
+                double v = dcp + t->radius[q];
+                if (v > r) r = v;
+            }
+        }
+        t->radius[c] = r;
+    }
     return t;
+}
+
+void orc_tree_radii(const orc_tree *t, double *r)
+{
+    for (int64_t c = 0; c < t->ncell; ++c) r[c] = t->radius[c];
 }
 
 void orc_tree_free(orc_tree *t)
@@ -470,6 +502,7 @@ void orc_tree_free(orc_tree *t)
     free(t->perm); free(t->keys); free(t->level);
     for (int k = 0; k < 3; ++k) free(t->c[k]);
     free(t->first); free(t->count); free(t->child_first); free(t->parent); free(t->nchild);
+    free(t->radius);
     free(t->m2l.a); free(t->m2l.b); free(t->p2p.a); free(t->p2p.b);
     free(t->on_path);
     free(t);
@@ -521,10 +554,18 @@ int orc_well_separated(const orc_tree *t, int64_t a, int64_t b)
         int64_t gk = dk - (ha + hb);
         if (gk > 0) g2 += gk * gk;
     }
-    double theta2 = t->prm.theta * t->prm.theta;
-    double kappa2 = t->prm.kappa * t->prm.kappa;
-    double rsum = (double)(2 * (ha + hb));
-    int mac = (double)d2 * theta2 > kappa2 * (rsum * rsum);
+    int mac;
+    if (t->prm.mac == 1) {
+        /* enclosing spheres: R_a + R_b < theta |z_a - z_b|, the distance from the exact integer offset
+         * (units of L / 2^(lf+1), a power of two) */
+        double d = sqrt((double)d2) * ldexp(t->L, -(lf + 1));
+        mac = t->radius[a] + t->radius[b] < t->prm.theta * d;
+    } else {
+        double theta2 = t->prm.theta * t->prm.theta;
+        double kappa2 = t->prm.kappa * t->prm.kappa;
+        double rsum = (double)(2 * (ha + hb));
+        mac = (double)d2 * theta2 > kappa2 * (rsum * rsum);
+    }
     if (!mac) return 0;
     if (t->prm.kernel == ORC_WENDLAND_C2) {
         /* eps in units of u = L / 2^(lf+1): exact power-of-two scaling */

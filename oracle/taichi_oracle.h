@@ -30,6 +30,8 @@ typedef struct {
     double theta;     /* opening angle of the MAC, Eq. (1)                        */
     double kappa;     /* R = kappa * cell side in Eq. (1)                          */
     double eps;       /* softening length                                          */
+    int mac;          /* 0: R = kappa * side (the paper's Eq. 1); 1: R = radius of a  */
+                      /* sphere about the cell centre enclosing its particles        */
 } orc_params;
 
 typedef struct {
@@ -74,6 +76,9 @@ void orc_tree_geometry(const orc_tree *t, double lo[3], double *L);
 void orc_tree_walk(orc_tree *t, int64_t *n_m2l, int64_t *n_p2p);
 void orc_tree_lists(const orc_tree *t, int64_t *m2l_a, int64_t *m2l_b, int64_t *p2p_a, int64_t *p2p_b);
 int orc_well_separated(const orc_tree *t, int64_t a, int64_t b);
+/* enclosing radius of every cell (used by mac = 1): leaves the largest particle distance from the
+ * cell centre, parents max over children of (|z_child - z_parent| + R_child) */
+void orc_tree_radii(const orc_tree *t, double *r);
 
 /* expansion operators on one cell (for pinning): coefficient arrays of length orc_num_coeffs(p) */
 void orc_p2m(int p, int64_t n, const double *x, const double *y, const double *z, const double *m,
