@@ -48,6 +48,9 @@ def parse():
                     help="theta / p sweep of the unit-cube collapse with HHS and the traditional integrator")
     ap.add_argument("--contrast-n", type=int, default=10000)
     ap.add_argument("--contrast-t", type=float, default=1.0)
+    ap.add_argument("--mac", default="side", choices=["side", "sphere"],
+                    help="multipole acceptance: the paper's R = kappa*side, or enclosing-sphere radii")
+    ap.add_argument("--theta", type=float, default=PARAMS["theta"])
     ap.add_argument("--eta-tot", type=float, default=0.0,
                     help="eta_1 of the Eq. (9) minimum timestep from the total acceleration (0 = off)")
     ap.add_argument("--no-fp64-plain", action="store_true",
@@ -183,7 +186,9 @@ def run_ours(args):
     # replicas only: each rank integrates its own independent system (seed per rank)
     pos0, vel0, mass0 = workload(n, seed=1002 + rank)
     prec = tg.TG_PREC_FP32 if args.precision == "fp32" else tg.TG_PREC_FP64
-    prm = tg.Params(precision=prec, **dict(PARAMS, n_crit=args.n_crit, eta_tot=args.eta_tot))
+    run_params = dict(PARAMS, n_crit=args.n_crit, eta_tot=args.eta_tot, theta=args.theta,
+                      mac=1 if args.mac == "sphere" else 0)
+    prm = tg.Params(precision=prec, **run_params)
     solver = tg.Solver(prm, stream)
     P0 = torch.tensor(pos0, device=dev)
     V0 = torch.tensor(vel0, device=dev)
@@ -272,8 +277,7 @@ def run_ours(args):
     # same tree, walk and schedule, float64 P2P tiles and the generic float64 M2L, no potential skipping
     fp64 = None
     if rank == 0 and prec == tg.TG_PREC_FP32 and not args.no_fp64_plain:
-        s64 = tg.Solver(tg.Params(precision=tg.TG_PREC_FP64, **dict(PARAMS, n_crit=args.n_crit, eta_tot=args.eta_tot)),
-                        stream)
+        s64 = tg.Solver(tg.Params(precision=tg.TG_PREC_FP64, **run_params), stream)
         P64, V64 = P0.clone(), V0.clone()
         s64.hhs_init(P64, V64, M)
         tg.tg_hhs_set_accel(s64.ctx, aold0, acur0, atot0)
@@ -346,7 +350,7 @@ def run_ours(args):
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "n": n, "l2": "flushed (256 MB write) between timed steps",
                    "parallelism": f"replicas x{world}", "kappa": PARAMS["kappa"], "n_crit": args.n_crit,
-                   "eta_tot": args.eta_tot},
+                   "eta_tot": args.eta_tot, "theta": args.theta, "mac": args.mac},
         "accuracy": {"median_force_err_vs_fp64_direct": float(np.median(err)),
                      "p99_force_err": float(np.percentile(err, 99)), "sample_sinks": int(sample.numel()),
                      "momentum_drift_one_step": float(np.abs(d_end[:3] - d_start[:3]).max()),

@@ -51,6 +51,15 @@ typedef enum {
                        /* moments, drift, reductions and outputs in float64                */
 } tg_precision;
 
+typedef enum {
+    TG_MAC_SIDE = 0,    /* Eq. (1) with R = kappa * cell side (the paper's criterion)          */
+    TG_MAC_SPHERE = 1   /* R = radius of a sphere about the cell centre enclosing its particles */
+                        /* (leaves: farthest particle; parents: max over children of            */
+                        /* |z_c - z_p| + R_c), accepted when R_a + R_b < theta |z_a - z_b|,     */
+                        /* decided in float64 with explicit rounding; the eps gap rule stays.  */
+                        /* Not the paper's criterion: the alternative it names (Sec. 2.3, 4)   */
+} tg_mac;
+
 typedef struct {
     int p;            /* expansion order: Taylor terms of total degree <= p, 1 <= p <= 8      */
     int n_crit;       /* a cell holding more than n_crit particles is split (Sec. 2.3), 1..128 */
@@ -66,6 +75,7 @@ typedef struct {
     double eta_tot;   /* eta_1 of the minimum-timestep constraint of Eq. (9), >= 0; 0 = off:  */
                       /* dt_i = min(dt_i, sqrt(eta_tot * eps / |a|_tot,i)), |a|_tot from all  */
                       /* masses, recorded at the second kickFS2S of rung 0 (the whole system) */
+    int mac;          /* tg_mac: the multipole acceptance criterion of the walk             */
 } tg_params;
 
 typedef struct tg_ctx tg_ctx;

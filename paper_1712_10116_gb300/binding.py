@@ -22,6 +22,8 @@ TG_KERNEL_WENDLAND_C2 = 0
 TG_KERNEL_PLUMMER = 1
 TG_PREC_FP64 = 0
 TG_PREC_FP32 = 1
+TG_MAC_SIDE = 0
+TG_MAC_SPHERE = 1
 
 STATUS = {0: "TG_OK", -1: "TG_ERR_ARG", -2: "TG_ERR_OOM", -3: "TG_ERR_CUDA", -4: "TG_ERR_TIMEOUT",
           -5: "TG_ERR_NONFINITE", -6: "TG_ERR_CAPACITY", -7: "TG_ERR_STATE",
@@ -37,7 +39,8 @@ class TGError(RuntimeError):
 class tg_params(C.Structure):
     _fields_ = [("p", C.c_int), ("n_crit", C.c_int), ("kernel", C.c_int), ("precision", C.c_int),
                 ("max_level", C.c_int), ("k_max", C.c_int), ("theta", C.c_double), ("kappa", C.c_double),
-                ("eps", C.c_double), ("eta", C.c_double), ("dt_max", C.c_double), ("eta_tot", C.c_double)]
+                ("eps", C.c_double), ("eta", C.c_double), ("dt_max", C.c_double), ("eta_tot", C.c_double),
+                ("mac", C.c_int)]
 
 
 class tg_stats(C.Structure):
@@ -68,11 +71,12 @@ class Params:
     dt_max: float = 1.0 / 64
     k_max: int = 10
     eta_tot: float = 0.0   # Eq. (9) minimum-timestep constraint, 0 = off
+    mac: int = 0           # TG_MAC_SIDE (the paper's Eq. 1) or TG_MAC_SPHERE (enclosing radii)
 
     def to_c(self) -> tg_params:
         return tg_params(p=self.p, n_crit=self.n_crit, kernel=self.kernel, precision=self.precision,
                          max_level=self.max_level, k_max=self.k_max, theta=self.theta, kappa=self.kappa,
-                         eps=self.eps, eta=self.eta, dt_max=self.dt_max, eta_tot=self.eta_tot)
+                         eps=self.eps, eta=self.eta, dt_max=self.dt_max, eta_tot=self.eta_tot, mac=self.mac)
 
 
 _lib = None

@@ -31,6 +31,7 @@ tg_status validate(const tg_params *p, std::string &why)
     else if (!(p->eta > 0.0) || !std::isfinite(p->eta)) why = "eta must be > 0";
     else if (!(p->dt_max > 0.0) || !std::isfinite(p->dt_max)) why = "dt_max must be > 0";
     else if (!(p->eta_tot >= 0.0) || !std::isfinite(p->eta_tot)) why = "eta_tot must be >= 0";
+    else if (p->mac != TG_MAC_SIDE && p->mac != TG_MAC_SPHERE) why = "unknown mac";
     return why.empty() ? TG_OK : TG_ERR_ARG;
 }
 
@@ -459,7 +460,7 @@ bool same_params(const tg_params &a, const tg_params &b)
 {
     return a.p == b.p && a.n_crit == b.n_crit && a.kernel == b.kernel && a.precision == b.precision &&
            a.max_level == b.max_level && a.k_max == b.k_max && a.theta == b.theta && a.kappa == b.kappa &&
-           a.eps == b.eps && a.eta == b.eta && a.dt_max == b.dt_max && a.eta_tot == b.eta_tot;
+           a.eps == b.eps && a.eta == b.eta && a.dt_max == b.dt_max && a.eta_tot == b.eta_tot && a.mac == b.mac;
 }
 
 }  // namespace

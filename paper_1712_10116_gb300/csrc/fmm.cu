@@ -34,6 +34,9 @@ struct MacParams {
     long long mac_min_d2[kMaxLevel + 1];   // well separated iff d2 >= mac_min_d2[dl]
     long long gap_min_g2[kMaxLevel + 1];   // gap rule passes iff g2 >= gap_min_g2[lf]
     int wendland;
+    int sphere;                            // TG_MAC_SPHERE: R_a + R_b < theta d with the cell radii
+    int log2L;
+    double theta;
 };
 
 // smallest integer v >= 0 with pred(v) (pred monotone), searched over [0, 2^62)
@@ -65,6 +68,9 @@ static MacParams make_mac_params(const tg_params &prm, int log2L)
         mp.gap_min_g2[lf] = min_true([&](long long g2) { return (double)g2 > E; });
     }
     mp.wendland = prm.kernel == TG_KERNEL_WENDLAND_C2;
+    mp.sphere = prm.mac == TG_MAC_SPHERE;
+    mp.log2L = log2L;
+    mp.theta = prm.theta;
     return mp;
 }
 
@@ -83,9 +89,102 @@ __device__ __forceinline__ bool well_separated(const TreeView &t, const MacParam
         const long long gk = dk - (ha + hb);
         if (gk > 0) g2 += gk * gk;
     }
-    if (d2 < mp.mac_min_d2[la > lb ? la - lb : lb - la]) return false;
+    if (mp.sphere) {
+        // R_a + R_b < theta d: a float test settles everything but a 1e-5 band about the threshold,
+        // where the decision is taken in float64 with explicitly rounded operations
+        const float df = sqrtf((float)d2) * pow2f(mp.log2L - lf - 1);
+        const float lhs = t.radf[a] + t.radf[b], rhs = (float)mp.theta * df;
+        bool ok;
+        if (lhs < rhs * (1.0f - 1e-5f)) ok = true;
+        else if (lhs > rhs * (1.0f + 1e-5f)) ok = false;
+        else {
+            const double d = sqrt((double)d2) * ldexp(1.0, mp.log2L - lf - 1);
+            ok = __dadd_rn(t.rad[a], t.rad[b]) < __dmul_rn(mp.theta, d);
+        }
+        if (!ok) return false;
+    } else if (d2 < mp.mac_min_d2[la > lb ? la - lb : lb - la]) {
+        return false;
+    }
     if (mp.wendland && g2 < mp.gap_min_g2[lf]) return false;
     return true;
+}
+
+// ------------------------------------------------------------------ enclosing radii (TG_MAC_SPHERE)
+// Cell centre and distances with explicitly rounded float64 operations (no contraction into FMA), so
+// that the radii are reproducible bit for bit: the acceptance decisions depend on them.
+__device__ __forceinline__ double exact_centre(const Geom &g, const TreeView &t, int c, int axis)
+{
+    const uint32_t ci = axis == 0 ? t.cx[c] : (axis == 1 ? t.cy[c] : t.cz[c]);
+    return __dadd_rn(g.lo[axis], __dmul_rn((double)ci + 0.5, ldexp(g.L, -(int)t.level[c])));
+}
+
+// leaves: the farthest particle from the cell centre (warp per leaf, lanes over particles)
+__global__ void cell_radii_leaves(TreeView t, const Geom *gp, const double *xs, const double *ys, const double *zs,
+                                  double *rad, float *radf)
+{
+    const Geom g = *gp;
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (int c = warp; c < t.ncell; c += nwarps) {
+        if (t.nchild[c] != 0) continue;
+        const double zx = exact_centre(g, t, c, 0), zy = exact_centre(g, t, c, 1), zz = exact_centre(g, t, c, 2);
+        double r = 0.0;
+        for (int s = t.first[c] + lane; s < t.first[c] + t.count[c]; s += 32) {
+            const double dx = __dsub_rn(xs[s], zx), dy = __dsub_rn(ys[s], zy), dz = __dsub_rn(zs[s], zz);
+            const double d = sqrt(__dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz)));
+            r = d > r ? d : r;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const double v = __shfl_xor_sync(0xffffffffu, r, o);
+            r = v > r ? v : r;
+        }
+        if (lane == 0) {
+            rad[c] = r;
+            radf[c] = (float)r;
+        }
+    }
+}
+
+// parents of one level: max over children of |z_c - z_p| + R_c, with |z_c - z_p| = sqrt(3) side / 4
+__global__ void cell_radii_level(TreeView t, int lb, int le, const Geom *gp, double *rad, float *radf)
+{
+    const double L = gp->L;
+    for (int c = lb + blockIdx.x * blockDim.x + threadIdx.x; c < le; c += gridDim.x * blockDim.x) {
+        const int nch = t.nchild[c];
+        if (nch == 0) continue;
+        const double dcp = __dmul_rn(sqrt(3.0), ldexp(L, -((int)t.level[c] + 2)));
+        double r = 0.0;
+        for (int q = 0; q < nch; ++q) {
+            const double v = __dadd_rn(dcp, rad[t.child_first[c] + q]);
+            r = v > r ? v : r;
+        }
+        rad[c] = r;
+        radf[c] = (float)r;
+    }
+}
+
+static tg_status cell_radii(tg_ctx *c, TreeView &t, const Geom *d_geom)
+{
+    tg_status st;
+    double *rad;
+    float *radf;
+    if ((st = ensure_t(c, B_C_RAD, t.ncell, &rad)) || (st = ensure_t(c, B_C_RADF, t.ncell, &radf))) return st;
+    const double *xs = static_cast<const double *>(c->buf[B_XS].p), *ys = static_cast<const double *>(c->buf[B_YS].p),
+                 *zs = static_cast<const double *>(c->buf[B_ZS].p);
+    {
+        ProfScope ps_(c, TG_K_TREE);
+        cell_radii_leaves<<<grid_for((int64_t)t.ncell * 32, 256), 256, 0, c->stream>>>(t, d_geom, xs, ys, zs, rad, radf);
+    }
+    const int nlev = (int)c->level_begin.size() - 1;
+    for (int l = nlev - 2; l >= 0; --l) {
+        const int lb = c->level_begin[l], le = c->level_begin[l + 1];
+        ProfScope ps_(c, TG_K_TREE);
+        cell_radii_level<<<grid_for(le - lb, 128), 128, 0, c->stream>>>(t, lb, le, d_geom, rad, radf);
+    }
+    t.rad = rad;
+    t.radf = radf;
+    return cuda_check(c, cudaGetLastError(), "cell radii");
 }
 
 __device__ __forceinline__ double to_double(float v) { return f2d_exact(v); }
@@ -999,6 +1098,7 @@ tg_status fmm_eval(tg_ctx *c, int n, const double *pos, int64_t stride, const in
     int ncell = 0;
     if ((st = build_octree(c, n, &ncell))) return st;
     TreeView t = tree_view(c, n, ncell);
+    if (c->prm.mac == TG_MAC_SPHERE && (st = cell_radii(c, t, d_geom))) return st;
     int64_t n_blocks = 0, n_m2l = 0, n_p2p = 0, n_self = 0;
     if ((st = run_walk(c, t, &n_blocks, &n_m2l, &n_p2p, &n_self))) return st;
     c->last_n = n;

@@ -52,11 +52,14 @@ struct TreeView {
     const uint32_t *cx, *cy, *cz;   // integer coordinates at the cell's own level
     const int32_t *first, *count, *child_first, *parent;
     const uint8_t *nchild;
+    const double *rad = nullptr;   // enclosing radii (TG_MAC_SPHERE), float64 and float32 copies
+    const float *radf = nullptr;
 };
 
 }  // namespace tg
 
 // ---------------------------------------------------------------- context
+constexpr int kMaxSlots = 96;   // capacity of tg_ctx::buf; the slot enum below is checked against it
 struct tg_ctx {
     tg_params prm;
     cudaStream_t stream = nullptr;
@@ -66,7 +69,7 @@ struct tg_ctx {
     tg_stats stats{};
 
     // scratch buffers, grown on demand
-    tg::Buf buf[64];
+    tg::Buf buf[kMaxSlots];
 
     // counters on the device (p2p pair count) and pinned host mirrors
     unsigned long long *d_counters = nullptr;   // 32 words: [0] p2p particle pairs
@@ -103,7 +106,7 @@ enum Slot {
     B_XS, B_YS, B_ZS, B_MS, B_FS, B_PF, B_LEAF_OF,
     B_XS2, B_YS2, B_ZS2, B_MS2, B_FS2, B_PERM2, B_NSLOW,
     B_C_LEVEL, B_C_X, B_C_Y, B_C_Z, B_C_FIRST, B_C_COUNT, B_C_CHILD, B_C_PARENT, B_C_NCHILD,
-    B_C_TMP0, B_C_TMP1,
+    B_C_TMP0, B_C_TMP1, B_C_RAD, B_C_RADF,
     B_MOM, B_MOMF, B_MOM01, B_LOC, B_ACC,
     B_FRONT0, B_FRONT1, B_M2L, B_P2P, B_WALK_CNT,
     B_SUB_ACC, B_HHS_AOLD, B_HHS_ACUR, B_HHS_ATOT, B_TRAD_ACC, B_TRAD_END, B_HHS_DT, B_HHS_RUNG, B_HHS_IDX, B_HHS_FLAG,
@@ -111,6 +114,7 @@ enum Slot {
     B_OWN_CNT, B_OWN_FILL, B_OWN_OFF, B_OWN_LIST, B_OWN_TAG, B_OWN_PART,
     B_LAST_SLOT
 };
+static_assert(B_LAST_SLOT <= kMaxSlots, "tg_ctx::buf holds fewer entries than there are slots");
 
 tg_status set_err(tg_ctx *c, tg_status code, const char *fmt, ...);
 tg_status cuda_check(tg_ctx *c, cudaError_t e, const char *what);

@@ -40,7 +40,7 @@ def _t(a, dtype=torch.float64):
 
 def _oprm(prm):
     return oracle.params(p=prm.p, theta=prm.theta, eps=prm.eps, kernel=prm.kernel, n_crit=prm.n_crit,
-                         kappa=prm.kappa, max_level=prm.max_level)
+                         kappa=prm.kappa, max_level=prm.max_level, mac=prm.mac)
 
 
 def _rel(a, b, floor=0.0):
@@ -103,6 +103,42 @@ def test_interaction_lists_match_oracle(kind, n, theta, n_crit, kernel):
     assert len({tuple(sorted(p)) for p in p2p.T}) == p2p.shape[1]
     assert _directed(m2l) == set(map(tuple, om2l.T.tolist()))
     assert _directed(p2p) == set(map(tuple, op2p.T.tolist()))
+
+
+@pytest.mark.parametrize("kind,n,theta,n_crit,kernel", [
+    ("plummer", 4000, 0.5, 32, 0), ("clustered", 6000, 0.7, 16, 1), ("sphere", 3000, 0.35, 24, 0)])
+def test_sphere_mac_lists_match_oracle(kind, n, theta, n_crit, kernel):
+    # the enclosing-sphere criterion: radii and decisions in float64 with the oracle's rounding, so
+    # the lists must be identical
+    pos, _, mass = _case(kind, n)
+    prm = tg.Params(p=3, theta=theta, eps=0.02, n_crit=n_crit, kernel=kernel, mac=tg.TG_MAC_SPHERE)
+    s = tg.Solver(prm)
+    s.fmm_forces(_t(pos), _t(mass))
+    m2l, p2p = tg.tg_get_lists(s.ctx)
+    t = oracle.Tree(pos, _oprm(prm))
+    om2l, op2p = t.lists()
+    assert _directed(m2l) == set(map(tuple, om2l.T.tolist()))
+    assert _directed(p2p) == set(map(tuple, op2p.T.tolist()))
+    # and it differs from the side criterion on the same input
+    t_side = oracle.Tree(pos, oracle.params(p=3, theta=theta, eps=0.02, n_crit=n_crit, kernel=kernel))
+    assert set(map(tuple, t_side.lists()[0].T.tolist())) != set(map(tuple, om2l.T.tolist()))
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("masked", [False, True])
+def test_sphere_mac_forces_match_oracle(precision, masked):
+    n = 6000
+    pos, _, _ = _case("clustered", n)
+    mass = ics.random_masses(n, 11)
+    fast = ics.random_fast_mask(n, 12) if masked else None
+    prm = tg.Params(p=5, theta=0.5, eps=0.01, kernel=0, precision=precision, n_crit=32, mac=tg.TG_MAC_SPHERE)
+    s = tg.Solver(prm)
+    acc, pot = s.fmm_forces(_t(pos), _t(mass), None if fast is None else _t(fast, torch.uint8))
+    a_o, p_o = oracle.fmm(pos, mass, _oprm(prm), fast)
+    if precision == tg.TG_PREC_FP64:
+        assert _rel(acc.cpu().numpy(), a_o).max() < 1e-12
+    else:
+        assert _rel(acc.cpu().numpy(), a_o, FP32_FLOOR).max() < FP32_TOL
 
 
 @pytest.mark.parametrize("kernel", [0, 1])

@@ -20,7 +20,7 @@ def _t(a):
 
 def _oprm(prm):
     return oracle.params(p=prm.p, theta=prm.theta, eps=prm.eps, kernel=prm.kernel, n_crit=prm.n_crit,
-                         kappa=prm.kappa, max_level=prm.max_level)
+                         kappa=prm.kappa, max_level=prm.max_level, mac=prm.mac)
 
 
 @pytest.mark.parametrize("kernel", [0, 1])
