@@ -121,7 +121,7 @@ __device__ __noinline__ void owner_rows(const float4 *__restrict__ pf, const Own
                 float gk, ph;
                 if (CLAMP) {
                     close |= r2 < eps2;
-                    const float ri = rsqrtf(fmaxf(r2, eps2));
+                    const float ri = rsqrt_ftz(fmaxf(r2, eps2));
                     ph = -ri;
                     gk = ri * ri * ri;
                 } else {

@@ -10,6 +10,17 @@ namespace tg {
 
 constexpr int kP2PThreads = 64;
 
+// PTX rsqrt.approx.ftz.f32: the hardware approximate reciprocal square root with a subnormal
+// argument flushed to zero.  Only used where the argument is at least eps^2 (or a squared
+// distance between distinct leaves, which is larger), so the flush never applies and the
+// subnormal handling of the non-flushing form is saved.
+__device__ __forceinline__ float rsqrt_ftz(float x)
+{
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 template <class T>
 __device__ __forceinline__ T tg_rsqrt(T x);
 // float: hardware reciprocal square root refined by one Newton step (relative error ~1e-7)
@@ -160,7 +171,7 @@ __device__ __forceinline__ void pair_kernel_f32(float r2, float eps, float eps2,
         g = si * si * si;
         return;
     }
-    const float ri = rsqrtf(r2);
+    const float ri = NEAR ? rsqrtf(r2) : rsqrt_ftz(r2);   // far pairs: r2 >= eps^2
     phi = -ri;
     g = ri * ri * ri;
     if (NEAR && r2 < eps2) pair_kernel<float, TG_KERNEL_WENDLAND_C2>(r2, eps, eps2, inv_eps, inv_eps3, g, phi);
