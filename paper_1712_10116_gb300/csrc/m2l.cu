@@ -1,10 +1,38 @@
 // m2l.cu -- launchers of the mutual M2L kernels (Sec. 2.1): float32 fixed-order block kernels for
-// p <= 6, the generic kernel otherwise and in float64.  Its own translation unit, so that the large
+// p <= 6 (harmonic contraction set for the Wendland kernel, full set for Plummer softening), the
+// generic kernel otherwise and in float64.  Its own translation unit, so that the large
 // generated contractions compile in parallel with the rest.
 #include "tg_common.cuh"
 #include "m2l_sym.cuh"
 
 namespace tg {
+
+// Harmonic set (G = -1/|d|, P <= 6): fold the moments, contract the reduced sets into Lr, complete L.
+template <int P>
+static tg_status m2l_f32_harmonic(tg_ctx *c, const TreeView &t, const M2LBlock *blocks, int64_t nblocks, const float *Ms,
+                                  float *L, int ncp, bool masked, bool pot, int grid)
+{
+    constexpr int NH = M2LGenH<P>::NC;
+    const int ncpr = (NH + 3) & ~3;
+    const int64_t rows = (int64_t)t.ncell * 2;
+    float *Mr, *Lr;
+    tg_status st;
+    if ((st = ensure_t(c, B_MOMH, (size_t)rows * ncpr, &Mr)) || (st = ensure_t(c, B_LOCH, (size_t)rows * ncpr, &Lr)))
+        return st;
+    ProfScope ps_(c, TG_K_M2L);
+    m2l_reduce_moments_h<P><<<grid_for(rows, 128), 128, 0, c->stream>>>(rows, Ms, ncp, Mr, ncpr);
+    cudaMemsetAsync(Lr, 0, sizeof(float) * (size_t)rows * ncpr, c->stream);
+    using G = M2LHarm<P>;
+    if (masked) {
+        if (pot) m2l_blocks_f32<G, true, true><<<grid, 128, 0, c->stream>>>(t, blocks, nblocks, Mr, Lr, ncpr, 0.f, 0);
+        else m2l_blocks_f32<G, true, false><<<grid, 128, 0, c->stream>>>(t, blocks, nblocks, Mr, Lr, ncpr, 0.f, 0);
+    } else {
+        if (pot) m2l_blocks_f32<G, false, true><<<grid, 128, 0, c->stream>>>(t, blocks, nblocks, Mr, Lr, ncpr, 0.f, 0);
+        else m2l_blocks_f32<G, false, false><<<grid, 128, 0, c->stream>>>(t, blocks, nblocks, Mr, Lr, ncpr, 0.f, 0);
+    }
+    m2l_complete_locals_h<P><<<grid_for(rows, 128), 128, 0, c->stream>>>(rows, Lr, ncpr, L, ncp);
+    return cuda_check(c, cudaGetLastError(), "m2l launch");
+}
 
 tg_status launch_m2l_f32(tg_ctx *c, const TreeView &t, const M2LBlock *blocks, int64_t nblocks, const float *Ms,
                          float *L, int p, int nc, int ncp, bool masked, bool pot)
@@ -12,8 +40,19 @@ tg_status launch_m2l_f32(tg_ctx *c, const TreeView &t, const M2LBlock *blocks, i
     const int plummer = c->prm.kernel == TG_KERNEL_PLUMMER;
     const float eoL = (float)ldexp(c->prm.eps, -c->walk_log2L);
     const int grid = grid_for(nblocks * 32, 128, c->num_sms * 16);
+    // Wendland C2: the walk's eps gap rule leaves every M2L pair at r >= eps, where G = -1/r is harmonic
+    if (!plummer && p >= 1 && p <= 6) {
+        switch (p) {
+        case 1: return m2l_f32_harmonic<1>(c, t, blocks, nblocks, Ms, L, ncp, masked, pot, grid);
+        case 2: return m2l_f32_harmonic<2>(c, t, blocks, nblocks, Ms, L, ncp, masked, pot, grid);
+        case 3: return m2l_f32_harmonic<3>(c, t, blocks, nblocks, Ms, L, ncp, masked, pot, grid);
+        case 4: return m2l_f32_harmonic<4>(c, t, blocks, nblocks, Ms, L, ncp, masked, pot, grid);
+        case 5: return m2l_f32_harmonic<5>(c, t, blocks, nblocks, Ms, L, ncp, masked, pot, grid);
+        default: return m2l_f32_harmonic<6>(c, t, blocks, nblocks, Ms, L, ncp, masked, pot, grid);
+        }
+    }
     ProfScope ps_(c, TG_K_M2L);
-#define TG_M2L_F32_(PP, MK, PT) m2l_blocks_f32<PP, MK, PT><<<grid, 128, 0, c->stream>>>(t, blocks, nblocks, Ms, L, ncp, eoL, plummer)
+#define TG_M2L_F32_(PP, MK, PT) m2l_blocks_f32<M2LFull<PP>, MK, PT><<<grid, 128, 0, c->stream>>>(t, blocks, nblocks, Ms, L, ncp, eoL, plummer)
 #define TG_M2L_F32(PP)                                                                                            \
     case PP:                                                                                                      \
         if (masked) { if (pot) TG_M2L_F32_(PP, true, true); else TG_M2L_F32_(PP, true, false); }                   \

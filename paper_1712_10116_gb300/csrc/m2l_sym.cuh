@@ -24,14 +24,6 @@
 
 namespace tg {
 
-// total degree of the k-th multi-index (ordering by total degree)
-__host__ __device__ constexpr int order_of(int k)
-{
-    int o = 0;
-    while ((o + 1) * (o + 2) * (o + 3) / 6 <= k) ++o;
-    return o;
-}
-
 // children of the opened cells (a cell that is not opened stands for itself)
 struct BlockGeom {
     int baseA, baseB, ni, nj, lx, ly;
@@ -69,13 +61,69 @@ __device__ __forceinline__ void pair_offset(const TreeView &t, int x, int y, int
 // round).  The 8 lanes of a row and the 4 lanes of a column combine their partial expansions with a
 // reduce-scatter (coefficients padded to RL per row lane, CL per column lane), after which every
 // lane adds its own slice to global memory: no lane holds the whole sum.
-template <int P>
+template <int NC_>
 struct M2LScatter {
-    static constexpr int NC = M2LGen<P>::NC;
+    static constexpr int NC = NC_;
     static constexpr int RL = (NC + 31) / 32 * 4;   // coefficients per lane after the row reduction
     static constexpr int CL = (NC + 15) / 16 * 4;   // ... after the column reduction
     static constexpr int NP = 8 * RL > 4 * CL ? 8 * RL : 4 * CL;
 };
+
+// The two contraction sets of the block kernel.  Full: every coefficient |k| <= P, any G (the
+// softened one included).  Harmonic (G = -1/|d| only): moments folded to j_z <= 1 per cell, locals
+// formed for n_z <= 1 and completed per cell, D for k_z <= 2 (see gen_m2l.py); same result in exact
+// arithmetic, (P+1)^2 instead of (P+1)(P+2)(P+3)/6 coefficients per side.
+template <int P>
+struct M2LFull : M2LGen<P> {
+    static constexpr int ND = M2LGen<P>::NC;
+    static constexpr bool HARMONIC = false;
+    static __device__ __forceinline__ void dt(float dx, float dy, float dz, float soft2, float (&D)[ND])
+    {
+        M2LGen<P>::dtensor(dx, dy, dz, soft2, D);
+    }
+};
+template <int P>
+struct M2LHarm : M2LGenH<P> {
+    static constexpr int ND = M2LGenH<P>::ND;
+    static constexpr bool HARMONIC = true;
+    static __device__ __forceinline__ void dt(float dx, float dy, float dz, float, float (&D)[ND])
+    {
+        M2LGenH<P>::dtensor(dx, dy, dz, D);
+    }
+};
+
+// first index of total degree o in a coefficient list (both lists are ordered by total degree)
+__host__ __device__ constexpr int first_of_order(bool harmonic, int o)
+{
+    return harmonic ? o * o : o * (o + 1) * (o + 2) / 6;
+}
+__host__ __device__ constexpr int order_in(bool harmonic, int k)
+{
+    int o = 0;
+    while (first_of_order(harmonic, o + 1) <= k) ++o;
+    return o;
+}
+
+// per cell and class: fold the moments onto j_z <= 1 (pads zeroed)
+template <int P>
+__global__ void m2l_reduce_moments_h(int64_t nrows, const float *__restrict__ Ms, int ncp, float *__restrict__ Mr, int ncpr)
+{
+    for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < nrows; w += (int64_t)gridDim.x * blockDim.x) {
+        M2LGenH<P>::reduce_moments(Ms + w * ncp, Mr + w * ncpr);
+        for (int k = M2LGenH<P>::NC; k < ncpr; ++k) Mr[w * ncpr + k] = 0.f;
+    }
+}
+
+// per cell and class: the full local expansion from its n_z <= 1 coefficients (pads zeroed)
+template <int P>
+__global__ void m2l_complete_locals_h(int64_t nrows, const float *__restrict__ Lr, int ncpr, float *__restrict__ L, int ncp)
+{
+    constexpr int NC = M2LGen<P>::NC;
+    for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < nrows; w += (int64_t)gridDim.x * blockDim.x) {
+        M2LGenH<P>::complete_locals(Lr + w * ncpr, L + w * ncp);
+        for (int k = NC; k < ncp; ++k) L[w * ncp + k] = 0.f;
+    }
+}
 
 // halve the live coefficients once: lanes with bit d keep the upper half, the others the lower half
 template <int NP, int H>
@@ -91,13 +139,14 @@ __device__ __forceinline__ void m2l_halve(float (&v)[NP], int lane, int d)
 }
 
 // POT = false: accelerations only, L^0 is left at zero (see the generated *_forces contractions).
-template <int P, bool MASKED, bool POT>
+// G: M2LFull<P> or M2LHarm<P>; Ms and L hold that set's coefficients with row stride ncp.
+template <class G, bool MASKED, bool POT>
 __global__ void __launch_bounds__(128) m2l_blocks_f32(TreeView t, const M2LBlock *__restrict__ blocks, int64_t nblocks,
                                                       const float *__restrict__ Ms, float *L, int ncp, float eps_over_L,
                                                       int plummer)
 {
-    using S = M2LScatter<P>;
-    constexpr int NC = S::NC, RL = S::RL, CL = S::CL, NP = S::NP;
+    using S = M2LScatter<G::NC>;
+    constexpr int NC = S::NC, RL = S::RL, CL = S::CL, NP = S::NP, ND = G::ND;
     const int lane = threadIdx.x & 31;
     const int j = lane & 7, rr = (lane >> 3) & 3;
     const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -128,14 +177,14 @@ __global__ void __launch_bounds__(128) m2l_blocks_f32(TreeView t, const M2LBlock
             // inactive lanes run the contractions on a zero tensor and an existing cell's moments
             const int x = bg.baseA + (i < 0 ? 0 : i), y = bg.baseB + j;
             const int xs = active ? x : bg.baseA, ys = active ? y : bg.baseB;
-            float D[NC];
+            float D[ND];
             if (active) {
                 float dx, dy, dz;
                 pair_offset<float>(t, x, y, bg.lx, bg.ly, dx, dy, dz);
-                M2LGen<P>::dtensor(dx, dy, dz, soft2, D);
+                G::dt(dx, dy, dz, soft2, D);
             } else {
 #pragma unroll
-                for (int k = 0; k < NC; ++k) D[k] = 0.f;
+                for (int k = 0; k < ND; ++k) D[k] = 0.f;
             }
             const bool row_used = ((amask >> (lane & ~7)) & 0xffu) != 0u;   // this lane's row, this round
             const bool col_used = (amask & (0x01010101u << j)) != 0u;      // this lane's column, this round
@@ -146,8 +195,8 @@ __global__ void __launch_bounds__(128) m2l_blocks_f32(TreeView t, const M2LBlock
                 // lane j keeps coefficients RL*j .. RL*j + RL - 1
 #pragma unroll
                 for (int k = NC; k < NP; ++k) Lc[k] = 0.f;
-                if (POT) M2LGen<P>::side_a(D, Ms + ((size_t)ys * 2 + cls) * ncp, rho, reinterpret_cast<float(&)[NC]>(Lc));
-                else M2LGen<P>::side_a_forces(D, Ms + ((size_t)ys * 2 + cls) * ncp, rho, reinterpret_cast<float(&)[NC]>(Lc));
+                if (POT) G::side_a(D, Ms + ((size_t)ys * 2 + cls) * ncp, rho, reinterpret_cast<float(&)[NC]>(Lc));
+                else G::side_a_forces(D, Ms + ((size_t)ys * 2 + cls) * ncp, rho, reinterpret_cast<float(&)[NC]>(Lc));
                 m2l_halve<NP, 4 * RL>(Lc, lane, 4);
                 m2l_halve<NP, 2 * RL>(Lc, lane, 2);
                 m2l_halve<NP, RL>(Lc, lane, 1);
@@ -163,16 +212,16 @@ __global__ void __launch_bounds__(128) m2l_blocks_f32(TreeView t, const M2LBlock
                 // lane (rr, j) keeps coefficients CL*rr .. CL*rr + CL - 1 of column j
 #pragma unroll
                 for (int k = NC; k < NP; ++k) Lc[k] = 0.f;
-                if (POT) M2LGen<P>::side_b(D, Ms + ((size_t)xs * 2 + cls) * ncp, reinterpret_cast<float(&)[NC]>(Lc));
-                else M2LGen<P>::side_b_forces(D, Ms + ((size_t)xs * 2 + cls) * ncp, reinterpret_cast<float(&)[NC]>(Lc));
+                if (POT) G::side_b(D, Ms + ((size_t)xs * 2 + cls) * ncp, reinterpret_cast<float(&)[NC]>(Lc));
+                else G::side_b_forces(D, Ms + ((size_t)xs * 2 + cls) * ncp, reinterpret_cast<float(&)[NC]>(Lc));
                 m2l_halve<NP, 2 * CL>(Lc, lane, 16);
                 m2l_halve<NP, CL>(Lc, lane, 8);
                 if (col_used) {
                     // the sums are in the x normalisation: L~_y^n carries rho^(|n|+1)
                     float *dst = L + ((size_t)y * 2 + cls) * ncp;
                     const int k0 = CL * rr;
-                    int o = order_of(k0);
-                    int next = (o + 1) * (o + 2) * (o + 3) / 6;   // first index of order o + 1
+                    int o = order_in(G::HARMONIC, k0);
+                    int next = first_of_order(G::HARMONIC, o + 1);
                     float sc = ldexpf(1.0f, (bg.lx - bg.ly) * (o + 1));
 #pragma unroll
                     for (int g = 0; g < CL; g += 4) {
@@ -182,7 +231,7 @@ __global__ void __launch_bounds__(128) m2l_blocks_f32(TreeView t, const M2LBlock
                             const int k = k0 + g + q;
                             if (k == next) {
                                 ++o;
-                                next = (o + 1) * (o + 2) * (o + 3) / 6;
+                                next = first_of_order(G::HARMONIC, o + 1);
                                 sc *= rho;
                             }
                             v[q] = Lc[g + q] * sc;

@@ -107,7 +107,7 @@ enum Slot {
     B_XS2, B_YS2, B_ZS2, B_MS2, B_FS2, B_PERM2, B_NSLOW,
     B_C_LEVEL, B_C_X, B_C_Y, B_C_Z, B_C_FIRST, B_C_COUNT, B_C_CHILD, B_C_PARENT, B_C_NCHILD,
     B_C_TMP0, B_C_TMP1, B_C_RAD, B_C_RADF,
-    B_MOM, B_MOMF, B_MOM01, B_LOC, B_ACC,
+    B_MOM, B_MOMF, B_MOM01, B_LOC, B_ACC, B_MOMH, B_LOCH,
     B_FRONT0, B_FRONT1, B_M2L, B_P2P, B_WALK_CNT,
     B_SUB_ACC, B_HHS_AOLD, B_HHS_ACUR, B_HHS_ATOT, B_TRAD_ACC, B_TRAD_END, B_HHS_DT, B_HHS_RUNG, B_HHS_IDX, B_HHS_FLAG,
     B_HHS_SCAN, B_HHS_TMP, B_RED, B_DIAG_POT, B_DIAG_ACC,
