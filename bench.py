@@ -44,6 +44,8 @@ def parse():
     ap.add_argument("--momentum-contrast", action="store_true",
                     help="run HHS and the traditional integrator to t = --contrast-t on the unit-cube collapse "
                          "and print |sum m v| for both")
+    ap.add_argument("--sweep-grid", default="",
+                    help="with --sweep: comma-separated theta:p points instead of the default grid")
     ap.add_argument("--sweep", action="store_true",
                     help="theta / p sweep of the unit-cube collapse with HHS and the traditional integrator")
     ap.add_argument("--contrast-n", type=int, default=10000)
@@ -509,7 +511,11 @@ def run_sweep(args):
     pos, vel, mass = ics.uniform_cube(n, 1006)
     dt_max = 1.0 / 64
     steps = int(round(args.contrast_t / dt_max))
-    grid = [(th, 5) for th in (0.7, 0.45, 0.3, 0.2, 0.1, 0.05)] + [(0.45, p) for p in (3, 4, 6, 7, 8)]
+    if args.sweep_grid:
+        grid = [(float(a), int(b)) for a, b in (item.split(":") for item in args.sweep_grid.split(","))]
+    else:
+        grid = [(th, 5) for th in (0.7, 0.45, 0.3, 0.2, 0.1, 0.05)] + \
+               [(0.45, p) for p in (3, 4, 6, 7, 8, 10, 12, 16, 20)]
     rows = []
     for theta, p in grid:
         row = {"theta": theta, "p": p}

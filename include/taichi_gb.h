@@ -61,7 +61,9 @@ typedef enum {
 } tg_mac;
 
 typedef struct {
-    int p;            /* expansion order: Taylor terms of total degree <= p, 1 <= p <= 8      */
+    int p;            /* expansion order: Taylor terms of total degree <= p, 1 <= p <= 20     */
+                      /* (p <= 6: generated float32 contractions; p > 8: table-free kernels   */
+                      /* for the order sweeps of Sec. 3.2, slower)                             */
     int n_crit;       /* a cell holding more than n_crit particles is split (Sec. 2.3), 1..128 */
     int kernel;       /* tg_kernel                                                          */
     int precision;    /* tg_precision                                                       */

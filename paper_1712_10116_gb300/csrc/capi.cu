@@ -19,7 +19,7 @@ tg_status validate(const tg_params *p, std::string &why)
         why = "params is NULL";
         return TG_ERR_ARG;
     }
-    if (p->p < 1 || p->p > kPMaxGpu) why = "p must be in [1, 8]";
+    if (p->p < 1 || p->p > kPHigh) why = "p must be in [1, 20]";
     else if (p->n_crit < 1 || p->n_crit > kMaxNcrit) why = "n_crit must be in [1, 128]";
     else if (p->kernel != TG_KERNEL_WENDLAND_C2 && p->kernel != TG_KERNEL_PLUMMER) why = "unknown kernel";
     else if (p->precision != TG_PREC_FP64 && p->precision != TG_PREC_FP32) why = "unknown precision";

@@ -17,13 +17,6 @@
 
 namespace tg {
 
-// ------------------------------------------------------------------ cell geometry
-__device__ __forceinline__ double cell_centre(const Geom &g, const TreeView &t, int c, int axis)
-{
-    const uint32_t ci = axis == 0 ? t.cx[c] : (axis == 1 ? t.cy[c] : t.cz[c]);
-    return g.lo[axis] + ((double)ci + 0.5) * ldexp(g.L, -(int)t.level[c]);
-}
-
 // Eq. (1) with R = kappa * side, and the rule that cell pairs closer than eps (cube gap) never use
 // M2L for the Wendland kernel.  In integer units of half the finer cell's side the tests read
 //   (double)d2 * theta^2 > kappa^2 * (2 (h_a + h_b))^2   and   (double)g2 > (eps / u)^2,
@@ -477,6 +470,21 @@ __global__ void __launch_bounds__(kM2MThreads) m2m_level(TreeView t, int lb, int
 
 // M2L operands: Ms[c][0] = (M~_S + M~_F)/j!, Ms[c][1] = M~_S/j! in precision T (padding zero);
 // the monopole and dipole come from the float64 sums.
+// 1/(kx! ky! kz!) for a multi-index past the tables (orders above TG_PMAX)
+__device__ double inv_fact_beyond_tables(int k)
+{
+    int o = 0;
+    while ((o + 1) * (o + 2) * (o + 3) / 6 <= k) ++o;
+    int r = k - o * (o + 1) * (o + 2) / 6, a = 0;
+    while ((a + 1) * (a + 2) / 2 <= r) ++a;
+    const int kz = r - a * (a + 1) / 2, kx = o - a, ky = a - kz;
+    double f = 1.0;
+    for (int i = 2; i <= kx; ++i) f *= i;
+    for (int i = 2; i <= ky; ++i) f *= i;
+    for (int i = 2; i <= kz; ++i) f *= i;
+    return 1.0 / f;
+}
+
 template <class T>
 __global__ void scale_moments(int ncell, int nc, int ncp, const T *M, const double *M01, T *Ms)
 {
@@ -491,7 +499,7 @@ __global__ void scale_moments(int ncell, int nc, int ncp, const T *M, const doub
             Ms[(c * 2 + 1) * ncp + k] = (T)(mS * f);
         } else {
             const T mS = M[(c * 2 + 0) * ncp + k], mF = M[(c * 2 + 1) * ncp + k];
-            const T f = k < nc ? inv_fact_t<T>(k) : T(0);
+            const T f = k < nc ? (k < TG_NCOEF_MAX ? inv_fact_t<T>(k) : (T)inv_fact_beyond_tables(k)) : T(0);
             Ms[(c * 2 + 0) * ncp + k] = (mS + mF) * f;
             Ms[(c * 2 + 1) * ncp + k] = mS * f;
         }
@@ -1034,7 +1042,10 @@ static tg_status eval_typed(tg_ctx *c, int n, int ncell, const TreeView &t, cons
         ProfScope ps_(c, TG_K_UP);
         leaf_particles<T4><<<grid_for((int64_t)ncell * 32, 256), 256, 0, c->stream>>>(t, d_geom, xs, ys, zs, ms, pf, leaf_of);
     }
-    {
+    const bool high = p > TG_PMAX;   // orders past the tables: high_order.cu
+    if (high) {
+        if ((st = launch_p2m_hi<T, T4>(c, t, d_geom, xs, ys, zs, ms, fs, pf, p, nc, ncp, M, M01))) return st;
+    } else {
         ProfScope ps_(c, TG_K_UP);
         p2m_leaves<T, T4><<<grid_for((int64_t)ncell * 32, 128), 128, 0, c->stream>>>(t, d_geom, xs, ys, zs, ms, fs, pf, p, nc,
                                                                                      ncp, M, M01);
@@ -1042,6 +1053,10 @@ static tg_status eval_typed(tg_ctx *c, int n, int ncell, const TreeView &t, cons
     const int nlev = (int)c->level_begin.size() - 1;
     for (int l = nlev - 2; l >= 0; --l) {
         const int lb = c->level_begin[l], le = c->level_begin[l + 1];
+        if (high) {
+            if ((st = launch_m2m_hi<T>(c, t, lb, le, p, nc, ncp, M, M01))) return st;
+            continue;
+        }
         ProfScope ps_(c, TG_K_UP);
         m2m_level<T><<<std::min(le - lb, c->num_sms * 8), kM2MThreads, 8 * 2 * ncp * sizeof(T), c->stream>>>(
             t, lb, le, p, nc, ncp, M, M01);
@@ -1056,12 +1071,18 @@ static tg_status eval_typed(tg_ctx *c, int n, int ncell, const TreeView &t, cons
     if (n_blocks > 0 && (st = launch_m2l_t(c, t, blocks, n_blocks, Ms, L, p, nc, ncp, masked, want_pot))) return st;
     for (int l = 1; l < nlev; ++l) {
         const int lb = c->level_begin[l], le = c->level_begin[l + 1];
+        if (high) {
+            if ((st = launch_l2l_hi<T>(c, t, lb, le, p, nc, ncp, ncls, want_pot ? 0 : 1, L))) return st;
+            continue;
+        }
         ProfScope ps_(c, TG_K_DOWN);
         l2l_level<T><<<grid_for((int64_t)(le - lb) * 32, 32 * kM2MWarps), 32 * kM2MWarps,
                        kM2MWarps * 2 * ncp * sizeof(T), c->stream>>>(t, lb, le, p, nc, ncp, ncls,
                                                                      want_pot ? 0 : 1, L);
     }
-    {
+    if (high) {
+        if ((st = launch_l2p_hi<T, T4>(c, n, t, pf, leaf_of, fs, masked, p, ncp, L, acc4))) return st;
+    } else {
         ProfScope ps_(c, TG_K_DOWN);
         const int g = grid_for(n, 128), mk = masked ? 1 : 0;
 #define TG_L2P(PP)                                                                                                 \

@@ -1,6 +1,6 @@
 // m2l.cu -- launchers of the mutual M2L kernels (Sec. 2.1): float32 fixed-order block kernels for
 // p <= 6 (harmonic contraction set for the Wendland kernel, full set for Plummer softening), the
-// generic kernel otherwise and in float64.  Its own translation unit, so that the large
+// generic kernel otherwise and in float64 up to the table order, high_order.cu above it.  Its own translation unit, so that the large
 // generated contractions compile in parallel with the rest.
 #include "tg_common.cuh"
 #include "m2l_sym.cuh"
@@ -39,6 +39,7 @@ tg_status launch_m2l_f32(tg_ctx *c, const TreeView &t, const M2LBlock *blocks, i
 {
     const int plummer = c->prm.kernel == TG_KERNEL_PLUMMER;
     const float eoL = (float)ldexp(c->prm.eps, -c->walk_log2L);
+    if (p > TG_PMAX) return launch_m2l_hi<float>(c, t, blocks, nblocks, Ms, L, p, nc, ncp, masked, pot);
     const int grid = grid_for(nblocks * 32, 128, c->num_sms * 16);
     // Wendland C2: the walk's eps gap rule leaves every M2L pair at r >= eps, where G = -1/r is harmonic
     if (!plummer && p >= 1 && p <= 6) {
@@ -79,6 +80,7 @@ tg_status launch_m2l_f32(tg_ctx *c, const TreeView &t, const M2LBlock *blocks, i
 tg_status launch_m2l_f64(tg_ctx *c, const TreeView &t, const M2LBlock *blocks, int64_t nblocks, const double *Ms,
                          double *L, int p, int nc, int ncp, bool masked)
 {
+    if (p > TG_PMAX) return launch_m2l_hi<double>(c, t, blocks, nblocks, Ms, L, p, nc, ncp, masked, true);
     const int plummer = c->prm.kernel == TG_KERNEL_PLUMMER;
     const double eoL = ldexp(c->prm.eps, -c->walk_log2L);
     const int grid = grid_for(nblocks * 32, 128, c->num_sms * 16);

@@ -13,7 +13,6 @@ namespace tg {
 
 constexpr int kMaxLevel = 21;         // Morton keys carry 21 bits per axis
 constexpr int kMaxNcrit = 128;        // leaf capacity supported by the P2P tiles
-constexpr int kPMaxGpu = 8;           // expansion orders supported on the GPU
 
 inline int ncoef(int p) { return (p + 1) * (p + 2) * (p + 3) / 6; }
 
@@ -146,6 +145,24 @@ tg_status keys_sort_gather(tg_ctx *c, int n, const double *pos, int64_t stride, 
 tg_status build_octree(tg_ctx *c, int n, int *ncell_out);
 TreeView tree_view(tg_ctx *c, int n, int ncell);
 
+// Expansion kernels for orders above the fixed tables (TG_PMAX < p <= kPHigh), high_order.cu.
+constexpr int kPHigh = 20;
+template <class T, class T4>
+tg_status launch_p2m_hi(tg_ctx *c, const TreeView &t, const Geom *d_geom, const double *xs, const double *ys,
+                        const double *zs, const double *ms, const uint8_t *fs, const T4 *pf, int p, int nc, int ncp,
+                        T *M, double *M01);
+template <class T>
+tg_status launch_m2m_hi(tg_ctx *c, const TreeView &t, int lb, int le, int p, int nc, int ncp, T *M, double *M01);
+template <class T>
+tg_status launch_m2l_hi(tg_ctx *c, const TreeView &t, const M2LBlock *blocks, int64_t nblocks, const T *Ms, T *L,
+                        int p, int nc, int ncp, bool masked, bool pot);
+template <class T>
+tg_status launch_l2l_hi(tg_ctx *c, const TreeView &t, int lb, int le, int p, int nc, int ncp, int ncls, int n_first,
+                        T *L);
+template <class T, class T4>
+tg_status launch_l2p_hi(tg_ctx *c, int n, const TreeView &t, const T4 *pf, const int32_t *leaf_of, const uint8_t *fs,
+                        bool masked, int p, int ncp, const T *L, double *acc4);
+
 // Device-wide exclusive scan of uint32 (in place allowed); optional total to a device word.
 tg_status exclusive_scan_u32(tg_ctx *c, const uint32_t *in, uint32_t *out, int n, uint32_t *d_total);
 
@@ -243,6 +260,13 @@ __device__ __forceinline__ long long centre_delta(uint32_t ca, int la, uint32_t 
 __device__ __forceinline__ float pow2f(int e) { return __int_as_float((e + 127) << 23); }
 
 __host__ __device__ __forceinline__ int ncoef_dev(int p) { return (p + 1) * (p + 2) * (p + 3) / 6; }
+
+// centre of cell c along one axis: lo + (i + 1/2) L / 2^level (exact: dyadic)
+__device__ __forceinline__ double cell_centre(const Geom &g, const TreeView &t, int c, int axis)
+{
+    const uint32_t ci = axis == 0 ? t.cx[c] : (axis == 1 ? t.cy[c] : t.cz[c]);
+    return g.lo[axis] + ((double)ci + 0.5) * ldexp(g.L, -(int)t.level[c]);
+}
 
 template <class T>
 __device__ __forceinline__ T warp_sum(T v)

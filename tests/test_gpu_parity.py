@@ -318,6 +318,8 @@ def test_argument_errors_leave_outputs():
         tg.tg_hhs_step(s.ctx)
     with pytest.raises(tg.TGError):
         tg.tg_create(tg.Params(p=0))
+    with pytest.raises(tg.TGError):
+        tg.tg_create(tg.Params(p=21))
 
 
 # ---------------------------------------------------------------- HHS
@@ -441,3 +443,40 @@ def test_cold_collapse_full_size_sampled():
     ad, _ = s.direct_forces(_t(pos), _t(mass), None, _t(sample, torch.int64))
     e = np.linalg.norm(a - ad.cpu().numpy(), axis=0) / np.linalg.norm(ad.cpu().numpy(), axis=0)
     assert np.median(e) < 1e-4
+
+
+# ---------------------------------------------------------------- orders above the fixed tables
+@pytest.mark.parametrize("p,kernel,masked,precision", [(10, 0, False, 0), (14, 0, True, 0), (20, 0, False, 0),
+                                                       (20, 0, True, 0), (12, 1, False, 0), (12, 1, True, 0),
+                                                       (10, 0, False, 1), (10, 0, True, 1)])
+def test_high_order_matches_oracle(p, kernel, masked, precision):
+    # table-free kernels for 8 < p <= 20 (harmonic M2L for Wendland, the full set for Plummer)
+    n = 1200
+    pos, _, _ = _case("clustered", n)
+    mass = ics.random_masses(n, 11)
+    fast = ics.random_fast_mask(n, 12) if masked else None
+    prm = tg.Params(p=p, theta=0.5, eps=0.01, kernel=kernel, precision=precision, n_crit=32)
+    s = tg.Solver(prm)
+    acc, pot = s.fmm_forces(_t(pos), _t(mass), None if fast is None else _t(fast, torch.uint8))
+    a_o, p_o = oracle.fmm(pos, mass, _oprm(prm), fast)
+    a = acc.cpu().numpy()
+    if precision == tg.TG_PREC_FP64:
+        assert _rel(a, a_o).max() < 1e-12
+        assert np.abs(pot.cpu().numpy() - p_o).max() < 1e-12 * np.abs(p_o).max()
+    else:
+        assert _rel(a, a_o, FP32_FLOOR).max() < FP32_TOL
+
+
+def test_high_order_error_falls_to_roundoff():
+    n = 1500
+    pos, _, _ = _case("clustered", n)
+    mass = ics.random_masses(n, 11)
+    ad, _ = oracle.direct(pos, mass, 0.01, oracle.WENDLAND_C2)
+    med = []
+    for p in (8, 12, 16, 20):
+        s = tg.Solver(tg.Params(p=p, theta=0.5, eps=0.01, kernel=0, precision=tg.TG_PREC_FP64, n_crit=32))
+        acc, _ = s.fmm_forces(_t(pos), _t(mass))
+        med.append(np.median(_rel(acc.cpu().numpy(), ad)))
+    assert all(b < a / 20 for a, b in zip(med, med[1:]))
+    assert med[-1] < 1e-12
+

@@ -87,12 +87,14 @@ def _m2l_error(p, dist):
 
 def test_m2l_converges_with_order():
     # cubes of side 1 at centre distance ~4.2: convergence ratio (r_A + r_B)/d ~ 0.41
-    errs = [_m2l_error(p, 4.0) for p in (1, 2, 4, 6, 8, 10)]
+    orders = (1, 2, 4, 6, 8, 10, 14, 20)   # up to the highest order of the sweeps (Sec. 3.2)
+    errs = [_m2l_error(p, 4.0) for p in orders]
     assert all(b < a for a, b in zip(errs, errs[1:]))
     ratio = 2 * (np.sqrt(3) / 2) / np.linalg.norm([4.0, 1.2, 0.8])
-    for p, e in zip((1, 2, 4, 6, 8, 10), errs):
+    for p, e in zip(orders, errs):
         assert e < 3.0 * ratio ** (p + 1)
-    assert errs[-1] < 1e-5
+    assert errs[orders.index(10)] < 1e-5
+    assert errs[-1] < 1e-10
 
 
 def test_m2l_mutual_forces_cancel():

@@ -99,3 +99,18 @@ def test_edge_cases():
     a, _ = oracle.fmm(pos, m, prm)
     ad, _ = oracle.direct(pos, m, 0.01)
     assert np.median(_rel_err(a, ad)) < 1e-6
+
+
+def test_high_orders_converge_to_direct_summation():
+    # orders up to 20 (the sweeps of Sec. 3.2): the error against direct summation keeps falling
+    # geometrically and reaches the float64 roundoff level
+    pos, _, _ = ics.clustered(500, 1007)
+    m = ics.random_masses(500, 11)
+    ad, _ = oracle.direct(pos, m, 0.01, oracle.WENDLAND_C2)
+    med = []
+    for p in (6, 12, 20):
+        a, _ = oracle.fmm(pos, m, oracle.params(p=p, theta=0.5, eps=0.01, n_crit=8))
+        med.append(np.median(_rel_err(a, ad)))
+    assert med[0] > 30 * med[1] > 900 * med[2]
+    assert med[2] < 1e-12
+
