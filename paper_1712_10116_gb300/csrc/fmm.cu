@@ -556,8 +556,8 @@ __global__ void walk_step(TreeView t, MacParams mp, const uint2 *front_in, const
         const bool active = w < n_in;
         int A = 0, B = 0, ni = 0, nj = 0, baseA = 0, baseB = 0;
         bool self = false;
-        unsigned long long mask = 0;
-        unsigned n_front = 0, n_p2p = 0, n_self = 0;
+        // classes of the child pairs, bit 8i + j: well separated (M2L), P2P, self P2P, frontier
+        unsigned long long mask = 0, mp2p = 0, mself = 0, mfront = 0;
         if (active) {
             const uint2 pr = front_in[w];
             A = (int)pr.x;
@@ -568,48 +568,47 @@ __global__ void walk_step(TreeView t, MacParams mp, const uint2 *front_in, const
             nj = openB ? t.nchild[B] : 1;
             baseA = openA ? t.child_first[A] : A;
             baseB = openB ? t.child_first[B] : B;
-            // pass 1: classify and count
+            // classify every child pair once
             for (int i = 0; i < ni; ++i)
                 for (int j = self ? i : 0; j < nj; ++j) {
                     const int x = baseA + i, y = baseB + j;
                     const bool lx = t.nchild[x] == 0, ly = t.nchild[y] == 0;
+                    const unsigned long long bit = 1ull << (8 * i + j);
                     if (x == y) {
-                        if (lx) ++n_self;
-                        else ++n_front;
+                        if (lx) mself |= bit;
+                        else mfront |= bit;
                     } else if (well_separated(t, mp, x, y)) {
-                        mask |= 1ull << (8 * i + j);
+                        mask |= bit;
                     } else if (lx && ly) {
-                        ++n_p2p;
+                        mp2p |= bit;
                     } else {
-                        ++n_front;
+                        mfront |= bit;
                     }
                 }
         }
-        unsigned long long fb = warp_reserve(o.front_ctr, n_front);
-        unsigned long long pb = warp_reserve(o.counters + 2, n_p2p);
-        unsigned long long sb = warp_reserve(o.counters + 4, n_self);
+        unsigned long long fb = warp_reserve(o.front_ctr, (unsigned)__popcll(mfront));
+        unsigned long long pb = warp_reserve(o.counters + 2, (unsigned)__popcll(mp2p));
+        unsigned long long sb = warp_reserve(o.counters + 4, (unsigned)__popcll(mself));
         const unsigned long long bb = warp_reserve(o.counters + 1, mask ? 1u : 0u);
         warp_reserve(o.counters + 3, (unsigned)__popcll(mask));
         if (!active) continue;
         if (mask && bb < o.cap_blocks) o.blocks[bb] = M2LBlock{(uint32_t)A, (uint32_t)B, mask};
-        if (!n_front && !n_p2p && !n_self) continue;
-        // pass 2: write the frontier and P2P entries
-        for (int i = 0; i < ni; ++i)
-            for (int j = self ? i : 0; j < nj; ++j) {
-                if ((mask >> (8 * i + j)) & 1ull) continue;
-                const int x = baseA + i, y = baseB + j;
-                const bool lx = t.nchild[x] == 0, ly = t.nchild[y] == 0;
-                if (x == y && lx) {
-                    if (sb < o.cap_p2p) o.p2p[o.cap_p2p - 1 - sb] = make_uint2(x, x);
-                    ++sb;
-                } else if (x != y && lx && ly) {
-                    if (pb < o.cap_p2p) o.p2p[pb] = make_uint2(x, y);
-                    ++pb;
-                } else {
-                    if (fb < o.cap_front) o.front_out[fb] = make_uint2(x, y);
-                    ++fb;
-                }
-            }
+        // write the entries of each class from its bits (lowest bit first, the order of the loops above)
+        for (unsigned long long m = mself; m; m &= m - 1) {
+            const int b = __ffsll((long long)m) - 1, x = baseA + (b >> 3);
+            if (sb < o.cap_p2p) o.p2p[o.cap_p2p - 1 - sb] = make_uint2(x, x);
+            ++sb;
+        }
+        for (unsigned long long m = mp2p; m; m &= m - 1) {
+            const int b = __ffsll((long long)m) - 1;
+            if (pb < o.cap_p2p) o.p2p[pb] = make_uint2(baseA + (b >> 3), baseB + (b & 7));
+            ++pb;
+        }
+        for (unsigned long long m = mfront; m; m &= m - 1) {
+            const int b = __ffsll((long long)m) - 1;
+            if (fb < o.cap_front) o.front_out[fb] = make_uint2(baseA + (b >> 3), baseB + (b & 7));
+            ++fb;
+        }
     }
 }
 

@@ -137,3 +137,142 @@ def clustered(n: int, seed: int = 1007, n_clumps: int = 8, clump_scale: float = 
     vel = 0.1 * g.standard_normal((3, n))
     mass = np.full(n, 1.0 / n)
     return pos, vel, mass
+
+
+def _nfw_radii(g: np.random.Generator, n: int, c: float, r200: float) -> np.ndarray:
+    """Radii drawn from an NFW profile of concentration c truncated at r200: the enclosed mass
+    m(x) = ln(1 + x) - x / (1 + x), x = r / r_s, r_s = r200 / c, inverted by bisection."""
+    u = g.uniform(0.0, 1.0, n) * (np.log1p(c) - c / (1.0 + c))
+    lo, hi = np.zeros(n), np.full(n, float(c))
+    for _ in range(60):
+        mid = 0.5 * (lo + hi)
+        below = np.log1p(mid) - mid / (1.0 + mid) < u
+        lo = np.where(below, mid, lo)
+        hi = np.where(below, hi, mid)
+    return 0.5 * (lo + hi) * (r200 / c)
+
+
+def disk_galaxy(n: int = 1 << 22, seed: int = 1003, rd: float = 3.0, z0: float = 0.3, bulge_a: float = 0.6,
+                halo_c: float = 10.0, r200: float = 30.0):
+    """Isolated disk galaxy, positions and masses: an exponential disk (surface density ~ exp(-R/rd),
+    vertical sech^2(z/z0)) with 10 % of the mass and of the particles, a Hernquist bulge of scale
+    bulge_a with 5 %, and an NFW halo (concentration halo_c, truncated at r200) with 85 %; equal
+    masses within a component.  Velocities are not drawn: the set serves force evaluations."""
+    g = rng(seed)
+    disk, bulge, halo = _disk_galaxy_parts(g, n, rd, z0, bulge_a, halo_c, r200)
+    nd, nb, nh = disk.shape[1], bulge.shape[1], halo.shape[1]
+    pos = np.concatenate([disk, bulge, halo], axis=1)
+    mass = np.concatenate([np.full(nd, 0.10 / nd), np.full(nb, 0.05 / nb), np.full(nh, 0.85 / nh)])
+    perm = g.permutation(n)
+    return np.ascontiguousarray(pos[:, perm]), mass[perm]
+
+
+def _disk_galaxy_parts(g, n, rd, z0, bulge_a, halo_c, r200):
+    """The three components of disk_galaxy, in that order, before they are mixed."""
+    nd, nb = int(round(0.10 * n)), int(round(0.05 * n))
+    nh = n - nd - nb
+    R = g.gamma(2.0, rd, nd)                          # p(R) ~ R exp(-R / rd)
+    phi = g.uniform(0.0, 2.0 * np.pi, nd)
+    z = z0 * np.arctanh(g.uniform(-1.0, 1.0, nd) * (1.0 - 1e-12))
+    disk = np.stack([R * np.cos(phi), R * np.sin(phi), z])
+    s = np.sqrt(g.uniform(0.0, 0.999, nb))            # Hernquist: M(r) ~ r^2 / (r + a)^2
+    bulge = _isotropic(g, nb) * (bulge_a * s / (1.0 - s))
+    halo = _isotropic(g, nh) * _nfw_radii(g, nh, halo_c, r200)
+    return disk, bulge, halo
+
+
+def clustered_box(n_side: int = 256, seed: int = 1004, n_clumps: int = 1000, disp_rms: float = 0.5,
+                  clump_cap: float = 0.5, c: float = 10.0):
+    """Clustered cosmology-like set of n_side^3 equal-mass particles in the unit cube (isolated): a
+    lattice displaced by the Zel'dovich approximation of a Gaussian random field with P(k) ~ k^-2,
+    scaled to an rms displacement of disp_rms cells, then n_clumps NFW halos (concentration c) made
+    by moving randomly chosen particles onto the halo profiles.  Halo masses are log-uniform in
+    1e-5 .. 1e-2 of the total and rescaled to sum to clump_cap when they exceed it (their expected
+    sum, 1.45, would exceed the total); r200 follows from M = 200 (4 pi / 3) r200^3 (mean density 1)."""
+    g = rng(seed)
+    ns = n_side
+    n, h = ns ** 3, 1.0 / ns
+    k1 = 2.0 * np.pi * np.fft.fftfreq(ns, d=h)
+    kr = 2.0 * np.pi * np.fft.rfftfreq(ns, d=h)
+    kx, ky, kz = np.meshgrid(k1, k1, kr, indexing="ij")
+    k2 = kx * kx + ky * ky + kz * kz
+    k2[0, 0, 0] = 1.0
+    delta = (g.standard_normal(k2.shape) + 1j * g.standard_normal(k2.shape)) / np.sqrt(k2)   # sqrt(P(k)) = 1/k
+    delta[0, 0, 0] = 0.0
+    psi = np.empty((3, n))
+    for a, ka in enumerate((kx, ky, kz)):
+        psi[a] = np.fft.irfftn(1j * ka / k2 * delta, s=(ns, ns, ns), axes=(0, 1, 2)).reshape(-1)
+    del kx, ky, kz, k2, delta
+    psi *= disp_rms * h / np.sqrt((psi * psi).sum(axis=0).mean())
+    pos = (np.indices((ns, ns, ns)).reshape(3, -1) + 0.5) * h + psi
+    m = np.exp(g.uniform(np.log(1e-5), np.log(1e-2), n_clumps))
+    if m.sum() > clump_cap:
+        m *= clump_cap / m.sum()
+    counts = np.maximum(1, np.round(m * n).astype(np.int64))
+    order = g.permutation(n)
+    centres = pos[:, g.integers(0, n, n_clumps)]
+    start = 0
+    for i in range(n_clumps):
+        idx = order[start:start + counts[i]]
+        start += counts[i]
+        r200 = (3.0 * m[i] / (800.0 * np.pi)) ** (1.0 / 3.0)
+        pos[:, idx] = centres[:, i:i + 1] + _isotropic(g, idx.size) * _nfw_radii(g, idx.size, c, r200)
+    return np.ascontiguousarray(pos), np.full(n, 1.0 / n)
+
+
+def _king_profile(w0: float, dr: float = 1e-3):
+    """King (1966) model in core radii: the dimensionless potential W(r) from W(0) = w0 down to the
+    tidal radius (W = 0), with density rho(W) ~ e^W erf(sqrt W) - sqrt(4W/pi) (1 + 2W/3) and
+    W'' + 2W'/r = -9 rho(W) / rho(w0) (fourth-order Runge-Kutta).  Returns radii and the enclosed mass
+    fraction, which is proportional to -r^2 W'(r)."""
+    from math import erf, exp, pi, sqrt
+
+    def rho(w):
+        return exp(w) * erf(sqrt(w)) - sqrt(4.0 * w / pi) * (1.0 + 2.0 * w / 3.0) if w > 0 else 0.0
+
+    r0 = rho(w0)
+
+    def f(r, y):
+        return (y[1], -9.0 * rho(y[0]) / r0 - 2.0 * y[1] / r)
+
+    r = dr
+    y = (w0 - 1.5 * dr * dr, -3.0 * dr)   # series start: W = w0 - 3/2 r^2
+    rs, ms = [0.0, r], [0.0, -r * r * y[1]]
+    while y[0] > 0.0:
+        k1 = f(r, y)
+        k2 = f(r + dr / 2, (y[0] + dr / 2 * k1[0], y[1] + dr / 2 * k1[1]))
+        k3 = f(r + dr / 2, (y[0] + dr / 2 * k2[0], y[1] + dr / 2 * k2[1]))
+        k4 = f(r + dr, (y[0] + dr * k3[0], y[1] + dr * k3[1]))
+        y = (y[0] + dr / 6 * (k1[0] + 2 * k2[0] + 2 * k3[0] + k4[0]),
+             y[1] + dr / 6 * (k1[1] + 2 * k2[1] + 2 * k3[1] + k4[1]))
+        r += dr
+        rs.append(r)
+        ms.append(-r * r * y[1])
+    ms = np.maximum.accumulate(np.array(ms))
+    return np.array(rs), ms / ms[-1]
+
+
+def king(n: int, w0: float = 6.0, seed: int = 1005, r_half: float = 1.305):
+    """King (1966) sphere with central potential w0, positions and equal masses, scaled to the
+    half-mass radius r_half (1.305 is that of the Plummer sphere with a = 1)."""
+    g = rng(seed)
+    r, mfrac = _king_profile(w0)
+    radii = np.interp(g.uniform(0.0, 1.0, n), mfrac, r)
+    radii *= r_half / np.interp(0.5, mfrac, r)
+    return np.ascontiguousarray(_isotropic(g, n) * radii), np.full(n, 1.0 / n)
+
+
+def ensemble(seed: int = 1005, n_systems: int = 64, log2n=(10.0, 17.0)):
+    """Ensemble of independent systems: sizes round(2^U(10, 17)); even members Plummer spheres
+    (a = 1), odd members King W0 = 6 spheres of the same half-mass radius; each of total mass 1.
+    Returns a list of (pos, mass)."""
+    g = rng(seed)
+    sizes = np.round(2.0 ** g.uniform(log2n[0], log2n[1], n_systems)).astype(np.int64)
+    out = []
+    for s, ns in enumerate(sizes):
+        if s % 2 == 0:
+            pos, _, mass = plummer(int(ns), seed * 1000 + s)
+        else:
+            pos, mass = king(int(ns), 6.0, seed * 1000 + s)
+        out.append((pos, mass))
+    return out

@@ -1,0 +1,55 @@
+"""The seeded inputs of the benchmark table's other workloads, checked against the profiles they are
+drawn from (CPU): component masses and shapes of the disk galaxy, the displacement scale and clump
+mass of the clustered box, the King W0 = 6 concentration and the ensemble's size range."""
+import numpy as np
+
+from paper_1712_10116_gb300 import ics
+
+
+def test_disk_galaxy_components():
+    pos, mass = ics.disk_galaxy(200_000, seed=11)
+    assert pos.shape == (3, 200_000) and abs(mass.sum() - 1.0) < 1e-12
+    # particle numbers split like the masses (10 / 5 / 85 %), so every particle weighs 1/N
+    assert np.allclose(mass, 1.0 / 200_000, rtol=1e-12)
+    disk, bulge, halo = ics._disk_galaxy_parts(ics.rng(12), 200_000, 3.0, 0.3, 0.6, 10.0, 30.0)
+    assert (disk.shape[1], bulge.shape[1], halo.shape[1]) == (20_000, 10_000, 170_000)
+    R = np.hypot(disk[0], disk[1])
+    assert abs(R.mean() / 6.0 - 1.0) < 0.02                    # <R> = 2 Rd for an exponential disk
+    assert abs(np.median(np.abs(disk[2])) / (0.3 * np.arctanh(0.5)) - 1.0) < 0.03   # sech^2: median |z|
+    rb = np.linalg.norm(bulge, axis=0)
+    assert abs(np.median(rb) / (0.6 / (np.sqrt(2.0) - 1.0)) - 1.0) < 0.03   # Hernquist half-mass radius
+    assert np.linalg.norm(halo, axis=0).max() <= 30.0 * (1 + 1e-9)   # NFW truncated at r200
+
+
+def test_nfw_radii_follow_the_enclosed_mass():
+    g = ics.rng(3)
+    r = ics._nfw_radii(g, 100_000, 10.0, 30.0)
+    x = np.array([0.5, 1.0, 3.0, 10.0])
+    m = (np.log1p(x) - x / (1 + x)) / (np.log1p(10.0) - 10.0 / 11.0)
+    emp = np.array([(r <= xi * 3.0).mean() for xi in x])
+    assert np.abs(emp - m).max() < 0.01
+
+
+def test_clustered_box_scale_and_clumps():
+    pos, mass = ics.clustered_box(32, seed=4, n_clumps=50)
+    assert pos.shape == (3, 32 ** 3) and np.allclose(mass, 1.0 / 32 ** 3)
+    # most particles stay within a few cells of their lattice site; the clumps pull the rest in
+    grid = (np.indices((32, 32, 32)).reshape(3, -1) + 0.5) / 32
+    d = np.linalg.norm(pos - grid, axis=0) * 32
+    assert 0.2 < np.median(d) < 2.0
+
+
+def test_king_concentration():
+    r, m = ics._king_profile(6.0)
+    assert abs(np.log10(r[-1]) - 1.26) < 0.02                  # c = log10(r_t / r_c) for W0 = 6
+    assert m[0] == 0.0 and m[-1] == 1.0 and np.all(np.diff(m) >= 0)
+    pos, _ = ics.king(50_000, 6.0, seed=2)
+    rr = np.linalg.norm(pos, axis=0)
+    assert abs(np.median(rr) / 1.305 - 1.0) < 0.02
+
+
+def test_ensemble_sizes():
+    systems = ics.ensemble()
+    sizes = np.array([p.shape[1] for p, _ in systems])
+    assert len(systems) == 64 and sizes.min() >= 2 ** 10 and sizes.max() <= 2 ** 17
+    assert all(abs(m.sum() - 1.0) < 1e-12 for _, m in systems)
