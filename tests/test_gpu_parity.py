@@ -141,6 +141,24 @@ def test_sphere_mac_forces_match_oracle(precision, masked):
         assert _rel(acc.cpu().numpy(), a_o, FP32_FLOOR).max() < FP32_TOL
 
 
+@pytest.mark.parametrize("split", ["half", "shell"])
+@pytest.mark.parametrize("p,kernel", [(6, 0), (5, 1)])
+def test_fmm_fp32_spatial_classes_match_oracle(split, p, kernel):
+    # fast particles in one region (a half-space, or an outer shell like the HHS rungs of a collapse):
+    # most cells hold a single class, where M2L reuses or drops the class-1 contraction
+    n = 12000
+    pos, _, mass = _case("sphere", n)
+    r = np.linalg.norm(pos, axis=0)
+    fast = ((pos[0] > 0.1) if split == "half" else (r > 0.7)).astype(np.uint8)
+    prm = tg.Params(p=p, theta=0.5, eps=0.005 if kernel == 0 else 0.01, kernel=kernel, precision=tg.TG_PREC_FP32,
+                    n_crit=32)
+    s = tg.Solver(prm)
+    for want_pot in (True, False):
+        acc, _ = s.fmm_forces(_t(pos), _t(mass), _t(fast, torch.uint8), want_pot=want_pot)
+        a_o, _ = oracle.fmm(pos, mass, _oprm(prm), fast)
+        assert _rel(acc.cpu().numpy(), a_o, FP32_FLOOR).max() < FP32_TOL
+
+
 @pytest.mark.parametrize("kernel", [0, 1])
 @pytest.mark.parametrize("p", [2, 4, 6])
 @pytest.mark.parametrize("masked", [False, True])
