@@ -326,6 +326,46 @@ def test_coincident_particles_and_all_fast():
     assert torch.all(acc2 == 0) and torch.all(pot2 == 0)
 
 
+def test_empty_input():
+    for precision in (tg.TG_PREC_FP64, tg.TG_PREC_FP32):
+        s = tg.Solver(tg.Params(p=4, precision=precision))
+        acc, pot = s.fmm_forces(torch.zeros((3, 0), dtype=torch.float64, device=DEV),
+                                torch.zeros(0, dtype=torch.float64, device=DEV))
+        assert acc.shape == (3, 0) and pot.shape == (0,)
+
+
+@pytest.mark.parametrize("shape", ["planar", "collinear", "big_clump", "shallow"])
+@pytest.mark.parametrize("precision", [0, 1])
+def test_degenerate_geometry_matches_oracle(shape, precision):
+    # flat and one-dimensional sets (zero extent along some axes), a clump of coincident particles
+    # larger than one column stage (a deepest-level leaf with 300 > 128 particles), and a tree cut off
+    # at level 1 (eight leaves of ~400 particles): the chunked P2P paths
+    g = np.random.default_rng(31)
+    n, max_level, n_crit = 3000, 21, 16
+    if shape == "planar":
+        pos = np.concatenate([g.uniform(-1, 1, (2, n)), np.zeros((1, n))])
+    elif shape == "collinear":
+        pos = np.concatenate([g.uniform(-1, 1, (1, n)), np.zeros((2, n))])
+    elif shape == "big_clump":
+        pos = np.concatenate([np.full((3, 300), 0.25), g.uniform(-1, 1, (3, n - 300))], axis=1)
+    else:
+        pos, max_level, n_crit = g.uniform(-1, 1, (3, n)), 1, 8
+    mass = ics.random_masses(n, 32)
+    fast = ics.random_fast_mask(n, 33)
+    prm = tg.Params(p=4, theta=0.5, eps=0.02, kernel=0, precision=precision, n_crit=n_crit, max_level=max_level)
+    s = tg.Solver(prm)
+    for mask in (None, fast):
+        acc, _ = s.fmm_forces(_t(pos), _t(mass), None if mask is None else _t(mask, torch.uint8))
+        a_o, _ = oracle.fmm(pos, mass, _oprm(prm), mask)
+        # on a line (and, less so, in a plane) the pulls from both sides cancel to a small net force
+        # for the particles in the middle, so the bound is taken against max(|a|, 0.1 median |a|)
+        # in float64 too, as for float32
+        if precision == tg.TG_PREC_FP64:
+            assert _rel(acc.cpu().numpy(), a_o, FP32_FLOOR).max() < 1e-12
+        else:
+            assert _rel(acc.cpu().numpy(), a_o, FP32_FLOOR).max() < FP32_TOL
+
+
 def test_argument_errors_leave_outputs():
     prm = tg.Params()
     s = tg.Solver(prm)
