@@ -1,7 +1,7 @@
 // fmm.cu -- one FMM evaluation (the Poisson-solver call of Algorithm 3, Zhu 2017):
 // upward pass (P2M, M2M), dual tree walk (Algorithm 4) emitting blocks of unordered cell pairs,
 // mutual M2L and P2P (Sec. 2.1: F_AB = -F_BA), downward pass (L2L, L2P) and the
-// direct-summation reference used to measure force errors.
+// float64 direct summation (tg_direct_forces) that the force errors are measured against.
 //
 // Expansions are Cartesian Taylor series truncated at total degree p, stored normalised by the
 // cell side s:

@@ -14,8 +14,9 @@ namespace tg {
 
 // ------------------------------------------------------------------ timestep and split
 // rung k pivot step dt_k = dt_max / 2^k; slow = {dt_i >= dt_k} (everything at k = k_max)
-// dt_i of Sec. 2.2, capped by Eq. (9) when a_tot is given and eta_tot_eps > 0 (same IEEE operations
-// as the float64 reference: eta*eps on the host, one division, one square root)
+// dt_i of Sec. 2.2, capped by Eq. (9) when a_tot is given and eta_tot_eps > 0, with a fixed sequence of
+// correctly rounded float64 operations (eta*eps on the host, one division, one square root), so
+// that rungs are reproducible bit for bit
 __device__ __forceinline__ double timestep_of(double a_old, double a_cur, double eta_eps, const double *a_tot,
                                               double eta_tot_eps, int64_t i)
 {
@@ -301,7 +302,8 @@ tg_status timesteps(tg_ctx *c, int64_t n, const double *a_old, const double *a_c
 // with a half kick, takes a new rung from dt_i = sqrt(eta eps / |a_i|) deepened until the next step
 // starts on a multiple of itself, and opens it with a half kick.  Time runs on a grid of 2^k_max
 // substeps per rung-0 step; end[i] is the substep where particle i's step ends.  The float64
-// operations follow the reference order with explicit rounding (no contraction).
+// operations are written out in a fixed order with explicit rounding (no contraction), so that the
+// rungs are reproducible bit for bit.
 __device__ __forceinline__ double trad_amag(double ax, double ay, double az)
 {
     return sqrt(__dadd_rn(__dadd_rn(__dmul_rn(ax, ax), __dmul_rn(ay, ay)), __dmul_rn(az, az)));
