@@ -470,9 +470,11 @@ def run_momentum_contrast(args):
     dt_max = 1.0 / 64
     steps = int(round(args.contrast_t / dt_max))
     prm = tg.Params(p=5, theta=0.45, eps=eps, kernel=0, precision=tg.TG_PREC_FP64, n_crit=64, eta=0.02,
-                    dt_max=dt_max, k_max=10, eta_tot=args.eta_tot)
-    out = {"mode": "momentum-contrast", "eta_tot": args.eta_tot, "workload": f"cold collapse of a unit cube at rest, N={n}, eps={eps:.4g} "
-           f"Wendland C2, theta=0.45, p=5, float64, eta=0.02, dt_max=1/64, k_max=10, t=0..{args.contrast_t}",
+                    dt_max=dt_max, k_max=10, eta_tot=args.eta_tot, mac=1 if args.mac == "sphere" else 0)
+    out = {"mode": "momentum-contrast", "eta_tot": args.eta_tot, "mac": args.mac,
+           "workload": f"cold collapse of a unit cube at rest, N={n}, eps={eps:.4g} "
+           f"Wendland C2, theta=0.45 ({args.mac} criterion), p=5, float64, eta=0.02, dt_max=1/64, k_max=10, "
+           f"t=0..{args.contrast_t}",
            "data": "synthetic"}
     for name in ("hhs", "traditional"):
         s = tg.Solver(prm)
