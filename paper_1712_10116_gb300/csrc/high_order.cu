@@ -11,27 +11,9 @@
 // the result is the same in exact arithmetic.
 #include "tg_common.cuh"
 #include "m2l_geom.cuh"
+#include "high_order.cuh"
 
 namespace tg {
-
-// position of (x, y, z) in the order by total degree, then x descending, then y descending
-__device__ __forceinline__ int hi_index(int x, int y, int z)
-{
-    const int o = x + y + z, a = o - x;
-    return o * (o + 1) * (o + 2) / 6 + a * (a + 1) / 2 + z;
-}
-
-__device__ __forceinline__ void hi_decode(int k, int &x, int &y, int &z)
-{
-    int o = 0;
-    while ((o + 1) * (o + 2) * (o + 3) / 6 <= k) ++o;
-    const int r = k - o * (o + 1) * (o + 2) / 6;
-    int a = 0;
-    while ((a + 1) * (a + 2) / 2 <= r) ++a;
-    z = r - a * (a + 1) / 2;
-    x = o - a;
-    y = a - z;
-}
 
 // 1/n! for n <= 20 (n! is exact in float64 up to 22!, so each entry is the correctly rounded quotient)
 __constant__ double c_hi_inv_fact[kPHigh + 1] = {
@@ -202,19 +184,7 @@ template <class T>
 __global__ void fold_moments_hi(int64_t nrows, const T *__restrict__ Ms, T *__restrict__ Mf, int p, int ncp)
 {
     for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < nrows; w += (int64_t)gridDim.x * blockDim.x) {
-        const T *src = Ms + w * ncp;
-        T *dst = Mf + w * ncp;
-        for (int k = 0; k < ncp; ++k) dst[k] = src[k];
-        for (int jz = p; jz >= 2; --jz)
-            for (int o = jz; o <= p; ++o)
-                for (int jx = o - jz; jx >= 0; --jx) {
-                    const int jy = o - jz - jx;
-                    const int k = hi_index(jx, jy, jz);
-                    const T v = dst[k];
-                    dst[hi_index(jx + 2, jy, jz - 2)] -= v;
-                    dst[hi_index(jx, jy + 2, jz - 2)] -= v;
-                    dst[k] = T(0);
-                }
+        hi_fold_row<T>(Ms + w * ncp, Mf + w * ncp, p, ncp);
     }
 }
 
@@ -224,13 +194,7 @@ template <class T>
 __global__ void complete_locals_hi(int64_t nrows, T *L, int p, int ncp)
 {
     for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < nrows; w += (int64_t)gridDim.x * blockDim.x) {
-        T *row = L + w * ncp;
-        for (int o = 2; o <= p; ++o)
-            for (int kx = o - 2; kx >= 0; --kx)
-                for (int kz = 2; kz <= o - kx; ++kz) {
-                    const int ky = o - kx - kz;
-                    row[hi_index(kx, ky, kz)] = -row[hi_index(kx + 2, ky, kz - 2)] - row[hi_index(kx, ky + 2, kz - 2)];
-                }
+        hi_complete_row<T>(L + w * ncp, p);
     }
 }
 
