@@ -240,12 +240,12 @@ tg_status tg_timesteps(tg_ctx *ctx, int64_t n, const double *a_old, const double
  *
  * It allocates nothing (no cudaMalloc, cudaFree or allocating library call).  Its scratch is one
  * file-scope device array of about 6.3 MB that every GPU loading the library holds until the
- * process exits.  The first call on a device looks up that array's device address
- * (cudaGetSymbolAddress) with the device current; make that first call before any stream
- * capture.  All calls share the array, so two calls whose work overlaps on the GPU (different
- * streams, or host threads racing) corrupt each other's results: serialise them.  Returns
- * TG_ERR_ARG for bad sizes or non-device pointers and TG_ERR_CUDA if a launch fails; the call is
- * asynchronous otherwise. */
+ * process exits.  Every call looks up that array's device address (cudaGetSymbolAddress, which
+ * allocates nothing) on the current device, so pos, keys_out and perm_out must be memory of the
+ * current device (or managed memory).  All calls share the array, so two calls whose work
+ * overlaps on the GPU (different streams, or host threads racing) corrupt each other's results:
+ * serialise them.  Returns TG_ERR_ARG for bad sizes or for pointers that are not memory of the
+ * current device, and TG_ERR_CUDA if a launch fails; the call is asynchronous otherwise. */
 #define TG_NOALLOC_MAX_N 262144
 tg_status tg_morton_sort_noalloc(int64_t n, const double *pos, uint64_t *keys_out, int64_t *perm_out,
                                  void *cuda_stream);

@@ -179,6 +179,19 @@ def direct(pos, mass, eps, kernel=WENDLAND_C2, is_fast=None, sinks=None):
     return acc, pot
 
 
+def diagnostics(pos, vel, mass, pot=None):
+    """Conservation diagnostics (Sec. 3.2): [P (3), L = sum m x cross v (3), E = sum m v^2/2 + sum m phi/2]."""
+    pos = _f64(pos)
+    vel = _f64(vel)
+    mass = _f64(mass)
+    out = np.zeros(7)
+    pot = None if pot is None else _f64(pot)
+    pp = None if pot is None else pot.ctypes.data_as(_vp)
+    lib().orc_diagnostics(mass.shape[0], _p(pos[0]), _p(pos[1]), _p(pos[2]), _p(vel[0]), _p(vel[1]), _p(vel[2]),
+                          _p(mass), pp, _p(out))
+    return out
+
+
 def root_cube(pos):
     pos = _f64(pos)
     lo = np.zeros(3)

@@ -17,7 +17,7 @@
  * uses spherical harmonics; for G = -1/r both truncations give the same approximation).
  * Derivative tensors follow the McMurchie & Davidson (1978) auxiliary recurrence.
  *
- * Readings of points the paper leaves open (each also listed in the design notes):
+ * Readings of points the paper leaves open:
  *   R in Eq. (1) = kappa * side (kappa = 1: the paper calls R the cell side length), or with mac = 1
  *   the radius of a sphere about the cell centre that encloses the cell's particles;
  *   a cell is split iff it holds more than n_crit particles (leaves hold <= n_crit);

@@ -300,7 +300,11 @@ def tg_morton_sort_noalloc(pos, keys_out=None, perm_out=None, stream=None):
         keys_out = torch.empty(n, dtype=torch.int64, device=pos.device)
     if perm_out is None:
         perm_out = torch.empty(n, dtype=torch.int64, device=pos.device)
-    rc = load().tg_morton_sort_noalloc(n, _ptr(pos), _ptr(keys_out), _ptr(perm_out), _vp(_stream_handle(stream)))
+    # the library launches on the current device: make it pos's, and default to that device's stream
+    with torch.cuda.device(pos.device):
+        if stream is None:
+            stream = torch.cuda.current_stream(pos.device)
+        rc = load().tg_morton_sort_noalloc(n, _ptr(pos), _ptr(keys_out), _ptr(perm_out), _vp(_stream_handle(stream)))
     if rc != 0:
         raise TGError(rc, "tg_morton_sort_noalloc")
     return keys_out, perm_out

@@ -42,15 +42,19 @@ tg_status begin(tg_ctx *c)
     return TG_OK;
 }
 
+// Device memory of the current device (managed memory is reachable from any device).  Memory of
+// another GPU is refused: the kernels run on the current one.
 int check_device_ptr(const void *p)
 {
     if (!p) return 0;
     cudaPointerAttributes a;
-    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    int dev = -1;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess || cudaGetDevice(&dev) != cudaSuccess) {
         cudaGetLastError();
         return 0;
     }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+    if (a.type == cudaMemoryTypeManaged) return 1;
+    return a.type == cudaMemoryTypeDevice && a.device == dev;
 }
 
 }  // namespace

@@ -9,10 +9,8 @@
 //
 // The array lives in every GPU that loads the library until the process exits.  Host code must
 // not use the array's name as a pointer: on the host it is only a stand-in for the device
-// symbol.  The device address is looked up once per device with cudaGetSymbolAddress, on the
-// first call made with that device current.
-#include <mutex>
-
+// symbol.  Every call looks the device address up with cudaGetSymbolAddress, with the caller's
+// device current (a cheap query that allocates nothing), so no address outlives a device reset.
 #include "tg_common.cuh"
 
 namespace {
@@ -24,6 +22,10 @@ constexpr int kMaxSortBlocks = (int)((kMaxN + kSortTileItems - 1) / kSortTileIte
 constexpr int kMaxBboxBlocks = 2 * 152;
 constexpr int64_t kHistItems = (int64_t)kSortBins * kMaxSortBlocks;
 constexpr int64_t kScanTmpItems = 2 * ((kHistItems + kScanTileItems - 1) / kScanTileItems) + 64;
+
+// levels of the tile-sum recursion of the histogram scan: scan_with_scratch keeps at most 8
+constexpr int scan_levels(int64_t m) { return m <= kScanTileItems ? 1 : 1 + scan_levels((m + kScanTileItems - 1) / kScanTileItems); }
+static_assert(scan_levels(kHistItems) <= 8, "the histogram scan of the largest input needs more than 8 levels");
 
 // byte layout of the scratch array (every part 256-byte aligned)
 constexpr size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -41,30 +43,17 @@ static_assert(kScratchBytes < (8u << 20), "the allocation-free scratch must stay
 // The scratch.  Device code could name it directly; host code uses the looked-up address.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_setup_mutex;
-unsigned char *g_scratch_addr[kMaxDevices] = {nullptr};
-
-// Address of the scratch on the current device (looked up on the first call per device).
+// Address of the scratch on the current device.  Looked up on every call: the query is cheap,
+// allocates nothing, and stays right after a device reset reloads the module.
 tg_status scratch_for_current_device(unsigned char **out)
 {
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) {
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || p == nullptr) {
         cudaGetLastError();
         return TG_ERR_CUDA;
     }
-    if (dev < 0 || dev >= kMaxDevices) return TG_ERR_ARG;
-    std::lock_guard<std::mutex> lock(g_setup_mutex);
-    if (!g_scratch_addr[dev]) {
-        void *p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess || p == nullptr) {
-            cudaGetLastError();
-            return TG_ERR_CUDA;
-        }
-        g_scratch_addr[dev] = static_cast<unsigned char *>(p);
-    }
-    *out = g_scratch_addr[dev];
+    *out = static_cast<unsigned char *>(p);
     return TG_OK;
 }
 
@@ -86,29 +75,37 @@ cudaError_t scan_with_scratch(cudaStream_t st, const uint32_t *in, uint32_t *out
     uint32_t *cout = out;
     int cn = n;
     uint32_t *cursor = tmp;
+    bool complete = false;
     while (depth < 8) {
         const int nt = (cn + kScanTileItems - 1) / kScanTileItems;
         lv[depth] = {cout, cn, nt, cursor, cursor + nt};
-        scan_tiles<<<nt, 512, 0, st>>>(cin, cout, cursor, cn);
+        scan_tiles<<<nt, kScanThreads, 0, st>>>(cin, cout, cursor, cn);
         ++depth;
-        if (nt == 1) break;
+        if (nt == 1) {
+            complete = true;
+            break;
+        }
         cin = cursor;
         cout = cursor + nt;
         cn = nt;
         cursor += 2 * nt + 2;
     }
-    for (int d = depth - 2; d >= 0; --d) scan_add<<<lv[d].ntiles, 512, 0, st>>>(lv[d].out, lv[d].pre, lv[d].n);
+    if (!complete) return cudaErrorInvalidValue;   // excluded by the static_assert on scan_levels
+    for (int d = depth - 2; d >= 0; --d) scan_add<<<lv[d].ntiles, kScanThreads, 0, st>>>(lv[d].out, lv[d].pre, lv[d].n);
     return cudaGetLastError();
 }
 
+// device memory of the current device (managed memory is reachable from any device)
 int check_dev(const void *p)
 {
     cudaPointerAttributes a;
-    if (!p || cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    int dev = -1;
+    if (!p || cudaPointerGetAttributes(&a, p) != cudaSuccess || cudaGetDevice(&dev) != cudaSuccess) {
         cudaGetLastError();
         return 0;
     }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+    if (a.type == cudaMemoryTypeManaged) return 1;
+    return a.type == cudaMemoryTypeDevice && a.device == dev;
 }
 
 }  // namespace

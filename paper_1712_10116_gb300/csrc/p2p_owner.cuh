@@ -347,9 +347,8 @@ namespace tg {
 
 // Every P2P pair in float32, one launch: the distinct leaf pairs grouped by owner, then the self pairs.
 // pot = false: accelerations only (the potential slot of acc4 is left out).
-static tg_status launch_p2p_owner(tg_ctx *c, const TreeView &t, const uint2 *pairs, int64_t npairs,
-                                  const uint2 *self_pairs, int64_t nself, const float4 *pf, const int32_t *nslow,
-                                  bool pot, double *acc4)
+tg_status launch_p2p_f32(tg_ctx *c, const TreeView &t, const uint2 *pairs, int64_t npairs, const uint2 *self_pairs,
+                         int64_t nself, const float4 *pf, const int32_t *nslow, bool pot, double *acc4)
 {
     tg_status st;
     const int ncell = t.ncell;

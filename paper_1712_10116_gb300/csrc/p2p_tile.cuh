@@ -301,19 +301,18 @@ static tg_status launch_p2p_generic(tg_ctx *c, const TreeView &t, const Geom *d_
     return cuda_check(c, cudaGetLastError(), "p2p launch");
 }
 
-// float64 P2P (one block per leaf pair, self pairs included); float32 goes through p2p_owner.cuh.
-template <class T, class T4>
-static tg_status launch_p2p(tg_ctx *c, const TreeView &t, const Geom *d_geom, const uint2 *pairs, int64_t npairs,
-                            const T4 *pf, const uint8_t *fs, const int32_t *nslow, bool masked, bool self, double *acc4);
-
-template <>
-tg_status launch_p2p<double, dbl4>(tg_ctx *c, const TreeView &t, const Geom *d_geom, const uint2 *pairs, int64_t npairs,
-                                   const dbl4 *pf, const uint8_t *fs, const int32_t *nslow, bool masked, bool self,
-                                   double *acc4)
+// float64 P2P: one block per leaf pair, the distinct pairs then the self pairs (the tile tells them
+// apart at run time and masks fast-fast pairs one by one); float32 goes through p2p_owner.cuh.
+tg_status launch_p2p_f64(tg_ctx *c, const TreeView &t, const Geom *d_geom, const uint2 *pairs, int64_t npairs,
+                         const uint2 *self_pairs, int64_t nself, const dbl4 *pf, const uint8_t *fs, bool masked,
+                         double *acc4)
 {
-    (void)nslow;   // the float64 tile masks fast-fast pairs one by one
-    (void)self;   // the float64 tile handles self pairs at run time
-    return launch_p2p_generic<double, dbl4>(c, t, d_geom, pairs, npairs, pf, fs, masked, acc4);
+    tg_status st;
+    if (npairs > 0 && (st = launch_p2p_generic<double, dbl4>(c, t, d_geom, pairs, npairs, pf, fs, masked, acc4)))
+        return st;
+    if (nself > 0 && (st = launch_p2p_generic<double, dbl4>(c, t, d_geom, self_pairs, nself, pf, fs, masked, acc4)))
+        return st;
+    return TG_OK;
 }
 
 }  // namespace tg

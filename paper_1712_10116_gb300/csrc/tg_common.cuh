@@ -184,7 +184,8 @@ constexpr int kSortTileItems = 2048;     // items per radix-sort block (256 thre
 constexpr int kSortBits = 9;             // radix digit width: 7 passes cover the 63 key bits
 constexpr int kSortBins = 1 << kSortBits;
 constexpr int kSortPasses = (63 + kSortBits - 1) / kSortBits;
-constexpr int kScanTileItems = 2048;     // items per scan block (512 threads x 4)
+constexpr int kScanThreads = 512;        // threads per scan block
+constexpr int kScanTileItems = 2048;     // items per scan block (kScanThreads x 4)
 __global__ void scan_tiles(const uint32_t *in, uint32_t *out, uint32_t *tile_sums, int n);
 __global__ void scan_add(uint32_t *out, const uint32_t *tile_pre, int n);
 __global__ void bbox_partial(const double *pos, int64_t stride, const int64_t *sub, int n, double *partial);

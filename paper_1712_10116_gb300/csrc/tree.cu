@@ -137,9 +137,9 @@ tg_status prof_collect(tg_ctx *c)
 }
 
 // ------------------------------------------------------------------ exclusive scan (uint32)
-constexpr int kScanThreads = 512;
 constexpr int kScanItems = 4;
 constexpr int kScanTile = kScanThreads * kScanItems;
+static_assert(kScanTile == kScanTileItems, "scan tile shared with the allocation-free sort");
 
 __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t *total)
 {

@@ -153,18 +153,144 @@ def _nfw_radii(g: np.random.Generator, n: int, c: float, r200: float) -> np.ndar
 
 
 def disk_galaxy(n: int = 1 << 22, seed: int = 1003, rd: float = 3.0, z0: float = 0.3, bulge_a: float = 0.6,
-                halo_c: float = 10.0, r200: float = 30.0):
-    """Isolated disk galaxy, positions and masses: an exponential disk (surface density ~ exp(-R/rd),
-    vertical sech^2(z/z0)) with 10 % of the mass and of the particles, a Hernquist bulge of scale
-    bulge_a with 5 %, and an NFW halo (concentration halo_c, truncated at r200) with 85 %; equal
-    masses within a component.  Velocities are not drawn: the set serves force evaluations."""
+                halo_c: float = 10.0, r200: float = 30.0, velocities: bool = False, toomre_q: float = 1.5):
+    """Isolated disk galaxy: an exponential disk (surface density ~ exp(-R/rd), vertical sech^2(z/z0))
+    with 10 % of the mass and of the particles, a Hernquist bulge of scale bulge_a with 5 %, and an
+    NFW halo (concentration halo_c, truncated at r200) with 85 %; equal masses within a component.
+
+    Returns (pos, mass), or with velocities=True (pos, vel, mass): velocities from Jeans moments in the
+    model's own potential (disk_galaxy_velocities), drawn from a separate stream so that the positions
+    are the same either way."""
     g = rng(seed)
     disk, bulge, halo = _disk_galaxy_parts(g, n, rd, z0, bulge_a, halo_c, r200)
     nd, nb, nh = disk.shape[1], bulge.shape[1], halo.shape[1]
     pos = np.concatenate([disk, bulge, halo], axis=1)
     mass = np.concatenate([np.full(nd, 0.10 / nd), np.full(nb, 0.05 / nb), np.full(nh, 0.85 / nh)])
     perm = g.permutation(n)
-    return np.ascontiguousarray(pos[:, perm]), mass[perm]
+    if not velocities:
+        return np.ascontiguousarray(pos[:, perm]), mass[perm]
+    model = DiskGalaxyModel(rd=rd, z0=z0, bulge_a=bulge_a, halo_c=halo_c, r200=r200, toomre_q=toomre_q)
+    vel = disk_galaxy_velocities(rng(seed + 7919), model, disk, bulge, halo)
+    vel = vel - (vel * mass).sum(axis=1, keepdims=True) / mass.sum()
+    return np.ascontiguousarray(pos[:, perm]), np.ascontiguousarray(vel[:, perm]), mass[perm]
+
+
+class DiskGalaxyModel:
+    """Mass profiles and Jeans moments of the disk galaxy (G = 1, total mass 1).
+
+    Spherical parts: Hernquist bulge (mass 0.05, scale a, truncated where its enclosed-mass fraction
+    reaches 0.999, as the sampler does) and NFW halo (mass 0.85 within r200, concentration c).  The
+    disk (mass 0.10, scale rd) enters the spheres' Jeans equation through its enclosed mass
+    0.1 [1 - (1 + r/rd) e^(-r/rd)] (a spherical average), and the disk's own rotation curve through
+    Freeman's (1970) exact midplane formula for a thin exponential disk."""
+
+    M_DISK, M_BULGE, M_HALO = 0.10, 0.05, 0.85
+
+    def __init__(self, rd=3.0, z0=0.3, bulge_a=0.6, halo_c=10.0, r200=30.0, toomre_q=1.5):
+        self.rd, self.z0, self.a, self.c, self.r200, self.q = rd, z0, bulge_a, halo_c, r200, toomre_q
+        s = np.sqrt(0.999)
+        self.rt_bulge = bulge_a * s / (1.0 - s)
+        self.rs = r200 / halo_c
+        self._mu_c = np.log1p(halo_c) - halo_c / (1.0 + halo_c)
+        self.r_ref = 2.43 * rd      # radius where Q is set (Hernquist 1993: the solar neighbourhood)
+
+    # -- enclosed masses and densities of the spherical parts
+    def m_bulge(self, r):
+        r = np.minimum(r, self.rt_bulge)
+        return self.M_BULGE / 0.999 * (r / (r + self.a)) ** 2
+
+    def rho_bulge(self, r):
+        return np.where(r < self.rt_bulge, self.M_BULGE / 0.999 * self.a / (2.0 * np.pi * r * (r + self.a) ** 3), 0.0)
+
+    def m_halo(self, r):
+        x = np.minimum(r, self.r200) / self.rs
+        return self.M_HALO * (np.log1p(x) - x / (1.0 + x)) / self._mu_c
+
+    def rho_halo(self, r):
+        x = r / self.rs
+        rho0 = self.M_HALO / (4.0 * np.pi * self.rs ** 3 * self._mu_c)
+        return np.where(r < self.r200, rho0 / (x * (1.0 + x) ** 2), 0.0)
+
+    def m_disk_sph(self, r):
+        y = r / self.rd
+        return self.M_DISK * (1.0 - (1.0 + y) * np.exp(-y))
+
+    def m_total(self, r):
+        return self.m_bulge(r) + self.m_halo(r) + self.m_disk_sph(r)
+
+    def sigma_r2(self, comp, r):
+        """Isotropic Jeans equation of a spherical component in the total enclosed mass:
+        rho sigma^2 (r) = int_r^r_t rho(s) M(<s) / s^2 ds, integrated on a logarithmic grid."""
+        rt = self.rt_bulge if comp == "bulge" else self.r200
+        rho = self.rho_bulge if comp == "bulge" else self.rho_halo
+        grid = np.geomspace(1e-5, rt, 6000)
+        f = rho(grid) * self.m_total(grid) / grid ** 2
+        seg = 0.5 * (f[1:] + f[:-1]) * np.diff(grid)
+        tail = np.concatenate([np.cumsum(seg[::-1])[::-1], [0.0]])   # int_grid[i]^rt
+        rs = np.clip(r, grid[0], rt)
+        integral = np.interp(rs, grid, tail)
+        with np.errstate(divide="ignore", invalid="ignore"):
+            s2 = integral / rho(rs)
+        return np.where(np.isfinite(s2), np.maximum(s2, 0.0), 0.0)
+
+    # -- disk kinematics (epicyclic approximation)
+    def sigma_disk(self, R):
+        return self.M_DISK / (2.0 * np.pi * self.rd ** 2) * np.exp(-R / self.rd)
+
+    def vc2(self, R):
+        """Circular speed squared in the midplane: spheres plus Freeman's thin-disk term
+        4 pi Sigma_0 rd y^2 [I0 K0 - I1 K1](y), y = R / (2 rd)."""
+        from scipy.special import i0e, i1e, k0e, k1e
+        y = np.maximum(R, 1e-12) / (2.0 * self.rd)
+        sig0 = self.M_DISK / (2.0 * np.pi * self.rd ** 2)
+        disk = 4.0 * np.pi * sig0 * self.rd * y * y * (i0e(y) * k0e(y) - i1e(y) * k1e(y))   # e^y e^-y cancel
+        sph = (self.m_bulge(R) + self.m_halo(R)) / np.maximum(R, 1e-12)
+        return sph + disk
+
+    def kappa2_omega2(self, R):
+        """kappa^2 = R dOmega^2/dR + 4 Omega^2 and Omega^2 = v_c^2 / R^2 (numerical derivative on a log grid)."""
+        grid = np.geomspace(1e-3, 20.0 * self.rd + 1.0, 4000)
+        om2 = self.vc2(grid) / grid ** 2
+        k2 = grid * np.gradient(om2, grid) + 4.0 * om2
+        Rc = np.clip(R, grid[0], grid[-1])
+        return np.interp(Rc, grid, k2), np.interp(Rc, grid, om2)
+
+    def sigma_R2_norm(self):
+        """sigma_R^2 = A exp(-R/rd) (Hernquist 1993), with A set by Toomre's Q = sigma_R kappa / (3.36 Sigma)
+        at r_ref."""
+        k2, _ = self.kappa2_omega2(np.array([self.r_ref]))
+        sR = 3.36 * self.q * self.sigma_disk(self.r_ref) / np.sqrt(k2[0])
+        return sR * sR * np.exp(self.r_ref / self.rd)
+
+    def disk_moments(self, R):
+        """(sigma_R^2, sigma_phi^2, sigma_z^2, mean v_phi) of the disk at cylindrical radius R:
+        sigma_z^2 = pi Sigma z0 (isothermal sheet), sigma_phi^2 = sigma_R^2 kappa^2 / (4 Omega^2), and the
+        asymmetric drift v_phi^2 = v_c^2 + sigma_R^2 (1 - kappa^2 / (4 Omega^2) - 2 R / rd), clipped at 0."""
+        sR2 = self.sigma_R2_norm() * np.exp(-R / self.rd)
+        k2, om2 = self.kappa2_omega2(R)
+        ratio = k2 / (4.0 * om2)
+        sphi2 = sR2 * ratio
+        sz2 = np.pi * self.sigma_disk(R) * self.z0
+        vphi2 = self.vc2(R) + sR2 * (1.0 - ratio - 2.0 * R / self.rd)
+        return sR2, sphi2, sz2, np.sqrt(np.maximum(vphi2, 0.0))
+
+
+def disk_galaxy_velocities(g, model, disk, bulge, halo):
+    """Velocities of the three components (positions as _disk_galaxy_parts returns them), concatenated:
+    Gaussian draws with the Jeans moments of `model` (Hernquist 1993's approach); the bulge and the halo
+    are isotropic, the disk streams with the asymmetric-drift-corrected rotation."""
+    R = np.hypot(disk[0], disk[1])
+    sR2, sphi2, sz2, vphi = model.disk_moments(R)
+    vR = g.standard_normal(R.size) * np.sqrt(sR2)
+    vp = vphi + g.standard_normal(R.size) * np.sqrt(sphi2)
+    vz = g.standard_normal(R.size) * np.sqrt(sz2)
+    cphi, sphi = disk[0] / np.maximum(R, 1e-300), disk[1] / np.maximum(R, 1e-300)
+    vdisk = np.stack([vR * cphi - vp * sphi, vR * sphi + vp * cphi, vz])
+    parts = [vdisk]
+    for comp, p in (("bulge", bulge), ("halo", halo)):
+        s = np.sqrt(model.sigma_r2(comp, np.sqrt((p * p).sum(0))))
+        parts.append(g.standard_normal(p.shape) * s)
+    return np.concatenate(parts, axis=1)
 
 
 def _disk_galaxy_parts(g, n, rd, z0, bulge_a, halo_c, r200):

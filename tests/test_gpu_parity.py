@@ -19,7 +19,7 @@ if torch.cuda.is_available():
 # particle.  Float32 positions relative to a leaf centre carry a rounding of ~6e-8 of the leaf size,
 # so the absolute force error is ~1e-6 of the typical (median) force whatever a particle's own net
 # force; particles whose contributions cancel to below 10% of the typical force are therefore held
-# to 1e-5 of that floor (see the design notes).
+# to 1e-5 of that floor, since their own float32 net force cannot be resolved to 1e-5 of itself.
 FP32_TOL = 1e-5
 FP32_FLOOR = 0.1
 

@@ -53,3 +53,61 @@ def test_ensemble_sizes():
     sizes = np.array([p.shape[1] for p, _ in systems])
     assert len(systems) == 64 and sizes.min() >= 2 ** 10 and sizes.max() <= 2 ** 17
     assert all(abs(m.sum() - 1.0) < 1e-12 for _, m in systems)
+
+
+# ---------------------------------------------------------------- disk galaxy velocities (Jeans moments)
+def _disk_sample(n=1 << 15, seed=1003):
+    pos, vel, mass = ics.disk_galaxy(n, seed, velocities=True)
+    pos0, mass0 = ics.disk_galaxy(n, seed)
+    assert np.array_equal(pos, pos0) and np.array_equal(mass, mass0)   # velocities do not move the particles
+    return pos, vel, mass
+
+
+def test_disk_galaxy_virial_ratio():
+    # the sampled system is near equilibrium: 2K / |W| = 1 within a few per cent, W from float64 direct
+    # summation of the sample (Wendland eps = 0.02, the workload's softening)
+    import oracle
+    pos, vel, m = _disk_sample()
+    _, pot = oracle.direct(pos, m, 0.02)
+    K = 0.5 * float((m * (vel * vel).sum(0)).sum())
+    W = 0.5 * float((m * pot).sum())
+    assert abs(2.0 * K / -W - 1.0) < 0.05
+    assert np.abs((vel * m).sum(1)).max() < 1e-15   # centre-of-mass frame
+
+
+def test_disk_galaxy_rotation_curve_matches_direct_forces():
+    # the model's midplane circular speed (spherical parts + Freeman's thin exponential disk) against the
+    # radial pull measured by direct summation on particles near the midplane, in three annuli
+    import oracle
+    pos, vel, m = _disk_sample()
+    model = ics.DiskGalaxyModel()
+    R = np.hypot(pos[0], pos[1])
+    plane = np.nonzero(np.abs(pos[2]) < 0.15)[0]   # sinks near the midplane (any component)
+    for r0 in (3.0, 6.0, 9.0):
+        sel = plane[np.abs(R[plane] - r0) < 0.5][:400]
+        assert sel.size >= 100
+        acc, _ = oracle.direct(pos, m, 0.02, sinks=sel)
+        aR = -(acc[0] * pos[0, sel] + acc[1] * pos[1, sel]) / R[sel]
+        vc2_meas = float(np.mean(aR * R[sel]))
+        assert abs(vc2_meas / float(model.vc2(np.array([r0]))[0]) - 1.0) < 0.08, r0
+
+
+def test_disk_galaxy_toomre_q_measured_back():
+    # Q = sigma_R kappa / (3.36 Sigma) at the reference radius 2.43 rd, with sigma_R and Sigma measured
+    # from the disk particles of an annulus and kappa from the model's rotation curve
+    n = 1 << 18
+    g = ics.rng(1003)
+    disk, bulge, halo = ics._disk_galaxy_parts(g, n, 3.0, 0.3, 0.6, 10.0, 30.0)
+    model = ics.DiskGalaxyModel()
+    v = ics.disk_galaxy_velocities(ics.rng(1003 + 7919), model, disk, bulge, halo)[:, :disk.shape[1]]
+    R = np.hypot(disk[0], disk[1])
+    r0, half = model.r_ref, 0.4
+    sel = np.abs(R - r0) < half
+    vR = (v[0, sel] * disk[0, sel] + v[1, sel] * disk[1, sel]) / R[sel]
+    sigma_surf = sel.sum() * (0.1 / disk.shape[1]) / (np.pi * ((r0 + half) ** 2 - (r0 - half) ** 2))
+    k2, _ = model.kappa2_omega2(np.array([r0]))
+    q = vR.std() * np.sqrt(k2[0]) / (3.36 * sigma_surf)
+    assert abs(q / 1.5 - 1.0) < 0.06
+    # the disk rotates: mean v_phi there is positive and below the circular speed (asymmetric drift)
+    vphi = (-v[0, sel] * disk[1, sel] + v[1, sel] * disk[0, sel]) / R[sel]
+    assert 0.0 < vphi.mean() < np.sqrt(model.vc2(np.array([r0]))[0])

@@ -246,3 +246,49 @@ def test_traditional_scheme_breaks_momentum_conservation():
     assert len(np.unique(t.rung)) >= 3
     assert p_hhs < 1e-14
     assert p_trad > 1e3 * max(p_hhs, 1e-16)
+
+
+# ---------------------------------------------------------------- conservation diagnostics (Sec. 3.2)
+def test_diagnostics_circular_kepler_pair():
+    # two masses 1/2 on a circular orbit of separation a = 1 (G = M = 1): P = 0,
+    # L = mu a v_rel = (1/4) a sqrt(1/a) along +z, E = -m1 m2 / (2 a)
+    pos, vel, m, a = ics.two_body(1.0, 0.0)
+    _, pot = oracle.direct(pos, m, 1e-4)
+    d = oracle.diagnostics(pos, vel, m, pot)
+    assert np.abs(d[:3]).max() < 1e-16
+    assert d[3:6] == pytest.approx([0.0, 0.0, 0.25 * a * math.sqrt(1.0 / a)], abs=1e-16)
+    assert d[6] == pytest.approx(-0.25 / (2.0 * a), rel=1e-15)
+
+
+def test_diagnostics_rigid_rotation_and_translation():
+    # v = u + omega x x: P = M u + omega x (sum m x), and L = sum m x cross u + I omega with the inertia tensor
+    # I = sum m (|x|^2 1 - x x^T) (the x cross (omega cross x) expansion); K = (1/2) sum m |v|^2
+    g = np.random.default_rng(11)
+    n = 257
+    pos = g.standard_normal((3, n))
+    m = ics.random_masses(n, 5)
+    u = np.array([0.3, -0.2, 0.7])
+    om = np.array([-0.4, 1.1, 0.25])
+    vel = u[:, None] + np.cross(om, pos.T).T
+    d = oracle.diagnostics(pos, vel, m)
+    assert d[:3] == pytest.approx(m.sum() * u + np.cross(om, (pos * m).sum(1)), rel=1e-13, abs=1e-15)
+    inertia = np.einsum("i,ji,ki->jk", m, pos, pos)
+    I = np.eye(3) * np.trace(inertia) - inertia
+    L_want = np.cross((pos * m).sum(1), u) + I @ om
+    assert d[3:6] == pytest.approx(L_want, rel=1e-12, abs=1e-14)
+    K = 0.5 * float((m * (vel * vel).sum(0)).sum())
+    assert d[6] == pytest.approx(K, rel=1e-13)
+
+
+def test_diagnostics_plummer_virial_and_binding_energy():
+    # a Plummer sphere drawn from its distribution function is in virial equilibrium, 2K + W = 0, and
+    # its potential energy is W = -3 pi / 32 (G = M = a = 1; Plummer-softened with a small eps the
+    # pairwise sum differs little).  Both hold within the sampling noise of 8192 particles.
+    n = 8192
+    pos, vel, m = ics.plummer(n, 1001)
+    _, pot = oracle.direct(pos, m, 1e-3, kernel=oracle.PLUMMER)
+    d_all = oracle.diagnostics(pos, vel, m, pot)
+    K = oracle.diagnostics(pos, vel, m)[6]
+    W = d_all[6] - K
+    assert W == pytest.approx(-3.0 * math.pi / 32.0, rel=0.05)
+    assert 2.0 * K / -W == pytest.approx(1.0, abs=0.06)

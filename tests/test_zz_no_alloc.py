@@ -28,7 +28,11 @@ def _reference(pos):
 
 def test_noalloc_sort_matches_allocating_path_twice():
     dev = torch.device("cuda:0")
-    cases = [ics.plummer(200003, 1001)[0], ics.clustered(77777, 1007)[0]]
+    # 98 and 38 sort tiles, the largest size the static scratch is laid out for (128 full tiles),
+    # and a size just below it that ends in a ragged tile
+    nmax = tg.TG_NOALLOC_MAX_N
+    cases = [ics.plummer(200003, 1001)[0], ics.clustered(77777, 1007)[0], ics.uniform_sphere(nmax, 1002)[0],
+             ics.plummer(nmax - 2047 - 64, 1008)[0]]
     for pos_np in cases:
         pos = torch.tensor(np.ascontiguousarray(pos_np), device=dev)
         keys, perm = tg.tg_morton_sort_noalloc(pos)
