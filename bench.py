@@ -1,8 +1,13 @@
 """Benchmark: particle-forces/s of the momentum-conserving FMM + HHS step on one GB300.
 
-Workload (default): cold collapse of a uniform-density sphere, N = 2^20, R = 1, at rest,
-Wendland C2 softening eps = 0.005, p = 6, theta = 0.5, kappa = 1, n_crit = 96 (measured best of 48-128), float32 P2P/M2L,
-HHS with eta = 0.025, k_max = 10 and dt_max = 1/16 (the t = 0 sphere then spans rungs 0-3).
+Workload (default, the largest single-GPU FMM + HHS configuration): an isolated disk galaxy,
+N = 2^22 -- exponential disk (R_d = 3, z0 = 0.3, 10 %, velocities from Jeans moments with Toomre
+Q = 1.5), Hernquist bulge (5 %), NFW halo (c = 10, 85 %) -- Wendland C2 softening eps = 0.02, p = 6,
+theta = 0.6, kappa = 1, float32 P2P/M2L, HHS with eta = 0.025, dt_max = 2 and k_max = 14 (the
+initial galaxy then spans rungs 0-6).  `--workload collapse` selects the cold collapse of a uniform
+sphere (N = 2^20, eps = 0.005, p = 6, theta = 0.5, dt_max = 1/16, k_max = 10), whose t = 0 step is
+also reported beside the headline.
+
 One step = one rung-0 step of EVOLVE_HOLD (every stage of the hot path: keys, sort, octree,
 P2M/M2M, walk, M2L, P2P, L2L/L2P, timestep split, kicks, drifts), starting each time from the
 same initial state.  A particle-force is one sink's acceleration from one FMM evaluation.
@@ -26,10 +31,23 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "particle-forces/s (FMM+HHS, 1 GB300) at median force err <=1e-4; |sum m v| drift"
-WORKLOAD = "cold-collapse uniform sphere N=2^20, eps=0.005 Wendland C2, p=6, theta=0.5, fp32 P2P/M2L, " \
-           "HHS k_max=10 dt_max=1/16 eta=0.025 (one rung-0 step from t=0)"
-SM_COUNT = 152
 FP32_LANES_PER_SM = 128
+
+WORKLOADS = {
+    "disk": dict(
+        n=1 << 22, seed=1003,
+        desc="isolated disk galaxy N={n}: exponential disk (Rd=3, z0=0.3, 10%, Jeans velocities, Toomre Q=1.5) + "
+             "Hernquist bulge (5%) + NFW halo (c=10, 85%), eps=0.02 Wendland C2, p=6, theta=0.6, fp32 P2P/M2L, "
+             "HHS k_max=14 dt_max=2 eta=0.025 (one rung-0 step from t=0)",
+        params=dict(p=6, theta=0.6, eps=0.02, kernel=0, n_crit=96, kappa=1.0, eta=0.025, dt_max=2.0, k_max=14)),
+    "collapse": dict(
+        n=1 << 20, seed=1002,
+        desc="cold-collapse uniform sphere N={n}, eps=0.005 Wendland C2, p=6, theta=0.5, fp32 P2P/M2L, "
+             "HHS k_max=10 dt_max=1/16 eta=0.025 (one rung-0 step from t=0)",
+        params=dict(p=6, theta=0.5, eps=0.005, kernel=0, n_crit=96, kappa=1.0, eta=0.025, dt_max=1.0 / 16, k_max=10)),
+}
+# the default workload's parameters (the θ/p sweeps and momentum runs keep their own)
+PARAMS = WORKLOADS["disk"]["params"]
 
 
 def parse():
@@ -38,9 +56,13 @@ def parse():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--n", type=int, default=1 << 20)
+    ap.add_argument("--workload", default="disk", choices=sorted(WORKLOADS))
+    ap.add_argument("--n", type=int, default=0, help="particle count (0: the workload's own)")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extra", action="store_true", help="skip the cold-collapse t = 0 figures beside the headline")
+    ap.add_argument("--evolved", action="store_true",
+                    help="also time the cold collapse from an evolved state (untimed evolution to t = 1 first)")
     ap.add_argument("--momentum-contrast", action="store_true",
                     help="run HHS and the traditional integrator to t = --contrast-t on the unit-cube collapse "
                          "and print |sum m v| for both")
@@ -52,25 +74,38 @@ def parse():
     ap.add_argument("--contrast-t", type=float, default=1.0)
     ap.add_argument("--mac", default="side", choices=["side", "sphere"],
                     help="multipole acceptance: the paper's R = kappa*side, or enclosing-sphere radii")
-    ap.add_argument("--theta", type=float, default=PARAMS["theta"])
+    ap.add_argument("--theta", type=float, default=0.0, help="opening angle (0: the workload's own)")
     ap.add_argument("--eta-tot", type=float, default=0.0,
                     help="eta_1 of the Eq. (9) minimum timestep from the total acceleration (0 = off)")
     ap.add_argument("--no-fp64-plain", action="store_true",
-                    help="skip the one-step timing of the plain float64 GPU path beside the float32 one")
-    ap.add_argument("--cpu-sample", type=int, default=3072)
-    ap.add_argument("--n-crit", type=int, default=PARAMS["n_crit"])
+                    help="skip the timing of the plain float64 GPU path beside the float32 one")
+    ap.add_argument("--cpu-sample", type=int, default=1024)
+    ap.add_argument("--n-crit", type=int, default=0, help="leaf size (0: the workload's own)")
     ap.add_argument("--eval-only", action="store_true",
                     help="run warmup + steps single FMM evaluations of the workload (for profiler captures)")
     ap.add_argument("--masked", action="store_true", help="with --eval-only: 30%% of the particles in the fast set")
     return ap.parse_args()
 
 
-def workload(n, seed=1002):
+def workload(name, n, seed=None):
+    """(pos, vel, mass) of a workload: seeded synthetic inputs (CPU, float64)."""
     from paper_1712_10116_gb300 import ics
+    w = WORKLOADS[name]
+    seed = w["seed"] if seed is None else seed
+    if name == "disk":
+        return ics.disk_galaxy(n, seed, velocities=True)
     return ics.uniform_sphere(n, seed)
 
 
-PARAMS = dict(p=6, theta=0.5, eps=0.005, kernel=0, n_crit=96, kappa=1.0, eta=0.025, dt_max=1.0 / 16, k_max=10)
+def run_params(args, name):
+    prm = dict(WORKLOADS[name]["params"])
+    if args.n_crit:
+        prm["n_crit"] = args.n_crit
+    if args.theta:
+        prm["theta"] = args.theta
+    prm["eta_tot"] = args.eta_tot
+    prm["mac"] = 1 if args.mac == "sphere" else 0
+    return prm
 
 
 def combine_ranks(t_dev, sinks, device, world):
@@ -133,11 +168,12 @@ class Clocks:
 
 
 # ---------------------------------------------------------------- reference arm: the CPU oracle
-def cpu_oracle_rate(n, n_sample, seed=7):
+def cpu_oracle_rate(name, n, n_sample, args, seed=7):
     import oracle
-    pos, _, mass = workload(n)
-    prm = oracle.params(p=PARAMS["p"], theta=PARAMS["theta"], eps=PARAMS["eps"], kernel=PARAMS["kernel"],
-                        n_crit=PARAMS["n_crit"], kappa=PARAMS["kappa"])
+    pos, _, mass = workload(name, n)
+    prm_d = run_params(args, name)
+    prm = oracle.params(p=prm_d["p"], theta=prm_d["theta"], eps=prm_d["eps"], kernel=prm_d["kernel"],
+                        n_crit=prm_d["n_crit"], kappa=prm_d["kappa"], mac=prm_d["mac"])
     sample = np.random.default_rng(seed).choice(n, n_sample, replace=False)
     t0 = time.perf_counter()
     oracle.fmm_sample(pos, mass, prm, sample)
@@ -149,19 +185,21 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
+    name = args.workload
+    n = args.n or WORKLOADS[name]["n"]
     n_sample = max(16, args.cpu_sample // 4)
     times = []
     for i in range(args.warmup + args.steps):
-        rate, dt, cores = cpu_oracle_rate(args.n, n_sample, seed=100 + i)
+        rate, dt, cores = cpu_oracle_rate(name, n, n_sample, args, seed=100 + i)
         if i >= args.warmup:
             times.append(dt)
     value = n_sample * len(times) / sum(times)
-    sample_desc = f"oracle FMM (FP64, C, OpenMP) for {n_sample} random sinks of the N={args.n} sphere per step, " \
-                  f"tree + moments of all N included"
+    sample_desc = f"oracle FMM (FP64, C, OpenMP) for {n_sample} random sinks of the N={n} {name} workload per " \
+                  f"step, tree + moments of all N included"
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "particle-forces/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "n": args.n, "l2": "cpu"},
+            "config": {"workload": WORKLOADS[name]["desc"].format(n=n), "n": n, "l2": "cpu"},
             "cpu_baseline": {"value": value, "unit": "particle-forces/s", "cores": cores, "kind": "oracle",
                              "sample": sample_desc},
             "e2e": {"value": value, "unit": "particle-forces/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -169,6 +207,64 @@ def run_reference(args):
 
 
 # ---------------------------------------------------------------- our arm
+class HHSRun:
+    """One bound HHS system on the GPU that can be reset to its initial state between timed steps."""
+
+    def __init__(self, tg, prm, pos0, vel0, mass0, dev, stream):
+        import torch
+        self.tg = tg
+        self.solver = tg.Solver(prm, stream)
+        self.P0 = torch.tensor(pos0, device=dev)
+        self.V0 = torch.tensor(vel0, device=dev)
+        self.M = torch.tensor(mass0, device=dev)
+        self.P = self.P0.clone()
+        self.V = self.V0.clone()
+        self.solver.hhs_init(self.P, self.V, self.M)
+        n = self.M.shape[0]
+        _, self.aold0, self.acur0, self.atot0 = tg.tg_hhs_state(self.solver.ctx, n, dev, with_total=True)
+
+    def reset(self):
+        self.P.copy_(self.P0)
+        self.V.copy_(self.V0)
+        self.tg.tg_hhs_set_accel(self.solver.ctx, self.aold0, self.acur0, self.atot0)
+
+    def close(self):
+        self.solver.close()
+
+
+def time_hhs_steps(run, steps, warmup, stream, flush, prof_level=1, clocks=None, barrier=None):
+    """Warm-up steps, then `steps` timed rung-0 steps (each from the initial state, L2 flushed before
+    each); returns (per-step ms list, stats, profile)."""
+    import torch
+    tg = run.tg
+    for _ in range(warmup):
+        run.reset()
+        run.solver.hhs_step()
+    torch.cuda.synchronize()
+    tg.tg_set_profiling(run.solver.ctx, prof_level)
+    tg.tg_reset_stats(run.solver.ctx)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    if barrier:
+        barrier()
+    torch.cuda.synchronize()
+    if clocks:
+        clocks.start()
+    for k in range(steps):
+        run.reset()
+        flush.zero_()
+        ev[k][0].record(stream)
+        run.solver.hhs_step()
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    if clocks:
+        clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    stats = run.solver.stats()
+    prof = tg.tg_get_profile(run.solver.ctx)
+    tg.tg_set_profiling(run.solver.ctx, 0)
+    return step_ms, stats, prof
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -183,61 +279,30 @@ def run_ours(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
 
-    n = args.n
+    name = args.workload
+    n = args.n or WORKLOADS[name]["n"]
     # replicas only: each rank integrates its own independent system (seed per rank)
-    pos0, vel0, mass0 = workload(n, seed=1002 + rank)
+    pos0, vel0, mass0 = workload(name, n, seed=WORKLOADS[name]["seed"] + rank)
     prec = tg.TG_PREC_FP32 if args.precision == "fp32" else tg.TG_PREC_FP64
-    run_params = dict(PARAMS, n_crit=args.n_crit, eta_tot=args.eta_tot, theta=args.theta,
-                      mac=1 if args.mac == "sphere" else 0)
-    prm = tg.Params(precision=prec, **run_params)
-    solver = tg.Solver(prm, stream)
-    P0 = torch.tensor(pos0, device=dev)
-    V0 = torch.tensor(vel0, device=dev)
-    M = torch.tensor(mass0, device=dev)
-    P = P0.clone()
-    V = V0.clone()
-    solver.hhs_init(P, V, M)
-    _, aold0, acur0, atot0 = tg.tg_hhs_state(solver.ctx, n, dev, with_total=True)
+    rp = run_params(args, name)
+    prm = tg.Params(precision=prec, **rp)
+    run = HHSRun(tg, prm, pos0, vel0, mass0, dev, stream)
+    solver = run.solver
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # 256 MB > 129 MB L2
 
-    def reset():
-        P.copy_(P0)
-        V.copy_(V0)
-        tg.tg_hhs_set_accel(solver.ctx, aold0, acur0, atot0)
-
     d_start = solver.diagnostics()
-    for _ in range(args.warmup):
-        reset()
-        solver.hhs_step()
-    torch.cuda.synchronize()
-    tg.tg_set_profiling(solver.ctx, 1)
-    tg.tg_reset_stats(solver.ctx)
     clocks = Clocks()
-    clocks.start()
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    if world > 1:
-        dist.barrier()
-    torch.cuda.synchronize()
+    barrier = dist.barrier if world > 1 else None
     wall0 = time.perf_counter()
-    for k in range(args.steps):
-        reset()
-        flush.zero_()
-        ev[k][0].record(stream)
-        solver.hhs_step()
-        ev[k][1].record(stream)
-    torch.cuda.synchronize()
+    step_ms, stats, prof = time_hhs_steps(run, args.steps, args.warmup, stream, flush, 1, clocks, barrier)
     wall = time.perf_counter() - wall0
-    clocks.stop()
-    step_ms = [a.elapsed_time(b) for a, b in ev]
-    stats = solver.stats()
-    prof = tg.tg_get_profile(solver.ctx)
-    tg.tg_set_profiling(solver.ctx, 0)
-    d_end = solver.diagnostics()
+    d_end = solver.diagnostics()   # the state after the last timed step (one rung-0 step from t = 0)
     # one extra (untimed) step with every launch timed, for the per-stage breakdown
     tg.tg_reset_stats(solver.ctx)
     tg.tg_set_profiling(solver.ctx, 2)
-    reset()
+    run.reset()
     solver.hhs_step()
     breakdown = {k: v["ms"] for k, v in tg.tg_get_profile(solver.ctx).items() if k != "_all"}
     tg.tg_set_profiling(solver.ctx, 0)
@@ -247,15 +312,15 @@ def run_ours(args):
     value = sinks_all / t_max
 
     # accuracy gate: one float32 evaluation of the initial state vs float64 direct summation
-    acc, _ = solver.fmm_forces(P0, M, want_pot=False)
+    acc, _ = solver.fmm_forces(run.P0, run.M, want_pot=False)
     sample = torch.tensor(np.random.default_rng(3).choice(n, 4096, replace=False), device=dev)
-    ad, _ = solver.direct_forces(P0, M, None, sample)
+    ad, _ = solver.direct_forces(run.P0, run.M, None, sample)
     a = acc[:, sample]
     err = (torch.linalg.norm(a - ad, dim=0) / torch.linalg.norm(ad, dim=0)).cpu().numpy()
 
     # end to end through the C ABI with host buffers: pinned H2D of the state, the step, D2H
-    hP = P0.cpu().pin_memory()
-    hV = V0.cpu().pin_memory()
+    hP = run.P0.cpu().pin_memory()
+    hV = run.V0.cpu().pin_memory()
     oP = torch.empty_like(hP).pin_memory()
     oV = torch.empty_like(hV).pin_memory()
     e2e_steps = max(1, min(args.steps, 3))
@@ -263,51 +328,94 @@ def run_ours(args):
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
-        P.copy_(hP, non_blocking=True)
-        V.copy_(hV, non_blocking=True)
-        tg.tg_hhs_set_accel(solver.ctx, aold0, acur0, atot0)
+        run.P.copy_(hP, non_blocking=True)
+        run.V.copy_(hV, non_blocking=True)
+        tg.tg_hhs_set_accel(solver.ctx, run.aold0, run.acur0, run.atot0)
         solver.hhs_step()
-        oP.copy_(P, non_blocking=True)
-        oV.copy_(V, non_blocking=True)
+        oP.copy_(run.P, non_blocking=True)
+        oV.copy_(run.V, non_blocking=True)
         torch.cuda.synchronize()
     e2e_t = time.perf_counter() - t0
     e2e_sinks = solver.stats()["sink_forces"]
     h2d = 2 * 3 * n * 8
     d2h = 2 * 3 * n * 8
 
-    # the plain float64 path on the same initial state (one rung-0 step, after its own hhs_init):
-    # same tree, walk and schedule, float64 P2P tiles and the generic float64 M2L, no potential skipping
+    # the plain float64 path against the float32 path on one evaluation of the whole initial state
+    # (same tree and walk; float64 P2P tiles, generic float64 M2L with the potential)
     fp64 = None
     if rank == 0 and prec == tg.TG_PREC_FP32 and not args.no_fp64_plain:
-        s64 = tg.Solver(tg.Params(precision=tg.TG_PREC_FP64, **run_params), stream)
-        P64, V64 = P0.clone(), V0.clone()
-        s64.hhs_init(P64, V64, M)
-        tg.tg_hhs_set_accel(s64.ctx, aold0, acur0, atot0)
-        tg.tg_reset_stats(s64.ctx)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        flush.zero_()
-        torch.cuda.synchronize()
-        e0.record(stream)
-        s64.hhs_step()
-        e1.record(stream)
-        torch.cuda.synchronize()
-        ms64 = e0.elapsed_time(e1)
-        sinks64 = s64.stats()["sink_forces"]
-        fp64 = {"ms_per_step": ms64, "value": sinks64 / (ms64 / 1e3), "unit": "particle-forces/s",
-                "steps": 1, "speedup_of_fp32_path": (sinks / t_max) / (sinks64 / (ms64 / 1e3)),
-                "note": "plain float64 path: same tree, walk and HHS schedule, float64 P2P (block per leaf pair) "
-                        "and generic float64 M2L; one rung-0 step from the same state"}
-        s64.close()
+        fp64 = compare_fp64_plain(tg, rp, run, stream, flush)
+
+    extra = {}
+    if rank == 0 and not args.no_extra and name != "collapse":
+        extra["cold_collapse_t0"] = measure_other(tg, args, "collapse", dev, stream, flush, evolved=False)
+    if rank == 0 and args.evolved:
+        extra["cold_collapse_evolved_t1"] = measure_other(tg, args, "collapse", dev, stream, flush, evolved=True)
 
     if rank != 0:
-        solver.close()
+        run.close()
         if world > 1:
             dist.barrier()
             dist.destroy_process_group()
         return
 
-    # roofline of the dominant kernel (by live CUDA-event time)
     clk = clocks.summary()
+    roof = roofline(prof, stats, rp["p"], sm_count)
+    cpu = None
+    if not args.no_cpu_baseline and (world == 1 or args.gpus == 1):
+        rate, dt, cores = cpu_oracle_rate(name, n, args.cpu_sample, args)
+        cpu = {"value": rate, "unit": "particle-forces/s", "cores": cores, "kind": "oracle",
+               "sample": f"oracle FMM (FP64) of {args.cpu_sample} random sinks of the same N={n} {name} workload, "
+                         f"tree + moments of all N included, {dt:.1f} s"}
+    mom_scale = float((run.M * run.V0.abs().sum(0)).sum()) or 1.0
+    launches = int(prof.get("_all", {}).get("launches", 0))
+    line = {
+        "metric": METRIC, "value": value, "unit": "particle-forces/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32" if prec == tg.TG_PREC_FP32 else "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOADS[name]["desc"].format(n=n), "n": n,
+                   "l2": "flushed (256 MB write) between timed steps",
+                   "parallelism": f"replicas x{world}", "kappa": rp["kappa"], "n_crit": rp["n_crit"],
+                   "eta_tot": rp["eta_tot"], "theta": rp["theta"], "mac": args.mac, "dt_max": rp["dt_max"],
+                   "k_max": rp["k_max"]},
+        "accuracy": {"median_force_err_vs_fp64_direct": float(np.median(err)),
+                     "p99_force_err": float(np.percentile(err, 99)), "sample_sinks": int(sample.numel()),
+                     "momentum_drift_one_step": float(np.abs(d_end[:3] - d_start[:3]).max()),
+                     "momentum_scale": mom_scale},
+        "work": per_step_work(stats, launches, args.steps),
+        "kernels_ms_per_step": {k: v["ms"] / args.steps for k, v in prof.items()
+                                if k != "_all" and v["launches"] > 0 and v["ms"] > 0},
+        "stage_ms_one_step_all_timed": breakdown,
+        "roofline": roof,
+        "fp64_plain_gpu": fp64,
+        "extra": extra,
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_sinks / e2e_t, "unit": "particle-forces/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches,
+        "clocks": clk,
+        "wall_s_timed": wall,
+    }
+    print(json.dumps(line), flush=True)
+    run.close()
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def per_step_work(stats, launches, steps):
+    return {"sink_forces_per_step": stats["sink_forces"] / steps,
+            "evaluations_per_step": stats["evaluations"] / steps,
+            "kdk_frames_per_step": stats["kdk_frames"] / steps,
+            "kernel_launches_per_step": launches / steps,
+            "host_syncs_per_step": stats["host_syncs"] / steps,
+            "p2p_pairs_per_step": stats["p2p_pairs"] / steps,
+            "m2l_pairs_per_step": stats["m2l_pairs"] / steps, "max_rung": stats["max_rung"]}
+
+
+def roofline(prof, stats, p, sm_count):
+    """Roofline of the dominant kernel class (by live CUDA-event time over the timed steps)."""
     peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     sm_max = 2070.0
     if os.path.exists(peaks_path):
@@ -315,67 +423,82 @@ def run_ours(args):
             sm_max = float(json.load(open(peaks_path)).get("sm_max_mhz", 2070.0))
         except Exception:
             pass
-    fp32_peak_tflops = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    fp32_peak_tflops = sm_count * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
     kernels = {k: v for k, v in prof.items() if v["launches"] > 0 and k != "_all"}
     traffic = captured_traffic()
     dom = max(kernels.items(), key=lambda kv: kv[1]["ms"])[0] if kernels else None
-    roof = None
     if dom == "p2p":
         flops = float(P2P_FLOPS_PER_PAIR) * stats["p2p_pairs"]
-        achieved = flops / (kernels["p2p"]["ms"] / 1e3) / 1e12
         units = stats["p2p_pairs"] / kernels["p2p"]["launches"]
-        roof = {"kernel": "p2p_mutual", "bound": "alu", "achieved": achieved, "peak": fp32_peak_tflops,
-                "unit": "TFLOP/s", "frac": achieved / fp32_peak_tflops,
-                "traffic": scaled_traffic(traffic, "p2p", units),
-                "per_launch": {"flops": flops / kernels["p2p"]["launches"],
-                               "ms": kernels["p2p"]["ms"] / kernels["p2p"]["launches"]}}
+        kname = "p2p_mutual"
     elif dom == "m2l":
-        flops = m2l_flops(PARAMS["p"], stats["m2l_pairs"], stats)
-        achieved = flops / (kernels["m2l"]["ms"] / 1e3) / 1e12
+        flops = m2l_flops(p, stats["m2l_pairs"], stats)
         units = stats["m2l_pairs"] / kernels["m2l"]["launches"]
-        roof = {"kernel": "m2l_mutual", "bound": "alu", "achieved": achieved, "peak": fp32_peak_tflops,
-                "unit": "TFLOP/s", "frac": achieved / fp32_peak_tflops,
-                "traffic": scaled_traffic(traffic, "m2l", units),
-                "per_launch": {"flops": flops / kernels["m2l"]["launches"],
-                               "ms": kernels["m2l"]["ms"] / kernels["m2l"]["launches"]}}
-    cpu = None
-    if not args.no_cpu_baseline and world == 1 or (not args.no_cpu_baseline and rank == 0 and args.gpus == 1):
-        rate, dt, cores = cpu_oracle_rate(n, args.cpu_sample)
-        cpu = {"value": rate, "unit": "particle-forces/s", "cores": cores, "kind": "oracle",
-               "sample": f"oracle FMM (FP64) of {args.cpu_sample} random sinks of the same N={n} sphere, "
-                         f"tree + moments of all N included, {dt:.1f} s"}
-    mom_scale = float((M * V0.abs().sum(0)).sum()) or 1.0
-    line = {
-        "metric": METRIC, "value": value, "unit": "particle-forces/s", "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32" if prec == tg.TG_PREC_FP32 else "f64",
-        "data": "synthetic",
-        "config": {"workload": WORKLOAD, "n": n, "l2": "flushed (256 MB write) between timed steps",
-                   "parallelism": f"replicas x{world}", "kappa": PARAMS["kappa"], "n_crit": args.n_crit,
-                   "eta_tot": args.eta_tot, "theta": args.theta, "mac": args.mac},
-        "accuracy": {"median_force_err_vs_fp64_direct": float(np.median(err)),
-                     "p99_force_err": float(np.percentile(err, 99)), "sample_sinks": int(sample.numel()),
-                     "momentum_drift_one_step": float(np.abs(d_end[:3] - d_start[:3]).max()),
-                     "momentum_scale": mom_scale},
-        "work": {"sink_forces_per_step": sinks / args.steps, "evaluations_per_step": stats["evaluations"] / args.steps,
-                 "p2p_pairs_per_step": stats["p2p_pairs"] / args.steps,
-                 "m2l_pairs_per_step": stats["m2l_pairs"] / args.steps, "max_rung": stats["max_rung"]},
-        "kernels_ms_per_step": {k: v["ms"] / args.steps for k, v in kernels.items() if v["ms"] > 0},
-        "stage_ms_one_step_all_timed": breakdown,
-        "roofline": roof,
-        "fp64_plain_gpu": fp64,
-        "cpu_baseline": cpu,
-        "e2e": {"value": e2e_sinks / e2e_t, "unit": "particle-forces/s", "h2d_bytes_per_step": h2d,
-                "d2h_bytes_per_step": d2h},
-        "gpu_launches": int(prof.get("_all", {}).get("launches", 0)),
-        "clocks": clk,
-        "wall_s_timed": wall,
-    }
-    print(json.dumps(line), flush=True)
-    solver.close()
-    if world > 1:
-        dist.barrier()
-        dist.destroy_process_group()
+        kname = "m2l_mutual"
+    else:
+        return None
+    achieved = flops / (kernels[dom]["ms"] / 1e3) / 1e12
+    return {"kernel": kname, "bound": "alu", "achieved": achieved, "peak": fp32_peak_tflops, "unit": "TFLOP/s",
+            "frac": achieved / fp32_peak_tflops, "traffic": scaled_traffic(traffic, dom, units),
+            "peak_note": f"float32 SIMT peak = {sm_count} SMs x 128 lanes x 2 flop x {sm_max:.0f} MHz (max SM clock)",
+            "per_launch": {"flops": flops / kernels[dom]["launches"], "ms": kernels[dom]["ms"] / kernels[dom]["launches"]}}
+
+
+def compare_fp64_plain(tg, rp, run, stream, flush):
+    """One evaluation of the whole initial state in the plain float64 path and in the float32 path."""
+    import torch
+    out = {}
+    for key, prec in (("fp64", tg.TG_PREC_FP64), ("fp32", tg.TG_PREC_FP32)):
+        s = tg.Solver(tg.Params(precision=prec, **rp), stream)
+        s.fmm_forces(run.P0, run.M, want_pot=False)   # warm-up (buffers)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        flush.zero_()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        s.fmm_forces(run.P0, run.M, want_pot=False)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        out[key] = e0.elapsed_time(e1)
+        s.close()
+    n = run.M.shape[0]
+    return {"eval_ms_fp64": out["fp64"], "eval_ms_fp32": out["fp32"],
+            "value_fp64": n / (out["fp64"] / 1e3), "unit": "particle-forces/s",
+            "speedup_of_fp32_path": out["fp64"] / out["fp32"],
+            "note": "one all-from-all evaluation of the initial state: plain float64 path (float64 P2P block per "
+                    "leaf pair, generic float64 M2L, potentials) vs the float32 path (accelerations only)"}
+
+
+def measure_other(tg, args, name, dev, stream, flush, evolved):
+    """Figures of a second workload: a few timed rung-0 steps (after an untimed evolution to t = 1
+    when `evolved`)."""
+    w = WORKLOADS[name]
+    n = w["n"]
+    pos0, vel0, mass0 = workload(name, n)
+    rp = dict(w["params"], eta_tot=0.0, mac=0)
+    run = HHSRun(tg, tg.Params(precision=tg.TG_PREC_FP32, **rp), pos0, vel0, mass0, dev, stream)
+    t_evolve = 0.0
+    if evolved:
+        import torch
+        nsteps = int(round(1.0 / rp["dt_max"]))
+        w0 = time.perf_counter()
+        for _ in range(nsteps):
+            run.solver.hhs_step()
+        torch.cuda.synchronize()
+        t_evolve = time.perf_counter() - w0
+        # the evolved state becomes the state each timed step starts from
+        run.P0.copy_(run.P)
+        run.V0.copy_(run.V)
+        _, run.aold0, run.acur0, run.atot0 = tg.tg_hhs_state(run.solver.ctx, n, dev, with_total=True)
+    steps = 2 if evolved else 3
+    step_ms, stats, prof = time_hhs_steps(run, steps, 1 if evolved else 2, stream, flush)
+    t = sum(step_ms) / 1e3
+    out = {"workload": w["desc"].format(n=n).replace("from t=0", "from t=1" if evolved else "from t=0"),
+           "value": stats["sink_forces"] / t, "unit": "particle-forces/s", "ms_per_step": 1e3 * t / steps,
+           "steps": steps, "work": per_step_work(stats, int(prof.get("_all", {}).get("launches", 0)), steps)}
+    if evolved:
+        out["untimed_evolution_s"] = t_evolve
+    run.close()
+    return out
 
 
 def captured_traffic():
@@ -432,12 +555,13 @@ def run_eval_only(args):
     from paper_1712_10116_gb300 import ics
 
     dev = torch.device("cuda", 0)
-    pos, _, mass = workload(args.n)
+    n = args.n or WORKLOADS[args.workload]["n"]
+    pos, _, mass = workload(args.workload, n)
     prec = tg.TG_PREC_FP32 if args.precision == "fp32" else tg.TG_PREC_FP64
-    solver = tg.Solver(tg.Params(precision=prec, **dict(PARAMS, n_crit=args.n_crit)))
+    solver = tg.Solver(tg.Params(precision=prec, **run_params(args, args.workload)))
     P = torch.tensor(pos, device=dev)
     M = torch.tensor(mass, device=dev)
-    F = torch.tensor(ics.random_fast_mask(args.n, 17), device=dev) if args.masked else None
+    F = torch.tensor(ics.random_fast_mask(n, 17), device=dev) if args.masked else None
     for _ in range(args.warmup):
         solver.fmm_forces(P, M, F, want_pot=False)
     torch.cuda.synchronize()
@@ -452,7 +576,7 @@ def run_eval_only(args):
     solver.fmm_forces(P, M, F, want_pot=False)
     stages = {k: round(v["ms"], 3) for k, v in tg.tg_get_profile(solver.ctx).items()}
     tg.tg_set_profiling(solver.ctx, 0)
-    print(json.dumps({"mode": "eval-only", "n": args.n, "n_crit": args.n_crit, "masked": bool(args.masked),
+    print(json.dumps({"mode": "eval-only", "workload": args.workload, "n": n, "masked": bool(args.masked),
                       "ms_per_eval": 1e3 * dt, "stage_ms": stages, "stats": solver.stats()}), flush=True)
     solver.close()
 

@@ -93,6 +93,8 @@ typedef struct {
     int64_t kdk_frames;      /* KDK frames of the HHS schedule                                  */
     int64_t max_rung;        /* deepest rung that held a slow particle                          */
     int64_t m2l_class_pairs; /* M2L cell pairs x local-expansion classes (1, or 2 for a kick pair) */
+    int64_t list_regrowths;  /* dual walks re-run because an interaction list outgrew its buffer  */
+    int64_t host_syncs;      /* host waits on the stream inside evaluations and HHS steps         */
 } tg_stats;
 
 /* Create a context bound to `cuda_stream` (a cudaStream_t, NULL = legacy default stream) on the
@@ -117,7 +119,8 @@ tg_status tg_build_tree(tg_ctx *ctx, int64_t n, const double *pos);
  *           Algorithm 2 evaluated on a single tree and walk.
  *   acc     device, 3*n float64 output (SoA), overwritten
  *   pot     device, n float64 output or NULL
- * Not synchronising (host reads of list sizes aside). */
+ * TG_ERR_NONFINITE if a position or mass is NaN or infinite (checked on the device first; acc
+ * and pot are then untouched).  Not synchronising (host reads of sizes aside). */
 tg_status tg_fmm_forces(tg_ctx *ctx, int64_t n, const double *pos, const double *mass,
                         const uint8_t *is_fast, double *acc, double *pot);
 
@@ -132,10 +135,16 @@ tg_status tg_direct_forces(tg_ctx *ctx, int64_t n, const double *pos, const doub
 /* HOLD integrator (Sec. 2.2).  tg_hhs_init binds caller-owned device arrays pos (3*n), vel (3*n)
  * and mass (n) to the context; they are updated in place by every tg_hhs_step and must stay
  * allocated until tg_destroy or the next tg_hhs_init.  It performs the initial all-from-all
- * evaluation that sets |a_current|; |a_old| starts at 0. */
+ * evaluation that sets |a_current|; |a_old| starts at 0.  TG_ERR_NONFINITE if a position or
+ * mass is not finite. */
 tg_status tg_hhs_init(tg_ctx *ctx, int64_t n, double *pos, double *vel, const double *mass);
 /* One rung-0 step of EVOLVE_HOLD (Algorithm 1) of length params.dt_max: recursive
  * slow/fast split, KDK (Algorithm 2) with the kickS2F/kickFS2S pairs of Algorithm 3, drifts.
+ * The step length is params.dt_max (the survey's hhs_step(dt) reads dt from the parameters, fixed
+ * at tg_create, so that the rung ladder dt_max / 2^k stays the same for the whole run).
+ * The step is transactional: the bound pos and vel and the integrator state are saved first, and
+ * any error inside the step (TG_ERR_OOM, TG_ERR_CAPACITY, ...) restores them before returning.
+ * TG_ERR_NONFINITE (nothing changed) if a bound position or mass is not finite at the start.
  * Synchronising (the recursion reads the set sizes of each split). */
 tg_status tg_hhs_step(tg_ctx *ctx);
 /* The traditional integrator with individual timesteps that the paper sets beside HHS (Sec. 2.3),
@@ -193,6 +202,19 @@ tg_status tg_get_tree(tg_ctx *ctx, uint64_t *keys, int64_t *perm, int32_t *level
  * then pairs (int64 a[], b[]). */
 tg_status tg_list_counts(tg_ctx *ctx, int64_t *n_m2l, int64_t *n_p2p);
 tg_status tg_get_lists(tg_ctx *ctx, int64_t *m2l_a, int64_t *m2l_b, int64_t *p2p_a, int64_t *p2p_b);
+
+/* Failure injection and capacity control for tests of the error paths (host side only; nothing
+ * here makes a kernel fault).  what:
+ *   TG_DEBUG_FAIL_ALLOC      value >= 0: after `value` more successful scratch allocations of this
+ *                            context, every further one fails as if cudaMalloc had (TG_ERR_OOM);
+ *                            value < 0 switches the injection off.
+ *   TG_DEBUG_LIST_CAPACITY   value > 0: the walk's per-cell estimates of the interaction-list sizes
+ *                            are set to value / 1000 (tiny values force the regrowth path: the
+ *                            lists are sized from the estimates, overflow, and the walk is re-run
+ *                            with larger buffers; tg_stats.list_regrowths counts the re-runs).
+ * TG_ERR_ARG for an unknown `what`.  Not synchronising. */
+typedef enum { TG_DEBUG_FAIL_ALLOC = 1, TG_DEBUG_LIST_CAPACITY = 2 } tg_debug_what;
+tg_status tg_debug_control(tg_ctx *ctx, int what, int64_t value);
 
 /* ---- live kernel timing (CUDA events on the context's stream) ---- */
 typedef enum {

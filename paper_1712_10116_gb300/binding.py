@@ -46,7 +46,8 @@ class tg_params(C.Structure):
 class tg_stats(C.Structure):
     _fields_ = [("evaluations", C.c_int64), ("sink_forces", C.c_int64), ("p2p_pairs", C.c_int64),
                 ("m2l_pairs", C.c_int64), ("p2p_cell_pairs", C.c_int64), ("cells", C.c_int64),
-                ("kdk_frames", C.c_int64), ("max_rung", C.c_int64), ("m2l_class_pairs", C.c_int64)]
+                ("kdk_frames", C.c_int64), ("max_rung", C.c_int64), ("m2l_class_pairs", C.c_int64),
+                ("list_regrowths", C.c_int64), ("host_syncs", C.c_int64)]
 
 
 KERNEL_CLASSES = ["tree", "up", "walk", "m2l", "p2p", "down", "hhs", "other"]
@@ -119,12 +120,13 @@ def load() -> C.CDLL:
             L.tg_timesteps.argtypes = [_vp, _i64, _vp, _vp, _vp, _vp, _vp]
             L.tg_morton_sort_noalloc.argtypes = [_i64, _vp, _vp, _vp, _vp]
             L.tg_morton_sort_noalloc.restype = C.c_int
+            L.tg_debug_control.argtypes = [_vp, C.c_int, _i64]
             L.tg_set_profiling.argtypes = [_vp, C.c_int]
             L.tg_get_profile.argtypes = [_vp, C.POINTER(tg_profile)]
             for name in ("tg_create", "tg_destroy", "tg_get_stats", "tg_reset_stats", "tg_build_tree",
                          "tg_fmm_forces", "tg_direct_forces", "tg_hhs_init", "tg_hhs_step", "tg_hhs_state",
                          "tg_hhs_set_accel", "tg_diagnostics", "tg_tree_info", "tg_get_tree", "tg_list_counts",
-                         "tg_get_lists", "tg_timesteps", "tg_set_profiling", "tg_get_profile"):
+                         "tg_get_lists", "tg_timesteps", "tg_set_profiling", "tg_get_profile", "tg_debug_control"):
                 getattr(L, name).restype = C.c_int
             _lib = L
     return _lib
@@ -308,6 +310,14 @@ def tg_morton_sort_noalloc(pos, keys_out=None, perm_out=None, stream=None):
     if rc != 0:
         raise TGError(rc, "tg_morton_sort_noalloc")
     return keys_out, perm_out
+
+
+TG_DEBUG_FAIL_ALLOC = 1
+TG_DEBUG_LIST_CAPACITY = 2
+
+
+def tg_debug_control(ctx, what: int, value: int):
+    _check(ctx, load().tg_debug_control(ctx, what, value))
 
 
 def tg_timesteps(ctx, a_old, a_cur, a_tot=None):

@@ -193,6 +193,7 @@ tg_status tg_fmm_forces(tg_ctx *c, int64_t n, const double *pos, const double *m
     if (!check_device_ptr(pos) || !check_device_ptr(mass) || !check_device_ptr(acc) ||
         (is_fast && !check_device_ptr(is_fast)) || (pot && !check_device_ptr(pot)))
         return set_err(c, TG_ERR_ARG, "tg_fmm_forces: arrays must be device memory");
+    if ((st = check_finite(c, n, pos, n, nullptr, mass))) return st;
     return fmm_eval(c, (int)n, pos, n, nullptr, mass, is_fast, acc, n, pot, true);
 }
 
@@ -216,6 +217,8 @@ tg_status tg_hhs_init(tg_ctx *c, int64_t n, double *pos, double *vel, const doub
     if (st) return st;
     if (n <= 0 || n > INT32_MAX / 4 || !check_device_ptr(pos) || !check_device_ptr(vel) || !check_device_ptr(mass))
         return set_err(c, TG_ERR_ARG, "tg_hhs_init: need n > 0 and device arrays");
+    if ((st = check_finite(c, n, pos, n, nullptr, mass)) || (st = check_finite(c, n, vel, n, nullptr, nullptr)))
+        return st;
     c->hhs_n = n;
     c->hhs_pos = pos;
     c->hhs_vel = vel;
@@ -305,6 +308,23 @@ tg_status tg_diagnostics(tg_ctx *c, double out[8])
     if (!out) return set_err(c, TG_ERR_ARG, "out is NULL");
     if (c->hhs_n <= 0) return set_err(c, TG_ERR_STATE, "tg_diagnostics before tg_hhs_init");
     return hhs_diagnostics(c, out);
+}
+
+tg_status tg_debug_control(tg_ctx *c, int what, int64_t value)
+{
+    tg_status st = begin(c);
+    if (st) return st;
+    switch (what) {
+    case TG_DEBUG_FAIL_ALLOC:
+        c->debug_fail_alloc_after = value < 0 ? -1 : value;
+        return TG_OK;
+    case TG_DEBUG_LIST_CAPACITY:
+        if (value <= 0) return set_err(c, TG_ERR_ARG, "tg_debug_control: list capacity estimate must be > 0");
+        c->walk_front_per_cell = c->walk_blocks_per_cell = c->walk_p2p_per_cell = (double)value / 1000.0;
+        return TG_OK;
+    default:
+        return set_err(c, TG_ERR_ARG, "tg_debug_control: unknown control %d", what);
+    }
 }
 
 tg_status tg_tree_info(tg_ctx *c, double lo[3], double *L, int64_t *n, int64_t *n_cells)

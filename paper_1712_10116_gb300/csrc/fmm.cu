@@ -883,7 +883,7 @@ static tg_status run_walk(tg_ctx *c, const TreeView &t, int64_t *n_blocks, int64
     {
         const Geom *dg = static_cast<const Geom *>(c->buf[B_GEOM].p);
         cudaMemcpyAsync(c->h_pinned + 32, &dg->log2L, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
-        cudaError_t e = cudaStreamSynchronize(c->stream);
+        cudaError_t e = stream_sync(c);
         if (e != cudaSuccess) return cuda_check(c, e, "walk setup");
         log2L = *reinterpret_cast<int *>(c->h_pinned + 32);
     }
@@ -914,7 +914,7 @@ static tg_status run_walk(tg_ctx *c, const TreeView &t, int64_t *n_blocks, int64
             *n_m2l = 0;
             *n_p2p = 0;
             *n_self = 1;
-            return cuda_check(c, cudaStreamSynchronize(c->stream), "walk");
+            return cuda_check(c, stream_sync(c), "walk");
         }
         {
             ProfScope ps_(c, TG_K_WALK);
@@ -931,7 +931,7 @@ static tg_status run_walk(tg_ctx *c, const TreeView &t, int64_t *n_blocks, int64
         }
         cudaMemcpyAsync(c->h_pinned, ctr, (8 + nsteps + 1) * sizeof(unsigned long long), cudaMemcpyDeviceToHost,
                         c->stream);
-        cudaError_t e = cudaStreamSynchronize(c->stream);
+        cudaError_t e = stream_sync(c);
         if (e != cudaSuccess) return cuda_check(c, e, "walk");
         const unsigned long long *h = reinterpret_cast<const unsigned long long *>(c->h_pinned);
         tot_blocks = h[1];
@@ -953,6 +953,7 @@ static tg_status run_walk(tg_ctx *c, const TreeView &t, int64_t *n_blocks, int64
             *n_self = (int64_t)tot_self;
             return TG_OK;
         }
+        c->stats.list_regrowths += 1;
         cap_front = std::max(cap_front * 2, need_front + need_front / 2);
         cap_blocks = tot_blocks > cap_blocks ? tot_blocks * 2 : cap_blocks * 3 / 2;
         cap_p2p = tot_p2p + tot_self > cap_p2p ? (tot_p2p + tot_self) * 2 : cap_p2p * 3 / 2;

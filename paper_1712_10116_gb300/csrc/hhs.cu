@@ -206,7 +206,7 @@ static tg_status evolve_hold(Sched &s, int k, int64_t ns, double dt, int calc)
     }
     uint32_t *h = reinterpret_cast<uint32_t *>(c->h_pinned + 40);
     cudaMemcpyAsync(h, d_total, sizeof(uint32_t), cudaMemcpyDeviceToHost, c->stream);
-    cudaError_t e = cudaStreamSynchronize(c->stream);
+    cudaError_t e = stream_sync(c);
     if (e != cudaSuccess) return cuda_check(c, e, "hhs split");
     const int64_t nF = (int64_t)*h, nS = ns - nF;
     if (nS > 0 && k > c->stats.max_rung) c->stats.max_rung = k;
@@ -255,20 +255,63 @@ tg_status hhs_init(tg_ctx *c)
     return cuda_check(c, cudaGetLastError(), "hhs init");
 }
 
+// Snapshot of the integrator state (pos, vel, |a_old|, |a_cur|, |a|_tot, rungs) that makes a rung-0 step
+// transactional: an error inside the step copies it back.
+static tg_status snapshot_state(tg_ctx *c, const Sched &s, char **snap)
+{
+    const size_t n = (size_t)s.n;
+    tg_status st = ensure_t(c, B_SNAP, n * (9 * sizeof(double) + sizeof(int32_t)), snap);
+    if (st) return st;
+    double *d = reinterpret_cast<double *>(*snap);
+    cudaMemcpyAsync(d, c->hhs_pos, 3 * n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream);
+    cudaMemcpyAsync(d + 3 * n, c->hhs_vel, 3 * n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream);
+    cudaMemcpyAsync(d + 6 * n, s.a_old, n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream);
+    cudaMemcpyAsync(d + 7 * n, s.a_cur, n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream);
+    cudaMemcpyAsync(d + 8 * n, s.a_tot, n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream);
+    cudaMemcpyAsync(d + 9 * n, s.rung, n * sizeof(int32_t), cudaMemcpyDeviceToDevice, c->stream);
+    return cuda_check(c, cudaGetLastError(), "hhs snapshot");
+}
+
+static void restore_state(tg_ctx *c, const Sched &s, const char *snap)
+{
+    const size_t n = (size_t)s.n;
+    const double *d = reinterpret_cast<const double *>(snap);
+    cudaMemcpyAsync(c->hhs_pos, d, 3 * n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream);
+    cudaMemcpyAsync(c->hhs_vel, d + 3 * n, 3 * n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream);
+    cudaMemcpyAsync(s.a_old, d + 6 * n, n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream);
+    cudaMemcpyAsync(s.a_cur, d + 7 * n, n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream);
+    cudaMemcpyAsync(s.a_tot, d + 8 * n, n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream);
+    cudaMemcpyAsync(s.rung, d + 9 * n, n * sizeof(int32_t), cudaMemcpyDeviceToDevice, c->stream);
+    stream_sync(c);
+}
+
 tg_status hhs_step(tg_ctx *c)
 {
     Sched s;
     tg_status st = make_sched(c, s);
     if (st) return st;
-    if ((st = level_buffers(c, s.n, s.lv, c->prm.k_max))) return st;
-    {
-        ProfScope ps_(c, TG_K_HHS);
-        hhs_iota<<<grid_for(s.n, 256), 256, 0, c->stream>>>(s.n, s.lv[0].sys);
+    if ((st = check_finite(c, s.n, c->hhs_pos, s.n, nullptr, c->hhs_mass))) return st;
+    char *snap = nullptr;
+    if ((st = snapshot_state(c, s, &snap))) return st;
+    const tg_stats stats0 = c->stats;
+    if ((st = level_buffers(c, s.n, s.lv, c->prm.k_max)) == TG_OK) {
+        {
+            ProfScope ps_(c, TG_K_HHS);
+            hhs_iota<<<grid_for(s.n, 256), 256, 0, c->stream>>>(s.n, s.lv[0].sys);
+        }
+        st = evolve_hold(s, 0, s.n, c->prm.dt_max, 1);
+        if (st == TG_OK) st = cuda_check(c, stream_sync(c), "hhs step");
     }
-    if ((st = evolve_hold(s, 0, s.n, c->prm.dt_max, 1))) return st;
+    if (st) {
+        // the buffers may have moved while growing: the snapshot slot is looked up again
+        restore_state(c, s, static_cast<const char *>(c->buf[B_SNAP].p));
+        const int64_t regrow = c->stats.list_regrowths;
+        c->stats = stats0;
+        c->stats.list_regrowths = regrow;
+        return st;
+    }
     c->hhs_time += c->prm.dt_max;
-    cudaError_t e = cudaStreamSynchronize(c->stream);
-    return cuda_check(c, e, "hhs step");
+    return TG_OK;
 }
 
 __global__ void timestep_rungs(int64_t n, const double *a_old, const double *a_cur, double eta_eps, const double *a_tot,
@@ -447,7 +490,7 @@ tg_status trad_step(tg_ctx *c)
         }
         unsigned long long *h = reinterpret_cast<unsigned long long *>(c->h_pinned + 48);
         cudaMemcpyAsync(h, ctr, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, c->stream);
-        cudaError_t e = cudaStreamSynchronize(c->stream);
+        cudaError_t e = stream_sync(c);
         if (e != cudaSuccess) return cuda_check(c, e, "traditional step");
         const int64_t t = (int64_t)h[0], na = (int64_t)h[1];
         if (t > m_end || na <= 0) return set_err(c, TG_ERR_STATE, "traditional step: no boundary found");
@@ -469,7 +512,7 @@ tg_status trad_step(tg_ctx *c)
     }
     unsigned long long *h = reinterpret_cast<unsigned long long *>(c->h_pinned + 48);
     cudaMemcpyAsync(h, ctr + 2, sizeof(unsigned long long), cudaMemcpyDeviceToHost, c->stream);
-    if ((st = cuda_check(c, cudaStreamSynchronize(c->stream), "traditional step"))) return st;
+    if ((st = cuda_check(c, stream_sync(c), "traditional step"))) return st;
     if ((int64_t)h[0] > c->stats.max_rung) c->stats.max_rung = (int64_t)h[0];
     c->hhs_time += dt_max;
     return TG_OK;
@@ -524,7 +567,7 @@ tg_status hhs_diagnostics(tg_ctx *c, double out[8])
     }
     std::vector<double> h(nb * 8);
     cudaError_t e = cudaMemcpyAsync(h.data(), partial, sizeof(double) * nb * 8, cudaMemcpyDeviceToHost, c->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e == cudaSuccess) e = stream_sync(c);
     if (e != cudaSuccess) return cuda_check(c, e, "diagnostics");
     double q[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     for (int b = 0; b < nb; ++b)

@@ -95,6 +95,9 @@ struct tg_ctx {
     const double *hhs_mass = nullptr;
     double hhs_time = 0.0;
     int bound_integrator = 0;                   // 1: HHS (tg_hhs_init), 2: traditional (tg_trad_init)
+
+    // failure injection (tg_debug_control): allocations allowed before they fail, < 0 = off
+    int64_t debug_fail_alloc_after = -1;
 };
 
 namespace tg {
@@ -110,12 +113,14 @@ enum Slot {
     B_FRONT0, B_FRONT1, B_M2L, B_P2P, B_WALK_CNT,
     B_SUB_ACC, B_HHS_AOLD, B_HHS_ACUR, B_HHS_ATOT, B_TRAD_ACC, B_TRAD_END, B_HHS_DT, B_HHS_RUNG, B_HHS_IDX, B_HHS_FLAG,
     B_HHS_SCAN, B_HHS_TMP, B_RED, B_DIAG_POT, B_DIAG_ACC,
-    B_OWN_CNT, B_OWN_FILL, B_OWN_OFF, B_OWN_LIST, B_OWN_TAG, B_OWN_PART,
+    B_OWN_CNT, B_OWN_FILL, B_OWN_OFF, B_OWN_LIST, B_OWN_TAG, B_OWN_PART, B_SNAP,
     B_LAST_SLOT
 };
 static_assert(B_LAST_SLOT <= kMaxSlots, "tg_ctx::buf holds fewer entries than there are slots");
 
 tg_status set_err(tg_ctx *c, tg_status code, const char *fmt, ...);
+// Host wait on the context's stream inside the pipeline (counted in tg_stats.host_syncs).
+cudaError_t stream_sync(tg_ctx *c);
 tg_status cuda_check(tg_ctx *c, cudaError_t e, const char *what);
 // Make buffer `slot` at least `bytes` long (contents are not preserved when it grows).
 tg_status ensure(tg_ctx *c, int slot, size_t bytes, void **out);
@@ -162,6 +167,13 @@ tg_status launch_l2l_hi(tg_ctx *c, const TreeView &t, int lb, int le, int p, int
 template <class T, class T4>
 tg_status launch_l2p_hi(tg_ctx *c, int n, const TreeView &t, const T4 *pf, const int32_t *leaf_of, const uint8_t *fs,
                         bool masked, int p, int ncp, const T *L, double *acc4);
+
+// Count the non-finite positions (gathered through sub when non-null) and masses of n particles on the
+// device; TG_ERR_NONFINITE (with a message) if there is one.  Synchronising.
+tg_status check_finite(tg_ctx *c, int64_t n, const double *pos, int64_t stride, const int64_t *sub,
+                       const double *mass);
+// Consume one allocation of the failure injection; TG_ERR_OOM when it says this one fails.
+tg_status injected_alloc_failure(tg_ctx *c, size_t bytes, int slot);
 
 // Device-wide exclusive scan of uint32 (in place allowed); optional total to a device word.
 tg_status exclusive_scan_u32(tg_ctx *c, const uint32_t *in, uint32_t *out, int n, uint32_t *d_total);

@@ -26,6 +26,12 @@ tg_status set_err(tg_ctx *c, tg_status code, const char *fmt, ...)
     return code;
 }
 
+cudaError_t stream_sync(tg_ctx *c)
+{
+    c->stats.host_syncs += 1;
+    return cudaStreamSynchronize(c->stream);
+}
+
 tg_status cuda_check(tg_ctx *c, cudaError_t e, const char *what)
 {
     if (e == cudaSuccess) return TG_OK;
@@ -33,13 +39,23 @@ tg_status cuda_check(tg_ctx *c, cudaError_t e, const char *what)
                    cudaGetErrorString(e));
 }
 
+tg_status injected_alloc_failure(tg_ctx *c, size_t bytes, int slot)
+{
+    if (c->debug_fail_alloc_after < 0) return TG_OK;
+    if (c->debug_fail_alloc_after == 0)
+        return set_err(c, TG_ERR_OOM, "allocation of %zu bytes for scratch slot %d failed (injected)", bytes, slot);
+    c->debug_fail_alloc_after -= 1;
+    return TG_OK;
+}
+
 tg_status ensure(tg_ctx *c, int slot, size_t bytes, void **out)
 {
     Buf &b = c->buf[slot];
     if (b.bytes < bytes) {
         size_t nb = bytes + bytes / 4 + 256;
+        if (tg_status inj = injected_alloc_failure(c, nb, slot)) return inj;
         if (b.p) {
-            cudaError_t e = cudaStreamSynchronize(c->stream);
+            cudaError_t e = stream_sync(c);
             if (e != cudaSuccess) return cuda_check(c, e, "sync before regrow");
             cudaFree(b.p);
             b.p = nullptr;
@@ -65,6 +81,7 @@ static tg_status ensure_keep(tg_ctx *c, int slot, size_t bytes, size_t keep, voi
         return TG_OK;
     }
     size_t nb = bytes + bytes / 2 + 256;
+    if (tg_status inj = injected_alloc_failure(c, nb, slot)) return inj;
     void *np = nullptr;
     cudaError_t e = cudaMalloc(&np, nb);
     if (e != cudaSuccess) {
@@ -73,7 +90,7 @@ static tg_status ensure_keep(tg_ctx *c, int slot, size_t bytes, size_t keep, voi
     }
     if (b.p) {
         if (keep) cudaMemcpyAsync(np, b.p, keep, cudaMemcpyDeviceToDevice, c->stream);
-        e = cudaStreamSynchronize(c->stream);
+        e = stream_sync(c);
         if (e != cudaSuccess) return cuda_check(c, e, "sync before regrow");
         cudaFree(b.p);
     }
@@ -123,7 +140,7 @@ ProfScope::~ProfScope()
 tg_status prof_collect(tg_ctx *c)
 {
     if (c->prof_used == 0) return TG_OK;
-    cudaError_t e = cudaStreamSynchronize(c->stream);
+    cudaError_t e = stream_sync(c);
     if (e != cudaSuccess) return cuda_check(c, e, "profile collect");
     for (size_t i = 0; i < c->prof_used; ++i) {
         float ms = 0.f;
@@ -357,6 +374,38 @@ tg_status root_cube(tg_ctx *c, int n, const double *pos, int64_t stride, const i
         bbox_final<<<1, 32, 0, c->stream>>>(partial, nb, n, d_geom);
     }
     return cuda_check(c, cudaGetLastError(), "root cube");
+}
+
+// ------------------------------------------------------------------ input check
+__global__ void count_nonfinite(const double *pos, int64_t stride, const int64_t *sub, int64_t n, const double *mass,
+                                unsigned long long *bad)
+{
+    unsigned long long cnt = 0;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = sub ? sub[q] : q;
+        const bool ok = isfinite(pos[i]) && isfinite(pos[stride + i]) && isfinite(pos[2 * stride + i]) &&
+                        (mass == nullptr || isfinite(mass[i]));
+        cnt += ok ? 0ull : 1ull;
+    }
+    cnt = warp_sum(cnt);
+    if ((threadIdx.x & 31) == 0 && cnt) atomicAdd(bad, cnt);
+}
+
+tg_status check_finite(tg_ctx *c, int64_t n, const double *pos, int64_t stride, const int64_t *sub, const double *mass)
+{
+    if (n <= 0) return TG_OK;
+    unsigned long long *bad = c->d_counters + 10;
+    cudaMemsetAsync(bad, 0, sizeof(unsigned long long), c->stream);
+    {
+        ProfScope ps_(c, TG_K_OTHER);
+        count_nonfinite<<<grid_for(n, 256, 2 * c->num_sms), 256, 0, c->stream>>>(pos, stride, sub, n, mass, bad);
+    }
+    unsigned long long *h = reinterpret_cast<unsigned long long *>(c->h_pinned + 56);
+    cudaMemcpyAsync(h, bad, sizeof(unsigned long long), cudaMemcpyDeviceToHost, c->stream);
+    cudaError_t e = stream_sync(c);
+    if (e != cudaSuccess) return cuda_check(c, e, "finiteness check");
+    if (*h) return set_err(c, TG_ERR_NONFINITE, "%llu particles have a non-finite position or mass", *h);
+    return TG_OK;
 }
 
 // ------------------------------------------------------------------ keys
@@ -685,7 +734,7 @@ tg_status build_octree(tg_ctx *c, int n, int *ncell_out)
         }
         if ((st = exclusive_scan_u32(c, cnt, off, m, d_total))) return st;
         cudaMemcpyAsync(h_total, d_total, sizeof(uint32_t), cudaMemcpyDeviceToHost, c->stream);
-        cudaError_t e = cudaStreamSynchronize(c->stream);
+        cudaError_t e = stream_sync(c);
         if (e != cudaSuccess) return cuda_check(c, e, "octree level");
         const int total = (int)*h_total;
         if (le + total > cap) {

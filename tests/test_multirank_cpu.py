@@ -28,7 +28,7 @@ def _rank_main(rank, world, port, out_dir):
     t_dev = 1.5 + rank          # rank 1 is the slow one
     sinks = 1000.0 * (rank + 1)
     t_max, sinks_all = bench.combine_ranks(t_dev, sinks, torch.device("cpu"), world)
-    pos, _, _ = bench.workload(64, seed=1002 + rank)
+    pos, _, _ = bench.workload("disk", 64, seed=1003 + rank)
     np.save(os.path.join(out_dir, f"r{rank}.npy"), np.array([t_max, sinks_all]))
     np.save(os.path.join(out_dir, f"p{rank}.npy"), pos)
     dist.barrier()
