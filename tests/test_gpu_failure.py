@@ -127,7 +127,7 @@ def test_injected_allocation_failure_inside_a_step_is_transactional():
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
 def test_interaction_lists_regrow_from_tiny_capacities(precision):
     pos, _, mass = ics.clustered(20000, 1007)
-    P = torch.tensor(pos, device=DEV)
+    P = torch.tensor(np.ascontiguousarray(pos), device=DEV)
     M = torch.tensor(mass, device=DEV)
     prec = tg.TG_PREC_FP64 if precision == "fp64" else tg.TG_PREC_FP32
     prm = tg.Params(p=4, n_crit=32, precision=prec)
