@@ -81,6 +81,8 @@ def parse():
                     help="skip the timing of the plain float64 GPU path beside the float32 one")
     ap.add_argument("--cpu-sample", type=int, default=1024)
     ap.add_argument("--n-crit", type=int, default=0, help="leaf size (0: the workload's own)")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the workload's leaf size and the default launch shapes (no tg_autotune)")
     ap.add_argument("--eval-only", action="store_true",
                     help="run warmup + steps single FMM evaluations of the workload (for profiler captures)")
     ap.add_argument("--masked", action="store_true", help="with --eval-only: 30%% of the particles in the fast set")
@@ -291,6 +293,15 @@ def run_ours(args):
     run = HHSRun(tg, prm, pos0, vel0, mass0, dev, stream)
     solver = run.solver
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # 256 MB > 129 MB L2
+    tuning = None
+    if not args.no_autotune and not args.n_crit:
+        # kick-pair objective: the fast set of a representative split, particles below the median timestep
+        _, rung0 = tg.tg_timesteps(solver.ctx, run.aold0, run.acur0, run.atot0)
+        fast = (rung0 > rung0.float().median()).to(torch.uint8)
+        w0 = time.perf_counter()
+        tuning = solver.autotune(run.P0, run.M, fast)
+        tuning["wall_s"] = time.perf_counter() - w0
+        tuning["objective"] = "one all-from-all evaluation + one kick-pair evaluation (fast = rungs above the median)"
 
     d_start = solver.diagnostics()
     clocks = Clocks()
@@ -378,7 +389,8 @@ def run_ours(args):
                    "l2": "flushed (256 MB write) between timed steps",
                    "parallelism": f"replicas x{world}", "kappa": rp["kappa"], "n_crit": rp["n_crit"],
                    "eta_tot": rp["eta_tot"], "theta": rp["theta"], "mac": args.mac, "dt_max": rp["dt_max"],
-                   "k_max": rp["k_max"]},
+                   "k_max": rp["k_max"], "autotune": tuning,
+                   "n_crit_used": tg.tg_get_tuning(solver.ctx)["n_crit"]},
         "accuracy": {"median_force_err_vs_fp64_direct": float(np.median(err)),
                      "p99_force_err": float(np.percentile(err, 99)), "sample_sinks": int(sample.numel()),
                      "momentum_drift_one_step": float(np.abs(d_end[:3] - d_start[:3]).max()),

@@ -216,6 +216,32 @@ tg_status tg_get_lists(tg_ctx *ctx, int64_t *m2l_a, int64_t *m2l_b, int64_t *p2p
 typedef enum { TG_DEBUG_FAIL_ALLOC = 1, TG_DEBUG_LIST_CAPACITY = 2 } tg_debug_what;
 tg_status tg_debug_control(tg_ctx *ctx, int what, int64_t value);
 
+/* ---- autotuner (the paper has no counterpart: it picks launch shapes and the leaf size of Sec. 2.3
+ * for this GPU and this particle distribution) ----
+ * tg_autotune times FMM evaluations of the given system (CUDA events on the context's stream, one
+ * warm-up, best of two) for candidate settings and keeps the fastest in the context:
+ *   n_crit            leaf size: 48, 64, 80, 96, 112, 128 (the tree, and so the results, change within
+ *                     the FMM's own accuracy; params.n_crit of the context is replaced)
+ *   p2p_rows          rows per lane of the float32 P2P tile: 1, 2, 3 (results unchanged)
+ *   m2l_blocks_per_sm grid of the float32 M2L kernel in blocks per SM: 4, 8, 16, 32 (results unchanged)
+ * searched one after another in that order (each at the best of the ones before).  The objective is
+ * the time of one all-from-all evaluation plus, when is_fast is given, one kick-pair evaluation with
+ * that fast set (accelerations only, as the HHS kicks ask).  pos: device 3*n float64, mass: device n
+ * float64, is_fast: device n uint8 or NULL.  out (host, nullable) receives the choice.  Synchronising;
+ * writes no caller array.  The float64 path has no tunable launch shapes: only n_crit is searched.
+ * tg_get_tuning reports the settings in use (the defaults before any tuning). */
+typedef struct {
+    int n_crit;              /* leaf size in use                                                 */
+    int p2p_rows;            /* rows per lane of the float32 P2P tile                            */
+    int m2l_blocks_per_sm;   /* float32 M2L grid, blocks per SM                                  */
+    int candidates;          /* settings timed by the last tg_autotune (0: never tuned)           */
+    double objective_ms;     /* objective at the chosen settings                                 */
+    double objective_ms_initial; /* objective at the settings the context had before tuning      */
+} tg_tuning;
+tg_status tg_autotune(tg_ctx *ctx, int64_t n, const double *pos, const double *mass, const uint8_t *is_fast,
+                      tg_tuning *out);
+tg_status tg_get_tuning(const tg_ctx *ctx, tg_tuning *out);
+
 /* ---- live kernel timing (CUDA events on the context's stream) ---- */
 typedef enum {
     TG_K_TREE = 0,   /* root cube, Morton keys, radix sort, gather, octree build            */

@@ -53,6 +53,11 @@ class tg_stats(C.Structure):
 KERNEL_CLASSES = ["tree", "up", "walk", "m2l", "p2p", "down", "hhs", "other"]
 
 
+class tg_tuning(C.Structure):
+    _fields_ = [("n_crit", C.c_int), ("p2p_rows", C.c_int), ("m2l_blocks_per_sm", C.c_int), ("candidates", C.c_int),
+                ("objective_ms", C.c_double), ("objective_ms_initial", C.c_double)]
+
+
 class tg_profile(C.Structure):
     _fields_ = [("ms", C.c_double * 8), ("launches", C.c_int64 * 8)]
 
@@ -121,12 +126,15 @@ def load() -> C.CDLL:
             L.tg_morton_sort_noalloc.argtypes = [_i64, _vp, _vp, _vp, _vp]
             L.tg_morton_sort_noalloc.restype = C.c_int
             L.tg_debug_control.argtypes = [_vp, C.c_int, _i64]
+            L.tg_autotune.argtypes = [_vp, _i64, _vp, _vp, _vp, C.POINTER(tg_tuning)]
+            L.tg_get_tuning.argtypes = [_vp, C.POINTER(tg_tuning)]
             L.tg_set_profiling.argtypes = [_vp, C.c_int]
             L.tg_get_profile.argtypes = [_vp, C.POINTER(tg_profile)]
             for name in ("tg_create", "tg_destroy", "tg_get_stats", "tg_reset_stats", "tg_build_tree",
                          "tg_fmm_forces", "tg_direct_forces", "tg_hhs_init", "tg_hhs_step", "tg_hhs_state",
                          "tg_hhs_set_accel", "tg_diagnostics", "tg_tree_info", "tg_get_tree", "tg_list_counts",
-                         "tg_get_lists", "tg_timesteps", "tg_set_profiling", "tg_get_profile", "tg_debug_control"):
+                         "tg_get_lists", "tg_timesteps", "tg_set_profiling", "tg_get_profile", "tg_debug_control",
+                         "tg_autotune", "tg_get_tuning"):
                 getattr(L, name).restype = C.c_int
             _lib = L
     return _lib
@@ -320,6 +328,23 @@ def tg_debug_control(ctx, what: int, value: int):
     _check(ctx, load().tg_debug_control(ctx, what, value))
 
 
+def _tuning_dict(t) -> dict:
+    return {k: getattr(t, k) for k, _ in tg_tuning._fields_}
+
+
+def tg_autotune(ctx, pos, mass, is_fast=None) -> dict:
+    """Time evaluations of this system over leaf size and launch shapes; the context keeps the fastest."""
+    out = tg_tuning()
+    _check(ctx, load().tg_autotune(ctx, mass.shape[0], _ptr(pos), _ptr(mass), _ptr(is_fast), C.byref(out)))
+    return _tuning_dict(out)
+
+
+def tg_get_tuning(ctx) -> dict:
+    out = tg_tuning()
+    _check(ctx, load().tg_get_tuning(ctx, C.byref(out)))
+    return _tuning_dict(out)
+
+
 def tg_timesteps(ctx, a_old, a_cur, a_tot=None):
     n = a_old.shape[0]
     dt = torch.empty(n, dtype=torch.float64, device=a_old.device)
@@ -337,6 +362,9 @@ class Solver:
 
     def fmm_forces(self, pos, mass, is_fast=None, want_pot=True):
         return tg_fmm_forces(self.ctx, pos, mass, is_fast, want_pot=want_pot)
+
+    def autotune(self, pos, mass, is_fast=None):
+        return tg_autotune(self.ctx, pos, mass, is_fast)
 
     def direct_forces(self, pos, mass, is_fast=None, sinks=None):
         return tg_direct_forces(self.ctx, pos, mass, is_fast, sinks)

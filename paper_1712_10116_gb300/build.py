@@ -16,7 +16,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libtaichi_gb.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
-SOURCES = ["tree.cu", "fmm.cu", "m2l.cu", "p2p.cu", "hhs.cu", "capi.cu", "noalloc.cu", "high_order.cu"]
+SOURCES = ["tree.cu", "fmm.cu", "m2l.cu", "p2p.cu", "hhs.cu", "capi.cu", "noalloc.cu", "high_order.cu", "tune.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-Xcompiler", "-Wall", "-I", CSRC, "-I", INCLUDE]

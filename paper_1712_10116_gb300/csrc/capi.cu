@@ -327,6 +327,26 @@ tg_status tg_debug_control(tg_ctx *c, int what, int64_t value)
     }
 }
 
+tg_status tg_autotune(tg_ctx *c, int64_t n, const double *pos, const double *mass, const uint8_t *is_fast,
+                      tg_tuning *out)
+{
+    tg_status st = begin(c);
+    if (st) return st;
+    if (n <= 0 || n > INT32_MAX / 4) return set_err(c, TG_ERR_ARG, "tg_autotune: n out of range");
+    if (!check_device_ptr(pos) || !check_device_ptr(mass) || (is_fast && !check_device_ptr(is_fast)))
+        return set_err(c, TG_ERR_ARG, "tg_autotune: arrays must be device memory");
+    if ((st = check_finite(c, n, pos, n, nullptr, mass))) return st;
+    return autotune(c, (int)n, pos, mass, is_fast, out);
+}
+
+tg_status tg_get_tuning(const tg_ctx *c, tg_tuning *out)
+{
+    if (!c || !out) return TG_ERR_ARG;
+    *out = c->tune;
+    out->n_crit = c->prm.n_crit;
+    return TG_OK;
+}
+
 tg_status tg_tree_info(tg_ctx *c, double lo[3], double *L, int64_t *n, int64_t *n_cells)
 {
     tg_status st = begin(c);

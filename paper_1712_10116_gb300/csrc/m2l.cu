@@ -40,7 +40,7 @@ tg_status launch_m2l_f32(tg_ctx *c, const TreeView &t, const M2LBlock *blocks, i
     const int plummer = c->prm.kernel == TG_KERNEL_PLUMMER;
     const float eoL = (float)ldexp(c->prm.eps, -c->walk_log2L);
     if (p > TG_PMAX) return launch_m2l_hi<float>(c, t, blocks, nblocks, Ms, L, p, nc, ncp, masked, pot);
-    const int grid = grid_for(nblocks * 32, 128, c->num_sms * 16);
+    const int grid = grid_for(nblocks * 32, 128, c->num_sms * c->tune.m2l_blocks_per_sm);
     // Wendland C2: the walk's eps gap rule leaves every M2L pair at r >= eps, where G = -1/r is harmonic
     if (!plummer && p >= 1 && p <= 6) {
         switch (p) {

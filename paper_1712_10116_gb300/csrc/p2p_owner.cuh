@@ -381,25 +381,38 @@ tg_status launch_p2p_f32(tg_ctx *c, const TreeView &t, const uint2 *pairs, int64
     unsigned long long *pc = c->d_counters;
     const bool plummer = c->prm.kernel == TG_KERNEL_PLUMMER;
     ProfScope ps_(c, TG_K_P2P);
-    // two rows per lane: rows are packed densely, so the chunk is full whatever the leaf size
-    // occupancy is the same for every instantiation (same registers and shared memory)
-    static int occ = 0;
-    if (occ == 0) {
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, p2p_owner_f32<TG_KERNEL_WENDLAND_C2, 2, true>, 256, 0) !=
-                cudaSuccess || occ < 1)
-            occ = 1;
+    // rows per lane (tg_autotune: 1, 2 or 3); rows are packed densely, so the chunk is full whatever
+    // the leaf size.  Resident blocks per SM, queried once per rows setting
+    const int rows = c->tune.p2p_rows;
+    static int occ[4] = {0, 0, 0, 0};
+    if (occ[rows] == 0) {
+        cudaError_t e = cudaErrorInvalidValue;
+        if (rows == 1) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[1], p2p_owner_f32<TG_KERNEL_WENDLAND_C2, 1, false>, 256, 0);
+        if (rows == 2) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[2], p2p_owner_f32<TG_KERNEL_WENDLAND_C2, 2, false>, 256, 0);
+        if (rows == 3) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[3], p2p_owner_f32<TG_KERNEL_WENDLAND_C2, 3, false>, 256, 0);
+        if (e != cudaSuccess || occ[rows] < 1) {
+            cudaGetLastError();
+            occ[rows] = 1;
+        }
     }
-    const int grid = c->num_sms * occ;
-#define TG_OWNER(K, PT)                                                                                           \
-    p2p_owner_f32<K, 2, PT><<<grid, 256, 0, c->stream>>>(t, c->walk_log2L, units, ctr, own_off, own_cnt, partners,  \
+    const int grid = c->num_sms * occ[rows];
+#define TG_OWNER(K, R, PT)                                                                                        \
+    p2p_owner_f32<K, R, PT><<<grid, 256, 0, c->stream>>>(t, c->walk_log2L, units, ctr, own_off, own_cnt, partners,  \
                                                          self_pairs, (uint32_t)nself, pf, nslow, eps, acc4, t.n, pc)
-    if (plummer) {
-        if (pot) TG_OWNER(TG_KERNEL_PLUMMER, true);
-        else TG_OWNER(TG_KERNEL_PLUMMER, false);
-    } else {
-        if (pot) TG_OWNER(TG_KERNEL_WENDLAND_C2, true);
-        else TG_OWNER(TG_KERNEL_WENDLAND_C2, false);
+#define TG_OWNER_ROWS(K, PT)                                                                                      \
+    switch (rows) {                                                                                               \
+    case 1: TG_OWNER(K, 1, PT); break;                                                                            \
+    case 3: TG_OWNER(K, 3, PT); break;                                                                            \
+    default: TG_OWNER(K, 2, PT);                                                                                  \
     }
+    if (plummer) {
+        if (pot) TG_OWNER_ROWS(TG_KERNEL_PLUMMER, true)
+        else TG_OWNER_ROWS(TG_KERNEL_PLUMMER, false)
+    } else {
+        if (pot) TG_OWNER_ROWS(TG_KERNEL_WENDLAND_C2, true)
+        else TG_OWNER_ROWS(TG_KERNEL_WENDLAND_C2, false)
+    }
+#undef TG_OWNER_ROWS
 #undef TG_OWNER
     return cuda_check(c, cudaGetLastError(), "p2p owner launch");
 }

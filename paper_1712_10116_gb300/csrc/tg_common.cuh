@@ -98,6 +98,9 @@ struct tg_ctx {
 
     // failure injection (tg_debug_control): allocations allowed before they fail, < 0 = off
     int64_t debug_fail_alloc_after = -1;
+
+    // launch shapes picked by tg_autotune (n_crit lives in prm)
+    tg_tuning tune{0, 2, 16, 0, 0.0, 0.0};
 };
 
 namespace tg {
@@ -113,7 +116,7 @@ enum Slot {
     B_FRONT0, B_FRONT1, B_M2L, B_P2P, B_WALK_CNT,
     B_SUB_ACC, B_HHS_AOLD, B_HHS_ACUR, B_HHS_ATOT, B_TRAD_ACC, B_TRAD_END, B_HHS_DT, B_HHS_RUNG, B_HHS_IDX, B_HHS_FLAG,
     B_HHS_SCAN, B_HHS_TMP, B_RED, B_DIAG_POT, B_DIAG_ACC,
-    B_OWN_CNT, B_OWN_FILL, B_OWN_OFF, B_OWN_LIST, B_OWN_TAG, B_OWN_PART, B_SNAP,
+    B_OWN_CNT, B_OWN_FILL, B_OWN_OFF, B_OWN_LIST, B_OWN_TAG, B_OWN_PART, B_SNAP, B_TUNE_ACC,
     B_LAST_SLOT
 };
 static_assert(B_LAST_SLOT <= kMaxSlots, "tg_ctx::buf holds fewer entries than there are slots");
@@ -216,6 +219,9 @@ tg_status fmm_eval(tg_ctx *c, int n, const double *pos, int64_t stride, const in
                    bool keep_tree);
 tg_status direct_eval(tg_ctx *c, int64_t n, const double *pos, const double *mass, const uint8_t *fast,
                       int64_t n_sink, const int64_t *sink_idx, double *acc, double *pot);
+
+// ---- tune.cu
+tg_status autotune(tg_ctx *c, int n, const double *pos, const double *mass, const uint8_t *fast, tg_tuning *out);
 
 // ---- hhs.cu
 tg_status hhs_init(tg_ctx *c);

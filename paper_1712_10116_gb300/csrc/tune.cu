@@ -1,0 +1,132 @@
+// tune.cu -- tg_autotune: the leaf size (n_crit of Sec. 2.3) and the launch shapes of the float32
+// P2P and M2L kernels, picked by timing FMM evaluations of the caller's own system on this GPU.
+//
+// The search is a coordinate descent: n_crit first (it changes the tree, hence the balance between
+// M2L and P2P work), then the P2P rows per lane and the M2L grid at the chosen n_crit (these change
+// launch shapes only, not results).  Each setting is timed with CUDA events on the context's stream
+// around one all-from-all evaluation plus, when a fast set is given, one kick-pair evaluation: one
+// warm-up round, then the best of two.
+#include <algorithm>
+
+#include "tg_common.cuh"
+
+namespace tg {
+
+namespace {
+
+struct TuneRun {
+    tg_ctx *c;
+    int n;
+    const double *pos, *mass;
+    const uint8_t *fast;
+    double *acc;
+    cudaEvent_t e0, e1;
+    int timed = 0;
+};
+
+tg_status objective(TuneRun &r, double *ms_out)
+{
+    tg_ctx *c = r.c;
+    tg_status st;
+    double best = 1e300;
+    for (int rep = 0; rep < 3; ++rep) {
+        cudaEventRecord(r.e0, c->stream);
+        if ((st = fmm_eval(c, r.n, r.pos, r.n, nullptr, r.mass, nullptr, r.acc, r.n, nullptr, false))) return st;
+        if (r.fast && (st = fmm_eval(c, r.n, r.pos, r.n, nullptr, r.mass, r.fast, r.acc, r.n, nullptr, false)))
+            return st;
+        cudaEventRecord(r.e1, c->stream);
+        if ((st = cuda_check(c, cudaEventSynchronize(r.e1), "autotune timing"))) return st;
+        float ms = 0.f;
+        if ((st = cuda_check(c, cudaEventElapsedTime(&ms, r.e0, r.e1), "autotune timing"))) return st;
+        if (rep > 0) best = std::min(best, (double)ms);   // rep 0 warms up buffers and caches
+    }
+    r.timed += 1;
+    *ms_out = best;
+    return TG_OK;
+}
+
+}  // namespace
+
+tg_status autotune(tg_ctx *c, int n, const double *pos, const double *mass, const uint8_t *fast, tg_tuning *out)
+{
+    tg_status st;
+    TuneRun r{c, n, pos, mass, fast, nullptr, nullptr, nullptr, 0};
+    if ((st = ensure_t(c, B_TUNE_ACC, (size_t)3 * n, &r.acc))) return st;
+    if (cudaEventCreate(&r.e0) != cudaSuccess || cudaEventCreate(&r.e1) != cudaSuccess) {
+        cudaGetLastError();
+        return set_err(c, TG_ERR_CUDA, "autotune: cannot create events");
+    }
+    // the tuning evaluations are not the caller's work: counters and event timing are left as they were
+    const tg_stats stats0 = c->stats;
+    const int prof0 = c->prof_level;
+    c->prof_level = 0;
+    const tg_params prm0 = c->prm;
+    const tg_tuning tune0 = c->tune;
+    auto finish = [&](tg_status s) {
+        const int64_t regrow = c->stats.list_regrowths, syncs = c->stats.host_syncs;
+        c->stats = stats0;
+        c->stats.list_regrowths = regrow;
+        c->stats.host_syncs = syncs;
+        c->prof_level = prof0;
+        cudaEventDestroy(r.e0);
+        cudaEventDestroy(r.e1);
+        if (s) {
+            c->prm = prm0;
+            c->tune = tune0;
+        }
+        return s;
+    };
+    double initial = 0.0, best = 0.0;
+    if ((st = objective(r, &initial))) return finish(st);
+    best = initial;
+    tg_tuning choice = c->tune;
+    choice.n_crit = c->prm.n_crit;
+    const int ncrit_cand[] = {48, 64, 80, 96, 112, 128};
+    for (int nc : ncrit_cand) {
+        if (nc == prm0.n_crit) continue;
+        c->prm.n_crit = nc;
+        double ms;
+        if ((st = objective(r, &ms))) return finish(st);
+        if (ms < best) {
+            best = ms;
+            choice.n_crit = nc;
+        }
+    }
+    c->prm.n_crit = choice.n_crit;
+    if (c->prm.precision == TG_PREC_FP32) {
+        // the objective at the chosen n_crit with the current shapes, then the other shapes
+        if ((st = objective(r, &best))) return finish(st);
+        const int rows_cand[] = {1, 2, 3};
+        for (int rows : rows_cand) {
+            if (rows == choice.p2p_rows) continue;
+            c->tune.p2p_rows = rows;
+            double ms;
+            if ((st = objective(r, &ms))) return finish(st);
+            if (ms < best) {
+                best = ms;
+                choice.p2p_rows = rows;
+            }
+        }
+        c->tune.p2p_rows = choice.p2p_rows;
+        const int grid_cand[] = {4, 8, 16, 32};
+        for (int g : grid_cand) {
+            if (g == choice.m2l_blocks_per_sm) continue;
+            c->tune.m2l_blocks_per_sm = g;
+            double ms;
+            if ((st = objective(r, &ms))) return finish(st);
+            if (ms < best) {
+                best = ms;
+                choice.m2l_blocks_per_sm = g;
+            }
+        }
+    }
+    choice.candidates = r.timed;
+    choice.objective_ms = best;
+    choice.objective_ms_initial = initial;
+    c->tune = choice;
+    c->tune.n_crit = c->prm.n_crit;
+    if (out) *out = c->tune;
+    return finish(TG_OK);
+}
+
+}  // namespace tg

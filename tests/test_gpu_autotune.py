@@ -1,0 +1,55 @@
+"""The autotuner (tg_autotune): it times evaluations of the caller's system over the leaf size and the
+float32 launch shapes, keeps the fastest in the context, changes no counter of the caller's work, and
+leaves the evaluation correct: forces after tuning match the oracle at the chosen leaf size."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1712_10116_gb300 import ics
+
+pytestmark = pytest.mark.gpu
+
+if torch.cuda.is_available():
+    from paper_1712_10116_gb300 import binding as tg
+    DEV = torch.device("cuda:0")
+
+
+def _t(a, dtype=torch.float64):
+    return torch.tensor(np.ascontiguousarray(a), dtype=dtype, device=DEV)
+
+
+def test_defaults_before_tuning():
+    s = tg.Solver(tg.Params(p=6, n_crit=64, precision=tg.TG_PREC_FP32))
+    t = tg.tg_get_tuning(s.ctx)
+    assert t["n_crit"] == 64 and t["p2p_rows"] == 2 and t["m2l_blocks_per_sm"] == 16 and t["candidates"] == 0
+    s.close()
+
+
+@pytest.mark.parametrize("precision", [1, 0])
+def test_autotune_picks_a_candidate_and_stays_correct(precision):
+    n = 1 << 15 if precision == 1 else 6000
+    pos, _, mass = ics.plummer(n, 1001)
+    fast = ics.random_fast_mask(n, 17)
+    prm = tg.Params(p=6 if precision == 1 else 4, theta=0.5, eps=0.01, kernel=0, precision=precision, n_crit=96)
+    s = tg.Solver(prm)
+    P, M, F = _t(pos), _t(mass), _t(fast, torch.uint8)
+    t = s.autotune(P, M, F)
+    assert t["n_crit"] in (48, 64, 80, 96, 112, 128)
+    if precision == 1:
+        assert t["p2p_rows"] in (1, 2, 3) and t["m2l_blocks_per_sm"] in (4, 8, 16, 32)
+        assert t["candidates"] == 1 + 5 + 1 + 2 + 3
+    else:
+        assert t["p2p_rows"] == 2 and t["m2l_blocks_per_sm"] == 16 and t["candidates"] == 6
+    assert 0 < t["objective_ms"] <= 1.25 * t["objective_ms_initial"]
+    assert tg.tg_get_tuning(s.ctx) == t
+    st = s.stats()
+    assert st["evaluations"] == 0 and st["sink_forces"] == 0   # tuning is not counted as work
+    # the tuned context evaluates the system like the oracle at the chosen leaf size
+    acc, _ = s.fmm_forces(P, M, F)
+    a_o, _ = oracle.fmm(pos, mass, oracle.params(p=prm.p, theta=0.5, eps=0.01, n_crit=t["n_crit"]), fast)
+    a = acc.cpu().numpy()
+    nb = np.linalg.norm(a_o, axis=0)
+    r = np.linalg.norm(a - a_o, axis=0) / np.maximum(nb, 0.1 * np.median(nb))
+    assert r.max() < (1e-5 if precision == 1 else 1e-12), r.max()
+    s.close()
