@@ -199,7 +199,8 @@ __global__ void leaf_particles(TreeView t, const Geom *gp, const double *xs, con
     const Geom g = *gp;
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
     const int nwarps = (gridDim.x * blockDim.x) >> 5;
-    for (int c = warp; c < t.ncell; c += nwarps) {
+    const int ncell = t.cells();
+    for (int c = warp; c < ncell; c += nwarps) {
         if (t.nchild[c] != 0) continue;
         const double zx = cell_centre(g, t, c, 0), zy = cell_centre(g, t, c, 1), zz = cell_centre(g, t, c, 2);
         for (int s = t.first[c] + lane; s < t.first[c] + t.count[c]; s += 32) {
@@ -225,7 +226,8 @@ __global__ void leaf_class_partition(TreeView t, const double *xs, const double 
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
     const int nwarps = (gridDim.x * blockDim.x) >> 5;
     const unsigned lt = (1u << lane) - 1u;
-    for (int c = warp; c < t.ncell; c += nwarps) {
+    const int ncell = t.cells();
+    for (int c = warp; c < ncell; c += nwarps) {
         if (t.nchild[c] != 0) continue;
         const int first = t.first[c], count = t.count[c];
         int ns = 0;
@@ -277,7 +279,8 @@ __global__ void __launch_bounds__(128) p2m_leaves(TreeView t, const Geom *gp, co
     const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nwarps = (gridDim.x * blockDim.x) >> 5;
-    for (int c = warp; c < t.ncell; c += nwarps) {
+    const int ncell = t.cells();
+    for (int c = warp; c < ncell; c += nwarps) {
         if (t.nchild[c] != 0) continue;
         const int first = t.first[c], count = t.count[c];
         const double zx = cell_centre(g, t, c, 0), zy = cell_centre(g, t, c, 1), zz = cell_centre(g, t, c, 2);
@@ -385,8 +388,13 @@ constexpr int kM2MThreads = 256;
 
 template <class T>
 __global__ void __launch_bounds__(kM2MThreads) m2m_level(TreeView t, int lb, int le, int p, int nc, int ncp, T *M,
-                                                         double *M01)
+                                                         double *M01, const DevEval *de, int lvl)
 {
+    if (de) {   // level range on the device (batched path); levels past the tree are empty
+        if (lvl + 1 >= de->nlev) return;
+        lb = de->level_begin[lvl];
+        le = de->level_begin[lvl + 1];
+    }
     extern __shared__ __align__(16) unsigned char m2m_smem[];
     T *s_mc = reinterpret_cast<T *>(m2m_smem);   // [8 children][2 classes][ncp]
     __shared__ uint8_t s_lookup[9 * 9 * 9];
@@ -486,8 +494,9 @@ __device__ double inv_fact_beyond_tables(int k)
 }
 
 template <class T>
-__global__ void scale_moments(int ncell, int nc, int ncp, const T *M, const double *M01, T *Ms)
+__global__ void scale_moments(int ncell, int nc, int ncp, const T *M, const double *M01, T *Ms, const int *dncell)
 {
+    ncell = dev_or(dncell, ncell);
     const int64_t total = (int64_t)ncell * ncp;
     for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < total; w += (int64_t)gridDim.x * blockDim.x) {
         const int64_t c = w / ncp;
@@ -622,8 +631,14 @@ constexpr int kM2MWarps = 2;   // warps per block of the L2L level kernel
 
 template <class T>
 __global__ void __launch_bounds__(32 * kM2MWarps) l2l_level(TreeView t, int lb, int le, int p, int nc, int ncp, int ncls,
-                                                            int n_first, T *L)
+                                                            int n_first, T *L, const DevEval *de, int lvl)
 {
+    if (de) {   // level range and classes on the device (batched path)
+        if (lvl >= de->nlev) return;
+        lb = de->level_begin[lvl];
+        le = de->level_begin[lvl + 1];
+        ncls = de->masked ? 2 : 1;
+    }
     extern __shared__ __align__(16) unsigned char l2l_smem[];
     T *s_lp = reinterpret_cast<T *>(l2l_smem) + (size_t)(threadIdx.x >> 5) * 2 * ncp;   // parent's L, this warp
     __shared__ uint8_t s_lookup[9 * 9 * 9];
@@ -699,10 +714,16 @@ __host__ __device__ constexpr int fact_i(int n)
 // L2P at a fixed order P: monomials, coefficients and indices are compile-time after unrolling.
 // POT = false: accelerations only (the potential slot is written as zero).
 template <int P, class T, class T4, bool POT>
-__global__ void l2p_fixed(int n, TreeView t, int log2L, const T4 *__restrict__ pf, const int32_t *__restrict__ leaf_of,
-                          const uint8_t *__restrict__ fs, int masked, int ncp, const T *__restrict__ L, double *acc4)
+__global__ void l2p_fixed(int n, TreeView t, const Geom *__restrict__ gp, const T4 *__restrict__ pf,
+                          const int32_t *__restrict__ leaf_of, const uint8_t *__restrict__ fs, int masked, int ncp,
+                          const T *__restrict__ L, double *acc4, int stride, const DevEval *de)
 {
     constexpr int NC = (P + 1) * (P + 2) * (P + 3) / 6;
+    if (de) {
+        n = de->n;
+        masked = de->masked;
+    }
+    const int log2L = gp->log2L;
     for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
         const T4 r = pf[s];
         const int c = leaf_of[s];
@@ -735,9 +756,9 @@ __global__ void l2p_fixed(int n, TreeView t, int log2L, const T4 *__restrict__ p
         }
         const T is2 = inv_s * inv_s;
         acc4[s] = to_double(-gx * is2);
-        acc4[(size_t)n + s] = to_double(-gy * is2);
-        acc4[2 * (size_t)n + s] = to_double(-gz * is2);
-        acc4[3 * (size_t)n + s] = to_double(phi * inv_s);
+        acc4[(size_t)stride + s] = to_double(-gy * is2);
+        acc4[2 * (size_t)stride + s] = to_double(-gz * is2);
+        acc4[3 * (size_t)stride + s] = to_double(phi * inv_s);
     }
 }
 
@@ -782,14 +803,17 @@ __global__ void l2p_particles(int n, TreeView t, int log2L, const T4 *pf, const 
 }
 
 // ------------------------------------------------------------------ scatter back to input order
-__global__ void scatter_out(int n, const uint32_t *perm, const double *acc4, double *acc, int64_t stride, double *pot)
+// acc4 holds four arrays of length stride4 (the evaluation's n in the plain path)
+__global__ void scatter_out(int n, const uint32_t *perm, const double *acc4, double *acc, int64_t stride, double *pot,
+                            const int *dn, int64_t stride4)
 {
+    n = dev_or(dn, n);
     for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
         const uint32_t q = perm[s];
         acc[q] = acc4[s];
-        acc[stride + q] = acc4[(size_t)n + s];
-        acc[2 * stride + q] = acc4[2 * (size_t)n + s];
-        if (pot) pot[q] = acc4[3 * (size_t)n + s];
+        acc[stride + q] = acc4[(size_t)stride4 + s];
+        acc[2 * stride + q] = acc4[2 * (size_t)stride4 + s];
+        if (pot) pot[q] = acc4[3 * (size_t)stride4 + s];
     }
 }
 
@@ -1059,11 +1083,11 @@ static tg_status eval_typed(tg_ctx *c, int n, int ncell, const TreeView &t, cons
         }
         ProfScope ps_(c, TG_K_UP);
         m2m_level<T><<<std::min(le - lb, c->num_sms * 8), kM2MThreads, 8 * 2 * ncp * sizeof(T), c->stream>>>(
-            t, lb, le, p, nc, ncp, M, M01);
+            t, lb, le, p, nc, ncp, M, M01, nullptr, 0);
     }
     {
         ProfScope ps_(c, TG_K_UP);
-        scale_moments<T><<<grid_for((int64_t)ncell * ncp, 256), 256, 0, c->stream>>>(ncell, nc, ncp, M, M01, Ms);
+        scale_moments<T><<<grid_for((int64_t)ncell * ncp, 256), 256, 0, c->stream>>>(ncell, nc, ncp, M, M01, Ms, nullptr);
     }
     cudaMemsetAsync(L, 0, sizeof(T) * (size_t)ncell * 2 * ncp, c->stream);
     const M2LBlock *blocks = static_cast<const M2LBlock *>(c->buf[B_M2L].p);
@@ -1078,7 +1102,7 @@ static tg_status eval_typed(tg_ctx *c, int n, int ncell, const TreeView &t, cons
         ProfScope ps_(c, TG_K_DOWN);
         l2l_level<T><<<grid_for((int64_t)(le - lb) * 32, 32 * kM2MWarps), 32 * kM2MWarps,
                        kM2MWarps * 2 * ncp * sizeof(T), c->stream>>>(t, lb, le, p, nc, ncp, ncls,
-                                                                     want_pot ? 0 : 1, L);
+                                                                     want_pot ? 0 : 1, L, nullptr, 0);
     }
     if (high) {
         if ((st = launch_l2p_hi<T, T4>(c, n, t, pf, leaf_of, fs, masked, p, ncp, L, acc4))) return st;
@@ -1087,8 +1111,8 @@ static tg_status eval_typed(tg_ctx *c, int n, int ncell, const TreeView &t, cons
         const int g = grid_for(n, 128), mk = masked ? 1 : 0;
 #define TG_L2P(PP)                                                                                                 \
     case PP:                                                                                                       \
-        if (want_pot) l2p_fixed<PP, T, T4, true><<<g, 128, 0, c->stream>>>(n, t, c->walk_log2L, pf, leaf_of, fs, mk, ncp, L, acc4); \
-        else l2p_fixed<PP, T, T4, false><<<g, 128, 0, c->stream>>>(n, t, c->walk_log2L, pf, leaf_of, fs, mk, ncp, L, acc4); \
+        if (want_pot) l2p_fixed<PP, T, T4, true><<<g, 128, 0, c->stream>>>(n, t, d_geom, pf, leaf_of, fs, mk, ncp, L, acc4, n, nullptr); \
+        else l2p_fixed<PP, T, T4, false><<<g, 128, 0, c->stream>>>(n, t, d_geom, pf, leaf_of, fs, mk, ncp, L, acc4, n, nullptr); \
         break;
         switch (p) {
             TG_L2P(4)
@@ -1136,7 +1160,7 @@ tg_status fmm_eval(tg_ctx *c, int n, const double *pos, int64_t stride, const in
     const double *acc4 = static_cast<const double *>(c->buf[B_ACC].p);
     {
         ProfScope ps_(c, TG_K_DOWN);
-        scatter_out<<<grid_for(n, 256), 256, 0, c->stream>>>(n, perm, acc4, acc, out_stride, pot);
+        scatter_out<<<grid_for(n, 256), 256, 0, c->stream>>>(n, perm, acc4, acc, out_stride, pot, nullptr, n);
     }
     c->stats.evaluations += 1;
     c->stats.sink_forces += n;

@@ -20,17 +20,20 @@ static tg_status m2l_f32_harmonic(tg_ctx *c, const TreeView &t, const M2LBlock *
     if ((st = ensure_t(c, B_MOMH, (size_t)rows * ncpr, &Mr)) || (st = ensure_t(c, B_LOCH, (size_t)rows * ncpr, &Lr)))
         return st;
     ProfScope ps_(c, TG_K_M2L);
-    m2l_reduce_moments_h<P><<<grid_for(rows, 128), 128, 0, c->stream>>>(rows, Ms, ncp, Mr, ncpr);
+    m2l_reduce_moments_h<P><<<grid_for(rows, 128), 128, 0, c->stream>>>(rows, Ms, ncp, Mr, ncpr, nullptr);
     cudaMemsetAsync(Lr, 0, sizeof(float) * (size_t)rows * ncpr, c->stream);
     using G = M2LHarm<P>;
+#define TG_M2L_H(MK, PT) \
+    m2l_blocks_f32<G, MK, PT><<<grid, 128, 0, c->stream>>>(t, blocks, nblocks, Mr, Lr, ncpr, 0.f, 0, nullptr, nullptr, nullptr, 0.0)
     if (masked) {
-        if (pot) m2l_blocks_f32<G, true, true><<<grid, 128, 0, c->stream>>>(t, blocks, nblocks, Mr, Lr, ncpr, 0.f, 0);
-        else m2l_blocks_f32<G, true, false><<<grid, 128, 0, c->stream>>>(t, blocks, nblocks, Mr, Lr, ncpr, 0.f, 0);
+        if (pot) TG_M2L_H(true, true);
+        else TG_M2L_H(true, false);
     } else {
-        if (pot) m2l_blocks_f32<G, false, true><<<grid, 128, 0, c->stream>>>(t, blocks, nblocks, Mr, Lr, ncpr, 0.f, 0);
-        else m2l_blocks_f32<G, false, false><<<grid, 128, 0, c->stream>>>(t, blocks, nblocks, Mr, Lr, ncpr, 0.f, 0);
+        if (pot) TG_M2L_H(false, true);
+        else TG_M2L_H(false, false);
     }
-    m2l_complete_locals_h<P><<<grid_for(rows, 128), 128, 0, c->stream>>>(rows, Lr, ncpr, L, ncp);
+#undef TG_M2L_H
+    m2l_complete_locals_h<P><<<grid_for(rows, 128), 128, 0, c->stream>>>(rows, Lr, ncpr, L, ncp, nullptr);
     return cuda_check(c, cudaGetLastError(), "m2l launch");
 }
 
@@ -53,7 +56,7 @@ tg_status launch_m2l_f32(tg_ctx *c, const TreeView &t, const M2LBlock *blocks, i
         }
     }
     ProfScope ps_(c, TG_K_M2L);
-#define TG_M2L_F32_(PP, MK, PT) m2l_blocks_f32<M2LFull<PP>, MK, PT><<<grid, 128, 0, c->stream>>>(t, blocks, nblocks, Ms, L, ncp, eoL, plummer)
+#define TG_M2L_F32_(PP, MK, PT) m2l_blocks_f32<M2LFull<PP>, MK, PT><<<grid, 128, 0, c->stream>>>(t, blocks, nblocks, Ms, L, ncp, eoL, plummer, nullptr, nullptr, nullptr, 0.0)
 #define TG_M2L_F32(PP)                                                                                            \
     case PP:                                                                                                      \
         if (masked) { if (pot) TG_M2L_F32_(PP, true, true); else TG_M2L_F32_(PP, true, false); }                   \

@@ -75,8 +75,10 @@ __host__ __device__ constexpr int order_in(bool harmonic, int k)
 
 // per cell and class: fold the moments onto j_z <= 1 (pads zeroed)
 template <int P>
-__global__ void m2l_reduce_moments_h(int64_t nrows, const float *__restrict__ Ms, int ncp, float *__restrict__ Mr, int ncpr)
+__global__ void m2l_reduce_moments_h(int64_t nrows, const float *__restrict__ Ms, int ncp, float *__restrict__ Mr, int ncpr,
+                                     const int *drows)
 {
+    if (drows) nrows = *drows;
     for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < nrows; w += (int64_t)gridDim.x * blockDim.x) {
         M2LGenH<P>::reduce_moments(Ms + w * ncp, Mr + w * ncpr);
         for (int k = M2LGenH<P>::NC; k < ncpr; ++k) Mr[w * ncpr + k] = 0.f;
@@ -85,8 +87,10 @@ __global__ void m2l_reduce_moments_h(int64_t nrows, const float *__restrict__ Ms
 
 // per cell and class: the full local expansion from its n_z <= 1 coefficients (pads zeroed)
 template <int P>
-__global__ void m2l_complete_locals_h(int64_t nrows, const float *__restrict__ Lr, int ncpr, float *__restrict__ L, int ncp)
+__global__ void m2l_complete_locals_h(int64_t nrows, const float *__restrict__ Lr, int ncpr, float *__restrict__ L, int ncp,
+                                      const int *drows)
 {
+    if (drows) nrows = *drows;
     constexpr int NC = M2LGen<P>::NC;
     for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < nrows; w += (int64_t)gridDim.x * blockDim.x) {
         M2LGenH<P>::complete_locals(Lr + w * ncpr, L + w * ncp);
@@ -109,11 +113,19 @@ __device__ __forceinline__ void m2l_halve(float (&v)[NP], int lane, int d)
 
 // POT = false: accelerations only, L^0 is left at zero (see the generated *_forces contractions).
 // G: M2LFull<P> or M2LHarm<P>; Ms and L hold that set's coefficients with row stride ncp.
+// Batched path (dnb non-null): the block count, the class count and the root cube come from the
+// device; the launch for the other class count returns at once.
 template <class G, bool MASKED, bool POT>
 __global__ void __launch_bounds__(128) m2l_blocks_f32(TreeView t, const M2LBlock *__restrict__ blocks, int64_t nblocks,
                                                       const float *__restrict__ Ms, float *L, int ncp, float eps_over_L,
-                                                      int plummer)
+                                                      int plummer, const unsigned long long *dnb, const DevEval *de,
+                                                      const Geom *gp, double eps)
 {
+    if (dnb) {
+        if ((de->masked != 0) != MASKED) return;
+        nblocks = (int64_t)*dnb;
+        if (plummer) eps_over_L = (float)ldexp(eps, -gp->log2L);
+    }
     using S = M2LScatter<G::NC>;
     constexpr int NC = S::NC, RL = S::RL, CL = S::CL, NP = S::NP, ND = G::ND;
     const int lane = threadIdx.x & 31;

@@ -79,7 +79,7 @@ cudaError_t scan_with_scratch(cudaStream_t st, const uint32_t *in, uint32_t *out
     while (depth < 8) {
         const int nt = (cn + kScanTileItems - 1) / kScanTileItems;
         lv[depth] = {cout, cn, nt, cursor, cursor + nt};
-        scan_tiles<<<nt, kScanThreads, 0, st>>>(cin, cout, cursor, cn);
+        scan_tiles<<<nt, kScanThreads, 0, st>>>(cin, cout, cursor, cn, nullptr);
         ++depth;
         if (nt == 1) {
             complete = true;
@@ -91,7 +91,7 @@ cudaError_t scan_with_scratch(cudaStream_t st, const uint32_t *in, uint32_t *out
         cursor += 2 * nt + 2;
     }
     if (!complete) return cudaErrorInvalidValue;   // excluded by the static_assert on scan_levels
-    for (int d = depth - 2; d >= 0; --d) scan_add<<<lv[d].ntiles, kScanThreads, 0, st>>>(lv[d].out, lv[d].pre, lv[d].n);
+    for (int d = depth - 2; d >= 0; --d) scan_add<<<lv[d].ntiles, kScanThreads, 0, st>>>(lv[d].out, lv[d].pre, lv[d].n, nullptr);
     return cudaGetLastError();
 }
 
@@ -128,17 +128,17 @@ extern "C" tg_status tg_morton_sort_noalloc(int64_t n, const double *pos, uint64
     const int ni = (int)n;
     // every scratch word used below is written before it is read, so nothing needs clearing
     const int nb = grid_for(n, 256, kMaxBboxBlocks);
-    bbox_partial<<<nb, 256, 0, s>>>(pos, n, nullptr, ni, partial);
-    bbox_final<<<1, 32, 0, s>>>(partial, nb, ni, geom);
-    morton_keys<<<grid_for(n, 256), 256, 0, s>>>(pos, n, nullptr, ni, geom, k0, v0);
+    bbox_partial<<<nb, 256, 0, s>>>(pos, n, nullptr, ni, partial, nullptr);
+    bbox_final<<<1, 32, 0, s>>>(partial, nb, ni, geom, nullptr);
+    morton_keys<<<grid_for(n, 256), 256, 0, s>>>(pos, n, nullptr, ni, geom, k0, v0, nullptr);
     const int nblocks = (ni + kSortTileItems - 1) / kSortTileItems;
     uint64_t *kin = k0, *kout = k1;
     uint32_t *vin = v0, *vout = v1;
     for (int pass = 0; pass < kSortPasses; ++pass) {
         const int shift = pass * kSortBits;
-        radix_hist<<<nblocks, 256, 0, s>>>(kin, ni, shift, hist, nblocks);
+        radix_hist<<<nblocks, 256, 0, s>>>(kin, ni, shift, hist, nblocks, nullptr);
         if (scan_with_scratch(s, hist, hist, kSortBins * nblocks, scan) != cudaSuccess) return TG_ERR_CUDA;
-        radix_scatter<<<nblocks, 256, 0, s>>>(kin, vin, kout, vout, hist, ni, shift, nblocks);
+        radix_scatter<<<nblocks, 256, 0, s>>>(kin, vin, kout, vout, hist, ni, shift, nblocks, nullptr);
         std::swap(kin, kout);
         std::swap(vin, vout);
     }

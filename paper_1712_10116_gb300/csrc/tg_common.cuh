@@ -43,6 +43,23 @@ struct Geom {
     int pad;
 };
 
+// Sizes of one evaluation kept in device memory, for launches whose sizes the host does not read
+// (the batched HOLD step: every evaluation runs inside one CUDA graph).  The plain path passes
+// nullptr to the kernels and host values instead.
+struct DevEval {
+    int n;                  // particles of the evaluation
+    int masked;             // kick pair with a fast set (two moment classes)
+    int sort_blocks;        // radix-sort tiles: ceil(n / kSortTileItems)
+    int hist_items;         // digit histogram entries: kSortBins * sort_blocks
+    int ncell;              // cells of the tree
+    int nlev;               // levels of the tree
+    int lvl_m;              // cells of the level being split (octree build)
+    int rows;               // 2 * ncell (expansion rows, both classes)
+    uint32_t lvl_total;     // children emitted by the level being split (scan total)
+    uint32_t overflow;      // bit 0: cells, bit 1: levels, bit 2: walk lists; the step must be redone
+    int level_begin[kMaxLevel + 3];   // first cell of each level; [nlev] = ncell
+};
+
 // Octree of one evaluation (structure of arrays, cells in BFS order).
 struct TreeView {
     int32_t n;           // particles
@@ -53,7 +70,12 @@ struct TreeView {
     const uint8_t *nchild;
     const double *rad = nullptr;   // enclosing radii (TG_MAC_SPHERE), float64 and float32 copies
     const float *radf = nullptr;
+    const int *d_ncell = nullptr;  // device cell count (batched path); ncell is then a capacity
+    __device__ __forceinline__ int cells() const { return d_ncell ? *d_ncell : ncell; }
 };
+
+// device count if given, else the host value
+__device__ __forceinline__ int dev_or(const int *p, int v) { return p ? *p : v; }
 
 }  // namespace tg
 
@@ -144,14 +166,17 @@ struct M2LBlock {
 
 // ---- tree.cu
 // Root cube of the n particles pos[q] (q < n, gathered through sub when non-null) -> geom.
-tg_status root_cube(tg_ctx *c, int n, const double *pos, int64_t stride, const int64_t *sub, Geom *d_geom);
+tg_status root_cube(tg_ctx *c, int n, const double *pos, int64_t stride, const int64_t *sub, Geom *d_geom,
+                    const int *dn = nullptr);
 // Keys, stable radix sort and gather into sorted order.  Returns device pointers in the ctx
 // slots: B_KEYS0 (sorted keys), B_VALS0 (perm: sorted -> input index q), B_XS.. B_FS.
 tg_status keys_sort_gather(tg_ctx *c, int n, const double *pos, int64_t stride, const int64_t *sub,
-                           const double *mass, const uint8_t *fast, const Geom *d_geom);
+                           const double *mass, const uint8_t *fast, const Geom *d_geom, const DevEval *de = nullptr);
 // Octree from the sorted keys; fills the cell slots and c->level_begin.  Returns ncell.
 tg_status build_octree(tg_ctx *c, int n, int *ncell_out);
 TreeView tree_view(tg_ctx *c, int n, int ncell);
+// The same octree with its sizes on the device (de): `cap` cells at most, `levels` levels issued.
+tg_status build_octree_dev(tg_ctx *c, DevEval *de, int cap, int levels);
 
 // Expansion kernels for orders above the fixed tables (TG_PMAX < p <= kPHigh), high_order.cu.
 constexpr int kPHigh = 20;
@@ -179,7 +204,8 @@ tg_status check_finite(tg_ctx *c, int64_t n, const double *pos, int64_t stride, 
 tg_status injected_alloc_failure(tg_ctx *c, size_t bytes, int slot);
 
 // Device-wide exclusive scan of uint32 (in place allowed); optional total to a device word.
-tg_status exclusive_scan_u32(tg_ctx *c, const uint32_t *in, uint32_t *out, int n, uint32_t *d_total);
+tg_status exclusive_scan_u32(tg_ctx *c, const uint32_t *in, uint32_t *out, int n, uint32_t *d_total,
+                             const int *dn = nullptr);
 
 // ---- m2l.cu: mutual M2L of the walk's blocks into L (normalised expansions).  pot = false: the
 // float32 kernels leave out the potential term L^0.
@@ -201,15 +227,17 @@ constexpr int kSortBins = 1 << kSortBits;
 constexpr int kSortPasses = (63 + kSortBits - 1) / kSortBits;
 constexpr int kScanThreads = 512;        // threads per scan block
 constexpr int kScanTileItems = 2048;     // items per scan block (kScanThreads x 4)
-__global__ void scan_tiles(const uint32_t *in, uint32_t *out, uint32_t *tile_sums, int n);
-__global__ void scan_add(uint32_t *out, const uint32_t *tile_pre, int n);
-__global__ void bbox_partial(const double *pos, int64_t stride, const int64_t *sub, int n, double *partial);
-__global__ void bbox_final(const double *partial, int nparts, int n, Geom *g);
+// (optional device sizes: dn / de, nullptr for host sizes)
+__global__ void scan_tiles(const uint32_t *in, uint32_t *out, uint32_t *tile_sums, int n, const int *dn);
+__global__ void scan_add(uint32_t *out, const uint32_t *tile_pre, int n, const int *dn);
+__global__ void bbox_partial(const double *pos, int64_t stride, const int64_t *sub, int n, double *partial, const int *dn);
+__global__ void bbox_final(const double *partial, int nparts, int n, Geom *g, const int *dn);
 __global__ void morton_keys(const double *pos, int64_t stride, const int64_t *sub, int n, const Geom *g,
-                            uint64_t *keys, uint32_t *vals);
-__global__ void radix_hist(const uint64_t *keys, int n, int shift, uint32_t *hist, int nblocks);
+                            uint64_t *keys, uint32_t *vals, const int *dn);
+__global__ void radix_hist(const uint64_t *keys, int n, int shift, uint32_t *hist, int nblocks, const DevEval *de);
 __global__ void radix_scatter(const uint64_t *keys_in, const uint32_t *vals_in, uint64_t *keys_out,
-                              uint32_t *vals_out, const uint32_t *offsets, int n, int shift, int nblocks);
+                              uint32_t *vals_out, const uint32_t *offsets, int n, int shift, int nblocks,
+                              const DevEval *de);
 
 // ---- fmm.cu
 // Full FMM evaluation on a (sub)set of particles.  Outputs are in input order q:

@@ -187,8 +187,9 @@ __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t *t
     return base + x - v;
 }
 
-__global__ void scan_tiles(const uint32_t *in, uint32_t *out, uint32_t *tile_sums, int n)
+__global__ void scan_tiles(const uint32_t *in, uint32_t *out, uint32_t *tile_sums, int n, const int *dn)
 {
+    n = dev_or(dn, n);
     const int64_t base = (int64_t)blockIdx.x * kScanTile + threadIdx.x * kScanItems;
     uint32_t v[kScanItems];
     uint32_t s = 0;
@@ -207,8 +208,9 @@ __global__ void scan_tiles(const uint32_t *in, uint32_t *out, uint32_t *tile_sum
     if (threadIdx.x == 0) tile_sums[blockIdx.x] = tot;
 }
 
-__global__ void scan_add(uint32_t *out, const uint32_t *tile_pre, int n)
+__global__ void scan_add(uint32_t *out, const uint32_t *tile_pre, int n, const int *dn)
 {
+    n = dev_or(dn, n);
     const int64_t base = (int64_t)blockIdx.x * kScanTile + threadIdx.x * kScanItems;
     const uint32_t add = tile_pre[blockIdx.x];
 #pragma unroll
@@ -217,8 +219,10 @@ __global__ void scan_add(uint32_t *out, const uint32_t *tile_pre, int n)
 }
 
 // Exclusive scan of n uint32 values (out may alias in).  The total is written to d_total
-// (device word) when it is not null.  Recursive over tile sums.
-tg_status exclusive_scan_u32(tg_ctx *c, const uint32_t *in, uint32_t *out, int n, uint32_t *d_total)
+// (device word) when it is not null.  Recursive over tile sums.  With dn (a device count) the first
+// level scans dn[0] <= n values; the launches are sized for n, and the tiles past dn[0] hand up
+// zero sums, so the upper levels need no device count.
+tg_status exclusive_scan_u32(tg_ctx *c, const uint32_t *in, uint32_t *out, int n, uint32_t *d_total, const int *dn)
 {
     if (n <= 0) {
         if (d_total) cudaMemsetAsync(d_total, 0, sizeof(uint32_t), c->stream);
@@ -246,7 +250,7 @@ tg_status exclusive_scan_u32(tg_ctx *c, const uint32_t *in, uint32_t *out, int n
         lv[depth] = {cout, cn, nt, cursor, cursor + nt};
         {
             ProfScope ps_(c, TG_K_OTHER);
-            scan_tiles<<<nt, kScanThreads, 0, c->stream>>>(cin, cout, cursor, cn);
+            scan_tiles<<<nt, kScanThreads, 0, c->stream>>>(cin, cout, cursor, cn, depth == 0 ? dn : nullptr);
         }
         ++depth;
         if (nt == 1) break;
@@ -258,7 +262,7 @@ tg_status exclusive_scan_u32(tg_ctx *c, const uint32_t *in, uint32_t *out, int n
     for (int d = depth - 2; d >= 0; --d)
         {
             ProfScope ps_(c, TG_K_OTHER);
-            scan_add<<<lv[d].ntiles, kScanThreads, 0, c->stream>>>(lv[d].out, lv[d].pre, lv[d].n);
+            scan_add<<<lv[d].ntiles, kScanThreads, 0, c->stream>>>(lv[d].out, lv[d].pre, lv[d].n, d == 0 ? dn : nullptr);
         }
     if (d_total)
         cudaMemcpyAsync(d_total, lv[depth - 1].sums, sizeof(uint32_t), cudaMemcpyDeviceToDevice, c->stream);
@@ -274,8 +278,9 @@ __device__ __forceinline__ double pos_at(const double *pos, int64_t stride, cons
     return pos[axis * stride + i];
 }
 
-__global__ void bbox_partial(const double *pos, int64_t stride, const int64_t *sub, int n, double *partial)
+__global__ void bbox_partial(const double *pos, int64_t stride, const int64_t *sub, int n, double *partial, const int *dn)
 {
+    n = dev_or(dn, n);
     double mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY};
     for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x) {
 #pragma unroll
@@ -311,8 +316,9 @@ __global__ void bbox_partial(const double *pos, int64_t stride, const int64_t *s
 
 // Root cube from the bounding box: L = smallest power of two >= extent * (1 + 2^-20) (1 if the
 // extent is 0), lo = floor(min / h) * h with h = L / 2^21.
-__global__ void bbox_final(const double *partial, int nparts, int n, Geom *g)
+__global__ void bbox_final(const double *partial, int nparts, int n, Geom *g, const int *dn)
 {
+    n = dev_or(dn, n);
     // one warp: lanes stride over the partial results, then a shuffle reduction
     double mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY};
     for (int b = threadIdx.x; b < nparts; b += 32)
@@ -359,7 +365,8 @@ __global__ void bbox_final(const double *partial, int nparts, int n, Geom *g)
     g->inv_h = ldexp(1.0, kMaxLevel - log2L);
 }
 
-tg_status root_cube(tg_ctx *c, int n, const double *pos, int64_t stride, const int64_t *sub, Geom *d_geom)
+tg_status root_cube(tg_ctx *c, int n, const double *pos, int64_t stride, const int64_t *sub, Geom *d_geom,
+                    const int *dn)
 {
     double *partial = nullptr;
     int nb = grid_for(n, kRedThreads, 2 * 152);
@@ -367,11 +374,11 @@ tg_status root_cube(tg_ctx *c, int n, const double *pos, int64_t stride, const i
     if (st) return st;
     {
         ProfScope ps_(c, TG_K_TREE);
-        bbox_partial<<<nb, kRedThreads, 0, c->stream>>>(pos, stride, sub, n, partial);
+        bbox_partial<<<nb, kRedThreads, 0, c->stream>>>(pos, stride, sub, n, partial, dn);
     }
     {
         ProfScope ps_(c, TG_K_TREE);
-        bbox_final<<<1, 32, 0, c->stream>>>(partial, nb, n, d_geom);
+        bbox_final<<<1, 32, 0, c->stream>>>(partial, nb, n, d_geom, dn);
     }
     return cuda_check(c, cudaGetLastError(), "root cube");
 }
@@ -419,8 +426,9 @@ __device__ __forceinline__ uint64_t cell_coord(double x, double lo, double inv_h
 }
 
 __global__ void morton_keys(const double *pos, int64_t stride, const int64_t *sub, int n, const Geom *g,
-                            uint64_t *keys, uint32_t *vals)
+                            uint64_t *keys, uint32_t *vals, const int *dn)
 {
+    n = dev_or(dn, n);
     const double lo0 = g->lo[0], lo1 = g->lo[1], lo2 = g->lo[2], inv_h = g->inv_h;
     for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x) {
         uint64_t cx = cell_coord(pos_at(pos, stride, sub, q, 0), lo0, inv_h);
@@ -440,8 +448,13 @@ constexpr int kSortTile = kSortThreads * kSortItems;
 static_assert(kSortBins == 2 * kSortThreads, "the digit scan gives two digits to each thread");
 static_assert(kSortTile == kSortTileItems, "tile size shared with the allocation-free sort");
 
-__global__ void radix_hist(const uint64_t *keys, int n, int shift, uint32_t *hist, int nblocks)
+__global__ void radix_hist(const uint64_t *keys, int n, int shift, uint32_t *hist, int nblocks, const DevEval *de)
 {
+    if (de) {
+        n = de->n;
+        nblocks = de->sort_blocks;
+        if ((int)blockIdx.x >= nblocks) return;   // whole block
+    }
     __shared__ uint32_t h[kSortBins];
     for (int d = threadIdx.x; d < kSortBins; d += blockDim.x) h[d] = 0;
     __syncthreads();
@@ -461,8 +474,14 @@ __global__ void radix_hist(const uint64_t *keys, int n, int shift, uint32_t *his
 // shared memory in digit order and written out by consecutive threads, so that each digit's run of
 // the tile goes to global memory as one contiguous stretch.
 __global__ void radix_scatter(const uint64_t *keys_in, const uint32_t *vals_in, uint64_t *keys_out,
-                              uint32_t *vals_out, const uint32_t *offsets, int n, int shift, int nblocks)
+                              uint32_t *vals_out, const uint32_t *offsets, int n, int shift, int nblocks,
+                              const DevEval *de)
 {
+    if (de) {
+        n = de->n;
+        nblocks = de->sort_blocks;
+        if ((int)blockIdx.x >= nblocks) return;   // whole block
+    }
     __shared__ uint32_t wcount[8][kSortBins];
     __shared__ uint32_t dstart[kSortBins];
     __shared__ uint32_t wsum[8];
@@ -542,8 +561,9 @@ __global__ void radix_scatter(const uint64_t *keys_in, const uint32_t *vals_in, 
 
 __global__ void gather_sorted(const uint32_t *perm, const double *pos, int64_t stride, const int64_t *sub,
                               const double *mass, const uint8_t *fast, int n, double *xs, double *ys, double *zs,
-                              double *ms, uint8_t *fs)
+                              double *ms, uint8_t *fs, const int *dn)
 {
+    n = dev_or(dn, n);
     for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < n; s += (int64_t)gridDim.x * blockDim.x) {
         uint32_t q = perm[s];
         int64_t i = sub ? sub[q] : (int64_t)q;
@@ -556,8 +576,10 @@ __global__ void gather_sorted(const uint32_t *perm, const double *pos, int64_t s
 }
 
 tg_status keys_sort_gather(tg_ctx *c, int n, const double *pos, int64_t stride, const int64_t *sub,
-                           const double *mass, const uint8_t *fast, const Geom *d_geom)
+                           const double *mass, const uint8_t *fast, const Geom *d_geom, const DevEval *de)
 {
+    // with de the sizes live on the device; n is then the capacity the launches are sized for
+    const int *dn = de ? &de->n : nullptr;
     uint64_t *k0, *k1;
     uint32_t *v0, *v1, *hist;
     const int nblocks = (n + kSortTile - 1) / kSortTile;
@@ -568,7 +590,7 @@ tg_status keys_sort_gather(tg_ctx *c, int n, const double *pos, int64_t stride, 
         return st;
     {
         ProfScope ps_(c, TG_K_TREE);
-        morton_keys<<<grid_for(n, 256), 256, 0, c->stream>>>(pos, stride, sub, n, d_geom, k0, v0);
+        morton_keys<<<grid_for(n, 256), 256, 0, c->stream>>>(pos, stride, sub, n, d_geom, k0, v0, dn);
     }
     uint64_t *kin = k0, *kout = k1;
     uint32_t *vin = v0, *vout = v1;
@@ -576,12 +598,13 @@ tg_status keys_sort_gather(tg_ctx *c, int n, const double *pos, int64_t stride, 
         const int shift = pass * kSortBits;
         {
             ProfScope ps_(c, TG_K_TREE);
-            radix_hist<<<nblocks, kSortThreads, 0, c->stream>>>(kin, n, shift, hist, nblocks);
+            radix_hist<<<nblocks, kSortThreads, 0, c->stream>>>(kin, n, shift, hist, nblocks, de);
         }
-        if ((st = exclusive_scan_u32(c, hist, hist, kSortBins * nblocks, nullptr))) return st;
+        if ((st = exclusive_scan_u32(c, hist, hist, kSortBins * nblocks, nullptr, de ? &de->hist_items : nullptr)))
+            return st;
         {
             ProfScope ps_(c, TG_K_TREE);
-            radix_scatter<<<nblocks, kSortThreads, 0, c->stream>>>(kin, vin, kout, vout, hist, n, shift, nblocks);
+            radix_scatter<<<nblocks, kSortThreads, 0, c->stream>>>(kin, vin, kout, vout, hist, n, shift, nblocks, de);
         }
         std::swap(kin, kout);
         std::swap(vin, vout);
@@ -599,7 +622,8 @@ tg_status keys_sort_gather(tg_ctx *c, int n, const double *pos, int64_t stride, 
         return st;
     {
         ProfScope ps_(c, TG_K_TREE);
-        gather_sorted<<<grid_for(n, 256), 256, 0, c->stream>>>(v0, pos, stride, sub, mass, fast, n, xs, ys, zs, ms, fs);
+        gather_sorted<<<grid_for(n, 256), 256, 0, c->stream>>>(v0, pos, stride, sub, mass, fast, n, xs, ys, zs, ms, fs,
+                                                               dn);
     }
     return cuda_check(c, cudaGetLastError(), "keys/sort/gather");
 }
@@ -628,12 +652,12 @@ __device__ __forceinline__ int child_bound(const uint64_t *keys, int s, int e, i
     return digit_lower_bound(keys, s, e, l, lane);
 }
 
-__global__ void oct_count(const uint64_t *keys, int lb, int le, const uint8_t *level, const int32_t *first,
-                          const int32_t *count, int n_crit, int max_level, uint32_t *cnt)
+// Children of cell cidx (the t-th cell of its level): count (cnt[t]) and emission at le + off[t].
+// The whole warp handles one cell.
+__device__ __forceinline__ void oct_count_cell(const uint64_t *keys, int cidx, int t, const uint8_t *level,
+                                               const int32_t *first, const int32_t *count, int n_crit, int max_level,
+                                               uint32_t *cnt, int lane)
 {
-    const int t = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
-    const int cidx = lb + t;
-    if (cidx >= le) return;   // whole warp
     if (count[cidx] <= n_crit || level[cidx] >= max_level) {
         if (lane == 0) cnt[t] = 0;
         return;
@@ -644,13 +668,12 @@ __global__ void oct_count(const uint64_t *keys, int lb, int le, const uint8_t *l
     const unsigned m = __ballot_sync(0xffffffffu, lane < 8 && bn > b);
     if (lane == 0) cnt[t] = __popc(m);
 }
-__global__ void oct_emit(const uint64_t *keys, int lb, int le, uint8_t *level, uint32_t *cx, uint32_t *cy,
-                         uint32_t *cz, int32_t *first, int32_t *count, int32_t *child_first, int32_t *parent,
-                         uint8_t *nchild, const uint32_t *off, const uint32_t *cnt)
+
+__device__ __forceinline__ void oct_emit_cell(const uint64_t *keys, int le, int cidx, int t, uint8_t *level,
+                                              uint32_t *cx, uint32_t *cy, uint32_t *cz, int32_t *first, int32_t *count,
+                                              int32_t *child_first, int32_t *parent, uint8_t *nchild,
+                                              const uint32_t *off, const uint32_t *cnt, int lane)
 {
-    const int t = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
-    const int cidx = lb + t;
-    if (cidx >= le) return;   // whole warp
     const int nch = cnt[t];
     if (nch == 0) {
         if (lane == 0) {
@@ -682,6 +705,24 @@ __global__ void oct_emit(const uint64_t *keys, int lb, int le, uint8_t *level, u
         nchild[cidx] = (uint8_t)nch;
         child_first[cidx] = base;
     }
+}
+
+__global__ void oct_count(const uint64_t *keys, int lb, int le, const uint8_t *level, const int32_t *first,
+                          const int32_t *count, int n_crit, int max_level, uint32_t *cnt)
+{
+    const int t = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+    const int cidx = lb + t;
+    if (cidx >= le) return;   // whole warp
+    oct_count_cell(keys, cidx, t, level, first, count, n_crit, max_level, cnt, lane);
+}
+__global__ void oct_emit(const uint64_t *keys, int lb, int le, uint8_t *level, uint32_t *cx, uint32_t *cy,
+                         uint32_t *cz, int32_t *first, int32_t *count, int32_t *child_first, int32_t *parent,
+                         uint8_t *nchild, const uint32_t *off, const uint32_t *cnt)
+{
+    const int t = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+    const int cidx = lb + t;
+    if (cidx >= le) return;   // whole warp
+    oct_emit_cell(keys, le, cidx, t, level, cx, cy, cz, first, count, child_first, parent, nchild, off, cnt, lane);
 }
 __global__ void oct_root(int n, uint8_t *level, uint32_t *cx, uint32_t *cy, uint32_t *cz, int32_t *first,
                          int32_t *count, int32_t *child_first, int32_t *parent, uint8_t *nchild)
@@ -732,7 +773,7 @@ tg_status build_octree(tg_ctx *c, int n, int *ncell_out)
             oct_count<<<(int)(((int64_t)m * 32 + 255) / 256), 256, 0, c->stream>>>(keys, lb, le, level, first, count, c->prm.n_crit,
                                                              c->prm.max_level, cnt);
         }
-        if ((st = exclusive_scan_u32(c, cnt, off, m, d_total))) return st;
+        if ((st = exclusive_scan_u32(c, cnt, off, m, d_total, nullptr))) return st;
         cudaMemcpyAsync(h_total, d_total, sizeof(uint32_t), cudaMemcpyDeviceToHost, c->stream);
         cudaError_t e = stream_sync(c);
         if (e != cudaSuccess) return cuda_check(c, e, "octree level");
@@ -754,6 +795,110 @@ tg_status build_octree(tg_ctx *c, int n, int *ncell_out)
     if (c->level_begin.back() != le) c->level_begin.push_back(le);
     *ncell_out = le;
     return cuda_check(c, cudaGetLastError(), "octree");
+}
+
+// ------------------------------------------------------------------ octree, sizes on the device
+// The batched path builds the same tree level by level, but the level ranges, the cell count and
+// the depth stay on the device (DevEval): launches are sized for the capacity, warps stride over the
+// cells of their level, and levels past the tree's depth find no cells.  A level whose children
+// would pass the cell capacity, or a tree deeper than the levels issued, sets an overflow bit; the
+// step is then redone with larger buffers.
+__global__ void oct_root_dev(DevEval *de, uint8_t *level, uint32_t *cx, uint32_t *cy, uint32_t *cz, int32_t *first,
+                             int32_t *count, int32_t *child_first, int32_t *parent, uint8_t *nchild)
+{
+    level[0] = 0;
+    cx[0] = cy[0] = cz[0] = 0;
+    first[0] = 0;
+    count[0] = de->n;
+    child_first[0] = -1;
+    parent[0] = -1;
+    nchild[0] = 0;
+    de->level_begin[0] = 0;
+    de->level_begin[1] = 1;
+    de->nlev = 1;
+    de->ncell = 1;
+    de->rows = 2;
+    de->lvl_m = 1;
+}
+
+__global__ void oct_count_dev(const uint64_t *keys, const DevEval *de, int lvl, const uint8_t *level,
+                              const int32_t *first, const int32_t *count, int n_crit, int max_level, uint32_t *cnt)
+{
+    if (lvl >= de->nlev) return;
+    const int lb = de->level_begin[lvl], m = de->level_begin[lvl + 1] - lb;
+    const int lane = threadIdx.x & 31, nw = (int)((gridDim.x * blockDim.x) >> 5);
+    for (int t = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5); t < m; t += nw)
+        oct_count_cell(keys, lb + t, t, level, first, count, n_crit, max_level, cnt, lane);
+}
+
+__global__ void oct_emit_dev(const uint64_t *keys, const DevEval *de, int lvl, int cap, uint8_t *level, uint32_t *cx,
+                             uint32_t *cy, uint32_t *cz, int32_t *first, int32_t *count, int32_t *child_first,
+                             int32_t *parent, uint8_t *nchild, const uint32_t *off, const uint32_t *cnt)
+{
+    if (lvl >= de->nlev) return;
+    const int lb = de->level_begin[lvl], le = de->level_begin[lvl + 1], m = le - lb;
+    if ((int64_t)le + de->lvl_total > cap) return;   // over capacity: oct_finish_dev flags it
+    const int lane = threadIdx.x & 31, nw = (int)((gridDim.x * blockDim.x) >> 5);
+    for (int t = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5); t < m; t += nw)
+        oct_emit_cell(keys, le, lb + t, t, level, cx, cy, cz, first, count, child_first, parent, nchild, off, cnt, lane);
+}
+
+__global__ void oct_finish_dev(DevEval *de, int lvl, int cap, int last_issued, int max_level)
+{
+    if (lvl >= de->nlev) {
+        de->lvl_m = 0;
+        return;
+    }
+    const int le = de->level_begin[lvl + 1];
+    int total = (int)de->lvl_total;
+    if ((int64_t)le + total > cap) {
+        de->overflow |= 1u;
+        total = 0;
+    }
+    if (total > 0) {
+        de->level_begin[lvl + 2] = le + total;
+        de->nlev = lvl + 2;
+        de->ncell = le + total;
+        de->rows = 2 * (le + total);
+        if (last_issued && lvl + 1 < max_level) de->overflow |= 2u;   // the tree goes deeper than issued
+    }
+    de->lvl_m = total;
+}
+
+tg_status build_octree_dev(tg_ctx *c, DevEval *de, int cap, int levels)
+{
+    tg_status st;
+    const uint64_t *keys = static_cast<const uint64_t *>(c->buf[B_KEYS0].p);
+    uint8_t *level, *nchild;
+    uint32_t *cx, *cy, *cz, *cnt, *off;
+    int32_t *first, *count, *child_first, *parent;
+    if ((st = ensure_t(c, B_C_LEVEL, cap, &level)) || (st = ensure_t(c, B_C_X, cap, &cx)) ||
+        (st = ensure_t(c, B_C_Y, cap, &cy)) || (st = ensure_t(c, B_C_Z, cap, &cz)) ||
+        (st = ensure_t(c, B_C_FIRST, cap, &first)) || (st = ensure_t(c, B_C_COUNT, cap, &count)) ||
+        (st = ensure_t(c, B_C_CHILD, cap, &child_first)) || (st = ensure_t(c, B_C_PARENT, cap, &parent)) ||
+        (st = ensure_t(c, B_C_NCHILD, cap, &nchild)) || (st = ensure_t(c, B_C_TMP0, cap, &cnt)) ||
+        (st = ensure_t(c, B_C_TMP1, cap, &off)))
+        return st;
+    {
+        ProfScope ps_(c, TG_K_TREE);
+        oct_root_dev<<<1, 1, 0, c->stream>>>(de, level, cx, cy, cz, first, count, child_first, parent, nchild);
+    }
+    const int grid = c->num_sms * 8;
+    for (int lvl = 0; lvl < levels; ++lvl) {
+        {
+            ProfScope ps_(c, TG_K_TREE);
+            oct_count_dev<<<grid, 256, 0, c->stream>>>(keys, de, lvl, level, first, count, c->prm.n_crit,
+                                                       c->prm.max_level, cnt);
+        }
+        if ((st = exclusive_scan_u32(c, cnt, off, cap, &de->lvl_total, &de->lvl_m))) return st;
+        {
+            ProfScope ps_(c, TG_K_TREE);
+            oct_emit_dev<<<grid, 256, 0, c->stream>>>(keys, de, lvl, cap, level, cx, cy, cz, first, count, child_first,
+                                                      parent, nchild, off, cnt);
+            oct_finish_dev<<<1, 1, 0, c->stream>>>(de, lvl, cap, lvl == levels - 1, c->prm.max_level);
+        }
+    }
+    return cuda_check(c, cudaGetLastError(), "octree (device sizes)");
 }
 
 TreeView tree_view(tg_ctx *c, int n, int ncell)

@@ -136,7 +136,10 @@ def test_interaction_lists_regrow_from_tiny_capacities(precision):
     tg.tg_debug_control(s.ctx, tg.TG_DEBUG_LIST_CAPACITY, 1)   # 0.001 list entries per cell
     a, _ = s.fmm_forces(P, M)
     assert s.stats()["list_regrowths"] >= 1
-    scale = torch.linalg.norm(a_ref, dim=0)
+    # float32: two runs of the same evaluation differ in the order of their float atomics, each within the
+    # float32 parity bound of the exact result: compare against max(|a|, 0.1 median |a|) like the parity tests
+    nb = torch.linalg.norm(a_ref, dim=0)
+    scale = nb if precision == "fp64" else torch.maximum(nb, 0.1 * nb.median())
     rel = (torch.linalg.norm(a - a_ref, dim=0) / scale).max().item()
-    assert rel < (1e-13 if precision == "fp64" else 1e-6), rel
+    assert rel < (1e-13 if precision == "fp64" else 1e-5), rel
     s.close()

@@ -172,14 +172,42 @@ class _State:
         self.pos, self.vel, self.rung, self.a_old, self.a_cur = st
 
 
-@pytest.mark.parametrize("precision", [0, 1])
-def test_disk_galaxy_hhs_matches_oracle(disk_oracle_run, precision):
+def test_disk_galaxy_hhs_fp64_matches_oracle(disk_oracle_run):
     (pos, vel, mass), states = disk_oracle_run
-    prm = tg.Params(precision=precision, **DISK_PRM)
-    s = tg.Solver(prm)
+    s = tg.Solver(tg.Params(precision=tg.TG_PREC_FP64, **DISK_PRM))
     P, V, M = _t(pos), _t(vel), _t(mass)
     s.hhs_init(P, V, M)
     for step in range(3):
         s.hhs_step()
-        _compare_hhs(s, P, V, _State(states[step]), DISK_N, f"disk 2^14 prec={precision} step {step}", precision == 1)
+        _compare_hhs(s, P, V, _State(states[step]), DISK_N, f"disk 2^14 fp64 step {step}", False)
     assert s.stats()["max_rung"] >= 6
+
+
+def test_disk_galaxy_hhs_fp32_matches_oracle(disk_oracle_run):
+    # The galaxy's dense centre is collisional on these time scales (t = 0..6 in units where its
+    # crossing time is ~0.1), so two trajectories that start apart by float32 rounding separate
+    # exponentially: after the first rung-0 step they still agree to float32 accuracy, later only
+    # statistically.  The float32 forces are held to their bound on every state of the oracle's
+    # trajectory, kick pairs included.
+    (pos, vel, mass), states = disk_oracle_run
+    prm = tg.Params(precision=tg.TG_PREC_FP32, **DISK_PRM)
+    s = tg.Solver(prm)
+    P, V, M = _t(pos), _t(vel), _t(mass)
+    s.hhs_init(P, V, M)
+    s.hhs_step()
+    _compare_hhs(s, P, V, _State(states[0]), DISK_N, "disk 2^14 fp32 step 0", True)
+    s.hhs_step()
+    s.hhs_step()
+    st = _State(states[2])
+    rung = tg.tg_hhs_state(s.ctx, DISK_N)[0].cpu().numpy()
+    dv = np.abs(V.cpu().numpy() - st.vel).max(axis=0) / np.abs(st.vel).max()
+    print(f"disk 2^14 fp32 after 3 steps: {(rung != st.rung).sum()} particles on another rung, median |dv| / max|v| "
+          f"{np.median(dv):.2e}, {(dv > 1e-4).sum()} beyond 1e-4")
+    assert (rung != st.rung).mean() < 0.01 and np.median(dv) < 1e-6 and (dv > 1e-4).mean() < 0.01
+    ev = tg.Solver(prm)
+    for k, (x, _, r, _, _) in enumerate(states):
+        fast = (r > np.median(r)).astype(np.uint8)
+        for mask in (None, fast):
+            acc, _ = ev.fmm_forces(_t(x), M, None if mask is None else _t(mask, torch.uint8), want_pot=False)
+            a_o, _ = oracle.fmm(x, mass, _oprm(prm), mask)
+            _check_fp32(acc.cpu().numpy(), a_o, f"disk 2^14 state {k} masked={mask is not None}")
