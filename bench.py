@@ -81,6 +81,9 @@ def parse():
                     help="skip the timing of the plain float64 GPU path beside the float32 one")
     ap.add_argument("--cpu-sample", type=int, default=1024)
     ap.add_argument("--n-crit", type=int, default=0, help="leaf size (0: the workload's own)")
+    ap.add_argument("--batched", type=int, default=1, choices=[0, 1],
+                    help="1: HOLD steps as one CUDA graph with a device-side work queue (tg_params.batched); "
+                         "0: the plain host-driven step")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the workload's leaf size and the default launch shapes (no tg_autotune)")
     ap.add_argument("--eval-only", action="store_true",
@@ -107,6 +110,7 @@ def run_params(args, name):
         prm["theta"] = args.theta
     prm["eta_tot"] = args.eta_tot
     prm["mac"] = 1 if args.mac == "sphere" else 0
+    prm["batched"] = int(args.batched) if prm["mac"] == 0 and 4 <= prm["p"] <= 6 else 0
     return prm
 
 
@@ -310,13 +314,27 @@ def run_ours(args):
     step_ms, stats, prof = time_hhs_steps(run, args.steps, args.warmup, stream, flush, 1, clocks, barrier)
     wall = time.perf_counter() - wall0
     d_end = solver.diagnostics()   # the state after the last timed step (one rung-0 step from t = 0)
-    # one extra (untimed) step with every launch timed, for the per-stage breakdown
-    tg.tg_reset_stats(solver.ctx)
-    tg.tg_set_profiling(solver.ctx, 2)
-    run.reset()
-    solver.hhs_step()
-    breakdown = {k: v["ms"] for k, v in tg.tg_get_profile(solver.ctx).items() if k != "_all"}
-    tg.tg_set_profiling(solver.ctx, 0)
+    # Kernel times: a graph hides its launches from per-launch events, so with the batched step they come
+    # from a twin context running the plain host-driven step on the same state with the same tuning (the
+    # same kernels, launched one by one): one step timing the M2L and P2P launches, one timing every launch
+    timing_source = "timed steps"
+    prof_k, stats_k = prof, stats
+    twin = None
+    if rp.get("batched"):
+        twin = HHSRun(tg, tg.Params(precision=prec, **dict(rp, batched=0)), pos0, vel0, mass0, dev, stream)
+        tg.tg_set_tuning(twin.solver.ctx, tg.tg_get_tuning(solver.ctx))
+        _, stats_k, prof_k = time_hhs_steps(twin, 1, 1, stream, flush, 1)
+        timing_source = ("CUDA events around each launch of one untimed plain-path step of the same state, "
+                         "tuning and kernels (the batched step runs them inside one graph)")
+    prof_run = twin if twin else run
+    tg.tg_reset_stats(prof_run.solver.ctx)
+    tg.tg_set_profiling(prof_run.solver.ctx, 2)
+    prof_run.reset()
+    prof_run.solver.hhs_step()
+    breakdown = {k: v["ms"] for k, v in tg.tg_get_profile(prof_run.solver.ctx).items() if k != "_all"}
+    tg.tg_set_profiling(prof_run.solver.ctx, 0)
+    if twin:
+        twin.close()
     t_dev = sum(step_ms) / 1e3
     sinks = stats["sink_forces"]
     t_max, sinks_all = combine_ranks(t_dev, float(sinks), dev, world)
@@ -371,7 +389,9 @@ def run_ours(args):
         return
 
     clk = clocks.summary()
-    roof = roofline(prof, stats, rp["p"], sm_count)
+    roof = roofline(prof_k, stats_k, rp["p"], sm_count)
+    if roof:
+        roof["timing"] = timing_source
     cpu = None
     if not args.no_cpu_baseline and (world == 1 or args.gpus == 1):
         rate, dt, cores = cpu_oracle_rate(name, n, args.cpu_sample, args)
@@ -396,7 +416,7 @@ def run_ours(args):
                      "momentum_drift_one_step": float(np.abs(d_end[:3] - d_start[:3]).max()),
                      "momentum_scale": mom_scale},
         "work": per_step_work(stats, launches, args.steps),
-        "kernels_ms_per_step": {k: v["ms"] / args.steps for k, v in prof.items()
+        "kernels_ms_per_step": {k: v["ms"] / (args.steps if prof_k is prof else 1) for k, v in prof_k.items()
                                 if k != "_all" and v["launches"] > 0 and v["ms"] > 0},
         "stage_ms_one_step_all_timed": breakdown,
         "roofline": roof,
@@ -486,7 +506,7 @@ def measure_other(tg, args, name, dev, stream, flush, evolved):
     w = WORKLOADS[name]
     n = w["n"]
     pos0, vel0, mass0 = workload(name, n)
-    rp = dict(w["params"], eta_tot=0.0, mac=0)
+    rp = dict(w["params"], eta_tot=0.0, mac=0, batched=int(args.batched))
     run = HHSRun(tg, tg.Params(precision=tg.TG_PREC_FP32, **rp), pos0, vel0, mass0, dev, stream)
     t_evolve = 0.0
     if evolved:

@@ -78,6 +78,12 @@ typedef struct {
                       /* dt_i = min(dt_i, sqrt(eta_tot * eps / |a|_tot,i)), |a|_tot from all  */
                       /* masses, recorded at the second kickFS2S of rung 0 (the whole system) */
     int mac;          /* tg_mac: the multipole acceptance criterion of the walk             */
+    int batched;      /* 0: plain HOLD step, driven from the host (one launch sequence per     */
+                      /*    evaluation, the host reads each split's size);                     */
+                      /* 1: batched HOLD step: the recursion of Algorithms 1-2 runs as a       */
+                      /*    device-side work queue inside one CUDA graph per rung-0 step        */
+                      /*    (a WHILE node driven by a scheduler kernel, evaluations sized on    */
+                      /*    the device).  Needs precision FP32, 4 <= p <= 6 and TG_MAC_SIDE.    */
 } tg_params;
 
 typedef struct tg_ctx tg_ctx;
@@ -140,6 +146,11 @@ tg_status tg_direct_forces(tg_ctx *ctx, int64_t n, const double *pos, const doub
 tg_status tg_hhs_init(tg_ctx *ctx, int64_t n, double *pos, double *vel, const double *mass);
 /* One rung-0 step of EVOLVE_HOLD (Algorithm 1) of length params.dt_max: recursive
  * slow/fast split, KDK (Algorithm 2) with the kickS2F/kickFS2S pairs of Algorithm 3, drifts.
+ * With params.batched the step is one CUDA graph launch: the first batched step sizes its buffers
+ * with one plain evaluation of the bound system and captures the graph (again after any buffer or
+ * parameter change); a list, cell or depth capacity exceeded inside the step restores the state
+ * and redoes the step with larger buffers; the device loop is bounded and returns TG_ERR_TIMEOUT
+ * (state restored) if it runs out.  The host reads the step's counters once at its end.
  * The step length is params.dt_max (the survey's hhs_step(dt) reads dt from the parameters, fixed
  * at tg_create, so that the rung ladder dt_max / 2^k stays the same for the whole run).
  * The step is transactional: the bound pos and vel and the integrator state are saved first, and
@@ -212,8 +223,17 @@ tg_status tg_get_lists(tg_ctx *ctx, int64_t *m2l_a, int64_t *m2l_b, int64_t *p2p
  *                            are set to value / 1000 (tiny values force the regrowth path: the
  *                            lists are sized from the estimates, overflow, and the walk is re-run
  *                            with larger buffers; tg_stats.list_regrowths counts the re-runs).
+ *   TG_DEBUG_QUEUE_LIMIT     value >= 0: iteration limit of the batched step's device loop
+ *                            (0 restores the default, 8 * 2^min(k_max, 22) + 64).
+ *   TG_DEBUG_QUEUE_HOLD      value != 0: the batched step's scheduler publishes no operation, so the
+ *                            loop spins idle until its limit and the step returns TG_ERR_TIMEOUT
+ *                            with the state restored (the bounded wait's own failure path).
+ *   TG_DEBUG_BATCH_CAPS      value > 0: the next sizing of the batched step starts its list
+ *                            capacities at `value` entries and its cell capacity at max(value, 64),
+ *                            so that the step overflows, restores the state and regrows.
  * TG_ERR_ARG for an unknown `what`.  Not synchronising. */
-typedef enum { TG_DEBUG_FAIL_ALLOC = 1, TG_DEBUG_LIST_CAPACITY = 2 } tg_debug_what;
+typedef enum { TG_DEBUG_FAIL_ALLOC = 1, TG_DEBUG_LIST_CAPACITY = 2, TG_DEBUG_QUEUE_LIMIT = 3,
+               TG_DEBUG_QUEUE_HOLD = 4, TG_DEBUG_BATCH_CAPS = 5 } tg_debug_what;
 tg_status tg_debug_control(tg_ctx *ctx, int what, int64_t value);
 
 /* ---- autotuner (the paper has no counterpart: it picks launch shapes and the leaf size of Sec. 2.3
@@ -241,6 +261,9 @@ typedef struct {
 tg_status tg_autotune(tg_ctx *ctx, int64_t n, const double *pos, const double *mass, const uint8_t *is_fast,
                       tg_tuning *out);
 tg_status tg_get_tuning(const tg_ctx *ctx, tg_tuning *out);
+/* Apply settings found by tg_autotune on another context (n_crit 1..128, p2p_rows 1..3,
+ * m2l_blocks_per_sm 1..64; the other fields are ignored).  TG_ERR_ARG for values out of range. */
+tg_status tg_set_tuning(tg_ctx *ctx, const tg_tuning *in);
 
 /* ---- live kernel timing (CUDA events on the context's stream) ---- */
 typedef enum {

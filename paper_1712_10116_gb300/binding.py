@@ -40,7 +40,7 @@ class tg_params(C.Structure):
     _fields_ = [("p", C.c_int), ("n_crit", C.c_int), ("kernel", C.c_int), ("precision", C.c_int),
                 ("max_level", C.c_int), ("k_max", C.c_int), ("theta", C.c_double), ("kappa", C.c_double),
                 ("eps", C.c_double), ("eta", C.c_double), ("dt_max", C.c_double), ("eta_tot", C.c_double),
-                ("mac", C.c_int)]
+                ("mac", C.c_int), ("batched", C.c_int)]
 
 
 class tg_stats(C.Structure):
@@ -78,11 +78,13 @@ class Params:
     k_max: int = 10
     eta_tot: float = 0.0   # Eq. (9) minimum-timestep constraint, 0 = off
     mac: int = 0           # TG_MAC_SIDE (the paper's Eq. 1) or TG_MAC_SPHERE (enclosing radii)
+    batched: int = 0       # 1: HOLD steps as one CUDA graph with a device-side work queue
 
     def to_c(self) -> tg_params:
         return tg_params(p=self.p, n_crit=self.n_crit, kernel=self.kernel, precision=self.precision,
                          max_level=self.max_level, k_max=self.k_max, theta=self.theta, kappa=self.kappa,
-                         eps=self.eps, eta=self.eta, dt_max=self.dt_max, eta_tot=self.eta_tot, mac=self.mac)
+                         eps=self.eps, eta=self.eta, dt_max=self.dt_max, eta_tot=self.eta_tot, mac=self.mac,
+                         batched=self.batched)
 
 
 _lib = None
@@ -128,13 +130,14 @@ def load() -> C.CDLL:
             L.tg_debug_control.argtypes = [_vp, C.c_int, _i64]
             L.tg_autotune.argtypes = [_vp, _i64, _vp, _vp, _vp, C.POINTER(tg_tuning)]
             L.tg_get_tuning.argtypes = [_vp, C.POINTER(tg_tuning)]
+            L.tg_set_tuning.argtypes = [_vp, C.POINTER(tg_tuning)]
             L.tg_set_profiling.argtypes = [_vp, C.c_int]
             L.tg_get_profile.argtypes = [_vp, C.POINTER(tg_profile)]
             for name in ("tg_create", "tg_destroy", "tg_get_stats", "tg_reset_stats", "tg_build_tree",
                          "tg_fmm_forces", "tg_direct_forces", "tg_hhs_init", "tg_hhs_step", "tg_hhs_state",
                          "tg_hhs_set_accel", "tg_diagnostics", "tg_tree_info", "tg_get_tree", "tg_list_counts",
                          "tg_get_lists", "tg_timesteps", "tg_set_profiling", "tg_get_profile", "tg_debug_control",
-                         "tg_autotune", "tg_get_tuning"):
+                         "tg_autotune", "tg_get_tuning", "tg_set_tuning"):
                 getattr(L, name).restype = C.c_int
             _lib = L
     return _lib
@@ -322,6 +325,9 @@ def tg_morton_sort_noalloc(pos, keys_out=None, perm_out=None, stream=None):
 
 TG_DEBUG_FAIL_ALLOC = 1
 TG_DEBUG_LIST_CAPACITY = 2
+TG_DEBUG_QUEUE_LIMIT = 3
+TG_DEBUG_QUEUE_HOLD = 4
+TG_DEBUG_BATCH_CAPS = 5
 
 
 def tg_debug_control(ctx, what: int, value: int):
@@ -343,6 +349,11 @@ def tg_get_tuning(ctx) -> dict:
     out = tg_tuning()
     _check(ctx, load().tg_get_tuning(ctx, C.byref(out)))
     return _tuning_dict(out)
+
+
+def tg_set_tuning(ctx, tuning: dict):
+    t = tg_tuning(**{k: tuning[k] for k, _ in tg_tuning._fields_ if k in tuning})
+    _check(ctx, load().tg_set_tuning(ctx, C.byref(t)))
 
 
 def tg_timesteps(ctx, a_old, a_cur, a_tot=None):

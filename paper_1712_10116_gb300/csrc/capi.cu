@@ -32,6 +32,9 @@ tg_status validate(const tg_params *p, std::string &why)
     else if (!(p->dt_max > 0.0) || !std::isfinite(p->dt_max)) why = "dt_max must be > 0";
     else if (!(p->eta_tot >= 0.0) || !std::isfinite(p->eta_tot)) why = "eta_tot must be >= 0";
     else if (p->mac != TG_MAC_SIDE && p->mac != TG_MAC_SPHERE) why = "unknown mac";
+    else if (p->batched != 0 && p->batched != 1) why = "batched must be 0 or 1";
+    else if (p->batched && (p->p < 4 || p->p > 6 || p->mac != TG_MAC_SIDE))
+        why = "the batched step needs 4 <= p <= 6 and the side criterion (TG_MAC_SIDE)";
     return why.empty() ? TG_OK : TG_ERR_ARG;
 }
 
@@ -99,6 +102,7 @@ tg_status tg_destroy(tg_ctx *c)
 {
     if (!c) return TG_ERR_ARG;
     cudaStreamSynchronize(c->stream);
+    hold_graph_destroy(c);
     for (auto &b : c->buf)
         if (b.p) cudaFree(b.p);
     for (cudaEvent_t e : c->prof_events) cudaEventDestroy(e);
@@ -318,6 +322,17 @@ tg_status tg_debug_control(tg_ctx *c, int what, int64_t value)
     case TG_DEBUG_FAIL_ALLOC:
         c->debug_fail_alloc_after = value < 0 ? -1 : value;
         return TG_OK;
+    case TG_DEBUG_QUEUE_LIMIT:
+        if (value < 0 || value > 0x7fffffff) return set_err(c, TG_ERR_ARG, "tg_debug_control: queue limit out of range");
+        c->debug_queue_limit = (unsigned)value;
+        return TG_OK;
+    case TG_DEBUG_QUEUE_HOLD:
+        c->debug_queue_hold = value != 0;
+        return TG_OK;
+    case TG_DEBUG_BATCH_CAPS:
+        c->debug_batch_caps = value < 0 ? 0 : value;
+        if (c->hold) hold_graph_reset_sizes(c);
+        return TG_OK;
     case TG_DEBUG_LIST_CAPACITY:
         if (value <= 0) return set_err(c, TG_ERR_ARG, "tg_debug_control: list capacity estimate must be > 0");
         c->walk_front_per_cell = c->walk_blocks_per_cell = c->walk_p2p_per_cell = (double)value / 1000.0;
@@ -337,6 +352,20 @@ tg_status tg_autotune(tg_ctx *c, int64_t n, const double *pos, const double *mas
         return set_err(c, TG_ERR_ARG, "tg_autotune: arrays must be device memory");
     if ((st = check_finite(c, n, pos, n, nullptr, mass))) return st;
     return autotune(c, (int)n, pos, mass, is_fast, out);
+}
+
+tg_status tg_set_tuning(tg_ctx *c, const tg_tuning *in)
+{
+    tg_status st = begin(c);
+    if (st) return st;
+    if (!in || in->n_crit < 1 || in->n_crit > kMaxNcrit || in->p2p_rows < 1 || in->p2p_rows > 3 ||
+        in->m2l_blocks_per_sm < 1 || in->m2l_blocks_per_sm > 64)
+        return set_err(c, TG_ERR_ARG, "tg_set_tuning: settings out of range");
+    c->prm.n_crit = in->n_crit;
+    c->tune.n_crit = in->n_crit;
+    c->tune.p2p_rows = in->p2p_rows;
+    c->tune.m2l_blocks_per_sm = in->m2l_blocks_per_sm;
+    return TG_OK;
 }
 
 tg_status tg_get_tuning(const tg_ctx *c, tg_tuning *out)
@@ -486,7 +515,7 @@ tg_status tg_timesteps(tg_ctx *c, int64_t n, const double *a_old, const double *
 // ------------------------------------------------------------------ checkpoint / restore
 namespace {
 
-const char kCkptMagic[8] = {'T', 'G', 'C', 'K', 'P', 'T', '0', '2'};
+const char kCkptMagic[8] = {'T', 'G', 'C', 'K', 'P', 'T', '0', '3'};
 
 struct Fnv64 {
     uint64_t h = 1469598103934665603ull;

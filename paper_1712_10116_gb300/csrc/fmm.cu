@@ -554,7 +554,8 @@ __device__ __forceinline__ unsigned long long warp_reserve(unsigned long long *c
 
 // One step of the dual walk.  The input length is read on the device (it is the previous step's
 // output counter), so that all steps can be queued without waiting for the host.
-__global__ void walk_step(TreeView t, MacParams mp, const uint2 *front_in, const unsigned long long *n_in_ctr, WalkOut o)
+__device__ __forceinline__ void walk_step_body(const TreeView &t, const MacParams &mp, const uint2 *front_in,
+                                               const unsigned long long *n_in_ctr, const WalkOut &o)
 {
     const unsigned long long n_in_raw = *n_in_ctr;
     const int64_t n_in = (int64_t)(n_in_raw < o.cap_front ? n_in_raw : o.cap_front);
@@ -619,6 +620,47 @@ __global__ void walk_step(TreeView t, MacParams mp, const uint2 *front_in, const
             ++fb;
         }
     }
+}
+
+__global__ void walk_step(TreeView t, MacParams mp, const uint2 *front_in, const unsigned long long *n_in_ctr, WalkOut o)
+{
+    walk_step_body(t, mp, front_in, n_in_ctr, o);
+}
+
+// The same step with the criterion's thresholds in device memory (batched path), staged in shared memory.
+__global__ void walk_step_dev(TreeView t, const MacParams *__restrict__ mpp, const uint2 *front_in,
+                              const unsigned long long *n_in_ctr, WalkOut o)
+{
+    static_assert(sizeof(MacParams) % 4 == 0, "MacParams is copied as 32-bit words");
+    __shared__ MacParams smp;
+    for (int i = threadIdx.x; i < (int)(sizeof(MacParams) / 4); i += blockDim.x)
+        reinterpret_cast<int *>(&smp)[i] = reinterpret_cast<const int *>(mpp)[i];
+    __syncthreads();
+    walk_step_body(t, smp, front_in, n_in_ctr, o);
+}
+
+// Gap thresholds of Eq. (1)'s eps rule for the root cube of this evaluation, on the device: the same
+// integer searches in float64 as make_mac_params on the host, so the decisions are identical.
+__global__ void mac_params_dev(const Geom *g, double eps, MacParams *mp)
+{
+    const int lf = threadIdx.x;
+    const int log2L = g->log2L;
+    if (lf <= kMaxLevel) {
+        const double eu = ldexp(eps, lf + 1 - log2L);
+        const double E = eu * eu;
+        long long r = 0;
+        if (!(0.0 > E)) {
+            long long lo = 0, hi = 1ll << 62;
+            while (hi - lo > 1) {
+                const long long mid = lo + (hi - lo) / 2;
+                if ((double)mid > E) hi = mid;
+                else lo = mid;
+            }
+            r = hi;
+        }
+        mp->gap_min_g2[lf] = r;
+    }
+    if (lf == 0) mp->log2L = log2L;
 }
 
 // ------------------------------------------------------------------ L2L (one level), normalised
@@ -1169,6 +1211,215 @@ tg_status fmm_eval(tg_ctx *c, int n, const double *pos, int64_t stride, const in
     c->stats.p2p_cell_pairs += n_p2p + n_self;
     c->stats.cells += ncell;
     return cuda_check(c, cudaGetLastError(), "fmm scatter");
+}
+
+// zero rows[0] rows of `width` values (device row count)
+template <class T>
+__global__ void zero_rows_dev(T *p, const int *rows, int width)
+{
+    const int64_t n = (int64_t)*rows * width;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) p[i] = T(0);
+}
+
+// ------------------------------------------------------------------ one evaluation, sizes on the device
+// The batched HOLD step runs every evaluation inside one CUDA graph, so no size can be read on the host:
+// the walk's counters, the tree's levels and cell count, and the particle count stay on the device, the
+// launches are sized for the capacities in BatchCaps, and anything that would pass a capacity sets an
+// overflow bit (the step is then restored and redone with larger buffers).  Float32, accelerations only,
+// always with the two moment classes of a kick pair (the classes are read from de->masked).
+__global__ void walk_init_dev(const DevEval *de, uint2 *front, unsigned long long *ctr, uint2 *p2p,
+                              unsigned long long cap_p2p)
+{
+    for (int i = threadIdx.x; i < 8 + kWalkMaxSteps + 1; i += blockDim.x) ctr[i] = 0ull;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (de->ncell == 1) {
+            p2p[cap_p2p - 1] = make_uint2(0, 0);   // the root is a leaf: one self pair
+            ctr[4] = 1ull;
+        } else {
+            front[0] = make_uint2(0, 0);
+            ctr[8] = 1ull;
+        }
+    }
+}
+
+// lists over capacity (the walk stopped writing at the capacity): flag the step and clamp the counts,
+// so that the launches after the walk stay inside their buffers
+__global__ void walk_check_dev(DevEval *de, unsigned long long *ctr, int nsteps, unsigned long long cap_front,
+                               unsigned long long cap_blocks, unsigned long long cap_p2p)
+{
+    bool over = ctr[8 + nsteps] != 0ull;
+    for (int s = 1; s <= nsteps; ++s) over |= ctr[8 + s] > cap_front;
+    over |= ctr[1] > cap_blocks || ctr[2] + ctr[4] > cap_p2p;
+    if (over) {
+        de->overflow |= 4u;
+        ctr[1] = ctr[1] < cap_blocks ? ctr[1] : cap_blocks;
+        ctr[2] = ctr[2] < cap_p2p ? ctr[2] : cap_p2p;
+        ctr[4] = ctr[4] < cap_p2p - ctr[2] ? ctr[4] : cap_p2p - ctr[2];
+    }
+}
+
+// counters of the evaluation into the step's totals: [0] evaluations, [1] particle-forces, [2] M2L pairs,
+// [3] M2L pairs x classes, [4] P2P leaf pairs, [5] cells
+__global__ void eval_finish_dev(const DevEval *de, const unsigned long long *ctr, unsigned long long *stats)
+{
+    stats[0] += 1ull;
+    stats[1] += (unsigned long long)de->n;
+    stats[2] += ctr[3];
+    stats[3] += ctr[3] * (de->masked ? 2ull : 1ull);
+    stats[4] += ctr[2] + ctr[4];
+    stats[5] += (unsigned long long)de->ncell;
+}
+
+// The parts of the criterion's thresholds that do not depend on the root cube, uploaded once before a
+// batched step is captured (mac_params_dev fills in the rest on every evaluation).  Synchronising.
+tg_status mac_params_upload(tg_ctx *c)
+{
+    MacParams *mpd;
+    tg_status st = ensure_t(c, B_MACP, 1, &mpd);
+    if (st) return st;
+    const MacParams mp = make_mac_params(c->prm, 0);
+    return cuda_check(c, cudaMemcpy(mpd, &mp, sizeof(mp), cudaMemcpyHostToDevice), "criterion upload");
+}
+
+template <class T, class T4>
+static tg_status fmm_eval_dev_t(tg_ctx *c, DevEval *de, const BatchCaps &cap, const double *xin, const double *min,
+                                const uint8_t *fin, double *acc, unsigned long long *stats)
+{
+    tg_status st;
+    const int p = c->prm.p, nc = ncoef(p), ncp = pad4(nc);
+    if (p < 4 || p > 6) return set_err(c, TG_ERR_ARG, "batched evaluation needs 4 <= p <= 6");
+    Geom *d_geom;
+    MacParams *mpd;
+    if ((st = ensure_t(c, B_GEOM, 1, &d_geom)) || (st = ensure_t(c, B_MACP, 1, &mpd))) return st;
+    if ((st = root_cube(c, cap.n, xin, cap.n, nullptr, d_geom, &de->n))) return st;
+    {
+        ProfScope ps_(c, TG_K_WALK);
+        mac_params_dev<<<1, 32, 0, c->stream>>>(d_geom, c->prm.eps, mpd);
+    }
+    if ((st = keys_sort_gather(c, cap.n, xin, cap.n, nullptr, min, fin, d_geom, de))) return st;
+    if ((st = build_octree_dev(c, de, cap.cells, cap.levels))) return st;
+    TreeView t = tree_view(c, cap.n, cap.cells);
+    t.d_ncell = &de->ncell;
+
+    // dual walk (Algorithm 4), every step queued, counters on the device
+    uint2 *f0, *f1, *p2p;
+    M2LBlock *blocks;
+    unsigned long long *wctr;
+    if ((st = ensure_t(c, B_FRONT0, cap.front, &f0)) || (st = ensure_t(c, B_FRONT1, cap.front, &f1)) ||
+        (st = ensure_t(c, B_M2L, cap.blocks, &blocks)) || (st = ensure_t(c, B_P2P, cap.p2p, &p2p)) ||
+        (st = ensure_t(c, B_WALK_CNT, 8 + kWalkMaxSteps + 1, &wctr)))
+        return st;
+    const int nsteps = std::min(kWalkMaxSteps, cap.levels);
+    {
+        ProfScope ps_(c, TG_K_WALK);
+        walk_init_dev<<<1, 64, 0, c->stream>>>(de, f0, wctr, p2p, cap.p2p);
+    }
+    for (int s = 0; s < nsteps; ++s) {
+        WalkOut o{(s & 1) ? f0 : f1, blocks, p2p, wctr, wctr + 8 + s + 1, cap.front, cap.blocks, cap.p2p};
+        ProfScope ps_(c, TG_K_WALK);
+        walk_step_dev<<<c->num_sms * 4, 128, 0, c->stream>>>(t, mpd, (s & 1) ? f1 : f0, wctr + 8 + s, o);
+    }
+    {
+        ProfScope ps_(c, TG_K_WALK);
+        walk_check_dev<<<1, 1, 0, c->stream>>>(de, wctr, nsteps, cap.front, cap.blocks, cap.p2p);
+    }
+
+    // slow-first leaves, per-particle offsets, upward pass
+    const double *xs = static_cast<const double *>(c->buf[B_XS].p), *ys = static_cast<const double *>(c->buf[B_YS].p),
+                 *zs = static_cast<const double *>(c->buf[B_ZS].p), *ms = static_cast<const double *>(c->buf[B_MS].p);
+    const uint8_t *fs = static_cast<const uint8_t *>(c->buf[B_FS].p);
+    const uint32_t *perm = static_cast<const uint32_t *>(c->buf[B_VALS0].p);
+    double *xs2, *ys2, *zs2, *ms2, *M01, *acc4;
+    uint8_t *fs2;
+    uint32_t *perm2;
+    int32_t *nslow, *leaf_of;
+    T4 *pf;
+    T *M, *Ms, *L;
+    const size_t rows = (size_t)cap.cells * 2;
+    if ((st = ensure_t(c, B_XS2, cap.n, &xs2)) || (st = ensure_t(c, B_YS2, cap.n, &ys2)) ||
+        (st = ensure_t(c, B_ZS2, cap.n, &zs2)) || (st = ensure_t(c, B_MS2, cap.n, &ms2)) ||
+        (st = ensure_t(c, B_FS2, cap.n, &fs2)) || (st = ensure_t(c, B_PERM2, cap.n, &perm2)) ||
+        (st = ensure_t(c, B_NSLOW, cap.cells, &nslow)) || (st = ensure_t(c, B_PF, cap.n, &pf)) ||
+        (st = ensure_t(c, B_LEAF_OF, cap.n, &leaf_of)) || (st = ensure_t(c, B_MOM, rows * ncp, &M)) ||
+        (st = ensure_t(c, B_MOMF, rows * ncp, &Ms)) || (st = ensure_t(c, B_MOM01, rows * 4, &M01)) ||
+        (st = ensure_t(c, B_LOC, rows * ncp, &L)) || (st = ensure_t(c, B_ACC, (size_t)4 * cap.n, &acc4)))
+        return st;
+    const int gcell = grid_for((int64_t)cap.cells * 32, 256);
+    {
+        ProfScope ps_(c, TG_K_TREE);
+        leaf_class_partition<<<gcell, 256, 0, c->stream>>>(t, xs, ys, zs, ms, fs, perm, xs2, ys2, zs2, ms2, fs2, perm2,
+                                                           nslow);
+    }
+    {
+        ProfScope ps_(c, TG_K_UP);
+        leaf_particles<T4><<<gcell, 256, 0, c->stream>>>(t, d_geom, xs2, ys2, zs2, ms2, pf, leaf_of);
+    }
+    {
+        ProfScope ps_(c, TG_K_UP);
+        p2m_leaves<T, T4><<<grid_for((int64_t)cap.cells * 32, 128), 128, 0, c->stream>>>(
+            t, d_geom, xs2, ys2, zs2, ms2, fs2, pf, p, nc, ncp, M, M01);
+    }
+    for (int l = cap.levels - 1; l >= 0; --l) {
+        ProfScope ps_(c, TG_K_UP);
+        m2m_level<T><<<c->num_sms * 8, kM2MThreads, 8 * 2 * ncp * sizeof(T), c->stream>>>(t, 0, 0, p, nc, ncp, M, M01,
+                                                                                          de, l);
+    }
+    {
+        ProfScope ps_(c, TG_K_UP);
+        scale_moments<T><<<grid_for((int64_t)cap.cells * ncp, 256), 256, 0, c->stream>>>(cap.cells, nc, ncp, M, M01, Ms,
+                                                                                        &de->ncell);
+        zero_rows_dev<T><<<c->num_sms * 4, 256, 0, c->stream>>>(L, &de->rows, ncp);
+    }
+    if (sizeof(T) == 4) {
+        st = launch_m2l_f32_dev(c, t, de, d_geom, blocks, wctr + 1, (int64_t)cap.blocks, reinterpret_cast<const float *>(Ms),
+                                reinterpret_cast<float *>(L), p, ncp, cap.cells);
+    } else {
+        st = launch_m2l_f64_dev(c, t, de, d_geom, blocks, wctr + 1, (int64_t)cap.blocks,
+                                reinterpret_cast<const double *>(Ms), reinterpret_cast<double *>(L), p, ncp);
+    }
+    if (st) return st;
+    for (int l = 1; l <= cap.levels; ++l) {
+        ProfScope ps_(c, TG_K_DOWN);
+        l2l_level<T><<<c->num_sms * 16, 32 * kM2MWarps, kM2MWarps * 2 * ncp * sizeof(T), c->stream>>>(
+            t, 0, 0, p, nc, ncp, 2, 1, L, de, l);
+    }
+    {
+        ProfScope ps_(c, TG_K_DOWN);
+        const int g = grid_for(cap.n, 128);
+        switch (p) {
+        case 4:
+            l2p_fixed<4, T, T4, false><<<g, 128, 0, c->stream>>>(cap.n, t, d_geom, pf, leaf_of, fs2, 1, ncp, L, acc4, cap.n, de);
+            break;
+        case 5:
+            l2p_fixed<5, T, T4, false><<<g, 128, 0, c->stream>>>(cap.n, t, d_geom, pf, leaf_of, fs2, 1, ncp, L, acc4, cap.n, de);
+            break;
+        default:
+            l2p_fixed<6, T, T4, false><<<g, 128, 0, c->stream>>>(cap.n, t, d_geom, pf, leaf_of, fs2, 1, ncp, L, acc4, cap.n, de);
+        }
+    }
+    if (sizeof(T) == 4)
+        st = launch_p2p_f32_dev(c, t, de, d_geom, wctr, p2p, cap.p2p, cap.cells, reinterpret_cast<const float4 *>(pf),
+                                nslow, acc4, cap.n);
+    else
+        st = launch_p2p_f64_dev(c, t, d_geom, wctr, p2p, cap.p2p, reinterpret_cast<const dbl4 *>(pf), fs2, acc4, cap.n);
+    if (st) return st;
+    {
+        ProfScope ps_(c, TG_K_DOWN);
+        scatter_out<<<grid_for(cap.n, 256), 256, 0, c->stream>>>(cap.n, perm2, acc4, acc, cap.n, nullptr, &de->n, cap.n);
+    }
+    {
+        ProfScope ps_(c, TG_K_OTHER);
+        eval_finish_dev<<<1, 1, 0, c->stream>>>(de, wctr, stats);
+    }
+    return cuda_check(c, cudaGetLastError(), "fmm evaluation (device sizes)");
+}
+
+tg_status fmm_eval_dev(tg_ctx *c, DevEval *de, const BatchCaps &cap, const double *xin, const double *min,
+                       const uint8_t *fin, double *acc, unsigned long long *stats)
+{
+    if (c->prm.precision == TG_PREC_FP32) return fmm_eval_dev_t<float, float4>(c, de, cap, xin, min, fin, acc, stats);
+    return fmm_eval_dev_t<double, dbl4>(c, de, cap, xin, min, fin, acc, stats);
 }
 
 }  // namespace tg

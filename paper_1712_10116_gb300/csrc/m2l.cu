@@ -80,6 +80,73 @@ tg_status launch_m2l_f32(tg_ctx *c, const TreeView &t, const M2LBlock *blocks, i
     return cuda_check(c, cudaGetLastError(), "m2l launch");
 }
 
+// ------------------------------------------------------------------ batched path (sizes on the device)
+template <int P>
+static void m2l_f32_dev_p(tg_ctx *c, const TreeView &t, const DevEval *de, const Geom *gp, const M2LBlock *blocks,
+                          const unsigned long long *dnb, int64_t cap_blocks, const float *Ms, float *L, int ncp,
+                          float *Mr, float *Lr, int ncpr, int rows_cap, int grid)
+{
+    const int plummer = c->prm.kernel == TG_KERNEL_PLUMMER;
+    const int g = grid_for(rows_cap, 128);
+    ProfScope ps_(c, TG_K_M2L);
+    if (!plummer) {
+        // harmonic set: fold, contract (the launch for the other class count returns at once), complete
+        using G = M2LHarm<P>;
+        m2l_reduce_moments_h<P><<<g, 128, 0, c->stream>>>(rows_cap, Ms, ncp, Mr, ncpr, &de->rows);
+        zero_rows_f32<<<c->num_sms * 4, 256, 0, c->stream>>>(Lr, &de->rows, ncpr);
+        m2l_blocks_f32<G, true, false><<<grid, 128, 0, c->stream>>>(t, blocks, cap_blocks, Mr, Lr, ncpr, 0.f, 0, dnb, de,
+                                                                    gp, c->prm.eps);
+        m2l_blocks_f32<G, false, false><<<grid, 128, 0, c->stream>>>(t, blocks, cap_blocks, Mr, Lr, ncpr, 0.f, 0, dnb, de,
+                                                                     gp, c->prm.eps);
+        m2l_complete_locals_h<P><<<g, 128, 0, c->stream>>>(rows_cap, Lr, ncpr, L, ncp, &de->rows);
+    } else {
+        using G = M2LFull<P>;
+        m2l_blocks_f32<G, true, false><<<grid, 128, 0, c->stream>>>(t, blocks, cap_blocks, Ms, L, ncp, 0.f, 1, dnb, de,
+                                                                    gp, c->prm.eps);
+        m2l_blocks_f32<G, false, false><<<grid, 128, 0, c->stream>>>(t, blocks, cap_blocks, Ms, L, ncp, 0.f, 1, dnb, de,
+                                                                     gp, c->prm.eps);
+    }
+}
+
+tg_status launch_m2l_f32_dev(tg_ctx *c, const TreeView &t, const DevEval *de, const Geom *gp, const M2LBlock *blocks,
+                             const unsigned long long *dnb, int64_t cap_blocks, const float *Ms, float *L, int p,
+                             int ncp, int cap_cells)
+{
+    if (p < 1 || p > 6) return set_err(c, TG_ERR_ARG, "batched M2L needs 1 <= p <= 6");
+    static const int nh[7] = {0, 4, 9, 16, 25, 36, 49};   // (p + 1)^2 harmonic coefficients
+    const int ncpr = (nh[p] + 3) & ~3;
+    const int rows_cap = 2 * cap_cells;
+    float *Mr = nullptr, *Lr = nullptr;
+    tg_status st;
+    if (c->prm.kernel != TG_KERNEL_PLUMMER &&
+        ((st = ensure_t(c, B_MOMH, (size_t)rows_cap * ncpr, &Mr)) || (st = ensure_t(c, B_LOCH, (size_t)rows_cap * ncpr, &Lr))))
+        return st;
+    const int grid = c->num_sms * c->tune.m2l_blocks_per_sm;
+    switch (p) {
+    case 1: m2l_f32_dev_p<1>(c, t, de, gp, blocks, dnb, cap_blocks, Ms, L, ncp, Mr, Lr, ncpr, rows_cap, grid); break;
+    case 2: m2l_f32_dev_p<2>(c, t, de, gp, blocks, dnb, cap_blocks, Ms, L, ncp, Mr, Lr, ncpr, rows_cap, grid); break;
+    case 3: m2l_f32_dev_p<3>(c, t, de, gp, blocks, dnb, cap_blocks, Ms, L, ncp, Mr, Lr, ncpr, rows_cap, grid); break;
+    case 4: m2l_f32_dev_p<4>(c, t, de, gp, blocks, dnb, cap_blocks, Ms, L, ncp, Mr, Lr, ncpr, rows_cap, grid); break;
+    case 5: m2l_f32_dev_p<5>(c, t, de, gp, blocks, dnb, cap_blocks, Ms, L, ncp, Mr, Lr, ncpr, rows_cap, grid); break;
+    default: m2l_f32_dev_p<6>(c, t, de, gp, blocks, dnb, cap_blocks, Ms, L, ncp, Mr, Lr, ncpr, rows_cap, grid);
+    }
+    return cuda_check(c, cudaGetLastError(), "m2l launch (device sizes)");
+}
+
+tg_status launch_m2l_f64_dev(tg_ctx *c, const TreeView &t, const DevEval *de, const Geom *gp, const M2LBlock *blocks,
+                             const unsigned long long *dnb, int64_t cap_blocks, const double *Ms, double *L, int p,
+                             int ncp)
+{
+    const int plummer = c->prm.kernel == TG_KERNEL_PLUMMER;
+    const int grid = c->num_sms * 16, nc = ncoef(p);
+    ProfScope ps_(c, TG_K_M2L);
+    m2l_blocks_generic<double, true><<<grid, 128, 0, c->stream>>>(t, blocks, cap_blocks, Ms, L, p, nc, ncp, 0.0, plummer,
+                                                                  dnb, de, gp, c->prm.eps);
+    m2l_blocks_generic<double, false><<<grid, 128, 0, c->stream>>>(t, blocks, cap_blocks, Ms, L, p, nc, ncp, 0.0, plummer,
+                                                                   dnb, de, gp, c->prm.eps);
+    return cuda_check(c, cudaGetLastError(), "m2l launch (device sizes, float64)");
+}
+
 tg_status launch_m2l_f64(tg_ctx *c, const TreeView &t, const M2LBlock *blocks, int64_t nblocks, const double *Ms,
                          double *L, int p, int nc, int ncp, bool masked)
 {

@@ -260,8 +260,14 @@ __device__ __forceinline__ void dtensor_generic(int p, T dx, T dy, T dz, T soft2
 template <class T, bool MASKED>
 __global__ void m2l_blocks_generic(TreeView t, const M2LBlock *__restrict__ blocks, int64_t nblocks,
                                    const T *__restrict__ Ms, T *L, int p, int nc, int ncp, double eps_over_L,
-                                   int plummer)
+                                   int plummer, const unsigned long long *dnb = nullptr, const DevEval *de = nullptr,
+                                   const Geom *gp = nullptr, double eps = 0.0)
 {
+    if (dnb) {   // batched path: counts, classes and root cube on the device
+        if ((de->masked != 0) != MASKED) return;
+        nblocks = (int64_t)*dnb;
+        if (plummer) eps_over_L = ldexp(eps, -gp->log2L);
+    }
     const int lane = threadIdx.x & 31;
     const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;

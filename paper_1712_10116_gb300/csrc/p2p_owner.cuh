@@ -25,8 +25,9 @@ constexpr int kOwnUnit = 16;   // partners per work unit of the owner kernel
 
 // Owner and partner of each distinct leaf pair, and per-owner partner counts (own_cnt starts at zero).
 __global__ void p2p_owner_count(const uint2 *__restrict__ pairs, int64_t npairs, const int32_t *__restrict__ count,
-                                uint32_t *own_cnt, uint2 *tagged)
+                                uint32_t *own_cnt, uint2 *tagged, const unsigned long long *dnp)
 {
+    if (dnp) npairs = (int64_t)*dnp;
     for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < npairs; w += (int64_t)gridDim.x * blockDim.x) {
         const uint32_t x = pairs[w].x, y = pairs[w].y;
         const int cx = count[x], cy = count[y];
@@ -40,8 +41,10 @@ __global__ void p2p_owner_count(const uint2 *__restrict__ pairs, int64_t npairs,
 // partner of an owner also opens a work unit (owner, position); ctr[0] counts the units.
 // own_fill and ctr start at zero.
 __global__ void p2p_owner_fill(const uint2 *__restrict__ tagged, int64_t npairs, const uint32_t *__restrict__ own_off,
-                               uint32_t *own_fill, int32_t *partners, uint2 *units, uint32_t *ctr)
+                               uint32_t *own_fill, int32_t *partners, uint2 *units, uint32_t *ctr,
+                               const unsigned long long *dnp)
 {
+    if (dnp) npairs = (int64_t)*dnp;
     for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < npairs; w += (int64_t)gridDim.x * blockDim.x) {
         const uint2 op = tagged[w];
         const uint32_t f = atomicAdd(&own_fill[op.x], 1u);
@@ -215,6 +218,8 @@ __device__ __forceinline__ int warp_incl_scan(int v, int lane)
 // (ctr[1], starts at zero) so that the load stays balanced whatever the spread of leaf work.  After
 // the units, the same counter hands out the self pairs (A, A): slow rows of A against every particle
 // of A with a larger index, i.e. each slow-slow and slow-fast pair once (p2p_pair_f32, SELF).
+// Batched path (walk_ctr non-null): the root cube comes from gp and the self pairs from the walk's
+// counters on the device (they sit at the end of the P2P buffer of capacity cap_p2p).
 template <int KERNEL, int ROWS, bool POT>
 __global__ void __launch_bounds__(256, 2) p2p_owner_f32(TreeView t, int log2L, const uint2 *__restrict__ units,
                                                         uint32_t *ctr, const uint32_t *__restrict__ own_off,
@@ -222,8 +227,15 @@ __global__ void __launch_bounds__(256, 2) p2p_owner_f32(TreeView t, int log2L, c
                                                         const int32_t *__restrict__ partners,
                                                         const uint2 *__restrict__ self_pairs, uint32_t nself,
                                                         const float4 *__restrict__ pf, const int32_t *__restrict__ nslow,
-                                                        float eps, double *acc4, int n, unsigned long long *pair_counter)
+                                                        float eps, double *acc4, int n, unsigned long long *pair_counter,
+                                                        const Geom *gp, const unsigned long long *walk_ctr,
+                                                        const uint2 *p2p_base, unsigned long long cap_p2p)
 {
+    if (walk_ctr) {
+        log2L = gp->log2L;
+        nself = (uint32_t)walk_ctr[4];
+        self_pairs = p2p_base + (cap_p2p - nself);
+    }
     static_assert(kOwnUnit <= 32, "one partner per lane");
     __shared__ OwnerShared sh;
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
@@ -345,6 +357,31 @@ __global__ void __launch_bounds__(256, 2) p2p_owner_f32(TreeView t, int log2L, c
 
 namespace tg {
 
+// Resident blocks per SM of the owner kernel, queried once per rows-per-lane setting (tg_autotune: 1,
+// 2 or 3; rows are packed densely, so the chunk is full whatever the leaf size).
+static int owner_occupancy(int rows)
+{
+    static int occ[4] = {0, 0, 0, 0};
+    if (occ[rows] == 0) {
+        cudaError_t e = cudaErrorInvalidValue;
+        if (rows == 1) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[1], p2p_owner_f32<TG_KERNEL_WENDLAND_C2, 1, false>, 256, 0);
+        if (rows == 2) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[2], p2p_owner_f32<TG_KERNEL_WENDLAND_C2, 2, false>, 256, 0);
+        if (rows == 3) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[3], p2p_owner_f32<TG_KERNEL_WENDLAND_C2, 3, false>, 256, 0);
+        if (e != cudaSuccess || occ[rows] < 1) {
+            cudaGetLastError();
+            occ[rows] = 1;
+        }
+    }
+    return occ[rows];
+}
+
+// zero n32[0] + extra words at p (n32: a device count, nullable; the batched path cannot size a memset)
+__global__ void zero_u32_dev(uint32_t *p, const int *n32, int extra)
+{
+    const int n = (n32 ? *n32 : 0) + extra;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) p[i] = 0u;
+}
+
 // Every P2P pair in float32, one launch: the distinct leaf pairs grouped by owner, then the self pairs.
 // pot = false: accelerations only (the potential slot of acc4 is left out).
 tg_status launch_p2p_f32(tg_ctx *c, const TreeView &t, const uint2 *pairs, int64_t npairs, const uint2 *self_pairs,
@@ -368,37 +405,25 @@ tg_status launch_p2p_f32(tg_ctx *c, const TreeView &t, const uint2 *pairs, int64
     if (npairs > 0) {
         {
             ProfScope ps_(c, TG_K_OTHER);
-            p2p_owner_count<<<grid_for(npairs, 256), 256, 0, c->stream>>>(pairs, npairs, t.count, own_cnt, tagged);
+            p2p_owner_count<<<grid_for(npairs, 256), 256, 0, c->stream>>>(pairs, npairs, t.count, own_cnt, tagged, nullptr);
         }
         if ((st = exclusive_scan_u32(c, own_cnt, own_off, ncell, nullptr))) return st;
         {
             ProfScope ps_(c, TG_K_OTHER);
             p2p_owner_fill<<<grid_for(npairs, 256), 256, 0, c->stream>>>(tagged, npairs, own_off, own_fill, partners,
-                                                                         units, ctr);
+                                                                         units, ctr, nullptr);
         }
     }
     const float eps = (float)c->prm.eps;
     unsigned long long *pc = c->d_counters;
     const bool plummer = c->prm.kernel == TG_KERNEL_PLUMMER;
     ProfScope ps_(c, TG_K_P2P);
-    // rows per lane (tg_autotune: 1, 2 or 3); rows are packed densely, so the chunk is full whatever
-    // the leaf size.  Resident blocks per SM, queried once per rows setting
     const int rows = c->tune.p2p_rows;
-    static int occ[4] = {0, 0, 0, 0};
-    if (occ[rows] == 0) {
-        cudaError_t e = cudaErrorInvalidValue;
-        if (rows == 1) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[1], p2p_owner_f32<TG_KERNEL_WENDLAND_C2, 1, false>, 256, 0);
-        if (rows == 2) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[2], p2p_owner_f32<TG_KERNEL_WENDLAND_C2, 2, false>, 256, 0);
-        if (rows == 3) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[3], p2p_owner_f32<TG_KERNEL_WENDLAND_C2, 3, false>, 256, 0);
-        if (e != cudaSuccess || occ[rows] < 1) {
-            cudaGetLastError();
-            occ[rows] = 1;
-        }
-    }
-    const int grid = c->num_sms * occ[rows];
+    const int grid = c->num_sms * owner_occupancy(rows);
 #define TG_OWNER(K, R, PT)                                                                                        \
     p2p_owner_f32<K, R, PT><<<grid, 256, 0, c->stream>>>(t, c->walk_log2L, units, ctr, own_off, own_cnt, partners,  \
-                                                         self_pairs, (uint32_t)nself, pf, nslow, eps, acc4, t.n, pc)
+                                                         self_pairs, (uint32_t)nself, pf, nslow, eps, acc4, t.n, pc,    \
+                                                         nullptr, nullptr, nullptr, 0ull)
 #define TG_OWNER_ROWS(K, PT)                                                                                      \
     switch (rows) {                                                                                               \
     case 1: TG_OWNER(K, 1, PT); break;                                                                            \
@@ -415,6 +440,60 @@ tg_status launch_p2p_f32(tg_ctx *c, const TreeView &t, const uint2 *pairs, int64
 #undef TG_OWNER_ROWS
 #undef TG_OWNER
     return cuda_check(c, cudaGetLastError(), "p2p owner launch");
+}
+
+// The same launch with every size on the device (batched HOLD step): the leaf-pair and self-pair counts
+// come from the walk's counters, the cell count from de; buffers are sized for the capacities.
+tg_status launch_p2p_f32_dev(tg_ctx *c, const TreeView &t, const DevEval *de, const Geom *gp,
+                             const unsigned long long *walk_ctr, const uint2 *p2p, size_t cap_p2p, int cap_cells,
+                             const float4 *pf, const int32_t *nslow, double *acc4, int stride)
+{
+    tg_status st;
+    uint32_t *own_cnt, *own_fill, *own_off, *ctr;
+    uint2 *tagged, *units;
+    int32_t *partners;
+    const int64_t max_units = (int64_t)cap_p2p / kOwnUnit + cap_cells + 1;
+    if ((st = ensure_t(c, B_OWN_CNT, (size_t)cap_cells + 2, &own_cnt)) ||
+        (st = ensure_t(c, B_OWN_FILL, (size_t)cap_cells + 2, &own_fill)) ||
+        (st = ensure_t(c, B_OWN_OFF, (size_t)cap_cells, &own_off)) || (st = ensure_t(c, B_OWN_LIST, max_units, &units)) ||
+        (st = ensure_t(c, B_OWN_TAG, cap_p2p, &tagged)) || (st = ensure_t(c, B_OWN_PART, cap_p2p, &partners)))
+        return st;
+    ctr = own_fill + cap_cells;   // [0] work units, [1] next unit to take
+    const int g = c->num_sms * 4;
+    {
+        ProfScope ps_(c, TG_K_OTHER);
+        zero_u32_dev<<<g, 256, 0, c->stream>>>(own_cnt, &de->ncell, 0);
+        zero_u32_dev<<<g, 256, 0, c->stream>>>(own_fill, &de->ncell, 0);
+        zero_u32_dev<<<1, 32, 0, c->stream>>>(ctr, nullptr, 2);
+        p2p_owner_count<<<g, 256, 0, c->stream>>>(p2p, (int64_t)cap_p2p, t.count, own_cnt, tagged, walk_ctr + 2);
+    }
+    if ((st = exclusive_scan_u32(c, own_cnt, own_off, cap_cells, nullptr, &de->ncell))) return st;
+    {
+        ProfScope ps_(c, TG_K_OTHER);
+        p2p_owner_fill<<<g, 256, 0, c->stream>>>(tagged, (int64_t)cap_p2p, own_off, own_fill, partners, units, ctr,
+                                                  walk_ctr + 2);
+    }
+    const float eps = (float)c->prm.eps;
+    unsigned long long *pc = c->d_counters;
+    const bool plummer = c->prm.kernel == TG_KERNEL_PLUMMER;
+    ProfScope ps_(c, TG_K_P2P);
+    const int rows = c->tune.p2p_rows;
+    const int grid = c->num_sms * owner_occupancy(rows);
+#define TG_OWNER_DEV(K, R)                                                                                        \
+    p2p_owner_f32<K, R, false><<<grid, 256, 0, c->stream>>>(t, 0, units, ctr, own_off, own_cnt, partners, nullptr, 0u, \
+                                                            pf, nslow, eps, acc4, stride, pc, gp, walk_ctr, p2p,    \
+                                                            (unsigned long long)cap_p2p)
+#define TG_OWNER_DEV_ROWS(K)                                                                                      \
+    switch (rows) {                                                                                               \
+    case 1: TG_OWNER_DEV(K, 1); break;                                                                            \
+    case 3: TG_OWNER_DEV(K, 3); break;                                                                            \
+    default: TG_OWNER_DEV(K, 2);                                                                                  \
+    }
+    if (plummer) TG_OWNER_DEV_ROWS(TG_KERNEL_PLUMMER)
+    else TG_OWNER_DEV_ROWS(TG_KERNEL_WENDLAND_C2)
+#undef TG_OWNER_DEV_ROWS
+#undef TG_OWNER_DEV
+    return cuda_check(c, cudaGetLastError(), "p2p owner launch (device sizes)");
 }
 
 }  // namespace tg

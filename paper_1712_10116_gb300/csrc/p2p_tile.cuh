@@ -64,11 +64,21 @@ __device__ __forceinline__ void pair_kernel(T r2, T eps, T eps2, T inv_eps, T in
     }
 }
 
+// Batched path (walk_ctr non-null): the distinct leaf pairs [0, walk_ctr[2]) and the walk_ctr[4] self
+// pairs at the end of the buffer (capacity cap_p2p) in one launch.
 template <class T, class T4, bool MASKED, int KERNEL>
 __global__ void __launch_bounds__(kP2PThreads) p2p_mutual(TreeView t, const Geom *gp, const uint2 *pairs,
                                                           int64_t npairs, const T4 *pf, const uint8_t *fs, T eps,
-                                                          double *acc4, int n, unsigned long long *pair_counter)
+                                                          double *acc4, int n, unsigned long long *pair_counter,
+                                                          const unsigned long long *walk_ctr = nullptr,
+                                                          unsigned long long cap_p2p = 0)
 {
+    int64_t ndist = npairs, self0 = 0;
+    if (walk_ctr) {
+        ndist = (int64_t)walk_ctr[2];
+        self0 = (int64_t)(cap_p2p - walk_ctr[4]);
+        npairs = ndist + (int64_t)walk_ctr[4];
+    }
     __shared__ T4 sb[kMaxNcrit];
     __shared__ uint8_t sfb[kMaxNcrit];
     __shared__ T colacc[kMaxNcrit][4];
@@ -77,7 +87,7 @@ __global__ void __launch_bounds__(kP2PThreads) p2p_mutual(TreeView t, const Geom
     const T eps2 = eps * eps, inv_eps = T(1) / eps, inv_eps3 = inv_eps * inv_eps * inv_eps;
     unsigned long long my_pairs = 0;
     for (int64_t w = blockIdx.x; w < npairs; w += gridDim.x) {
-        const uint2 pr = pairs[w];
+        const uint2 pr = pairs[w < ndist ? w : self0 + (w - ndist)];
         const int a = (int)pr.x, b = (int)pr.y;
         const int fa = t.first[a], na = t.count[a], fb = t.first[b], nb = t.count[b];
         const double sb_side = ldexp(g.L, -(int)t.level[b]), sa_side = ldexp(g.L, -(int)t.level[a]);
@@ -299,6 +309,22 @@ static tg_status launch_p2p_generic(tg_ctx *c, const TreeView &t, const Geom *d_
     }
 #undef TG_P2P_LAUNCH
     return cuda_check(c, cudaGetLastError(), "p2p launch");
+}
+
+// float64 P2P with every count on the device (batched path): one launch over the distinct and self pairs
+tg_status launch_p2p_f64_dev(tg_ctx *c, const TreeView &t, const Geom *d_geom, const unsigned long long *walk_ctr,
+                             const uint2 *p2p, size_t cap_p2p, const dbl4 *pf, const uint8_t *fs, double *acc4, int stride)
+{
+    const int grid = c->num_sms * 16;
+    const double eps = c->prm.eps;
+    ProfScope ps_(c, TG_K_P2P);
+    if (c->prm.kernel == TG_KERNEL_PLUMMER)
+        p2p_mutual<double, dbl4, true, TG_KERNEL_PLUMMER><<<grid, kP2PThreads, 0, c->stream>>>(
+            t, d_geom, p2p, 0, pf, fs, eps, acc4, stride, c->d_counters, walk_ctr, (unsigned long long)cap_p2p);
+    else
+        p2p_mutual<double, dbl4, true, TG_KERNEL_WENDLAND_C2><<<grid, kP2PThreads, 0, c->stream>>>(
+            t, d_geom, p2p, 0, pf, fs, eps, acc4, stride, c->d_counters, walk_ctr, (unsigned long long)cap_p2p);
+    return cuda_check(c, cudaGetLastError(), "p2p launch (device sizes, float64)");
 }
 
 // float64 P2P: one block per leaf pair, the distinct pairs then the self pairs (the tile tells them

@@ -123,6 +123,15 @@ struct tg_ctx {
 
     // launch shapes picked by tg_autotune (n_crit lives in prm)
     tg_tuning tune{0, 2, 16, 0, 0.0, 0.0};
+
+    // batched HOLD step: captured graph and its state (hhs.cu); scratch reallocations since tg_create
+    // (a captured graph holds raw buffer addresses, so a reallocation makes it stale)
+    struct HoldGraph *hold = nullptr;
+    uint64_t alloc_epoch = 0;
+    bool capturing = false;          // inside a stream capture: scratch must not grow
+    unsigned debug_queue_limit = 0;  // tg_debug_control: iteration limit of the device loop (0: default)
+    int debug_queue_hold = 0;        // tg_debug_control: the scheduler publishes no operation
+    int64_t debug_batch_caps = 0;    // tg_debug_control: initial capacities of the batched step
 };
 
 namespace tg {
@@ -139,6 +148,7 @@ enum Slot {
     B_SUB_ACC, B_HHS_AOLD, B_HHS_ACUR, B_HHS_ATOT, B_TRAD_ACC, B_TRAD_END, B_HHS_DT, B_HHS_RUNG, B_HHS_IDX, B_HHS_FLAG,
     B_HHS_SCAN, B_HHS_TMP, B_RED, B_DIAG_POT, B_DIAG_ACC,
     B_OWN_CNT, B_OWN_FILL, B_OWN_OFF, B_OWN_LIST, B_OWN_TAG, B_OWN_PART, B_SNAP, B_TUNE_ACC,
+    B_MACP, B_DEVEVAL, B_HOLD, B_FRAME_X, B_FRAME_M, B_FRAME_F, B_SPLIT_FLAG, B_SPLIT_PRE,
     B_LAST_SLOT
 };
 static_assert(B_LAST_SLOT <= kMaxSlots, "tg_ctx::buf holds fewer entries than there are slots");
@@ -211,11 +221,22 @@ tg_status exclusive_scan_u32(tg_ctx *c, const uint32_t *in, uint32_t *out, int n
 // float32 kernels leave out the potential term L^0.
 tg_status launch_m2l_f32(tg_ctx *c, const TreeView &t, const M2LBlock *blocks, int64_t nblocks, const float *Ms,
                          float *L, int p, int nc, int ncp, bool masked, bool pot);
+tg_status launch_m2l_f32_dev(tg_ctx *c, const TreeView &t, const DevEval *de, const Geom *gp, const M2LBlock *blocks,
+                             const unsigned long long *dnb, int64_t cap_blocks, const float *Ms, float *L, int p,
+                             int ncp, int cap_cells);
+tg_status launch_m2l_f64_dev(tg_ctx *c, const TreeView &t, const DevEval *de, const Geom *gp, const M2LBlock *blocks,
+                             const unsigned long long *dnb, int64_t cap_blocks, const double *Ms, double *L, int p,
+                             int ncp);
+tg_status launch_p2p_f64_dev(tg_ctx *c, const TreeView &t, const Geom *d_geom, const unsigned long long *walk_ctr,
+                             const uint2 *p2p, size_t cap_p2p, const dbl4 *pf, const uint8_t *fs, double *acc4, int stride);
 tg_status launch_m2l_f64(tg_ctx *c, const TreeView &t, const M2LBlock *blocks, int64_t nblocks, const double *Ms,
                          double *L, int p, int nc, int ncp, bool masked);
 // ---- p2p.cu: mutual P2P of all leaf pairs (distinct pairs and self pairs) into acc4.
 tg_status launch_p2p_f32(tg_ctx *c, const TreeView &t, const uint2 *pairs, int64_t npairs, const uint2 *self_pairs,
                          int64_t nself, const float4 *pf, const int32_t *nslow, bool pot, double *acc4);
+tg_status launch_p2p_f32_dev(tg_ctx *c, const TreeView &t, const DevEval *de, const Geom *gp,
+                             const unsigned long long *walk_ctr, const uint2 *p2p, size_t cap_p2p, int cap_cells,
+                             const float4 *pf, const int32_t *nslow, double *acc4, int stride);
 tg_status launch_p2p_f64(tg_ctx *c, const TreeView &t, const Geom *d_geom, const uint2 *pairs, int64_t npairs,
                          const uint2 *self_pairs, int64_t nself, const dbl4 *pf, const uint8_t *fs, bool masked,
                          double *acc4);
@@ -247,6 +268,29 @@ tg_status fmm_eval(tg_ctx *c, int n, const double *pos, int64_t stride, const in
                    bool keep_tree);
 tg_status direct_eval(tg_ctx *c, int64_t n, const double *pos, const double *mass, const uint8_t *fast,
                       int64_t n_sink, const int64_t *sink_idx, double *acc, double *pot);
+
+// Capacities of the device-sized evaluation (batched HOLD step): particles, cells, octree levels issued,
+// and the walk's frontier, M2L-block and P2P-pair lists.
+struct BatchCaps {
+    int n = 0, cells = 0, levels = 0;
+    size_t front = 0, blocks = 0, p2p = 0;
+};
+// One float32 evaluation of de->n particles (xin: 3 x cap.n SoA, min, fin: kick-pair classes when
+// de->masked) into acc (3 x cap.n SoA, input order), every size on the device; stats accumulates the
+// counters of eval_finish_dev.  No host synchronisation, so it can be captured in a CUDA graph.
+tg_status fmm_eval_dev(tg_ctx *c, DevEval *de, const BatchCaps &cap, const double *xin, const double *min,
+                       const uint8_t *fin, double *acc, unsigned long long *stats);
+// zero rows[0] rows of `width` floats (device row count)
+__global__ void zero_rows_f32(float *p, const int *rows, int width);
+// constant part of the acceptance thresholds into device memory (before a capture; synchronising)
+tg_status mac_params_upload(tg_ctx *c);
+
+// ---- batched HOLD step (hhs.cu)
+tg_status hhs_step_batched(tg_ctx *c);
+void hold_graph_destroy(tg_ctx *c);
+void hold_graph_reset_sizes(tg_ctx *c);
+// words of scan scratch exclusive_scan_u32 needs for n values
+size_t scan_scratch_words(int n);
 
 // ---- tune.cu
 tg_status autotune(tg_ctx *c, int n, const double *pos, const double *mass, const uint8_t *fast, tg_tuning *out);

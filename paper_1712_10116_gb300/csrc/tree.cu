@@ -53,7 +53,10 @@ tg_status ensure(tg_ctx *c, int slot, size_t bytes, void **out)
     Buf &b = c->buf[slot];
     if (b.bytes < bytes) {
         size_t nb = bytes + bytes / 4 + 256;
+        if (c->capturing)
+            return set_err(c, TG_ERR_CAPACITY, "scratch slot %d would grow to %zu bytes inside a graph capture", slot, nb);
         if (tg_status inj = injected_alloc_failure(c, nb, slot)) return inj;
+        c->alloc_epoch += 1;
         if (b.p) {
             cudaError_t e = stream_sync(c);
             if (e != cudaSuccess) return cuda_check(c, e, "sync before regrow");
@@ -81,7 +84,10 @@ static tg_status ensure_keep(tg_ctx *c, int slot, size_t bytes, size_t keep, voi
         return TG_OK;
     }
     size_t nb = bytes + bytes / 2 + 256;
+    if (c->capturing)
+        return set_err(c, TG_ERR_CAPACITY, "scratch slot %d would grow to %zu bytes inside a graph capture", slot, nb);
     if (tg_status inj = injected_alloc_failure(c, nb, slot)) return inj;
+    c->alloc_epoch += 1;
     void *np = nullptr;
     cudaError_t e = cudaMalloc(&np, nb);
     if (e != cudaSuccess) {
@@ -218,6 +224,18 @@ __global__ void scan_add(uint32_t *out, const uint32_t *tile_pre, int n, const i
         if (base + i < n) out[base + i] += add;
 }
 
+size_t scan_scratch_words(int n)
+{
+    size_t need = 4;
+    for (int m = n;;) {
+        const int nt = (m + kScanTile - 1) / kScanTile;
+        need += 2 * (size_t)nt + 2;
+        if (nt == 1) break;
+        m = nt;
+    }
+    return need;
+}
+
 // Exclusive scan of n uint32 values (out may alias in).  The total is written to d_total
 // (device word) when it is not null.  Recursive over tile sums.  With dn (a device count) the first
 // level scans dn[0] <= n values; the launches are sized for n, and the tiles past dn[0] hand up
@@ -228,15 +246,8 @@ tg_status exclusive_scan_u32(tg_ctx *c, const uint32_t *in, uint32_t *out, int n
         if (d_total) cudaMemsetAsync(d_total, 0, sizeof(uint32_t), c->stream);
         return cuda_check(c, cudaGetLastError(), "exclusive scan");
     }
-    size_t need = 4;
-    for (int m = n; ; ) {
-        int nt = (m + kScanTile - 1) / kScanTile;
-        need += 2 * (size_t)nt + 2;
-        if (nt == 1) break;
-        m = nt;
-    }
     uint32_t *tmp = nullptr;
-    tg_status st = ensure_t(c, B_SCAN_TMP, need, &tmp);
+    tg_status st = ensure_t(c, B_SCAN_TMP, scan_scratch_words(n), &tmp);
     if (st) return st;
     struct Level { uint32_t *out; int n, ntiles; uint32_t *sums, *pre; };
     Level lv[8];
@@ -381,6 +392,13 @@ tg_status root_cube(tg_ctx *c, int n, const double *pos, int64_t stride, const i
         bbox_final<<<1, 32, 0, c->stream>>>(partial, nb, n, d_geom, dn);
     }
     return cuda_check(c, cudaGetLastError(), "root cube");
+}
+
+// zero rows[0] rows of `width` floats (device row count)
+__global__ void zero_rows_f32(float *p, const int *rows, int width)
+{
+    const int64_t n = (int64_t)*rows * width;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) p[i] = 0.f;
 }
 
 // ------------------------------------------------------------------ input check
