@@ -54,7 +54,8 @@ KERNEL_CLASSES = ["tree", "up", "walk", "m2l", "p2p", "down", "hhs", "other"]
 
 
 class tg_tuning(C.Structure):
-    _fields_ = [("n_crit", C.c_int), ("p2p_rows", C.c_int), ("m2l_blocks_per_sm", C.c_int), ("candidates", C.c_int),
+    _fields_ = [("n_crit", C.c_int), ("p2p_rows", C.c_int), ("m2l_blocks_per_sm", C.c_int), ("m2l_form", C.c_int),
+                ("candidates", C.c_int),
                 ("objective_ms", C.c_double), ("objective_ms_initial", C.c_double)]
 
 

@@ -359,12 +359,13 @@ tg_status tg_set_tuning(tg_ctx *c, const tg_tuning *in)
     tg_status st = begin(c);
     if (st) return st;
     if (!in || in->n_crit < 1 || in->n_crit > kMaxNcrit || in->p2p_rows < 1 || in->p2p_rows > 3 ||
-        in->m2l_blocks_per_sm < 1 || in->m2l_blocks_per_sm > 64)
+        in->m2l_blocks_per_sm < 1 || in->m2l_blocks_per_sm > 64 || in->m2l_form < 0 || in->m2l_form > 1)
         return set_err(c, TG_ERR_ARG, "tg_set_tuning: settings out of range");
     c->prm.n_crit = in->n_crit;
     c->tune.n_crit = in->n_crit;
     c->tune.p2p_rows = in->p2p_rows;
     c->tune.m2l_blocks_per_sm = in->m2l_blocks_per_sm;
+    c->tune.m2l_form = in->m2l_form;
     return TG_OK;
 }
 

@@ -1373,7 +1373,7 @@ static tg_status fmm_eval_dev_t(tg_ctx *c, DevEval *de, const BatchCaps &cap, co
     }
     if (sizeof(T) == 4) {
         st = launch_m2l_f32_dev(c, t, de, d_geom, blocks, wctr + 1, (int64_t)cap.blocks, reinterpret_cast<const float *>(Ms),
-                                reinterpret_cast<float *>(L), p, ncp, cap.cells);
+                                reinterpret_cast<float *>(L), p, ncp, cap.cells, cap.m2l_src);
     } else {
         st = launch_m2l_f64_dev(c, t, de, d_geom, blocks, wctr + 1, (int64_t)cap.blocks,
                                 reinterpret_cast<const double *>(Ms), reinterpret_cast<double *>(L), p, ncp);

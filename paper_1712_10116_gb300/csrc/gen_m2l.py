@@ -21,6 +21,8 @@ The harmonic set (m2l_*_h_P, M2LGenH<P>) uses it twice, without changing any res
     once per cell (m2l_complete_locals_h_P);
   * D is needed for k_z <= 2 only: the recurrence runs over (k_x, k_y) with k_z = 0, the k_z = 1
     components take one step along z, and the k_z = 2 ones follow from the harmonic relation.
+For the directed form (one target cell, its sources one after another) m2l_acc_h[_forces]_P adds one
+source's contribution to the target's reduced locals: L^n += sum_j (-1)^|j| rho^|j| Mr^j D^{n+j}.
 Run: python gen_m2l.py > m2l_gen.cuh
 """
 
@@ -216,6 +218,28 @@ def gen_h(P):
             out.append("    }")
         out.append("}")
         out.append("")
+        # directed accumulation: L^n += sum_j (-1)^|j| rho^|j| Mr^j D^{n+j} (one target, one source)
+        out.append(f"__device__ __forceinline__ void m2l_acc_h{suf}_{P}(const float (&D)[{nd}], const float *__restrict__ Mr, float rho, float (&L)[{nh}])")
+        out.append("{")
+        out.append("    float rp = 1.0f;")
+        prev_order = 0
+        for j, (jx, jy, jz) in enumerate(H):
+            oj = jx + jy + jz
+            if not pot and oj == P:
+                continue
+            if oj != prev_order:
+                out.append("    rp *= rho;")
+                prev_order = oj
+            neg = (oj % 2) == 1
+            out.append(f"    {{ const float m = {'-' if neg else ''}__ldg(Mr + {j}) * rp;")
+            for n, (nx, ny, nz) in enumerate(H):
+                if n < first_n or nx + ny + nz + oj > P:
+                    continue
+                t = didx[(nx + jx, ny + jy, nz + jz)]
+                out.append(f"      L[{n}] = fmaf(D[{t}], m, L[{n}]);")
+            out.append("    }")
+        out.append("}")
+        out.append("")
         out.append(f"__device__ __forceinline__ void m2l_side_b_h{suf}_{P}(const float (&D)[{nd}], const float *__restrict__ Mr, float (&L)[{nh}])")
         out.append("{")
         if not pot:
@@ -301,6 +325,8 @@ def main():
         print(f"    static __device__ __forceinline__ void side_b(const float (&D)[{nd}], const float *Mr, float (&L)[{nh}]) {{ m2l_side_b_h_{P}(D, Mr, L); }}")
         print(f"    static __device__ __forceinline__ void side_a_forces(const float (&D)[{nd}], const float *Mr, float rho, float (&L)[{nh}]) {{ m2l_side_a_h_forces_{P}(D, Mr, rho, L); }}")
         print(f"    static __device__ __forceinline__ void side_b_forces(const float (&D)[{nd}], const float *Mr, float (&L)[{nh}]) {{ m2l_side_b_h_forces_{P}(D, Mr, L); }}")
+        print(f"    static __device__ __forceinline__ void acc(const float (&D)[{nd}], const float *Mr, float rho, float (&L)[{nh}]) {{ m2l_acc_h_{P}(D, Mr, rho, L); }}")
+        print(f"    static __device__ __forceinline__ void acc_forces(const float (&D)[{nd}], const float *Mr, float rho, float (&L)[{nh}]) {{ m2l_acc_h_forces_{P}(D, Mr, rho, L); }}")
         print(f"    static __device__ __forceinline__ void reduce_moments(const float *Ms, float *Mr) {{ m2l_reduce_moments_h_{P}(Ms, Mr); }}")
         print(f"    static __device__ __forceinline__ void complete_locals(const float *Lr, float *L) {{ m2l_complete_locals_h_{P}(Lr, L); }}")
         print("};")

@@ -672,6 +672,7 @@ static tg_status hold_presize(tg_ctx *c, const Sched &s, const BatchCaps &cap, c
         {B_WALK_CNT, 8 * (8 + 24 + 1)},
         {B_OWN_CNT, 4ull * (C + 2)}, {B_OWN_FILL, 4ull * (C + 2)}, {B_OWN_OFF, 4ull * C},
         {B_OWN_LIST, 8ull * max_units}, {B_OWN_TAG, 8 * cap.p2p}, {B_OWN_PART, 4 * cap.p2p},
+        {B_M2L_CNT, 4ull * C}, {B_M2L_OFF, 4ull * C}, {B_M2L_FILL, 4ull * C}, {B_M2L_SRC, 4 * cap.m2l_src},
         {B_FRAME_X, 24ull * n}, {B_FRAME_M, 8ull * n}, {B_FRAME_F, 1ull * n}, {B_SPLIT_FLAG, 4ull * n},
         {B_SPLIT_PRE, 4ull * n}, {B_HOLD, sizeof(HoldState)}, {B_DEVEVAL, sizeof(DevEval)},
     };
@@ -702,8 +703,9 @@ static tg_status hold_size(tg_ctx *c, Sched &s, BatchCaps &cap)
     cap.front = (size_t)(cap.cells * c->walk_front_per_cell * 1.25) + 4096;
     cap.blocks = (size_t)(cap.cells * c->walk_blocks_per_cell * 1.25) + 4096;
     cap.p2p = (size_t)(cap.cells * c->walk_p2p_per_cell * 1.25) + 4096;
+    cap.m2l_src = (size_t)(2.0 * c->last_nm2l * 1.5) + 4096;
     if (c->debug_batch_caps > 0) {   // test hook: start too small, so that the step must regrow
-        cap.front = cap.blocks = cap.p2p = (size_t)c->debug_batch_caps;
+        cap.front = cap.blocks = cap.p2p = cap.m2l_src = (size_t)c->debug_batch_caps;
         cap.cells = (int)std::max<int64_t>(64, c->debug_batch_caps);
     }
     return TG_OK;
@@ -894,7 +896,8 @@ tg_status hhs_step_batched(tg_ctx *c)
     for (int attempt = 0; attempt < 24; ++attempt) {
         const bool stale = !g->exec || g->epoch != c->alloc_epoch || !same_capture_params(g->prm, c->prm) ||
                            g->tune.p2p_rows != c->tune.p2p_rows ||
-                           g->tune.m2l_blocks_per_sm != c->tune.m2l_blocks_per_sm || g->n != s.n ||
+                           g->tune.m2l_blocks_per_sm != c->tune.m2l_blocks_per_sm ||
+                           g->tune.m2l_form != c->tune.m2l_form || g->n != s.n ||
                            g->bound[0] != c->hhs_pos || g->bound[1] != c->hhs_vel || g->bound[2] != c->hhs_mass;
         if (stale) {
             if ((st = hold_capture(c, g, s, s.lv, per))) return fail(st);
@@ -931,6 +934,7 @@ tg_status hhs_step_batched(tg_ctx *c)
                 g->caps.front *= 4;
                 g->caps.blocks *= 4;
                 g->caps.p2p *= 4;
+                g->caps.m2l_src *= 4;
             }
             if (g->exec) cudaGraphExecDestroy(g->exec);
             g->exec = nullptr;

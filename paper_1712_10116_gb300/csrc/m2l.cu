@@ -7,11 +7,84 @@
 
 namespace tg {
 
+// zero n (+ extra) words, n from the device when dn is given (dn[0] + extra)
+__global__ void zero_u32(uint32_t *p, int n, const int *dn, int extra)
+{
+    if (dn) n = dn[0] + extra;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) p[i] = 0u;
+}
+
+
+// Directed M2L lists from the walk's blocks: per cell the count of its sources (cnt, zeroed first), their
+// offsets (exclusive scan of cnt) and the sources themselves (src, `cap` entries).
+// dncell / dnb: device counts (batched path), else the host values.
+static tg_status m2l_lists(tg_ctx *c, const TreeView &t, const M2LBlock *blocks, int64_t nblocks, int ncell,
+                           uint32_t *cnt, uint32_t *off, uint32_t *fill, uint32_t *src, uint64_t cap,
+                           const unsigned long long *dnb, const int *dncell)
+{
+    tg_status st;
+    const int g = c->num_sms * 8;
+    {
+        ProfScope ps_(c, TG_K_M2L);
+        zero_u32<<<g, 256, 0, c->stream>>>(cnt, ncell, dncell, 0);
+        zero_u32<<<g, 256, 0, c->stream>>>(fill, ncell, dncell, 0);
+        m2l_list_count<<<g, 256, 0, c->stream>>>(t, blocks, nblocks, cnt, dnb);
+    }
+    if ((st = exclusive_scan_u32(c, cnt, off, ncell, nullptr, dncell))) return st;
+    {
+        ProfScope ps_(c, TG_K_M2L);
+        m2l_list_fill<<<g, 256, 0, c->stream>>>(t, blocks, nblocks, off, fill, src, cap, dnb);
+    }
+    return cuda_check(c, cudaGetLastError(), "m2l lists");
+}
+
+template <int P>
+static void m2l_directed_launch(tg_ctx *c, const TreeView &t, const uint32_t *off, const uint32_t *cnt,
+                                const uint32_t *src, uint64_t cap, const float *Mr, float *Lr, int ncpr, bool masked,
+                                bool pot, const DevEval *de)
+{
+    const int grid = c->num_sms * c->tune.m2l_blocks_per_sm;
+#define TG_DIR(MK, PT, DE) m2l_directed_h<P, MK, PT><<<grid, 128, 0, c->stream>>>(t, off, cnt, src, cap, Mr, Lr, ncpr, DE)
+    if (de) {   // batched: both class counts launched, the other one returns at once
+        TG_DIR(true, false, de);
+        TG_DIR(false, false, de);
+    } else if (masked) {
+        if (pot) TG_DIR(true, true, nullptr);
+        else TG_DIR(true, false, nullptr);
+    } else {
+        if (pot) TG_DIR(false, true, nullptr);
+        else TG_DIR(false, false, nullptr);
+    }
+#undef TG_DIR
+}
+
 // Harmonic set (G = -1/|d|, P <= 6): fold the moments, contract the reduced sets into Lr, complete L.
 template <int P>
 static tg_status m2l_f32_harmonic(tg_ctx *c, const TreeView &t, const M2LBlock *blocks, int64_t nblocks, const float *Ms,
                                   float *L, int ncp, bool masked, bool pot, int grid)
 {
+    if (c->tune.m2l_form == 1) {
+        // directed by target cell
+        constexpr int NH = M2LGenH<P>::NC;
+        const int ncpr = (NH + 3) & ~3;
+        const int ncell = t.ncell;
+        const int64_t rows = (int64_t)ncell * 2;
+        const uint64_t cap = 2ull * (uint64_t)c->last_nm2l + 16;
+        float *Mr, *Lr;
+        uint32_t *cnt, *off, *fill, *src;
+        tg_status st;
+        if ((st = ensure_t(c, B_MOMH, (size_t)rows * ncpr, &Mr)) || (st = ensure_t(c, B_LOCH, (size_t)rows * ncpr, &Lr)) ||
+            (st = ensure_t(c, B_M2L_CNT, (size_t)ncell, &cnt)) || (st = ensure_t(c, B_M2L_OFF, (size_t)ncell, &off)) ||
+            (st = ensure_t(c, B_M2L_FILL, (size_t)ncell, &fill)) || (st = ensure_t(c, B_M2L_SRC, cap, &src)))
+            return st;
+        if ((st = m2l_lists(c, t, blocks, nblocks, ncell, cnt, off, fill, src, cap, nullptr, nullptr))) return st;
+        ProfScope ps_(c, TG_K_M2L);
+        m2l_reduce_moments_h<P><<<grid_for(rows, 128), 128, 0, c->stream>>>(rows, Ms, ncp, Mr, ncpr, nullptr);
+        cudaMemsetAsync(Lr, 0, sizeof(float) * (size_t)rows * ncpr, c->stream);
+        m2l_directed_launch<P>(c, t, off, cnt, src, cap, Mr, Lr, ncpr, masked, pot, nullptr);
+        m2l_complete_locals_h<P><<<grid_for(rows, 128), 128, 0, c->stream>>>(rows, Lr, ncpr, L, ncp, nullptr);
+        return cuda_check(c, cudaGetLastError(), "m2l launch (directed)");
+    }
     constexpr int NH = M2LGenH<P>::NC;
     const int ncpr = (NH + 3) & ~3;
     const int64_t rows = (int64_t)t.ncell * 2;
@@ -81,13 +154,38 @@ tg_status launch_m2l_f32(tg_ctx *c, const TreeView &t, const M2LBlock *blocks, i
 }
 
 // ------------------------------------------------------------------ batched path (sizes on the device)
+// directed lists over capacity: flag the step (the fill and the kernel stay inside the buffer)
+__global__ void m2l_list_check(const uint32_t *off, const uint32_t *cnt, DevEval *de, uint64_t cap)
+{
+    const int last = de->ncell - 1;
+    if ((uint64_t)off[last] + cnt[last] > cap) de->overflow |= 4u;
+}
+
 template <int P>
-static void m2l_f32_dev_p(tg_ctx *c, const TreeView &t, const DevEval *de, const Geom *gp, const M2LBlock *blocks,
-                          const unsigned long long *dnb, int64_t cap_blocks, const float *Ms, float *L, int ncp,
-                          float *Mr, float *Lr, int ncpr, int rows_cap, int grid)
+static tg_status m2l_f32_dev_p(tg_ctx *c, const TreeView &t, const DevEval *de, const Geom *gp, const M2LBlock *blocks,
+                               const unsigned long long *dnb, int64_t cap_blocks, const float *Ms, float *L, int ncp,
+                               float *Mr, float *Lr, int ncpr, int rows_cap, int grid, size_t cap_src)
 {
     const int plummer = c->prm.kernel == TG_KERNEL_PLUMMER;
     const int g = grid_for(rows_cap, 128);
+    if (!plummer && c->tune.m2l_form == 1) {
+        const int cap_cells = rows_cap / 2;
+        uint32_t *cnt, *off, *fill, *src;
+        tg_status st;
+        if ((st = ensure_t(c, B_M2L_CNT, (size_t)cap_cells, &cnt)) ||
+            (st = ensure_t(c, B_M2L_OFF, (size_t)cap_cells, &off)) ||
+            (st = ensure_t(c, B_M2L_FILL, (size_t)cap_cells, &fill)) || (st = ensure_t(c, B_M2L_SRC, cap_src, &src)))
+            return st;
+        if ((st = m2l_lists(c, t, blocks, cap_blocks, cap_cells, cnt, off, fill, src, cap_src, dnb, &de->ncell)))
+            return st;
+        ProfScope ps_(c, TG_K_M2L);
+        m2l_list_check<<<1, 1, 0, c->stream>>>(off, cnt, const_cast<DevEval *>(de), cap_src);
+        m2l_reduce_moments_h<P><<<g, 128, 0, c->stream>>>(rows_cap, Ms, ncp, Mr, ncpr, &de->rows);
+        zero_rows_f32<<<c->num_sms * 4, 256, 0, c->stream>>>(Lr, &de->rows, ncpr);
+        m2l_directed_launch<P>(c, t, off, cnt, src, cap_src, Mr, Lr, ncpr, true, false, de);
+        m2l_complete_locals_h<P><<<g, 128, 0, c->stream>>>(rows_cap, Lr, ncpr, L, ncp, &de->rows);
+        return TG_OK;
+    }
     ProfScope ps_(c, TG_K_M2L);
     if (!plummer) {
         // harmonic set: fold, contract (the launch for the other class count returns at once), complete
@@ -106,11 +204,12 @@ static void m2l_f32_dev_p(tg_ctx *c, const TreeView &t, const DevEval *de, const
         m2l_blocks_f32<G, false, false><<<grid, 128, 0, c->stream>>>(t, blocks, cap_blocks, Ms, L, ncp, 0.f, 1, dnb, de,
                                                                      gp, c->prm.eps);
     }
+    return TG_OK;
 }
 
 tg_status launch_m2l_f32_dev(tg_ctx *c, const TreeView &t, const DevEval *de, const Geom *gp, const M2LBlock *blocks,
                              const unsigned long long *dnb, int64_t cap_blocks, const float *Ms, float *L, int p,
-                             int ncp, int cap_cells)
+                             int ncp, int cap_cells, size_t cap_src)
 {
     if (p < 1 || p > 6) return set_err(c, TG_ERR_ARG, "batched M2L needs 1 <= p <= 6");
     static const int nh[7] = {0, 4, 9, 16, 25, 36, 49};   // (p + 1)^2 harmonic coefficients
@@ -123,13 +222,14 @@ tg_status launch_m2l_f32_dev(tg_ctx *c, const TreeView &t, const DevEval *de, co
         return st;
     const int grid = c->num_sms * c->tune.m2l_blocks_per_sm;
     switch (p) {
-    case 1: m2l_f32_dev_p<1>(c, t, de, gp, blocks, dnb, cap_blocks, Ms, L, ncp, Mr, Lr, ncpr, rows_cap, grid); break;
-    case 2: m2l_f32_dev_p<2>(c, t, de, gp, blocks, dnb, cap_blocks, Ms, L, ncp, Mr, Lr, ncpr, rows_cap, grid); break;
-    case 3: m2l_f32_dev_p<3>(c, t, de, gp, blocks, dnb, cap_blocks, Ms, L, ncp, Mr, Lr, ncpr, rows_cap, grid); break;
-    case 4: m2l_f32_dev_p<4>(c, t, de, gp, blocks, dnb, cap_blocks, Ms, L, ncp, Mr, Lr, ncpr, rows_cap, grid); break;
-    case 5: m2l_f32_dev_p<5>(c, t, de, gp, blocks, dnb, cap_blocks, Ms, L, ncp, Mr, Lr, ncpr, rows_cap, grid); break;
-    default: m2l_f32_dev_p<6>(c, t, de, gp, blocks, dnb, cap_blocks, Ms, L, ncp, Mr, Lr, ncpr, rows_cap, grid);
+    case 1: st = m2l_f32_dev_p<1>(c, t, de, gp, blocks, dnb, cap_blocks, Ms, L, ncp, Mr, Lr, ncpr, rows_cap, grid, cap_src); break;
+    case 2: st = m2l_f32_dev_p<2>(c, t, de, gp, blocks, dnb, cap_blocks, Ms, L, ncp, Mr, Lr, ncpr, rows_cap, grid, cap_src); break;
+    case 3: st = m2l_f32_dev_p<3>(c, t, de, gp, blocks, dnb, cap_blocks, Ms, L, ncp, Mr, Lr, ncpr, rows_cap, grid, cap_src); break;
+    case 4: st = m2l_f32_dev_p<4>(c, t, de, gp, blocks, dnb, cap_blocks, Ms, L, ncp, Mr, Lr, ncpr, rows_cap, grid, cap_src); break;
+    case 5: st = m2l_f32_dev_p<5>(c, t, de, gp, blocks, dnb, cap_blocks, Ms, L, ncp, Mr, Lr, ncpr, rows_cap, grid, cap_src); break;
+    default: st = m2l_f32_dev_p<6>(c, t, de, gp, blocks, dnb, cap_blocks, Ms, L, ncp, Mr, Lr, ncpr, rows_cap, grid, cap_src);
     }
+    if (st) return st;
     return cuda_check(c, cudaGetLastError(), "m2l launch (device sizes)");
 }
 

@@ -225,6 +225,130 @@ __global__ void __launch_bounds__(128) m2l_blocks_f32(TreeView t, const M2LBlock
     }
 }
 
+// ------------------------------------------------------------------ directed, by target cell (harmonic set)
+// The walk's blocks hold each well-separated cell pair once.  The directed form lists, for every cell,
+// the cells it receives from (both members of each pair), and a warp takes one target: lanes stride
+// over its sources, each adds its sources' contributions to the target's reduced locals in registers
+// (m2l_acc_h), and one warp reduction per target writes them.  The derivative tensor is computed once
+// per direction instead of once per pair, but no pair needs a reduction across lanes or an atomic.
+
+// per block: sources gained by each row cell (its row's bits) and each column cell (its column's bits)
+__global__ void m2l_list_count(TreeView t, const M2LBlock *__restrict__ blocks, int64_t nblocks, uint32_t *cnt,
+                               const unsigned long long *dnb)
+{
+    if (dnb) nblocks = (int64_t)*dnb;
+    for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < nblocks; w += (int64_t)gridDim.x * blockDim.x) {
+        const M2LBlock blk = blocks[w];
+        const BlockGeom bg = block_geom(t, blk);
+        unsigned long long colbits = 0ull;   // bit 8j + i: the transposed mask
+        for (int i = 0; i < 8; ++i) {
+            const unsigned row = (unsigned)((blk.mask >> (8 * i)) & 0xffull);
+            if (row) atomicAdd(&cnt[bg.baseA + i], (uint32_t)__popc(row));
+            for (unsigned r = row; r; r &= r - 1) colbits |= 1ull << (8 * (__ffs(r) - 1) + i);
+        }
+        for (int j = 0; j < 8; ++j) {
+            const unsigned col = (unsigned)((colbits >> (8 * j)) & 0xffull);
+            if (col) atomicAdd(&cnt[bg.baseB + j], (uint32_t)__popc(col));
+        }
+    }
+}
+
+// sources of each cell at off[cell] + fill[cell]; entries past `cap` are dropped (capacity overflow is
+// detected by the caller from the total)
+__global__ void m2l_list_fill(TreeView t, const M2LBlock *__restrict__ blocks, int64_t nblocks,
+                              const uint32_t *__restrict__ off, uint32_t *fill, uint32_t *src, uint64_t cap,
+                              const unsigned long long *dnb)
+{
+    if (dnb) nblocks = (int64_t)*dnb;
+    for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < nblocks; w += (int64_t)gridDim.x * blockDim.x) {
+        const M2LBlock blk = blocks[w];
+        const BlockGeom bg = block_geom(t, blk);
+        unsigned long long colbits = 0ull;
+        for (int i = 0; i < 8; ++i) {
+            const unsigned row = (unsigned)((blk.mask >> (8 * i)) & 0xffull);
+            if (!row) continue;
+            const int x = bg.baseA + i;
+            uint64_t at = (uint64_t)off[x] + atomicAdd(&fill[x], (uint32_t)__popc(row));
+            for (unsigned r = row; r; r &= r - 1) {
+                const int j = __ffs(r) - 1;
+                if (at < cap) src[at] = (uint32_t)(bg.baseB + j);
+                ++at;
+                colbits |= 1ull << (8 * j + i);
+            }
+        }
+        for (int j = 0; j < 8; ++j) {
+            const unsigned col = (unsigned)((colbits >> (8 * j)) & 0xffull);
+            if (!col) continue;
+            const int y = bg.baseB + j;
+            uint64_t at = (uint64_t)off[y] + atomicAdd(&fill[y], (uint32_t)__popc(col));
+            for (unsigned r = col; r; r &= r - 1) {
+                if (at < cap) src[at] = (uint32_t)(bg.baseA + __ffs(r) - 1);
+                ++at;
+            }
+        }
+    }
+}
+
+// sum of v over the warp, scattered: afterwards lane l holds coefficients 2l and 2l + 1 (NP = 64)
+template <int NP>
+__device__ __forceinline__ void warp_reduce_scatter64(float (&v)[NP], int lane)
+{
+    static_assert(NP == 64, "64 coefficients: two per lane");
+    m2l_halve<NP, 32>(v, lane, 16);
+    m2l_halve<NP, 16>(v, lane, 8);
+    m2l_halve<NP, 8>(v, lane, 4);
+    m2l_halve<NP, 4>(v, lane, 2);
+    m2l_halve<NP, 2>(v, lane, 1);
+}
+
+template <int P, bool MASKED, bool POT>
+__global__ void __launch_bounds__(128) m2l_directed_h(TreeView t, const uint32_t *__restrict__ off,
+                                                      const uint32_t *__restrict__ cnt,
+                                                      const uint32_t *__restrict__ src, uint64_t cap,
+                                                      const float *__restrict__ Mr, float *__restrict__ Lr, int ncpr,
+                                                      const DevEval *de)
+{
+    using G = M2LGenH<P>;
+    constexpr int NC = G::NC, ND = G::ND, NP = 64;
+    static_assert(NC <= NP, "reduced set fits in two coefficients per lane");
+    if (de && (de->masked != 0) != MASKED) return;
+    const int ncell = t.cells();
+    const int lane = threadIdx.x & 31;
+    const int nw = (int)((gridDim.x * blockDim.x) >> 5);
+    for (int x = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5); x < ncell; x += nw) {
+        const uint32_t b = off[x], e = (uint32_t)min((uint64_t)off[x] + cnt[x], cap);
+        if (b >= e) continue;   // whole warp
+        const int lx = t.level[x];
+        float a0[NP], a1[NP];
+#pragma unroll
+        for (int k = 0; k < NP; ++k) a0[k] = a1[k] = 0.f;
+        for (uint32_t q = b + lane; q < e; q += 32) {
+            const int y = (int)src[q];
+            const int ly = t.level[y];
+            float dx, dy, dz;
+            pair_offset<float>(t, x, y, lx, ly, dx, dy, dz);
+            float D[ND];
+            G::dtensor(dx, dy, dz, D);
+            const float rho = ldexpf(1.0f, lx - ly);
+            if (POT) G::acc(D, Mr + (size_t)y * 2 * ncpr, rho, reinterpret_cast<float(&)[NC]>(a0));
+            else G::acc_forces(D, Mr + (size_t)y * 2 * ncpr, rho, reinterpret_cast<float(&)[NC]>(a0));
+            if (MASKED) {
+                if (POT) G::acc(D, Mr + ((size_t)y * 2 + 1) * ncpr, rho, reinterpret_cast<float(&)[NC]>(a1));
+                else G::acc_forces(D, Mr + ((size_t)y * 2 + 1) * ncpr, rho, reinterpret_cast<float(&)[NC]>(a1));
+            }
+        }
+        warp_reduce_scatter64<NP>(a0, lane);
+        float *dst = Lr + (size_t)x * 2 * ncpr;
+        if (2 * lane < NC) dst[2 * lane] = a0[0];
+        if (2 * lane + 1 < NC) dst[2 * lane + 1] = a0[1];
+        if (MASKED) {
+            warp_reduce_scatter64<NP>(a1, lane);
+            if (2 * lane < NC) dst[ncpr + 2 * lane] = a1[0];
+            if (2 * lane + 1 < NC) dst[ncpr + 2 * lane + 1] = a1[1];
+        }
+    }
+}
+
 // ------------------------------------------------------------------ generic (p <= 8, float or double)
 // Same block layout; each active lane evaluates its pair with run-time loops and adds both sides
 // directly to global memory.  Used by the float64 path and by float32 for p > 6.

@@ -122,7 +122,7 @@ struct tg_ctx {
     int64_t debug_fail_alloc_after = -1;
 
     // launch shapes picked by tg_autotune (n_crit lives in prm)
-    tg_tuning tune{0, 2, 16, 0, 0.0, 0.0};
+    tg_tuning tune{0, 2, 16, 1, 0, 0.0, 0.0};
 
     // batched HOLD step: captured graph and its state (hhs.cu); scratch reallocations since tg_create
     // (a captured graph holds raw buffer addresses, so a reallocation makes it stale)
@@ -149,6 +149,7 @@ enum Slot {
     B_HHS_SCAN, B_HHS_TMP, B_RED, B_DIAG_POT, B_DIAG_ACC,
     B_OWN_CNT, B_OWN_FILL, B_OWN_OFF, B_OWN_LIST, B_OWN_TAG, B_OWN_PART, B_SNAP, B_TUNE_ACC,
     B_MACP, B_DEVEVAL, B_HOLD, B_FRAME_X, B_FRAME_M, B_FRAME_F, B_SPLIT_FLAG, B_SPLIT_PRE,
+    B_M2L_CNT, B_M2L_OFF, B_M2L_FILL, B_M2L_SRC,
     B_LAST_SLOT
 };
 static_assert(B_LAST_SLOT <= kMaxSlots, "tg_ctx::buf holds fewer entries than there are slots");
@@ -223,7 +224,7 @@ tg_status launch_m2l_f32(tg_ctx *c, const TreeView &t, const M2LBlock *blocks, i
                          float *L, int p, int nc, int ncp, bool masked, bool pot);
 tg_status launch_m2l_f32_dev(tg_ctx *c, const TreeView &t, const DevEval *de, const Geom *gp, const M2LBlock *blocks,
                              const unsigned long long *dnb, int64_t cap_blocks, const float *Ms, float *L, int p,
-                             int ncp, int cap_cells);
+                             int ncp, int cap_cells, size_t cap_src);
 tg_status launch_m2l_f64_dev(tg_ctx *c, const TreeView &t, const DevEval *de, const Geom *gp, const M2LBlock *blocks,
                              const unsigned long long *dnb, int64_t cap_blocks, const double *Ms, double *L, int p,
                              int ncp);
@@ -274,6 +275,7 @@ tg_status direct_eval(tg_ctx *c, int64_t n, const double *pos, const double *mas
 struct BatchCaps {
     int n = 0, cells = 0, levels = 0;
     size_t front = 0, blocks = 0, p2p = 0;
+    size_t m2l_src = 0;   // entries of the directed M2L source lists (two per cell pair)
 };
 // One float32 evaluation of de->n particles (xin: 3 x cap.n SoA, min, fin: kick-pair classes when
 // de->masked) into acc (3 x cap.n SoA, input order), every size on the device; stats accumulates the

@@ -119,6 +119,21 @@ tg_status autotune(tg_ctx *c, int n, const double *pos, const double *mass, cons
                 choice.m2l_blocks_per_sm = g;
             }
         }
+        c->tune.m2l_blocks_per_sm = choice.m2l_blocks_per_sm;
+        if (c->prm.kernel == TG_KERNEL_WENDLAND_C2 && c->prm.p <= 6) {
+            // the mutual and the directed form of the harmonic M2L
+            for (int form = 0; form <= 1; ++form) {
+                if (form == choice.m2l_form) continue;
+                c->tune.m2l_form = form;
+                double ms;
+                if ((st = objective(r, &ms))) return finish(st);
+                if (ms < best) {
+                    best = ms;
+                    choice.m2l_form = form;
+                }
+            }
+            c->tune.m2l_form = choice.m2l_form;
+        }
     }
     choice.candidates = r.timed;
     choice.objective_ms = best;

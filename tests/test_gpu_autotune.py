@@ -22,7 +22,8 @@ def _t(a, dtype=torch.float64):
 def test_defaults_before_tuning():
     s = tg.Solver(tg.Params(p=6, n_crit=64, precision=tg.TG_PREC_FP32))
     t = tg.tg_get_tuning(s.ctx)
-    assert t["n_crit"] == 64 and t["p2p_rows"] == 2 and t["m2l_blocks_per_sm"] == 16 and t["candidates"] == 0
+    assert t["n_crit"] == 64 and t["p2p_rows"] == 2 and t["m2l_blocks_per_sm"] == 16 and t["m2l_form"] == 1
+    assert t["candidates"] == 0
     s.close()
 
 
@@ -37,8 +38,8 @@ def test_autotune_picks_a_candidate_and_stays_correct(precision):
     t = s.autotune(P, M, F)
     assert t["n_crit"] in (48, 64, 80, 96, 112, 128)
     if precision == 1:
-        assert t["p2p_rows"] in (1, 2, 3) and t["m2l_blocks_per_sm"] in (4, 8, 16, 32)
-        assert t["candidates"] == 1 + 5 + 1 + 2 + 3
+        assert t["p2p_rows"] in (1, 2, 3) and t["m2l_blocks_per_sm"] in (4, 8, 16, 32) and t["m2l_form"] in (0, 1)
+        assert t["candidates"] == 1 + 5 + 1 + 2 + 3 + 1
     else:
         assert t["p2p_rows"] == 2 and t["m2l_blocks_per_sm"] == 16 and t["candidates"] == 6
     assert 0 < t["objective_ms"] <= 1.25 * t["objective_ms_initial"]

@@ -572,3 +572,24 @@ def test_high_order_error_falls_to_roundoff():
     assert all(b < a / 20 for a, b in zip(med, med[1:]))
     assert med[-1] < 1e-12
 
+
+
+# ---------------------------------------------------------------- both forms of the harmonic float32 M2L
+@pytest.mark.parametrize("form", [0, 1])
+@pytest.mark.parametrize("masked", [False, True])
+def test_fp32_m2l_forms_match_oracle(form, masked):
+    # 0: mutual, a lane per cell pair of a walk block, both sides combined across lanes;
+    # 1: directed, a warp per target cell over its source list (the default)
+    n = 6000
+    pos, _, _ = _case("clustered", n)
+    mass = ics.random_masses(n, 11)
+    fast = ics.random_fast_mask(n, 12) if masked else None
+    prm = tg.Params(p=6, theta=0.5, eps=0.005, kernel=0, precision=tg.TG_PREC_FP32, n_crit=32)
+    s = tg.Solver(prm)
+    t = tg.tg_get_tuning(s.ctx)
+    t["m2l_form"] = form
+    tg.tg_set_tuning(s.ctx, t)
+    acc, pot = s.fmm_forces(_t(pos), _t(mass), None if fast is None else _t(fast, torch.uint8))
+    a_o, p_o = oracle.fmm(pos, mass, _oprm(prm), fast)
+    _check_fp32(acc.cpu().numpy(), a_o, f"m2l form {form} masked={masked}")
+    assert np.abs(pot.cpu().numpy() - p_o).max() < FP32_TOL * np.abs(p_o).max()
