@@ -233,7 +233,7 @@ __global__ void __launch_bounds__(128) m2l_blocks_f32(TreeView t, const M2LBlock
 // per direction instead of once per pair, but no pair needs a reduction across lanes or an atomic.
 
 // per block: sources gained by each row cell (its row's bits) and each column cell (its column's bits)
-__global__ void m2l_list_count(TreeView t, const M2LBlock *__restrict__ blocks, int64_t nblocks, uint32_t *cnt,
+static __global__ void m2l_list_count(TreeView t, const M2LBlock *__restrict__ blocks, int64_t nblocks, uint32_t *cnt,
                                const unsigned long long *dnb)
 {
     if (dnb) nblocks = (int64_t)*dnb;
@@ -255,7 +255,7 @@ __global__ void m2l_list_count(TreeView t, const M2LBlock *__restrict__ blocks, 
 
 // sources of each cell at off[cell] + fill[cell]; entries past `cap` are dropped (capacity overflow is
 // detected by the caller from the total)
-__global__ void m2l_list_fill(TreeView t, const M2LBlock *__restrict__ blocks, int64_t nblocks,
+static __global__ void m2l_list_fill(TreeView t, const M2LBlock *__restrict__ blocks, int64_t nblocks,
                               const uint32_t *__restrict__ off, uint32_t *fill, uint32_t *src, uint64_t cap,
                               const unsigned long long *dnb)
 {
