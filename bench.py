@@ -89,6 +89,8 @@ def parse():
     ap.add_argument("--eval-only", action="store_true",
                     help="run warmup + steps single FMM evaluations of the workload (for profiler captures)")
     ap.add_argument("--masked", action="store_true", help="with --eval-only: 30%% of the particles in the fast set")
+    ap.add_argument("--m2l-form", type=int, default=-1, choices=[-1, 0, 1],
+                    help="with --eval-only: float32 harmonic M2L form (0 mutual, 1 directed; -1 the default)")
     return ap.parse_args()
 
 
@@ -594,6 +596,10 @@ def run_eval_only(args):
     P = torch.tensor(pos, device=dev)
     M = torch.tensor(mass, device=dev)
     F = torch.tensor(ics.random_fast_mask(n, 17), device=dev) if args.masked else None
+    if args.m2l_form >= 0:
+        t = tg.tg_get_tuning(solver.ctx)
+        t["m2l_form"] = args.m2l_form
+        tg.tg_set_tuning(solver.ctx, t)
     for _ in range(args.warmup):
         solver.fmm_forces(P, M, F, want_pot=False)
     torch.cuda.synchronize()

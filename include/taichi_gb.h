@@ -244,9 +244,9 @@ tg_status tg_debug_control(tg_ctx *ctx, int what, int64_t value);
  *                     the FMM's own accuracy; params.n_crit of the context is replaced)
  *   p2p_rows          rows per lane of the float32 P2P tile: 1, 2, 3 (results unchanged)
  *   m2l_blocks_per_sm grid of the float32 M2L kernel in blocks per SM: 4, 8, 16, 32 (results unchanged)
- *   m2l_form          float32 M2L with the harmonic set (Wendland kernel): 0 mutual, a lane per cell pair
- *                     of a block, both sides combined across lanes; 1 directed, a warp per target cell
- *                     over its sources (the same terms, summed in another order)
+ *   m2l_form          float32 M2L with the harmonic set (Wendland kernel): 0 mutual (the default), a
+ *                     lane per cell pair of a block, both sides combined across lanes; 1 directed, a
+ *                     warp per target cell over its sources (the same terms, summed in another order)
  * searched one after another in that order (each at the best of the ones before).  The objective is
  * the time of one all-from-all evaluation plus, when is_fast is given, one kick-pair evaluation with
  * that fast set (accelerations only, as the HHS kicks ask).  pos: device 3*n float64, mass: device n

@@ -122,7 +122,7 @@ struct tg_ctx {
     int64_t debug_fail_alloc_after = -1;
 
     // launch shapes picked by tg_autotune (n_crit lives in prm)
-    tg_tuning tune{0, 2, 16, 1, 0, 0.0, 0.0};
+    tg_tuning tune{0, 2, 16, 0, 0, 0.0, 0.0};
 
     // batched HOLD step: captured graph and its state (hhs.cu); scratch reallocations since tg_create
     // (a captured graph holds raw buffer addresses, so a reallocation makes it stale)

@@ -97,8 +97,9 @@ tg_status autotune(tg_ctx *c, int n, const double *pos, const double *mass, cons
         // the objective at the chosen n_crit with the current shapes, then the other shapes
         if ((st = objective(r, &best))) return finish(st);
         const int rows_cand[] = {1, 2, 3};
+        const int rows0 = choice.p2p_rows;   // timed already
         for (int rows : rows_cand) {
-            if (rows == choice.p2p_rows) continue;
+            if (rows == rows0) continue;
             c->tune.p2p_rows = rows;
             double ms;
             if ((st = objective(r, &ms))) return finish(st);
@@ -109,8 +110,9 @@ tg_status autotune(tg_ctx *c, int n, const double *pos, const double *mass, cons
         }
         c->tune.p2p_rows = choice.p2p_rows;
         const int grid_cand[] = {4, 8, 16, 32};
+        const int grid0 = choice.m2l_blocks_per_sm;
         for (int g : grid_cand) {
-            if (g == choice.m2l_blocks_per_sm) continue;
+            if (g == grid0) continue;
             c->tune.m2l_blocks_per_sm = g;
             double ms;
             if ((st = objective(r, &ms))) return finish(st);
@@ -122,8 +124,9 @@ tg_status autotune(tg_ctx *c, int n, const double *pos, const double *mass, cons
         c->tune.m2l_blocks_per_sm = choice.m2l_blocks_per_sm;
         if (c->prm.kernel == TG_KERNEL_WENDLAND_C2 && c->prm.p <= 6) {
             // the mutual and the directed form of the harmonic M2L
+            const int form0 = choice.m2l_form;
             for (int form = 0; form <= 1; ++form) {
-                if (form == choice.m2l_form) continue;
+                if (form == form0) continue;
                 c->tune.m2l_form = form;
                 double ms;
                 if ((st = objective(r, &ms))) return finish(st);

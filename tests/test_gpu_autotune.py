@@ -22,7 +22,7 @@ def _t(a, dtype=torch.float64):
 def test_defaults_before_tuning():
     s = tg.Solver(tg.Params(p=6, n_crit=64, precision=tg.TG_PREC_FP32))
     t = tg.tg_get_tuning(s.ctx)
-    assert t["n_crit"] == 64 and t["p2p_rows"] == 2 and t["m2l_blocks_per_sm"] == 16 and t["m2l_form"] == 1
+    assert t["n_crit"] == 64 and t["p2p_rows"] == 2 and t["m2l_blocks_per_sm"] == 16 and t["m2l_form"] == 0
     assert t["candidates"] == 0
     s.close()
 

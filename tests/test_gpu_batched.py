@@ -147,11 +147,11 @@ def test_batched_queue_limit_times_out_and_restores():
 
 
 def test_batched_overflow_restores_regrows_and_redoes_the_step():
+    # a Plummer sphere with a softening that keeps it far from close encounters: the float64 trajectories
+    # of the plain and the regrown batched steps then differ only by the rounding of their float atomics
     n = 20000
-    pos, vel, mass = ics.clustered(n, 1007)
-    mass = ics.random_masses(n, 31)
-    vel = vel - (vel * mass).sum(1, keepdims=True) / mass.sum()
-    base = dict(p=5, theta=0.45, eps=0.002, precision=tg.TG_PREC_FP64, n_crit=32, eta=0.02, dt_max=1.0 / 16, k_max=8)
+    pos, vel, mass = ics.plummer(n, 1001)
+    base = dict(p=5, theta=0.45, eps=0.01, precision=tg.TG_PREC_FP64, n_crit=32, eta=0.02, dt_max=1.0 / 16, k_max=8)
     xp, vp, rp, sp = _run(tg.Params(**base), pos, vel, mass, 2)
     s = tg.Solver(tg.Params(batched=1, **base))
     P, V, M = _t(pos), _t(vel), _t(mass)
@@ -164,10 +164,7 @@ def test_batched_overflow_restores_regrows_and_redoes_the_step():
     st = s.stats()
     assert st["list_regrowths"] >= 2   # both lists and cells ran out at least once
     assert st["evaluations"] == sp["evaluations"]
-    # float64 differences come from the order of the float atomics only (the batched float64 P2P takes the
-    # distinct and self pairs in one launch); this clustered set's close encounters amplify them to a few
-    # 1e-12 over two steps, so it is held to the oracle parity bound of 1e-11
     x, v = P.cpu().numpy(), V.cpu().numpy()
-    assert np.abs(x - xp).max() < 1e-11 * np.abs(xp).max()
-    assert np.abs(v - vp).max() < 1e-10 * np.abs(vp).max()
+    assert np.abs(x - xp).max() < 1e-12 * np.abs(xp).max()
+    assert np.abs(v - vp).max() < 1e-12 * np.abs(vp).max()
     s.close()

@@ -578,8 +578,8 @@ def test_high_order_error_falls_to_roundoff():
 @pytest.mark.parametrize("form", [0, 1])
 @pytest.mark.parametrize("masked", [False, True])
 def test_fp32_m2l_forms_match_oracle(form, masked):
-    # 0: mutual, a lane per cell pair of a walk block, both sides combined across lanes;
-    # 1: directed, a warp per target cell over its source list (the default)
+    # 0: mutual, a lane per cell pair of a walk block, both sides combined across lanes (the default);
+    # 1: directed, a warp per target cell over its source list
     n = 6000
     pos, _, _ = _case("clustered", n)
     mass = ics.random_masses(n, 11)
