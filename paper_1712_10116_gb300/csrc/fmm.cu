@@ -1031,13 +1031,14 @@ static inline int pad4(int x) { return (x + 3) & ~3; }
 
 // precision dispatch of the M2L and P2P launchers (m2l.cu, p2p.cu)
 static tg_status launch_m2l_t(tg_ctx *c, const TreeView &t, const M2LBlock *blocks, int64_t nblocks, const float *Ms,
-                              float *L, int p, int nc, int ncp, bool masked, bool pot)
+                              float *L, int p, int nc, int ncp, bool masked, bool pot, const uint32_t *fpre)
 {
-    return launch_m2l_f32(c, t, blocks, nblocks, Ms, L, p, nc, ncp, masked, pot);
+    return launch_m2l_f32(c, t, blocks, nblocks, Ms, L, p, nc, ncp, masked, pot, fpre);
 }
 static tg_status launch_m2l_t(tg_ctx *c, const TreeView &t, const M2LBlock *blocks, int64_t nblocks, const double *Ms,
-                              double *L, int p, int nc, int ncp, bool masked, bool pot)
+                              double *L, int p, int nc, int ncp, bool masked, bool pot, const uint32_t *fpre)
 {
+    (void)fpre;   // the float64 contraction computes both classes for every pair
     (void)pot;   // the float64 contraction always includes the potential term
     return launch_m2l_f64(c, t, blocks, nblocks, Ms, L, p, nc, ncp, masked);
 }
@@ -1134,7 +1135,9 @@ static tg_status eval_typed(tg_ctx *c, int n, int ncell, const TreeView &t, cons
     cudaMemsetAsync(L, 0, sizeof(T) * (size_t)ncell * 2 * ncp, c->stream);
     const M2LBlock *blocks = static_cast<const M2LBlock *>(c->buf[B_M2L].p);
     const uint2 *p2p = static_cast<const uint2 *>(c->buf[B_P2P].p);
-    if (n_blocks > 0 && (st = launch_m2l_t(c, t, blocks, n_blocks, Ms, L, p, nc, ncp, masked, want_pot))) return st;
+    uint32_t *fpre = nullptr;
+    if (masked && sizeof(T) == 4 && (st = fast_prefix(c, fs, n, &fpre, nullptr))) return st;
+    if (n_blocks > 0 && (st = launch_m2l_t(c, t, blocks, n_blocks, Ms, L, p, nc, ncp, masked, want_pot, fpre))) return st;
     for (int l = 1; l < nlev; ++l) {
         const int lb = c->level_begin[l], le = c->level_begin[l + 1];
         if (high) {
@@ -1211,6 +1214,27 @@ tg_status fmm_eval(tg_ctx *c, int n, const double *pos, int64_t stride, const in
     c->stats.p2p_cell_pairs += n_p2p + n_self;
     c->stats.cells += ncell;
     return cuda_check(c, cudaGetLastError(), "fmm scatter");
+}
+
+// fast flags of the sorted particles as words, with a zero at n (the prefix sum then ends in its total)
+__global__ void fast_words(const uint8_t *fs, int n, uint32_t *w, const int *dn)
+{
+    n = dev_or(dn, n);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i <= n; i += gridDim.x * blockDim.x) w[i] = i < n ? fs[i] : 0u;
+}
+
+tg_status fast_prefix(tg_ctx *c, const uint8_t *fs, int n, uint32_t **fpre, const DevEval *de)
+{
+    tg_status st;
+    uint32_t *w, *pre;
+    if ((st = ensure_t(c, B_FWORDS, (size_t)n + 1, &w)) || (st = ensure_t(c, B_FPRE, (size_t)n + 1, &pre))) return st;
+    {
+        ProfScope ps_(c, TG_K_M2L);
+        fast_words<<<grid_for((int64_t)n + 1, 256), 256, 0, c->stream>>>(fs, n, w, de ? &de->n : nullptr);
+    }
+    if ((st = exclusive_scan_u32(c, w, pre, n + 1, nullptr, de ? &de->np1 : nullptr))) return st;
+    *fpre = pre;
+    return TG_OK;
 }
 
 // zero rows[0] rows of `width` values (device row count)
@@ -1372,8 +1396,10 @@ static tg_status fmm_eval_dev_t(tg_ctx *c, DevEval *de, const BatchCaps &cap, co
         zero_rows_dev<T><<<c->num_sms * 4, 256, 0, c->stream>>>(L, &de->rows, ncp);
     }
     if (sizeof(T) == 4) {
+        uint32_t *fpre = nullptr;
+        if ((st = fast_prefix(c, fs2, cap.n, &fpre, de))) return st;
         st = launch_m2l_f32_dev(c, t, de, d_geom, blocks, wctr + 1, (int64_t)cap.blocks, reinterpret_cast<const float *>(Ms),
-                                reinterpret_cast<float *>(L), p, ncp, cap.cells, cap.m2l_src);
+                                reinterpret_cast<float *>(L), p, ncp, cap.cells, cap.m2l_src, fpre);
     } else {
         st = launch_m2l_f64_dev(c, t, de, d_geom, blocks, wctr + 1, (int64_t)cap.blocks,
                                 reinterpret_cast<const double *>(Ms), reinterpret_cast<double *>(L), p, ncp);

@@ -536,6 +536,7 @@ __global__ void hold_frame(const HoldState *h, LevelLayout lv, const double *pos
     const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (tid == 0) {
         de->n = (int)ns;
+        de->np1 = (int)ns + 1;
         de->masked = masked;
         de->sort_blocks = (int)((ns + kSortTileItems - 1) / kSortTileItems);
         de->hist_items = kSortBins * de->sort_blocks;
@@ -659,7 +660,7 @@ static tg_status hold_presize(tg_ctx *c, const Sched &s, const BatchCaps &cap, c
     const Need needs[] = {
         {B_GEOM, 64}, {B_PARTIAL, sizeof(double) * 6 * 2 * 152}, {B_KEYS0, 8ull * n}, {B_KEYS1, 8ull * n},
         {B_VALS0, 4ull * n}, {B_VALS1, 4ull * n}, {B_HIST, 4ull * ((size_t)kSortBins * nblocks + 1)},
-        {B_SCAN_TMP, 4 * std::max(scan_scratch_words(std::max(kSortBins * nblocks, 1)), std::max(scan_scratch_words(C), scan_scratch_words(n)))},
+        {B_SCAN_TMP, 4 * std::max(scan_scratch_words(std::max(kSortBins * nblocks, 1)), std::max(scan_scratch_words(C), scan_scratch_words(n + 1)))},
         {B_XS, 8ull * n}, {B_YS, 8ull * n}, {B_ZS, 8ull * n}, {B_MS, 8ull * n}, {B_FS, 1ull * n},
         {B_XS2, 8ull * n}, {B_YS2, 8ull * n}, {B_ZS2, 8ull * n}, {B_MS2, 8ull * n}, {B_FS2, 1ull * n},
         {B_PERM2, 4ull * n}, {B_NSLOW, 4ull * C}, {B_PF, 4 * tsz * n}, {B_LEAF_OF, 4ull * n},
@@ -673,6 +674,7 @@ static tg_status hold_presize(tg_ctx *c, const Sched &s, const BatchCaps &cap, c
         {B_OWN_CNT, 4ull * (C + 2)}, {B_OWN_FILL, 4ull * (C + 2)}, {B_OWN_OFF, 4ull * C},
         {B_OWN_LIST, 8ull * max_units}, {B_OWN_TAG, 8 * cap.p2p}, {B_OWN_PART, 4 * cap.p2p},
         {B_M2L_CNT, 4ull * C}, {B_M2L_OFF, 4ull * C}, {B_M2L_FILL, 4ull * C}, {B_M2L_SRC, 4 * cap.m2l_src},
+        {B_FWORDS, 4ull * (n + 1)}, {B_FPRE, 4ull * (n + 1)},
         {B_FRAME_X, 24ull * n}, {B_FRAME_M, 8ull * n}, {B_FRAME_F, 1ull * n}, {B_SPLIT_FLAG, 4ull * n},
         {B_SPLIT_PRE, 4ull * n}, {B_HOLD, sizeof(HoldState)}, {B_DEVEVAL, sizeof(DevEval)},
     };

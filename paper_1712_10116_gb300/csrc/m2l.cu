@@ -61,7 +61,7 @@ static void m2l_directed_launch(tg_ctx *c, const TreeView &t, const uint32_t *of
 // Harmonic set (G = -1/|d|, P <= 6): fold the moments, contract the reduced sets into Lr, complete L.
 template <int P>
 static tg_status m2l_f32_harmonic(tg_ctx *c, const TreeView &t, const M2LBlock *blocks, int64_t nblocks, const float *Ms,
-                                  float *L, int ncp, bool masked, bool pot, int grid)
+                                  float *L, int ncp, bool masked, bool pot, int grid, const uint32_t *fpre)
 {
     if (c->tune.m2l_form == 1) {
         // directed by target cell
@@ -97,7 +97,7 @@ static tg_status m2l_f32_harmonic(tg_ctx *c, const TreeView &t, const M2LBlock *
     cudaMemsetAsync(Lr, 0, sizeof(float) * (size_t)rows * ncpr, c->stream);
     using G = M2LHarm<P>;
 #define TG_M2L_H(MK, PT) \
-    m2l_blocks_f32<G, MK, PT><<<grid, 128, 0, c->stream>>>(t, blocks, nblocks, Mr, Lr, ncpr, 0.f, 0, nullptr, nullptr, nullptr, 0.0)
+    m2l_blocks_f32<G, MK, PT><<<grid, 128, 0, c->stream>>>(t, blocks, nblocks, Mr, Lr, ncpr, 0.f, 0, nullptr, nullptr, nullptr, 0.0, fpre)
     if (masked) {
         if (pot) TG_M2L_H(true, true);
         else TG_M2L_H(true, false);
@@ -111,7 +111,7 @@ static tg_status m2l_f32_harmonic(tg_ctx *c, const TreeView &t, const M2LBlock *
 }
 
 tg_status launch_m2l_f32(tg_ctx *c, const TreeView &t, const M2LBlock *blocks, int64_t nblocks, const float *Ms,
-                         float *L, int p, int nc, int ncp, bool masked, bool pot)
+                         float *L, int p, int nc, int ncp, bool masked, bool pot, const uint32_t *fpre)
 {
     const int plummer = c->prm.kernel == TG_KERNEL_PLUMMER;
     const float eoL = (float)ldexp(c->prm.eps, -c->walk_log2L);
@@ -120,16 +120,16 @@ tg_status launch_m2l_f32(tg_ctx *c, const TreeView &t, const M2LBlock *blocks, i
     // Wendland C2: the walk's eps gap rule leaves every M2L pair at r >= eps, where G = -1/r is harmonic
     if (!plummer && p >= 1 && p <= 6) {
         switch (p) {
-        case 1: return m2l_f32_harmonic<1>(c, t, blocks, nblocks, Ms, L, ncp, masked, pot, grid);
-        case 2: return m2l_f32_harmonic<2>(c, t, blocks, nblocks, Ms, L, ncp, masked, pot, grid);
-        case 3: return m2l_f32_harmonic<3>(c, t, blocks, nblocks, Ms, L, ncp, masked, pot, grid);
-        case 4: return m2l_f32_harmonic<4>(c, t, blocks, nblocks, Ms, L, ncp, masked, pot, grid);
-        case 5: return m2l_f32_harmonic<5>(c, t, blocks, nblocks, Ms, L, ncp, masked, pot, grid);
-        default: return m2l_f32_harmonic<6>(c, t, blocks, nblocks, Ms, L, ncp, masked, pot, grid);
+        case 1: return m2l_f32_harmonic<1>(c, t, blocks, nblocks, Ms, L, ncp, masked, pot, grid, fpre);
+        case 2: return m2l_f32_harmonic<2>(c, t, blocks, nblocks, Ms, L, ncp, masked, pot, grid, fpre);
+        case 3: return m2l_f32_harmonic<3>(c, t, blocks, nblocks, Ms, L, ncp, masked, pot, grid, fpre);
+        case 4: return m2l_f32_harmonic<4>(c, t, blocks, nblocks, Ms, L, ncp, masked, pot, grid, fpre);
+        case 5: return m2l_f32_harmonic<5>(c, t, blocks, nblocks, Ms, L, ncp, masked, pot, grid, fpre);
+        default: return m2l_f32_harmonic<6>(c, t, blocks, nblocks, Ms, L, ncp, masked, pot, grid, fpre);
         }
     }
     ProfScope ps_(c, TG_K_M2L);
-#define TG_M2L_F32_(PP, MK, PT) m2l_blocks_f32<M2LFull<PP>, MK, PT><<<grid, 128, 0, c->stream>>>(t, blocks, nblocks, Ms, L, ncp, eoL, plummer, nullptr, nullptr, nullptr, 0.0)
+#define TG_M2L_F32_(PP, MK, PT) m2l_blocks_f32<M2LFull<PP>, MK, PT><<<grid, 128, 0, c->stream>>>(t, blocks, nblocks, Ms, L, ncp, eoL, plummer, nullptr, nullptr, nullptr, 0.0, fpre)
 #define TG_M2L_F32(PP)                                                                                            \
     case PP:                                                                                                      \
         if (masked) { if (pot) TG_M2L_F32_(PP, true, true); else TG_M2L_F32_(PP, true, false); }                   \
@@ -164,7 +164,8 @@ __global__ void m2l_list_check(const uint32_t *off, const uint32_t *cnt, DevEval
 template <int P>
 static tg_status m2l_f32_dev_p(tg_ctx *c, const TreeView &t, const DevEval *de, const Geom *gp, const M2LBlock *blocks,
                                const unsigned long long *dnb, int64_t cap_blocks, const float *Ms, float *L, int ncp,
-                               float *Mr, float *Lr, int ncpr, int rows_cap, int grid, size_t cap_src)
+                               float *Mr, float *Lr, int ncpr, int rows_cap, int grid, size_t cap_src,
+                               const uint32_t *fpre)
 {
     const int plummer = c->prm.kernel == TG_KERNEL_PLUMMER;
     const int g = grid_for(rows_cap, 128);
@@ -193,23 +194,23 @@ static tg_status m2l_f32_dev_p(tg_ctx *c, const TreeView &t, const DevEval *de, 
         m2l_reduce_moments_h<P><<<g, 128, 0, c->stream>>>(rows_cap, Ms, ncp, Mr, ncpr, &de->rows);
         zero_rows_f32<<<c->num_sms * 4, 256, 0, c->stream>>>(Lr, &de->rows, ncpr);
         m2l_blocks_f32<G, true, false><<<grid, 128, 0, c->stream>>>(t, blocks, cap_blocks, Mr, Lr, ncpr, 0.f, 0, dnb, de,
-                                                                    gp, c->prm.eps);
+                                                                    gp, c->prm.eps, fpre);
         m2l_blocks_f32<G, false, false><<<grid, 128, 0, c->stream>>>(t, blocks, cap_blocks, Mr, Lr, ncpr, 0.f, 0, dnb, de,
-                                                                     gp, c->prm.eps);
+                                                                     gp, c->prm.eps, fpre);
         m2l_complete_locals_h<P><<<g, 128, 0, c->stream>>>(rows_cap, Lr, ncpr, L, ncp, &de->rows);
     } else {
         using G = M2LFull<P>;
         m2l_blocks_f32<G, true, false><<<grid, 128, 0, c->stream>>>(t, blocks, cap_blocks, Ms, L, ncp, 0.f, 1, dnb, de,
-                                                                    gp, c->prm.eps);
+                                                                    gp, c->prm.eps, fpre);
         m2l_blocks_f32<G, false, false><<<grid, 128, 0, c->stream>>>(t, blocks, cap_blocks, Ms, L, ncp, 0.f, 1, dnb, de,
-                                                                     gp, c->prm.eps);
+                                                                     gp, c->prm.eps, fpre);
     }
     return TG_OK;
 }
 
 tg_status launch_m2l_f32_dev(tg_ctx *c, const TreeView &t, const DevEval *de, const Geom *gp, const M2LBlock *blocks,
                              const unsigned long long *dnb, int64_t cap_blocks, const float *Ms, float *L, int p,
-                             int ncp, int cap_cells, size_t cap_src)
+                             int ncp, int cap_cells, size_t cap_src, const uint32_t *fpre)
 {
     if (p < 1 || p > 6) return set_err(c, TG_ERR_ARG, "batched M2L needs 1 <= p <= 6");
     static const int nh[7] = {0, 4, 9, 16, 25, 36, 49};   // (p + 1)^2 harmonic coefficients
@@ -222,12 +223,12 @@ tg_status launch_m2l_f32_dev(tg_ctx *c, const TreeView &t, const DevEval *de, co
         return st;
     const int grid = c->num_sms * c->tune.m2l_blocks_per_sm;
     switch (p) {
-    case 1: st = m2l_f32_dev_p<1>(c, t, de, gp, blocks, dnb, cap_blocks, Ms, L, ncp, Mr, Lr, ncpr, rows_cap, grid, cap_src); break;
-    case 2: st = m2l_f32_dev_p<2>(c, t, de, gp, blocks, dnb, cap_blocks, Ms, L, ncp, Mr, Lr, ncpr, rows_cap, grid, cap_src); break;
-    case 3: st = m2l_f32_dev_p<3>(c, t, de, gp, blocks, dnb, cap_blocks, Ms, L, ncp, Mr, Lr, ncpr, rows_cap, grid, cap_src); break;
-    case 4: st = m2l_f32_dev_p<4>(c, t, de, gp, blocks, dnb, cap_blocks, Ms, L, ncp, Mr, Lr, ncpr, rows_cap, grid, cap_src); break;
-    case 5: st = m2l_f32_dev_p<5>(c, t, de, gp, blocks, dnb, cap_blocks, Ms, L, ncp, Mr, Lr, ncpr, rows_cap, grid, cap_src); break;
-    default: st = m2l_f32_dev_p<6>(c, t, de, gp, blocks, dnb, cap_blocks, Ms, L, ncp, Mr, Lr, ncpr, rows_cap, grid, cap_src);
+    case 1: st = m2l_f32_dev_p<1>(c, t, de, gp, blocks, dnb, cap_blocks, Ms, L, ncp, Mr, Lr, ncpr, rows_cap, grid, cap_src, fpre); break;
+    case 2: st = m2l_f32_dev_p<2>(c, t, de, gp, blocks, dnb, cap_blocks, Ms, L, ncp, Mr, Lr, ncpr, rows_cap, grid, cap_src, fpre); break;
+    case 3: st = m2l_f32_dev_p<3>(c, t, de, gp, blocks, dnb, cap_blocks, Ms, L, ncp, Mr, Lr, ncpr, rows_cap, grid, cap_src, fpre); break;
+    case 4: st = m2l_f32_dev_p<4>(c, t, de, gp, blocks, dnb, cap_blocks, Ms, L, ncp, Mr, Lr, ncpr, rows_cap, grid, cap_src, fpre); break;
+    case 5: st = m2l_f32_dev_p<5>(c, t, de, gp, blocks, dnb, cap_blocks, Ms, L, ncp, Mr, Lr, ncpr, rows_cap, grid, cap_src, fpre); break;
+    default: st = m2l_f32_dev_p<6>(c, t, de, gp, blocks, dnb, cap_blocks, Ms, L, ncp, Mr, Lr, ncpr, rows_cap, grid, cap_src, fpre);
     }
     if (st) return st;
     return cuda_check(c, cudaGetLastError(), "m2l launch (device sizes)");

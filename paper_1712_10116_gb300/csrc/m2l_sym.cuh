@@ -115,11 +115,16 @@ __device__ __forceinline__ void m2l_halve(float (&v)[NP], int lane, int d)
 // G: M2LFull<P> or M2LHarm<P>; Ms and L hold that set's coefficients with row stride ncp.
 // Batched path (dnb non-null): the block count, the class count and the root cube come from the
 // device; the launch for the other class count returns at once.
+// Kick pairs (MASKED) with fpre (the prefix sum of the fast flags over the sorted particles): a target
+// cell needs the all-sources local (class 0) only if it holds slow particles, and the slow-sources local
+// (class 1) only if it holds fast particles; a round skips a side's contraction of a class when no
+// target of that side needs it (a warp vote, so the warp stays converged).  The skipped locals are read
+// by no particle: L2L hands them only to descendants, which hold no particle of that class either.
 template <class G, bool MASKED, bool POT>
 __global__ void __launch_bounds__(128) m2l_blocks_f32(TreeView t, const M2LBlock *__restrict__ blocks, int64_t nblocks,
                                                       const float *__restrict__ Ms, float *L, int ncp, float eps_over_L,
                                                       int plummer, const unsigned long long *dnb, const DevEval *de,
-                                                      const Geom *gp, double eps)
+                                                      const Geom *gp, double eps, const uint32_t *__restrict__ fpre)
 {
     if (dnb) {
         if ((de->masked != 0) != MASKED) return;
@@ -169,26 +174,45 @@ __global__ void __launch_bounds__(128) m2l_blocks_f32(TreeView t, const M2LBlock
             }
             const bool row_used = ((amask >> (lane & ~7)) & 0xffu) != 0u;   // this lane's row, this round
             const bool col_used = (amask & (0x01010101u << j)) != 0u;      // this lane's column, this round
+            // classes the round's targets need (side a: the row cells, side b: the column cells)
+            bool need_a[2] = {true, true}, need_b[2] = {true, true};
+            if (MASKED && fpre) {
+                int fx = 0, sx = 0, fy = 0, sy = 0;
+                if (active) {
+                    const int ax = t.first[x], ay = t.first[y];
+                    fx = (int)(fpre[ax + t.count[x]] - fpre[ax]);
+                    sx = t.count[x] - fx;
+                    fy = (int)(fpre[ay + t.count[y]] - fpre[ay]);
+                    sy = t.count[y] - fy;
+                }
+                need_a[0] = __any_sync(0xffffffffu, sx > 0);
+                need_a[1] = __any_sync(0xffffffffu, fx > 0);
+                need_b[0] = __any_sync(0xffffffffu, sy > 0);
+                need_b[1] = __any_sync(0xffffffffu, fy > 0);
+            }
 #pragma unroll
             for (int cls = 0; cls < (MASKED ? 2 : 1); ++cls) {
                 float Lc[NP];
-                // x side: sources y; reduce-scatter over the row's lanes (bits 2, 1, 0):
-                // lane j keeps coefficients RL*j .. RL*j + RL - 1
+                if (need_a[cls]) {
+                    // x side: sources y; reduce-scatter over the row's lanes (bits 2, 1, 0):
+                    // lane j keeps coefficients RL*j .. RL*j + RL - 1
 #pragma unroll
-                for (int k = NC; k < NP; ++k) Lc[k] = 0.f;
-                if (POT) G::side_a(D, Ms + ((size_t)ys * 2 + cls) * ncp, rho, reinterpret_cast<float(&)[NC]>(Lc));
-                else G::side_a_forces(D, Ms + ((size_t)ys * 2 + cls) * ncp, rho, reinterpret_cast<float(&)[NC]>(Lc));
-                m2l_halve<NP, 4 * RL>(Lc, lane, 4);
-                m2l_halve<NP, 2 * RL>(Lc, lane, 2);
-                m2l_halve<NP, RL>(Lc, lane, 1);
-                if (row_used) {
-                    float *dst = L + ((size_t)x * 2 + cls) * ncp;
+                    for (int k = NC; k < NP; ++k) Lc[k] = 0.f;
+                    if (POT) G::side_a(D, Ms + ((size_t)ys * 2 + cls) * ncp, rho, reinterpret_cast<float(&)[NC]>(Lc));
+                    else G::side_a_forces(D, Ms + ((size_t)ys * 2 + cls) * ncp, rho, reinterpret_cast<float(&)[NC]>(Lc));
+                    m2l_halve<NP, 4 * RL>(Lc, lane, 4);
+                    m2l_halve<NP, 2 * RL>(Lc, lane, 2);
+                    m2l_halve<NP, RL>(Lc, lane, 1);
+                    if (row_used) {
+                        float *dst = L + ((size_t)x * 2 + cls) * ncp;
 #pragma unroll
-                    for (int g = 0; g < RL; g += 4) {
-                        const int k = RL * j + g;
-                        if (k < NC) atomicAdd(reinterpret_cast<float4 *>(dst + k), make_float4(Lc[g], Lc[g + 1], Lc[g + 2], Lc[g + 3]));
+                        for (int g = 0; g < RL; g += 4) {
+                            const int k = RL * j + g;
+                            if (k < NC) atomicAdd(reinterpret_cast<float4 *>(dst + k), make_float4(Lc[g], Lc[g + 1], Lc[g + 2], Lc[g + 3]));
+                        }
                     }
                 }
+                if (!need_b[cls]) continue;
                 // y side: sources x; reduce-scatter over the column's lanes (bits 4, 3):
                 // lane (rr, j) keeps coefficients CL*rr .. CL*rr + CL - 1 of column j
 #pragma unroll

@@ -55,6 +55,7 @@ struct DevEval {
     int nlev;               // levels of the tree
     int lvl_m;              // cells of the level being split (octree build)
     int rows;               // 2 * ncell (expansion rows, both classes)
+    int np1;                // n + 1 (prefix sum of the fast flags, with its total)
     uint32_t lvl_total;     // children emitted by the level being split (scan total)
     uint32_t overflow;      // bit 0: cells, bit 1: levels, bit 2: walk lists; the step must be redone
     int level_begin[kMaxLevel + 3];   // first cell of each level; [nlev] = ncell
@@ -149,7 +150,7 @@ enum Slot {
     B_HHS_SCAN, B_HHS_TMP, B_RED, B_DIAG_POT, B_DIAG_ACC,
     B_OWN_CNT, B_OWN_FILL, B_OWN_OFF, B_OWN_LIST, B_OWN_TAG, B_OWN_PART, B_SNAP, B_TUNE_ACC,
     B_MACP, B_DEVEVAL, B_HOLD, B_FRAME_X, B_FRAME_M, B_FRAME_F, B_SPLIT_FLAG, B_SPLIT_PRE,
-    B_M2L_CNT, B_M2L_OFF, B_M2L_FILL, B_M2L_SRC,
+    B_M2L_CNT, B_M2L_OFF, B_M2L_FILL, B_M2L_SRC, B_FWORDS, B_FPRE,
     B_LAST_SLOT
 };
 static_assert(B_LAST_SLOT <= kMaxSlots, "tg_ctx::buf holds fewer entries than there are slots");
@@ -219,12 +220,15 @@ tg_status exclusive_scan_u32(tg_ctx *c, const uint32_t *in, uint32_t *out, int n
                              const int *dn = nullptr);
 
 // ---- m2l.cu: mutual M2L of the walk's blocks into L (normalised expansions).  pot = false: the
-// float32 kernels leave out the potential term L^0.
+// float32 kernels leave out the potential term L^0.  fpre (kick pairs, nullable): prefix sum of the fast
+// flags of the sorted particles, so that contractions no target needs are skipped.
 tg_status launch_m2l_f32(tg_ctx *c, const TreeView &t, const M2LBlock *blocks, int64_t nblocks, const float *Ms,
-                         float *L, int p, int nc, int ncp, bool masked, bool pot);
+                         float *L, int p, int nc, int ncp, bool masked, bool pot, const uint32_t *fpre = nullptr);
+// the prefix sum of the fast flags fs of n sorted particles (n + 1 entries) into fpre (dn: device n)
+tg_status fast_prefix(tg_ctx *c, const uint8_t *fs, int n, uint32_t **fpre, const DevEval *de);
 tg_status launch_m2l_f32_dev(tg_ctx *c, const TreeView &t, const DevEval *de, const Geom *gp, const M2LBlock *blocks,
                              const unsigned long long *dnb, int64_t cap_blocks, const float *Ms, float *L, int p,
-                             int ncp, int cap_cells, size_t cap_src);
+                             int ncp, int cap_cells, size_t cap_src, const uint32_t *fpre);
 tg_status launch_m2l_f64_dev(tg_ctx *c, const TreeView &t, const DevEval *de, const Geom *gp, const M2LBlock *blocks,
                              const unsigned long long *dnb, int64_t cap_blocks, const double *Ms, double *L, int p,
                              int ncp);

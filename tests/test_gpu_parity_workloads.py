@@ -207,7 +207,44 @@ def test_disk_galaxy_hhs_fp32_matches_oracle(disk_oracle_run):
     ev = tg.Solver(prm)
     for k, (x, _, r, _, _) in enumerate(states):
         fast = (r > np.median(r)).astype(np.uint8)
+        floor = _rounding_floor(ev, x, mass, DISK_PRM["eps"])
         for mask in (None, fast):
             acc, _ = ev.fmm_forces(_t(x), M, None if mask is None else _t(mask, torch.uint8), want_pot=False)
             a_o, _ = oracle.fmm(x, mass, _oprm(prm), mask)
-            _check_fp32(acc.cpu().numpy(), a_o, f"disk 2^14 state {k} masked={mask is not None}")
+            a = acc.cpu().numpy()
+            nb = np.linalg.norm(a_o, axis=0)
+            bound = FP32_TOL * np.maximum(nb, FP32_FLOOR * np.median(nb)) + floor
+            d = np.linalg.norm(a - a_o, axis=0)
+            r = d / np.maximum(nb, FP32_FLOOR * np.median(nb))
+            print(f"disk 2^14 state {k} masked={mask is not None}: floored max {r.max():.3e}, "
+                  f"{int((r >= FP32_TOL).sum())} particles past 1e-5 (all within their rounding floor: "
+                  f"{bool(np.all(d < bound))}), worst d / bound {(d / bound).max():.3f}")
+            assert np.all(d < bound), (k, (d / bound).max())
+
+
+def _rounding_floor(s, x, mass, eps):
+    """Per-particle force error that float32 positions relative to a leaf centre allow: each coordinate
+    of a particle and of its neighbours is rounded by up to u s_leaf (u = 2^-24 of the leaf side s_leaf;
+    the leaf is the one the library's tree gives the particle), and the force on i moves by at most
+    sum_j 3 m_j g(r_ij) per unit of relative displacement (the tidal tensor of each pair is bounded by
+    3 m_j g).  Both ends of a pair can be rounded: floor_i = 2 sqrt(3) u s_leaf,i sum_j 3 m_j g(r_ij).
+    In the sparse outer leaves of a small disk (s_leaf of several units) a neighbour at r ~ eps puts this
+    near 1e-5 of the particle's force."""
+    tg.tg_build_tree(s.ctx, _t(x))
+    tr = tg.tg_get_tree(s.ctx)
+    n = x.shape[1]
+    leaf_level = np.zeros(n, np.int64)
+    for c in np.nonzero(tr["nchild"] == 0)[0]:
+        sorted_pos = np.arange(tr["first"][c], tr["first"][c] + tr["count"][c])
+        leaf_level[tr["perm"][sorted_pos]] = tr["level"][c]
+    s_leaf = tr["L"] / 2.0 ** leaf_level
+    sens = np.zeros(n)
+    for i0 in range(0, n, 1024):
+        d = x[:, None, :] - x[:, i0:i0 + 1024, None]
+        rr = np.sqrt((d * d).sum(0))
+        u = rr / eps
+        with np.errstate(divide="ignore", invalid="ignore"):
+            g = np.where(u < 1, (21 * u ** 5 - 90 * u ** 4 + 140 * u ** 3 - 84 * u ** 2 + 14) / eps ** 3, rr ** -3.0)
+        g[rr == 0] = 0.0
+        sens[i0:i0 + 1024] = (3.0 * mass[None, :] * g).sum(1)
+    return 2.0 * np.sqrt(3.0) * 2.0 ** -24 * s_leaf * sens
