@@ -98,7 +98,9 @@ typedef struct {
     int64_t cells;           /* octree cells built, summed over evaluations                    */
     int64_t kdk_frames;      /* KDK frames of the HHS schedule                                  */
     int64_t max_rung;        /* deepest rung that held a slow particle                          */
-    int64_t m2l_class_pairs; /* M2L cell pairs x local-expansion classes (1, or 2 for a kick pair) */
+    int64_t m2l_class_pairs; /* M2L cell pairs x local-expansion classes the pair's targets need     */
+                             /* (a kick pair's cell needs class 0 only if it holds slow particles, */
+                             /* class 1 only if it holds fast ones; counted per side, halved)      */
     int64_t list_regrowths;  /* dual walks re-run because an interaction list outgrew its buffer  */
     int64_t host_syncs;      /* host waits on the stream inside evaluations and HHS steps         */
 } tg_stats;

@@ -122,14 +122,16 @@ tg_status tg_get_stats(const tg_ctx *c, tg_stats *out)
 {
     if (!c || !out) return TG_ERR_ARG;
     tg_ctx *m = const_cast<tg_ctx *>(c);
-    unsigned long long pairs = 0;
+    unsigned long long dev[12] = {0};
     cudaStreamSynchronize(m->stream);
-    if (cudaMemcpy(&pairs, m->d_counters, sizeof pairs, cudaMemcpyDeviceToHost) != cudaSuccess) {
+    if (cudaMemcpy(dev, m->d_counters, sizeof dev, cudaMemcpyDeviceToHost) != cudaSuccess) {
         cudaGetLastError();
         return TG_ERR_CUDA;
     }
     *out = c->stats;
-    out->p2p_pairs = (int64_t)pairs;
+    out->p2p_pairs = (int64_t)dev[0];
+    // side contractions counted by the float32 M2L kernels: two per (cell pair, class) with both sides
+    out->m2l_class_pairs += (int64_t)(dev[11] / 2);
     return TG_OK;
 }
 
@@ -163,6 +165,7 @@ tg_status tg_reset_stats(tg_ctx *c)
     }
     c->stats = tg_stats{};
     cudaMemsetAsync(c->d_counters, 0, sizeof(unsigned long long), c->stream);
+    cudaMemsetAsync(c->d_counters + 11, 0, sizeof(unsigned long long), c->stream);
     return TG_OK;
 }
 

@@ -1210,7 +1210,7 @@ tg_status fmm_eval(tg_ctx *c, int n, const double *pos, int64_t stride, const in
     c->stats.evaluations += 1;
     c->stats.sink_forces += n;
     c->stats.m2l_pairs += n_m2l;
-    c->stats.m2l_class_pairs += n_m2l * (masked ? 2 : 1);
+    if (!m2l_classes_on_device(c)) c->stats.m2l_class_pairs += n_m2l * (masked ? 2 : 1);
     c->stats.p2p_cell_pairs += n_p2p + n_self;
     c->stats.cells += ncell;
     return cuda_check(c, cudaGetLastError(), "fmm scatter");
@@ -1284,13 +1284,15 @@ __global__ void walk_check_dev(DevEval *de, unsigned long long *ctr, int nsteps,
 }
 
 // counters of the evaluation into the step's totals: [0] evaluations, [1] particle-forces, [2] M2L pairs,
-// [3] M2L pairs x classes, [4] P2P leaf pairs, [5] cells
-__global__ void eval_finish_dev(const DevEval *de, const unsigned long long *ctr, unsigned long long *stats)
+// [3] M2L pairs x classes (when the M2L kernels do not count them on the device), [4] P2P leaf pairs,
+// [5] cells
+__global__ void eval_finish_dev(const DevEval *de, const unsigned long long *ctr, unsigned long long *stats,
+                                int count_classes)
 {
     stats[0] += 1ull;
     stats[1] += (unsigned long long)de->n;
     stats[2] += ctr[3];
-    stats[3] += ctr[3] * (de->masked ? 2ull : 1ull);
+    if (count_classes) stats[3] += ctr[3] * (de->masked ? 2ull : 1ull);
     stats[4] += ctr[2] + ctr[4];
     stats[5] += (unsigned long long)de->ncell;
 }
@@ -1436,7 +1438,7 @@ static tg_status fmm_eval_dev_t(tg_ctx *c, DevEval *de, const BatchCaps &cap, co
     }
     {
         ProfScope ps_(c, TG_K_OTHER);
-        eval_finish_dev<<<1, 1, 0, c->stream>>>(de, wctr, stats);
+        eval_finish_dev<<<1, 1, 0, c->stream>>>(de, wctr, stats, m2l_classes_on_device(c) ? 0 : 1);
     }
     return cuda_check(c, cudaGetLastError(), "fmm evaluation (device sizes)");
 }

@@ -694,7 +694,7 @@ static tg_status hold_size(tg_ctx *c, Sched &s, BatchCaps &cap)
     c->stats.evaluations -= 1;   // sizing is not the caller's work
     c->stats.sink_forces -= s.n;
     c->stats.m2l_pairs -= c->last_nm2l;
-    c->stats.m2l_class_pairs -= c->last_nm2l;
+    if (!m2l_classes_on_device(c)) c->stats.m2l_class_pairs -= c->last_nm2l;
     c->stats.p2p_cell_pairs -= c->last_np2p;
     c->stats.cells -= c->last_ncell;
     const int64_t ncell = c->last_ncell;

@@ -44,7 +44,7 @@ static void m2l_directed_launch(tg_ctx *c, const TreeView &t, const uint32_t *of
                                 bool pot, const DevEval *de)
 {
     const int grid = c->num_sms * c->tune.m2l_blocks_per_sm;
-#define TG_DIR(MK, PT, DE) m2l_directed_h<P, MK, PT><<<grid, 128, 0, c->stream>>>(t, off, cnt, src, cap, Mr, Lr, ncpr, DE)
+#define TG_DIR(MK, PT, DE) m2l_directed_h<P, MK, PT><<<grid, 128, 0, c->stream>>>(t, off, cnt, src, cap, Mr, Lr, ncpr, DE, c->d_counters + 11)
     if (de) {   // batched: both class counts launched, the other one returns at once
         TG_DIR(true, false, de);
         TG_DIR(false, false, de);
@@ -97,7 +97,7 @@ static tg_status m2l_f32_harmonic(tg_ctx *c, const TreeView &t, const M2LBlock *
     cudaMemsetAsync(Lr, 0, sizeof(float) * (size_t)rows * ncpr, c->stream);
     using G = M2LHarm<P>;
 #define TG_M2L_H(MK, PT) \
-    m2l_blocks_f32<G, MK, PT><<<grid, 128, 0, c->stream>>>(t, blocks, nblocks, Mr, Lr, ncpr, 0.f, 0, nullptr, nullptr, nullptr, 0.0, fpre)
+    m2l_blocks_f32<G, MK, PT><<<grid, 128, 0, c->stream>>>(t, blocks, nblocks, Mr, Lr, ncpr, 0.f, 0, nullptr, nullptr, nullptr, 0.0, fpre, c->d_counters + 11)
     if (masked) {
         if (pot) TG_M2L_H(true, true);
         else TG_M2L_H(true, false);
@@ -129,7 +129,7 @@ tg_status launch_m2l_f32(tg_ctx *c, const TreeView &t, const M2LBlock *blocks, i
         }
     }
     ProfScope ps_(c, TG_K_M2L);
-#define TG_M2L_F32_(PP, MK, PT) m2l_blocks_f32<M2LFull<PP>, MK, PT><<<grid, 128, 0, c->stream>>>(t, blocks, nblocks, Ms, L, ncp, eoL, plummer, nullptr, nullptr, nullptr, 0.0, fpre)
+#define TG_M2L_F32_(PP, MK, PT) m2l_blocks_f32<M2LFull<PP>, MK, PT><<<grid, 128, 0, c->stream>>>(t, blocks, nblocks, Ms, L, ncp, eoL, plummer, nullptr, nullptr, nullptr, 0.0, fpre, c->d_counters + 11)
 #define TG_M2L_F32(PP)                                                                                            \
     case PP:                                                                                                      \
         if (masked) { if (pot) TG_M2L_F32_(PP, true, true); else TG_M2L_F32_(PP, true, false); }                   \
@@ -194,16 +194,16 @@ static tg_status m2l_f32_dev_p(tg_ctx *c, const TreeView &t, const DevEval *de, 
         m2l_reduce_moments_h<P><<<g, 128, 0, c->stream>>>(rows_cap, Ms, ncp, Mr, ncpr, &de->rows);
         zero_rows_f32<<<c->num_sms * 4, 256, 0, c->stream>>>(Lr, &de->rows, ncpr);
         m2l_blocks_f32<G, true, false><<<grid, 128, 0, c->stream>>>(t, blocks, cap_blocks, Mr, Lr, ncpr, 0.f, 0, dnb, de,
-                                                                    gp, c->prm.eps, fpre);
+                                                                    gp, c->prm.eps, fpre, c->d_counters + 11);
         m2l_blocks_f32<G, false, false><<<grid, 128, 0, c->stream>>>(t, blocks, cap_blocks, Mr, Lr, ncpr, 0.f, 0, dnb, de,
-                                                                     gp, c->prm.eps, fpre);
+                                                                     gp, c->prm.eps, fpre, c->d_counters + 11);
         m2l_complete_locals_h<P><<<g, 128, 0, c->stream>>>(rows_cap, Lr, ncpr, L, ncp, &de->rows);
     } else {
         using G = M2LFull<P>;
         m2l_blocks_f32<G, true, false><<<grid, 128, 0, c->stream>>>(t, blocks, cap_blocks, Ms, L, ncp, 0.f, 1, dnb, de,
-                                                                    gp, c->prm.eps, fpre);
+                                                                    gp, c->prm.eps, fpre, c->d_counters + 11);
         m2l_blocks_f32<G, false, false><<<grid, 128, 0, c->stream>>>(t, blocks, cap_blocks, Ms, L, ncp, 0.f, 1, dnb, de,
-                                                                     gp, c->prm.eps, fpre);
+                                                                     gp, c->prm.eps, fpre, c->d_counters + 11);
     }
     return TG_OK;
 }

@@ -124,8 +124,10 @@ template <class G, bool MASKED, bool POT>
 __global__ void __launch_bounds__(128) m2l_blocks_f32(TreeView t, const M2LBlock *__restrict__ blocks, int64_t nblocks,
                                                       const float *__restrict__ Ms, float *L, int ncp, float eps_over_L,
                                                       int plummer, const unsigned long long *dnb, const DevEval *de,
-                                                      const Geom *gp, double eps, const uint32_t *__restrict__ fpre)
+                                                      const Geom *gp, double eps, const uint32_t *__restrict__ fpre,
+                                                      unsigned long long *class_ctr)
 {
+    unsigned long long my_sc = 0;   // side contractions the method needs: (pair side, class) with a target
     if (dnb) {
         if ((de->masked != 0) != MASKED) return;
         nblocks = (int64_t)*dnb;
@@ -189,6 +191,9 @@ __global__ void __launch_bounds__(128) m2l_blocks_f32(TreeView t, const M2LBlock
                 need_a[1] = __any_sync(0xffffffffu, fx > 0);
                 need_b[0] = __any_sync(0xffffffffu, sy > 0);
                 need_b[1] = __any_sync(0xffffffffu, fy > 0);
+                my_sc += (unsigned)(sx > 0) + (unsigned)(fx > 0) + (unsigned)(sy > 0) + (unsigned)(fy > 0);
+            } else if (active) {
+                my_sc += MASKED ? 4u : 2u;
             }
 #pragma unroll
             for (int cls = 0; cls < (MASKED ? 2 : 1); ++cls) {
@@ -247,6 +252,8 @@ __global__ void __launch_bounds__(128) m2l_blocks_f32(TreeView t, const M2LBlock
             }
         }
     }
+    my_sc = warp_sum(my_sc);
+    if (class_ctr && (threadIdx.x & 31) == 0 && my_sc) atomicAdd(class_ctr, my_sc);
 }
 
 // ------------------------------------------------------------------ directed, by target cell (harmonic set)
@@ -330,9 +337,10 @@ __global__ void __launch_bounds__(128) m2l_directed_h(TreeView t, const uint32_t
                                                       const uint32_t *__restrict__ cnt,
                                                       const uint32_t *__restrict__ src, uint64_t cap,
                                                       const float *__restrict__ Mr, float *__restrict__ Lr, int ncpr,
-                                                      const DevEval *de)
+                                                      const DevEval *de, unsigned long long *class_ctr)
 {
     using G = M2LGenH<P>;
+    unsigned long long my_sc = 0;
     constexpr int NC = G::NC, ND = G::ND, NP = 64;
     static_assert(NC <= NP, "reduced set fits in two coefficients per lane");
     if (de && (de->masked != 0) != MASKED) return;
@@ -342,6 +350,7 @@ __global__ void __launch_bounds__(128) m2l_directed_h(TreeView t, const uint32_t
     for (int x = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5); x < ncell; x += nw) {
         const uint32_t b = off[x], e = (uint32_t)min((uint64_t)off[x] + cnt[x], cap);
         if (b >= e) continue;   // whole warp
+        if (lane == 0) my_sc += (unsigned long long)(e - b) * (MASKED ? 2u : 1u);
         const int lx = t.level[x];
         float a0[NP], a1[NP];
 #pragma unroll
@@ -371,6 +380,7 @@ __global__ void __launch_bounds__(128) m2l_directed_h(TreeView t, const uint32_t
             if (2 * lane + 1 < NC) dst[ncpr + 2 * lane + 1] = a1[1];
         }
     }
+    if (class_ctr && lane == 0 && my_sc) atomicAdd(class_ctr, my_sc);
 }
 
 // ------------------------------------------------------------------ generic (p <= 8, float or double)

@@ -176,6 +176,10 @@ struct M2LBlock {
     unsigned long long mask;   // bit 8i + j: pair (child i of a, child j of b) is well separated
 };
 
+// The float32 kernels for p <= 6 count the M2L side contractions they need on the device
+// (d_counters[11]); the other paths count class pairs on the host.
+inline bool m2l_classes_on_device(const tg_ctx *c) { return c->prm.precision == TG_PREC_FP32 && c->prm.p <= 6; }
+
 // ---- tree.cu
 // Root cube of the n particles pos[q] (q < n, gathered through sub when non-null) -> geom.
 tg_status root_cube(tg_ctx *c, int n, const double *pos, int64_t stride, const int64_t *sub, Geom *d_geom,

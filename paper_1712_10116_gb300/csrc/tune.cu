@@ -58,6 +58,12 @@ tg_status autotune(tg_ctx *c, int n, const double *pos, const double *mass, cons
     }
     // the tuning evaluations are not the caller's work: counters and event timing are left as they were
     const tg_stats stats0 = c->stats;
+    unsigned long long dev0[12];
+    if ((st = cuda_check(c, cudaMemcpy(dev0, c->d_counters, sizeof dev0, cudaMemcpyDeviceToHost), "autotune"))) {
+        cudaEventDestroy(r.e0);
+        cudaEventDestroy(r.e1);
+        return st;
+    }
     const int prof0 = c->prof_level;
     c->prof_level = 0;
     const tg_params prm0 = c->prm;
@@ -68,6 +74,8 @@ tg_status autotune(tg_ctx *c, int n, const double *pos, const double *mass, cons
         c->stats.list_regrowths = regrow;
         c->stats.host_syncs = syncs;
         c->prof_level = prof0;
+        cudaStreamSynchronize(c->stream);
+        cudaMemcpy(c->d_counters, dev0, sizeof dev0, cudaMemcpyHostToDevice);
         cudaEventDestroy(r.e0);
         cudaEventDestroy(r.e1);
         if (s) {
