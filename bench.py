@@ -380,6 +380,8 @@ def run_ours(args):
     extra = {}
     if rank == 0 and not args.no_extra and name != "collapse":
         extra["cold_collapse_t0"] = measure_other(tg, args, "collapse", dev, stream, flush, evolved=False)
+    if rank == 0 and not args.no_extra:
+        extra["ensemble_64"] = measure_ensemble(tg, dev, stream, flush)
     if rank == 0 and args.evolved:
         extra["cold_collapse_evolved_t1"] = measure_other(tg, args, "collapse", dev, stream, flush, evolved=True)
 
@@ -500,6 +502,61 @@ def compare_fp64_plain(tg, rp, run, stream, flush):
             "speedup_of_fp32_path": out["fp64"] / out["fp32"],
             "note": "one all-from-all evaluation of the initial state: plain float64 path (float64 P2P block per "
                     "leaf pair, generic float64 M2L, potentials) vs the float32 path (accelerations only)"}
+
+
+ENSEMBLE_PARAMS = dict(p=4, theta=0.5, eps=0.01, kernel=1, n_crit=64, kappa=1.0, eta=0.025, dt_max=1.0 / 64, k_max=10)
+
+
+def measure_ensemble(tg, dev, stream, flush, steps=3, warmup=2):
+    """The 64-system ensemble (Plummer and King W0 = 6 spheres, N = round(2^U(10, 17)), each with its own
+    HHS rungs), float32: one rung-0 step of every system, (a) as 64 plain host-driven steps one after
+    another, (b) as one graph launch holding every system's work-queue loop (tg_ensemble_step)."""
+    import torch
+    from paper_1712_10116_gb300 import ics
+    systems = ics.ensemble(velocities=True)
+    out = {"workload": "64 systems: even Plummer (a=1), odd King W0=6 (r_half 1.305), N=round(2^U(10,17)), "
+                       "Plummer eps=0.01, p=4, theta=0.5, n_crit=64, fp32, HHS k_max=10 dt_max=1/64 eta=0.025",
+           "particles": int(sum(s[2].shape[0] for s in systems))}
+    for mode in ("plain", "ensemble"):
+        runs = [HHSRun(tg, tg.Params(precision=tg.TG_PREC_FP32, batched=int(mode == "ensemble"), **ENSEMBLE_PARAMS),
+                       pos, vel, mass, dev, stream) for pos, vel, mass in systems]
+        ctxs = [r.solver.ctx for r in runs]
+
+        def step():
+            if mode == "plain":
+                for r in runs:
+                    r.solver.hhs_step()
+            else:
+                tg.tg_ensemble_step(ctxs)
+
+        for _ in range(warmup):
+            for r in runs:
+                r.reset()
+            step()
+        torch.cuda.synchronize()
+        for r in runs:
+            tg.tg_reset_stats(r.solver.ctx)
+        ms = []
+        for _ in range(steps):
+            for r in runs:
+                r.reset()
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            step()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        st = [r.solver.stats() for r in runs]
+        sinks = sum(x["sink_forces"] for x in st)
+        out[mode] = {"ms_per_step": sum(ms) / steps, "value": sinks / (sum(ms) / 1e3), "unit": "particle-forces/s",
+                     "evaluations_per_step": sum(x["evaluations"] for x in st) / steps,
+                     "host_syncs_per_step": sum(x["host_syncs"] for x in st) / steps,
+                     "max_rung": max(x["max_rung"] for x in st)}
+        for r in runs:
+            r.close()
+    out["speedup_of_ensemble"] = out["plain"]["ms_per_step"] / out["ensemble"]["ms_per_step"]
+    return out
 
 
 def measure_other(tg, args, name, dev, stream, flush, evolved):

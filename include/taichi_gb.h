@@ -160,6 +160,17 @@ tg_status tg_hhs_init(tg_ctx *ctx, int64_t n, double *pos, double *vel, const do
  * TG_ERR_NONFINITE (nothing changed) if a bound position or mass is not finite at the start.
  * Synchronising (the recursion reads the set sizes of each split). */
 tg_status tg_hhs_step(tg_ctx *ctx);
+/* Ensemble of independent systems: one rung-0 HOLD step of every context in ctxs[0..count) as ONE
+ * CUDA graph launch.  Each context must be bound by tg_hhs_init, created with params.batched = 1, on the
+ * current device and with the same stream as ctxs[0]; no context may appear twice.  The graph holds
+ * every system's own work-queue loop (Algorithms 1-2, its own rungs) side by side with no dependencies
+ * between them, so the systems run side by side on the GPU; the host waits once for all of them.  Per
+ * system the step is transactional: a system whose buffers overflow is restored and redone alone; one
+ * whose loop runs out is restored and reported (TG_ERR_TIMEOUT); the other systems keep their step.
+ * The graph is captured on the first call and again when the members or their buffers change.
+ * Errors are reported on ctxs[0] (tg_last_error).  Synchronising. */
+tg_status tg_ensemble_step(tg_ctx **ctxs, int count);
+
 /* The traditional integrator with individual timesteps that the paper sets beside HHS (Sec. 2.3),
  * on the same FMM.  tg_trad_init binds pos/vel/mass like tg_hhs_init (caller-owned device float64
  * SoA), evaluates the forces and picks the first rungs from dt_i = sqrt(eta eps / |a_i|).

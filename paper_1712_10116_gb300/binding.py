@@ -130,6 +130,8 @@ def load() -> C.CDLL:
             L.tg_morton_sort_noalloc.restype = C.c_int
             L.tg_debug_control.argtypes = [_vp, C.c_int, _i64]
             L.tg_autotune.argtypes = [_vp, _i64, _vp, _vp, _vp, C.POINTER(tg_tuning)]
+            L.tg_ensemble_step.argtypes = [C.POINTER(_vp), C.c_int]
+            L.tg_ensemble_step.restype = C.c_int
             L.tg_get_tuning.argtypes = [_vp, C.POINTER(tg_tuning)]
             L.tg_set_tuning.argtypes = [_vp, C.POINTER(tg_tuning)]
             L.tg_set_profiling.argtypes = [_vp, C.c_int]
@@ -350,6 +352,12 @@ def tg_get_tuning(ctx) -> dict:
     out = tg_tuning()
     _check(ctx, load().tg_get_tuning(ctx, C.byref(out)))
     return _tuning_dict(out)
+
+
+def tg_ensemble_step(ctxs) -> None:
+    """One rung-0 HOLD step of every context (bound, batched, same stream) as one graph launch."""
+    arr = (_vp * len(ctxs))(*[c.value if isinstance(c, _vp) else c for c in ctxs])
+    _check(ctxs[0], load().tg_ensemble_step(arr, len(ctxs)))
 
 
 def tg_set_tuning(ctx, tuning: dict):

@@ -247,6 +247,25 @@ tg_status tg_hhs_step(tg_ctx *c)
     return hhs_step(c);
 }
 
+tg_status tg_ensemble_step(tg_ctx **cs, int count)
+{
+    if (!cs || count < 1 || !cs[0]) return TG_ERR_ARG;
+    tg_ctx *c0 = cs[0];
+    tg_status st = begin(c0);
+    if (st) return st;
+    for (int i = 0; i < count; ++i) {
+        if (!cs[i]) return set_err(c0, TG_ERR_ARG, "tg_ensemble_step: member %d is NULL", i);
+        if (cs[i]->hhs_n <= 0 || cs[i]->bound_integrator != 1)
+            return set_err(c0, TG_ERR_STATE, "tg_ensemble_step: member %d has no HHS system bound", i);
+        if (!cs[i]->prm.batched || cs[i]->stream != c0->stream || cs[i]->device != c0->device)
+            return set_err(c0, TG_ERR_ARG, "tg_ensemble_step: member %d is not batched on the first member's stream", i);
+        for (int j = 0; j < i; ++j)
+            if (cs[j] == cs[i]) return set_err(c0, TG_ERR_ARG, "tg_ensemble_step: member %d appears twice", i);
+        cs[i]->err = Err{};
+    }
+    return ensemble_step(cs, count);
+}
+
 tg_status tg_trad_init(tg_ctx *c, int64_t n, double *pos, double *vel, const double *mass)
 {
     tg_status st = begin(c);

@@ -599,6 +599,17 @@ __global__ void hold_drift(const HoldState *h, LevelLayout lv, double dt_max, in
 
 }  // namespace tg
 
+// One graph holding the step loops of several contexts, and what each member was captured with.
+struct EnsembleGraph {
+    std::vector<tg_ctx *> members;
+    std::vector<uint64_t> epochs;
+    std::vector<tg_params> prms;
+    std::vector<tg_tuning> tunes;
+    std::vector<const void *> bound;   // pos, vel, mass per member
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
+
 // The captured graph of the batched step and what it was captured with.
 struct HoldGraph {
     cudaGraph_t graph = nullptr;
@@ -613,14 +624,18 @@ struct HoldGraph {
     void *bound[3] = {nullptr, nullptr, nullptr};
     int64_t launches_split[TG_K_COUNT] = {0}, launches_eval[TG_K_COUNT] = {0};
     unsigned long long *h_read = nullptr;   // pinned: HoldState head + overflow word
+    struct EnsembleGraph *ens = nullptr;    // ensemble graph this context leads (tg_ensemble_step)
 };
 
 namespace tg {
+
+void ensemble_destroy(tg_ctx *c);
 
 void hold_graph_destroy(tg_ctx *c)
 {
     HoldGraph *g = c->hold;
     if (!g) return;
+    ensemble_destroy(c);
     if (g->exec) cudaGraphExecDestroy(g->exec);
     if (g->graph) cudaGraphDestroy(g->graph);
     if (g->cap_stream) cudaStreamDestroy(g->cap_stream);
@@ -748,13 +763,12 @@ static tg_status add_if(tg_ctx *c, cudaGraph_t parent, const cudaGraphNode_t *de
 }
 
 // Capture the step's graph: WHILE { scheduler; IF split { ... }; IF evaluation { ... } }.
-static tg_status hold_capture(tg_ctx *c, HoldGraph *g, Sched &s, const std::vector<Level> &lv, size_t per)
+// The step's loop, WHILE { scheduler; IF split { ... }; IF evaluation { ... } }, added to `parent` (the
+// context's own graph, or an ensemble graph holding the loops of several contexts side by side).
+static tg_status hold_capture_into(tg_ctx *c, HoldGraph *g, Sched &s, const std::vector<Level> &lv, size_t per,
+                                   cudaGraph_t parent)
 {
     tg_status st;
-    if (g->exec) cudaGraphExecDestroy(g->exec);
-    if (g->graph) cudaGraphDestroy(g->graph);
-    g->exec = nullptr;
-    g->graph = nullptr;
     if ((st = hold_presize(c, s, g->caps, lv))) return st;
     if ((st = mac_params_upload(c))) return st;
     HoldState *h = static_cast<HoldState *>(c->buf[B_HOLD].p);
@@ -766,10 +780,9 @@ static tg_status hold_capture(tg_ctx *c, HoldGraph *g, Sched &s, const std::vect
     const int64_t N = s.n;
     const int cap_n = g->caps.n;
     const int grid = grid_for(N, 256, c->num_sms * 8);
-    cudaError_t e = cudaGraphCreate(&g->graph, 0);
-    if (e != cudaSuccess) return cuda_check(c, e, "graph create");
+    cudaError_t e;
     cudaGraphConditionalHandle h_loop;
-    if ((e = cudaGraphConditionalHandleCreate(&h_loop, g->graph, 1, cudaGraphCondAssignDefault)) != cudaSuccess)
+    if ((e = cudaGraphConditionalHandleCreate(&h_loop, parent, 1, cudaGraphCondAssignDefault)) != cudaSuccess)
         return cuda_check(c, e, "conditional handle");
     cudaGraphNodeParams wp = {};
     wp.type = cudaGraphNodeTypeConditional;
@@ -777,7 +790,7 @@ static tg_status hold_capture(tg_ctx *c, HoldGraph *g, Sched &s, const std::vect
     wp.conditional.type = cudaGraphCondTypeWhile;
     wp.conditional.size = 1;
     cudaGraphNode_t wnode;
-    if ((e = cudaGraphAddNode(&wnode, g->graph, nullptr, nullptr, 0, &wp)) != cudaSuccess)
+    if ((e = cudaGraphAddNode(&wnode, parent, nullptr, nullptr, 0, &wp)) != cudaSuccess)
         return cuda_check(c, e, "conditional WHILE node");
     cudaGraph_t body = wp.conditional.phGraph_out[0];
     // handles of the IF nodes belong to the body graph that holds them
@@ -850,7 +863,11 @@ static tg_status hold_capture(tg_ctx *c, HoldGraph *g, Sched &s, const std::vect
     if (st || (st = st2)) return restore(st);
     for (int k = 0; k < TG_K_COUNT; ++k) g->launches_eval[k] = c->prof_launches[k] - launches0[k];
     restore(TG_OK);
-    if ((e = cudaGraphInstantiate(&g->exec, g->graph, 0)) != cudaSuccess) return cuda_check(c, e, "graph instantiate");
+    return TG_OK;
+}
+
+static void hold_record_capture(tg_ctx *c, HoldGraph *g, const Sched &s)
+{
     g->epoch = c->alloc_epoch;
     g->prm = c->prm;
     g->tune = c->tune;
@@ -858,7 +875,46 @@ static tg_status hold_capture(tg_ctx *c, HoldGraph *g, Sched &s, const std::vect
     g->bound[0] = c->hhs_pos;
     g->bound[1] = c->hhs_vel;
     g->bound[2] = const_cast<double *>(c->hhs_mass);
+}
+
+static tg_status hold_capture(tg_ctx *c, HoldGraph *g, Sched &s, const std::vector<Level> &lv, size_t per)
+{
+    tg_status st;
+    if (g->exec) cudaGraphExecDestroy(g->exec);
+    if (g->graph) cudaGraphDestroy(g->graph);
+    g->exec = nullptr;
+    g->graph = nullptr;
+    cudaError_t e = cudaGraphCreate(&g->graph, 0);
+    if (e != cudaSuccess) return cuda_check(c, e, "graph create");
+    if ((st = hold_capture_into(c, g, s, lv, per, g->graph))) return st;
+    if ((e = cudaGraphInstantiate(&g->exec, g->graph, 0)) != cudaSuccess) return cuda_check(c, e, "graph instantiate");
+    hold_record_capture(c, g, s);
     return TG_OK;
+}
+
+static bool hold_stale(const tg_ctx *c, const HoldGraph *g, const Sched &s)
+{
+    return g->epoch != c->alloc_epoch || !same_capture_params(g->prm, c->prm) || g->tune.p2p_rows != c->tune.p2p_rows ||
+           g->tune.m2l_blocks_per_sm != c->tune.m2l_blocks_per_sm || g->tune.m2l_form != c->tune.m2l_form ||
+           g->n != s.n || g->bound[0] != c->hhs_pos || g->bound[1] != c->hhs_vel || g->bound[2] != c->hhs_mass;
+}
+
+// counters of a finished step into the context (launches: the scheduler every iteration, the bodies as
+// often as they ran) and the time
+static void hold_commit(tg_ctx *c, const HoldGraph *g, const HoldState &head)
+{
+    c->prof_launches[TG_K_HHS] += 1 + (int64_t)head.iterations;
+    for (int k = 0; k < TG_K_COUNT; ++k)
+        c->prof_launches[k] += g->launches_split[k] * (int64_t)head.splits + g->launches_eval[k] * (int64_t)head.evals;
+    c->stats.evaluations += (int64_t)head.stats[0];
+    c->stats.sink_forces += (int64_t)head.stats[1];
+    c->stats.m2l_pairs += (int64_t)head.stats[2];
+    c->stats.m2l_class_pairs += (int64_t)head.stats[3];
+    c->stats.p2p_cell_pairs += (int64_t)head.stats[4];
+    c->stats.cells += (int64_t)head.stats[5];
+    c->stats.kdk_frames += (int64_t)head.stats[6];
+    if ((int64_t)head.stats[7] > c->stats.max_rung) c->stats.max_rung = (int64_t)head.stats[7];
+    c->hhs_time += c->prm.dt_max;
 }
 
 tg_status hhs_step_batched(tg_ctx *c)
@@ -896,12 +952,7 @@ tg_status hhs_step_batched(tg_ctx *c)
         g->sized = true;
     }
     for (int attempt = 0; attempt < 24; ++attempt) {
-        const bool stale = !g->exec || g->epoch != c->alloc_epoch || !same_capture_params(g->prm, c->prm) ||
-                           g->tune.p2p_rows != c->tune.p2p_rows ||
-                           g->tune.m2l_blocks_per_sm != c->tune.m2l_blocks_per_sm ||
-                           g->tune.m2l_form != c->tune.m2l_form || g->n != s.n ||
-                           g->bound[0] != c->hhs_pos || g->bound[1] != c->hhs_vel || g->bound[2] != c->hhs_mass;
-        if (stale) {
+        if (!g->exec || hold_stale(c, g, s)) {
             if ((st = hold_capture(c, g, s, s.lv, per))) return fail(st);
             // the capture may have grown nothing, but a stale epoch must not trigger a second capture
             g->epoch = c->alloc_epoch;
@@ -942,22 +993,148 @@ tg_status hhs_step_batched(tg_ctx *c)
             g->exec = nullptr;
             continue;
         }
-        // launches of the step: the scheduler every iteration, the bodies as often as they ran
-        c->prof_launches[TG_K_HHS] += 1 + (int64_t)head.iterations;
-        for (int k = 0; k < TG_K_COUNT; ++k)
-            c->prof_launches[k] += g->launches_split[k] * (int64_t)head.splits + g->launches_eval[k] * (int64_t)head.evals;
-        c->stats.evaluations += (int64_t)head.stats[0];
-        c->stats.sink_forces += (int64_t)head.stats[1];
-        c->stats.m2l_pairs += (int64_t)head.stats[2];
-        c->stats.m2l_class_pairs += (int64_t)head.stats[3];
-        c->stats.p2p_cell_pairs += (int64_t)head.stats[4];
-        c->stats.cells += (int64_t)head.stats[5];
-        c->stats.kdk_frames += (int64_t)head.stats[6];
-        if ((int64_t)head.stats[7] > c->stats.max_rung) c->stats.max_rung = (int64_t)head.stats[7];
-        c->hhs_time += c->prm.dt_max;
+        hold_commit(c, g, head);
         return TG_OK;
     }
     return fail(set_err(c, TG_ERR_CAPACITY, "batched step: buffers still too small after regrowth"));
+}
+
+// ------------------------------------------------------------------ ensemble of batched steps
+// Several bound systems stepped by ONE graph launch: the graph holds each system's work-queue loop side
+// by side (no edges between them), so every system keeps its own rung structure and small systems run
+// side by side on the GPU.  Per system the step is transactional as in hhs_step_batched; a system whose
+// buffers overflow is restored and redone alone (and the ensemble graph captured again next time).
+void ensemble_destroy(tg_ctx *c)
+{
+    if (!c->hold || !c->hold->ens) return;
+    EnsembleGraph *e = c->hold->ens;
+    if (e->exec) cudaGraphExecDestroy(e->exec);
+    if (e->graph) cudaGraphDestroy(e->graph);
+    delete e;
+    c->hold->ens = nullptr;
+}
+
+tg_status ensemble_step(tg_ctx **cs, int count)
+{
+    tg_status st;
+    tg_ctx *c0 = cs[0];
+    // per member: buffers, finiteness (one wait for all), snapshot, level lists, capacities
+    std::vector<Sched> sched(count);
+    std::vector<size_t> per(count);
+    for (int i = 0; i < count; ++i) {
+        tg_ctx *c = cs[i];
+        if ((st = make_sched(c, sched[i]))) return st;
+        if (!c->hold) {
+            c->hold = new (std::nothrow) HoldGraph();
+            if (!c->hold) return set_err(c0, TG_ERR_OOM, "ensemble step: host allocation failed");
+            cudaError_t e = cudaStreamCreateWithFlags(&c->hold->cap_stream, cudaStreamNonBlocking);
+            if (e == cudaSuccess) e = cudaMallocHost(&c->hold->h_read, 4096);
+            if (e != cudaSuccess) {
+                hold_graph_destroy(c);
+                return cuda_check(c0, e, "ensemble step setup");
+            }
+        }
+        unsigned long long *bad = c->d_counters + 10;
+        cudaMemsetAsync(bad, 0, sizeof(unsigned long long), c0->stream);
+        count_nonfinite<<<grid_for(sched[i].n, 256, 2 * c->num_sms), 256, 0, c0->stream>>>(
+            c->hhs_pos, sched[i].n, nullptr, sched[i].n, c->hhs_mass, bad);
+        cudaMemcpyAsync(c->hold->h_read + 65, bad, sizeof(unsigned long long), cudaMemcpyDeviceToHost, c0->stream);
+    }
+    if ((st = cuda_check(c0, stream_sync(c0), "ensemble finiteness check"))) return st;
+    for (int i = 0; i < count; ++i)
+        if (cs[i]->hold->h_read[65])
+            return set_err(c0, TG_ERR_NONFINITE, "ensemble member %d has a non-finite position or mass", i);
+    for (int i = 0; i < count; ++i) {
+        tg_ctx *c = cs[i];
+        char *snap;
+        if ((st = snapshot_state(c, sched[i], &snap)) || (st = level_buffers(c, sched[i].n, sched[i].lv, c->prm.k_max)))
+            return st;
+        per[i] = ((sched[i].n * (2 * sizeof(int64_t) + 2 * sizeof(uint32_t) + 1) + 64) + 255) & ~(size_t)255;
+        if (!c->hold->sized || c->hold->caps.n != (int)sched[i].n) {
+            if ((st = hold_size(c, sched[i], c->hold->caps))) return st;
+            c->hold->sized = true;
+        }
+    }
+    // the ensemble graph: captured again when the members or any member's buffers or parameters changed
+    EnsembleGraph *eg = c0->hold->ens;
+    bool stale = !eg || eg->members != std::vector<tg_ctx *>(cs, cs + count);
+    for (int i = 0; i < count && !stale; ++i) {
+        const tg_ctx *c = cs[i];
+        stale = eg->epochs[i] != c->alloc_epoch || !same_capture_params(eg->prms[i], c->prm) ||
+                eg->tunes[i].p2p_rows != c->tune.p2p_rows || eg->tunes[i].m2l_blocks_per_sm != c->tune.m2l_blocks_per_sm ||
+                eg->tunes[i].m2l_form != c->tune.m2l_form || eg->bound[3 * i] != c->hhs_pos ||
+                eg->bound[3 * i + 1] != c->hhs_vel || eg->bound[3 * i + 2] != c->hhs_mass;
+    }
+    if (stale) {
+        ensemble_destroy(c0);
+        eg = c0->hold->ens = new (std::nothrow) EnsembleGraph();
+        if (!eg) return set_err(c0, TG_ERR_OOM, "ensemble step: host allocation failed");
+        eg->members.assign(cs, cs + count);
+        cudaError_t e = cudaGraphCreate(&eg->graph, 0);
+        if (e != cudaSuccess) return cuda_check(c0, e, "ensemble graph create");
+        for (int i = 0; i < count; ++i) {
+            if ((st = hold_capture_into(cs[i], cs[i]->hold, sched[i], sched[i].lv, per[i], eg->graph))) {
+                ensemble_destroy(c0);
+                return st;
+            }
+        }
+        if ((e = cudaGraphInstantiate(&eg->exec, eg->graph, 0)) != cudaSuccess) {
+            ensemble_destroy(c0);
+            return cuda_check(c0, e, "ensemble graph instantiate");
+        }
+        for (int i = 0; i < count; ++i) {
+            const tg_ctx *c = cs[i];
+            eg->epochs.push_back(c->alloc_epoch);
+            eg->prms.push_back(c->prm);
+            eg->tunes.push_back(c->tune);
+            eg->bound.push_back(c->hhs_pos);
+            eg->bound.push_back(c->hhs_vel);
+            eg->bound.push_back(c->hhs_mass);
+        }
+    }
+    // start every member's queue, one launch for all loops, read every member's counters with one wait
+    for (int i = 0; i < count; ++i) {
+        tg_ctx *c = cs[i];
+        HoldState *h = static_cast<HoldState *>(c->buf[B_HOLD].p);
+        DevEval *de = static_cast<DevEval *>(c->buf[B_DEVEVAL].p);
+        const LevelLayout L{reinterpret_cast<char *>(sched[i].lv[0].sys), per[i], sched[i].n};
+        ProfScope ps_(c, TG_K_HHS);
+        hold_begin<<<grid_for(sched[i].n, 256), 256, 0, c0->stream>>>(h, de, L, sched[i].n, hold_limit(c),
+                                                                       c->debug_queue_hold);
+    }
+    cudaError_t e = cudaGraphLaunch(eg->exec, c0->stream);
+    if (e != cudaSuccess) return cuda_check(c0, e, "ensemble launch");
+    for (int i = 0; i < count; ++i) {
+        tg_ctx *c = cs[i];
+        unsigned long long *hr = c->hold->h_read;
+        cudaMemcpyAsync(hr, c->buf[B_HOLD].p, offsetof(HoldState, op), cudaMemcpyDeviceToHost, c0->stream);
+        cudaMemcpyAsync(hr + 64, &static_cast<DevEval *>(c->buf[B_DEVEVAL].p)->overflow, sizeof(uint32_t),
+                        cudaMemcpyDeviceToHost, c0->stream);
+    }
+    if ((st = cuda_check(c0, stream_sync(c0), "ensemble step"))) return st;
+    tg_status first = TG_OK;
+    for (int i = 0; i < count; ++i) {
+        tg_ctx *c = cs[i];
+        HoldState head;
+        std::memcpy(&head, c->hold->h_read, offsetof(HoldState, op));
+        const uint32_t overflow = *reinterpret_cast<const uint32_t *>(c->hold->h_read + 64);
+        if (head.status != 0) {
+            restore_state(c, sched[i], static_cast<const char *>(c->buf[B_SNAP].p));
+            if (!first) first = set_err(c0, TG_ERR_TIMEOUT, "ensemble member %d: the device loop stopped after %llu "
+                                                            "iterations", i, head.iterations);
+            continue;
+        }
+        if (overflow) {
+            // restore and redo this member alone; the batched step grows its buffers (and the ensemble graph
+            // is captured again on the next call, since the member's buffers moved)
+            restore_state(c, sched[i], static_cast<const char *>(c->buf[B_SNAP].p));
+            st = hhs_step_batched(c);
+            if (st && !first) first = set_err(c0, st, "ensemble member %d: %s", i, c->err.msg.c_str());
+            continue;
+        }
+        hold_commit(c, c->hold, head);
+    }
+    return first;
 }
 
 __global__ void timestep_rungs(int64_t n, const double *a_old, const double *a_cur, double eta_eps, const double *a_tot,

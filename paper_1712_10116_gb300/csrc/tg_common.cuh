@@ -216,6 +216,9 @@ tg_status launch_l2p_hi(tg_ctx *c, int n, const TreeView &t, const T4 *pf, const
 // device; TG_ERR_NONFINITE (with a message) if there is one.  Synchronising.
 tg_status check_finite(tg_ctx *c, int64_t n, const double *pos, int64_t stride, const int64_t *sub,
                        const double *mass);
+// count of the non-finite positions and masses of n particles, added to *bad (tree.cu)
+__global__ void count_nonfinite(const double *pos, int64_t stride, const int64_t *sub, int64_t n, const double *mass,
+                                unsigned long long *bad);
 // Consume one allocation of the failure injection; TG_ERR_OOM when it says this one fails.
 tg_status injected_alloc_failure(tg_ctx *c, size_t bytes, int slot);
 
@@ -297,6 +300,7 @@ tg_status mac_params_upload(tg_ctx *c);
 
 // ---- batched HOLD step (hhs.cu)
 tg_status hhs_step_batched(tg_ctx *c);
+tg_status ensemble_step(tg_ctx **cs, int count);
 void hold_graph_destroy(tg_ctx *c);
 void hold_graph_reset_sizes(tg_ctx *c);
 // words of scan scratch exclusive_scan_u32 needs for n values

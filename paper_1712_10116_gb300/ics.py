@@ -10,6 +10,8 @@ masses (n,) float64 summing to 1.
 """
 from __future__ import annotations
 
+import functools
+
 import numpy as np
 
 
@@ -346,11 +348,19 @@ def clustered_box(n_side: int = 256, seed: int = 1004, n_clumps: int = 1000, dis
     return np.ascontiguousarray(pos), np.full(n, 1.0 / n)
 
 
+@functools.lru_cache(maxsize=4)
 def _king_profile(w0: float, dr: float = 1e-3):
     """King (1966) model in core radii: the dimensionless potential W(r) from W(0) = w0 down to the
     tidal radius (W = 0), with density rho(W) ~ e^W erf(sqrt W) - sqrt(4W/pi) (1 + 2W/3) and
     W'' + 2W'/r = -9 rho(W) / rho(w0) (fourth-order Runge-Kutta).  Returns radii and the enclosed mass
     fraction, which is proportional to -r^2 W'(r)."""
+    r, m, _ = _king_solution(w0, dr)
+    return r, m
+
+
+@functools.lru_cache(maxsize=4)
+def _king_solution(w0: float, dr: float = 1e-3):
+    """Radii, enclosed mass fractions and W(r) of the King model (see _king_profile)."""
     from math import erf, exp, pi, sqrt
 
     def rho(w):
@@ -363,7 +373,7 @@ def _king_profile(w0: float, dr: float = 1e-3):
 
     r = dr
     y = (w0 - 1.5 * dr * dr, -3.0 * dr)   # series start: W = w0 - 3/2 r^2
-    rs, ms = [0.0, r], [0.0, -r * r * y[1]]
+    rs, ms, ws = [0.0, r], [0.0, -r * r * y[1]], [w0, y[0]]
     while y[0] > 0.0:
         k1 = f(r, y)
         k2 = f(r + dr / 2, (y[0] + dr / 2 * k1[0], y[1] + dr / 2 * k1[1]))
@@ -374,31 +384,69 @@ def _king_profile(w0: float, dr: float = 1e-3):
         r += dr
         rs.append(r)
         ms.append(-r * r * y[1])
+        ws.append(max(y[0], 0.0))
     ms = np.maximum.accumulate(np.array(ms))
-    return np.array(rs), ms / ms[-1]
+    return np.array(rs), ms / ms[-1], np.array(ws)
 
 
-def king(n: int, w0: float = 6.0, seed: int = 1005, r_half: float = 1.305):
+def king(n: int, w0: float = 6.0, seed: int = 1005, r_half: float = 1.305, velocities: bool = False):
     """King (1966) sphere with central potential w0, positions and equal masses, scaled to the
-    half-mass radius r_half (1.305 is that of the Plummer sphere with a = 1)."""
+    half-mass radius r_half (1.305 is that of the Plummer sphere with a = 1).
+
+    With velocities=True also returns velocities from the King distribution function, a lowered
+    Maxwellian f ~ exp(W - v^2 / (2 s^2)) - 1 for v^2 < 2 W s^2 (W the local dimensionless potential):
+    speeds in units of s by rejection from p(u) ~ u^2 (e^(W - u^2/2) - 1), u < sqrt(2W), isotropic
+    directions; s is then set by the virial theorem, 2K = -W_pot, with the potential energy of the
+    spherical mass profile, -sum_i m_i M(< r_i) / r_i (G = 1).  Returns (pos, vel, mass), centre-of-mass
+    frame for the velocities."""
     g = rng(seed)
-    r, mfrac = _king_profile(w0)
-    radii = np.interp(g.uniform(0.0, 1.0, n), mfrac, r)
-    radii *= r_half / np.interp(0.5, mfrac, r)
-    return np.ascontiguousarray(_isotropic(g, n) * radii), np.full(n, 1.0 / n)
+    r, mfrac, wr = _king_solution(w0)
+    u0 = g.uniform(0.0, 1.0, n)
+    core = np.interp(u0, mfrac, r)                     # radii in core radii
+    scale = r_half / np.interp(0.5, mfrac, r)
+    pos = np.ascontiguousarray(_isotropic(g, n) * (core * scale))
+    mass = np.full(n, 1.0 / n)
+    if not velocities:
+        return pos, mass
+    w = np.interp(core, r, wr)                        # local depth W of every particle
+    umax = np.sqrt(2.0 * np.maximum(w, 0.0))
+    speed = np.zeros(n)
+    todo = np.nonzero(umax > 0)[0]
+    # envelope: p(u) <= u^2 e^(W - u^2/2) <= 2 e^(W - 1) / ... ; bound it by its maximum on a grid per W
+    grid = np.linspace(0.0, 1.0, 257)[1:]
+    while todo.size:
+        uu = g.uniform(0.0, 1.0, todo.size) * umax[todo]
+        wt = w[todo]
+        f = uu * uu * (np.exp(wt - 0.5 * uu * uu) - 1.0)
+        ug = grid[None, :] * umax[todo, None]
+        fmax = (ug * ug * (np.exp(wt[:, None] - 0.5 * ug * ug) - 1.0)).max(axis=1) * 1.05
+        ok = g.uniform(0.0, 1.0, todo.size) * fmax < f
+        speed[todo[ok]] = uu[ok]
+        todo = todo[~ok]
+    vel = _isotropic(g, n) * speed
+    # the velocity unit from the virial theorem of the sampled positions
+    order = np.argsort(np.linalg.norm(pos, axis=0))
+    rr = np.linalg.norm(pos, axis=0)[order]
+    menc = np.cumsum(mass[order]) - mass[order]
+    w_pot = -float(np.sum(mass[order] * menc / np.maximum(rr, 1e-12)))
+    k_unit = 0.5 * float(np.sum(mass * (vel * vel).sum(0)))
+    vel *= np.sqrt(-w_pot / (2.0 * k_unit))
+    vel -= (vel * mass).sum(axis=1, keepdims=True) / mass.sum()
+    return pos, np.ascontiguousarray(vel), mass
 
 
-def ensemble(seed: int = 1005, n_systems: int = 64, log2n=(10.0, 17.0)):
+def ensemble(seed: int = 1005, n_systems: int = 64, log2n=(10.0, 17.0), velocities: bool = False):
     """Ensemble of independent systems: sizes round(2^U(10, 17)); even members Plummer spheres
     (a = 1), odd members King W0 = 6 spheres of the same half-mass radius; each of total mass 1.
-    Returns a list of (pos, mass)."""
+    Returns a list of (pos, mass), or with velocities=True of (pos, vel, mass) (Plummer and King
+    distribution functions)."""
     g = rng(seed)
     sizes = np.round(2.0 ** g.uniform(log2n[0], log2n[1], n_systems)).astype(np.int64)
     out = []
     for s, ns in enumerate(sizes):
         if s % 2 == 0:
-            pos, _, mass = plummer(int(ns), seed * 1000 + s)
+            pos, vel, mass = plummer(int(ns), seed * 1000 + s)
+            out.append((pos, vel, mass) if velocities else (pos, mass))
         else:
-            pos, mass = king(int(ns), 6.0, seed * 1000 + s)
-        out.append((pos, mass))
+            out.append(king(int(ns), 6.0, seed * 1000 + s, velocities=velocities))
     return out

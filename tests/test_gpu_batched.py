@@ -168,3 +168,62 @@ def test_batched_overflow_restores_regrows_and_redoes_the_step():
     assert np.abs(x - xp).max() < 1e-12 * np.abs(xp).max()
     assert np.abs(v - vp).max() < 1e-12 * np.abs(vp).max()
     s.close()
+
+
+# ---------------------------------------------------------------- ensemble: one graph launch for many systems
+def _ensemble_members(precision, batched, systems, base):
+    out = []
+    for pos, vel, mass in systems:
+        s = tg.Solver(tg.Params(precision=precision, batched=batched, **base))
+        P, V, M = _t(pos), _t(vel), _t(mass)
+        s.hhs_init(P, V, M)
+        out.append((s, P, V, M))
+    return out
+
+
+def test_ensemble_step_equals_the_members_own_steps():
+    # six Plummer / King systems of different sizes, each with its own rungs; float64, so that the one-launch
+    # ensemble and the members' own batched steps agree to 1e-12
+    sizes = [1500, 3001, 700, 5000, 2048, 4097]
+    systems = [ics.plummer(n, 1001 + i) if i % 2 == 0 else ics.king(n, 6.0, 1005 + i, velocities=True)
+               for i, n in enumerate(sizes)]
+    base = dict(p=4, theta=0.5, eps=0.01, kernel=1, n_crit=32, eta=0.025, dt_max=1.0 / 32, k_max=8)
+    ens = _ensemble_members(tg.TG_PREC_FP64, 1, systems, base)
+    own = _ensemble_members(tg.TG_PREC_FP64, 1, systems, base)
+    for s, *_ in ens + own:
+        tg.tg_reset_stats(s.ctx)
+    for _ in range(2):
+        tg.tg_ensemble_step([s.ctx for s, *_ in ens])
+        for s, *_ in own:
+            s.hhs_step()
+    torch.cuda.synchronize()
+    for (se, Pe, Ve, _), (so, Po, Vo, _) in zip(ens, own):
+        a, b = se.stats(), so.stats()
+        assert a["evaluations"] == b["evaluations"] and a["sink_forces"] == b["sink_forces"]
+        assert a["max_rung"] == b["max_rung"]
+        re = tg.tg_hhs_state(se.ctx, Pe.shape[1])[0]
+        ro = tg.tg_hhs_state(so.ctx, Po.shape[1])[0]
+        assert torch.equal(re, ro)
+        assert (Pe - Po).abs().max().item() < 1e-12 * Po.abs().max().item()
+        assert (Ve - Vo).abs().max().item() < 1e-12 * Vo.abs().max().item()
+        assert tg.tg_diagnostics(se.ctx)[7] == pytest.approx(2.0 / 32)
+    # one wait per ensemble step on the first member's context (the sizing call aside)
+    s0 = ens[0][0]
+    tg.tg_reset_stats(s0.ctx)
+    tg.tg_ensemble_step([s.ctx for s, *_ in ens])
+    assert s0.stats()["host_syncs"] == 2
+    for s, *_ in ens + own:
+        s.close()
+
+
+def test_ensemble_step_rejects_bad_member_lists():
+    pos, vel, mass = ics.plummer(800, 1001)
+    base = dict(p=4, theta=0.5, eps=0.01, kernel=1, n_crit=32, dt_max=1.0 / 32, k_max=6)
+    a = _ensemble_members(tg.TG_PREC_FP32, 1, [(pos, vel, mass)], base)[0][0]
+    b = _ensemble_members(tg.TG_PREC_FP32, 0, [(pos, vel, mass)], base)[0][0]
+    with pytest.raises(tg.TGError):
+        tg.tg_ensemble_step([a.ctx, a.ctx])      # twice
+    with pytest.raises(tg.TGError):
+        tg.tg_ensemble_step([a.ctx, b.ctx])      # a plain (not batched) member
+    a.close()
+    b.close()

@@ -111,3 +111,38 @@ def test_disk_galaxy_toomre_q_measured_back():
     # the disk rotates: mean v_phi there is positive and below the circular speed (asymmetric drift)
     vphi = (-v[0, sel] * disk[1, sel] + v[1, sel] * disk[0, sel]) / R[sel]
     assert 0.0 < vphi.mean() < np.sqrt(model.vc2(np.array([r0]))[0])
+
+
+# ---------------------------------------------------------------- King velocities (lowered Maxwellian)
+def _king_u2(w):
+    # <u^2> of p(u) ~ u^2 (e^(W - u^2/2) - 1), 0 < u < sqrt(2W), by quadrature
+    u = np.linspace(0.0, np.sqrt(2.0 * w), 4001)
+    f = u * u * (np.exp(w - 0.5 * u * u) - 1.0)
+    return np.trapezoid(u * u * f, u) / np.trapezoid(f, u)
+
+
+def test_king_velocity_profile_follows_the_distribution_function():
+    # the mean square speed at depth W(r), relative to the core's, is that of the lowered Maxwellian:
+    # this checks the rejection sampler and the potential profile, whatever the velocity unit
+    pos, vel, m = ics.king(60_000, 6.0, 1005, velocities=True)
+    pos0, m0 = ics.king(60_000, 6.0, 1005)
+    assert np.array_equal(pos, pos0)
+    r_c, mfrac, wr = ics._king_solution(6.0)
+    scale = 1.305 / np.interp(0.5, mfrac, r_c)
+    r = np.linalg.norm(pos, axis=0) / scale          # in core radii
+    v2 = (vel * vel).sum(0)
+    core = r < 0.5
+    ref = v2[core].mean() / np.mean([_king_u2(w) for w in np.interp(r[core], r_c, wr)])
+    for lo, hi in [(1.0, 2.0), (3.0, 5.0), (6.0, 9.0)]:
+        sel = (r >= lo) & (r < hi)
+        want = np.mean([_king_u2(w) for w in np.interp(r[sel], r_c, wr)])
+        assert abs(v2[sel].mean() / ref / want - 1.0) < 0.06, (lo, hi)
+
+
+def test_king_virial_ratio_against_direct_summation():
+    import oracle
+    pos, vel, m = ics.king(12_000, 6.0, 1005, velocities=True)
+    _, pot = oracle.direct(pos, m, 1e-3, kernel=oracle.PLUMMER)
+    K = 0.5 * float((m * (vel * vel).sum(0)).sum())
+    W = 0.5 * float((m * pot).sum())
+    assert abs(2.0 * K / -W - 1.0) < 0.02
