@@ -263,8 +263,15 @@ tg_status tg_debug_control(tg_ctx *ctx, int what, int64_t value);
  * searched one after another in that order (each at the best of the ones before).  The objective is
  * the time of one all-from-all evaluation plus, when is_fast is given, one kick-pair evaluation with
  * that fast set (accelerations only, as the HHS kicks ask).  pos: device 3*n float64, mass: device n
- * float64, is_fast: device n uint8 or NULL.  out (host, nullable) receives the choice.  Synchronising;
- * writes no caller array.  The float64 path has no tunable launch shapes: only n_crit is searched.
+ * float64, is_fast: device n uint8 or NULL.
+ * With pos = mass = is_fast = NULL (n = 0 or the bound size) the objective is instead one rung-0 HOLD
+ * step of the system bound by tg_hhs_init (Algorithm 1, batched or plain as params.batched says),
+ * timed after one untimed step at the same setting: a step's evaluations run from the whole system down
+ * to the deepest rung's, so its best leaf size can differ from the largest evaluation's.  The bound
+ * pos, vel, |a| bookkeeping, rungs and time are saved first and put back after every step and at the
+ * end; TG_ERR_STATE without a bound system.
+ * out (host, nullable) receives the choice.  Synchronising; leaves every caller array as it found it.
+ * The float64 path has no tunable launch shapes: only n_crit is searched.
  * tg_get_tuning reports the settings in use (the defaults before any tuning). */
 typedef struct {
     int n_crit;              /* leaf size in use                                                 */

@@ -341,10 +341,12 @@ def _tuning_dict(t) -> dict:
     return {k: getattr(t, k) for k, _ in tg_tuning._fields_}
 
 
-def tg_autotune(ctx, pos, mass, is_fast=None) -> dict:
-    """Time evaluations of this system over leaf size and launch shapes; the context keeps the fastest."""
+def tg_autotune(ctx, pos=None, mass=None, is_fast=None) -> dict:
+    """Time evaluations of this system (pos, mass given) or rung-0 steps of the system bound by
+    tg_hhs_init (pos = mass = None) over leaf size and launch shapes; the context keeps the fastest."""
     out = tg_tuning()
-    _check(ctx, load().tg_autotune(ctx, mass.shape[0], _ptr(pos), _ptr(mass), _ptr(is_fast), C.byref(out)))
+    n = 0 if mass is None else mass.shape[0]
+    _check(ctx, load().tg_autotune(ctx, n, _ptr(pos), _ptr(mass), _ptr(is_fast), C.byref(out)))
     return _tuning_dict(out)
 
 
@@ -383,7 +385,7 @@ class Solver:
     def fmm_forces(self, pos, mass, is_fast=None, want_pot=True):
         return tg_fmm_forces(self.ctx, pos, mass, is_fast, want_pot=want_pot)
 
-    def autotune(self, pos, mass, is_fast=None):
+    def autotune(self, pos=None, mass=None, is_fast=None):
         return tg_autotune(self.ctx, pos, mass, is_fast)
 
     def direct_forces(self, pos, mass, is_fast=None, sinks=None):

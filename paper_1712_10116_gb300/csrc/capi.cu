@@ -369,6 +369,14 @@ tg_status tg_autotune(tg_ctx *c, int64_t n, const double *pos, const double *mas
 {
     tg_status st = begin(c);
     if (st) return st;
+    if (!pos && !mass) {
+        // step objective on the system bound by tg_hhs_init
+        if (is_fast) return set_err(c, TG_ERR_ARG, "tg_autotune: is_fast needs pos and mass");
+        if (c->bound_integrator != 1) return set_err(c, TG_ERR_STATE, "tg_autotune: no system bound by tg_hhs_init");
+        if (n != 0 && n != c->hhs_n) return set_err(c, TG_ERR_ARG, "tg_autotune: n differs from the bound system");
+        if ((st = check_finite(c, c->hhs_n, c->hhs_pos, c->hhs_n, nullptr, c->hhs_mass))) return st;
+        return autotune(c, (int)c->hhs_n, nullptr, nullptr, nullptr, out);
+    }
     if (n <= 0 || n > INT32_MAX / 4) return set_err(c, TG_ERR_ARG, "tg_autotune: n out of range");
     if (!check_device_ptr(pos) || !check_device_ptr(mass) || (is_fast && !check_device_ptr(is_fast)))
         return set_err(c, TG_ERR_ARG, "tg_autotune: arrays must be device memory");

@@ -262,10 +262,10 @@ tg_status hhs_init(tg_ctx *c)
 
 // Snapshot of the integrator state (pos, vel, |a_old|, |a_cur|, |a|_tot, rungs) that makes a rung-0 step
 // transactional: an error inside the step copies it back.
-static tg_status snapshot_state(tg_ctx *c, const Sched &s, char **snap)
+static tg_status snapshot_state(tg_ctx *c, const Sched &s, char **snap, int slot = B_SNAP)
 {
     const size_t n = (size_t)s.n;
-    tg_status st = ensure_t(c, B_SNAP, n * (9 * sizeof(double) + sizeof(int32_t)), snap);
+    tg_status st = ensure_t(c, slot, n * (9 * sizeof(double) + sizeof(int32_t)), snap);
     if (st) return st;
     double *d = reinterpret_cast<double *>(*snap);
     cudaMemcpyAsync(d, c->hhs_pos, 3 * n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream);
@@ -288,6 +288,27 @@ static void restore_state(tg_ctx *c, const Sched &s, const char *snap)
     cudaMemcpyAsync(s.a_tot, d + 8 * n, n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream);
     cudaMemcpyAsync(s.rung, d + 9 * n, n * sizeof(int32_t), cudaMemcpyDeviceToDevice, c->stream);
     stream_sync(c);
+}
+
+// The bound integrator state (pos, vel, |a| and rungs) into / back from a scratch slot other than the
+// step's own snapshot (the autotuner's step objective); the step time is saved by the caller.
+tg_status hhs_save(tg_ctx *c, int slot)
+{
+    Sched s;
+    tg_status st = make_sched(c, s);
+    if (st) return st;
+    char *snap = nullptr;
+    return snapshot_state(c, s, &snap, slot);
+}
+
+tg_status hhs_load(tg_ctx *c, int slot)
+{
+    Sched s;
+    tg_status st = make_sched(c, s);
+    if (st) return st;
+    if (!c->buf[slot].p) return set_err(c, TG_ERR_STATE, "no saved integrator state");
+    restore_state(c, s, static_cast<const char *>(c->buf[slot].p));
+    return cuda_check(c, cudaGetLastError(), "hhs state restore");
 }
 
 tg_status hhs_step(tg_ctx *c)
@@ -689,7 +710,7 @@ static tg_status hold_presize(tg_ctx *c, const Sched &s, const BatchCaps &cap, c
         {B_OWN_CNT, 4ull * (C + 2)}, {B_OWN_FILL, 4ull * (C + 2)}, {B_OWN_OFF, 4ull * C},
         {B_OWN_LIST, 8ull * max_units}, {B_OWN_TAG, 8 * cap.p2p}, {B_OWN_PART, 4 * cap.p2p},
         {B_M2L_CNT, 4ull * C}, {B_M2L_OFF, 4ull * C}, {B_M2L_FILL, 4ull * C}, {B_M2L_SRC, 4 * cap.m2l_src},
-        {B_FWORDS, 4ull * (n + 1)}, {B_FPRE, 4ull * (n + 1)},
+        {B_FWORDS, 4ull * (n + 1)}, {B_FPRE, 4ull * (n + 1)}, {B_M2L_PART, 16 * cap.blocks}, {B_M2L_PCNT, 16},
         {B_FRAME_X, 24ull * n}, {B_FRAME_M, 8ull * n}, {B_FRAME_F, 1ull * n}, {B_SPLIT_FLAG, 4ull * n},
         {B_SPLIT_PRE, 4ull * n}, {B_HOLD, sizeof(HoldState)}, {B_DEVEVAL, sizeof(DevEval)},
     };

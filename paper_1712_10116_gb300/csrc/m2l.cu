@@ -2,6 +2,8 @@
 // p <= 6 (harmonic contraction set for the Wendland kernel, full set for Plummer softening), the
 // generic kernel otherwise and in float64 up to the table order, high_order.cu above it.  Its own translation unit, so that the large
 // generated contractions compile in parallel with the rest.
+#include <algorithm>
+
 #include "tg_common.cuh"
 #include "m2l_sym.cuh"
 
@@ -14,6 +16,23 @@ __global__ void zero_u32(uint32_t *p, int n, const int *dn, int extra)
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) p[i] = 0u;
 }
 
+
+// The walk's blocks partitioned for m2l_blocks_f32: multi-row blocks first, one-row blocks at the end
+// (counts in *pcnt, on the device).  nblocks: the count, or the capacity with dnb the device count.
+static tg_status m2l_partition_blocks(tg_ctx *c, const M2LBlock *blocks, int64_t nblocks,
+                                      const unsigned long long *dnb, M2LBlock **part, unsigned long long **pcnt)
+{
+    tg_status st;
+    if ((st = ensure_t(c, B_M2L_PART, (size_t)std::max<int64_t>(nblocks, 1), part)) ||
+        (st = ensure_t(c, B_M2L_PCNT, 2, pcnt)))
+        return st;
+    ProfScope ps_(c, TG_K_M2L);
+    cudaMemsetAsync(*pcnt, 0, 2 * sizeof(unsigned long long), c->stream);
+    if (nblocks > 0)
+        m2l_partition<<<dnb ? c->num_sms * 8 : grid_for(nblocks, 256, c->num_sms * 8), 256, 0, c->stream>>>(
+            blocks, nblocks, dnb, *part, nblocks, *pcnt);
+    return cuda_check(c, cudaGetLastError(), "m2l partition");
+}
 
 // Directed M2L lists from the walk's blocks: per cell the count of its sources (cnt, zeroed first), their
 // offsets (exclusive scan of cnt) and the sources themselves (src, `cap` entries).
@@ -89,15 +108,21 @@ static tg_status m2l_f32_harmonic(tg_ctx *c, const TreeView &t, const M2LBlock *
     const int ncpr = (NH + 3) & ~3;
     const int64_t rows = (int64_t)t.ncell * 2;
     float *Mr, *Lr;
+    M2LBlock *part;
+    unsigned long long *pcnt;
     tg_status st;
     if ((st = ensure_t(c, B_MOMH, (size_t)rows * ncpr, &Mr)) || (st = ensure_t(c, B_LOCH, (size_t)rows * ncpr, &Lr)))
         return st;
+    if ((st = m2l_partition_blocks(c, blocks, nblocks, nullptr, &part, &pcnt))) return st;
     ProfScope ps_(c, TG_K_M2L);
     m2l_reduce_moments_h<P><<<grid_for(rows, 128), 128, 0, c->stream>>>(rows, Ms, ncp, Mr, ncpr, nullptr);
     cudaMemsetAsync(Lr, 0, sizeof(float) * (size_t)rows * ncpr, c->stream);
     using G = M2LHarm<P>;
-#define TG_M2L_H(MK, PT) \
-    m2l_blocks_f32<G, MK, PT><<<grid, 128, 0, c->stream>>>(t, blocks, nblocks, Mr, Lr, ncpr, 0.f, 0, nullptr, nullptr, nullptr, 0.0, fpre, c->d_counters + 11)
+#define TG_M2L_H(MK, PT)                                                                                          \
+    do {                                                                                                          \
+        m2l_blocks_f32<G, MK, PT><<<grid, 128, 0, c->stream>>>(t, part, nblocks, pcnt, Mr, Lr, ncpr, 0.f, 0, nullptr, \
+                                                               nullptr, 0.0, fpre, c->d_counters + 11);            \
+    } while (0)
     if (masked) {
         if (pot) TG_M2L_H(true, true);
         else TG_M2L_H(true, false);
@@ -128,8 +153,19 @@ tg_status launch_m2l_f32(tg_ctx *c, const TreeView &t, const M2LBlock *blocks, i
         default: return m2l_f32_harmonic<6>(c, t, blocks, nblocks, Ms, L, ncp, masked, pot, grid, fpre);
         }
     }
+    M2LBlock *part = nullptr;
+    unsigned long long *pcnt = nullptr;
+    if (p <= 6) {
+        tg_status st;
+        if ((st = m2l_partition_blocks(c, blocks, nblocks, nullptr, &part, &pcnt))) return st;
+    }
     ProfScope ps_(c, TG_K_M2L);
-#define TG_M2L_F32_(PP, MK, PT) m2l_blocks_f32<M2LFull<PP>, MK, PT><<<grid, 128, 0, c->stream>>>(t, blocks, nblocks, Ms, L, ncp, eoL, plummer, nullptr, nullptr, nullptr, 0.0, fpre, c->d_counters + 11)
+#define TG_M2L_F32_(PP, MK, PT)                                                                                   \
+    do {                                                                                                          \
+        m2l_blocks_f32<M2LFull<PP>, MK, PT><<<grid, 128, 0, c->stream>>>(t, part, nblocks, pcnt, Ms, L, ncp, eoL,  \
+                                                                         plummer, nullptr, nullptr, 0.0, fpre,      \
+                                                                         c->d_counters + 11);                       \
+    } while (0)
 #define TG_M2L_F32(PP)                                                                                            \
     case PP:                                                                                                      \
         if (masked) { if (pot) TG_M2L_F32_(PP, true, true); else TG_M2L_F32_(PP, true, false); }                   \
@@ -187,22 +223,26 @@ static tg_status m2l_f32_dev_p(tg_ctx *c, const TreeView &t, const DevEval *de, 
         m2l_complete_locals_h<P><<<g, 128, 0, c->stream>>>(rows_cap, Lr, ncpr, L, ncp, &de->rows);
         return TG_OK;
     }
+    M2LBlock *part;
+    unsigned long long *pcnt;
+    tg_status st;
+    if ((st = m2l_partition_blocks(c, blocks, cap_blocks, dnb, &part, &pcnt))) return st;
     ProfScope ps_(c, TG_K_M2L);
     if (!plummer) {
         // harmonic set: fold, contract (the launch for the other class count returns at once), complete
         using G = M2LHarm<P>;
         m2l_reduce_moments_h<P><<<g, 128, 0, c->stream>>>(rows_cap, Ms, ncp, Mr, ncpr, &de->rows);
         zero_rows_f32<<<c->num_sms * 4, 256, 0, c->stream>>>(Lr, &de->rows, ncpr);
-        m2l_blocks_f32<G, true, false><<<grid, 128, 0, c->stream>>>(t, blocks, cap_blocks, Mr, Lr, ncpr, 0.f, 0, dnb, de,
+        m2l_blocks_f32<G, true, false><<<grid, 128, 0, c->stream>>>(t, part, cap_blocks, pcnt, Mr, Lr, ncpr, 0.f, 0, de,
                                                                     gp, c->prm.eps, fpre, c->d_counters + 11);
-        m2l_blocks_f32<G, false, false><<<grid, 128, 0, c->stream>>>(t, blocks, cap_blocks, Mr, Lr, ncpr, 0.f, 0, dnb, de,
+        m2l_blocks_f32<G, false, false><<<grid, 128, 0, c->stream>>>(t, part, cap_blocks, pcnt, Mr, Lr, ncpr, 0.f, 0, de,
                                                                      gp, c->prm.eps, fpre, c->d_counters + 11);
         m2l_complete_locals_h<P><<<g, 128, 0, c->stream>>>(rows_cap, Lr, ncpr, L, ncp, &de->rows);
     } else {
         using G = M2LFull<P>;
-        m2l_blocks_f32<G, true, false><<<grid, 128, 0, c->stream>>>(t, blocks, cap_blocks, Ms, L, ncp, 0.f, 1, dnb, de,
+        m2l_blocks_f32<G, true, false><<<grid, 128, 0, c->stream>>>(t, part, cap_blocks, pcnt, Ms, L, ncp, 0.f, 1, de,
                                                                     gp, c->prm.eps, fpre, c->d_counters + 11);
-        m2l_blocks_f32<G, false, false><<<grid, 128, 0, c->stream>>>(t, blocks, cap_blocks, Ms, L, ncp, 0.f, 1, dnb, de,
+        m2l_blocks_f32<G, false, false><<<grid, 128, 0, c->stream>>>(t, part, cap_blocks, pcnt, Ms, L, ncp, 0.f, 1, de,
                                                                      gp, c->prm.eps, fpre, c->d_counters + 11);
     }
     return TG_OK;

@@ -111,26 +111,83 @@ __device__ __forceinline__ void m2l_halve(float (&v)[NP], int lane, int d)
     }
 }
 
+// Blocks whose well-separated pairs lie in one row (a leaf facing the children of an opened cell, about
+// half of all blocks on clustered inputs) would fill 8 of the 32 lanes of a round.  m2l_partition puts
+// them at the end of the block list (a block whose pairs lie in one column is transposed first), and the
+// kernel takes them four at a time: row slot rr of a packed round holds its own block's row.  The row
+// (x side) reduction stays within the 8 lanes of a row; the column (y side) sums of different blocks
+// cannot be combined, so in a packed round every active lane adds its whole y-side expansion.
+// part: the partitioned blocks, multi-row ones at [0, pcnt[0]) and one-row ones at [cap - pcnt[1], cap).
+static __global__ void m2l_partition(const M2LBlock *__restrict__ in, int64_t nb, const unsigned long long *dnb,
+                              M2LBlock *part, int64_t cap, unsigned long long *pcnt)
+{
+    if (dnb) nb = (int64_t)*dnb;
+    const int lane = threadIdx.x & 31;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    // whole warps iterate together: slots are reserved per warp
+    for (int64_t w0 = (int64_t)blockIdx.x * blockDim.x; w0 < nb; w0 += stride) {
+        const int64_t w = w0 + threadIdx.x;
+        M2LBlock blk{0u, 0u, 0ull};
+        bool single = false;
+        if (w < nb) {
+            blk = in[w];
+            unsigned rows = 0u, cols = 0u;
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const unsigned r = (unsigned)((blk.mask >> (8 * i)) & 0xffull);
+                if (r) rows |= 1u << i;
+                cols |= r;
+            }
+            if (__popc(rows) == 1) {
+                single = true;
+            } else if (__popc(cols) == 1) {
+                // all pairs in column j0: the transposed block (b, a) has them in row j0
+                const int j0 = __ffs(cols) - 1;
+                unsigned long long t = 0ull;
+#pragma unroll
+                for (int i = 0; i < 8; ++i)
+                    if ((blk.mask >> (8 * i + j0)) & 1ull) t |= 1ull << (8 * j0 + i);
+                blk = M2LBlock{blk.b, blk.a, t};
+                single = true;
+            }
+        }
+        const bool valid = w < nb;
+        const unsigned bm = __ballot_sync(0xffffffffu, valid && !single);
+        const unsigned bs = __ballot_sync(0xffffffffu, valid && single);
+        unsigned long long base_m = 0ull, base_s = 0ull;
+        if (lane == 0) {
+            if (bm) base_m = atomicAdd(&pcnt[0], (unsigned long long)__popc(bm));
+            if (bs) base_s = atomicAdd(&pcnt[1], (unsigned long long)__popc(bs));
+        }
+        base_m = __shfl_sync(0xffffffffu, base_m, 0);
+        base_s = __shfl_sync(0xffffffffu, base_s, 0);
+        const unsigned lt = (1u << lane) - 1u;
+        if (valid && !single) part[base_m + __popc(bm & lt)] = blk;
+        if (valid && single) part[cap - 1 - (int64_t)(base_s + __popc(bs & lt))] = blk;
+    }
+}
+
 // POT = false: accelerations only, L^0 is left at zero (see the generated *_forces contractions).
 // G: M2LFull<P> or M2LHarm<P>; Ms and L hold that set's coefficients with row stride ncp.
-// Batched path (dnb non-null): the block count, the class count and the root cube come from the
-// device; the launch for the other class count returns at once.
+// Work items: the pcnt[0] multi-row blocks of part (rounds of four rows), then the pcnt[1] one-row
+// blocks at the end of part, four per packed round (see m2l_partition).
+// Batched path (de non-null): the class count and the root cube come from the device; the launch for
+// the other class count returns at once.
 // Kick pairs (MASKED) with fpre (the prefix sum of the fast flags over the sorted particles): a target
 // cell needs the all-sources local (class 0) only if it holds slow particles, and the slow-sources local
 // (class 1) only if it holds fast particles; a round skips a side's contraction of a class when no
 // target of that side needs it (a warp vote, so the warp stays converged).  The skipped locals are read
 // by no particle: L2L hands them only to descendants, which hold no particle of that class either.
 template <class G, bool MASKED, bool POT>
-__global__ void __launch_bounds__(128) m2l_blocks_f32(TreeView t, const M2LBlock *__restrict__ blocks, int64_t nblocks,
+__global__ void __launch_bounds__(128) m2l_blocks_f32(TreeView t, const M2LBlock *__restrict__ part, int64_t cap,
+                                                      const unsigned long long *__restrict__ pcnt,
                                                       const float *__restrict__ Ms, float *L, int ncp, float eps_over_L,
-                                                      int plummer, const unsigned long long *dnb, const DevEval *de,
-                                                      const Geom *gp, double eps, const uint32_t *__restrict__ fpre,
-                                                      unsigned long long *class_ctr)
+                                                      int plummer, const DevEval *de, const Geom *gp, double eps,
+                                                      const uint32_t *__restrict__ fpre, unsigned long long *class_ctr)
 {
     unsigned long long my_sc = 0;   // side contractions the method needs: (pair side, class) with a target
-    if (dnb) {
+    if (de) {
         if ((de->masked != 0) != MASKED) return;
-        nblocks = (int64_t)*dnb;
         if (plummer) eps_over_L = (float)ldexp(eps, -gp->log2L);
     }
     using S = M2LScatter<G::NC>;
@@ -139,8 +196,19 @@ __global__ void __launch_bounds__(128) m2l_blocks_f32(TreeView t, const M2LBlock
     const int j = lane & 7, rr = (lane >> 3) & 3;
     const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t w = wid; w < nblocks; w += nw) {
-        const M2LBlock blk = blocks[w];
+    constexpr int NC4 = (NC + 3) & ~3;
+    __shared__ float4 pk[128 * (NC4 / 4)];   // packed rounds: each lane's y-side expansion
+    const int64_t n_multi = (int64_t)pcnt[0], n_single = (int64_t)pcnt[1];
+    const int64_t n_items = n_multi + (n_single + 3) / 4;
+    for (int64_t w = wid; w < n_items; w += nw) {
+        const bool packed = w >= n_multi;   // warp-uniform
+        M2LBlock blk{0u, 0u, 0ull};
+        if (!packed) {
+            blk = part[w];
+        } else {
+            const int64_t s = (w - n_multi) * 4 + rr;
+            if (s < n_single) blk = part[cap - 1 - s];
+        }
         const BlockGeom bg = block_geom(t, blk);
         const float rho = ldexpf(1.0f, bg.lx - bg.ly);
         const float soft = plummer ? ldexpf(eps_over_L, bg.lx) : 0.0f;   // eps / s_x
@@ -149,12 +217,12 @@ __global__ void __launch_bounds__(128) m2l_blocks_f32(TreeView t, const M2LBlock
 #pragma unroll
         for (int i = 0; i < 8; ++i)
             if (((blk.mask >> (8 * i)) & 0xffull) != 0ull) rowmask |= 1u << i;
-        const int nrows = __popc(rowmask);
+        const int nrows = packed ? 1 : __popc(rowmask);
         for (int r0 = 0; r0 < nrows; r0 += 4) {
-            // this lane's row: the (r0 + rr)-th non-empty row
+            // this lane's row: the (r0 + rr)-th non-empty row of the block (packed: its block's one row)
             int i = -1;
             {
-                const int want = r0 + rr;
+                const int want = packed ? 0 : r0 + rr;
 #pragma unroll
                 for (int b = 0; b < 8; ++b)
                     if (((rowmask >> b) & 1u) && __popc(rowmask & ((1u << b) - 1u)) == want) i = b;
@@ -175,7 +243,8 @@ __global__ void __launch_bounds__(128) m2l_blocks_f32(TreeView t, const M2LBlock
                 for (int k = 0; k < ND; ++k) D[k] = 0.f;
             }
             const bool row_used = ((amask >> (lane & ~7)) & 0xffu) != 0u;   // this lane's row, this round
-            const bool col_used = (amask & (0x01010101u << j)) != 0u;      // this lane's column, this round
+            // this lane's column, this round (packed: the lane's own pair, its block has one row)
+            const bool col_used = packed ? active : (amask & (0x01010101u << j)) != 0u;
             // classes the round's targets need (side a: the row cells, side b: the column cells)
             bool need_a[2] = {true, true}, need_b[2] = {true, true};
             if (MASKED && fpre) {
@@ -218,35 +287,63 @@ __global__ void __launch_bounds__(128) m2l_blocks_f32(TreeView t, const M2LBlock
                     }
                 }
                 if (!need_b[cls]) continue;
-                // y side: sources x; reduce-scatter over the column's lanes (bits 4, 3):
-                // lane (rr, j) keeps coefficients CL*rr .. CL*rr + CL - 1 of column j
+                // y side: sources x.  Block rounds reduce-scatter over the column's lanes (bits 4, 3):
+                // lane (rr, j) keeps coefficients CL*rr .. CL*rr + CL - 1 of column j.  Packed rounds
+                // keep each lane's whole expansion (its column belongs to its own block).
 #pragma unroll
                 for (int k = NC; k < NP; ++k) Lc[k] = 0.f;
                 if (POT) G::side_b(D, Ms + ((size_t)xs * 2 + cls) * ncp, reinterpret_cast<float(&)[NC]>(Lc));
                 else G::side_b_forces(D, Ms + ((size_t)xs * 2 + cls) * ncp, reinterpret_cast<float(&)[NC]>(Lc));
-                m2l_halve<NP, 2 * CL>(Lc, lane, 16);
-                m2l_halve<NP, CL>(Lc, lane, 8);
-                if (col_used) {
-                    // the sums are in the x normalisation: L~_y^n carries rho^(|n|+1)
-                    float *dst = L + ((size_t)y * 2 + cls) * ncp;
-                    const int k0 = CL * rr;
-                    int o = order_in(G::HARMONIC, k0);
-                    int next = first_of_order(G::HARMONIC, o + 1);
-                    float sc = ldexpf(1.0f, (bg.lx - bg.ly) * (o + 1));
+                // the sums are in the x normalisation: L~_y^n carries rho^(|n|+1)
+                float *dst = L + ((size_t)y * 2 + cls) * ncp;
+                if (!packed) {
+                    m2l_halve<NP, 2 * CL>(Lc, lane, 16);
+                    m2l_halve<NP, CL>(Lc, lane, 8);
+                    if (col_used) {
+                        const int k0 = CL * rr;
+                        int o = order_in(G::HARMONIC, k0);
+                        int next = first_of_order(G::HARMONIC, o + 1);
+                        float sc = ldexpf(1.0f, (bg.lx - bg.ly) * (o + 1));
 #pragma unroll
-                    for (int g = 0; g < CL; g += 4) {
-                        float v[4];
+                        for (int g = 0; g < CL; g += 4) {
+                            float v[4];
 #pragma unroll
-                        for (int q = 0; q < 4; ++q) {
-                            const int k = k0 + g + q;
-                            if (k == next) {
-                                ++o;
-                                next = first_of_order(G::HARMONIC, o + 1);
-                                sc *= rho;
+                            for (int q = 0; q < 4; ++q) {
+                                const int k = k0 + g + q;
+                                if (k == next) {
+                                    ++o;
+                                    next = first_of_order(G::HARMONIC, o + 1);
+                                    sc *= rho;
+                                }
+                                v[q] = Lc[g + q] * sc;
                             }
-                            v[q] = Lc[g + q] * sc;
+                            if (k0 + g < NC) atomicAdd(reinterpret_cast<float4 *>(dst + k0 + g), make_float4(v[0], v[1], v[2], v[3]));
                         }
-                        if (k0 + g < NC) atomicAdd(reinterpret_cast<float4 *>(dst + k0 + g), make_float4(v[0], v[1], v[2], v[3]));
+                    }
+                } else {
+                    // the whole expansion, staged in shared memory so that it is not held in registers
+                    // beside the derivative tensor; coefficients of order o take rho^(o + 1)
+                    float4 *buf = pk + threadIdx.x * (NC4 / 4);
+#pragma unroll
+                    for (int g = 0; g < NC4; g += 4) buf[g / 4] = make_float4(Lc[g], Lc[g + 1], Lc[g + 2], Lc[g + 3]);
+                    if (col_used) {
+                        int o = 0, next = first_of_order(G::HARMONIC, 1);
+                        float sc = rho;   // order 0: rho^1
+#pragma unroll 1
+                        for (int g = 0; g < NC; g += 4) {
+                            const float4 u = buf[g / 4];
+                            float v[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+                            for (int q = 0; q < 4; ++q) {
+                                if (g + q == next) {
+                                    ++o;
+                                    next = first_of_order(G::HARMONIC, o + 1);
+                                    sc *= rho;
+                                }
+                                v[q] *= sc;
+                            }
+                            atomicAdd(reinterpret_cast<float4 *>(dst + g), make_float4(v[0], v[1], v[2], v[3]));
+                        }
                     }
                 }
             }

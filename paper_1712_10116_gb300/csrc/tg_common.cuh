@@ -150,7 +150,7 @@ enum Slot {
     B_HHS_SCAN, B_HHS_TMP, B_RED, B_DIAG_POT, B_DIAG_ACC,
     B_OWN_CNT, B_OWN_FILL, B_OWN_OFF, B_OWN_LIST, B_OWN_TAG, B_OWN_PART, B_SNAP, B_TUNE_ACC,
     B_MACP, B_DEVEVAL, B_HOLD, B_FRAME_X, B_FRAME_M, B_FRAME_F, B_SPLIT_FLAG, B_SPLIT_PRE,
-    B_M2L_CNT, B_M2L_OFF, B_M2L_FILL, B_M2L_SRC, B_FWORDS, B_FPRE,
+    B_M2L_CNT, B_M2L_OFF, B_M2L_FILL, B_M2L_SRC, B_FWORDS, B_FPRE, B_M2L_PART, B_M2L_PCNT, B_TUNE_SNAP,
     B_LAST_SLOT
 };
 static_assert(B_LAST_SLOT <= kMaxSlots, "tg_ctx::buf holds fewer entries than there are slots");
@@ -312,6 +312,8 @@ tg_status autotune(tg_ctx *c, int n, const double *pos, const double *mass, cons
 // ---- hhs.cu
 tg_status hhs_init(tg_ctx *c);
 tg_status hhs_step(tg_ctx *c);
+tg_status hhs_save(tg_ctx *c, int slot);
+tg_status hhs_load(tg_ctx *c, int slot);
 tg_status trad_init(tg_ctx *c);
 tg_status trad_step(tg_ctx *c);
 tg_status hhs_diagnostics(tg_ctx *c, double out[8]);

@@ -3,9 +3,14 @@
 //
 // The search is a coordinate descent: n_crit first (it changes the tree, hence the balance between
 // M2L and P2P work), then the P2P rows per lane and the M2L grid at the chosen n_crit (these change
-// launch shapes only, not results).  Each setting is timed with CUDA events on the context's stream
-// around one all-from-all evaluation plus, when a fast set is given, one kick-pair evaluation: one
-// warm-up round, then the best of two.
+// launch shapes only, not results).  Each setting is timed with CUDA events on the context's stream.
+// Evaluation objective (the caller's particles): one all-from-all evaluation plus, when a fast set is
+// given, one kick-pair evaluation; one warm-up round, then the best of two.  Step objective (no
+// particles given, a system bound by tg_hhs_init): one rung-0 HOLD step of the bound system after one
+// untimed step at the same setting (which sizes the buffers and captures the graph of a batched step);
+// the integrator state is saved before the search and put back before every step and at the end.  A
+// step holds evaluations of every rung's system, from the whole system down to the deepest rung's few
+// particles, so its best leaf size can differ from that of the largest evaluation alone.
 #include <algorithm>
 
 #include "tg_common.cuh"
@@ -22,10 +27,28 @@ struct TuneRun {
     double *acc;
     cudaEvent_t e0, e1;
     int timed = 0;
+    bool steps = false;   // step objective on the bound system
 };
+
+tg_status objective_step(TuneRun &r, double *ms_out)
+{
+    tg_ctx *c = r.c;
+    tg_status st;
+    if ((st = hhs_load(c, B_TUNE_SNAP)) || (st = hhs_step(c)) || (st = hhs_load(c, B_TUNE_SNAP))) return st;
+    cudaEventRecord(r.e0, c->stream);
+    if ((st = hhs_step(c))) return st;
+    cudaEventRecord(r.e1, c->stream);
+    if ((st = cuda_check(c, cudaEventSynchronize(r.e1), "autotune timing"))) return st;
+    float ms = 0.f;
+    if ((st = cuda_check(c, cudaEventElapsedTime(&ms, r.e0, r.e1), "autotune timing"))) return st;
+    r.timed += 1;
+    *ms_out = ms;
+    return TG_OK;
+}
 
 tg_status objective(TuneRun &r, double *ms_out)
 {
+    if (r.steps) return objective_step(r, ms_out);
     tg_ctx *c = r.c;
     tg_status st;
     double best = 1e300;
@@ -50,8 +73,13 @@ tg_status objective(TuneRun &r, double *ms_out)
 tg_status autotune(tg_ctx *c, int n, const double *pos, const double *mass, const uint8_t *fast, tg_tuning *out)
 {
     tg_status st;
-    TuneRun r{c, n, pos, mass, fast, nullptr, nullptr, nullptr, 0};
-    if ((st = ensure_t(c, B_TUNE_ACC, (size_t)3 * n, &r.acc))) return st;
+    TuneRun r{c, n, pos, mass, fast, nullptr, nullptr, nullptr, 0, pos == nullptr};
+    const double time0 = c->hhs_time;
+    if (r.steps) {
+        if ((st = hhs_save(c, B_TUNE_SNAP))) return st;
+    } else if ((st = ensure_t(c, B_TUNE_ACC, (size_t)3 * n, &r.acc))) {
+        return st;
+    }
     if (cudaEventCreate(&r.e0) != cudaSuccess || cudaEventCreate(&r.e1) != cudaSuccess) {
         cudaGetLastError();
         return set_err(c, TG_ERR_CUDA, "autotune: cannot create events");
@@ -74,6 +102,12 @@ tg_status autotune(tg_ctx *c, int n, const double *pos, const double *mass, cons
         c->stats.list_regrowths = regrow;
         c->stats.host_syncs = syncs;
         c->prof_level = prof0;
+        if (r.steps) {
+            // the bound system as it was before the search (also after a failed step)
+            const tg_status sl = hhs_load(c, B_TUNE_SNAP);
+            if (!s) s = sl;
+            c->hhs_time = time0;
+        }
         cudaStreamSynchronize(c->stream);
         cudaMemcpy(c->d_counters, dev0, sizeof dev0, cudaMemcpyHostToDevice);
         cudaEventDestroy(r.e0);
