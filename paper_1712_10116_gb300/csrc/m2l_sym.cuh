@@ -246,7 +246,7 @@ __global__ void __launch_bounds__(128) m2l_blocks_f32(TreeView t, const M2LBlock
             // this lane's column, this round (packed: the lane's own pair, its block has one row)
             const bool col_used = packed ? active : (amask & (0x01010101u << j)) != 0u;
             // classes the round's targets need (side a: the row cells, side b: the column cells)
-            bool need_a[2] = {true, true}, need_b[2] = {true, true};
+            unsigned need = 0xfu;   // bit cls: side a needs class cls; bit 2 + cls: side b does
             if (MASKED && fpre) {
                 int fx = 0, sx = 0, fy = 0, sy = 0;
                 if (active) {
@@ -256,24 +256,29 @@ __global__ void __launch_bounds__(128) m2l_blocks_f32(TreeView t, const M2LBlock
                     fy = (int)(fpre[ay + t.count[y]] - fpre[ay]);
                     sy = t.count[y] - fy;
                 }
-                need_a[0] = __any_sync(0xffffffffu, sx > 0);
-                need_a[1] = __any_sync(0xffffffffu, fx > 0);
-                need_b[0] = __any_sync(0xffffffffu, sy > 0);
-                need_b[1] = __any_sync(0xffffffffu, fy > 0);
+                need = (__any_sync(0xffffffffu, sx > 0) ? 1u : 0u) | (__any_sync(0xffffffffu, fx > 0) ? 2u : 0u) |
+                       (__any_sync(0xffffffffu, sy > 0) ? 4u : 0u) | (__any_sync(0xffffffffu, fy > 0) ? 8u : 0u);
                 my_sc += (unsigned)(sx > 0) + (unsigned)(fx > 0) + (unsigned)(sy > 0) + (unsigned)(fy > 0);
             } else if (active) {
                 my_sc += MASKED ? 4u : 2u;
             }
-#pragma unroll
-            for (int cls = 0; cls < (MASKED ? 2 : 1); ++cls) {
+            // One contraction in the code for both sides and both classes (the generated code is large; the
+            // warps of an SM fetch one copy instead of four).  Side 0 is the row cell x with sources y:
+            // L~_x^n = sum_j (-1)^|j| rho^|j| M~_y^j D^{n+j}.  Side 1 is the column cell y with sources x,
+            // the same contraction with rho = -1: sum_j M~_x^j D^{n+j}, which is (-1)^|n| times L~_y^n
+            // in the x normalisation; the flush applies (-1)^|n| rho^(|n|+1).
+#pragma unroll 1
+            for (int it = 0; it < (MASKED ? 4 : 2); ++it) {
+                const int cls = it >> 1, side = it & 1;
+                if (!(need & ((side ? 4u : 1u) << cls))) continue;
                 float Lc[NP];
-                if (need_a[cls]) {
-                    // x side: sources y; reduce-scatter over the row's lanes (bits 2, 1, 0):
-                    // lane j keeps coefficients RL*j .. RL*j + RL - 1
 #pragma unroll
-                    for (int k = NC; k < NP; ++k) Lc[k] = 0.f;
-                    if (POT) G::side_a(D, Ms + ((size_t)ys * 2 + cls) * ncp, rho, reinterpret_cast<float(&)[NC]>(Lc));
-                    else G::side_a_forces(D, Ms + ((size_t)ys * 2 + cls) * ncp, rho, reinterpret_cast<float(&)[NC]>(Lc));
+                for (int k = NC; k < NP; ++k) Lc[k] = 0.f;
+                const float *src = Ms + ((size_t)(side ? xs : ys) * 2 + cls) * ncp;
+                if (POT) G::side_a(D, src, side ? -1.0f : rho, reinterpret_cast<float(&)[NC]>(Lc));
+                else G::side_a_forces(D, src, side ? -1.0f : rho, reinterpret_cast<float(&)[NC]>(Lc));
+                if (side == 0) {
+                    // reduce-scatter over the row's lanes (bits 2, 1, 0): lane j keeps RL*j .. RL*j + RL - 1
                     m2l_halve<NP, 4 * RL>(Lc, lane, 4);
                     m2l_halve<NP, 2 * RL>(Lc, lane, 2);
                     m2l_halve<NP, RL>(Lc, lane, 1);
@@ -285,25 +290,20 @@ __global__ void __launch_bounds__(128) m2l_blocks_f32(TreeView t, const M2LBlock
                             if (k < NC) atomicAdd(reinterpret_cast<float4 *>(dst + k), make_float4(Lc[g], Lc[g + 1], Lc[g + 2], Lc[g + 3]));
                         }
                     }
+                    continue;
                 }
-                if (!need_b[cls]) continue;
-                // y side: sources x.  Block rounds reduce-scatter over the column's lanes (bits 4, 3):
-                // lane (rr, j) keeps coefficients CL*rr .. CL*rr + CL - 1 of column j.  Packed rounds
-                // keep each lane's whole expansion (its column belongs to its own block).
-#pragma unroll
-                for (int k = NC; k < NP; ++k) Lc[k] = 0.f;
-                if (POT) G::side_b(D, Ms + ((size_t)xs * 2 + cls) * ncp, reinterpret_cast<float(&)[NC]>(Lc));
-                else G::side_b_forces(D, Ms + ((size_t)xs * 2 + cls) * ncp, reinterpret_cast<float(&)[NC]>(Lc));
-                // the sums are in the x normalisation: L~_y^n carries rho^(|n|+1)
                 float *dst = L + ((size_t)y * 2 + cls) * ncp;
                 if (!packed) {
+                    // block rounds: reduce-scatter over the column's lanes (bits 4, 3): lane (rr, j) keeps
+                    // coefficients CL*rr .. CL*rr + CL - 1 of column j
                     m2l_halve<NP, 2 * CL>(Lc, lane, 16);
                     m2l_halve<NP, CL>(Lc, lane, 8);
                     if (col_used) {
                         const int k0 = CL * rr;
                         int o = order_in(G::HARMONIC, k0);
                         int next = first_of_order(G::HARMONIC, o + 1);
-                        float sc = ldexpf(1.0f, (bg.lx - bg.ly) * (o + 1));
+                        float sc = ldexpf((o & 1) ? -1.0f : 1.0f, (bg.lx - bg.ly) * (o + 1));
+                        const float nrho = -rho;
 #pragma unroll
                         for (int g = 0; g < CL; g += 4) {
                             float v[4];
@@ -313,7 +313,7 @@ __global__ void __launch_bounds__(128) m2l_blocks_f32(TreeView t, const M2LBlock
                                 if (k == next) {
                                     ++o;
                                     next = first_of_order(G::HARMONIC, o + 1);
-                                    sc *= rho;
+                                    sc *= nrho;
                                 }
                                 v[q] = Lc[g + q] * sc;
                             }
@@ -321,14 +321,15 @@ __global__ void __launch_bounds__(128) m2l_blocks_f32(TreeView t, const M2LBlock
                         }
                     }
                 } else {
-                    // the whole expansion, staged in shared memory so that it is not held in registers
-                    // beside the derivative tensor; coefficients of order o take rho^(o + 1)
+                    // packed rounds: each lane's whole expansion (its column belongs to its own block),
+                    // staged in shared memory so that it is not held in registers beside the derivative tensor
                     float4 *buf = pk + threadIdx.x * (NC4 / 4);
 #pragma unroll
                     for (int g = 0; g < NC4; g += 4) buf[g / 4] = make_float4(Lc[g], Lc[g + 1], Lc[g + 2], Lc[g + 3]);
                     if (col_used) {
                         int o = 0, next = first_of_order(G::HARMONIC, 1);
                         float sc = rho;   // order 0: rho^1
+                        const float nrho = -rho;
 #pragma unroll 1
                         for (int g = 0; g < NC; g += 4) {
                             const float4 u = buf[g / 4];
@@ -338,7 +339,7 @@ __global__ void __launch_bounds__(128) m2l_blocks_f32(TreeView t, const M2LBlock
                                 if (g + q == next) {
                                     ++o;
                                     next = first_of_order(G::HARMONIC, o + 1);
-                                    sc *= rho;
+                                    sc *= nrho;
                                 }
                                 v[q] *= sc;
                             }
