@@ -12,8 +12,10 @@
 // dynamically to the warps).
 //
 // With slow/fast classes the leaves hold their slow particles first.  Slow rows meet every
-// column; fast rows meet only the owner's slow columns, so fast-fast pairs are never computed
-// (a kickS2F feels the slow masses only).  Within a batch the partners whose cube lies closer
+// column; fast rows meet only the owner's slow columns, so no fast-fast pair reaches a sum (a
+// kickS2F feels the slow masses only).  The columns are staged in leaf order and padded to a
+// multiple of 8 once; in the fast-row pass the fast columns of the batch that holds the slow/fast
+// boundary carry zero mass and their reaction sums are dropped.  Within a batch the partners whose cube lies closer
 // than eps to the owner's come first; chunks made only of the other partners' rows need no softening
 // test, the others take the pair value at max(r, eps) and correct the rare pairs with r < eps.
 #pragma once
@@ -21,7 +23,7 @@
 
 namespace tg {
 
-constexpr int kOwnUnit = 16;   // partners per work unit of the owner kernel
+constexpr int kOwnUnit = 32;   // partners per work unit of the owner kernel (one per lane)
 
 // Owner and partner of each distinct leaf pair, and per-owner partner counts (own_cnt starts at zero).
 __global__ void p2p_owner_count(const uint2 *__restrict__ pairs, int64_t npairs, const int32_t *__restrict__ count,
@@ -72,11 +74,11 @@ struct OwnerShared {
 };
 
 // Rows i0 .. i0 + 32*ROWS of one phase (0: slow rows, 1: fast rows) against the first ncol staged
-// columns (a multiple of 8).
+// columns (a multiple of 8); the reaction sums of columns at or past nkeep are not kept.
 template <int KERNEL, int ROWS, bool NEAR, bool POT>
 __device__ __noinline__ void owner_rows(const float4 *__restrict__ pf, const OwnerBatch *ob, int phase, int i0, int nrows,
-                                        const float4 *sq, float (*sacc)[4], int ncol, float eps, double *acc4, int n,
-                                        int lane)
+                                        const float4 *sq, float (*sacc)[4], int ncol, int nkeep, float eps, double *acc4,
+                                        int n, int lane)
 {
     const float eps2 = eps * eps, inv_eps = 1.0f / eps, inv_eps3 = inv_eps * inv_eps * inv_eps;
     const int *inc = ob->inc[phase];
@@ -165,12 +167,12 @@ __device__ __noinline__ void owner_rows(const float4 *__restrict__ pf, const Own
                         ra[r][0] = fmaf(mq, dx, ra[r][0]);
                         ra[r][1] = fmaf(mq, dy, ra[r][1]);
                         ra[r][2] = fmaf(mq, dz, ra[r][2]);
-                        atomicAdd(&sacc[j][0], -mp * dx);
-                        atomicAdd(&sacc[j][1], -mp * dy);
-                        atomicAdd(&sacc[j][2], -mp * dz);
-                        if (POT) {
-                            ra[r][3] = fmaf(q.w, dph, ra[r][3]);
-                            atomicAdd(&sacc[j][3], p[r].w * dph);
+                        if (POT) ra[r][3] = fmaf(q.w, dph, ra[r][3]);
+                        if (j < nkeep) {
+                            atomicAdd(&sacc[j][0], -mp * dx);
+                            atomicAdd(&sacc[j][1], -mp * dy);
+                            atomicAdd(&sacc[j][2], -mp * dz);
+                            if (POT) atomicAdd(&sacc[j][3], p[r].w * dph);
                         }
                     }
                 }
@@ -194,7 +196,7 @@ __device__ __noinline__ void owner_rows(const float4 *__restrict__ pf, const Own
             }
         }
         // lane l holds column j0 + l/4, component l%4; each (column, component) has one lane
-        sacc[j0 + (lane >> 2)][lane & 3] += col[0];
+        if (j0 + (lane >> 2) < nkeep) sacc[j0 + (lane >> 2)][lane & 3] += col[0];
     }
 #pragma unroll
     for (int r = 0; r < ROWS; ++r)
@@ -320,32 +322,35 @@ __global__ void __launch_bounds__(256, 2) p2p_owner_f32(TreeView t, int log2L, c
             const int nearF = n_near ? __shfl_sync(0xffffffffu, incF, n_near - 1) : 0;
             for (int jc = 0; jc < nb; jc += kMaxNcrit) {
                 const int nbc = min(kMaxNcrit, nb - jc);
+                // columns in leaf order (slow first), padded to a multiple of 8 once
                 const int nsc = max(0, min(sB - jc, nbc));   // slow columns of this chunk (slow-first leaf)
-                const int ns8 = (nsc + 7) & ~7, nf = nbc - nsc, nt8 = ns8 + ((nf + 7) & ~7);
+                const int ns8 = (nsc + 7) & ~7, nt8 = (nbc + 7) & ~7;
                 __syncwarp();
                 for (int j = lane; j < nt8; j += 32) {
-                    const int src = j < nsc ? j : (j >= ns8 && j < ns8 + nf ? nsc + j - ns8 : -1);
-                    sq[j] = src >= 0 ? pf[fb + jc + src] : make_float4(-1e8f, -1e8f, -1e8f, 0.f);
+                    sq[j] = j < nbc ? pf[fb + jc + j] : make_float4(-1e8f, -1e8f, -1e8f, 0.f);
                     sacc[j][0] = sacc[j][1] = sacc[j][2] = sacc[j][3] = 0.f;
                 }
                 __syncwarp();
                 for (int i0 = 0; i0 < Ts; i0 += 32 * ROWS) {
-                    if (i0 < nearS) owner_rows<KERNEL, ROWS, true, POT>(pf, ob, 0, i0, Ts, sq, sacc, nt8, eps, acc4, n, lane);
-                    else owner_rows<KERNEL, ROWS, false, POT>(pf, ob, 0, i0, Ts, sq, sacc, nt8, eps, acc4, n, lane);
+                    if (i0 < nearS) owner_rows<KERNEL, ROWS, true, POT>(pf, ob, 0, i0, Ts, sq, sacc, nt8, nt8, eps, acc4, n, lane);
+                    else owner_rows<KERNEL, ROWS, false, POT>(pf, ob, 0, i0, Ts, sq, sacc, nt8, nt8, eps, acc4, n, lane);
                 }
-                if (nsc > 0)
+                if (nsc > 0 && Tf > 0) {
+                    // fast rows meet the slow columns only: the batch that holds the first fast columns runs
+                    // with their masses at zero (no force on the rows) and their reaction sums dropped
+                    __syncwarp();
+                    for (int j = nsc + lane; j < ns8; j += 32) sq[j].w = 0.f;
+                    __syncwarp();
                     for (int i0 = 0; i0 < Tf; i0 += 32 * ROWS) {
-                        if (i0 < nearF) owner_rows<KERNEL, ROWS, true, POT>(pf, ob, 1, i0, Tf, sq, sacc, ns8, eps, acc4, n, lane);
-                        else owner_rows<KERNEL, ROWS, false, POT>(pf, ob, 1, i0, Tf, sq, sacc, ns8, eps, acc4, n, lane);
+                        if (i0 < nearF) owner_rows<KERNEL, ROWS, true, POT>(pf, ob, 1, i0, Tf, sq, sacc, ns8, nsc, eps, acc4, n, lane);
+                        else owner_rows<KERNEL, ROWS, false, POT>(pf, ob, 1, i0, Tf, sq, sacc, ns8, nsc, eps, acc4, n, lane);
                     }
-                __syncwarp();
-                for (int j = lane; j < nt8; j += 32) {
-                    const int src = j < nsc ? j : (j >= ns8 && j < ns8 + nf ? nsc + j - ns8 : -1);
-                    if (src >= 0)
-#pragma unroll
-                        for (int comp = 0; comp < (POT ? 4 : 3); ++comp)
-                            atomicAdd(&acc4[(size_t)comp * n + fb + jc + src], f2d_exact(sacc[j][comp]));
                 }
+                __syncwarp();
+                for (int j = lane; j < nbc; j += 32)
+#pragma unroll
+                    for (int comp = 0; comp < (POT ? 4 : 3); ++comp)
+                        atomicAdd(&acc4[(size_t)comp * n + fb + jc + j], f2d_exact(sacc[j][comp]));
             }
         }
     }
