@@ -380,6 +380,8 @@ def run_ours(args):
         extra["cold_collapse_t0"] = measure_other(tg, args, "collapse", dev, stream, flush, evolved=False)
     if rank == 0 and not args.no_extra:
         extra["ensemble_64"] = measure_ensemble(tg, dev, stream, flush)
+        extra["plummer_4096_fp64"] = measure_plummer(tg, dev, stream)
+        extra["clustered_box_fp32_vs_fp64"] = measure_box(tg, dev, stream, flush)
     if rank == 0 and args.evolved:
         extra["cold_collapse_evolved_t1"] = measure_other(tg, args, "collapse", dev, stream, flush, evolved=True)
 
@@ -500,6 +502,86 @@ def compare_fp64_plain(tg, rp, run, stream, flush):
             "speedup_of_fp32_path": out["fp64"] / out["fp32"],
             "note": "one all-from-all evaluation of the initial state: plain float64 path (float64 P2P block per "
                     "leaf pair, generic float64 M2L, potentials) vs the float32 path (accelerations only)"}
+
+
+BOX_PARAMS = dict(p=6, theta=0.5, eps=1e-3, kernel=0, n_crit=96, kappa=1.0)
+
+
+def measure_box(tg, dev, stream, flush, n_sinks=10000):
+    """The clustered box (N = 2^24): one all-from-all evaluation in the float32 path and in the float64
+    path, each timed with CUDA events (after a warm-up evaluation, L2 flushed), and the force error of
+    both against float64 direct summation on n_sinks random sinks (the direct sum runs on the GPU)."""
+    import torch
+    from paper_1712_10116_gb300 import ics
+    pos, mass = ics.clustered_box(256)
+    P, M = torch.tensor(pos, device=dev), torch.tensor(mass, device=dev)
+    n = M.shape[0]
+    sinks = torch.tensor(np.random.default_rng(11).choice(n, n_sinks, replace=False), device=dev)
+    ref = tg.Solver(tg.Params(precision=tg.TG_PREC_FP64, **BOX_PARAMS), stream)
+    ad, _ = ref.direct_forces(P, M, sinks=sinks)
+    ref.close()
+    nd = torch.linalg.norm(ad, dim=0)
+    out = {"workload": "clustered box N=16777216: Zel'dovich-displaced 256^3 lattice (P(k)~k^-2, 0.5 cell rms) + "
+                       "1000 NFW clumps (c=10, log-uniform 1e-5..1e-2), eps=1e-3 Wendland C2, p=6, theta=0.5, "
+                       "n_crit=96; one all-from-all evaluation",
+           "n": n, "error_sinks": n_sinks, "reference": "float64 direct summation on the GPU"}
+    accs = {}
+    for key, prec in (("fp32", tg.TG_PREC_FP32), ("fp64", tg.TG_PREC_FP64)):
+        s = tg.Solver(tg.Params(precision=prec, **BOX_PARAMS), stream)
+        s.fmm_forces(P, M, want_pot=False)   # warm-up (buffers)
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        acc, _ = s.fmm_forces(P, M, want_pot=False)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        a = acc[:, sinks]
+        err = (torch.linalg.norm(a - ad, dim=0) / nd).cpu().numpy()
+        accs[key] = a
+        out[key] = {"eval_ms": ms, "value": n / (ms / 1e3), "unit": "particle-forces/s",
+                    "median_force_err": float(np.median(err)), "p99_force_err": float(np.quantile(err, 0.99))}
+        s.close()
+    d = (torch.linalg.norm(accs["fp32"] - accs["fp64"], dim=0) / torch.linalg.norm(accs["fp64"], dim=0)).cpu().numpy()
+    out["fp32_vs_fp64_median"] = float(np.median(d))
+    out["speedup_of_fp32"] = out["fp64"]["eval_ms"] / out["fp32"]["eval_ms"]
+    return out
+
+
+PLUMMER_PARAMS = dict(p=4, theta=0.5, eps=0.01, kernel=1, n_crit=64, kappa=1.0, eta=0.025, dt_max=1.0 / 64, k_max=10)
+
+
+def measure_plummer(tg, dev, stream, steps=16):
+    """The Plummer sphere (N = 4096, Plummer softening 0.01, p = 4, theta = 0.5, float64): the initial
+    evaluation and 16 rung-0 HOLD steps (batched), timed with CUDA events; momentum and energy drift."""
+    import torch
+    from paper_1712_10116_gb300 import ics
+    pos, vel, mass = ics.plummer(4096, 1001)
+    P, V, M = (torch.tensor(a, device=dev) for a in (pos, vel, mass))
+    s = tg.Solver(tg.Params(precision=tg.TG_PREC_FP64, batched=1, **PLUMMER_PARAMS), stream)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    torch.cuda.synchronize()
+    ev[0].record(stream)
+    s.hhs_init(P, V, M)
+    ev[1].record(stream)
+    d0 = s.diagnostics()   # untimed: the energy takes a fresh evaluation with potentials
+    ev[2].record(stream)
+    for _ in range(steps):
+        s.hhs_step()
+    ev[3].record(stream)
+    torch.cuda.synchronize()
+    d1 = s.diagnostics()
+    st = s.stats()
+    s.close()
+    ms = ev[0].elapsed_time(ev[1]) + ev[2].elapsed_time(ev[3])
+    pscale = float(np.sum(np.abs(mass * vel)))
+    return {"workload": "Plummer sphere N=4096 (a=1, distribution-function velocities), Plummer eps=0.01, p=4, "
+                        "theta=0.5, fp64, batched HHS k_max=10 dt_max=1/64 eta=0.025: initial evaluation + 16 steps",
+            "ms_total": ms, "value": st["sink_forces"] / (ms / 1e3), "unit": "particle-forces/s",
+            "evaluations": st["evaluations"], "max_rung": st["max_rung"],
+            "momentum_drift": float(np.linalg.norm(d1[:3] - d0[:3])) / pscale,
+            "energy_drift": float(abs((d1[6] - d0[6]) / d0[6]))}
 
 
 ENSEMBLE_PARAMS = dict(p=4, theta=0.5, eps=0.01, kernel=1, n_crit=64, kappa=1.0, eta=0.025, dt_max=1.0 / 64, k_max=10)
