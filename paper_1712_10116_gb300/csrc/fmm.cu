@@ -373,17 +373,27 @@ __global__ void __launch_bounds__(128) p2m_leaves(TreeView t, const Geom *gp, co
     }
 }
 
-__constant__ float c_binom_f[9][9] = {
-    {1, 0, 0, 0, 0, 0, 0, 0, 0},       {1, 1, 0, 0, 0, 0, 0, 0, 0},        {1, 2, 1, 0, 0, 0, 0, 0, 0},
-    {1, 3, 3, 1, 0, 0, 0, 0, 0},       {1, 4, 6, 4, 1, 0, 0, 0, 0},        {1, 5, 10, 10, 5, 1, 0, 0, 0},
-    {1, 6, 15, 20, 15, 6, 1, 0, 0},    {1, 7, 21, 35, 35, 21, 7, 1, 0},    {1, 8, 28, 56, 70, 56, 28, 8, 1}};
+// coefficient i of a generated translation list in the precision of the expansions
+template <class T>
+__device__ __forceinline__ T trans_coef(const float *cf, const double *cd, int i);
+template <>
+__device__ __forceinline__ float trans_coef<float>(const float *cf, const double *, int i)
+{
+    return cf[i];
+}
+template <>
+__device__ __forceinline__ double trans_coef<double>(const float *, const double *cd, int i)
+{
+    return cd[i];
+}
 
 // M2M for the parents of one level, normalised: with d = z_child - z_parent = (+-s/4)^3 and
 // s_child = s/2,  M~_P^n = sum_children sum_{k <= n} C(n,k) 2^-(2|n-k| + |k|) (+-1)^(n-k) M~_c^k.
 // Block per parent cell.  |n| <= 1 in float64 (M01, threads 0..7), every order also in T (M).
 // Orders >= 2: lane (n, q) with q = lane % 8 sums the terms k <= n (componentwise) of child q,
 // then the eight children are added with three shuffles.  The children's moments are staged in
-// shared memory; the multi-index tables too, since the lanes index them with different n.
+// shared memory; the terms of each n (coefficient index, parity of n - k, coefficient) come from the
+// generated lists g_m2m_* in the order of the sum, k_x outermost.
 constexpr int kM2MThreads = 256;
 
 template <class T>
@@ -397,16 +407,6 @@ __global__ void __launch_bounds__(kM2MThreads) m2m_level(TreeView t, int lb, int
     }
     extern __shared__ __align__(16) unsigned char m2m_smem[];
     T *s_mc = reinterpret_cast<T *>(m2m_smem);   // [8 children][2 classes][ncp]
-    __shared__ uint8_t s_lookup[9 * 9 * 9];
-    __shared__ uint8_t s_e[3][168];
-    __shared__ float s_binom[9][9];
-    for (int k = threadIdx.x; k < 729; k += blockDim.x) s_lookup[k] = c_mi_lookup[k];
-    for (int k = threadIdx.x; k < 168; k += blockDim.x) {
-        s_e[0][k] = k < nc ? c_mi_x[k] : 0;
-        s_e[1][k] = k < nc ? c_mi_y[k] : 0;
-        s_e[2][k] = k < nc ? c_mi_z[k] : 0;
-    }
-    for (int k = threadIdx.x; k < 81; k += blockDim.x) s_binom[k / 9][k % 9] = c_binom_f[k / 9][k % 9];
     const int lane = threadIdx.x & 31, q = lane & 7;
     const int sub = threadIdx.x >> 3;   // 0 .. blockDim/8 - 1: which n of the pass
     const int per_pass = blockDim.x >> 3;
@@ -436,31 +436,25 @@ __global__ void __launch_bounds__(kM2MThreads) m2m_level(TreeView t, int lb, int
             M01[((size_t)c * 2 + cls) * 4 + n] = acc;
             M[((size_t)c * 2 + cls) * ncp + n] = (T)acc;
         }
-        // this lane's child: offsets toward the negative side flip the sign of odd powers
-        bool neg_x = false, neg_y = false, neg_z = false;
-        if (q < nch) {
-            neg_x = !(t.cx[cf + q] & 1u);
-            neg_y = !(t.cy[cf + q] & 1u);
-            neg_z = !(t.cz[cf + q] & 1u);
-        }
+        // this lane's child: offsets toward the negative side flip the sign of odd powers (bit a of negm)
+        unsigned negm = 0u;
+        if (q < nch)
+            negm = (t.cx[cf + q] & 1u ? 0u : 1u) | (t.cy[cf + q] & 1u ? 0u : 2u) | (t.cz[cf + q] & 1u ? 0u : 4u);
         const T *MS = s_mc + q * 2 * ncp, *MF = MS + ncp;
         for (int n0 = 4; n0 < ncp; n0 += per_pass) {
             const int n = n0 + sub;
             T sS = 0, sF = 0;
             if (n < nc && q < nch) {
-                const int nx = s_e[0][n], ny = s_e[1][n], nz = s_e[2][n], on = nx + ny + nz;
-                for (int kx = 0; kx <= nx; ++kx)
-                    for (int ky = 0; ky <= ny; ++ky)
-                        for (int kz = 0; kz <= nz; ++kz) {
-                            const int k = s_lookup[(kx * 9 + ky) * 9 + kz], ok = kx + ky + kz;
-                            T coef = (T)(s_binom[nx][kx] * s_binom[ny][ky] * s_binom[nz][kz] *
-                                         pow2f(-(2 * (on - ok) + ok)));
-                            const bool neg = (neg_x && ((nx - kx) & 1)) ^ (neg_y && ((ny - ky) & 1)) ^
-                                             (neg_z && ((nz - kz) & 1));
-                            coef = neg ? -coef : coef;
-                            sS += coef * MS[k];
-                            sF += coef * MF[k];
-                        }
+                // the terms k <= n from the generated list: coefficient index, parity of n - k, coefficient
+                const int i1 = g_m2m_off[n + 1];
+                for (int i = g_m2m_off[n]; i < i1; ++i) {
+                    const unsigned kp = g_m2m_kp[i];
+                    const int k = (int)(kp & 0xffu);
+                    T coef = trans_coef<T>(g_m2m_cf, g_m2m_cd, i);
+                    coef = (__popc((kp >> 8) & negm) & 1) ? -coef : coef;
+                    sS += coef * MS[k];
+                    sF += coef * MF[k];
+                }
             }
             // sum over the eight children (lanes q = 0..7 of this n)
 #pragma unroll
@@ -667,8 +661,8 @@ __global__ void mac_params_dev(const Geom *g, double eps, MacParams *mp)
 // L~_c^n += sum_{d} L~_P^(n+d) (+-1)^d 2^-(2|d| + |n| + 1) / d!  over |d| <= p - |n|.
 // Warp per cell of the level, lanes over the coefficients n >= n_first (1 when only accelerations are
 // wanted: L^0 feeds no force), both classes.  d runs through the
-// multi-indices in their table order (the same d for every lane at each step); the index of n + d
-// comes from a lookup table in shared memory.
+// multi-indices in their table order; the index of n + d, the parity of d and the coefficient come
+// from the generated list g_l2l_* of n (built for order 8: order p takes its first terms).
 constexpr int kM2MWarps = 2;   // warps per block of the L2L level kernel
 
 template <class T>
@@ -683,36 +677,28 @@ __global__ void __launch_bounds__(32 * kM2MWarps) l2l_level(TreeView t, int lb, 
     }
     extern __shared__ __align__(16) unsigned char l2l_smem[];
     T *s_lp = reinterpret_cast<T *>(l2l_smem) + (size_t)(threadIdx.x >> 5) * 2 * ncp;   // parent's L, this warp
-    __shared__ uint8_t s_lookup[9 * 9 * 9];
-    __shared__ uint8_t s_e[3][168];
-    for (int k = threadIdx.x; k < 729; k += blockDim.x) s_lookup[k] = c_mi_lookup[k];
-    for (int k = threadIdx.x; k < 168; k += blockDim.x) {
-        s_e[0][k] = k < nc ? c_mi_x[k] : 0;
-        s_e[1][k] = k < nc ? c_mi_y[k] : 0;
-        s_e[2][k] = k < nc ? c_mi_z[k] : 0;
-    }
-    __syncthreads();
     const int lane = threadIdx.x & 31;
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nwarps = (gridDim.x * blockDim.x) >> 5;
     for (int c = lb + warp; c < le; c += nwarps) {
         const int par = t.parent[c];
         if (par < 0) continue;
-        const bool neg_x = !(t.cx[c] & 1u), neg_y = !(t.cy[c] & 1u), neg_z = !(t.cz[c] & 1u);
+        // offsets toward the negative side flip the sign of odd powers (bit a of negm)
+        const unsigned negm = (t.cx[c] & 1u ? 0u : 1u) | (t.cy[c] & 1u ? 0u : 2u) | (t.cz[c] & 1u ? 0u : 4u);
         __syncwarp();
 #pragma unroll 4
         for (int k = lane; k < ncls * ncp; k += 32) s_lp[k] = L[(size_t)par * 2 * ncp + k];
         __syncwarp();
         const T *Lp = s_lp;
         for (int n = n_first + lane; n < nc; n += 32) {
-            const int nx = s_e[0][n], ny = s_e[1][n], nz = s_e[2][n], on = nx + ny + nz;
-            const int nd = ncoef_dev(p - on);   // multi-indices d with |d| <= p - |n|
+            // the terms d with |d| <= p - |n|: the first ones of n's generated list (built for order 8)
+            const int nd = ncoef_dev(p - (int)c_mi_order[n]);
+            const int i0 = g_l2l_off[n];
             T acc0 = 0, acc1 = 0;
             for (int d = 0; d < nd; ++d) {
-                const int dx = c_mi_x[d], dy = c_mi_y[d], dz = c_mi_z[d];
-                const int k = s_lookup[((nx + dx) * 9 + ny + dy) * 9 + nz + dz];
-                const bool neg = (neg_x && (dx & 1)) ^ (neg_y && (dy & 1)) ^ (neg_z && (dz & 1));
-                const T coef = inv_fact_t<T>(d) * (T)pow2f(-(2 * (dx + dy + dz) + on + 1));
-                const T cs = neg ? -coef : coef;
+                const unsigned kp = g_l2l_kp[i0 + d];
+                const int k = (int)(kp & 0xffu);
+                const T coef = trans_coef<T>(g_l2l_cf, g_l2l_cd, i0 + d);
+                const T cs = (__popc((kp >> 8) & negm) & 1) ? -coef : coef;
                 acc0 += Lp[k] * cs;
                 if (ncls > 1) acc1 += Lp[ncp + k] * cs;
             }
