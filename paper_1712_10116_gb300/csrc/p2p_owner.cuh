@@ -26,32 +26,58 @@ namespace tg {
 constexpr int kOwnUnit = 32;   // partners per work unit of the owner kernel (one per lane)
 
 // Owner and partner of each distinct leaf pair, and per-owner partner counts (own_cnt starts at zero).
+// The walk writes the pairs of one row cell side by side, so lanes of a warp often share an owner:
+// the lanes with equal owners add their count with one atomic (whole warps iterate together).
 __global__ void p2p_owner_count(const uint2 *__restrict__ pairs, int64_t npairs, const int32_t *__restrict__ count,
                                 uint32_t *own_cnt, uint2 *tagged, const unsigned long long *dnp)
 {
     if (dnp) npairs = (int64_t)*dnp;
-    for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < npairs; w += (int64_t)gridDim.x * blockDim.x) {
-        const uint32_t x = pairs[w].x, y = pairs[w].y;
-        const int cx = count[x], cy = count[y];
-        const uint32_t owner = (cx > cy || (cx == cy && x > y)) ? x : y;
-        tagged[w] = make_uint2(owner, owner == x ? y : x);
-        atomicAdd(&own_cnt[owner], 1u);
+    const int lane = threadIdx.x & 31;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t w0 = (int64_t)blockIdx.x * blockDim.x; w0 < npairs; w0 += stride) {
+        const int64_t w = w0 + threadIdx.x;
+        uint32_t owner = 0xffffffffu;
+        if (w < npairs) {
+            const uint32_t x = pairs[w].x, y = pairs[w].y;
+            const int cx = count[x], cy = count[y];
+            owner = (cx > cy || (cx == cy && x > y)) ? x : y;
+            tagged[w] = make_uint2(owner, owner == x ? y : x);
+        }
+        const unsigned peers = __match_any_sync(0xffffffffu, owner);
+        if (owner != 0xffffffffu && lane == __ffs(peers) - 1) atomicAdd(&own_cnt[owner], (uint32_t)__popc(peers));
     }
 }
 
 // Partners grouped by owner: partners[own_off[B] .. own_off[B] + own_cnt[B]).  Every kOwnUnit-th
 // partner of an owner also opens a work unit (owner, position); ctr[0] counts the units.
-// own_fill and ctr start at zero.
+// own_fill and ctr start at zero.  Lanes with equal owners take consecutive slots with one atomic, and
+// the units a warp opens are reserved with one atomic on ctr[0] (whole warps iterate together).
 __global__ void p2p_owner_fill(const uint2 *__restrict__ tagged, int64_t npairs, const uint32_t *__restrict__ own_off,
                                uint32_t *own_fill, int32_t *partners, uint2 *units, uint32_t *ctr,
                                const unsigned long long *dnp)
 {
     if (dnp) npairs = (int64_t)*dnp;
-    for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < npairs; w += (int64_t)gridDim.x * blockDim.x) {
-        const uint2 op = tagged[w];
-        const uint32_t f = atomicAdd(&own_fill[op.x], 1u);
-        partners[own_off[op.x] + f] = (int32_t)op.y;
-        if (f % kOwnUnit == 0) units[atomicAdd(&ctr[0], 1u)] = make_uint2(op.x, f);
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t w0 = (int64_t)blockIdx.x * blockDim.x; w0 < npairs; w0 += stride) {
+        const int64_t w = w0 + threadIdx.x;
+        const bool valid = w < npairs;
+        uint2 op = make_uint2(0xffffffffu, 0u);
+        if (valid) op = tagged[w];
+        const unsigned peers = __match_any_sync(0xffffffffu, op.x);
+        const int leader = __ffs(peers) - 1;
+        uint32_t base = 0u;
+        if (valid && lane == leader) base = atomicAdd(&own_fill[op.x], (uint32_t)__popc(peers));
+        base = __shfl_sync(0xffffffffu, base, leader);
+        const uint32_t f = base + (uint32_t)__popc(peers & lt);
+        if (valid) partners[own_off[op.x] + f] = (int32_t)op.y;
+        const bool opens = valid && f % kOwnUnit == 0;
+        const unsigned ob = __ballot_sync(0xffffffffu, opens);
+        uint32_t ubase = 0u;
+        if (lane == 0 && ob) ubase = atomicAdd(&ctr[0], (uint32_t)__popc(ob));
+        ubase = __shfl_sync(0xffffffffu, ubase, 0);
+        if (opens) units[ubase + __popc(ob & lt)] = make_uint2(op.x, f);
     }
 }
 
