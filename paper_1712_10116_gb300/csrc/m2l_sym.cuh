@@ -196,8 +196,6 @@ __global__ void __launch_bounds__(128) m2l_blocks_f32(TreeView t, const M2LBlock
     const int j = lane & 7, rr = (lane >> 3) & 3;
     const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    constexpr int NC4 = (NC + 3) & ~3;
-    __shared__ float4 pk[128 * (NC4 / 4)];   // packed rounds: each lane's y-side expansion
     const int64_t n_multi = (int64_t)pcnt[0], n_single = (int64_t)pcnt[1];
     const int64_t n_items = n_multi + (n_single + 3) / 4;
     for (int64_t w = wid; w < n_items; w += nw) {
@@ -320,31 +318,19 @@ __global__ void __launch_bounds__(128) m2l_blocks_f32(TreeView t, const M2LBlock
                             if (k0 + g < NC) atomicAdd(reinterpret_cast<float4 *>(dst + k0 + g), make_float4(v[0], v[1], v[2], v[3]));
                         }
                     }
-                } else {
-                    // packed rounds: each lane's whole expansion (its column belongs to its own block),
-                    // staged in shared memory so that it is not held in registers beside the derivative tensor
-                    float4 *buf = pk + threadIdx.x * (NC4 / 4);
+                } else if (col_used) {
+                    // packed rounds: each lane's whole expansion (its column belongs to its own block)
+                    float sc = rho;   // order 0: rho^1
+                    const float nrho = -rho;
 #pragma unroll
-                    for (int g = 0; g < NC4; g += 4) buf[g / 4] = make_float4(Lc[g], Lc[g + 1], Lc[g + 2], Lc[g + 3]);
-                    if (col_used) {
-                        int o = 0, next = first_of_order(G::HARMONIC, 1);
-                        float sc = rho;   // order 0: rho^1
-                        const float nrho = -rho;
-#pragma unroll 1
-                        for (int g = 0; g < NC; g += 4) {
-                            const float4 u = buf[g / 4];
-                            float v[4] = {u.x, u.y, u.z, u.w};
+                    for (int g = 0; g < NC; g += 4) {
+                        float v[4];
 #pragma unroll
-                            for (int q = 0; q < 4; ++q) {
-                                if (g + q == next) {
-                                    ++o;
-                                    next = first_of_order(G::HARMONIC, o + 1);
-                                    sc *= nrho;
-                                }
-                                v[q] *= sc;
-                            }
-                            atomicAdd(reinterpret_cast<float4 *>(dst + g), make_float4(v[0], v[1], v[2], v[3]));
+                        for (int q = 0; q < 4; ++q) {
+                            if (g + q > 0 && order_in(G::HARMONIC, g + q) != order_in(G::HARMONIC, g + q - 1)) sc *= nrho;
+                            v[q] = Lc[g + q] * sc;
                         }
+                        atomicAdd(reinterpret_cast<float4 *>(dst + g), make_float4(v[0], v[1], v[2], v[3]));
                     }
                 }
             }
