@@ -67,13 +67,20 @@ static MacParams make_mac_params(const tg_params &prm, int log2L)
     return mp;
 }
 
-__device__ __forceinline__ bool well_separated(const TreeView &t, const MacParams &mp, int a, int b)
+// The test from the cells' levels and integer coordinates (the dual walk loads the eight column cells
+// of a pair once, side by side); a and b are only read by the sphere criterion.
+struct CellGeo {
+    uint32_t x, y, z;
+    int level;
+};
+__device__ __forceinline__ bool well_separated_geo(const TreeView &t, const MacParams &mp, int a, const CellGeo &ga,
+                                                   int b, const CellGeo &gb)
 {
-    const int la = t.level[a], lb = t.level[b];
+    const int la = ga.level, lb = gb.level;
     const int lf = la > lb ? la : lb;
     const long long ha = 1ll << (lf - la), hb = 1ll << (lf - lb);
-    const long long dxs[3] = {centre_delta(t.cx[a], la, t.cx[b], lb, lf), centre_delta(t.cy[a], la, t.cy[b], lb, lf),
-                              centre_delta(t.cz[a], la, t.cz[b], lb, lf)};
+    const long long dxs[3] = {centre_delta(ga.x, la, gb.x, lb, lf), centre_delta(ga.y, la, gb.y, lb, lf),
+                              centre_delta(ga.z, la, gb.z, lb, lf)};
     long long d2 = 0, g2 = 0;
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
@@ -100,6 +107,12 @@ __device__ __forceinline__ bool well_separated(const TreeView &t, const MacParam
     }
     if (mp.wendland && g2 < mp.gap_min_g2[lf]) return false;
     return true;
+}
+
+__device__ __forceinline__ bool well_separated(const TreeView &t, const MacParams &mp, int a, int b)
+{
+    return well_separated_geo(t, mp, a, CellGeo{t.cx[a], t.cy[a], t.cz[a], (int)t.level[a]}, b,
+                              CellGeo{t.cx[b], t.cy[b], t.cz[b], (int)t.level[b]});
 }
 
 // ------------------------------------------------------------------ enclosing radii (TG_MAC_SPHERE)
@@ -572,23 +585,37 @@ __device__ __forceinline__ void walk_step_body(const TreeView &t, const MacParam
             nj = openB ? t.nchild[B] : 1;
             baseA = openA ? t.child_first[A] : A;
             baseB = openB ? t.child_first[B] : B;
+            // the column cells' geometry, loaded once (independent loads, issued together)
+            CellGeo gy[8];
+            bool ly[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const int y = baseB + (j < nj ? j : 0);
+                gy[j] = CellGeo{t.cx[y], t.cy[y], t.cz[y], (int)t.level[y]};
+                ly[j] = t.nchild[y] == 0;
+            }
             // classify every child pair once
-            for (int i = 0; i < ni; ++i)
-                for (int j = self ? i : 0; j < nj; ++j) {
-                    const int x = baseA + i, y = baseB + j;
-                    const bool lx = t.nchild[x] == 0, ly = t.nchild[y] == 0;
+            for (int i = 0; i < ni; ++i) {
+                const int x = baseA + i;
+                const CellGeo gx{t.cx[x], t.cy[x], t.cz[x], (int)t.level[x]};
+                const bool lx = t.nchild[x] == 0;
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    if (j >= nj || (self && j < i)) continue;
+                    const int y = baseB + j;
                     const unsigned long long bit = 1ull << (8 * i + j);
                     if (x == y) {
                         if (lx) mself |= bit;
                         else mfront |= bit;
-                    } else if (well_separated(t, mp, x, y)) {
+                    } else if (well_separated_geo(t, mp, x, gx, y, gy[j])) {
                         mask |= bit;
-                    } else if (lx && ly) {
+                    } else if (lx && ly[j]) {
                         mp2p |= bit;
                     } else {
                         mfront |= bit;
                     }
                 }
+            }
         }
         unsigned long long fb = warp_reserve(o.front_ctr, (unsigned)__popcll(mfront));
         unsigned long long pb = warp_reserve(o.counters + 2, (unsigned)__popcll(mp2p));
