@@ -64,7 +64,7 @@ typedef struct {
     int p;            /* expansion order: Taylor terms of total degree <= p, 1 <= p <= 20     */
                       /* (p <= 6: generated float32 contractions; p > 8: table-free kernels   */
                       /* for the order sweeps of Sec. 3.2, slower)                             */
-    int n_crit;       /* a cell holding more than n_crit particles is split (Sec. 2.3), 1..128 */
+    int n_crit;       /* a cell holding more than n_crit particles is split (Sec. 2.3), 1..256 */
     int kernel;       /* tg_kernel                                                          */
     int precision;    /* tg_precision                                                       */
     int max_level;    /* deepest octree level, 1..21 (21 = Morton-key resolution)           */
@@ -253,7 +253,7 @@ tg_status tg_debug_control(tg_ctx *ctx, int what, int64_t value);
  * for this GPU and this particle distribution) ----
  * tg_autotune times FMM evaluations of the given system (CUDA events on the context's stream, one
  * warm-up, best of two) for candidate settings and keeps the fastest in the context:
- *   n_crit            leaf size: 48, 64, 80, 96, 112, 128 (the tree, and so the results, change within
+ *   n_crit            leaf size: 48, 64, 80, 96, 112, 128, 160, 192 (the tree, and so the results, change within
  *                     the FMM's own accuracy; params.n_crit of the context is replaced)
  *   p2p_rows          rows per lane of the float32 P2P tile: 1, 2, 3 (results unchanged)
  *   m2l_blocks_per_sm grid of the float32 M2L kernel in blocks per SM: 4, 8, 16, 32 (results unchanged)
@@ -285,7 +285,7 @@ typedef struct {
 tg_status tg_autotune(tg_ctx *ctx, int64_t n, const double *pos, const double *mass, const uint8_t *is_fast,
                       tg_tuning *out);
 tg_status tg_get_tuning(const tg_ctx *ctx, tg_tuning *out);
-/* Apply settings found by tg_autotune on another context (n_crit 1..128, p2p_rows 1..3,
+/* Apply settings found by tg_autotune on another context (n_crit 1..256, p2p_rows 1..3,
  * m2l_blocks_per_sm 1..64; the other fields are ignored).  TG_ERR_ARG for values out of range. */
 tg_status tg_set_tuning(tg_ctx *ctx, const tg_tuning *in);
 

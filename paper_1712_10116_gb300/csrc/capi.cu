@@ -20,7 +20,7 @@ tg_status validate(const tg_params *p, std::string &why)
         return TG_ERR_ARG;
     }
     if (p->p < 1 || p->p > kPHigh) why = "p must be in [1, 20]";
-    else if (p->n_crit < 1 || p->n_crit > kMaxNcrit) why = "n_crit must be in [1, 128]";
+    else if (p->n_crit < 1 || p->n_crit > 2 * kMaxNcrit) why = "n_crit must be in [1, 256]";
     else if (p->kernel != TG_KERNEL_WENDLAND_C2 && p->kernel != TG_KERNEL_PLUMMER) why = "unknown kernel";
     else if (p->precision != TG_PREC_FP64 && p->precision != TG_PREC_FP32) why = "unknown precision";
     else if (p->max_level < 1 || p->max_level > kMaxLevel) why = "max_level must be in [1, 21]";
@@ -388,7 +388,7 @@ tg_status tg_set_tuning(tg_ctx *c, const tg_tuning *in)
 {
     tg_status st = begin(c);
     if (st) return st;
-    if (!in || in->n_crit < 1 || in->n_crit > kMaxNcrit || in->p2p_rows < 1 || in->p2p_rows > 3 ||
+    if (!in || in->n_crit < 1 || in->n_crit > 2 * kMaxNcrit || in->p2p_rows < 1 || in->p2p_rows > 3 ||
         in->m2l_blocks_per_sm < 1 || in->m2l_blocks_per_sm > 64 || in->m2l_form < 0 || in->m2l_form > 1)
         return set_err(c, TG_ERR_ARG, "tg_set_tuning: settings out of range");
     c->prm.n_crit = in->n_crit;

@@ -12,7 +12,7 @@
 namespace tg {
 
 constexpr int kMaxLevel = 21;         // Morton keys carry 21 bits per axis
-constexpr int kMaxNcrit = 128;        // leaf capacity supported by the P2P tiles
+constexpr int kMaxNcrit = 128;        // columns of a P2P tile: larger leaves (n_crit up to 256) take several
 
 inline int ncoef(int p) { return (p + 1) * (p + 2) * (p + 3) / 6; }
 

@@ -123,7 +123,7 @@ tg_status autotune(tg_ctx *c, int n, const double *pos, const double *mass, cons
     best = initial;
     tg_tuning choice = c->tune;
     choice.n_crit = c->prm.n_crit;
-    const int ncrit_cand[] = {48, 64, 80, 96, 112, 128};
+    const int ncrit_cand[] = {48, 64, 80, 96, 112, 128, 160, 192};
     for (int nc : ncrit_cand) {
         if (nc == prm0.n_crit) continue;
         c->prm.n_crit = nc;

@@ -37,12 +37,12 @@ def test_autotune_picks_a_candidate_and_stays_correct(precision):
     s = tg.Solver(prm)
     P, M, F = _t(pos), _t(mass), _t(fast, torch.uint8)
     t = s.autotune(P, M, F)
-    assert t["n_crit"] in (48, 64, 80, 96, 112, 128)
+    assert t["n_crit"] in (48, 64, 80, 96, 112, 128, 160, 192)
     if precision == 1:
         assert t["p2p_rows"] in (1, 2, 3) and t["m2l_blocks_per_sm"] in (4, 8, 16, 32) and t["m2l_form"] in (0, 1)
-        assert t["candidates"] == 1 + 5 + 1 + 2 + 3 + 1
+        assert t["candidates"] == 1 + 7 + 1 + 2 + 3 + 1
     else:
-        assert t["p2p_rows"] == 2 and t["m2l_blocks_per_sm"] == 16 and t["candidates"] == 6
+        assert t["p2p_rows"] == 2 and t["m2l_blocks_per_sm"] == 16 and t["candidates"] == 8
     assert 0 < t["objective_ms"] <= 1.25 * t["objective_ms_initial"]
     assert tg.tg_get_tuning(s.ctx) == t
     st = s.stats()
@@ -75,8 +75,8 @@ def test_step_autotune_leaves_the_bound_system_as_it_was(batched):
     time0 = s.diagnostics()[7]
     t = s.autotune()
     torch.cuda.synchronize()
-    assert t["candidates"] == 1 + 5 + 1 + 2 + 3 + 1 - (1 if prm["kernel"] == 1 else 0)
-    assert t["n_crit"] in (48, 64, 80, 96, 112, 128) and t["objective_ms"] > 0
+    assert t["candidates"] == 1 + 7 + 1 + 2 + 3 + 1 - (1 if prm["kernel"] == 1 else 0)
+    assert t["n_crit"] in (48, 64, 80, 96, 112, 128, 160, 192) and t["objective_ms"] > 0
     assert torch.equal(P, P0) and torch.equal(V, V0)
     for a, b in zip(tg.tg_hhs_state(s.ctx, n, DEV, with_total=True), state0):
         assert torch.equal(a, b)

@@ -223,6 +223,27 @@ def test_fmm_fp32_matches_oracle(kind, kernel, p, theta, masked):
     assert np.abs(pot.cpu().numpy() - p_o).max() < FP32_TOL * np.abs(p_o).max()
 
 
+@pytest.mark.parametrize("n_crit", [160, 256])
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_leaves_wider_than_a_p2p_tile(n_crit, precision):
+    # leaves of more than 128 particles: the P2P kernels take their columns in several tiles
+    n = 20000
+    pos, _, mass = _case("clustered", n)
+    fast = ics.random_fast_mask(n, 19)
+    prec = tg.TG_PREC_FP64 if precision == "fp64" else tg.TG_PREC_FP32
+    prm = tg.Params(p=6, theta=0.5, eps=0.005, kernel=0, precision=prec, n_crit=n_crit)
+    s = tg.Solver(prm)
+    for mask in (None, fast):
+        acc, _ = s.fmm_forces(_t(pos), _t(mass), None if mask is None else _t(mask, torch.uint8))
+        a_o, _ = oracle.fmm(pos, mass, _oprm(prm), mask)
+        if precision == "fp64":
+            nb = np.linalg.norm(a_o, axis=0)
+            assert (np.linalg.norm(acc.cpu().numpy() - a_o, axis=0) / nb).max() < 1e-12
+        else:
+            _check_fp32(acc.cpu().numpy(), a_o)
+    s.close()
+
+
 @pytest.mark.parametrize("kind", ["sphere", "clustered"])
 @pytest.mark.parametrize("masked", [False, True])
 def test_fmm_fp32_wide_softening(kind, masked):
