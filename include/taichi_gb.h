@@ -100,7 +100,8 @@ typedef struct {
     int64_t max_rung;        /* deepest rung that held a slow particle                          */
     int64_t m2l_class_pairs; /* M2L cell pairs x local-expansion classes the pair's targets need     */
                              /* (a kick pair's cell needs class 0 only if it holds slow particles, */
-                             /* class 1 only if it holds fast ones; counted per side, halved)      */
+                             /* class 1 only if it holds fast ones and the source slow ones, since */
+                             /* class 1 carries the slow masses; counted per side, halved)         */
     int64_t list_regrowths;  /* dual walks re-run because an interaction list outgrew its buffer  */
     int64_t host_syncs;      /* host waits on the stream inside evaluations and HHS steps         */
 } tg_stats;

@@ -175,9 +175,11 @@ static __global__ void m2l_partition(const M2LBlock *__restrict__ in, int64_t nb
 // the other class count returns at once.
 // Kick pairs (MASKED) with fpre (the prefix sum of the fast flags over the sorted particles): a target
 // cell needs the all-sources local (class 0) only if it holds slow particles, and the slow-sources local
-// (class 1) only if it holds fast particles; a round skips a side's contraction of a class when no
-// target of that side needs it (a warp vote, so the warp stays converged).  The skipped locals are read
-// by no particle: L2L hands them only to descendants, which hold no particle of that class either.
+// (class 1) only if it holds fast particles, and a class-1 contraction adds something only if its source
+// holds slow particles (class 1 carries the slow masses); a round skips a side's contraction of a class
+// when no pair of the round needs it (a warp vote, so the warp stays converged).  The skipped locals are
+// read by no particle (L2L hands them only to descendants, which hold no particle of that class either),
+// and the skipped class-1 terms are zero.
 template <class G, bool MASKED, bool POT>
 __global__ void __launch_bounds__(128) m2l_blocks_f32(TreeView t, const M2LBlock *__restrict__ part, int64_t cap,
                                                       const unsigned long long *__restrict__ pcnt,
@@ -243,7 +245,9 @@ __global__ void __launch_bounds__(128) m2l_blocks_f32(TreeView t, const M2LBlock
             const bool row_used = ((amask >> (lane & ~7)) & 0xffu) != 0u;   // this lane's row, this round
             // this lane's column, this round (packed: the lane's own pair, its block has one row)
             const bool col_used = packed ? active : (amask & (0x01010101u << j)) != 0u;
-            // classes the round's targets need (side a: the row cells, side b: the column cells)
+            // classes the round's targets need (side a: the row cells, side b: the column cells).  Class 1
+            // holds the slow masses only: a source without slow particles has zero class-1 moments, so
+            // its class-1 contraction adds nothing and is left out with the others of the round.
             unsigned need = 0xfu;   // bit cls: side a needs class cls; bit 2 + cls: side b does
             if (MASKED && fpre) {
                 int fx = 0, sx = 0, fy = 0, sy = 0;
@@ -254,9 +258,10 @@ __global__ void __launch_bounds__(128) m2l_blocks_f32(TreeView t, const M2LBlock
                     fy = (int)(fpre[ay + t.count[y]] - fpre[ay]);
                     sy = t.count[y] - fy;
                 }
-                need = (__any_sync(0xffffffffu, sx > 0) ? 1u : 0u) | (__any_sync(0xffffffffu, fx > 0) ? 2u : 0u) |
-                       (__any_sync(0xffffffffu, sy > 0) ? 4u : 0u) | (__any_sync(0xffffffffu, fy > 0) ? 8u : 0u);
-                my_sc += (unsigned)(sx > 0) + (unsigned)(fx > 0) + (unsigned)(sy > 0) + (unsigned)(fy > 0);
+                const bool a1 = fx > 0 && sy > 0, b1 = fy > 0 && sx > 0;
+                need = (__any_sync(0xffffffffu, sx > 0) ? 1u : 0u) | (__any_sync(0xffffffffu, a1) ? 2u : 0u) |
+                       (__any_sync(0xffffffffu, sy > 0) ? 4u : 0u) | (__any_sync(0xffffffffu, b1) ? 8u : 0u);
+                my_sc += (unsigned)(sx > 0) + (unsigned)a1 + (unsigned)(sy > 0) + (unsigned)b1;
             } else if (active) {
                 my_sc += MASKED ? 4u : 2u;
             }

@@ -346,13 +346,19 @@ __global__ void __launch_bounds__(256, 2) p2p_owner_f32(TreeView t, int log2L, c
             const int Ts = __shfl_sync(0xffffffffu, incS, 31), Tf = __shfl_sync(0xffffffffu, incF, 31);
             const int nearS = n_near ? __shfl_sync(0xffffffffu, incS, n_near - 1) : 0;
             const int nearF = n_near ? __shfl_sync(0xffffffffu, incF, n_near - 1) : 0;
+            // nothing to evaluate: no slow rows, and no slow column for the fast rows (kick pairs of the
+            // lowest rungs, whose slow set is a few particles of the whole system)
+            if (Ts == 0 && (Tf == 0 || sB == 0)) continue;
             for (int jc = 0; jc < nb; jc += kMaxNcrit) {
                 const int nbc = min(kMaxNcrit, nb - jc);
-                // columns in leaf order (slow first), padded to a multiple of 8 once
+                // columns in leaf order (slow first), padded to a multiple of 8 once; without slow rows only
+                // the slow columns (for the fast rows) are staged and flushed
                 const int nsc = max(0, min(sB - jc, nbc));   // slow columns of this chunk (slow-first leaf)
                 const int ns8 = (nsc + 7) & ~7, nt8 = (nbc + 7) & ~7;
+                const int nstage = Ts > 0 ? nt8 : ns8, nflush = Ts > 0 ? nbc : nsc;
+                if (nstage == 0) continue;
                 __syncwarp();
-                for (int j = lane; j < nt8; j += 32) {
+                for (int j = lane; j < nstage; j += 32) {
                     sq[j] = j < nbc ? pf[fb + jc + j] : make_float4(-1e8f, -1e8f, -1e8f, 0.f);
                     sacc[j][0] = sacc[j][1] = sacc[j][2] = sacc[j][3] = 0.f;
                 }
@@ -373,7 +379,7 @@ __global__ void __launch_bounds__(256, 2) p2p_owner_f32(TreeView t, int log2L, c
                     }
                 }
                 __syncwarp();
-                for (int j = lane; j < nbc; j += 32)
+                for (int j = lane; j < nflush; j += 32)
 #pragma unroll
                     for (int comp = 0; comp < (POT ? 4 : 3); ++comp)
                         atomicAdd(&acc4[(size_t)comp * n + fb + jc + j], f2d_exact(sacc[j][comp]));
