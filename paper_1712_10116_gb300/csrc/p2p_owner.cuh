@@ -281,6 +281,7 @@ __global__ void __launch_bounds__(256, 2) p2p_owner_f32(TreeView t, int log2L, c
             if (k - nunits >= nself) break;
             const int A = (int)self_pairs[k - nunits].x;
             const int fa = t.first[A], na = t.count[A], sa = nslow ? nslow[A] : na;
+            if (sa == 0) continue;   // no slow row: every pair of the leaf is fast-fast
             __syncwarp();
             p2p_pair_f32<KERNEL, true, ROWS, true>(pf, fa, sa, fa, na, 0.f, 0.f, 0.f, eps, acc4, n, lane, sq);
             if (lane == 0) {
