@@ -92,6 +92,17 @@ tg_status tg_create(const tg_params *params, void *cuda_stream, tg_ctx **out)
         delete c;
         return TG_ERR_OOM;
     }
+    if (cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        if (c->side) cudaStreamDestroy(c->side);
+        if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+        cudaFreeHost(c->h_pinned);
+        cudaFree(c->d_counters);
+        delete c;
+        return TG_ERR_CUDA;
+    }
     cudaMemset(c->d_counters, 0, 32 * sizeof(unsigned long long));
     std::memset(c->h_pinned, 0, 64 * sizeof(int64_t));
     *out = c;
@@ -102,12 +113,16 @@ tg_status tg_destroy(tg_ctx *c)
 {
     if (!c) return TG_ERR_ARG;
     cudaStreamSynchronize(c->stream);
+    if (c->side) cudaStreamSynchronize(c->side);
     hold_graph_destroy(c);
     for (auto &b : c->buf)
         if (b.p) cudaFree(b.p);
     for (cudaEvent_t e : c->prof_events) cudaEventDestroy(e);
     if (c->d_counters) cudaFree(c->d_counters);
     if (c->h_pinned) cudaFreeHost(c->h_pinned);
+    if (c->side) cudaStreamDestroy(c->side);
+    if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+    if (c->ev_join) cudaEventDestroy(c->ev_join);
     delete c;
     return TG_OK;
 }

@@ -860,15 +860,28 @@ __global__ void l2p_particles(int n, TreeView t, int log2L, const T4 *pf, const 
 // ------------------------------------------------------------------ scatter back to input order
 // acc4 holds four arrays of length stride4 (the evaluation's n in the plain path)
 __global__ void scatter_out(int n, const uint32_t *perm, const double *acc4, double *acc, int64_t stride, double *pot,
-                            const int *dn, int64_t stride4)
+                            const int *dn, int64_t stride4, const double *acc4b = nullptr)
 {
     n = dev_or(dn, n);
     for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
         const uint32_t q = perm[s];
-        acc[q] = acc4[s];
-        acc[stride + q] = acc4[(size_t)stride4 + s];
-        acc[2 * stride + q] = acc4[2 * (size_t)stride4 + s];
+        // acc4b (nullable): the P2P sums kept apart when P2P ran beside the far field (accelerations only)
+        acc[q] = acc4b ? acc4[s] + acc4b[s] : acc4[s];
+        acc[stride + q] = acc4b ? acc4[(size_t)stride4 + s] + acc4b[(size_t)stride4 + s] : acc4[(size_t)stride4 + s];
+        acc[2 * stride + q] =
+            acc4b ? acc4[2 * (size_t)stride4 + s] + acc4b[2 * (size_t)stride4 + s] : acc4[2 * (size_t)stride4 + s];
         if (pot) pot[q] = acc4[3 * (size_t)stride4 + s];
+    }
+}
+
+// zero the three acceleration rows of an acc4 array for the first dn[0] particles
+__global__ void zero_acc3(double *acc4, int64_t stride4, const int *dn)
+{
+    const int n = dn[0];
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
+        acc4[s] = 0.0;
+        acc4[(size_t)stride4 + s] = 0.0;
+        acc4[2 * (size_t)stride4 + s] = 0.0;
     }
 }
 
@@ -1394,6 +1407,31 @@ static tg_status fmm_eval_dev_t(tg_ctx *c, DevEval *de, const BatchCaps &cap, co
         ProfScope ps_(c, TG_K_UP);
         leaf_particles<T4><<<gcell, 256, 0, c->stream>>>(t, d_geom, xs2, ys2, zs2, ms2, pf, leaf_of);
     }
+    // float32: P2P needs only the walk's lists and the leaf offsets, so it runs on the side stream beside
+    // the moments, M2L and the downward pass, into its own sums (acc4p, added by scatter_out); its scan
+    // takes its own scratch slot.  The fork and join are events, which a stream capture turns into graph
+    // edges.
+    double *acc4p = nullptr;
+    const bool fork = sizeof(T) == 4;
+    if (fork) {
+        if ((st = ensure_t(c, B_ACC_P2P, (size_t)4 * cap.n, &acc4p))) return st;
+        cudaEventRecord(c->ev_fork, c->stream);
+        cudaStreamWaitEvent(c->side, c->ev_fork, 0);
+        cudaStream_t main_stream = c->stream;
+        c->stream = c->side;
+        {
+            ProfScope ps_(c, TG_K_OTHER);
+            zero_acc3<<<c->num_sms * 4, 256, 0, c->stream>>>(acc4p, cap.n, &de->n);
+        }
+        st = launch_p2p_f32_dev(c, t, de, d_geom, wctr, p2p, cap.p2p, cap.cells, reinterpret_cast<const float4 *>(pf),
+                                nslow, acc4p, cap.n, B_SCAN_TMP2);
+        c->stream = main_stream;
+        cudaEventRecord(c->ev_join, c->side);
+        if (st) {
+            cudaStreamWaitEvent(c->stream, c->ev_join, 0);
+            return st;
+        }
+    }
     {
         ProfScope ps_(c, TG_K_UP);
         p2m_leaves<T, T4><<<grid_for((int64_t)cap.cells * 32, 128), 128, 0, c->stream>>>(
@@ -1412,14 +1450,19 @@ static tg_status fmm_eval_dev_t(tg_ctx *c, DevEval *de, const BatchCaps &cap, co
     }
     if (sizeof(T) == 4) {
         uint32_t *fpre = nullptr;
-        if ((st = fast_prefix(c, fs2, cap.n, &fpre, de))) return st;
-        st = launch_m2l_f32_dev(c, t, de, d_geom, blocks, wctr + 1, (int64_t)cap.blocks, reinterpret_cast<const float *>(Ms),
-                                reinterpret_cast<float *>(L), p, ncp, cap.cells, cap.m2l_src, fpre);
+        st = fast_prefix(c, fs2, cap.n, &fpre, de);
+        if (!st)
+            st = launch_m2l_f32_dev(c, t, de, d_geom, blocks, wctr + 1, (int64_t)cap.blocks,
+                                    reinterpret_cast<const float *>(Ms), reinterpret_cast<float *>(L), p, ncp, cap.cells,
+                                    cap.m2l_src, fpre);
     } else {
         st = launch_m2l_f64_dev(c, t, de, d_geom, blocks, wctr + 1, (int64_t)cap.blocks,
                                 reinterpret_cast<const double *>(Ms), reinterpret_cast<double *>(L), p, ncp);
     }
-    if (st) return st;
+    if (st) {
+        if (fork) cudaStreamWaitEvent(c->stream, c->ev_join, 0);   // no unjoined work on the side stream
+        return st;
+    }
     for (int l = 1; l <= cap.levels; ++l) {
         ProfScope ps_(c, TG_K_DOWN);
         l2l_level<T><<<c->num_sms * 16, 32 * kM2MWarps, kM2MWarps * 2 * ncp * sizeof(T), c->stream>>>(
@@ -1439,15 +1482,16 @@ static tg_status fmm_eval_dev_t(tg_ctx *c, DevEval *de, const BatchCaps &cap, co
             l2p_fixed<6, T, T4, false><<<g, 128, 0, c->stream>>>(cap.n, t, d_geom, pf, leaf_of, fs2, 1, ncp, L, acc4, cap.n, de);
         }
     }
-    if (sizeof(T) == 4)
-        st = launch_p2p_f32_dev(c, t, de, d_geom, wctr, p2p, cap.p2p, cap.cells, reinterpret_cast<const float4 *>(pf),
-                                nslow, acc4, cap.n);
-    else
-        st = launch_p2p_f64_dev(c, t, d_geom, wctr, p2p, cap.p2p, reinterpret_cast<const dbl4 *>(pf), fs2, acc4, cap.n);
-    if (st) return st;
+    if (fork) {
+        cudaStreamWaitEvent(c->stream, c->ev_join, 0);
+    } else if ((st = launch_p2p_f64_dev(c, t, d_geom, wctr, p2p, cap.p2p, reinterpret_cast<const dbl4 *>(pf), fs2, acc4,
+                                         cap.n))) {
+        return st;
+    }
     {
         ProfScope ps_(c, TG_K_DOWN);
-        scatter_out<<<grid_for(cap.n, 256), 256, 0, c->stream>>>(cap.n, perm2, acc4, acc, cap.n, nullptr, &de->n, cap.n);
+        scatter_out<<<grid_for(cap.n, 256), 256, 0, c->stream>>>(cap.n, perm2, acc4, acc, cap.n, nullptr, &de->n, cap.n,
+                                                                  acc4p);
     }
     {
         ProfScope ps_(c, TG_K_OTHER);

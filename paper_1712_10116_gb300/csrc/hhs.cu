@@ -711,6 +711,8 @@ static tg_status hold_presize(tg_ctx *c, const Sched &s, const BatchCaps &cap, c
         {B_OWN_LIST, 8ull * max_units}, {B_OWN_TAG, 8 * cap.p2p}, {B_OWN_PART, 4 * cap.p2p},
         {B_M2L_CNT, 4ull * C}, {B_M2L_OFF, 4ull * C}, {B_M2L_FILL, 4ull * C}, {B_M2L_SRC, 4 * cap.m2l_src},
         {B_FWORDS, 4ull * (n + 1)}, {B_FPRE, 4ull * (n + 1)}, {B_M2L_PART, 16 * cap.blocks}, {B_M2L_PCNT, 16},
+        {B_SCAN_TMP2, 4 * std::max(scan_scratch_words(std::max(kSortBins * nblocks, 1)), std::max(scan_scratch_words(C), scan_scratch_words(n + 1)))},
+        {B_ACC_P2P, 32ull * n},
         {B_FRAME_X, 24ull * n}, {B_FRAME_M, 8ull * n}, {B_FRAME_F, 1ull * n}, {B_SPLIT_FLAG, 4ull * n},
         {B_SPLIT_PRE, 4ull * n}, {B_HOLD, sizeof(HoldState)}, {B_DEVEVAL, sizeof(DevEval)},
     };

@@ -484,7 +484,7 @@ tg_status launch_p2p_f32(tg_ctx *c, const TreeView &t, const uint2 *pairs, int64
 // come from the walk's counters, the cell count from de; buffers are sized for the capacities.
 tg_status launch_p2p_f32_dev(tg_ctx *c, const TreeView &t, const DevEval *de, const Geom *gp,
                              const unsigned long long *walk_ctr, const uint2 *p2p, size_t cap_p2p, int cap_cells,
-                             const float4 *pf, const int32_t *nslow, double *acc4, int stride)
+                             const float4 *pf, const int32_t *nslow, double *acc4, int stride, int scan_scratch)
 {
     tg_status st;
     uint32_t *own_cnt, *own_fill, *own_off, *ctr;
@@ -505,7 +505,7 @@ tg_status launch_p2p_f32_dev(tg_ctx *c, const TreeView &t, const DevEval *de, co
         zero_u32_dev<<<1, 32, 0, c->stream>>>(ctr, nullptr, 2);
         p2p_owner_count<<<g, 256, 0, c->stream>>>(p2p, (int64_t)cap_p2p, t.count, own_cnt, tagged, walk_ctr + 2);
     }
-    if ((st = exclusive_scan_u32(c, own_cnt, own_off, cap_cells, nullptr, &de->ncell))) return st;
+    if ((st = exclusive_scan_u32(c, own_cnt, own_off, cap_cells, nullptr, &de->ncell, scan_scratch))) return st;
     {
         ProfScope ps_(c, TG_K_OTHER);
         p2p_owner_fill<<<g, 256, 0, c->stream>>>(tagged, (int64_t)cap_p2p, own_off, own_fill, partners, units, ctr,

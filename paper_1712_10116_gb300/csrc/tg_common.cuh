@@ -85,6 +85,9 @@ constexpr int kMaxSlots = 96;   // capacity of tg_ctx::buf; the slot enum below 
 struct tg_ctx {
     tg_params prm;
     cudaStream_t stream = nullptr;
+    // the batched evaluation runs P2P on `side` beside M2L and the downward pass (fork and join events)
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     int device = 0;
     int num_sms = 0;
     tg::Err err;
@@ -150,7 +153,7 @@ enum Slot {
     B_HHS_SCAN, B_HHS_TMP, B_RED, B_DIAG_POT, B_DIAG_ACC,
     B_OWN_CNT, B_OWN_FILL, B_OWN_OFF, B_OWN_LIST, B_OWN_TAG, B_OWN_PART, B_SNAP, B_TUNE_ACC,
     B_MACP, B_DEVEVAL, B_HOLD, B_FRAME_X, B_FRAME_M, B_FRAME_F, B_SPLIT_FLAG, B_SPLIT_PRE,
-    B_M2L_CNT, B_M2L_OFF, B_M2L_FILL, B_M2L_SRC, B_FWORDS, B_FPRE, B_M2L_PART, B_M2L_PCNT, B_TUNE_SNAP,
+    B_M2L_CNT, B_M2L_OFF, B_M2L_FILL, B_M2L_SRC, B_FWORDS, B_FPRE, B_M2L_PART, B_M2L_PCNT, B_TUNE_SNAP, B_SCAN_TMP2, B_ACC_P2P,
     B_LAST_SLOT
 };
 static_assert(B_LAST_SLOT <= kMaxSlots, "tg_ctx::buf holds fewer entries than there are slots");
@@ -224,7 +227,7 @@ tg_status injected_alloc_failure(tg_ctx *c, size_t bytes, int slot);
 
 // Device-wide exclusive scan of uint32 (in place allowed); optional total to a device word.
 tg_status exclusive_scan_u32(tg_ctx *c, const uint32_t *in, uint32_t *out, int n, uint32_t *d_total,
-                             const int *dn = nullptr);
+                             const int *dn = nullptr, int scratch = B_SCAN_TMP);
 
 // ---- m2l.cu: mutual M2L of the walk's blocks into L (normalised expansions).  pot = false: the
 // float32 kernels leave out the potential term L^0.  fpre (kick pairs, nullable): prefix sum of the fast
@@ -248,7 +251,8 @@ tg_status launch_p2p_f32(tg_ctx *c, const TreeView &t, const uint2 *pairs, int64
                          int64_t nself, const float4 *pf, const int32_t *nslow, bool pot, double *acc4);
 tg_status launch_p2p_f32_dev(tg_ctx *c, const TreeView &t, const DevEval *de, const Geom *gp,
                              const unsigned long long *walk_ctr, const uint2 *p2p, size_t cap_p2p, int cap_cells,
-                             const float4 *pf, const int32_t *nslow, double *acc4, int stride);
+                             const float4 *pf, const int32_t *nslow, double *acc4, int stride,
+                             int scan_scratch = B_SCAN_TMP);
 tg_status launch_p2p_f64(tg_ctx *c, const TreeView &t, const Geom *d_geom, const uint2 *pairs, int64_t npairs,
                          const uint2 *self_pairs, int64_t nself, const dbl4 *pf, const uint8_t *fs, bool masked,
                          double *acc4);

@@ -236,18 +236,20 @@ size_t scan_scratch_words(int n)
     return need;
 }
 
-// Exclusive scan of n uint32 values (out may alias in).  The total is written to d_total
-// (device word) when it is not null.  Recursive over tile sums.  With dn (a device count) the first
+// Exclusive scan of n uint32 values (out may alias in), with its scratch in slot `scratch` (a scan on
+// another stream at the same time takes another slot).  The total is written to d_total (device word)
+// when it is not null.  Recursive over tile sums.  With dn (a device count) the first
 // level scans dn[0] <= n values; the launches are sized for n, and the tiles past dn[0] hand up
 // zero sums, so the upper levels need no device count.
-tg_status exclusive_scan_u32(tg_ctx *c, const uint32_t *in, uint32_t *out, int n, uint32_t *d_total, const int *dn)
+tg_status exclusive_scan_u32(tg_ctx *c, const uint32_t *in, uint32_t *out, int n, uint32_t *d_total, const int *dn,
+                             int scratch)
 {
     if (n <= 0) {
         if (d_total) cudaMemsetAsync(d_total, 0, sizeof(uint32_t), c->stream);
         return cuda_check(c, cudaGetLastError(), "exclusive scan");
     }
     uint32_t *tmp = nullptr;
-    tg_status st = ensure_t(c, B_SCAN_TMP, scan_scratch_words(n), &tmp);
+    tg_status st = ensure_t(c, scratch, scan_scratch_words(n), &tmp);
     if (st) return st;
     struct Level { uint32_t *out; int n, ntiles; uint32_t *sums, *pre; };
     Level lv[8];
