@@ -94,10 +94,12 @@ tg_status tg_create(const tg_params *params, void *cuda_stream, tg_ctx **out)
     }
     if (cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_walk, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess) {
         cudaGetLastError();
         if (c->side) cudaStreamDestroy(c->side);
         if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+        if (c->ev_walk) cudaEventDestroy(c->ev_walk);
         cudaFreeHost(c->h_pinned);
         cudaFree(c->d_counters);
         delete c;
@@ -122,6 +124,7 @@ tg_status tg_destroy(tg_ctx *c)
     if (c->h_pinned) cudaFreeHost(c->h_pinned);
     if (c->side) cudaStreamDestroy(c->side);
     if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+    if (c->ev_walk) cudaEventDestroy(c->ev_walk);
     if (c->ev_join) cudaEventDestroy(c->ev_join);
     delete c;
     return TG_OK;

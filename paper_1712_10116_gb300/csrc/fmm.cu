@@ -1363,19 +1363,29 @@ static tg_status fmm_eval_dev_t(tg_ctx *c, DevEval *de, const BatchCaps &cap, co
         (st = ensure_t(c, B_WALK_CNT, 8 + kWalkMaxSteps + 1, &wctr)))
         return st;
     const int nsteps = std::min(kWalkMaxSteps, cap.levels);
+    // the walk reads only the cells: it runs on the side stream beside the leaf passes and the moments
+    // (ev_walk marks its end for M2L), and P2P follows it there
+    cudaEventRecord(c->ev_fork, c->stream);
+    cudaStreamWaitEvent(c->side, c->ev_fork, 0);
     {
-        ProfScope ps_(c, TG_K_WALK);
-        walk_init_dev<<<1, 64, 0, c->stream>>>(de, f0, wctr, p2p, cap.p2p);
+        cudaStream_t main_stream = c->stream;
+        c->stream = c->side;
+        {
+            ProfScope ps_(c, TG_K_WALK);
+            walk_init_dev<<<1, 64, 0, c->stream>>>(de, f0, wctr, p2p, cap.p2p);
+        }
+        for (int s = 0; s < nsteps; ++s) {
+            WalkOut o{(s & 1) ? f0 : f1, blocks, p2p, wctr, wctr + 8 + s + 1, cap.front, cap.blocks, cap.p2p};
+            ProfScope ps_(c, TG_K_WALK);
+            walk_step_dev<<<c->num_sms * 4, 128, 0, c->stream>>>(t, mpd, (s & 1) ? f1 : f0, wctr + 8 + s, o);
+        }
+        {
+            ProfScope ps_(c, TG_K_WALK);
+            walk_check_dev<<<1, 1, 0, c->stream>>>(de, wctr, nsteps, cap.front, cap.blocks, cap.p2p);
+        }
+        c->stream = main_stream;
     }
-    for (int s = 0; s < nsteps; ++s) {
-        WalkOut o{(s & 1) ? f0 : f1, blocks, p2p, wctr, wctr + 8 + s + 1, cap.front, cap.blocks, cap.p2p};
-        ProfScope ps_(c, TG_K_WALK);
-        walk_step_dev<<<c->num_sms * 4, 128, 0, c->stream>>>(t, mpd, (s & 1) ? f1 : f0, wctr + 8 + s, o);
-    }
-    {
-        ProfScope ps_(c, TG_K_WALK);
-        walk_check_dev<<<1, 1, 0, c->stream>>>(de, wctr, nsteps, cap.front, cap.blocks, cap.p2p);
-    }
+    cudaEventRecord(c->ev_walk, c->side);
 
     // slow-first leaves, per-particle offsets, upward pass
     const double *xs = static_cast<const double *>(c->buf[B_XS].p), *ys = static_cast<const double *>(c->buf[B_YS].p),
@@ -1395,8 +1405,10 @@ static tg_status fmm_eval_dev_t(tg_ctx *c, DevEval *de, const BatchCaps &cap, co
         (st = ensure_t(c, B_NSLOW, cap.cells, &nslow)) || (st = ensure_t(c, B_PF, cap.n, &pf)) ||
         (st = ensure_t(c, B_LEAF_OF, cap.n, &leaf_of)) || (st = ensure_t(c, B_MOM, rows * ncp, &M)) ||
         (st = ensure_t(c, B_MOMF, rows * ncp, &Ms)) || (st = ensure_t(c, B_MOM01, rows * 4, &M01)) ||
-        (st = ensure_t(c, B_LOC, rows * ncp, &L)) || (st = ensure_t(c, B_ACC, (size_t)4 * cap.n, &acc4)))
+        (st = ensure_t(c, B_LOC, rows * ncp, &L)) || (st = ensure_t(c, B_ACC, (size_t)4 * cap.n, &acc4))) {
+        cudaStreamWaitEvent(c->stream, c->ev_walk, 0);   // no unjoined work on the side stream
         return st;
+    }
     const int gcell = grid_for((int64_t)cap.cells * 32, 256);
     {
         ProfScope ps_(c, TG_K_TREE);
@@ -1407,15 +1419,18 @@ static tg_status fmm_eval_dev_t(tg_ctx *c, DevEval *de, const BatchCaps &cap, co
         ProfScope ps_(c, TG_K_UP);
         leaf_particles<T4><<<gcell, 256, 0, c->stream>>>(t, d_geom, xs2, ys2, zs2, ms2, pf, leaf_of);
     }
-    // float32: P2P needs only the walk's lists and the leaf offsets, so it runs on the side stream beside
-    // the moments, M2L and the downward pass, into its own sums (acc4p, added by scatter_out); its scan
-    // takes its own scratch slot.  The fork and join are events, which a stream capture turns into graph
-    // edges.
+    // float32: P2P needs only the walk's lists and the leaf offsets, so it runs on the side stream (after
+    // the walk) beside the moments, M2L and the downward pass, into its own sums (acc4p, added by
+    // scatter_out); its scan takes its own scratch slot.  The forks and joins are events, which a stream
+    // capture turns into graph edges.
     double *acc4p = nullptr;
     const bool fork = sizeof(T) == 4;
     if (fork) {
-        if ((st = ensure_t(c, B_ACC_P2P, (size_t)4 * cap.n, &acc4p))) return st;
-        cudaEventRecord(c->ev_fork, c->stream);
+        if ((st = ensure_t(c, B_ACC_P2P, (size_t)4 * cap.n, &acc4p))) {
+            cudaStreamWaitEvent(c->stream, c->ev_walk, 0);
+            return st;
+        }
+        cudaEventRecord(c->ev_fork, c->stream);   // the leaf offsets; the side stream is past the walk
         cudaStreamWaitEvent(c->side, c->ev_fork, 0);
         cudaStream_t main_stream = c->stream;
         c->stream = c->side;
@@ -1431,6 +1446,8 @@ static tg_status fmm_eval_dev_t(tg_ctx *c, DevEval *de, const BatchCaps &cap, co
             cudaStreamWaitEvent(c->stream, c->ev_join, 0);
             return st;
         }
+    } else {
+        cudaEventRecord(c->ev_join, c->side);   // float64: P2P follows on the main stream
     }
     {
         ProfScope ps_(c, TG_K_UP);
@@ -1448,6 +1465,7 @@ static tg_status fmm_eval_dev_t(tg_ctx *c, DevEval *de, const BatchCaps &cap, co
                                                                                         &de->ncell);
         zero_rows_dev<T><<<c->num_sms * 4, 256, 0, c->stream>>>(L, &de->rows, ncp);
     }
+    cudaStreamWaitEvent(c->stream, c->ev_walk, 0);   // M2L reads the walk's blocks
     if (sizeof(T) == 4) {
         uint32_t *fpre = nullptr;
         st = fast_prefix(c, fs2, cap.n, &fpre, de);
@@ -1460,7 +1478,7 @@ static tg_status fmm_eval_dev_t(tg_ctx *c, DevEval *de, const BatchCaps &cap, co
                                 reinterpret_cast<const double *>(Ms), reinterpret_cast<double *>(L), p, ncp);
     }
     if (st) {
-        if (fork) cudaStreamWaitEvent(c->stream, c->ev_join, 0);   // no unjoined work on the side stream
+        cudaStreamWaitEvent(c->stream, c->ev_join, 0);   // no unjoined work on the side stream
         return st;
     }
     for (int l = 1; l <= cap.levels; ++l) {
@@ -1482,12 +1500,10 @@ static tg_status fmm_eval_dev_t(tg_ctx *c, DevEval *de, const BatchCaps &cap, co
             l2p_fixed<6, T, T4, false><<<g, 128, 0, c->stream>>>(cap.n, t, d_geom, pf, leaf_of, fs2, 1, ncp, L, acc4, cap.n, de);
         }
     }
-    if (fork) {
-        cudaStreamWaitEvent(c->stream, c->ev_join, 0);
-    } else if ((st = launch_p2p_f64_dev(c, t, d_geom, wctr, p2p, cap.p2p, reinterpret_cast<const dbl4 *>(pf), fs2, acc4,
-                                         cap.n))) {
+    cudaStreamWaitEvent(c->stream, c->ev_join, 0);
+    if (!fork && (st = launch_p2p_f64_dev(c, t, d_geom, wctr, p2p, cap.p2p, reinterpret_cast<const dbl4 *>(pf), fs2, acc4,
+                                         cap.n)))
         return st;
-    }
     {
         ProfScope ps_(c, TG_K_DOWN);
         scatter_out<<<grid_for(cap.n, 256), 256, 0, c->stream>>>(cap.n, perm2, acc4, acc, cap.n, nullptr, &de->n, cap.n,

@@ -85,9 +85,10 @@ constexpr int kMaxSlots = 96;   // capacity of tg_ctx::buf; the slot enum below 
 struct tg_ctx {
     tg_params prm;
     cudaStream_t stream = nullptr;
-    // the batched evaluation runs P2P on `side` beside M2L and the downward pass (fork and join events)
+    // the batched evaluation runs the walk and P2P on `side` beside the leaf passes, the moments, M2L and
+    // the downward pass (fork, walk-done and join events)
     cudaStream_t side = nullptr;
-    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_walk = nullptr, ev_join = nullptr;
     int device = 0;
     int num_sms = 0;
     tg::Err err;
