@@ -89,18 +89,44 @@ struct OwnerBatch {
     int inc[2][32];    // inclusive row counts over slots: [0] slow rows, [1] fast rows
 };
 
-// Columns are staged as [slow | pad to 8 | fast | pad to 8]; the pads are massless particles far away
-// (on the other side of the origin from the padding rows), so every batch of 8 columns is full.
+// Columns are staged in leaf order (slow first) and padded to a multiple of 8 with massless
+// particles far away (on the other side of the origin from the padding rows), so every batch of 8
+// columns is full.  Two neighbouring columns 2m, 2m+1 share two float4 slots, component-major:
+// q[2m] = (x0, x1, y0, y1), q[2m+1] = (z0, z1, m0, m1), so one shared load gives each coordinate of
+// both columns as a float2 and the pair arithmetic runs on packed float2 operations.
 constexpr int kOwnCols = kMaxNcrit + 16;
 
 struct OwnerShared {
-    float4 q[8][kOwnCols];       // owner's particles (columns), per warp
+    float4 q[8][kOwnCols];       // owner's particles (columns), per warp, in column pairs
     float acc[8][kOwnCols][4];   // owner's reaction sums (ax, ay, az, phi), per warp
     OwnerBatch b[8];
 };
 
+__device__ __forceinline__ void col_put(float4 *sq, int j, float4 v)
+{
+    float *f = reinterpret_cast<float *>(sq) + 8 * (j >> 1) + (j & 1);
+    f[0] = v.x;
+    f[2] = v.y;
+    f[4] = v.z;
+    f[6] = v.w;
+}
+
+__device__ __forceinline__ float4 col_get(const float4 *sq, int j)
+{
+    const float *f = reinterpret_cast<const float *>(sq) + 8 * (j >> 1) + (j & 1);
+    return make_float4(f[0], f[2], f[4], f[6]);
+}
+
+__device__ __forceinline__ void col_zero_mass(float4 *sq, int j) { reinterpret_cast<float *>(sq)[8 * (j >> 1) + 6 + (j & 1)] = 0.f; }
+
+__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
+
 // Rows i0 .. i0 + 32*ROWS of one phase (0: slow rows, 1: fast rows) against the first ncol staged
 // columns (a multiple of 8); the reaction sums of columns at or past nkeep are not kept.
+// Each row meets two columns per packed operation: a row keeps two partial sums per component (one
+// per column parity, added when the chunk is flushed); a column pair keeps its two columns' sums in
+// one float2 across the rows.  Every product and sum is rounded as in the scalar form; only the order
+// in which a row's sum is accumulated differs.
 template <int KERNEL, int ROWS, bool NEAR, bool POT>
 __device__ __noinline__ void owner_rows(const float4 *__restrict__ pf, const OwnerBatch *ob, int phase, int i0, int nrows,
                                         const float4 *sq, float (*sacc)[4], int ncol, int nkeep, float eps, double *acc4,
@@ -108,14 +134,14 @@ __device__ __noinline__ void owner_rows(const float4 *__restrict__ pf, const Own
 {
     const float eps2 = eps * eps, inv_eps = 1.0f / eps, inv_eps3 = inv_eps * inv_eps * inv_eps;
     const int *inc = ob->inc[phase];
-    float4 p[ROWS];
+    float2 nx[ROWS], ny[ROWS], nz[ROWS], nm[ROWS];   // -x, -y, -z, -m of each row, in both halves
     int gi[ROWS];
-    float ra[ROWS][4];
+    float2 ra[ROWS][4];
 #pragma unroll
     for (int r = 0; r < ROWS; ++r) {
         const int i = i0 + lane + 32 * r;
         gi[r] = -1;
-        p[r] = make_float4(1e8f, 1e8f, 1e8f, 0.f);   // far away, massless
+        float4 q = make_float4(1e8f, 1e8f, 1e8f, 0.f);   // far away, massless
         if (i < nrows) {
             // slot s: the first with inc[s] > i (inc is non-decreasing and inc[31] = nrows > i)
             int s = 0;
@@ -125,111 +151,143 @@ __device__ __noinline__ void owner_rows(const float4 *__restrict__ pf, const Own
             const int loc = i - (s ? inc[s - 1] : 0);
             gi[r] = ob->first[s] + (phase ? ob->nslow[s] : 0) + loc;
             const float4 o = ob->off[s];
-            float4 q = pf[gi[r]];
+            q = pf[gi[r]];
             q.x += o.x;
             q.y += o.y;
             q.z += o.z;
-            p[r] = q;
         }
-        ra[r][0] = ra[r][1] = ra[r][2] = ra[r][3] = 0.f;
+        nx[r] = f2(-q.x, -q.x);
+        ny[r] = f2(-q.y, -q.y);
+        nz[r] = f2(-q.z, -q.z);
+        nm[r] = f2(-q.w, -q.w);
+#pragma unroll
+        for (int comp = 0; comp < 4; ++comp) ra[r][comp] = f2(0.f, 0.f);
     }
     // Wendland C2 and a partner closer than eps: the pair value is first taken at max(r, eps), where
     // it equals the Newtonian one, and pairs with r < eps are corrected after the batch (rare).
     constexpr bool CLAMP = NEAR && KERNEL == TG_KERNEL_WENDLAND_C2;
-    // columns in batches of 8; lane l visits column c ^ ((l >> 2) & 7) of a batch (see p2p_pair_f32)
-    const int cperm = (lane >> 2) & 7;
+    // columns in batches of 8 (4 pairs); lane l visits pair m ^ ((l >> 3) & 3) at step m, so the first
+    // two stages of the reduce-scatter below need no selects
+    const int pperm = (lane >> 3) & 3;
     for (int j0 = 0; j0 < ncol; j0 += 8) {
-        float col[32];
+        float2 col[4][4];   // [step][component]: (even column, odd column) of the pair visited at that step
         bool close = false;
 #pragma unroll
-        for (int c = 0; c < 8; ++c) {
-            const float4 q = sq[j0 + (c ^ cperm)];
-            float cx = 0.f, cy = 0.f, cz = 0.f, cp = 0.f;
+        for (int m = 0; m < 4; ++m) {
+            const int jp = (j0 >> 1) + (m ^ pperm);
+            const float4 qa = sq[2 * jp], qb = sq[2 * jp + 1];
+            const float2 qx = f2(qa.x, qa.y), qy = f2(qa.z, qa.w), qz = f2(qb.x, qb.y), qm = f2(qb.z, qb.w);
+            float2 cx = f2(0.f, 0.f), cy = cx, cz = cx, cp = cx;
 #pragma unroll
             for (int r = 0; r < ROWS; ++r) {
-                const float dx = q.x - p[r].x, dy = q.y - p[r].y, dz = q.z - p[r].z;
-                const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                float gk, ph;
-                if (CLAMP) {
-                    close |= r2 < eps2;
-                    const float ri = rsqrt_ftz(fmaxf(r2, eps2));
-                    ph = -ri;
-                    gk = ri * ri * ri;
+                const float2 dx = __fadd2_rn(qx, nx[r]), dy = __fadd2_rn(qy, ny[r]), dz = __fadd2_rn(qz, nz[r]);
+                const float2 r2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __fmul2_rn(dz, dz)));
+                float2 ri;
+                if (KERNEL == TG_KERNEL_PLUMMER) {
+                    ri = f2(tg_rsqrt<float>(r2.x + eps2), tg_rsqrt<float>(r2.y + eps2));
+                } else if (CLAMP) {
+                    close |= (r2.x < eps2) | (r2.y < eps2);
+                    ri = f2(rsqrt_ftz(fmaxf(r2.x, eps2)), rsqrt_ftz(fmaxf(r2.y, eps2)));
                 } else {
-                    pair_kernel_f32<KERNEL, false>(r2, eps, eps2, inv_eps, inv_eps3, gk, ph);
+                    ri = f2(rsqrt_ftz(r2.x), rsqrt_ftz(r2.y));   // far pairs: r2 >= eps^2
                 }
-                const float mq = q.w * gk, mp = p[r].w * gk;
-                ra[r][0] = fmaf(mq, dx, ra[r][0]);
-                ra[r][1] = fmaf(mq, dy, ra[r][1]);
-                ra[r][2] = fmaf(mq, dz, ra[r][2]);
-                if (POT) ra[r][3] = fmaf(q.w, ph, ra[r][3]);
-                cx = fmaf(-mp, dx, cx);
-                cy = fmaf(-mp, dy, cy);
-                cz = fmaf(-mp, dz, cz);
-                if (POT) cp = fmaf(p[r].w, ph, cp);
+                // g = ri^3, phi = -ri (a row keeps its potential sum negated and flips it at the flush; a column
+                // pair's potential sum, -m_row * ri, has its own sign)
+                const float2 g = __fmul2_rn(__fmul2_rn(ri, ri), ri);
+                const float2 mq = __fmul2_rn(qm, g), nmp = __fmul2_rn(nm[r], g);
+                ra[r][0] = __ffma2_rn(mq, dx, ra[r][0]);
+                ra[r][1] = __ffma2_rn(mq, dy, ra[r][1]);
+                ra[r][2] = __ffma2_rn(mq, dz, ra[r][2]);
+                if (POT) ra[r][3] = __ffma2_rn(qm, ri, ra[r][3]);
+                cx = __ffma2_rn(nmp, dx, cx);
+                cy = __ffma2_rn(nmp, dy, cy);
+                cz = __ffma2_rn(nmp, dz, cz);
+                if (POT) cp = __ffma2_rn(nm[r], ri, cp);
             }
-            col[4 * c + 0] = cx;
-            col[4 * c + 1] = cy;
-            col[4 * c + 2] = cz;
-            col[4 * c + 3] = cp;
+            col[m][0] = cx;
+            col[m][1] = cy;
+            col[m][2] = cz;
+            col[m][3] = cp;
         }
         if (CLAMP && __any_sync(0xffffffffu, close)) {
             // exact softened value minus the clamped one, for the pairs with r < eps; rows in registers,
             // columns straight into the shared sums (before the batch's own column sums are added)
 #pragma unroll 1
             for (int c = 0; c < 8; ++c) {
-                const int j = j0 + (c ^ cperm);
-                const float4 q = sq[j];
+                const int j = j0 + c;
+                const float4 q = col_get(sq, j);
 #pragma unroll
                 for (int r = 0; r < ROWS; ++r) {
-                    const float dx = q.x - p[r].x, dy = q.y - p[r].y, dz = q.z - p[r].z;
+                    const float dx = q.x + nx[r].x, dy = q.y + ny[r].x, dz = q.z + nz[r].x;
                     const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
                     if (r2 < eps2) {
                         const float ri = rsqrtf(eps2);
                         float g, ph;
                         pair_kernel<float, TG_KERNEL_WENDLAND_C2>(r2, eps, eps2, inv_eps, inv_eps3, g, ph);
                         const float dg = g - ri * ri * ri, dph = ph + ri;
-                        const float mq = q.w * dg, mp = p[r].w * dg;
-                        ra[r][0] = fmaf(mq, dx, ra[r][0]);
-                        ra[r][1] = fmaf(mq, dy, ra[r][1]);
-                        ra[r][2] = fmaf(mq, dz, ra[r][2]);
-                        if (POT) ra[r][3] = fmaf(q.w, dph, ra[r][3]);
+                        const float mq = q.w * dg, mp = -nm[r].x * dg;
+                        ra[r][0].x = fmaf(mq, dx, ra[r][0].x);
+                        ra[r][1].x = fmaf(mq, dy, ra[r][1].x);
+                        ra[r][2].x = fmaf(mq, dz, ra[r][2].x);
+                        if (POT) ra[r][3].x = fmaf(q.w, -dph, ra[r][3].x);
                         if (j < nkeep) {
                             atomicAdd(&sacc[j][0], -mp * dx);
                             atomicAdd(&sacc[j][1], -mp * dy);
                             atomicAdd(&sacc[j][2], -mp * dz);
-                            if (POT) atomicAdd(&sacc[j][3], p[r].w * dph);
+                            if (POT) atomicAdd(&sacc[j][3], -nm[r].x * dph);
                         }
                     }
                 }
             }
             __syncwarp();
         }
+        // reduce-scatter of the 8 columns x 4 components over the warp; lane l ends with column
+        // j0 + l/4, component l%4.  Pair bits (partners l^16, l^8) without selects ...
 #pragma unroll
-        for (int h = 16; h >= 4; h >>= 1)
+        for (int m = 0; m < 2; ++m)
 #pragma unroll
-            for (int q = 0; q < h; ++q)
-                if (POT || (q & 3) != 3)   // without the potential, slots 4c + 3 stay zero
-                    col[q] += __shfl_xor_sync(0xffffffffu, col[q + h], h);
+            for (int comp = 0; comp < (POT ? 4 : 3); ++comp)
+                col[m][comp] = __fadd2_rn(col[m][comp], f2(__shfl_xor_sync(0xffffffffu, col[m + 2][comp].x, 16),
+                                                            __shfl_xor_sync(0xffffffffu, col[m + 2][comp].y, 16)));
+#pragma unroll
+        for (int comp = 0; comp < (POT ? 4 : 3); ++comp)
+            col[0][comp] = __fadd2_rn(col[0][comp], f2(__shfl_xor_sync(0xffffffffu, col[1][comp].x, 8),
+                                                        __shfl_xor_sync(0xffffffffu, col[1][comp].y, 8)));
+        // ... column parity (l^4), then the component bits (l^2, l^1), with selects
+        float v[4];
+        {
+            const bool hi = (lane & 4) != 0;
+#pragma unroll
+            for (int comp = 0; comp < 4; ++comp) {
+                if (!POT && comp == 3) {
+                    v[3] = 0.f;
+                    continue;
+                }
+                const float send = hi ? col[0][comp].x : col[0][comp].y;
+                const float keep = hi ? col[0][comp].y : col[0][comp].x;
+                v[comp] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+            }
+        }
 #pragma unroll
         for (int h = 2; h >= 1; h >>= 1) {
             const bool hi = (lane & h) != 0;
 #pragma unroll
             for (int q = 0; q < h; ++q) {
-                const float send = hi ? col[q] : col[q + h];
-                const float keep = hi ? col[q + h] : col[q];
-                col[q] = keep + __shfl_xor_sync(0xffffffffu, send, h);
+                const float send = hi ? v[q] : v[q + h];
+                const float keep = hi ? v[q + h] : v[q];
+                v[q] = keep + __shfl_xor_sync(0xffffffffu, send, h);
             }
         }
-        // lane l holds column j0 + l/4, component l%4; each (column, component) has one lane
-        if (j0 + (lane >> 2) < nkeep) sacc[j0 + (lane >> 2)][lane & 3] += col[0];
+        if (j0 + (lane >> 2) < nkeep) sacc[j0 + (lane >> 2)][lane & 3] += v[0];
     }
 #pragma unroll
     for (int r = 0; r < ROWS; ++r)
-        if (gi[r] >= 0)
+        if (gi[r] >= 0) {
+            const float s[4] = {ra[r][0].x + ra[r][0].y, ra[r][1].x + ra[r][1].y, ra[r][2].x + ra[r][2].y,
+                                -(ra[r][3].x + ra[r][3].y)};
 #pragma unroll
-            for (int comp = 0; comp < (POT ? 4 : 3); ++comp)
-                atomicAdd(&acc4[(size_t)comp * n + gi[r]], f2d_exact(ra[r][comp]));
+            for (int comp = 0; comp < (POT ? 4 : 3); ++comp) atomicAdd(&acc4[(size_t)comp * n + gi[r]], f2d_exact(s[comp]));
+        }
 }
 
 __device__ __forceinline__ int warp_incl_scan(int v, int lane)
@@ -360,7 +418,7 @@ __global__ void __launch_bounds__(256, 2) p2p_owner_f32(TreeView t, int log2L, c
                 if (nstage == 0) continue;
                 __syncwarp();
                 for (int j = lane; j < nstage; j += 32) {
-                    sq[j] = j < nbc ? pf[fb + jc + j] : make_float4(-1e8f, -1e8f, -1e8f, 0.f);
+                    col_put(sq, j, j < nbc ? pf[fb + jc + j] : make_float4(-1e8f, -1e8f, -1e8f, 0.f));
                     sacc[j][0] = sacc[j][1] = sacc[j][2] = sacc[j][3] = 0.f;
                 }
                 __syncwarp();
@@ -372,7 +430,7 @@ __global__ void __launch_bounds__(256, 2) p2p_owner_f32(TreeView t, int log2L, c
                     // fast rows meet the slow columns only: the batch that holds the first fast columns runs
                     // with their masses at zero (no force on the rows) and their reaction sums dropped
                     __syncwarp();
-                    for (int j = nsc + lane; j < ns8; j += 32) sq[j].w = 0.f;
+                    for (int j = nsc + lane; j < ns8; j += 32) col_zero_mass(sq, j);
                     __syncwarp();
                     for (int i0 = 0; i0 < Tf; i0 += 32 * ROWS) {
                         if (i0 < nearF) owner_rows<KERNEL, ROWS, true, POT>(pf, ob, 1, i0, Tf, sq, sacc, ns8, nsc, eps, acc4, n, lane);
