@@ -211,10 +211,11 @@ __device__ __noinline__ void owner_rows(const float4 *__restrict__ pf, const Own
         }
         if (CLAMP && __any_sync(0xffffffffu, close)) {
             // exact softened value minus the clamped one, for the pairs with r < eps; rows in registers,
-            // columns straight into the shared sums (before the batch's own column sums are added)
+            // columns straight into the shared sums (before the batch's own column sums are added).  Lane l
+            // takes column c ^ ((l >> 2) & 7) at step c, so at most 4 lanes add to one column's sums at once.
 #pragma unroll 1
             for (int c = 0; c < 8; ++c) {
-                const int j = j0 + c;
+                const int j = j0 + (c ^ ((lane >> 2) & 7));
                 const float4 q = col_get(sq, j);
 #pragma unroll
                 for (int r = 0; r < ROWS; ++r) {
