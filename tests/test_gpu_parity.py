@@ -260,6 +260,33 @@ def test_fmm_fp32_wide_softening(kind, masked):
     assert np.abs(pot.cpu().numpy() - p_o).max() < FP32_TOL * np.abs(p_o).max()
 
 
+@pytest.mark.parametrize("rows", [1, 2, 3])
+@pytest.mark.parametrize("kernel", [0, 1])
+@pytest.mark.parametrize("masked", [False, True])
+def test_p2p_rows_per_lane_match_oracle(rows, kernel, masked):
+    # every rows-per-lane variant of the float32 P2P that the autotuner may choose, with and without the
+    # potential: wide Wendland softening puts many pairs of neighbouring leaves inside eps (the clamped
+    # pairs and their correction), and the mask adds the fast-row pass over the slow columns
+    n = 9000
+    pos, _, mass = _case("clustered", n)
+    fast = ics.random_fast_mask(n, 23) if masked else None
+    prm = tg.Params(p=5, theta=0.5, eps=0.1 if kernel == 0 else 0.01, kernel=kernel, precision=tg.TG_PREC_FP32,
+                    n_crit=64)
+    s = tg.Solver(prm)
+    t = tg.tg_get_tuning(s.ctx)
+    t["p2p_rows"] = rows
+    tg.tg_set_tuning(s.ctx, t)
+    assert tg.tg_get_tuning(s.ctx)["p2p_rows"] == rows
+    a_o, p_o = oracle.fmm(pos, mass, _oprm(prm), fast)
+    fs = None if fast is None else _t(fast, torch.uint8)
+    for want_pot in (False, True):
+        acc, pot = s.fmm_forces(_t(pos), _t(mass), fs, want_pot=want_pot)
+        _check_fp32(acc.cpu().numpy(), a_o, f"rows {rows} kernel {kernel} masked {masked} pot {want_pot}")
+        if want_pot:
+            assert np.abs(pot.cpu().numpy() - p_o).max() < FP32_TOL * np.abs(p_o).max()
+    s.close()
+
+
 @pytest.mark.parametrize("kind,kernel,p", [("sphere", 0, 6), ("plummer", 1, 5), ("clustered", 0, 4)])
 @pytest.mark.parametrize("masked", [False, True])
 def test_fmm_fp32_forces_only(kind, kernel, p, masked):
