@@ -107,7 +107,7 @@ def _mi(p):
 
 @functools.lru_cache(maxsize=None)
 def _dfuncs(p):
-    import sympy as sp
+    sp = pytest.importorskip("sympy")
     x, y, z, s2 = sp.symbols("x y z s2", real=True)
     G = -1 / sp.sqrt(x ** 2 + y ** 2 + z ** 2 + s2)
     out = {}
