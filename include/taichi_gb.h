@@ -256,8 +256,10 @@ tg_status tg_debug_control(tg_ctx *ctx, int what, int64_t value);
  * warm-up, best of two) for candidate settings and keeps the fastest in the context:
  *   n_crit            leaf size: 48, 64, 80, 96, 112, 128, 160, 192 (the tree, and so the results, change within
  *                     the FMM's own accuracy; params.n_crit of the context is replaced)
- *   p2p_rows          rows per lane of the float32 P2P tile: 1, 2, 3 (results unchanged)
- *   m2l_blocks_per_sm grid of the float32 M2L kernel in blocks per SM: 4, 8, 16, 32 (results unchanged)
+ *   p2p_rows          rows per lane of the float32 P2P tile: 1, 2, 3 (the same pairs and terms; the float32
+ *                     sums are added in another order, so results change only by rounding)
+ *   m2l_blocks_per_sm grid of the float32 M2L kernel in blocks per SM: 4, 8, 16, 32 (the same terms; only the
+ *                     order of the float32 atomics changes)
  *   m2l_form          float32 M2L with the harmonic set (Wendland kernel): 0 mutual (the default), a
  *                     lane per cell pair of a block, both sides combined across lanes; 1 directed, a
  *                     warp per target cell over its sources (the same terms, summed in another order)
