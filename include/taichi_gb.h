@@ -14,7 +14,10 @@
  *   - G = 1; potentials are negative (-m/r far from a mass).
  *   - The context owns all scratch memory (tree, lists, expansions) and grows it on demand.
  *   - All work is issued on the CUDA stream given to tg_create.  Calls return when the work is
- *     enqueued, except where a call is documented as synchronising.
+ *     enqueued, except where a call is documented as synchronising.  Inside a batched HOLD step the
+ *     dual walk and P2P of each evaluation run on a second stream that the context creates and owns;
+ *     it forks from and joins the caller's stream with events, so to the caller all the work is
+ *     ordered on its own stream.
  *   - Errors are returned as tg_status codes; no exception crosses the ABI.  On an argument
  *     error nothing is launched and outputs are untouched.  tg_last_error() gives a message.
  *   - A context is not thread-safe; use one context per host thread.
@@ -107,7 +110,8 @@ typedef struct {
 } tg_stats;
 
 /* Create a context bound to `cuda_stream` (a cudaStream_t, NULL = legacy default stream) on the
- * current device.  Validates params (TG_ERR_ARG).  Allocates only small control blocks. */
+ * current device.  Validates params (TG_ERR_ARG).  Allocates only small control blocks, plus the
+ * context's own non-blocking side stream and three events (TG_ERR_CUDA if they cannot be created). */
 tg_status tg_create(const tg_params *params, void *cuda_stream, tg_ctx **out);
 tg_status tg_destroy(tg_ctx *ctx);
 const char *tg_last_error(const tg_ctx *ctx);
